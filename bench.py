@@ -1,0 +1,374 @@
+"""Benchmark: F+J evaluations/s on the 70,000-bus synthetic grid (one GPU per rank).
+
+One step = one fused evaluation of the bus mismatches F and the Jacobian
+values J (tasks 1 and 2 of Newton power flow) at one of 10 Newton-like
+states, through the library's C ABI.  Inputs are resident in HBM; the L2
+cache (129 MB) is flushed by writing a 512 MB buffer between timed steps,
+outside the timed events.  Each step's evaluation is a captured CUDA graph
+(k_phasor + k_fused) replayed on the timing stream.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun every rank evaluates its own replica (the single-grid path
+does not shard); value = evaluations of all ranks / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gridgen  # noqa: E402
+
+N_STATES = 10
+FLUSH_BYTES = 512 << 20
+METRIC = "F+J evals/s on 70k-bus grid"
+WORKLOAD = ("70k-bus seeded synthetic grid (70,000 buses, 88,000 branches, 7,000 PV, 50,000 PQ loads, "
+            "3,000 shunts, 12% transformers), reduced polar formulation, FP64, 10 perturbed states")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20000)
+    p.add_argument("--warmup", type=int, default=200)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--e2e-steps", type=int, default=400)
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--profile", action="store_true",
+                   help="only run warmup + steps evaluations of the workload (for ncu), no timing")
+    return p.parse_args()
+
+
+def run_profile(args):
+    """A few plain evaluations of the bench workload, for an ncu capture."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_11880_gb300 import Context
+    sys_ = gridgen.grid_70k()
+    ctx = Context(sys_, "reduced")
+    X = [torch.from_numpy(gridgen.perturbed_state(sys_, k)).cuda() for k in range(1, N_STATES + 1)]
+    F, V = ctx.empty_f(), ctx.empty_vals()
+    for k in range(args.warmup + args.steps):
+        ctx.residual_jacobian(X[k % N_STATES], F, V)
+    torch.cuda.synchronize()
+    ctx.check_device()
+    print(f"profile run: {args.warmup + args.steps} evaluations, n_f={ctx.dims.n_f}, nnz={ctx.dims.nnz}")
+    return 0
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# algorithmic work per evaluation ("Roofline")
+# --------------------------------------------------------------------------
+
+def algorithmic_bytes(d, n_pv, n_load, n_shunt):
+    """Bytes the evaluation must move at least: read the state (theta, V),
+    the branch parameters (from, to: int32; r, x, b, tap, shift: FP64), the
+    PQ / PV / shunt models (bus int32 + 2 or 1 FP64 each), write F and J."""
+    n, m = d.n_bus, d.n_branch
+    read = 16 * n + m * (8 + 5 * 8) + n_load * 20 + n_pv * 12 + n_shunt * 20
+    write = 8 * (d.n_f + d.nnz)
+    return read + write
+
+
+def algorithmic_fp64_flops(d):
+    """FP64 flops of the rotated polar form: 16 operations per branch end
+    (4 multiplies + 6 FMAs + 4 multiplies + 2 adds; an FMA counts 2 flops:
+    22 flops), 11 per bus for F and the diagonal (9 of them FMA: 20 flops)
+    and one sin/cos pair per bus, counted as 2 x 8 FLOPs (a degree-7
+    polynomial each)."""
+    return d.n_inc * 22 + d.n_bus * (20 + 16)
+
+
+# --------------------------------------------------------------------------
+# reference arm: the CPU oracle on the host cores
+# --------------------------------------------------------------------------
+
+def time_oracle(sys_, states, seconds, reduced=True):
+    import oracle
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        x = states[n % len(states)]
+        oracle.residual(sys_, x)
+        oracle.jacobian(sys_, x)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or n >= 1000:
+            return n / el, n, el
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    sys_ = gridgen.grid_70k()
+    states = [gridgen.perturbed_state(sys_, k) for k in range(1, N_STATES + 1)]
+    total_steps = args.warmup + args.steps
+    budget = min(max(args.cpu_seconds, 5.0), 120.0)
+    rate, n, el = time_oracle(sys_, states, budget)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / rate,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"{n} oracle F+J evaluations"},
+        "e2e": {"value": rate, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "cpu_baseline": {"value": rate, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{n} F+J evaluations of the 70k grid ({el:.1f} s, numpy FP64, "
+                                   f"one thread; requested {total_steps} steps bounded to {budget:.0f} s)"},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.profile:
+        return run_profile(args)
+    if args.impl == "reference":
+        if world > 1 and "RANK" in os.environ:
+            world = int(os.environ["WORLD_SIZE"])
+        return run_reference(args, rank, max(world, 1))
+
+    import torch
+    import torch.distributed as dist
+
+    distributed = "RANK" in os.environ and int(os.environ.get("WORLD_SIZE", "1")) > 1
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if distributed:
+        dist.init_process_group("nccl", device_id=dev)
+    world = dist.get_world_size() if distributed else 1
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_11880_gb300 import Context
+
+    sys_ = gridgen.grid_70k()
+    states_np = [gridgen.perturbed_state(sys_, k) for k in range(1, N_STATES + 1)]
+    ctx = Context(sys_, "reduced")
+    d = ctx.dims
+    X = torch.from_numpy(np.stack(states_np)).to(dev)
+    F = torch.empty(d.n_f, dtype=torch.float64, device=dev)
+    V = torch.empty(d.nnz, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    with torch.cuda.stream(stream):
+        tuning = ctx.autotune(X[0], F, V)
+        # one graph per state: k_phasor + k_fused
+        graphs = []
+        for k in range(N_STATES):
+            ctx.residual_jacobian(X[k], F, V)          # warm the kernels before capture
+        torch.cuda.synchronize()
+        for k in range(N_STATES):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                ctx.residual_jacobian(X[k], F, V)
+            graphs.append(g)
+    torch.cuda.synchronize()
+
+    def step(k):
+        graphs[k % N_STATES].replay()
+
+    K, W = args.steps, max(args.warmup, 3)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    with torch.cuda.stream(stream):
+        for k in range(W):
+            flush.fill_(float(k))
+            step(k)
+    torch.cuda.synchronize()
+    if distributed:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    sampler.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        flush.fill_(-1.0)                          # lead work so the host runs ahead of the GPU
+        for k in range(K):
+            flush.fill_(float(k))
+            ev0[k].record(stream)
+            step(k)
+            ev1[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if distributed:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    step_ms = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])
+    t_sum = float(step_ms.sum()) / 1000.0
+    t = torch.tensor([t_sum], dtype=torch.float64, device=dev)
+    if distributed:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    value = world * K / t_max
+    ms_per_step = 1000.0 * t_max / K
+
+    # ---- end to end through the host-buffer entry point ----
+    E = min(args.e2e_steps, K)
+    xh = torch.from_numpy(np.stack(states_np)).pin_memory().numpy()
+    Fh = torch.empty(d.n_f, dtype=torch.float64).pin_memory().numpy()
+    Vh = torch.empty(d.nnz, dtype=torch.float64).pin_memory().numpy()
+    with torch.cuda.stream(stream):
+        for k in range(3):
+            ctx.residual_jacobian_host(xh[k], Fh, Vh, stream=stream)
+        e2e_t = 0.0
+        for k in range(E):
+            flush.fill_(float(k))
+            stream.synchronize()
+            t0 = time.perf_counter()
+            ctx.residual_jacobian_host(xh[k % N_STATES], Fh, Vh, stream=stream)
+            e2e_t += time.perf_counter() - t0
+    te = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
+    if distributed:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * E / float(te.item())
+
+    # ---- correctness spot check of the timed outputs (last state) against a fresh call ----
+    Fc, Vc = ctx.residual_jacobian(X[(K - 1) % N_STATES])
+    graphs[(K - 1) % N_STATES].replay()
+    torch.cuda.synchronize()
+    assert torch.equal(Fc, F) and torch.equal(Vc, V), "graph replay differs from a direct call"
+    ctx.check_device()
+
+    peaks, peak_kind = load_peaks()
+    n_pv, n_load, n_shunt = sys_.n_pv, sys_.load_bus.shape[0], sys_.sh_bus.shape[0]
+    bytes_alg = algorithmic_bytes(d, n_pv, n_load, n_shunt)
+    flops_alg = algorithmic_fp64_flops(d)
+    fp64_peak_tflops = 152 * 2 * 2 * (peaks.get("sm_max_mhz", 2070.0) * 1e6) / 1e12   # 2 DFMA/clk/SM
+    eval_s = t_max / K
+    achieved_tf = flops_alg / eval_s / 1e12
+    achieved_gbs = bytes_alg / eval_s / 1e9
+    frac_alu = achieved_tf / fp64_peak_tflops
+    frac_hbm = achieved_gbs / peaks["hbm_gbs"]
+    traffic = load_traffic()
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                "frac": frac_alu, "traffic": traffic,
+                "kernel": "k_phasor + k_fused (one evaluation)",
+                "peak_kind": "FP64 derived: 152 SMs x 2 DFMA/clk x 2 flops x max SM clock",
+                "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": peaks["hbm_gbs"], "frac": frac_hbm,
+                        "peak_kind": peak_kind, "algorithmic_bytes": bytes_alg}}
+
+    cpu = None
+    if rank == 0:
+        rate, n, el = time_oracle(sys_, states_np, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "evals/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n} F+J evaluations of the 70k grid in {el:.1f} s (numpy FP64, one thread)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_f": d.n_f, "nnz": d.nnz, "states": N_STATES,
+                   "l2": "flushed between timed steps (512 MB write, outside the timed events)",
+                   "tuning": tuning, "timed_region_wall_s": wall, "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": 8 * d.n_x,
+                "d2h_bytes_per_step": 8 * (d.n_f + d.nnz), "steps": E},
+        "gpu_launches": 2 * K,
+        "roofline": roofline,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if distributed:
+        dist.destroy_process_group()
+    return 0
+
+
+def load_traffic():
+    """DRAM bytes per evaluation from the committed ncu summary, if present."""
+    path = os.path.join(ROOT, "profiles", "traffic_70k.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh).get("dram_bytes_per_eval")
+    except Exception:
+        return None
+
+
+if __name__ == "__main__":
+    sys.exit(main())

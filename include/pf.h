@@ -1,0 +1,263 @@
+/*
+ * pf.h -- C ABI of the GB300 power-flow residual / Jacobian library (libpf.so).
+ *
+ * Tasks (1) and (2) of Newton power flow (Sec. I): evaluate the bus power
+ * mismatches F(theta, V) and the nonzero values of their Jacobian J in a
+ * fixed sparsity pattern, for the models of Sec. II-A (Bus, PQ load, PV
+ * generator, Slack, Line / two-winding transformer, Shunt) in either the
+ * extended formulation of Eqs. (1)-(3) or the classic reduced one.
+ *
+ * Conventions shared by every entry point
+ *   - Floating point is IEEE binary64 throughout; indices are int32 unless
+ *     noted; offsets into batched vectors are int64.
+ *   - Per-unit quantities, angles in radians.
+ *   - Residual sign: F = power flowing out of the bus into its branches
+ *     + shunt consumption + load - generation (the sign of Eq. 4, where
+ *     P_h leaves bus h).
+ *   - Branch model (Eq. 4 extended with reactive power, tap and shift):
+ *     g + jb = 1/(r + jx), charging b_c split b_c/2 per end, end
+ *     conductances g_fr, g_to, tap tau and shift phi on the from side,
+ *     delta = theta_f - theta_t - phi:
+ *       P_f =  V_f^2 (g+g_fr)/tau^2     - (V_f V_t/tau)(g cos d + b sin d)
+ *       Q_f = -V_f^2 (b+b_c/2)/tau^2    - (V_f V_t/tau)(g sin d - b cos d)
+ *       P_t =  V_t^2 (g+g_to)           - (V_f V_t/tau)(g cos d - b sin d)
+ *       Q_t = -V_t^2 (b+b_c/2)          + (V_f V_t/tau)(g sin d + b cos d)
+ *   - State vector x of one instance: [theta(N), V(N)] and, in the extended
+ *     formulation, [Q_g (PV units in input order, then the slack), P_s]
+ *     (Eq. 3).  In the reduced formulation x still carries every theta and
+ *     V; the slack angle and the PV / slack magnitudes are read as fixed.
+ *   - Reduced rows / columns: P / theta of the non-slack buses in ascending
+ *     bus order, then Q / V of the PQ-type buses in ascending bus order.
+ *     Extended rows: [g_p(N), g_q(N), g_V(gens), g_theta] (Eq. 2); columns
+ *     [theta(N), V(N), Q_g(gens), P_s] (Eq. 3); g_V = V - Vset and
+ *     g_theta = theta_s - theta_set.
+ *   - The J pattern is the structural union of every model's entries: CSR,
+ *     ascending columns, parallel branches merged, the four diagonal
+ *     entries of a bus always present when their row and column exist,
+ *     out-of-service / masked branches kept as explicit zeros.
+ *   - Results are deterministic: every F row and J value is a sum in a fixed
+ *     order (no floating-point atomics), identical run to run and for every
+ *     tuning choice.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Evaluation calls are asynchronous on that stream, allocate
+ *     nothing and may be captured in a CUDA graph; device buffers passed to
+ *     them must stay valid until the stream reaches the call.
+ *   - Every function returns PF_OK (0) or an error code; pf_last_error()
+ *     returns a message for the calling thread's last failure.
+ */
+#ifndef PF_H
+#define PF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define PF_API __attribute__((visibility("default")))
+#else
+#define PF_API
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PF_OK 0
+#define PF_ERR_INVALID 1      /* malformed system, bad argument or size    */
+#define PF_ERR_OOM 2          /* device or host allocation failed          */
+#define PF_ERR_CUDA 3         /* a CUDA runtime call or launch failed      */
+#define PF_ERR_TIMEOUT 4      /* a bounded device wait gave up             */
+#define PF_ERR_UNSUPPORTED 5  /* valid input outside the library's limits  */
+#define PF_ERR_DEVICE 6       /* a kernel raised the context's error flag  */
+
+/* ---- formulations (Sec. II-A) ------------------------------------------- */
+#define PF_REDUCED 0          /* classic: P/theta non-slack, Q/V PQ buses  */
+#define PF_EXTENDED 1         /* Eqs. (1)-(3): g_p, g_q, g_V, g_theta      */
+
+typedef struct pf_ctx pf_ctx;
+
+/* One network, as host arrays (the library copies them; the caller may
+ * free them when pf_build returns).  Optional arrays may be NULL. */
+typedef struct pf_system {
+  int32_t n_bus;                 /* N >= 2                                    */
+  int32_t n_branch;              /* M >= 0 (lines and transformers)           */
+  const int32_t *br_from;        /* [M] from bus, 0 <= . < N                  */
+  const int32_t *br_to;          /* [M] to bus, != from                       */
+  const double *br_r;            /* [M] series resistance                     */
+  const double *br_x;            /* [M] series reactance, r^2 + x^2 > 0       */
+  const double *br_b;            /* [M] total line charging b_c (NULL: 0)      */
+  const double *br_tap;          /* [M] off-nominal tap tau > 0 (NULL: 1)     */
+  const double *br_shift;        /* [M] phase shift phi, radians (NULL: 0)    */
+  const double *br_g_fr;         /* [M] from-end conductance g_{L,h} (NULL: 0)*/
+  const double *br_g_to;         /* [M] to-end conductance g_{L,k} (NULL: 0)  */
+  const uint8_t *br_status;      /* [M] 0 = out of service (NULL: all in)     */
+  int32_t n_load;
+  const int32_t *load_bus;       /* [n_load] PQ loads: bus, P, Q (constant)   */
+  const double *load_p;
+  const double *load_q;
+  int32_t n_pv;
+  const int32_t *pv_bus;         /* [n_pv] PV units: bus (!= slack), P, Vset  */
+  const double *pv_p;
+  const double *pv_vset;
+  int32_t slack_bus;             /* exactly one slack generator              */
+  double slack_vset;
+  double slack_theta;
+  int32_t n_shunt;
+  const int32_t *sh_bus;         /* [n_shunt] shunts: consumption g V^2, -b V^2 */
+  const double *sh_g;
+  const double *sh_b;
+} pf_system;
+
+/* One evaluation instance of a batch (spec batched form). */
+typedef struct pf_instance {
+  int32_t grid;                  /* index into the grids array of pf_build_batch */
+  int32_t outage;                /* branch of that grid taken out for this instance, -1: none */
+} pf_instance;
+
+typedef struct pf_dims {
+  int32_t formulation;
+  int32_t n_grids;
+  int32_t n_instances;
+  int32_t max_degree;            /* largest bus degree over all grids         */
+  int64_t n_bus;                 /* sum over grids                            */
+  int64_t n_branch;              /* sum over grids                            */
+  int64_t n_inc;                 /* branch ends = 2 * n_branch               */
+  int64_t n_x;                   /* sum over instances: length of x          */
+  int64_t n_f;                   /* sum over instances: length of F          */
+  int64_t nnz;                   /* sum over instances: length of J values   */
+  int64_t n_bus_inst;            /* sum over instances of N (p_inj / q_inj length) */
+  int64_t n_branch_inst;         /* sum over instances of M (status override length) */
+} pf_dims;
+
+/* Per-call overrides (device pointers; every field may be NULL). */
+typedef struct pf_overrides {
+  const double *p_inj;           /* [n_bus_inst] net P injection per bus (P_g - P_load),
+                                    replaces the system's (Sec. II-A PQ / PV models) */
+  const double *q_inj;           /* [n_bus_inst] net Q injection per bus (-Q_load) */
+  const uint8_t *status;         /* [n_branch_inst] per-instance branch mask, 0 = out;
+                                    combined with the instance's outage           */
+  const double *br_r;            /* [n_branch] per-grid parameter overrides of the */
+  const double *br_x;            /*   branch model (adjoint / sensitivity use);   */
+  const double *br_b;            /*   each NULL keeps the built value             */
+  const double *br_tap;
+} pf_overrides;
+
+/* Gradients of a vector-Jacobian product (device pointers; NULL skips).
+ * Layout: [n_cot][...] with the per-instance blocks concatenated. */
+typedef struct pf_grads {
+  double *x;                     /* [n_cot][n_x]      v^T dF/dx                  */
+  double *p_inj;                 /* [n_cot][n_bus_inst] v^T dF/dP_inj            */
+  double *q_inj;                 /* [n_cot][n_bus_inst] v^T dF/dQ_inj            */
+  double *br_r;                  /* [n_cot][n_branch_inst] v^T dF/dr             */
+  double *br_x;                  /* [n_cot][n_branch_inst] v^T dF/dx (reactance) */
+  double *br_b;                  /* [n_cot][n_branch_inst] v^T dF/db_c           */
+  double *br_tap;                /* [n_cot][n_branch_inst] v^T dF/dtau           */
+} pf_grads;
+
+typedef struct pf_tuning {
+  int32_t tile_inc;              /* branch ends staged per CTA tile: 64..1024, multiple of 32 */
+  int32_t ctas_per_sm;           /* persistent CTAs per SM; 0 = one CTA per tile */
+} pf_tuning;
+
+/* ---- build (once) -------------------------------------------------------- */
+
+/* Builds the device index maps of one network (Sec. III: the Jacobian pattern
+ * that the paper assembles from triplets on every call is built once here):
+ * the per-bus incidence list, the CSR pattern of J and the per-nonzero
+ * contribution list, all on the device with integer-only, deterministic
+ * kernels.  Validates the system on the host first.  Synchronises `stream`
+ * before returning.  On success *out owns all device memory of the context.
+ * Errors: PF_ERR_INVALID (index out of range, from == to, r = x = 0,
+ * tau <= 0, non-finite value, PV unit on the slack bus, two PV units on one
+ * bus in the extended formulation, bad formulation), PF_ERR_UNSUPPORTED
+ * (sizes beyond int32 index range), PF_ERR_OOM, PF_ERR_CUDA. */
+PF_API int pf_build(const pf_system *sys, int32_t formulation, void *stream, pf_ctx **out);
+
+/* Batched form: n_grids networks and n_inst instances over them, evaluated
+ * together by one persistent launch.  Instance k owns the k-th block of x, F
+ * and J values (offsets from pf_offsets).  Same errors as pf_build, plus
+ * PF_ERR_INVALID for a bad grid index or outage branch. */
+PF_API int pf_build_batch(const pf_system *grids, int32_t n_grids, const pf_instance *inst,
+                   int32_t n_inst, int32_t formulation, void *stream, pf_ctx **out);
+
+/* Frees every device and host resource of the context.  NULL is ignored. */
+PF_API void pf_destroy(pf_ctx *ctx);
+
+/* ---- sizes and maps (host-side copies) ------------------------------------ */
+
+PF_API int pf_get_dims(const pf_ctx *ctx, pf_dims *dims);
+
+/* Per-instance offsets into x, F and J values: three host arrays of
+ * n_instances + 1 entries each (any may be NULL). */
+PF_API int pf_offsets(const pf_ctx *ctx, int64_t *x_off, int64_t *f_off, int64_t *nnz_off);
+
+/* CSR pattern of J of grid `grid`: rowptr [n_f(grid)+1], colind [nnz(grid)],
+ * host buffers.  Identical for every instance of that grid. */
+PF_API int pf_pattern(const pf_ctx *ctx, int32_t grid, int32_t *rowptr, int32_t *colind);
+PF_API int pf_grid_sizes(const pf_ctx *ctx, int32_t grid, int32_t *n_f, int32_t *nnz, int32_t *n_x);
+
+/* Per-bus incidence list of grid `grid` (host buffers): ptr [N+1]; for each
+ * branch end at a bus, code = 2*branch + end (end 0 = from, 1 = to) and the
+ * other bus, ordered by (other bus, branch).  Local numbering. */
+PF_API int pf_incidence(const pf_ctx *ctx, int32_t grid, int32_t *ptr, int32_t *code, int32_t *other);
+
+/* Per-nonzero contribution list of J of grid `grid`, in CSR order: sources
+ * of each nonzero in summation order -- branch ends as incidence-list
+ * positions, shunts as 2*M + shunt index, -1 for the constant +-1 entries of
+ * the extended formulation.  ptr [nnz+1] (int64), src [ptr[nnz]] (host).
+ * Call with src == NULL to obtain ptr (and so the length) only. */
+PF_API int pf_contributions(const pf_ctx *ctx, int32_t grid, int64_t *ptr, int32_t *src);
+
+/* ---- evaluation (hot path) ------------------------------------------------ */
+
+/* Task (1): F(x) for every instance.  x: [n_x], F: [n_f] device buffers. */
+PF_API int pf_residual(pf_ctx *ctx, const double *x, double *F, void *stream);
+
+/* Task (2): J values in CSR order of pf_pattern.  vals: [nnz] device. */
+PF_API int pf_jacobian(pf_ctx *ctx, const double *x, double *vals, void *stream);
+
+/* Tasks (1) and (2) in one fused pass.  F or vals may be NULL to skip. */
+PF_API int pf_residual_jacobian(pf_ctx *ctx, const double *x, double *F, double *vals, void *stream);
+
+/* Same, with per-call overrides (ov may be NULL). */
+PF_API int pf_eval(pf_ctx *ctx, const double *x, const pf_overrides *ov, double *F, double *vals,
+            void *stream);
+
+/* End-to-end form for callers holding host memory: copies x (host) in,
+ * evaluates, copies F and vals (host; either may be NULL) out and
+ * synchronises `stream`.  Page-locked host buffers give the full copy rate.
+ * Device staging buffers are allocated on the first call and kept. */
+PF_API int pf_residual_jacobian_host(pf_ctx *ctx, const double *x_host, double *F_host,
+                              double *vals_host, void *stream);
+
+/* Adjoint (spec differentiation form): for n_cot cotangents v
+ * ([n_cot][n_f], device), the vector-Jacobian products v^T dF/d(x, P_inj,
+ * Q_inj, r, x, b_c, tau).  Trigonometric terms are recomputed, nothing from a
+ * forward call is stored.  ov may be NULL. */
+PF_API int pf_vjp(pf_ctx *ctx, const double *x, const pf_overrides *ov, const double *v,
+           int32_t n_cot, const pf_grads *g, void *stream);
+
+/* ---- tuning ------------------------------------------------------------------ */
+
+PF_API int pf_get_tuning(const pf_ctx *ctx, pf_tuning *t);
+/* Re-tiles the context (device work on `stream`, synchronised).  Never
+ * changes results.  PF_ERR_INVALID for values outside the documented range. */
+PF_API int pf_set_tuning(pf_ctx *ctx, const pf_tuning *t, void *stream);
+/* Times the fused evaluation at x for each candidate tiling, keeps the
+ * fastest and returns it in *chosen.  x, F, vals: device buffers used as
+ * scratch for the timing runs. */
+PF_API int pf_autotune(pf_ctx *ctx, const double *x, double *F, double *vals, void *stream,
+                pf_tuning *chosen);
+
+/* ---- errors --------------------------------------------------------------------- */
+
+PF_API const char *pf_error_string(int32_t code);
+PF_API const char *pf_last_error(void);
+/* Reads and clears the context's device error flag (a kernel found an
+ * inconsistent map or a bounded wait ran out).  Synchronises `stream`.
+ * Returns PF_OK or PF_ERR_DEVICE / PF_ERR_TIMEOUT. */
+PF_API int pf_check_device(pf_ctx *ctx, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PF_H */

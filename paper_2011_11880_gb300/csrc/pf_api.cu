@@ -1,0 +1,303 @@
+// C ABI of libpf.so (declarations and contracts in include/pf.h).
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pf_internal.cuh"
+
+struct pf_ctx {
+  pf::Ctx c;
+};
+
+namespace pf {
+
+thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int fail(int code, const std::string &msg) {
+  set_error(msg);
+  return code;
+}
+
+}  // namespace pf
+
+using pf::fail;
+
+namespace {
+
+cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+void free_ctx(pf_ctx *ctx) {
+  if (!ctx) return;
+  for (void *p : ctx->c.allocations) cudaFree(p);
+  for (void *p : ctx->c.tile_allocations) cudaFree(p);
+  if (ctx->c.stage_x) cudaFree(ctx->c.stage_x);
+  if (ctx->c.stage_f) cudaFree(ctx->c.stage_f);
+  if (ctx->c.stage_v) cudaFree(ctx->c.stage_v);
+  delete ctx;
+}
+
+int check_grid(const pf_ctx *ctx, int32_t grid) {
+  if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
+  if (grid < 0 || grid >= ctx->c.v.n_grids) return fail(PF_ERR_INVALID, "grid index out of range");
+  return PF_OK;
+}
+
+template <class T>
+int copy_out(T *dst, const T *src, size_t n) {
+  if (n == 0) return PF_OK;
+  PF_CUDA_TRY(cudaMemcpy(dst, src, n * sizeof(T), cudaMemcpyDeviceToHost));
+  return PF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pf_build_batch(const pf_system *grids, int32_t n_grids, const pf_instance *inst, int32_t n_inst,
+                   int32_t formulation, void *stream, pf_ctx **out) {
+  if (!out) return fail(PF_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  pf_ctx *ctx = new (std::nothrow) pf_ctx();
+  if (!ctx) return fail(PF_ERR_OOM, "host allocation failed");
+  int rc = pf::build_context(ctx->c, grids, n_grids, inst, n_inst, formulation, as_stream(stream));
+  if (rc) {
+    std::string msg = pf_last_error();
+    free_ctx(ctx);
+    pf::set_error(msg);
+    return rc;
+  }
+  *out = ctx;
+  return PF_OK;
+}
+
+int pf_build(const pf_system *sys, int32_t formulation, void *stream, pf_ctx **out) {
+  if (!sys) return fail(PF_ERR_INVALID, "sys is NULL");
+  pf_instance one{0, -1};
+  return pf_build_batch(sys, 1, &one, 1, formulation, stream, out);
+}
+
+void pf_destroy(pf_ctx *ctx) {
+  if (!ctx) return;
+  cudaDeviceSynchronize();
+  free_ctx(ctx);
+}
+
+int pf_get_dims(const pf_ctx *ctx, pf_dims *d) {
+  if (!ctx || !d) return fail(PF_ERR_INVALID, "NULL argument");
+  const pf::Ctx &c = ctx->c;
+  d->formulation = c.v.formulation;
+  d->n_grids = c.v.n_grids;
+  d->n_instances = c.v.n_inst;
+  d->max_degree = c.max_degree;
+  d->n_bus = c.v.n_bus;
+  d->n_branch = c.v.n_branch;
+  d->n_inc = c.v.n_inc;
+  d->n_x = c.n_x;
+  d->n_f = c.n_f;
+  d->nnz = c.nnz;
+  d->n_bus_inst = c.v.n_bus_inst;
+  d->n_branch_inst = c.n_branch_inst;
+  return PF_OK;
+}
+
+int pf_offsets(const pf_ctx *ctx, int64_t *x_off, int64_t *f_off, int64_t *nnz_off) {
+  if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
+  const pf::Ctx &c = ctx->c;
+  const size_t n = c.x_off.size();
+  if (x_off) std::memcpy(x_off, c.x_off.data(), n * sizeof(int64_t));
+  if (f_off) std::memcpy(f_off, c.f_off.data(), n * sizeof(int64_t));
+  if (nnz_off) std::memcpy(nnz_off, c.v_off.data(), n * sizeof(int64_t));
+  return PF_OK;
+}
+
+int pf_grid_sizes(const pf_ctx *ctx, int32_t grid, int32_t *n_f, int32_t *nnz, int32_t *n_x) {
+  PF_TRY(check_grid(ctx, grid));
+  if (n_f) *n_f = ctx->c.grid_nf[grid];
+  if (nnz) *nnz = ctx->c.grid_nnz[grid];
+  if (n_x) *n_x = ctx->c.grid_nx[grid];
+  return PF_OK;
+}
+
+int pf_pattern(const pf_ctx *ctx, int32_t grid, int32_t *rowptr, int32_t *colind) {
+  PF_TRY(check_grid(ctx, grid));
+  const pf::Ctx &c = ctx->c;
+  if (rowptr) PF_TRY(copy_out(rowptr, c.rowptr + c.grid_row_off[grid], (size_t)c.grid_nf[grid] + 1));
+  if (colind) PF_TRY(copy_out(colind, c.colind + c.grid_nnz_off[grid], (size_t)c.grid_nnz[grid]));
+  return PF_OK;
+}
+
+int pf_incidence(const pf_ctx *ctx, int32_t grid, int32_t *ptr, int32_t *code, int32_t *other) {
+  PF_TRY(check_grid(ctx, grid));
+  const pf::Ctx &c = ctx->c;
+  const int64_t b0 = c.grid_bus_off[grid], b1 = c.grid_bus_off[grid + 1];
+  const int64_t l0 = c.grid_br_off[grid], l1 = c.grid_br_off[grid + 1];
+  const int64_t e0 = 2 * l0, ne = 2 * (l1 - l0);
+  if (ptr) {
+    std::vector<int32_t> h(b1 - b0 + 1);
+    PF_TRY(copy_out(h.data(), c.v.inc_ptr + b0, h.size()));
+    for (auto &q : h) q -= (int32_t)e0;
+    std::memcpy(ptr, h.data(), h.size() * sizeof(int32_t));
+  }
+  if (code) {
+    std::vector<int32_t> h(ne);
+    PF_TRY(copy_out(h.data(), c.v.inc_code + e0, h.size()));
+    for (auto &q : h) q -= (int32_t)(2 * l0);
+    std::memcpy(code, h.data(), h.size() * sizeof(int32_t));
+  }
+  if (other) {
+    std::vector<int32_t> h(ne);
+    PF_TRY(copy_out(h.data(), c.v.inc_other + e0, h.size()));
+    for (auto &q : h) q -= (int32_t)b0;
+    std::memcpy(other, h.data(), h.size() * sizeof(int32_t));
+  }
+  return PF_OK;
+}
+
+int pf_contributions(const pf_ctx *ctx, int32_t grid, int64_t *ptr, int32_t *src) {
+  PF_TRY(check_grid(ctx, grid));
+  const pf::Ctx &c = ctx->c;
+  if (ptr) PF_TRY(copy_out(ptr, c.contrib_ptr + c.grid_cptr_off[grid], (size_t)c.grid_nnz[grid] + 1));
+  if (src)
+    PF_TRY(copy_out(src, c.contrib_src + c.grid_csrc_off[grid],
+                    (size_t)(c.grid_csrc_off[grid + 1] - c.grid_csrc_off[grid])));
+  return PF_OK;
+}
+
+int pf_eval(pf_ctx *ctx, const double *x, const pf_overrides *ov, double *F, double *vals, void *stream) {
+  if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
+  return pf::launch_eval(ctx->c, x, ov, F, vals, as_stream(stream));
+}
+
+int pf_residual(pf_ctx *ctx, const double *x, double *F, void *stream) {
+  if (!F) return fail(PF_ERR_INVALID, "F is NULL");
+  return pf_eval(ctx, x, nullptr, F, nullptr, stream);
+}
+
+int pf_jacobian(pf_ctx *ctx, const double *x, double *vals, void *stream) {
+  if (!vals) return fail(PF_ERR_INVALID, "vals is NULL");
+  return pf_eval(ctx, x, nullptr, nullptr, vals, stream);
+}
+
+int pf_residual_jacobian(pf_ctx *ctx, const double *x, double *F, double *vals, void *stream) {
+  return pf_eval(ctx, x, nullptr, F, vals, stream);
+}
+
+int pf_residual_jacobian_host(pf_ctx *ctx, const double *x_host, double *F_host, double *vals_host,
+                              void *stream) {
+  if (!ctx || !x_host) return fail(PF_ERR_INVALID, "NULL argument");
+  pf::Ctx &c = ctx->c;
+  cudaStream_t s = as_stream(stream);
+  if (!c.stage_x) {
+    PF_CUDA_TRY(cudaMalloc(&c.stage_x, std::max<int64_t>(c.n_x, 1) * sizeof(double)));
+    PF_CUDA_TRY(cudaMalloc(&c.stage_f, std::max<int64_t>(c.n_f, 1) * sizeof(double)));
+    PF_CUDA_TRY(cudaMalloc(&c.stage_v, std::max<int64_t>(c.nnz, 1) * sizeof(double)));
+  }
+  PF_CUDA_TRY(cudaMemcpyAsync(c.stage_x, x_host, c.n_x * sizeof(double), cudaMemcpyHostToDevice, s));
+  PF_TRY(pf::launch_eval(c, c.stage_x, nullptr, F_host ? c.stage_f : nullptr, vals_host ? c.stage_v : nullptr, s));
+  if (F_host) PF_CUDA_TRY(cudaMemcpyAsync(F_host, c.stage_f, c.n_f * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (vals_host)
+    PF_CUDA_TRY(cudaMemcpyAsync(vals_host, c.stage_v, c.nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
+  PF_CUDA_TRY(cudaStreamSynchronize(s));
+  return PF_OK;
+}
+
+int pf_vjp(pf_ctx *ctx, const double *x, const pf_overrides *ov, const double *v, int32_t n_cot,
+           const pf_grads *g, void *stream) {
+  if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
+  return pf::launch_vjp(ctx->c, x, ov, v, n_cot, g, as_stream(stream));
+}
+
+int pf_get_tuning(const pf_ctx *ctx, pf_tuning *t) {
+  if (!ctx || !t) return fail(PF_ERR_INVALID, "NULL argument");
+  *t = ctx->c.tuning;
+  return PF_OK;
+}
+
+int pf_set_tuning(pf_ctx *ctx, const pf_tuning *t, void *stream) {
+  if (!ctx || !t) return fail(PF_ERR_INVALID, "NULL argument");
+  if (t->tile_inc < pf::kMinTileInc || t->tile_inc > pf::kMaxTileInc || t->tile_inc % 32 != 0)
+    return fail(PF_ERR_INVALID, "tile_inc must be a multiple of 32 in [64, 1024]");
+  if (t->tile_inc < ctx->c.max_group) return fail(PF_ERR_INVALID, "tile_inc below the largest parallel group");
+  if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return fail(PF_ERR_INVALID, "ctas_per_sm must be in [0, 32]");
+  cudaStream_t s = as_stream(stream);
+  PF_CUDA_TRY(cudaStreamSynchronize(s));
+  if (t->tile_inc != ctx->c.tuning.tile_inc) PF_TRY(pf::build_tiles(ctx->c, t->tile_inc, s));
+  ctx->c.tuning.ctas_per_sm = t->ctas_per_sm;
+  return PF_OK;
+}
+
+int pf_autotune(pf_ctx *ctx, const double *x, double *F, double *vals, void *stream, pf_tuning *chosen) {
+  if (!ctx || !x) return fail(PF_ERR_INVALID, "NULL argument");
+  cudaStream_t s = as_stream(stream);
+  const int tiles[] = {128, 256, 512};
+  const int ctas[] = {0, 4, 8};
+  pf_tuning best = ctx->c.tuning;
+  float best_ms = 1e30f;
+  cudaEvent_t e0, e1;
+  PF_CUDA_TRY(cudaEventCreate(&e0));
+  PF_CUDA_TRY(cudaEventCreate(&e1));
+  int rc = PF_OK;
+  for (int ti : tiles) {
+    if (ti < ctx->c.max_group) continue;
+    for (int ca : ctas) {
+      pf_tuning t{ti, ca};
+      rc = pf_set_tuning(ctx, &t, stream);
+      if (rc) break;
+      for (int w = 0; w < 2 && !rc; ++w) rc = pf::launch_eval(ctx->c, x, nullptr, F, vals, s);
+      if (rc) break;
+      const int reps = 5;
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < reps && !rc; ++r) rc = pf::launch_eval(ctx->c, x, nullptr, F, vals, s);
+      cudaEventRecord(e1, s);
+      if (rc) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(PF_ERR_CUDA, "autotune timing"); break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = t;
+      }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  PF_TRY(pf_set_tuning(ctx, &best, stream));
+  if (chosen) *chosen = best;
+  return PF_OK;
+}
+
+const char *pf_error_string(int32_t code) {
+  switch (code) {
+    case PF_OK: return "ok";
+    case PF_ERR_INVALID: return "invalid argument or system";
+    case PF_ERR_OOM: return "out of memory";
+    case PF_ERR_CUDA: return "CUDA error";
+    case PF_ERR_TIMEOUT: return "bounded device wait timed out";
+    case PF_ERR_UNSUPPORTED: return "outside the library's limits";
+    case PF_ERR_DEVICE: return "device-side consistency check failed";
+    default: return "unknown error code";
+  }
+}
+
+const char *pf_last_error(void) { return pf::g_last_error.c_str(); }
+
+int pf_check_device(pf_ctx *ctx, void *stream) {
+  if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
+  int32_t h = 0;
+  cudaStream_t s = as_stream(stream);
+  PF_CUDA_TRY(cudaMemcpyAsync(&h, ctx->c.v.dev_error, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  PF_CUDA_TRY(cudaStreamSynchronize(s));
+  PF_CUDA_TRY(cudaMemsetAsync(ctx->c.v.dev_error, 0, sizeof(int32_t), s));
+  PF_CUDA_TRY(cudaStreamSynchronize(s));
+  if (h & pf::kErrTimeout) return fail(PF_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (h) return fail(PF_ERR_DEVICE, "device error flag " + std::to_string(h));
+  return PF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,1059 @@
+// pf_build: validates the systems on the host, then builds every index map on
+// the device with integer-only, deterministic kernels:
+//   * the per-bus incidence list (branch ends sorted by (own bus, other bus,
+//     branch)), with parallel-branch groups and mirror positions;
+//   * the formulation row / column maps (Sec. II-A, Eqs. 1-3 and the classic
+//     reduced form) and the CSR pattern of J (Sec. III: the pattern the paper
+//     assembles from triplets on every call is built once here);
+//   * the per-nonzero contribution list;
+//   * per-end branch coefficients and per-bus sums of the constant terms.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "pf_internal.cuh"
+#include "pf_sort_scan.cuh"
+
+namespace pf {
+
+namespace {
+
+constexpr int TB = 256;
+
+inline unsigned nblk(int64_t n, int tb = TB) { return (unsigned)((n + tb - 1) / tb); }
+
+struct TempList {
+  std::vector<void *> p;
+  ~TempList() {
+    for (void *q : p) cudaFree(q);
+  }
+  template <class T>
+  int alloc(T **out, size_t n) {
+    if (n == 0) n = 1;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+    if (e != cudaSuccess)
+      return fail(PF_ERR_OOM, "cudaMalloc (build scratch): " + std::string(cudaGetErrorString(e)));
+    p.push_back(q);
+    *out = static_cast<T *>(q);
+    return PF_OK;
+  }
+};
+
+// --------------------------------------------------------------------------
+// host validation
+// --------------------------------------------------------------------------
+
+bool finite(double v) { return std::isfinite(v); }
+
+int validate(const pf_system &g, int gi, int formulation, int *n_pv_distinct) {
+  auto bad = [&](const std::string &m) {
+    return fail(PF_ERR_INVALID, "grid " + std::to_string(gi) + ": " + m);
+  };
+  if (g.n_bus < 2) return bad("n_bus must be >= 2");
+  if (g.n_branch < 0 || g.n_load < 0 || g.n_pv < 0 || g.n_shunt < 0) return bad("negative count");
+  const int64_t n = g.n_bus;
+  if (g.n_branch > 0 && (!g.br_from || !g.br_to || !g.br_r || !g.br_x))
+    return bad("br_from, br_to, br_r and br_x are required");
+  for (int64_t k = 0; k < g.n_branch; ++k) {
+    const int f = g.br_from[k], t = g.br_to[k];
+    if (f < 0 || f >= n || t < 0 || t >= n) return bad("branch " + std::to_string(k) + ": bus index out of range");
+    if (f == t) return bad("branch " + std::to_string(k) + ": from == to");
+    const double r = g.br_r[k], x = g.br_x[k];
+    if (!finite(r) || !finite(x) || !(r * r + x * x > 0.0))
+      return bad("branch " + std::to_string(k) + ": r, x must be finite with r^2 + x^2 > 0");
+    if (g.br_b && !finite(g.br_b[k])) return bad("branch " + std::to_string(k) + ": b not finite");
+    if (g.br_tap && !(finite(g.br_tap[k]) && g.br_tap[k] > 0.0))
+      return bad("branch " + std::to_string(k) + ": tap must be finite and > 0");
+    if (g.br_shift && !finite(g.br_shift[k])) return bad("branch " + std::to_string(k) + ": shift not finite");
+    if (g.br_g_fr && !finite(g.br_g_fr[k])) return bad("branch " + std::to_string(k) + ": g_fr not finite");
+    if (g.br_g_to && !finite(g.br_g_to[k])) return bad("branch " + std::to_string(k) + ": g_to not finite");
+  }
+  if (g.slack_bus < 0 || g.slack_bus >= n) return bad("slack bus out of range");
+  if (!finite(g.slack_vset) || !finite(g.slack_theta)) return bad("slack set-points not finite");
+  if (g.n_load > 0 && (!g.load_bus || !g.load_p || !g.load_q)) return bad("load arrays missing");
+  for (int64_t k = 0; k < g.n_load; ++k) {
+    if (g.load_bus[k] < 0 || g.load_bus[k] >= n) return bad("load " + std::to_string(k) + ": bus out of range");
+    if (!finite(g.load_p[k]) || !finite(g.load_q[k])) return bad("load " + std::to_string(k) + ": not finite");
+  }
+  if (g.n_pv > 0 && (!g.pv_bus || !g.pv_p || !g.pv_vset)) return bad("PV arrays missing");
+  std::vector<char> seen(n, 0);
+  int distinct = 0;
+  for (int64_t k = 0; k < g.n_pv; ++k) {
+    const int b = g.pv_bus[k];
+    if (b < 0 || b >= n) return bad("PV " + std::to_string(k) + ": bus out of range");
+    if (b == g.slack_bus) return bad("PV " + std::to_string(k) + ": unit on the slack bus");
+    if (!finite(g.pv_p[k]) || !finite(g.pv_vset[k])) return bad("PV " + std::to_string(k) + ": not finite");
+    if (seen[b]) {
+      if (formulation == PF_EXTENDED)
+        return bad("PV " + std::to_string(k) + ": two PV units on one bus (extended formulation)");
+    } else {
+      ++distinct;
+    }
+    seen[b] = 1;
+  }
+  if (g.n_shunt > 0 && (!g.sh_bus || !g.sh_g || !g.sh_b)) return bad("shunt arrays missing");
+  for (int64_t k = 0; k < g.n_shunt; ++k) {
+    if (g.sh_bus[k] < 0 || g.sh_bus[k] >= n) return bad("shunt " + std::to_string(k) + ": bus out of range");
+    if (!finite(g.sh_g[k]) || !finite(g.sh_b[k])) return bad("shunt " + std::to_string(k) + ": not finite");
+  }
+  *n_pv_distinct = distinct;
+  return PF_OK;
+}
+
+// --------------------------------------------------------------------------
+// device kernels
+// --------------------------------------------------------------------------
+
+__global__ void k_bus_type(int8_t *type, const int32_t *pv_bus, int64_t n_pv, const int64_t *slack_glob,
+                           int n_grids) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_pv) type[pv_bus[i]] = 1;
+  if (i < n_grids) type[slack_glob[i]] = 2;  // a PV unit never sits on the slack bus
+}
+
+__global__ void k_flags(const int8_t *type, int64_t n, uint8_t *ns, uint8_t *pq) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  ns[b] = type[b] != 2;
+  pq[b] = type[b] == 0;
+}
+
+__global__ void k_row_maps(View v, const int8_t *type, const int64_t *ex_ns, const int64_t *ex_pq,
+                           int32_t *row_p, int32_t *row_q, int32_t *gen) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= v.n_bus) return;
+  const int g = v.bus_grid[b];
+  const int64_t b0 = v.grid_bus_off[g];
+  const int nb = v.grid_nbus[g];
+  gen[b] = -1;
+  if (v.formulation == PF_REDUCED) {
+    row_p[b] = type[b] != 2 ? (int32_t)(ex_ns[b] - ex_ns[b0]) : -1;
+    row_q[b] = type[b] == 0 ? (int32_t)(nb - 1 + ex_pq[b] - ex_pq[b0]) : -1;
+  } else {
+    row_p[b] = (int32_t)(b - b0);
+    row_q[b] = (int32_t)(nb + b - b0);
+  }
+}
+
+// extended: generator index of each generator bus; gen_bus of each generator
+__global__ void k_gen_map(View v, const int32_t *pv_bus, const int32_t *pv_grid, const int64_t *grid_pv_off,
+                          int64_t n_pv, int32_t *gen, int32_t *gen_bus) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_pv) {
+    const int g = pv_grid[i];
+    const int32_t gi = (int32_t)(i - grid_pv_off[g]);
+    gen[pv_bus[i]] = gi;
+    gen_bus[v.grid_gen_off[g] + gi] = pv_bus[i];
+  }
+  if (i < v.n_grids) {
+    const int g = (int)i;
+    const int32_t gi = v.grid_ngen[g] - 1;
+    const int32_t s = (int32_t)(v.grid_bus_off[g] + v.grid_slack[g]);
+    gen[s] = gi;
+    gen_bus[v.grid_gen_off[g] + gi] = s;
+  }
+}
+
+__global__ void k_make_keys(const int32_t *from, const int32_t *to, int64_t m, uint64_t *keys, uint32_t *vals) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 2 * m) return;
+  const int64_t l = e >> 1;
+  const uint32_t own = (uint32_t)((e & 1) ? to[l] : from[l]);
+  const uint32_t oth = (uint32_t)((e & 1) ? from[l] : to[l]);
+  keys[e] = ((uint64_t)own << 32) | oth;
+  vals[e] = (uint32_t)e;
+}
+
+__global__ void k_unpack(const uint64_t *keys, const uint32_t *vals, int64_t n, int32_t *own, int32_t *oth,
+                         int32_t *code, int32_t *pos_of, int32_t *deg) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t k = keys[i];
+  own[i] = (int32_t)(k >> 32);
+  oth[i] = (int32_t)(k & 0xffffffffu);
+  code[i] = (int32_t)vals[i];
+  pos_of[vals[i]] = (int32_t)i;
+  atomicAdd(deg + (int32_t)(k >> 32), 1);
+}
+
+__global__ void k_i64_to_i32(const int64_t *in, int32_t *out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (int32_t)in[i];
+}
+
+__global__ void k_mirror_groups(View v, const int32_t *pos_of, int32_t *mirror, int32_t *grp, int32_t *stats) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= v.n_inc) return;
+  mirror[i] = pos_of[v.inc_code[i] ^ 1];
+  const int32_t o = v.inc_own[i];
+  const int32_t lo = v.inc_ptr[o], hi = v.inc_ptr[o + 1];
+  const bool head = (i == lo) || (v.inc_other[i - 1] != v.inc_other[i]);
+  int32_t len = 0;
+  if (head) {
+    len = 1;
+    while (i + len < hi && v.inc_other[i + len] == v.inc_other[i]) ++len;
+    atomicMax(stats + 0, len);
+  }
+  grp[i] = len;
+  if (i == lo) atomicMax(stats + 1, hi - lo);
+}
+
+__device__ __forceinline__ bool has_col(const View &v, int32_t j, bool theta) {
+  return theta ? (v.row_p[j] >= 0) : (v.row_q[j] >= 0);
+}
+
+// Visits, in ascending bus order, the buses of {o} U {other ends of o's
+// branches} whose theta (or V) column exists: f(bus, head incidence or -1, group length).
+template <class F>
+__device__ __forceinline__ void walk_block(const View &v, int32_t o, bool theta, F &&f) {
+  const int32_t p0 = v.inc_ptr[o], p1 = v.inc_ptr[o + 1];
+  bool o_done = false;
+  for (int32_t i = p0; i < p1;) {
+    const int32_t len = v.inc_grp[i];
+    const int32_t k = v.inc_other[i];
+    if (!o_done && o < k) {
+      if (has_col(v, o, theta)) f(o, -1, 0);
+      o_done = true;
+    }
+    if (has_col(v, k, theta)) f(k, i, len);
+    i += (len > 0 ? len : 1);
+  }
+  if (!o_done && has_col(v, o, theta)) f(o, -1, 0);
+}
+
+// Row structure of every bus: in-row offsets of each neighbour's columns,
+// diagonal offsets, row lengths.
+__global__ void k_row_struct(View v, const int64_t *grid_f_off, int2 *inc_rt, int2 *diag, int32_t *len_tv,
+                             int32_t *rowlen) {
+  const int64_t ob = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (ob >= v.n_bus) return;
+  const int32_t o = (int32_t)ob;
+  int32_t nth = 0, nv = 0;
+  int2 d = make_int2(-1, -1);
+  walk_block(v, o, true, [&](int32_t j, int32_t i, int32_t len) {
+    if (i < 0) d.x = nth;
+    else for (int32_t q = 0; q < len; ++q) inc_rt[i + q].x = nth;
+    ++nth;
+  });
+  // ends whose other bus has no theta column
+  for (int32_t i = v.inc_ptr[o]; i < v.inc_ptr[o + 1]; ++i)
+    if (!has_col(v, v.inc_other[i], true)) inc_rt[i].x = -1;
+  walk_block(v, o, false, [&](int32_t j, int32_t i, int32_t len) {
+    if (i < 0) d.y = nth + nv;
+    else for (int32_t q = 0; q < len; ++q) inc_rt[i + q].y = nth + nv;
+    ++nv;
+  });
+  for (int32_t i = v.inc_ptr[o]; i < v.inc_ptr[o + 1]; ++i)
+    if (!has_col(v, v.inc_other[i], false)) inc_rt[i].y = -1;
+  diag[o] = d;
+  len_tv[o] = nth + nv;
+  const int g = v.bus_grid[o];
+  const bool ext = v.formulation == PF_EXTENDED;
+  const bool is_slack = (o == v.grid_bus_off[g] + v.grid_slack[g]);
+  if (v.row_p[o] >= 0) rowlen[grid_f_off[g] + v.row_p[o]] = nth + nv + ((ext && is_slack) ? 1 : 0);
+  if (v.row_q[o] >= 0) rowlen[grid_f_off[g] + v.row_q[o]] = nth + nv + ((ext && v.gen[o] >= 0) ? 1 : 0);
+}
+
+// extended: one-entry rows g_V (per generator) and g_theta (per grid)
+__global__ void k_gen_rowlen(View v, const int64_t *grid_f_off, int32_t *rowlen, int64_t n_gen_tot) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_gen_tot) {
+    const int32_t b = v.gen_bus[i];
+    const int g = v.bus_grid[b];
+    const int64_t gi = i - v.grid_gen_off[g];
+    rowlen[grid_f_off[g] + 2 * (int64_t)v.grid_nbus[g] + gi] = 1;
+  }
+  if (i < v.n_grids) {
+    const int g = (int)i;
+    rowlen[grid_f_off[g] + 2 * (int64_t)v.grid_nbus[g] + v.grid_ngen[g]] = 1;
+  }
+}
+
+// rowptr of grid g, entry r in [0, n_f(g)]: S[f_off + r] - S[f_off]
+__global__ void k_rowptr(const int64_t *S, const int64_t *grid_f_off, const int64_t *grid_row_off, int n_grids,
+                         int64_t total, int32_t *rowptr, int32_t *nnz_out, int32_t *err) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= total) return;
+  const int g = find_segment(grid_row_off, n_grids, q);
+  const int64_t r = q - grid_row_off[g];
+  const int64_t val = S[grid_f_off[g] + r] - S[grid_f_off[g]];
+  if (val > 0x7fffffffLL) atomicOr(err, kErrMap);
+  rowptr[q] = (int32_t)val;
+  if (q + 1 == grid_row_off[g + 1]) nnz_out[g] = (int32_t)val;
+}
+
+__global__ void k_colind(View v, const int32_t *rowptr, const int64_t *grid_row_off, const int64_t *grid_nnz_off,
+                         int32_t *base_p, int32_t *base_q, int32_t *colind) {
+  const int64_t ob = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (ob >= v.n_bus) return;
+  const int32_t o = (int32_t)ob;
+  const int g = v.bus_grid[o];
+  const int32_t *rp = rowptr + grid_row_off[g];
+  int32_t *ci = colind + grid_nnz_off[g];
+  const int64_t b0 = v.grid_bus_off[g];
+  const int32_t nb = v.grid_nbus[g];
+  const bool ext = v.formulation == PF_EXTENDED;
+  const bool is_slack = (o == b0 + v.grid_slack[g]);
+  for (int which = 0; which < 2; ++which) {
+    const int32_t row = which == 0 ? v.row_p[o] : v.row_q[o];
+    if (row < 0) {
+      (which == 0 ? base_p : base_q)[o] = -1;
+      continue;
+    }
+    const int32_t base = rp[row];
+    (which == 0 ? base_p : base_q)[o] = base;
+    int32_t pos = base;
+    walk_block(v, o, true, [&](int32_t j, int32_t, int32_t) { ci[pos++] = v.row_p[j]; });
+    walk_block(v, o, false, [&](int32_t j, int32_t, int32_t) { ci[pos++] = v.row_q[j]; });
+    if (ext && which == 0 && is_slack) ci[pos++] = 2 * nb + v.grid_ngen[g];       // P_s column
+    if (ext && which == 1 && v.gen[o] >= 0) ci[pos++] = 2 * nb + v.gen[o];         // Q_g column
+  }
+}
+
+// extended: the g_V and g_theta entries
+__global__ void k_gen_cols(View v, const int32_t *rowptr, const int64_t *grid_row_off, const int64_t *grid_nnz_off,
+                           int32_t *colind, int32_t *gen_pos, int32_t *grid_pos_gth, int32_t *grid_row_gth,
+                           int64_t n_gen_tot) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_gen_tot) {
+    const int32_t b = v.gen_bus[i];
+    const int g = v.bus_grid[b];
+    const int64_t gi = i - v.grid_gen_off[g];
+    const int32_t row = 2 * v.grid_nbus[g] + (int32_t)gi;
+    const int32_t pos = rowptr[grid_row_off[g] + row];
+    colind[grid_nnz_off[g] + pos] = v.row_q[b];
+    gen_pos[i] = pos;
+  }
+  if (i < v.n_grids) {
+    const int g = (int)i;
+    const int32_t row = 2 * v.grid_nbus[g] + v.grid_ngen[g];
+    const int32_t pos = rowptr[grid_row_off[g] + row];
+    colind[grid_nnz_off[g] + pos] = v.grid_slack[g];
+    grid_pos_gth[g] = pos;
+    grid_row_gth[g] = row;
+  }
+}
+
+__global__ void k_item_keys(const int32_t *bus, int64_t n, uint64_t *keys, uint32_t *vals) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  keys[i] = ((uint64_t)(uint32_t)bus[i] << 32) | (uint32_t)i;
+  vals[i] = (uint32_t)i;
+  (void)0;
+}
+
+__global__ void k_count_bus(const uint64_t *keys, int64_t n, int32_t *cnt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicAdd(cnt + (int32_t)(keys[i] >> 32), 1);
+}
+
+// per-bus sums of item values in item order (items sorted by (bus, index))
+__global__ void k_bus_sums(const int64_t *ptr, const uint32_t *order, const double *v0, const double *v1,
+                           int64_t n_bus, double *o0, double *o1, double s0, double s1) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_bus) return;
+  double a = 0.0, c = 0.0;
+  for (int64_t j = ptr[b]; j < ptr[b + 1]; ++j) {
+    a += v0[order[j]];
+    if (v1) c += v1[order[j]];
+  }
+  o0[b] = s0 * a;
+  if (o1) o1[b] = s1 * c;
+}
+
+__global__ void k_net_injection(const double *pg, const double *pl, const double *ql, int64_t n, double *p,
+                                double *q) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  p[b] = pg[b] - pl[b];
+  q[b] = -ql[b];
+}
+
+// per-end coefficients of the rotated branch form (see the evaluation kernel)
+__global__ void k_coeff(View v, const double *r_ov, const double *x_ov, const double *b_ov, const double *tap_ov,
+                        double2 *gb, double2 *ac) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= v.n_inc) return;
+  const int32_t code = v.inc_code[i];
+  const int32_t l = code >> 1;
+  if (!v.br_status[l]) {
+    gb[i] = make_double2(0.0, 0.0);
+    ac[i] = make_double2(0.0, 0.0);
+    return;
+  }
+  const double r = r_ov ? r_ov[l] : v.br_r[l];
+  const double x = x_ov ? x_ov[l] : v.br_x[l];
+  const double bc = b_ov ? b_ov[l] : v.br_b[l];
+  const double tau = tap_ov ? tap_ov[l] : v.br_tap[l];
+  const double d = r * r + x * x;
+  const double g = r / d, b = -x / d;
+  double sp, cp;
+  sincos(v.br_shift[l], &sp, &cp);
+  const double it = 1.0 / tau;
+  if ((code & 1) == 0) {  // from end: transformer side
+    gb[i] = make_double2((g * cp - b * sp) * it, (g * sp + b * cp) * it);
+    ac[i] = make_double2((g + v.br_gfr[l]) * it * it, (b + 0.5 * bc) * it * it);
+  } else {                // to end
+    gb[i] = make_double2((g * cp + b * sp) * it, (b * cp - g * sp) * it);
+    ac[i] = make_double2(g + v.br_gto[l], b + 0.5 * bc);
+  }
+}
+
+__global__ void k_hat(View v, const double2 *ac, double *ahat, double *chat) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= v.n_bus) return;
+  double sa = 0.0, sc = 0.0;
+  for (int32_t e = v.inc_ptr[o]; e < v.inc_ptr[o + 1]; ++e) {
+    const double2 t = ac[e];
+    sa += t.x;
+    sc += t.y;
+  }
+  ahat[o] = sa + v.g_sh[o];
+  chat[o] = sc + v.b_sh[o];
+}
+
+// per-nonzero contribution list: pass 0 counts, pass 1 writes
+__global__ void k_contrib(View v, int pass, const int64_t *grid_nnz_off, const int64_t *grid_cptr_off,
+                          const int64_t *grid_csrc_off, const int64_t *sh_ptr, const uint32_t *sh_order,
+                          const int64_t *grid_sh_off, const int64_t *grid_inc_off, const int32_t *grid_nbr,
+                          int32_t *count, const int64_t *cptr, int32_t *src) {
+  const int64_t ob = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (ob >= v.n_bus) return;
+  const int32_t o = (int32_t)ob;
+  const int g = v.bus_grid[o];
+  const bool ext = v.formulation == PF_EXTENDED;
+  const bool is_slack = (o == v.grid_bus_off[g] + v.grid_slack[g]);
+  const int64_t ioff = grid_inc_off[g];
+  const int32_t p0 = v.inc_ptr[o], p1 = v.inc_ptr[o + 1];
+  for (int which = 0; which < 2; ++which) {
+    const int32_t base = which == 0 ? v.base_p[o] : v.base_q[o];
+    if (base < 0) continue;
+    int32_t pos = base;
+    auto emit = [&](int32_t j, int32_t i, int32_t len, bool vcol) {
+      const int64_t k = grid_nnz_off[g] + pos;
+      if (pass == 0) {
+        int32_t n = (i < 0) ? (p1 - p0) : len;
+        if (i < 0 && vcol) n += (int32_t)(sh_ptr[o + 1] - sh_ptr[o]);
+        count[k] = n;
+      } else {
+        int64_t w = grid_csrc_off[g] + cptr[grid_cptr_off[g] + pos];
+        if (i < 0) {
+          for (int32_t e = p0; e < p1; ++e) src[w++] = (int32_t)(e - ioff);
+          if (vcol)
+            for (int64_t s = sh_ptr[o]; s < sh_ptr[o + 1]; ++s)
+              src[w++] = 2 * grid_nbr[g] + (int32_t)(sh_order[s] - grid_sh_off[g]);
+        } else {
+          for (int32_t e = i; e < i + len; ++e) src[w++] = (int32_t)(e - ioff);
+        }
+      }
+      ++pos;
+    };
+    walk_block(v, o, true, [&](int32_t j, int32_t i, int32_t len) { emit(j, i, len, false); });
+    walk_block(v, o, false, [&](int32_t j, int32_t i, int32_t len) { emit(j, i, len, true); });
+    const bool extra = ext && ((which == 0 && is_slack) || (which == 1 && v.gen[o] >= 0));
+    if (extra) {
+      const int64_t k = grid_nnz_off[g] + pos;
+      if (pass == 0) count[k] = 1;
+      else src[grid_csrc_off[g] + cptr[grid_cptr_off[g] + pos]] = -1;
+    }
+  }
+}
+
+__global__ void k_contrib_const(View v, int pass, const int64_t *grid_nnz_off, const int64_t *grid_cptr_off,
+                                const int64_t *grid_csrc_off, const int32_t *gen_pos, const int32_t *grid_pos_gth,
+                                int64_t n_gen_tot, int32_t *count, const int64_t *cptr, int32_t *src) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  auto put = [&](int g, int32_t pos) {
+    if (pass == 0) count[grid_nnz_off[g] + pos] = 1;
+    else src[grid_csrc_off[g] + cptr[grid_cptr_off[g] + pos]] = -1;
+  };
+  if (i < n_gen_tot) put(v.bus_grid[v.gen_bus[i]], gen_pos[i]);
+  if (i < v.n_grids) put((int)i, grid_pos_gth[i]);
+}
+
+// local contribution pointer of grid g: S[nnz_off + k] - S[nnz_off], k in [0, nnz(g)]
+__global__ void k_cptr(const int64_t *S, const int64_t *grid_nnz_off, const int64_t *grid_cptr_off, int n_grids,
+                       int64_t total, int64_t *cptr, int64_t *src_len) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= total) return;
+  const int g = find_segment(grid_cptr_off, n_grids, q);
+  const int64_t k = q - grid_cptr_off[g];
+  cptr[q] = S[grid_nnz_off[g] + k] - S[grid_nnz_off[g]];
+  if (q + 1 == grid_cptr_off[g + 1]) src_len[g] = cptr[q];
+}
+
+// greedy packing of consecutive buses into tiles of at most `cap` branch ends
+// and `cap` buses; a bus with more ends than `cap` forms a tile alone.
+__global__ void k_tiles(View v, int cap, const int64_t *tile_off, int32_t *count, int32_t *bus0, int32_t *bus1) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= v.n_grids) return;
+  const int64_t b0 = v.grid_bus_off[g], b1 = v.grid_bus_off[g + 1];
+  int64_t t = tile_off ? tile_off[g] : 0;
+  int32_t n = 0;
+  int64_t start = b0;
+  int32_t inc = 0, nb = 0;
+  for (int64_t b = b0; b < b1; ++b) {
+    const int32_t d = v.inc_ptr[b + 1] - v.inc_ptr[b];
+    if (nb > 0 && (inc + d > cap || nb + 1 > cap)) {
+      if (bus0) { bus0[t] = (int32_t)start; bus1[t] = (int32_t)b; ++t; }
+      ++n;
+      start = b;
+      inc = 0;
+      nb = 0;
+    }
+    inc += d;
+    ++nb;
+  }
+  if (bus0) { bus0[t] = (int32_t)start; bus1[t] = (int32_t)b1; }
+  ++n;
+  if (count) count[g] = n;
+}
+
+template <class T>
+std::vector<T> to_host(const T *d, size_t n, cudaStream_t s, int *rc) {
+  std::vector<T> h(n);
+  if (n) {
+    cudaError_t e = cudaMemcpyAsync(h.data(), d, n * sizeof(T), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) *rc = fail(PF_ERR_CUDA, std::string("copy to host: ") + cudaGetErrorString(e));
+  }
+  return h;
+}
+
+// Sums per bus of item values, in item order.
+int bus_sums(Ctx &c, TempList &tmp, const int32_t *d_item_bus, int64_t n_items, const double *d_v0,
+             const double *d_v1, double s0, double s1, double *out0, double *out1, int64_t **ptr_out,
+             uint32_t **order_out, cudaStream_t s) {
+  const int64_t n_bus = c.v.n_bus;
+  const int64_t np = sort_padded(n_items);
+  uint64_t *keys;
+  uint32_t *vals;
+  int32_t *cnt;
+  int64_t *ptr, *stmp;
+  PF_TRY(tmp.alloc(&keys, np));
+  PF_TRY(tmp.alloc(&vals, np));
+  PF_TRY(tmp.alloc(&cnt, n_bus));
+  PF_TRY(tmp.alloc(&ptr, n_bus + 1));
+  PF_TRY(tmp.alloc(&stmp, scan_tmp_elems(n_bus)));
+  PF_CUDA_TRY(cudaMemsetAsync(cnt, 0, n_bus * sizeof(int32_t), s));
+  if (n_items > 0) {
+    k_item_keys<<<nblk(n_items), TB, 0, s>>>(d_item_bus, n_items, keys, vals);
+    PF_TRY(bitonic_sort_pairs(keys, vals, n_items, s));
+    k_count_bus<<<nblk(n_items), TB, 0, s>>>(keys, n_items, cnt);
+  }
+  PF_TRY(exclusive_scan<int32_t>(cnt, ptr, n_bus, stmp, s));
+  k_bus_sums<<<nblk(n_bus), TB, 0, s>>>(ptr, vals, d_v0, d_v1, n_bus, out0, out1, s0, s1);
+  PF_CUDA_TRY(cudaGetLastError());
+  if (ptr_out) *ptr_out = ptr;
+  if (order_out) *order_out = vals;
+  return PF_OK;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------
+// coefficients (also used per call when branch parameters are overridden)
+// --------------------------------------------------------------------------
+
+int compute_coefficients(Ctx &c, const double *r, const double *x, const double *b, const double *tap,
+                         double2 *gb, double2 *ac, double *ahat, double *chat, cudaStream_t s) {
+  if (c.v.n_inc > 0) {
+    k_coeff<<<nblk(c.v.n_inc), TB, 0, s>>>(c.v, r, x, b, tap, gb, ac);
+    PF_CUDA_TRY(cudaGetLastError());
+  }
+  k_hat<<<nblk(c.v.n_bus), TB, 0, s>>>(c.v, ac, ahat, chat);
+  PF_CUDA_TRY(cudaGetLastError());
+  return PF_OK;
+}
+
+// --------------------------------------------------------------------------
+// tiles
+// --------------------------------------------------------------------------
+
+int build_tiles(Ctx &c, int tile_inc, cudaStream_t s) {
+  const int G = c.v.n_grids;
+  int32_t *cnt;
+  TempList tmp;
+  PF_TRY(tmp.alloc(&cnt, G));
+  k_tiles<<<nblk(G, 128), 128, 0, s>>>(c.v, tile_inc, nullptr, cnt, nullptr, nullptr);
+  PF_CUDA_TRY(cudaGetLastError());
+  int rc = PF_OK;
+  std::vector<int32_t> hc = to_host(cnt, G, s, &rc);
+  if (rc) return rc;
+  for (void *p : c.tile_allocations) cudaFree(p);
+  c.tile_allocations.clear();
+  c.grid_tile_off.assign(G + 1, 0);
+  for (int g = 0; g < G; ++g) c.grid_tile_off[g + 1] = c.grid_tile_off[g] + hc[g];
+  c.n_tiles = c.grid_tile_off[G];
+  PF_TRY(dev_alloc(c, &c.tile_bus0, c.n_tiles, &c.tile_allocations));
+  PF_TRY(dev_alloc(c, &c.tile_bus1, c.n_tiles, &c.tile_allocations));
+  PF_TRY(dev_alloc(c, &c.grid_tile_off_d, G + 1, &c.tile_allocations));
+  PF_CUDA_TRY(cudaMemcpyAsync(c.grid_tile_off_d, c.grid_tile_off.data(), (G + 1) * sizeof(int64_t),
+                              cudaMemcpyHostToDevice, s));
+  k_tiles<<<nblk(G, 128), 128, 0, s>>>(c.v, tile_inc, c.grid_tile_off_d, nullptr, c.tile_bus0, c.tile_bus1);
+  PF_CUDA_TRY(cudaGetLastError());
+  const int I = c.v.n_inst;
+  c.unit_off.assign(I + 1, 0);
+  for (int i = 0; i < I; ++i) {
+    const int g = c.inst_grid[i];
+    c.unit_off[i + 1] = c.unit_off[i] + (c.grid_tile_off[g + 1] - c.grid_tile_off[g]);
+  }
+  PF_TRY(dev_alloc(c, &c.inst_unit_off_d, I + 1, &c.tile_allocations));
+  PF_CUDA_TRY(cudaMemcpyAsync(c.inst_unit_off_d, c.unit_off.data(), (I + 1) * sizeof(int64_t),
+                              cudaMemcpyHostToDevice, s));
+  c.v.tile_bus0 = c.tile_bus0;
+  c.v.tile_bus1 = c.tile_bus1;
+  c.v.grid_tile_off = c.grid_tile_off_d;
+  c.v.inst_unit_off = c.inst_unit_off_d;
+  c.v.n_units = c.unit_off[I];
+  c.tuning.tile_inc = tile_inc;
+  PF_CUDA_TRY(cudaStreamSynchronize(s));
+  return PF_OK;
+}
+
+// --------------------------------------------------------------------------
+// the build
+// --------------------------------------------------------------------------
+
+int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance *inst, int n_inst,
+                  int formulation, cudaStream_t s) {
+  if (formulation != PF_REDUCED && formulation != PF_EXTENDED)
+    return fail(PF_ERR_INVALID, "formulation must be PF_REDUCED or PF_EXTENDED");
+  if (n_grids <= 0 || !grids) return fail(PF_ERR_INVALID, "no grids");
+  if (n_inst <= 0 || !inst) return fail(PF_ERR_INVALID, "no instances");
+  const bool ext = formulation == PF_EXTENDED;
+  View &v = c.v;
+  v.formulation = formulation;
+  v.n_grids = n_grids;
+  v.n_inst = n_inst;
+
+  // ---- host: validate, concatenate, sizes ----
+  std::vector<int> npv_distinct(n_grids);
+  int64_t N = 0, M = 0, NL = 0, NPV = 0, NSH = 0, NGEN = 0;
+  for (int g = 0; g < n_grids; ++g) {
+    PF_TRY(validate(grids[g], g, formulation, &npv_distinct[g]));
+    N += grids[g].n_bus;
+    M += grids[g].n_branch;
+    NL += grids[g].n_load;
+    NPV += grids[g].n_pv;
+    NSH += grids[g].n_shunt;
+    NGEN += ext ? grids[g].n_pv + 1 : 0;
+  }
+  if (N >= 0x7fffffffLL - 1 || 2 * M >= 0x7fffffffLL - 1 || NSH + 2 * M >= 0x7fffffffLL)
+    return fail(PF_ERR_UNSUPPORTED, "more buses or branch ends than int32 indices allow");
+  for (int i = 0; i < n_inst; ++i) {
+    if (inst[i].grid < 0 || inst[i].grid >= n_grids)
+      return fail(PF_ERR_INVALID, "instance " + std::to_string(i) + ": grid index out of range");
+    if (inst[i].outage < -1 || inst[i].outage >= grids[inst[i].grid].n_branch)
+      return fail(PF_ERR_INVALID, "instance " + std::to_string(i) + ": outage branch out of range");
+  }
+  v.n_bus = N;
+  v.n_branch = M;
+  v.n_inc = 2 * M;
+
+  std::vector<int32_t> h_from(M), h_to(M), h_bus_grid(N);
+  std::vector<double> h_r(M), h_x(M), h_b(M), h_tap(M), h_shift(M), h_gfr(M), h_gto(M);
+  std::vector<uint8_t> h_status(M);
+  std::vector<int32_t> h_load_bus(NL), h_pv_bus(NPV), h_pv_grid(NPV), h_sh_bus(NSH);
+  std::vector<double> h_load_p(NL), h_load_q(NL), h_pv_p(NPV), h_sh_g(NSH), h_sh_b(NSH), h_vset(NGEN);
+  std::vector<int64_t> h_grid_bus_off(n_grids + 1), h_grid_br_off(n_grids + 1), h_grid_pv_off(n_grids + 1),
+      h_grid_gen_off(n_grids + 1), h_slack_glob(n_grids), h_grid_sh_off(n_grids + 1);
+  std::vector<int32_t> h_grid_nbus(n_grids), h_grid_slack(n_grids), h_grid_ngen(n_grids), h_grid_nbr(n_grids);
+  std::vector<double> h_theta_set(n_grids);
+  c.grid_nf.resize(n_grids);
+  c.grid_nx.resize(n_grids);
+  c.grid_nshunt.resize(n_grids);
+  {
+    int64_t bo = 0, mo = 0, lo = 0, po = 0, so = 0, go = 0;
+    for (int g = 0; g < n_grids; ++g) {
+      const pf_system &G = grids[g];
+      h_grid_bus_off[g] = bo;
+      h_grid_br_off[g] = mo;
+      h_grid_pv_off[g] = po;
+      h_grid_gen_off[g] = go;
+      h_grid_sh_off[g] = so;
+      h_grid_nbus[g] = G.n_bus;
+      h_grid_nbr[g] = G.n_branch;
+      h_grid_slack[g] = G.slack_bus;
+      h_slack_glob[g] = bo + G.slack_bus;
+      h_theta_set[g] = G.slack_theta;
+      h_grid_ngen[g] = ext ? G.n_pv + 1 : 0;
+      c.grid_nshunt[g] = G.n_shunt;
+      for (int64_t b = 0; b < G.n_bus; ++b) h_bus_grid[bo + b] = g;
+      for (int64_t k = 0; k < G.n_branch; ++k) {
+        h_from[mo + k] = (int32_t)(bo + G.br_from[k]);
+        h_to[mo + k] = (int32_t)(bo + G.br_to[k]);
+        h_r[mo + k] = G.br_r[k];
+        h_x[mo + k] = G.br_x[k];
+        h_b[mo + k] = G.br_b ? G.br_b[k] : 0.0;
+        h_tap[mo + k] = G.br_tap ? G.br_tap[k] : 1.0;
+        h_shift[mo + k] = G.br_shift ? G.br_shift[k] : 0.0;
+        h_gfr[mo + k] = G.br_g_fr ? G.br_g_fr[k] : 0.0;
+        h_gto[mo + k] = G.br_g_to ? G.br_g_to[k] : 0.0;
+        h_status[mo + k] = G.br_status ? (G.br_status[k] ? 1 : 0) : 1;
+      }
+      for (int64_t k = 0; k < G.n_load; ++k) {
+        h_load_bus[lo + k] = (int32_t)(bo + G.load_bus[k]);
+        h_load_p[lo + k] = G.load_p[k];
+        h_load_q[lo + k] = G.load_q[k];
+      }
+      for (int64_t k = 0; k < G.n_pv; ++k) {
+        h_pv_bus[po + k] = (int32_t)(bo + G.pv_bus[k]);
+        h_pv_grid[po + k] = g;
+        h_pv_p[po + k] = G.pv_p[k];
+        if (ext) h_vset[go + k] = G.pv_vset[k];
+      }
+      if (ext) h_vset[go + G.n_pv] = G.slack_vset;
+      for (int64_t k = 0; k < G.n_shunt; ++k) {
+        h_sh_bus[so + k] = (int32_t)(bo + G.sh_bus[k]);
+        h_sh_g[so + k] = G.sh_g[k];
+        h_sh_b[so + k] = G.sh_b[k];
+      }
+      const int64_t n = G.n_bus;
+      c.grid_nf[g] = (int32_t)(ext ? 2 * n + G.n_pv + 2 : (n - 1) + (n - 1 - npv_distinct[g]));
+      c.grid_nx[g] = (int32_t)(ext ? 2 * n + G.n_pv + 2 : 2 * n);
+      bo += n;
+      mo += G.n_branch;
+      lo += G.n_load;
+      po += G.n_pv;
+      so += G.n_shunt;
+      go += ext ? G.n_pv + 1 : 0;
+    }
+    h_grid_bus_off[n_grids] = bo;
+    h_grid_br_off[n_grids] = mo;
+    h_grid_pv_off[n_grids] = po;
+    h_grid_gen_off[n_grids] = go;
+    h_grid_sh_off[n_grids] = so;
+  }
+  c.grid_bus_off = h_grid_bus_off;
+  c.grid_br_off = h_grid_br_off;
+  c.grid_sh_off = h_grid_sh_off;
+
+  // ---- upload ----
+  int32_t *d_from, *d_to, *d_bus_grid, *d_load_bus, *d_pv_bus, *d_pv_grid, *d_sh_bus;
+  double *d_r, *d_x, *d_b, *d_tap, *d_shift, *d_gfr, *d_gto, *d_vset;
+  uint8_t *d_status;
+  int64_t *d_grid_bus_off, *d_grid_br_off, *d_grid_gen_off;
+  int32_t *d_grid_nbus, *d_grid_slack, *d_grid_ngen;
+  double *d_theta_set;
+  PF_TRY(upload(c, &d_from, h_from, s));
+  PF_TRY(upload(c, &d_to, h_to, s));
+  PF_TRY(upload(c, &d_r, h_r, s));
+  PF_TRY(upload(c, &d_x, h_x, s));
+  PF_TRY(upload(c, &d_b, h_b, s));
+  PF_TRY(upload(c, &d_tap, h_tap, s));
+  PF_TRY(upload(c, &d_shift, h_shift, s));
+  PF_TRY(upload(c, &d_gfr, h_gfr, s));
+  PF_TRY(upload(c, &d_gto, h_gto, s));
+  PF_TRY(upload(c, &d_status, h_status, s));
+  PF_TRY(upload(c, &d_bus_grid, h_bus_grid, s));
+  PF_TRY(upload(c, &d_grid_bus_off, h_grid_bus_off, s));
+  PF_TRY(upload(c, &d_grid_br_off, h_grid_br_off, s));
+  PF_TRY(upload(c, &d_grid_gen_off, h_grid_gen_off, s));
+  PF_TRY(upload(c, &d_grid_nbus, h_grid_nbus, s));
+  PF_TRY(upload(c, &d_grid_slack, h_grid_slack, s));
+  PF_TRY(upload(c, &d_grid_ngen, h_grid_ngen, s));
+  PF_TRY(upload(c, &d_theta_set, h_theta_set, s));
+  PF_TRY(upload(c, &d_vset, h_vset, s));
+  TempList tmp;
+  int64_t *d_slack_glob, *d_grid_pv_off, *d_grid_sh_off;
+  {
+    auto up_tmp = [&](auto **p, const auto &h) -> int {
+      PF_TRY(tmp.alloc(p, h.size()));
+      if (!h.empty())
+        PF_CUDA_TRY(cudaMemcpyAsync(*p, h.data(), h.size() * sizeof(h[0]), cudaMemcpyHostToDevice, s));
+      return PF_OK;
+    };
+    PF_TRY(up_tmp(&d_load_bus, h_load_bus));
+    PF_TRY(up_tmp(&d_pv_bus, h_pv_bus));
+    PF_TRY(up_tmp(&d_pv_grid, h_pv_grid));
+    PF_TRY(up_tmp(&d_sh_bus, h_sh_bus));
+    PF_TRY(up_tmp(&d_slack_glob, h_slack_glob));
+    PF_TRY(up_tmp(&d_grid_pv_off, h_grid_pv_off));
+    PF_TRY(up_tmp(&d_grid_sh_off, h_grid_sh_off));
+    double *d_load_p, *d_load_q, *d_pv_p, *d_sh_g, *d_sh_b;
+    PF_TRY(up_tmp(&d_load_p, h_load_p));
+    PF_TRY(up_tmp(&d_load_q, h_load_q));
+    PF_TRY(up_tmp(&d_pv_p, h_pv_p));
+    PF_TRY(up_tmp(&d_sh_g, h_sh_g));
+    PF_TRY(up_tmp(&d_sh_b, h_sh_b));
+
+    v.br_from = d_from; v.br_to = d_to; v.br_r = d_r; v.br_x = d_x; v.br_b = d_b; v.br_tap = d_tap;
+    v.br_shift = d_shift; v.br_gfr = d_gfr; v.br_gto = d_gto; v.br_status = d_status;
+    v.bus_grid = d_bus_grid;
+    v.grid_bus_off = d_grid_bus_off; v.grid_br_off = d_grid_br_off; v.grid_gen_off = d_grid_gen_off;
+    v.grid_nbus = d_grid_nbus; v.grid_slack = d_grid_slack; v.grid_ngen = d_grid_ngen;
+    v.grid_theta_set = d_theta_set; v.gen_vset = d_vset;
+
+    // ---- injections and shunt totals per bus (sums in item order) ----
+    double *g_sh, *b_sh, *p_inj, *q_inj, *pl, *ql, *pg;
+    PF_TRY(dev_alloc(c, &g_sh, N));
+    PF_TRY(dev_alloc(c, &b_sh, N));
+    PF_TRY(dev_alloc(c, &p_inj, N));
+    PF_TRY(dev_alloc(c, &q_inj, N));
+    PF_TRY(tmp.alloc(&pl, N));
+    PF_TRY(tmp.alloc(&ql, N));
+    PF_TRY(tmp.alloc(&pg, N));
+    int64_t *sh_ptr;
+    uint32_t *sh_order;
+    PF_TRY(bus_sums(c, tmp, d_sh_bus, NSH, d_sh_g, d_sh_b, 1.0, 1.0, g_sh, b_sh, &sh_ptr, &sh_order, s));
+    PF_TRY(bus_sums(c, tmp, d_load_bus, NL, d_load_p, d_load_q, 1.0, 1.0, pl, ql, nullptr, nullptr, s));
+    PF_TRY(bus_sums(c, tmp, d_pv_bus, NPV, d_pv_p, nullptr, 1.0, 1.0, pg, nullptr, nullptr, nullptr, s));
+    k_net_injection<<<nblk(N), TB, 0, s>>>(pg, pl, ql, N, p_inj, q_inj);
+    PF_CUDA_TRY(cudaGetLastError());
+    v.g_sh = g_sh; v.b_sh = b_sh; v.p_inj = p_inj; v.q_inj = q_inj;
+
+    // ---- bus types and row maps ----
+    int8_t *type;
+    uint8_t *ns, *pq;
+    int64_t *ex_ns, *ex_pq, *stmp;
+    PF_TRY(tmp.alloc(&type, N));
+    PF_TRY(tmp.alloc(&ns, N));
+    PF_TRY(tmp.alloc(&pq, N));
+    PF_TRY(tmp.alloc(&ex_ns, N + 1));
+    PF_TRY(tmp.alloc(&ex_pq, N + 1));
+    PF_TRY(tmp.alloc(&stmp, scan_tmp_elems(std::max<int64_t>(N, 2 * M) + 1)));
+    PF_CUDA_TRY(cudaMemsetAsync(type, 0, N, s));
+    k_bus_type<<<nblk(std::max<int64_t>(NPV, n_grids)), TB, 0, s>>>(type, d_pv_bus, NPV, d_slack_glob, n_grids);
+    k_flags<<<nblk(N), TB, 0, s>>>(type, N, ns, pq);
+    PF_TRY(exclusive_scan<uint8_t>(ns, ex_ns, N, stmp, s));
+    PF_TRY(exclusive_scan<uint8_t>(pq, ex_pq, N, stmp, s));
+    int32_t *row_p, *row_q, *gen, *gen_bus;
+    PF_TRY(dev_alloc(c, &row_p, N));
+    PF_TRY(dev_alloc(c, &row_q, N));
+    PF_TRY(dev_alloc(c, &gen, N));
+    PF_TRY(dev_alloc(c, &gen_bus, NGEN));
+    k_row_maps<<<nblk(N), TB, 0, s>>>(v, type, ex_ns, ex_pq, row_p, row_q, gen);
+    PF_CUDA_TRY(cudaGetLastError());
+    if (ext) {
+      k_gen_map<<<nblk(std::max<int64_t>(NPV, n_grids)), TB, 0, s>>>(v, d_pv_bus, d_pv_grid, d_grid_pv_off, NPV,
+                                                                    gen, gen_bus);
+      PF_CUDA_TRY(cudaGetLastError());
+    }
+    v.row_p = row_p; v.row_q = row_q; v.gen = gen; v.gen_bus = gen_bus;
+
+    // ---- incidence list ----
+    const int64_t NI = 2 * M;
+    const int64_t np = sort_padded(NI);
+    uint64_t *keys;
+    uint32_t *vals;
+    int32_t *pos_of, *deg, *inc_own, *inc_other, *inc_code, *inc_ptr, *mirror, *grp, *stats;
+    int64_t *ptr64;
+    PF_TRY(tmp.alloc(&keys, np));
+    PF_TRY(tmp.alloc(&vals, np));
+    PF_TRY(tmp.alloc(&pos_of, NI));
+    PF_TRY(tmp.alloc(&deg, N));
+    PF_TRY(tmp.alloc(&ptr64, N + 1));
+    PF_TRY(tmp.alloc(&stats, 4));
+    PF_TRY(dev_alloc(c, &inc_own, NI));
+    PF_TRY(dev_alloc(c, &inc_other, NI));
+    PF_TRY(dev_alloc(c, &inc_code, NI));
+    PF_TRY(dev_alloc(c, &inc_ptr, N + 1));
+    PF_TRY(dev_alloc(c, &mirror, NI));
+    PF_TRY(dev_alloc(c, &grp, NI));
+    PF_CUDA_TRY(cudaMemsetAsync(deg, 0, N * sizeof(int32_t), s));
+    PF_CUDA_TRY(cudaMemsetAsync(stats, 0, 4 * sizeof(int32_t), s));
+    if (NI > 0) {
+      k_make_keys<<<nblk(NI), TB, 0, s>>>(d_from, d_to, M, keys, vals);
+      PF_TRY(bitonic_sort_pairs(keys, vals, NI, s));
+      k_unpack<<<nblk(NI), TB, 0, s>>>(keys, vals, NI, inc_own, inc_other, inc_code, pos_of, deg);
+      PF_CUDA_TRY(cudaGetLastError());
+    }
+    PF_TRY(exclusive_scan<int32_t>(deg, ptr64, N, stmp, s));
+    k_i64_to_i32<<<nblk(N + 1), TB, 0, s>>>(ptr64, inc_ptr, N + 1);
+    v.inc_own = inc_own; v.inc_other = inc_other; v.inc_code = inc_code; v.inc_ptr = inc_ptr;
+    if (NI > 0) {
+      k_mirror_groups<<<nblk(NI), TB, 0, s>>>(v, pos_of, mirror, grp, stats);
+      PF_CUDA_TRY(cudaGetLastError());
+    }
+    v.inc_mirror = mirror; v.inc_grp = grp;
+    int rc = PF_OK;
+    std::vector<int32_t> hstats = to_host(stats, 4, s, &rc);
+    if (rc) return rc;
+    c.max_group = hstats[0];
+    c.max_degree = hstats[1];
+    if (c.max_group > kMinTileInc)
+      return fail(PF_ERR_UNSUPPORTED, "more than " + std::to_string(kMinTileInc) +
+                                          " parallel branches between one pair of buses");
+
+    // ---- row structure, rowptr, colind ----
+    int64_t FT = 0;
+    std::vector<int64_t> h_grid_f_off(n_grids + 1), h_grid_row_off(n_grids + 1);
+    for (int g = 0; g < n_grids; ++g) {
+      h_grid_f_off[g] = FT;
+      h_grid_row_off[g] = FT + g;
+      FT += c.grid_nf[g];
+    }
+    h_grid_f_off[n_grids] = FT;
+    h_grid_row_off[n_grids] = FT + n_grids;
+    c.grid_row_off = h_grid_row_off;
+    int64_t *d_grid_f_off, *d_grid_row_off;
+    PF_TRY(up_tmp(&d_grid_f_off, h_grid_f_off));
+    PF_TRY(upload(c, &d_grid_row_off, h_grid_row_off, s));
+    int2 *inc_rt, *diag;
+    int32_t *len_tv, *rowlen, *rowptr, *nnz_g, *err;
+    int64_t *S, *stmp2;
+    PF_TRY(dev_alloc(c, &inc_rt, NI));
+    PF_TRY(dev_alloc(c, &diag, N));
+    PF_TRY(dev_alloc(c, &len_tv, N));
+    PF_TRY(tmp.alloc(&rowlen, FT));
+    PF_TRY(tmp.alloc(&S, FT + 1));
+    PF_TRY(tmp.alloc(&stmp2, scan_tmp_elems(FT) + 1));
+    PF_TRY(dev_alloc(c, &rowptr, FT + n_grids));
+    PF_TRY(tmp.alloc(&nnz_g, n_grids));
+    PF_TRY(dev_alloc(c, &err, 1));
+    PF_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
+    v.dev_error = err;
+    k_row_struct<<<nblk(N), TB, 0, s>>>(v, d_grid_f_off, inc_rt, diag, len_tv, rowlen);
+    if (ext) k_gen_rowlen<<<nblk(std::max<int64_t>(NGEN, n_grids)), TB, 0, s>>>(v, d_grid_f_off, rowlen, NGEN);
+    PF_CUDA_TRY(cudaGetLastError());
+    PF_TRY(exclusive_scan<int32_t>(rowlen, S, FT, stmp2, s));
+    k_rowptr<<<nblk(FT + n_grids), TB, 0, s>>>(S, d_grid_f_off, d_grid_row_off, n_grids, FT + n_grids, rowptr,
+                                               nnz_g, err);
+    PF_CUDA_TRY(cudaGetLastError());
+    v.inc_rt = inc_rt; v.diag = diag; v.len_tv = len_tv;
+    c.rowptr = rowptr;
+    c.grid_nnz = to_host(nnz_g, n_grids, s, &rc);
+    if (rc) return rc;
+    {
+      std::vector<int32_t> herr = to_host(err, 1, s, &rc);
+      if (rc) return rc;
+      if (herr[0]) return fail(PF_ERR_UNSUPPORTED, "a grid has more than 2^31 Jacobian nonzeros");
+    }
+    c.grid_nnz_off.assign(n_grids + 1, 0);
+    for (int g = 0; g < n_grids; ++g) c.grid_nnz_off[g + 1] = c.grid_nnz_off[g] + c.grid_nnz[g];
+    const int64_t NNZ = c.grid_nnz_off[n_grids];
+    int64_t *d_grid_nnz_off;
+    PF_TRY(upload(c, &d_grid_nnz_off, c.grid_nnz_off, s));
+    int32_t *base_p, *base_q, *colind, *gen_pos, *pos_gth, *row_gth;
+    PF_TRY(dev_alloc(c, &base_p, N));
+    PF_TRY(dev_alloc(c, &base_q, N));
+    PF_TRY(dev_alloc(c, &colind, NNZ));
+    PF_TRY(dev_alloc(c, &gen_pos, NGEN));
+    PF_TRY(dev_alloc(c, &pos_gth, n_grids));
+    PF_TRY(dev_alloc(c, &row_gth, n_grids));
+    PF_CUDA_TRY(cudaMemsetAsync(pos_gth, 0xff, n_grids * sizeof(int32_t), s));
+    PF_CUDA_TRY(cudaMemsetAsync(row_gth, 0xff, n_grids * sizeof(int32_t), s));
+    k_colind<<<nblk(N), TB, 0, s>>>(v, rowptr, d_grid_row_off, d_grid_nnz_off, base_p, base_q, colind);
+    if (ext)
+      k_gen_cols<<<nblk(std::max<int64_t>(NGEN, n_grids)), TB, 0, s>>>(v, rowptr, d_grid_row_off, d_grid_nnz_off,
+                                                                      colind, gen_pos, pos_gth, row_gth, NGEN);
+    PF_CUDA_TRY(cudaGetLastError());
+    v.base_p = base_p; v.base_q = base_q; v.gen_pos = gen_pos;
+    v.grid_pos_gth = pos_gth; v.grid_row_gth = row_gth;
+    c.colind = colind;
+
+    // ---- coefficients ----
+    double2 *gb, *ac;
+    double *ahat, *chat;
+    PF_TRY(dev_alloc(c, &gb, NI));
+    PF_TRY(dev_alloc(c, &ac, NI));
+    PF_TRY(dev_alloc(c, &ahat, N));
+    PF_TRY(dev_alloc(c, &chat, N));
+    PF_TRY(compute_coefficients(c, nullptr, nullptr, nullptr, nullptr, gb, ac, ahat, chat, s));
+    v.inc_gb = gb; v.inc_ac = ac; v.a_hat = ahat; v.c_hat = chat;
+    PF_TRY(dev_alloc(c, &c.ov_gb, NI));
+    PF_TRY(dev_alloc(c, &c.ov_ac, NI));
+    PF_TRY(dev_alloc(c, &c.ov_ahat, N));
+    PF_TRY(dev_alloc(c, &c.ov_chat, N));
+
+    // ---- contribution list ----
+    int32_t *count;
+    int64_t *S2, *stmp3, *src_len;
+    PF_TRY(tmp.alloc(&count, NNZ));
+    PF_TRY(tmp.alloc(&S2, NNZ + 1));
+    PF_TRY(tmp.alloc(&stmp3, scan_tmp_elems(NNZ) + 1));
+    PF_TRY(tmp.alloc(&src_len, n_grids));
+    std::vector<int64_t> h_grid_inc_off(n_grids + 1);
+    for (int g = 0; g <= n_grids; ++g) h_grid_inc_off[g] = 2 * h_grid_br_off[g];
+    int64_t *d_grid_inc_off;
+    int32_t *d_grid_nbr;
+    PF_TRY(up_tmp(&d_grid_inc_off, h_grid_inc_off));
+    PF_TRY(up_tmp(&d_grid_nbr, h_grid_nbr));
+    c.grid_cptr_off.assign(n_grids + 1, 0);
+    for (int g = 0; g < n_grids; ++g) c.grid_cptr_off[g + 1] = c.grid_cptr_off[g] + c.grid_nnz[g] + 1;
+    int64_t *d_grid_cptr_off;
+    PF_TRY(up_tmp(&d_grid_cptr_off, c.grid_cptr_off));
+    k_contrib<<<nblk(N), TB, 0, s>>>(v, 0, d_grid_nnz_off, d_grid_cptr_off, nullptr, sh_ptr, sh_order,
+                                     d_grid_sh_off, d_grid_inc_off, d_grid_nbr, count, nullptr, nullptr);
+    if (ext)
+      k_contrib_const<<<nblk(std::max<int64_t>(NGEN, n_grids)), TB, 0, s>>>(
+          v, 0, d_grid_nnz_off, d_grid_cptr_off, nullptr, gen_pos, pos_gth, NGEN, count, nullptr, nullptr);
+    PF_CUDA_TRY(cudaGetLastError());
+    PF_TRY(exclusive_scan<int32_t>(count, S2, NNZ, stmp3, s));
+    int64_t *cptr;
+    const int64_t CPT = c.grid_cptr_off[n_grids];
+    PF_TRY(dev_alloc(c, &cptr, CPT));
+    k_cptr<<<nblk(CPT), TB, 0, s>>>(S2, d_grid_nnz_off, d_grid_cptr_off, n_grids, CPT, cptr, src_len);
+    PF_CUDA_TRY(cudaGetLastError());
+    std::vector<int64_t> h_src_len = to_host(src_len, n_grids, s, &rc);
+    if (rc) return rc;
+    c.grid_csrc_off.assign(n_grids + 1, 0);
+    for (int g = 0; g < n_grids; ++g) c.grid_csrc_off[g + 1] = c.grid_csrc_off[g] + h_src_len[g];
+    int64_t *d_grid_csrc_off;
+    PF_TRY(up_tmp(&d_grid_csrc_off, c.grid_csrc_off));
+    int32_t *src;
+    PF_TRY(dev_alloc(c, &src, c.grid_csrc_off[n_grids]));
+    k_contrib<<<nblk(N), TB, 0, s>>>(v, 1, d_grid_nnz_off, d_grid_cptr_off, d_grid_csrc_off, sh_ptr, sh_order,
+                                     d_grid_sh_off, d_grid_inc_off, d_grid_nbr, nullptr, cptr, src);
+    if (ext)
+      k_contrib_const<<<nblk(std::max<int64_t>(NGEN, n_grids)), TB, 0, s>>>(
+          v, 1, d_grid_nnz_off, d_grid_cptr_off, d_grid_csrc_off, gen_pos, pos_gth, NGEN, nullptr, cptr, src);
+    PF_CUDA_TRY(cudaGetLastError());
+    c.contrib_ptr = cptr;
+    c.contrib_src = src;
+  }
+
+  // ---- instances ----
+  c.inst_grid.resize(n_inst);
+  c.inst_outage.resize(n_inst);
+  c.x_off.assign(n_inst + 1, 0);
+  c.f_off.assign(n_inst + 1, 0);
+  c.v_off.assign(n_inst + 1, 0);
+  c.bus_off.assign(n_inst + 1, 0);
+  c.br_off.assign(n_inst + 1, 0);
+  c.any_outage = false;
+  for (int i = 0; i < n_inst; ++i) {
+    const int g = inst[i].grid;
+    c.inst_grid[i] = g;
+    c.inst_outage[i] = inst[i].outage >= 0 ? (int32_t)(h_grid_br_off[g] + inst[i].outage) : -1;
+    c.any_outage |= inst[i].outage >= 0;
+    c.x_off[i + 1] = c.x_off[i] + c.grid_nx[g];
+    c.f_off[i + 1] = c.f_off[i] + c.grid_nf[g];
+    c.v_off[i + 1] = c.v_off[i] + c.grid_nnz[g];
+    c.bus_off[i + 1] = c.bus_off[i] + h_grid_nbus[g];
+    c.br_off[i + 1] = c.br_off[i] + h_grid_nbr[g];
+  }
+  c.n_x = c.x_off[n_inst];
+  c.n_f = c.f_off[n_inst];
+  c.nnz = c.v_off[n_inst];
+  v.n_bus_inst = c.bus_off[n_inst];
+  c.n_branch_inst = c.br_off[n_inst];
+  int32_t *d_inst_grid, *d_inst_outage;
+  int64_t *d_x_off, *d_f_off, *d_v_off, *d_bus_off, *d_br_off;
+  PF_TRY(upload(c, &d_inst_grid, c.inst_grid, s));
+  PF_TRY(upload(c, &d_inst_outage, c.inst_outage, s));
+  PF_TRY(upload(c, &d_x_off, c.x_off, s));
+  PF_TRY(upload(c, &d_f_off, c.f_off, s));
+  PF_TRY(upload(c, &d_v_off, c.v_off, s));
+  PF_TRY(upload(c, &d_bus_off, c.bus_off, s));
+  PF_TRY(upload(c, &d_br_off, c.br_off, s));
+  v.inst_grid = d_inst_grid; v.inst_outage = d_inst_outage;
+  v.inst_x_off = d_x_off; v.inst_f_off = d_f_off; v.inst_v_off = d_v_off;
+  v.inst_bus_off = d_bus_off; v.inst_br_off = d_br_off;
+  PF_TRY(dev_alloc(c, &v.phasor, v.n_bus_inst));
+
+  int dev = 0;
+  PF_CUDA_TRY(cudaGetDevice(&dev));
+  PF_CUDA_TRY(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev));
+
+  int tile = 256;
+  while (tile < c.max_group && tile < kMaxTileInc) tile *= 2;
+  PF_TRY(build_tiles(c, tile, s));
+  PF_CUDA_TRY(cudaStreamSynchronize(s));
+  return PF_OK;
+}
+
+}  // namespace pf

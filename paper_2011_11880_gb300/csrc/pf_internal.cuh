@@ -1,0 +1,190 @@
+// Internal layout of a pf_ctx.  `View` is the plain set of device pointers
+// and sizes that kernels receive by value; `Ctx` adds the host-side
+// bookkeeping.  All arrays are structure-of-arrays in HBM.
+//
+// Numbering: the grids of a context are concatenated, so every bus, branch
+// and branch end ("incidence") has one global index; F rows, J columns and
+// CSR positions are local to a grid (identical for all of its instances)
+// and are offset per instance into the caller's x / F / vals vectors.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pf.h"
+
+namespace pf {
+
+constexpr int kNumSMsDefault = 152;
+constexpr int kMaxTileInc = 1024;
+constexpr int kMinTileInc = 64;
+
+// Thread-local error message behind pf_last_error().
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+
+#define PF_CUDA_TRY(expr)                                                            \
+  do {                                                                               \
+    cudaError_t _e = (expr);                                                         \
+    if (_e != cudaSuccess)                                                           \
+      return ::pf::fail(_e == cudaErrorMemoryAllocation ? PF_ERR_OOM : PF_ERR_CUDA,  \
+                        std::string(#expr) + ": " + cudaGetErrorString(_e));         \
+  } while (0)
+
+#define PF_TRY(expr)         \
+  do {                       \
+    int _rc = (expr);        \
+    if (_rc) return _rc;     \
+  } while (0)
+
+// Device error flag bits (set with integer atomics).
+constexpr int kErrMap = 1;      // an index-map entry failed a consistency check
+constexpr int kErrTimeout = 2;  // a bounded wait gave up
+constexpr int kErrChunk = 4;    // a tile could not be cut at a parallel-group boundary
+
+struct View {
+  int formulation;
+  int n_grids, n_inst;
+  int64_t n_bus, n_branch, n_inc, n_units, n_bus_inst;
+
+  // per bus
+  const int32_t *inc_ptr;   // [n_bus+1] first incidence of each bus
+  const int32_t *row_p;     // [n_bus] local F row of the P mismatch, -1 absent
+  const int32_t *row_q;     // [n_bus] local F row of the Q mismatch, -1 absent
+  const int32_t *base_p;    // [n_bus] rowptr[row_p]: first CSR position of the P row
+  const int32_t *base_q;    // [n_bus] rowptr[row_q]
+  const int2 *diag;         // [n_bus] in-row offsets of columns (theta_o, V_o), -1 absent
+  const int32_t *len_tv;    // [n_bus] theta + V columns of the bus's rows
+  const int32_t *gen;       // [n_bus] extended: local generator index, -1 none
+  const double *a_hat;      // [n_bus] sum over ends of A_e, plus shunt g
+  const double *c_hat;      // [n_bus] sum over ends of C_e, plus shunt b
+  const double *g_sh;       // [n_bus] shunt conductance total
+  const double *b_sh;       // [n_bus] shunt susceptance total
+  const double *p_inj;      // [n_bus] net P injection (P_g - P_load)
+  const double *q_inj;      // [n_bus] net Q injection (-Q_load)
+  const int32_t *bus_grid;  // [n_bus]
+
+  // per branch
+  const int32_t *br_from, *br_to;   // global bus ids
+  const double *br_r, *br_x, *br_b, *br_tap, *br_shift, *br_gfr, *br_gto;
+  const uint8_t *br_status;
+
+  // per incidence, sorted by (own bus, other bus, branch)
+  const int32_t *inc_own, *inc_other, *inc_code;  // code = 2*branch + end
+  const double2 *inc_gb;    // (G, B) of this end (rotated series admittance / tau)
+  const double2 *inc_ac;    // (A, C) of this end: V_o^2 coefficients of P and -Q
+  const int2 *inc_rt;       // in-row offsets of (theta_k, V_k) columns, -1 absent
+  const int32_t *inc_grp;   // at a group head: parallel ends to the same bus; else 0
+  const int32_t *inc_mirror;// position of the other end of the same branch
+
+  // per grid
+  const int64_t *grid_bus_off, *grid_br_off;  // [n_grids+1]
+  const int32_t *grid_nbus, *grid_slack, *grid_ngen;
+  const int64_t *grid_gen_off;                // [n_grids+1]
+  const double *grid_theta_set;
+  const int32_t *grid_row_gth;                // extended: g_theta row, else -1
+  const int32_t *grid_pos_gth;                // CSR position of the g_theta entry
+  const double *gen_vset;                     // [sum ngen]
+  const int32_t *gen_pos;                     // [sum ngen] CSR position of the g_V entry
+  const int32_t *gen_bus;                     // [sum ngen] global bus of each generator
+
+  // tiles (contiguous bus ranges)
+  const int32_t *tile_bus0, *tile_bus1;
+  const int64_t *grid_tile_off;               // [n_grids+1]
+
+  // per instance
+  const int32_t *inst_grid, *inst_outage;     // outage: global branch id or -1
+  const int64_t *inst_x_off, *inst_f_off, *inst_v_off, *inst_bus_off, *inst_br_off;
+  const int64_t *inst_unit_off;               // [n_inst+1] tiles of earlier instances
+
+  // scratch
+  double2 *phasor;                            // [n_bus_inst] (cos theta, sin theta)
+  int32_t *dev_error;
+};
+
+struct Ctx {
+  View v{};
+  int num_sms = kNumSMsDefault;
+  pf_tuning tuning{256, 0};
+  int max_degree = 0, max_group = 0;
+  int64_t n_x = 0, n_f = 0, nnz = 0, n_branch_inst = 0, n_tiles = 0;
+
+  // host copies of per-grid / per-instance layout
+  std::vector<int64_t> grid_bus_off, grid_br_off, grid_row_off, grid_nnz_off, grid_cptr_off,
+      grid_csrc_off, grid_sh_off, grid_tile_off;
+  std::vector<int32_t> grid_nf, grid_nnz, grid_nx, grid_nshunt;
+  std::vector<int32_t> inst_grid, inst_outage;
+  std::vector<int64_t> x_off, f_off, v_off, bus_off, br_off, unit_off;
+  bool any_outage = false;
+
+  // device arrays not in View
+  int32_t *rowptr = nullptr;       // per grid n_f+1 local entries, at grid_row_off
+  int32_t *colind = nullptr;       // per grid nnz entries, at grid_nnz_off
+  int64_t *contrib_ptr = nullptr;  // per grid nnz+1 local entries, at grid_cptr_off
+  int32_t *contrib_src = nullptr;  // at grid_csrc_off
+  int32_t *tile_bus0 = nullptr, *tile_bus1 = nullptr;
+  int64_t *grid_tile_off_d = nullptr;
+  int64_t *inst_unit_off_d = nullptr;
+
+  // override scratch (coefficients recomputed from per-call parameters)
+  double2 *ov_gb = nullptr, *ov_ac = nullptr;
+  double *ov_ahat = nullptr, *ov_chat = nullptr;
+
+  // host-call staging, allocated on first use
+  double *stage_x = nullptr, *stage_f = nullptr, *stage_v = nullptr;
+
+  std::vector<void *> allocations;
+  std::vector<void *> tile_allocations;
+};
+
+template <class T>
+int dev_alloc(Ctx &c, T **p, size_t n, std::vector<void *> *list = nullptr) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+  if (e != cudaSuccess)
+    return fail(PF_ERR_OOM, "cudaMalloc of " + std::to_string(n * sizeof(T)) +
+                                " bytes: " + cudaGetErrorString(e));
+  (list ? *list : c.allocations).push_back(q);
+  *p = static_cast<T *>(q);
+  return PF_OK;
+}
+
+template <class T>
+int upload(Ctx &c, T **p, const std::vector<T> &h, cudaStream_t s) {
+  PF_TRY(dev_alloc(c, p, h.size()));
+  if (!h.empty())
+    PF_CUDA_TRY(cudaMemcpyAsync(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  return PF_OK;
+}
+
+// ---- build (pf_build.cu) ----
+int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance *inst,
+                  int n_inst, int formulation, cudaStream_t s);
+int build_tiles(Ctx &c, int tile_inc, cudaStream_t s);
+// Per-end coefficients (G, B, A, C) and per-bus sums (A_hat, C_hat) from the
+// branch parameters; any of r, x, b, tap may be overridden by device arrays.
+int compute_coefficients(Ctx &c, const double *r, const double *x, const double *b,
+                         const double *tap, double2 *gb, double2 *ac, double *ahat, double *chat,
+                         cudaStream_t s);
+
+// ---- evaluation (pf_eval.cu) ----
+int launch_eval(Ctx &c, const double *x, const pf_overrides *ov, double *F, double *vals,
+                cudaStream_t s);
+int launch_vjp(Ctx &c, const double *x, const pf_overrides *ov, const double *v, int n_cot,
+               const pf_grads *g, cudaStream_t s);
+
+// Largest i in [0, n) with off[i] <= key (off ascending, off[0] = 0).
+__device__ __forceinline__ int find_segment(const int64_t *__restrict__ off, int n, int64_t key) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(off + mid) <= key) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+}  // namespace pf

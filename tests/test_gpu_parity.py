@@ -1,0 +1,190 @@
+"""CUDA path vs the CPU oracle through the C ABI: bit-exact index maps, F and
+J values within 1e-12 rel / 1e-10 abs, determinism across runs and tunings,
+edge cases.  GPU only."""
+import numpy as np
+import pytest
+import torch
+
+import gridgen
+import oracle
+from oracle import REDUCED, EXTENDED
+from tests.gpu_common import assert_tol, edge_grid, star_grid, state, three_bus, two_bus
+
+pytestmark = pytest.mark.gpu
+
+MODES = [REDUCED, EXTENDED]
+MNAME = {REDUCED: "reduced", EXTENDED: "extended"}
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2011_11880_gb300 as p
+    return p
+
+
+def grids():
+    return {
+        "two_bus": two_bus(),
+        "three_bus": three_bus(),
+        "grid30": gridgen.synthetic_grid(30, 7, n_branch=39, end_g_frac=0.2, xfmr_frac=0.3, shift_frac=0.3,
+                                         cluster=10),
+        "grid200": gridgen.grid_200(),
+        "edge300": edge_grid(),
+        "star": star_grid(),
+        "grid2000": gridgen.synthetic_grid(2000, 21),
+    }
+
+
+GRIDS = grids()
+
+
+def gpu_eval(P, sys, x_np, mode, tuning=None):
+    ctx = P.Context(sys, MNAME[mode])
+    if tuning:
+        ctx.set_tuning(*tuning)
+    x = torch.from_numpy(x_np).cuda()
+    F, v = ctx.residual_jacobian(x)
+    torch.cuda.synchronize()
+    return ctx, F.cpu().numpy(), v.cpu().numpy()
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("name", list(GRIDS))
+def test_pattern_and_maps_bit_exact(P, name, mode):
+    sys = GRIDS[name]
+    ctx = P.Context(sys, MNAME[mode])
+    rp, ci = ctx.pattern()
+    x0 = gridgen.flat_state(sys, mode == EXTENDED)
+    rpo, cio, _ = oracle.jacobian(sys, x0, mode)
+    assert np.array_equal(rp, rpo) and np.array_equal(ci, cio)
+    ip, code, oth = ctx.incidence()
+    ipo, codeo, otho = oracle.incidence_lists(sys)
+    assert np.array_equal(ip, ipo) and np.array_equal(code, codeo) and np.array_equal(oth, otho)
+    if sys.n_bus <= 2000:
+        cp, src = ctx.contributions()
+        cpo, srco = oracle.contribution_lists(sys, mode)
+        assert np.array_equal(cp, cpo) and np.array_equal(src, srco)
+    d = ctx.dims
+    fm = oracle.Formulation(sys, mode)
+    assert d.n_f == fm.n_rows and d.nnz == rpo[-1] and d.n_x == x0.shape[0]
+    ctx.check_device()
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("name", list(GRIDS))
+def test_values_match_oracle(P, name, mode):
+    sys = GRIDS[name]
+    for k in (0, 1, 2):
+        x = state(sys, k, mode == EXTENDED)
+        ctx, F, v = gpu_eval(P, sys, x, mode)
+        assert_tol(F, oracle.residual(sys, x, mode), f"{name} F state {k}")
+        assert_tol(v, oracle.jacobian(sys, x, mode)[2], f"{name} J state {k}")
+        ctx.check_device()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_200bus_six_states_split_and_fused(P, mode):
+    """Config 1: flat start and 5 perturbed states; F only, J only and fused agree bit for bit."""
+    sys = gridgen.grid_200()
+    ctx = P.Context(sys, MNAME[mode])
+    for k in range(6):
+        xn = state(sys, k, mode == EXTENDED)
+        x = torch.from_numpy(xn).cuda()
+        F1 = ctx.residual(x)
+        v1 = ctx.jacobian(x)
+        F2, v2 = ctx.residual_jacobian(x)
+        assert torch.equal(F1, F2) and torch.equal(v1, v2)
+        assert_tol(F1.cpu().numpy(), oracle.residual(sys, xn, mode), f"F {k}")
+        assert_tol(v1.cpu().numpy(), oracle.jacobian(sys, xn, mode)[2], f"J {k}")
+
+
+def test_zero_residual_at_oracle_solution(P):
+    """F at the oracle's Newton solution of the 200-bus case is <= 1e-10."""
+    sys = gridgen.grid_200()
+    xs, hist = oracle.newton_dense(sys, gridgen.flat_state(sys))
+    assert hist[-1] <= 1e-10
+    ctx = P.Context(sys)
+    F = ctx.residual(torch.from_numpy(xs).cuda()).cpu().numpy()
+    assert np.max(np.abs(F)) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["grid200", "star", "edge300"])
+def test_deterministic_across_runs_and_tunings(P, name):
+    sys = GRIDS[name]
+    x = torch.from_numpy(state(sys, 3)).cuda()
+    ctx = P.Context(sys)
+    F0, v0 = ctx.residual_jacobian(x)
+    for _ in range(3):
+        F1, v1 = ctx.residual_jacobian(x)
+        assert torch.equal(F0, F1) and torch.equal(v0, v1)
+    for tile in (64, 96, 128, 512, 1024):
+        for ctas in (0, 1, 3):
+            ctx.set_tuning(tile, ctas)
+            F1, v1 = ctx.residual_jacobian(x)
+            assert torch.equal(F0, F1) and torch.equal(v0, v1), (tile, ctas)
+    ctx.check_device()
+
+
+def test_autotune_keeps_results(P):
+    sys = gridgen.synthetic_grid(2000, 5)
+    ctx = P.Context(sys)
+    x = torch.from_numpy(state(sys, 2)).cuda()
+    F0, v0 = ctx.residual_jacobian(x)
+    F, v = torch.empty_like(F0), torch.empty_like(v0)
+    t = ctx.autotune(x, F, v)
+    assert t["tile_inc"] in (128, 256, 512)
+    F1, v1 = ctx.residual_jacobian(x)
+    assert torch.equal(F0, F1) and torch.equal(v0, v1)
+
+
+def test_host_entry_point_matches_device(P):
+    sys = GRIDS["edge300"]
+    ctx = P.Context(sys)
+    xn = state(sys, 4)
+    F_d, v_d = ctx.residual_jacobian(torch.from_numpy(xn).cuda())
+    F_h = np.empty(ctx.dims.n_f)
+    v_h = np.empty(ctx.dims.nnz)
+    ctx.residual_jacobian_host(xn, F_h, v_h)
+    assert np.array_equal(F_h, F_d.cpu().numpy()) and np.array_equal(v_h, v_d.cpu().numpy())
+
+
+def test_parameter_overrides_match_oracle(P):
+    """pf_eval with per-call r, x, b_c, tap and injection overrides."""
+    sys = GRIDS["grid30"]
+    rng = np.random.default_rng(0)
+    r = sys.br_r * rng.uniform(0.8, 1.2, sys.n_branch)
+    xr = sys.br_x * rng.uniform(0.8, 1.2, sys.n_branch)
+    b = sys.br_b * rng.uniform(0.5, 1.5, sys.n_branch)
+    tap = sys.br_tap * rng.uniform(0.98, 1.02, sys.n_branch)
+    p0, q0 = oracle.net_injections(sys)
+    p = p0 + rng.normal(0, 0.1, sys.n_bus)
+    q = q0 + rng.normal(0, 0.1, sys.n_bus)
+    xn = state(sys, 2)
+    ctx = P.Context(sys)
+    c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    F, v = ctx.eval(c(xn), ctx.empty_f(), ctx.empty_vals(), br_r=c(r), br_x=c(xr), br_b=c(b), br_tap=c(tap),
+                    p_inj=c(p), q_inj=c(q))
+    s2 = sys.copy()
+    s2.br_r, s2.br_x, s2.br_b, s2.br_tap = r, xr, b, tap
+    assert_tol(F.cpu().numpy(), oracle.residual(s2, xn, REDUCED, p_inj=p, q_inj=q), "F overrides")
+    assert_tol(v.cpu().numpy(), oracle.jacobian(s2, xn, REDUCED)[2], "J overrides")
+    # without overrides the built values come back
+    F0 = ctx.residual(c(xn)).cpu().numpy()
+    assert_tol(F0, oracle.residual(sys, xn), "F built")
+
+
+def test_full_70k_against_oracle(P):
+    """Config 2: the 70,000-bus grid, every F row and J value, 3 of the 10 states."""
+    sys = gridgen.grid_70k()
+    ctx = P.Context(sys)
+    rp, ci = ctx.pattern()
+    rpo, cio, _ = oracle.jacobian(sys, gridgen.flat_state(sys))
+    assert np.array_equal(rp, rpo) and np.array_equal(ci, cio)
+    for k in (0, 1, 10):
+        xn = state(sys, k)
+        F, v = ctx.residual_jacobian(torch.from_numpy(xn).cuda())
+        assert_tol(F.cpu().numpy(), oracle.residual(sys, xn), f"70k F {k}")
+        assert_tol(v.cpu().numpy(), oracle.jacobian(sys, xn)[2], f"70k J {k}")
+    ctx.check_device()
