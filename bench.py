@@ -265,6 +265,7 @@ def main():
     sampler.start()
     time.sleep(0.3)
     wall0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("bench_timed")
     with torch.cuda.stream(stream):
         flush.fill_(-1.0)                          # lead work so the host runs ahead of the GPU
         for k in range(K):
@@ -273,6 +274,7 @@ def main():
             step(k)
             ev1[k].record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     wall = time.perf_counter() - wall0
     if distributed:
         dist.barrier()
