@@ -402,7 +402,7 @@ int launch_vjp(Ctx &c, const double *x, const pf_overrides *ov, const double *v,
     if (!c.any_outage) vv.inst_outage = nullptr;   // unmasked fast path unless outages exist
     if (r || xr || b || tap) vv.inc_ac = c.ov_ac;
     const size_t smem = (size_t)a.cap * sizeof(double) * 6;
-    if (smem > 48 * 1024)
+    if (smem > 46 * 1024)
       PF_CUDA_TRY(cudaFuncSetAttribute(k_vjp_state, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int64_t grid = c.v.n_units;
     if (c.tuning.ctas_per_sm > 0) grid = std::min<int64_t>(grid, (int64_t)c.tuning.ctas_per_sm * c.num_sms);

@@ -263,7 +263,8 @@ int launch_fused(Ctx &c, const EvalArgs &a, cudaStream_t s) {
   const int cap = a.cap;
   const size_t smem = (size_t)cap * sizeof(double) * ((WJ ? 6 : 2) + (MASKED ? 2 : 0));
   auto kern = k_fused<WF, WJ, MASKED>;
-  if (smem > 48 * 1024)
+  // the kernel also holds a few bytes of static shared memory: opt in above 46 KB
+  if (smem > 46 * 1024)
     PF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int64_t grid = c.v.n_units;
   if (c.tuning.ctas_per_sm > 0) grid = std::min<int64_t>(grid, (int64_t)c.tuning.ctas_per_sm * c.num_sms);
