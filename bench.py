@@ -131,7 +131,7 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------
-# algorithmic work per evaluation ("Roofline")
+# algorithmic work per launch / evaluation
 # --------------------------------------------------------------------------
 
 def algorithmic_bytes(d, n_pv, n_load, n_shunt):
@@ -144,13 +144,21 @@ def algorithmic_bytes(d, n_pv, n_load, n_shunt):
     return read + write
 
 
-def algorithmic_fp64_flops(d):
-    """FP64 flops of the rotated polar form: 16 operations per branch end
-    (4 multiplies + 6 FMAs + 4 multiplies + 2 adds; an FMA counts 2 flops:
-    22 flops), 11 per bus for F and the diagonal (9 of them FMA: 20 flops)
-    and one sin/cos pair per bus, counted as 2 x 8 FLOPs (a degree-7
-    polynomial each)."""
-    return d.n_inc * 22 + d.n_bus * (20 + 16)
+def fused_fp64_flops(d, n_groups):
+    """Algorithmic FP64 flops of one k_fused launch (F and J, no mask), an
+    FMA counting 2: per branch end 20 (the rotated terms u, w, xh, yh: 4
+    multiplies + 4 FMAs; the six products a, b, dP/dt_k, dQ/dt_k, dP/dV_k,
+    dQ/dV_k; 2 adds into the bus sums), per extra end of a parallel group 4
+    adds, per bus 16 (F_P, F_Q: 2 FMAs each; the four diagonal entries)."""
+    return d.n_inc * 20 + 4 * (d.n_inc - n_groups) + d.n_bus * 16
+
+
+def source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2011_11880_gb300", "csrc", "pf_eval.cu"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 # --------------------------------------------------------------------------
@@ -309,6 +317,21 @@ def main():
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_value = world * E / float(te.item())
 
+    # ---- the dominant kernel alone: phasor stage, then k_fused between events ----
+    KF = min(K, 2000)
+    evf0 = [torch.cuda.Event(enable_timing=True) for _ in range(KF)]
+    evf1 = [torch.cuda.Event(enable_timing=True) for _ in range(KF)]
+    with torch.cuda.stream(stream):
+        flush.fill_(-2.0)
+        for k in range(KF):
+            flush.fill_(float(k))
+            ctx.eval_stage(1, X[k % N_STATES], F, V, stream=stream)
+            evf0[k].record(stream)
+            ctx.eval_stage(2, X[k % N_STATES], F, V, stream=stream)
+            evf1[k].record(stream)
+    torch.cuda.synchronize()
+    kf_ms = float(np.mean([a.elapsed_time(b) for a, b in zip(evf0, evf1)]))
+
     # ---- correctness spot check of the timed outputs (last state) against a fresh call ----
     Fc, Vc = ctx.residual_jacobian(X[(K - 1) % N_STATES])
     graphs[(K - 1) % N_STATES].replay()
@@ -318,21 +341,25 @@ def main():
 
     peaks, peak_kind = load_peaks()
     n_pv, n_load, n_shunt = sys_.n_pv, sys_.load_bus.shape[0], sys_.sh_bus.shape[0]
+    ip, _, oth = ctx.incidence()
+    own = np.repeat(np.arange(d.n_bus), np.diff(ip))
+    n_groups = int(np.count_nonzero(np.r_[True, (oth[1:] != oth[:-1]) | (own[1:] != own[:-1])]))
+    flops_kf = fused_fp64_flops(d, n_groups)
     bytes_alg = algorithmic_bytes(d, n_pv, n_load, n_shunt)
-    flops_alg = algorithmic_fp64_flops(d)
-    fp64_peak_tflops = 152 * 2 * 2 * (peaks.get("sm_max_mhz", 2070.0) * 1e6) / 1e12   # 2 DFMA/clk/SM
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak_tflops = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12          # 2 DFMA/clk/SM, FMA = 2 flops
+    achieved_tf = flops_kf / (kf_ms * 1e-3) / 1e12
     eval_s = t_max / K
-    achieved_tf = flops_alg / eval_s / 1e12
-    achieved_gbs = bytes_alg / eval_s / 1e9
-    frac_alu = achieved_tf / fp64_peak_tflops
-    frac_hbm = achieved_gbs / peaks["hbm_gbs"]
-    traffic = load_traffic()
-    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                "frac": frac_alu, "traffic": traffic,
-                "kernel": "k_phasor + k_fused (one evaluation)",
-                "peak_kind": "FP64 derived: 152 SMs x 2 DFMA/clk x 2 flops x max SM clock",
-                "hbm": {"achieved_gbs": achieved_gbs, "peak_gbs": peaks["hbm_gbs"], "frac": frac_hbm,
-                        "peak_kind": peak_kind, "algorithmic_bytes": bytes_alg}}
+    tr = load_traffic()
+    roofline = {"bound": "alu", "kernel": "k_fused", "achieved": achieved_tf, "peak": fp64_peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak_tflops,
+                "traffic": tr.get("dram_bytes_per_launch") if tr else None,
+                "kernel_ms": kf_ms, "algorithmic_flops": flops_kf,
+                "peak_kind": "FP64 derived from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flops x "
+                             f"{sm_mhz:.0f} MHz",
+                "evaluation_hbm_view": {"algorithmic_bytes": bytes_alg, "achieved_gbs": bytes_alg / eval_s / 1e9,
+                                        "peak_gbs": peaks["hbm_gbs"], "peak_kind": peak_kind,
+                                        "frac": bytes_alg / eval_s / 1e9 / peaks["hbm_gbs"]}}
 
     cpu = None
     if rank == 0:
@@ -363,13 +390,15 @@ def main():
 
 
 def load_traffic():
-    """DRAM bytes per evaluation from the committed ncu summary, if present."""
-    path = os.path.join(ROOT, "profiles", "traffic_70k.json")
+    """DRAM bytes per k_fused launch from the committed ncu summary, used only
+    while the kernel source is the one that was profiled."""
+    path = os.path.join(ROOT, "profiles", "k_fused_traffic_70k.json")
     try:
         with open(path) as fh:
-            return json.load(fh).get("dram_bytes_per_eval")
+            rec = json.load(fh)
     except Exception:
         return None
+    return rec if rec.get("pf_eval_cu_sha256_16") == source_hash() else None
 
 
 if __name__ == "__main__":

@@ -107,7 +107,7 @@ typedef struct pf_system {
   const double *sh_b;
 } pf_system;
 
-/* One evaluation instance of a batch (spec batched form). */
+/* One evaluation instance of a batch (many contingency / scenario instances in one launch). */
 typedef struct pf_instance {
   int32_t grid;                  /* index into the grids array of pf_build_batch */
   int32_t outage;                /* branch of that grid taken out for this instance, -1: none */
@@ -222,6 +222,17 @@ PF_API int pf_residual_jacobian(pf_ctx *ctx, const double *x, double *F, double 
 PF_API int pf_eval(pf_ctx *ctx, const double *x, const pf_overrides *ov, double *F, double *vals,
             void *stream);
 
+/* The two kernels of an evaluation, one at a time: PF_STAGE_PHASOR computes
+ * (cos theta, sin theta) of every bus into the context's scratch;
+ * PF_STAGE_FUSED runs the fused F / J kernel, reading that scratch (a
+ * PF_STAGE_PHASOR call at the same x must precede it on the stream).
+ * pf_eval runs both.  For timing each kernel and for overlapping the stages
+ * with other work.  ov may be NULL; F or vals may be NULL. */
+#define PF_STAGE_PHASOR 1
+#define PF_STAGE_FUSED 2
+PF_API int pf_eval_stage(pf_ctx *ctx, int32_t stage, const double *x, const pf_overrides *ov, double *F,
+                         double *vals, void *stream);
+
 /* End-to-end form for callers holding host memory: copies x (host) in,
  * evaluates, copies F and vals (host; either may be NULL) out and
  * synchronises `stream`.  Page-locked host buffers give the full copy rate.
@@ -229,7 +240,7 @@ PF_API int pf_eval(pf_ctx *ctx, const double *x, const pf_overrides *ov, double 
 PF_API int pf_residual_jacobian_host(pf_ctx *ctx, const double *x_host, double *F_host,
                               double *vals_host, void *stream);
 
-/* Adjoint (spec differentiation form): for n_cot cotangents v
+/* Adjoint (differentiation of F): for n_cot cotangents v
  * ([n_cot][n_f], device), the vector-Jacobian products v^T dF/d(x, P_inj,
  * Q_inj, r, x, b_c, tau).  Trigonometric terms are recomputed, nothing from a
  * forward call is stored.  ov may be NULL. */

@@ -16,6 +16,8 @@ P = ctypes.POINTER
 PF_OK = 0
 PF_REDUCED = 0
 PF_EXTENDED = 1
+PF_STAGE_PHASOR = 1
+PF_STAGE_FUSED = 2
 ERRORS = {1: "PF_ERR_INVALID", 2: "PF_ERR_OOM", 3: "PF_ERR_CUDA", 4: "PF_ERR_TIMEOUT",
           5: "PF_ERR_UNSUPPORTED", 6: "PF_ERR_DEVICE"}
 
@@ -76,6 +78,7 @@ SIGNATURES = {
     "pf_jacobian": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "pf_residual_jacobian": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pf_eval": (c_int32, [c_void_p, c_void_p, P(PfOverrides), c_void_p, c_void_p, c_void_p]),
+    "pf_eval_stage": (c_int32, [c_void_p, c_int32, c_void_p, P(PfOverrides), c_void_p, c_void_p, c_void_p]),
     "pf_residual_jacobian_host": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pf_vjp": (c_int32, [c_void_p, c_void_p, P(PfOverrides), c_void_p, c_int32, P(PfGrads), c_void_p]),
     "pf_get_tuning": (c_int32, [c_void_p, P(PfTuning)]),

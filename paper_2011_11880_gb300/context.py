@@ -202,6 +202,14 @@ class Context:
                                 _stream(stream)), "pf_eval")
         return F, vals
 
+    def eval_stage(self, stage: int, x, F=None, vals=None, stream=None):
+        """One kernel of an evaluation: stage 1 (phasors) or 2 (fused F/J; needs a preceding stage 1)."""
+        d = self.dims
+        check(self._lib.pf_eval_stage(self._h, int(stage), _ptr(x, numel=d.n_x, name="x"), None,
+                                      _ptr(F, numel=d.n_f, name="F"), _ptr(vals, numel=d.nnz, name="vals"),
+                                      _stream(stream)), "pf_eval_stage")
+        return F, vals
+
     def residual(self, x, F=None, stream=None):
         F = self.empty_f(x.device) if F is None else F
         check(self._lib.pf_residual(self._h, _ptr(x, numel=self.dims.n_x, name="x"),

@@ -172,6 +172,14 @@ int pf_eval(pf_ctx *ctx, const double *x, const pf_overrides *ov, double *F, dou
   return pf::launch_eval(ctx->c, x, ov, F, vals, as_stream(stream));
 }
 
+int pf_eval_stage(pf_ctx *ctx, int32_t stage, const double *x, const pf_overrides *ov, double *F, double *vals,
+                  void *stream) {
+  if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
+  if (stage != PF_STAGE_PHASOR && stage != PF_STAGE_FUSED)
+    return fail(PF_ERR_INVALID, "stage must be PF_STAGE_PHASOR or PF_STAGE_FUSED");
+  return pf::launch_eval_stages(ctx->c, stage, x, ov, F, vals, as_stream(stream));
+}
+
 int pf_residual(pf_ctx *ctx, const double *x, double *F, void *stream) {
   if (!F) return fail(PF_ERR_INVALID, "F is NULL");
   return pf_eval(ctx, x, nullptr, F, nullptr, stream);

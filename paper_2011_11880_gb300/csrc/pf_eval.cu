@@ -286,7 +286,13 @@ int launch_fused(Ctx &c, const EvalArgs &a, cudaStream_t s) {
 }  // namespace
 
 int launch_eval(Ctx &c, const double *x, const pf_overrides *ov, double *F, double *vals, cudaStream_t s) {
+  return launch_eval_stages(c, 3, x, ov, F, vals, s);
+}
+
+int launch_eval_stages(Ctx &c, int stages, const double *x, const pf_overrides *ov, double *F, double *vals,
+                       cudaStream_t s) {
   if (!x) return fail(PF_ERR_INVALID, "x is NULL");
+  if (stages < 1 || stages > 3) return fail(PF_ERR_INVALID, "stage must be PF_STAGE_PHASOR or PF_STAGE_FUSED");
   if (!F && !vals) return PF_OK;
   EvalArgs a{};
   a.x = x;
@@ -302,8 +308,9 @@ int launch_eval(Ctx &c, const double *x, const pf_overrides *ov, double *F, doub
     a.q_inj = ov->q_inj;
     a.status = ov->status;
     if (ov->br_r || ov->br_x || ov->br_b || ov->br_tap) {
-      PF_TRY(compute_coefficients(c, ov->br_r, ov->br_x, ov->br_b, ov->br_tap, c.ov_gb, c.ov_ac, c.ov_ahat,
-                                  c.ov_chat, s));
+      if (stages & 2)
+        PF_TRY(compute_coefficients(c, ov->br_r, ov->br_x, ov->br_b, ov->br_tap, c.ov_gb, c.ov_ac, c.ov_ahat,
+                                    c.ov_chat, s));
       a.gb = c.ov_gb;
       a.ac = c.ov_ac;
       a.ahat = c.ov_ahat;
@@ -311,13 +318,14 @@ int launch_eval(Ctx &c, const double *x, const pf_overrides *ov, double *F, doub
     }
   }
   const bool masked = c.any_outage || a.status != nullptr;
-  {
+  if (stages & 1) {
     const int tb = 256;
     int64_t blocks = (c.v.n_bus_inst + tb - 1) / tb;
     blocks = std::min<int64_t>(blocks, (int64_t)c.num_sms * 16);
     k_phasor<<<(unsigned)std::max<int64_t>(blocks, 1), tb, 0, s>>>(c.v, x);
     PF_CUDA_TRY(cudaGetLastError());
   }
+  if (!(stages & 2)) return PF_OK;
   const bool wf = F != nullptr, wj = vals != nullptr;
   if (wf && wj) return masked ? launch_fused<true, true, true>(c, a, s) : launch_fused<true, true, false>(c, a, s);
   if (wf) return masked ? launch_fused<true, false, true>(c, a, s) : launch_fused<true, false, false>(c, a, s);

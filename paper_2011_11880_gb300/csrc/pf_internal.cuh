@@ -174,6 +174,9 @@ int compute_coefficients(Ctx &c, const double *r, const double *x, const double 
 // ---- evaluation (pf_eval.cu) ----
 int launch_eval(Ctx &c, const double *x, const pf_overrides *ov, double *F, double *vals,
                 cudaStream_t s);
+// stage mask: 1 = phasors, 2 = fused kernel, 3 = both
+int launch_eval_stages(Ctx &c, int stages, const double *x, const pf_overrides *ov, double *F, double *vals,
+                       cudaStream_t s);
 int launch_vjp(Ctx &c, const double *x, const pf_overrides *ov, const double *v, int n_cot,
                const pf_grads *g, cudaStream_t s);
 

@@ -4,7 +4,7 @@ import numpy as np
 import gridgen
 import oracle
 
-RTOL = 1e-12   # spec tolerance: |gpu - oracle| <= 1e-10 + 1e-12 |oracle|
+RTOL = 1e-12   # parity tolerance: |gpu - oracle| <= 1e-10 + 1e-12 |oracle|
 ATOL = 1e-10
 
 
