@@ -233,6 +233,25 @@ PF_API int pf_eval(pf_ctx *ctx, const double *x, const pf_overrides *ov, double 
 PF_API int pf_eval_stage(pf_ctx *ctx, int32_t stage, const double *x, const pf_overrides *ov, double *F,
                          double *vals, void *stream);
 
+/* Allocation-free variant of pf_residual_jacobian (the paper has no
+ * counterpart; it serves callers that cannot allocate device memory at call
+ * time -- code that must not synchronise the device, hosts with a fixed
+ * device-memory budget, plug-ins that may use only memory handed to them).
+ * Same inputs, outputs and results as pf_residual_jacobian; F or vals may be
+ * NULL.  It calls no cudaMalloc / cudaFree: the per-bus scratch of the
+ * evaluation is a static device array of 2^18 instance-buses (4 MiB), held by
+ * every GPU that loads the library until the process exits.
+ *   - Contexts with more than 2^18 buses summed over their instances are
+ *     rejected with PF_ERR_UNSUPPORTED (use pf_residual_jacobian).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call, from any context, shares the one array: calls whose GPU
+ *     work overlaps (other streams, other threads) race and give wrong
+ *     results.  The array keeps the last call's contents; nothing in it needs
+ *     to start at zero. */
+PF_API int pf_residual_jacobian_static(pf_ctx *ctx, const double *x, double *F, double *vals, void *stream);
+
 /* End-to-end form for callers holding host memory: copies x (host) in,
  * evaluates, copies F and vals (host; either may be NULL) out and
  * synchronises `stream`.  Page-locked host buffers give the full copy rate.

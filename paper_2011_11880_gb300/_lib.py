@@ -79,6 +79,7 @@ SIGNATURES = {
     "pf_residual_jacobian": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pf_eval": (c_int32, [c_void_p, c_void_p, P(PfOverrides), c_void_p, c_void_p, c_void_p]),
     "pf_eval_stage": (c_int32, [c_void_p, c_int32, c_void_p, P(PfOverrides), c_void_p, c_void_p, c_void_p]),
+    "pf_residual_jacobian_static": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pf_residual_jacobian_host": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pf_vjp": (c_int32, [c_void_p, c_void_p, P(PfOverrides), c_void_p, c_int32, P(PfGrads), c_void_p]),
     "pf_get_tuning": (c_int32, [c_void_p, P(PfTuning)]),

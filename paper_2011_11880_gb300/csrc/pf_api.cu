@@ -26,6 +26,8 @@ int fail(int code, const std::string &msg) {
 
 using pf::fail;
 
+pf::Ctx *pf::ctx_of(pf_ctx *h) { return h ? &h->c : nullptr; }
+
 namespace {
 
 cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }

@@ -333,3 +333,71 @@ int launch_eval_stages(Ctx &c, int stages, const double *x, const pf_overrides *
 }
 
 }  // namespace pf
+
+// ---------------------------------------------------------------------------
+// Evaluation with caller-provided phasor scratch (used by the allocation-free
+// entry point, whose scratch is a static device array).
+// ---------------------------------------------------------------------------
+
+namespace pf {
+
+namespace {
+
+template <bool WF, bool WJ, bool MASKED>
+int launch_fused_view(const View &v, int num_sms, const pf_tuning &t, const EvalArgs &a, cudaStream_t s) {
+  const size_t smem = (size_t)a.cap * sizeof(double) * ((WJ ? 6 : 2) + (MASKED ? 2 : 0));
+  auto kern = k_fused<WF, WJ, MASKED>;
+  if (smem > 46 * 1024)
+    PF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int64_t grid = v.n_units;
+  if (t.ctas_per_sm > 0) grid = std::min<int64_t>(grid, (int64_t)t.ctas_per_sm * num_sms);
+  if (grid < 1) grid = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)a.cap);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  PF_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, v, a));
+  return PF_OK;
+}
+
+}  // namespace
+
+int launch_eval_scratch(Ctx &c, const double *x, double *F, double *vals, double2 *scratch, cudaStream_t s) {
+  if (!x) return fail(PF_ERR_INVALID, "x is NULL");
+  if (!scratch) return fail(PF_ERR_INVALID, "scratch is NULL");
+  if (!F && !vals) return PF_OK;
+  View v = c.v;
+  v.phasor = scratch;
+  EvalArgs a{};
+  a.x = x;
+  a.F = F;
+  a.vals = vals;
+  a.gb = c.v.inc_gb;
+  a.ac = c.v.inc_ac;
+  a.ahat = c.v.a_hat;
+  a.chat = c.v.c_hat;
+  a.cap = c.tuning.tile_inc;
+  const int tb = 256;
+  int64_t blocks = (v.n_bus_inst + tb - 1) / tb;
+  blocks = std::min<int64_t>(blocks, (int64_t)c.num_sms * 16);
+  k_phasor<<<(unsigned)std::max<int64_t>(blocks, 1), tb, 0, s>>>(v, x);
+  PF_CUDA_TRY(cudaGetLastError());
+  const bool masked = c.any_outage;
+  const bool wf = F != nullptr, wj = vals != nullptr;
+  if (wf && wj)
+    return masked ? launch_fused_view<true, true, true>(v, c.num_sms, c.tuning, a, s)
+                  : launch_fused_view<true, true, false>(v, c.num_sms, c.tuning, a, s);
+  if (wf)
+    return masked ? launch_fused_view<true, false, true>(v, c.num_sms, c.tuning, a, s)
+                  : launch_fused_view<true, false, false>(v, c.num_sms, c.tuning, a, s);
+  return masked ? launch_fused_view<false, true, true>(v, c.num_sms, c.tuning, a, s)
+                : launch_fused_view<false, true, false>(v, c.num_sms, c.tuning, a, s);
+}
+
+}  // namespace pf

@@ -179,6 +179,10 @@ int launch_eval_stages(Ctx &c, int stages, const double *x, const pf_overrides *
                        cudaStream_t s);
 int launch_vjp(Ctx &c, const double *x, const pf_overrides *ov, const double *v, int n_cot,
                const pf_grads *g, cudaStream_t s);
+// F / J evaluation whose per-bus phasor scratch is `scratch` instead of the context's.
+int launch_eval_scratch(Ctx &c, const double *x, double *F, double *vals, double2 *scratch, cudaStream_t s);
+// The context behind a C-ABI handle.
+Ctx *ctx_of(pf_ctx *h);
 
 // Largest i in [0, n) with off[i] <= key (off ascending, off[0] = 0).
 __device__ __forceinline__ int find_segment(const int64_t *__restrict__ off, int n, int64_t key) {
