@@ -154,8 +154,8 @@ typedef struct pf_grads {
 } pf_grads;
 
 typedef struct pf_tuning {
-  int32_t tile_inc;              /* branch ends staged per CTA tile: 64..1024, multiple of 32 */
-  int32_t ctas_per_sm;           /* persistent CTAs per SM; 0 = one CTA per tile */
+  int32_t tile_inc;              /* branch ends per warp round: 32, 64, 96 or 128 (1-4 per lane) */
+  int32_t ctas_per_sm;           /* persistent CTAs per SM; 0 = enough CTAs for every round */
 } pf_tuning;
 
 /* ---- build (once) -------------------------------------------------------- */
@@ -277,6 +277,13 @@ PF_API int pf_set_tuning(pf_ctx *ctx, const pf_tuning *t, void *stream);
  * scratch for the timing runs. */
 PF_API int pf_autotune(pf_ctx *ctx, const double *x, double *F, double *vals, void *stream,
                 pf_tuning *chosen);
+
+/* The per-bus trigonometric routine of the evaluation (table-driven reduction
+ * by multiples of pi/128 and short Taylor polynomials), exposed so it can be
+ * checked against a reference sin / cos: cos_out[i], sin_out[i] of theta[i],
+ * n device entries each, asynchronous on `stream`. */
+PF_API int pf_sincos(pf_ctx *ctx, const double *theta, int64_t n, double *cos_out, double *sin_out,
+                     void *stream);
 
 /* ---- errors --------------------------------------------------------------------- */
 

@@ -278,5 +278,14 @@ class Context:
                                     ctypes.byref(t)), "pf_autotune")
         return {"tile_inc": t.tile_inc, "ctas_per_sm": t.ctas_per_sm}
 
+    def sincos(self, theta, stream=None):
+        """(cos, sin) of a float64 CUDA tensor by the evaluation's phasor routine."""
+        n = theta.numel()
+        c = torch.empty_like(theta)
+        s = torch.empty_like(theta)
+        check(self._lib.pf_sincos(self._h, _ptr(theta, numel=n, name="theta"), n, _ptr(c), _ptr(s),
+                                  _stream(stream)), "pf_sincos")
+        return c, s
+
     def check_device(self, stream=None):
         check(self._lib.pf_check_device(self._h, _stream(stream)), "pf_check_device")

@@ -31,7 +31,8 @@ struct VjpArgs {
   int n_cot;
   int64_t n_f;
   const double2 *gb;
-  const double *ahat, *chat;
+  const double2 *ac;
+  const double2 *hat;
   const uint8_t *status;
   double *gx;             // [n_cot][n_x]
   int64_t n_x;
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(1024) k_vjp_state(View v, VjpArgs a) {
         rpk = v.row_p[k];
         rqk = v.row_q[k];
         if (masked) {
-          const double2 ac = v.inc_ac[e];
+          const double2 ac = a.ac[e];
           s_ma[j] = in ? ac.x : 0.0;
           s_mc[j] = in ? ac.y : 0.0;
         }
@@ -153,8 +154,8 @@ __global__ void __launch_bounds__(1024) k_vjp_state(View v, VjpArgs a) {
           const int32_t o = ob;
           const int64_t lb = o - gb0;
           const double vo = Vi[o];
-          const double ah = masked ? ma + v.g_sh[o] : a.ahat[o];
-          const double ch = masked ? mc + v.b_sh[o] : a.chat[o];
+          const double ah = masked ? ma + v.bus_sh[o].x : a.hat[o].x;
+          const double ch = masked ? mc + v.bus_sh[o].y : a.hat[o].y;
           const int32_t rp = v.row_p[o], rq = v.row_q[o];
           const double vp = rp >= 0 ? vc[rp] : 0.0;
           const double vq = rq >= 0 ? vc[rq] : 0.0;
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(1024) k_vjp_state(View v, VjpArgs a) {
             s_g[j] = -vpk * (vv * my) + vqk * (vv * mx);
             s_h[j] = -vpk * (vk * mx) - vqk * (vk * my);
             if (masked) {
-              const double2 ac = v.inc_ac[e];
+              const double2 ac = a.ac[e];
               s_ma[j] = in ? ac.x : 0.0;
               s_mc[j] = in ? ac.y : 0.0;
             }
@@ -248,8 +249,8 @@ __global__ void __launch_bounds__(1024) k_vjp_state(View v, VjpArgs a) {
           const int32_t o = ob;
           const int64_t lb = o - gb0;
           const double vo = Vi[o];
-          const double ah = masked ? ma + v.g_sh[o] : a.ahat[o];
-          const double ch = masked ? mc + v.b_sh[o] : a.chat[o];
+          const double ah = masked ? ma + v.bus_sh[o].x : a.hat[o].x;
+          const double ch = masked ? mc + v.bus_sh[o].y : a.hat[o].y;
           const int32_t rp = v.row_p[o], rq = v.row_q[o];
           const double vp = rp >= 0 ? vc[rp] : 0.0;
           const double vq = rq >= 0 ? vc[rq] : 0.0;
@@ -383,24 +384,22 @@ int launch_vjp(Ctx &c, const double *x, const pf_overrides *ov, const double *v,
   k_phasor_adj<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((c.v.n_bus_inst + tb - 1) / tb, cap_blocks)),
                  tb, 0, s>>>(c.v, x);
   PF_CUDA_TRY(cudaGetLastError());
-  const double2 *gb = c.v.inc_gb;
-  const double *ahat = c.v.a_hat, *chat = c.v.c_hat;
+  const double2 *gb = c.v.inc_gb, *ac = c.v.inc_ac, *hat = c.v.bus_hat;
   const uint8_t *status = ov ? ov->status : nullptr;
   const double *r = nullptr, *xr = nullptr, *b = nullptr, *tap = nullptr;
   if (ov && (ov->br_r || ov->br_x || ov->br_b || ov->br_tap)) {
     r = ov->br_r; xr = ov->br_x; b = ov->br_b; tap = ov->br_tap;
-    PF_TRY(compute_coefficients(c, r, xr, b, tap, c.ov_gb, c.ov_ac, c.ov_ahat, c.ov_chat, s));
+    PF_TRY(compute_coefficients(c, r, xr, b, tap, c.ov_gb, c.ov_ac, c.ov_hat, s));
     gb = c.ov_gb;
-    ahat = c.ov_ahat;
-    chat = c.ov_chat;
+    ac = c.ov_ac;
+    hat = c.ov_hat;
   }
   if (g->x) {
     VjpArgs a{};
-    a.x = x; a.v = v; a.n_cot = n_cot; a.n_f = c.n_f; a.gb = gb; a.ahat = ahat; a.chat = chat;
+    a.x = x; a.v = v; a.n_cot = n_cot; a.n_f = c.n_f; a.gb = gb; a.ac = ac; a.hat = hat;
     a.status = status; a.gx = g->x; a.n_x = c.n_x; a.cap = c.tuning.tile_inc;
     View vv = c.v;
     if (!c.any_outage) vv.inst_outage = nullptr;   // unmasked fast path unless outages exist
-    if (r || xr || b || tap) vv.inc_ac = c.ov_ac;
     const size_t smem = (size_t)a.cap * sizeof(double) * 6;
     if (smem > 46 * 1024)
       PF_CUDA_TRY(cudaFuncSetAttribute(k_vjp_state, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

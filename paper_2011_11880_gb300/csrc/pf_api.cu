@@ -230,8 +230,7 @@ int pf_get_tuning(const pf_ctx *ctx, pf_tuning *t) {
 int pf_set_tuning(pf_ctx *ctx, const pf_tuning *t, void *stream) {
   if (!ctx || !t) return fail(PF_ERR_INVALID, "NULL argument");
   if (t->tile_inc < pf::kMinTileInc || t->tile_inc > pf::kMaxTileInc || t->tile_inc % 32 != 0)
-    return fail(PF_ERR_INVALID, "tile_inc must be a multiple of 32 in [64, 1024]");
-  if (t->tile_inc < ctx->c.max_group) return fail(PF_ERR_INVALID, "tile_inc below the largest parallel group");
+    return fail(PF_ERR_INVALID, "tile_inc must be 32, 64, 96 or 128");
   if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return fail(PF_ERR_INVALID, "ctas_per_sm must be in [0, 32]");
   cudaStream_t s = as_stream(stream);
   PF_CUDA_TRY(cudaStreamSynchronize(s));
@@ -243,8 +242,8 @@ int pf_set_tuning(pf_ctx *ctx, const pf_tuning *t, void *stream) {
 int pf_autotune(pf_ctx *ctx, const double *x, double *F, double *vals, void *stream, pf_tuning *chosen) {
   if (!ctx || !x) return fail(PF_ERR_INVALID, "NULL argument");
   cudaStream_t s = as_stream(stream);
-  const int tiles[] = {128, 256, 512};
-  const int ctas[] = {0, 4, 8};
+  const int tiles[] = {32, 64, 96, 128};
+  const int ctas[] = {0, 8, 16};
   pf_tuning best = ctx->c.tuning;
   float best_ms = 1e30f;
   cudaEvent_t e0, e1;
@@ -252,7 +251,6 @@ int pf_autotune(pf_ctx *ctx, const double *x, double *F, double *vals, void *str
   PF_CUDA_TRY(cudaEventCreate(&e1));
   int rc = PF_OK;
   for (int ti : tiles) {
-    if (ti < ctx->c.max_group) continue;
     for (int ca : ctas) {
       pf_tuning t{ti, ca};
       rc = pf_set_tuning(ctx, &t, stream);
@@ -280,6 +278,11 @@ int pf_autotune(pf_ctx *ctx, const double *x, double *F, double *vals, void *str
   PF_TRY(pf_set_tuning(ctx, &best, stream));
   if (chosen) *chosen = best;
   return PF_OK;
+}
+
+int pf_sincos(pf_ctx *ctx, const double *theta, int64_t n, double *cos_out, double *sin_out, void *stream) {
+  if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
+  return pf::launch_sincos(ctx->c, theta, n, cos_out, sin_out, as_stream(stream));
 }
 
 const char *pf_error_string(int32_t code) {

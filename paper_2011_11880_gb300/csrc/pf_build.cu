@@ -401,17 +401,41 @@ __global__ void k_coeff(View v, const double *r_ov, const double *x_ov, const do
   }
 }
 
-__global__ void k_hat(View v, const double2 *ac, double *ahat, double *chat) {
+// A^ = (sum of A_e over the bus's ends, in list order) + shunt g; same for C^.
+// The evaluation's masked path accumulates in the same order, so a mask of
+// all ones gives the same bits.
+__global__ void k_hat(View v, const double2 *ac, double2 *hat) {
   const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= v.n_bus) return;
   double sa = 0.0, sc = 0.0;
   for (int32_t e = v.inc_ptr[o]; e < v.inc_ptr[o + 1]; ++e) {
     const double2 t = ac[e];
-    sa += t.x;
-    sc += t.y;
+    sa = __dadd_rn(sa, t.x);
+    sc = __dadd_rn(sc, t.y);
   }
-  ahat[o] = sa + v.g_sh[o];
-  chat[o] = sc + v.b_sh[o];
+  const double2 sh = v.bus_sh[o];
+  hat[o] = make_double2(__dadd_rn(sa, sh.x), __dadd_rn(sc, sh.y));
+}
+
+__global__ void k_pack_bus(View v, const int32_t *base_p, const int32_t *base_q, const int2 *diag,
+                           const int32_t *len_tv, int4 *m1, int4 *m2) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= v.n_bus) return;
+  m1[o] = make_int4(v.row_p[o], v.row_q[o], base_p[o], base_q[o]);
+  const int2 d = diag[o];
+  m2[o] = make_int4(d.x, d.y, len_tv[o], v.gen[o]);
+}
+
+__global__ void k_pack_inc(View v, const int2 *rt, int4 *meta) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= v.n_inc) return;
+  const int2 r = rt[i];
+  meta[i] = make_int4(v.inc_own[i], v.inc_other[i], r.x, r.y);
+}
+
+__global__ void k_pack2(const double *a, const double *b, int64_t n, double2 *out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_double2(a[i], b[i]);
 }
 
 // per-nonzero contribution list: pass 0 counts, pass 1 writes
@@ -484,8 +508,8 @@ __global__ void k_cptr(const int64_t *S, const int64_t *grid_nnz_off, const int6
   if (q + 1 == grid_cptr_off[g + 1]) src_len[g] = cptr[q];
 }
 
-// greedy packing of consecutive buses into tiles of at most `cap` branch ends
-// and `cap` buses; a bus with more ends than `cap` forms a tile alone.
+// greedy packing of consecutive buses into rounds of at most `cap` branch ends
+// and kRoundBuses buses; a bus with more ends than `cap` forms a round alone.
 __global__ void k_tiles(View v, int cap, const int64_t *tile_off, int32_t *count, int32_t *bus0, int32_t *bus1) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= v.n_grids) return;
@@ -496,7 +520,7 @@ __global__ void k_tiles(View v, int cap, const int64_t *tile_off, int32_t *count
   int32_t inc = 0, nb = 0;
   for (int64_t b = b0; b < b1; ++b) {
     const int32_t d = v.inc_ptr[b + 1] - v.inc_ptr[b];
-    if (nb > 0 && (inc + d > cap || nb + 1 > cap)) {
+    if (nb > 0 && (inc + d > cap || nb + 1 > kRoundBuses)) {
       if (bus0) { bus0[t] = (int32_t)start; bus1[t] = (int32_t)b; ++t; }
       ++n;
       start = b;
@@ -558,12 +582,12 @@ int bus_sums(Ctx &c, TempList &tmp, const int32_t *d_item_bus, int64_t n_items, 
 // --------------------------------------------------------------------------
 
 int compute_coefficients(Ctx &c, const double *r, const double *x, const double *b, const double *tap,
-                         double2 *gb, double2 *ac, double *ahat, double *chat, cudaStream_t s) {
+                         double2 *gb, double2 *ac, double2 *hat, cudaStream_t s) {
   if (c.v.n_inc > 0) {
     k_coeff<<<nblk(c.v.n_inc), TB, 0, s>>>(c.v, r, x, b, tap, gb, ac);
     PF_CUDA_TRY(cudaGetLastError());
   }
-  k_hat<<<nblk(c.v.n_bus), TB, 0, s>>>(c.v, ac, ahat, chat);
+  k_hat<<<nblk(c.v.n_bus), TB, 0, s>>>(c.v, ac, hat);
   PF_CUDA_TRY(cudaGetLastError());
   return PF_OK;
 }
@@ -789,10 +813,10 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
 
     // ---- injections and shunt totals per bus (sums in item order) ----
     double *g_sh, *b_sh, *p_inj, *q_inj, *pl, *ql, *pg;
-    PF_TRY(dev_alloc(c, &g_sh, N));
-    PF_TRY(dev_alloc(c, &b_sh, N));
-    PF_TRY(dev_alloc(c, &p_inj, N));
-    PF_TRY(dev_alloc(c, &q_inj, N));
+    PF_TRY(tmp.alloc(&g_sh, N));
+    PF_TRY(tmp.alloc(&b_sh, N));
+    PF_TRY(tmp.alloc(&p_inj, N));
+    PF_TRY(tmp.alloc(&q_inj, N));
     PF_TRY(tmp.alloc(&pl, N));
     PF_TRY(tmp.alloc(&ql, N));
     PF_TRY(tmp.alloc(&pg, N));
@@ -803,7 +827,13 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
     PF_TRY(bus_sums(c, tmp, d_pv_bus, NPV, d_pv_p, nullptr, 1.0, 1.0, pg, nullptr, nullptr, nullptr, s));
     k_net_injection<<<nblk(N), TB, 0, s>>>(pg, pl, ql, N, p_inj, q_inj);
     PF_CUDA_TRY(cudaGetLastError());
-    v.g_sh = g_sh; v.b_sh = b_sh; v.p_inj = p_inj; v.q_inj = q_inj;
+    double2 *bus_sh, *bus_inj;
+    PF_TRY(dev_alloc(c, &bus_sh, N));
+    PF_TRY(dev_alloc(c, &bus_inj, N));
+    k_pack2<<<nblk(N), TB, 0, s>>>(g_sh, b_sh, N, bus_sh);
+    k_pack2<<<nblk(N), TB, 0, s>>>(p_inj, q_inj, N, bus_inj);
+    PF_CUDA_TRY(cudaGetLastError());
+    v.bus_sh = bus_sh; v.bus_inj = bus_inj;
 
     // ---- bus types and row maps ----
     int8_t *type;
@@ -874,8 +904,8 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
     if (rc) return rc;
     c.max_group = hstats[0];
     c.max_degree = hstats[1];
-    if (c.max_group > kMinTileInc)
-      return fail(PF_ERR_UNSUPPORTED, "more than " + std::to_string(kMinTileInc) +
+    if (c.max_group > kMaxGroup)
+      return fail(PF_ERR_UNSUPPORTED, "more than " + std::to_string(kMaxGroup) +
                                           " parallel branches between one pair of buses");
 
     // ---- row structure, rowptr, colind ----
@@ -946,18 +976,25 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
     c.colind = colind;
 
     // ---- coefficients ----
-    double2 *gb, *ac;
-    double *ahat, *chat;
+    double2 *gb, *ac, *hat;
     PF_TRY(dev_alloc(c, &gb, NI));
     PF_TRY(dev_alloc(c, &ac, NI));
-    PF_TRY(dev_alloc(c, &ahat, N));
-    PF_TRY(dev_alloc(c, &chat, N));
-    PF_TRY(compute_coefficients(c, nullptr, nullptr, nullptr, nullptr, gb, ac, ahat, chat, s));
-    v.inc_gb = gb; v.inc_ac = ac; v.a_hat = ahat; v.c_hat = chat;
+    PF_TRY(dev_alloc(c, &hat, N));
+    PF_TRY(compute_coefficients(c, nullptr, nullptr, nullptr, nullptr, gb, ac, hat, s));
+    v.inc_gb = gb; v.inc_ac = ac; v.bus_hat = hat;
     PF_TRY(dev_alloc(c, &c.ov_gb, NI));
     PF_TRY(dev_alloc(c, &c.ov_ac, NI));
-    PF_TRY(dev_alloc(c, &c.ov_ahat, N));
-    PF_TRY(dev_alloc(c, &c.ov_chat, N));
+    PF_TRY(dev_alloc(c, &c.ov_hat, N));
+
+    // ---- packed records for the evaluation kernels ----
+    int4 *bus_meta, *bus_meta2, *inc_meta;
+    PF_TRY(dev_alloc(c, &bus_meta, N));
+    PF_TRY(dev_alloc(c, &bus_meta2, N));
+    PF_TRY(dev_alloc(c, &inc_meta, NI));
+    k_pack_bus<<<nblk(N), TB, 0, s>>>(v, base_p, base_q, diag, len_tv, bus_meta, bus_meta2);
+    if (NI > 0) k_pack_inc<<<nblk(NI), TB, 0, s>>>(v, inc_rt, inc_meta);
+    PF_CUDA_TRY(cudaGetLastError());
+    v.bus_meta = bus_meta; v.bus_meta2 = bus_meta2; v.inc_meta = inc_meta;
 
     // ---- contribution list ----
     int32_t *count;
@@ -1049,9 +1086,20 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
   PF_CUDA_TRY(cudaGetDevice(&dev));
   PF_CUDA_TRY(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev));
 
-  int tile = 256;
-  while (tile < c.max_group && tile < kMaxTileInc) tile *= 2;
-  PF_TRY(build_tiles(c, tile, s));
+  // (cos, sin) of i pi / 128 for the table-driven phasor routine, evaluated in
+  // long double on the host and rounded once to double.
+  {
+    std::vector<double2> tab(kSinCosTable);
+    const long double pi = 3.14159265358979323846264338327950288419716939937510L;
+    for (int i = 0; i < kSinCosTable; ++i) {
+      const long double a = pi * (long double)i / 128.0L;
+      tab[i] = make_double2((double)cosl(a), (double)sinl(a));
+    }
+    double2 *d_tab;
+    PF_TRY(upload(c, &d_tab, tab, s));
+    v.sincos_tab = d_tab;
+  }
+  PF_TRY(build_tiles(c, 64, s));
   PF_CUDA_TRY(cudaStreamSynchronize(s));
   return PF_OK;
 }

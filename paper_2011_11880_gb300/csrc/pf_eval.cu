@@ -1,6 +1,5 @@
 // Evaluation kernels: tasks (1) and (2) of Newton power flow (Sec. I) for
-// every instance of a context, in one persistent pass over (instance, tile)
-// units.
+// every instance of a context.
 //
 // Arithmetic form.  For a branch end at bus o whose other end is bus k, with
 // per-end coefficients (G, B, A, C) built once from the branch model (see
@@ -11,19 +10,28 @@
 //     xh = cos(t_o) u + sin(t_o) w,   yh = sin(t_o) u - cos(t_o) w,
 //     u  = G cos(t_k) - B sin(t_k),   w  = G sin(t_k) + B cos(t_k),
 // which is the polar form with the angle difference expanded, so that the
-// only trigonometry is one sincos per bus (kernel k_phasor).  The partials
+// only trigonometry is one sin/cos pair per bus (k_phasor).  The partials
 // follow from the same expansion:
 //     dP_o/dt_k = -Y,  dQ_o/dt_k = X,  dP_o/dV_k = -V_o xh,  dQ_o/dV_k = -V_o yh,
 // and, summed over the ends of bus o with a = V_k xh, b = V_k yh,
 //     F_P = V_o (V_o A^ - sum a) - P_inj,    F_Q = -V_o (V_o C^ + sum b) - Q_inj,
 //     dF_P/dt_o = V_o sum b,   dF_Q/dt_o = -V_o sum a,
 //     dF_P/dV_o = 2 V_o A^ - sum a,   dF_Q/dV_o = -2 V_o C^ - sum b,
-// where A^ = sum A + shunt g and C^ = sum C + shunt b.  No division, 16
-// FP64 operations per branch end for F and J.
+// where A^ = sum A + shunt g and C^ = sum C + shunt b.  No division; 14
+// FP64 operations per branch end plus two adds into its bus's sums.
 //
-// Determinism: every sum runs in the order of the incidence list (one
-// thread per bus, one thread per parallel-branch group), so results are
-// bit-identical run to run and for every tile size.
+// Work decomposition.  One warp evaluates one round: up to 32 whole
+// consecutive buses with up to R = 32 * ITEMS branch ends (ITEMS ends per
+// lane); a bus with more than R ends is a round of its own, evaluated in
+// chunks of R.  Lanes compute the ends, owner lanes (one per bus) sum their
+// bus's ends and write the bus's F rows and diagonal J entries; the head end
+// of a group of parallel branches writes the group's off-diagonal entries
+// (its members are recomputed, which is rare and keeps groups independent of
+// chunking).
+//
+// Determinism: every operation is an explicitly rounded intrinsic and every
+// sum runs in incidence-list order, so results are bit-identical run to run,
+// across code paths and for every tuning.
 #include <algorithm>
 
 #include "pf_internal.cuh"
@@ -32,16 +40,54 @@ namespace pf {
 
 namespace {
 
-__global__ void k_phasor(View v, const double *__restrict__ x) {
+// ---------------------------------------------------------------------------
+// (cos t, sin t) by table-driven argument reduction (angle addition):
+//   t = k pi/128 + r, |r| <= pi/256, k = nearest integer to t 128/pi;
+//   r from a two-constant Cody-Waite split of pi/128 (the high part has 30
+//   significant bits, so k * STEP_HI is exact for |k| < 2^22);
+//   cos r, sin r by their Taylor series to degree 6 / 7 (truncation below
+//   1e-19 for |r| <= pi/256);
+//   cos t = C_k cos r - S_k sin r, sin t = S_k cos r + C_k sin r with the
+//   table (C_k, S_k) = (cos, sin)(k pi / 128) computed on the host in long
+//   double.  16 FP64 operations.  Arguments beyond |t| = 2^16 use sincos().
+// ---------------------------------------------------------------------------
+constexpr double kInvStep = 0x1.45f306dc9c883p+5;     // 128 / pi
+constexpr double kStepHi = 0x1.921fb54000000p-6;      // pi / 128, high 30 bits
+constexpr double kStepLo = 0x1.10b4611a62633p-36;     // pi / 128 - kStepHi
+constexpr double kRoundMagic = 6755399441055744.0;    // 1.5 * 2^52
+
+__device__ __forceinline__ double2 table_sincos(double t, const double2 *__restrict__ tab) {
+  if (!(fabs(t) < 65536.0)) {
+    double s, c;
+    sincos(t, &s, &c);
+    return make_double2(c, s);
+  }
+  const double km = __fma_rn(t, kInvStep, kRoundMagic);
+  const int ki = __double2loint(km);                  // nearest integer, two's complement
+  const double kd = __dsub_rn(km, kRoundMagic);
+  double r = __fma_rn(-kd, kStepHi, t);
+  r = __fma_rn(-kd, kStepLo, r);
+  const double z = __dmul_rn(r, r);
+  // sin r = r + r z (-1/6 + z (1/120 - z / 5040))
+  double ps = __fma_rn(z, -1.0 / 5040.0, 1.0 / 120.0);
+  ps = __fma_rn(z, ps, -1.0 / 6.0);
+  const double sr = __fma_rn(__dmul_rn(r, z), ps, r);
+  // cos r = 1 + z (-1/2 + z (1/24 - z / 720))
+  double pc = __fma_rn(z, -1.0 / 720.0, 1.0 / 24.0);
+  pc = __fma_rn(z, pc, -0.5);
+  const double cr = __fma_rn(z, pc, 1.0);
+  const double2 T = __ldg(tab + (ki & (kSinCosTable - 1)));
+  return make_double2(__fma_rn(T.x, cr, -__dmul_rn(T.y, sr)), __fma_rn(T.y, cr, __dmul_rn(T.x, sr)));
+}
+
+__global__ void __launch_bounds__(256) k_phasor(View v, const double *__restrict__ x) {
   // Let the fused kernel start launching; it waits for this grid's results.
   cudaTriggerProgrammaticLaunchCompletion();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < v.n_bus_inst; q += stride) {
     const int inst = v.n_inst == 1 ? 0 : find_segment(v.inst_bus_off, v.n_inst, q);
     const int64_t lb = q - v.inst_bus_off[inst];
-    double s, c;
-    sincos(__ldg(x + v.inst_x_off[inst] + lb), &s, &c);
-    v.phasor[q] = make_double2(c, s);
+    v.phasor[q] = table_sincos(__ldg(x + v.inst_x_off[inst] + lb), v.sincos_tab);
   }
 }
 
@@ -51,37 +97,50 @@ struct EvalArgs {
   double *vals;
   const double2 *gb;
   const double2 *ac;
-  const double *ahat;
-  const double *chat;
+  const double2 *hat;
   const double *p_inj;     // per-instance-bus override or nullptr
   const double *q_inj;
   const uint8_t *status;   // per-instance-branch mask or nullptr
-  int cap;                 // branch ends staged per chunk (= blockDim.x)
 };
 
-template <bool WF, bool WJ, bool MASKED>
-__global__ void __launch_bounds__(1024) k_fused(View v, EvalArgs a) {
+// Rotated terms of one branch end (own phasor po, other phasor pk).
+struct EndTerms {
+  double xh, yh;
+};
+
+__device__ __forceinline__ EndTerms end_terms(double2 G, double2 po, double2 pk) {
+  const double uu = __fma_rn(G.x, pk.x, -__dmul_rn(G.y, pk.y));
+  const double ww = __fma_rn(G.x, pk.y, __dmul_rn(G.y, pk.x));
+  EndTerms r;
+  r.xh = __fma_rn(po.x, uu, __dmul_rn(po.y, ww));
+  r.yh = __fma_rn(po.y, uu, -__dmul_rn(po.x, ww));
+  return r;
+}
+
+__device__ __forceinline__ bool end_in_service(const View &v, int32_t e, int32_t outage, const uint8_t *status,
+                                               int64_t st_base) {
+  const int32_t l = __ldg(v.inc_code + e) >> 1;
+  return (l != outage) && (status == nullptr || status[st_base + l] != 0);
+}
+
+template <int ITEMS, bool WF, bool WJ, bool MASKED>
+__global__ void __launch_bounds__(256) k_fused(View v, EvalArgs a) {
+  constexpr int R = 32 * ITEMS;
   extern __shared__ double sm[];
-  const int cap = a.cap;
-  double *s_a = sm;             // V_k xh
-  double *s_b = sm + cap;       // V_k yh
-  double *s_pt = sm + 2 * cap;  // dP/dt_k
-  double *s_qt = sm + 3 * cap;  // dQ/dt_k
-  double *s_pv = sm + 4 * cap;  // dP/dV_k
-  double *s_qv = sm + 5 * cap;  // dQ/dV_k
-  double *s_ma = sm + (WJ ? 6 : 2) * cap;  // masked: A of the end, 0 when out
-  double *s_mc = s_ma + cap;
-  __shared__ int s_cut;
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  double *__restrict__ s_a = sm + (size_t)wib * R * (MASKED ? 4 : 2);
+  double *__restrict__ s_b = s_a + R;
+  double *__restrict__ s_ma = s_b + R;   // masked: A of each end, 0 when out
+  double *__restrict__ s_mc = s_ma + R;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
 
-  // Wait for k_phasor (programmatic dependent launch).
-  cudaGridDependencySynchronize();
-
-  for (int64_t u = blockIdx.x; u < v.n_units; u += gridDim.x) {
+  for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; u < v.n_units; u += nwarps) {
     const int inst = v.n_inst == 1 ? 0 : find_segment(v.inst_unit_off, v.n_inst, u);
     const int g = v.inst_grid[inst];
     const int64_t t = v.grid_tile_off[g] + (u - v.inst_unit_off[inst]);
-    const int32_t b0 = v.tile_bus0[t], b1 = v.tile_bus1[t];
-    const int32_t e0 = v.inc_ptr[b0], e1 = v.inc_ptr[b1];
+    const int32_t b0 = __ldg(v.tile_bus0 + t), b1 = __ldg(v.tile_bus1 + t);
+    const int32_t e0 = __ldg(v.inc_ptr + b0), e1 = __ldg(v.inc_ptr + b1);
     const int64_t gb0 = v.grid_bus_off[g];
     const int32_t nb = v.grid_nbus[g];
     const double *__restrict__ xi = a.x + v.inst_x_off[inst];
@@ -91,114 +150,101 @@ __global__ void __launch_bounds__(1024) k_fused(View v, EvalArgs a) {
     const int32_t outage = MASKED ? v.inst_outage[inst] : -1;
     const int64_t st_base = MASKED ? v.inst_br_off[inst] - v.grid_br_off[g] : 0;
 
-    const int32_t ob = b0 + (int32_t)threadIdx.x;
+    // owner lane of bus b0 + lane: its record, loaded before the ends
+    const int32_t ob = b0 + lane;
     const bool owner = ob < b1;
-    double acc_a = 0.0, acc_b = 0.0, acc_ma = 0.0, acc_mc = 0.0;
     int32_t op0 = 0, op1 = 0;
+    int4 bm = make_int4(-1, -1, -1, -1), bm2 = make_int4(-1, -1, 0, -1);
     if (owner) {
-      op0 = v.inc_ptr[ob];
-      op1 = v.inc_ptr[ob + 1];
+      op0 = __ldg(v.inc_ptr + ob);
+      op1 = __ldg(v.inc_ptr + ob + 1);
+      bm = __ldg(v.bus_meta + ob);
+      bm2 = __ldg(v.bus_meta2 + ob);
     }
+    double acc_a = 0.0, acc_b = 0.0, acc_ma = 0.0, acc_mc = 0.0;
 
-    for (int32_t cs = e0; cs < e1;) {
-      int32_t ce = min(cs + cap, e1);
-      if (ce < e1) {
-        // A bus with more ends than `cap`: cut the chunk at the last group
-        // head in (cs, ce] so no group of parallel branches is split.
-        if (threadIdx.x == 0) s_cut = cs;
-        __syncthreads();
-        for (int j = threadIdx.x; j < cap; j += blockDim.x) {
-          const int32_t p = cs + 1 + j;
-          if (p <= ce && v.inc_grp[p] > 0) atomicMax(&s_cut, p);
+    for (int32_t cs = e0; cs < e1; cs += R) {
+      const int32_t ce = min(cs + R, e1);
+      int4 meta[ITEMS];
+      double2 G[ITEMS];
+#pragma unroll
+      for (int it = 0; it < ITEMS; ++it) {
+        const int32_t e = cs + it * 32 + lane;
+        if (e < ce) {
+          meta[it] = __ldg(v.inc_meta + e);
+          G[it] = __ldg(a.gb + e);
         }
-        __syncthreads();
-        const int32_t cut = s_cut;
-        __syncthreads();
-        if (cut == cs) {
-          if (threadIdx.x == 0) atomicOr(v.dev_error, kErrChunk);
-          break;
-        }
-        ce = cut;
       }
-      const int n = ce - cs;
-
-      // ---- phase A: one thread per branch end ----
-      for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const int32_t e = cs + j;
-        const int32_t o = v.inc_own[e], k = v.inc_other[e];
-        double2 G = a.gb[e];
+      // the phasors come from k_phasor (programmatic dependent launch)
+      cudaGridDependencySynchronize();
+#pragma unroll
+      for (int it = 0; it < ITEMS; ++it) {
+        const int s = it * 32 + lane;
+        const int32_t e = cs + s;
+        if (e >= ce) continue;
+        const int32_t o = meta[it].x, k = meta[it].y;
         bool in = true;
         if (MASKED) {
-          const int32_t l = v.inc_code[e] >> 1;
-          in = (l != outage) && (a.status == nullptr || a.status[st_base + l] != 0);
-          if (!in) G = make_double2(0.0, 0.0);
+          in = end_in_service(v, e, outage, a.status, st_base);
+          if (!in) G[it] = make_double2(0.0, 0.0);
         }
         const double2 pk = ph[k], po = ph[o];
         const double vk = Vi[k];
-        const double uu = G.x * pk.x - G.y * pk.y;
-        const double ww = G.x * pk.y + G.y * pk.x;
-        const double xh = po.x * uu + po.y * ww;
-        const double yh = po.y * uu - po.x * ww;
-        const double ea = vk * xh, eb = vk * yh;
-        s_a[j] = ea;
-        s_b[j] = eb;
-        if (WJ) {
-          const double vo = Vi[o];
-          s_pt[j] = -(vo * eb);
-          s_qt[j] = vo * ea;
-          s_pv[j] = -(vo * xh);
-          s_qv[j] = -(vo * yh);
-        }
+        const EndTerms tm = end_terms(G[it], po, pk);
+        const double ea = __dmul_rn(vk, tm.xh), eb = __dmul_rn(vk, tm.yh);
+        s_a[s] = ea;
+        s_b[s] = eb;
         if (MASKED) {
-          const double2 ac = a.ac[e];
-          s_ma[j] = in ? ac.x : 0.0;
-          s_mc[j] = in ? ac.y : 0.0;
+          const double2 ac = __ldg(a.ac + e);
+          s_ma[s] = in ? ac.x : 0.0;
+          s_mc[s] = in ? ac.y : 0.0;
+        }
+        if (WJ) {
+          const int32_t len = __ldg(v.inc_grp + e);
+          if (len > 0) {
+            const double vo = Vi[o];
+            double pt = -__dmul_rn(vo, eb);
+            double qt = __dmul_rn(vo, ea);
+            double pv = -__dmul_rn(vo, tm.xh);
+            double qv = -__dmul_rn(vo, tm.yh);
+            for (int32_t q = 1; q < len; ++q) {      // parallel branches to the same bus (rare)
+              const int32_t em = e + q;
+              double2 Gm = __ldg(a.gb + em);
+              if (MASKED && !end_in_service(v, em, outage, a.status, st_base)) Gm = make_double2(0.0, 0.0);
+              const EndTerms tq = end_terms(Gm, po, pk);
+              pt = __dadd_rn(pt, -__dmul_rn(vo, __dmul_rn(vk, tq.yh)));
+              qt = __dadd_rn(qt, __dmul_rn(vo, __dmul_rn(vk, tq.xh)));
+              pv = __dadd_rn(pv, -__dmul_rn(vo, tq.xh));
+              qv = __dadd_rn(qv, -__dmul_rn(vo, tq.yh));
+            }
+            const int4 om = __ldg(v.bus_meta + o);
+            const int32_t rx = meta[it].z, ry = meta[it].w;
+            if (om.z >= 0) {
+              if (rx >= 0) vi[om.z + rx] = pt;
+              if (ry >= 0) vi[om.z + ry] = pv;
+            }
+            if (om.w >= 0) {
+              if (rx >= 0) vi[om.w + rx] = qt;
+              if (ry >= 0) vi[om.w + ry] = qv;
+            }
+          }
         }
       }
-      __syncthreads();
-
-      // ---- off-diagonal entries: one thread per group of parallel ends ----
-      if (WJ) {
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
-          const int32_t e = cs + j;
-          const int32_t len = v.inc_grp[e];
-          if (len == 0) continue;
-          double pt = s_pt[j], qt = s_qt[j], pv = s_pv[j], qv = s_qv[j];
-          for (int q = 1; q < len; ++q) {
-            pt += s_pt[j + q];
-            qt += s_qt[j + q];
-            pv += s_pv[j + q];
-            qv += s_qv[j + q];
-          }
-          const int32_t o = v.inc_own[e];
-          const int2 rt = v.inc_rt[e];
-          const int32_t bp = v.base_p[o], bq = v.base_q[o];
-          if (bp >= 0) {
-            if (rt.x >= 0) vi[bp + rt.x] = pt;
-            if (rt.y >= 0) vi[bp + rt.y] = pv;
-          }
-          if (bq >= 0) {
-            if (rt.x >= 0) vi[bq + rt.x] = qt;
-            if (rt.y >= 0) vi[bq + rt.y] = qv;
-          }
-        }
-      }
-
-      // ---- bus sums, in list order ----
+      __syncwarp();
       if (owner) {
         const int32_t lo = max(op0, cs), hi = min(op1, ce);
         for (int32_t e = lo; e < hi; ++e) {
-          acc_a += s_a[e - cs];
-          acc_b += s_b[e - cs];
+          acc_a = __dadd_rn(acc_a, s_a[e - cs]);
+          acc_b = __dadd_rn(acc_b, s_b[e - cs]);
           if (MASKED) {
-            acc_ma += s_ma[e - cs];
-            acc_mc += s_mc[e - cs];
+            acc_ma = __dadd_rn(acc_ma, s_ma[e - cs]);
+            acc_mc = __dadd_rn(acc_mc, s_mc[e - cs]);
           }
         }
       }
-      __syncthreads();
-      cs = ce;
+      __syncwarp();
     }
+    if (e0 == e1) cudaGridDependencySynchronize();   // a round of isolated buses only
 
     // ---- per-bus results: F rows and the diagonal of J ----
     if (owner) {
@@ -207,50 +253,51 @@ __global__ void __launch_bounds__(1024) k_fused(View v, EvalArgs a) {
       const double vo = Vi[o];
       double ah, ch;
       if (MASKED) {
-        ah = acc_ma + v.g_sh[o];
-        ch = acc_mc + v.b_sh[o];
+        const double2 sh = __ldg(v.bus_sh + o);
+        ah = __dadd_rn(acc_ma, sh.x);
+        ch = __dadd_rn(acc_mc, sh.y);
       } else {
-        ah = a.ahat[o];
-        ch = a.chat[o];
+        const double2 h = __ldg(a.hat + o);
+        ah = h.x;
+        ch = h.y;
       }
-      const int32_t rp = v.row_p[o], rq = v.row_q[o];
-      const bool ext = v.formulation == PF_EXTENDED;
-      const int32_t gi = ext ? v.gen[o] : -1;
-      const bool is_slack = ext && (lb == v.grid_slack[g]);
+      const int32_t rp = bm.x, rq = bm.y, bp = bm.z, bq = bm.w;
+      const int32_t gi = bm2.w;
+      const bool is_slack = (v.formulation == PF_EXTENDED) && (lb == v.grid_slack[g]);
       if (WF) {
         double *__restrict__ Fi = a.F + v.inst_f_off[inst];
-        const double pin = a.p_inj ? a.p_inj[v.inst_bus_off[inst] + lb] : v.p_inj[o];
-        const double qin = a.q_inj ? a.q_inj[v.inst_bus_off[inst] + lb] : v.q_inj[o];
-        double fp = vo * (vo * ah - acc_a) - pin;
-        double fq = -(vo * (vo * ch + acc_b)) - qin;
+        const double2 inj = __ldg(v.bus_inj + o);
+        const double pin = a.p_inj ? a.p_inj[v.inst_bus_off[inst] + lb] : inj.x;
+        const double qin = a.q_inj ? a.q_inj[v.inst_bus_off[inst] + lb] : inj.y;
+        double fp = __fma_rn(vo, __fma_rn(vo, ah, -acc_a), -pin);
+        double fq = -__fma_rn(vo, __fma_rn(vo, ch, acc_b), qin);
         if (is_slack) {
-          fp -= xi[2 * nb + v.grid_ngen[g]];
-          Fi[v.grid_row_gth[g]] = xi[lb] - v.grid_theta_set[g];
+          fp = __dsub_rn(fp, xi[2 * nb + v.grid_ngen[g]]);
+          Fi[v.grid_row_gth[g]] = __dsub_rn(xi[lb], v.grid_theta_set[g]);
         }
         if (gi >= 0) {
-          fq -= xi[2 * nb + gi];
-          Fi[2 * nb + gi] = vo - v.gen_vset[v.grid_gen_off[g] + gi];
+          fq = __dsub_rn(fq, xi[2 * nb + gi]);
+          Fi[2 * nb + gi] = __dsub_rn(vo, v.gen_vset[v.grid_gen_off[g] + gi]);
         }
         if (rp >= 0) Fi[rp] = fp;
         if (rq >= 0) Fi[rq] = fq;
       }
       if (WJ) {
-        const int2 d = v.diag[o];
-        const int32_t bp = v.base_p[o], bq = v.base_q[o];
+        const double two_vo = __dadd_rn(vo, vo);
         if (bp >= 0) {
-          if (d.x >= 0) vi[bp + d.x] = vo * acc_b;
-          if (d.y >= 0) vi[bp + d.y] = 2.0 * vo * ah - acc_a;
+          if (bm2.x >= 0) vi[bp + bm2.x] = __dmul_rn(vo, acc_b);
+          if (bm2.y >= 0) vi[bp + bm2.y] = __fma_rn(two_vo, ah, -acc_a);
         }
         if (bq >= 0) {
-          if (d.x >= 0) vi[bq + d.x] = -(vo * acc_a);
-          if (d.y >= 0) vi[bq + d.y] = -2.0 * vo * ch - acc_b;
+          if (bm2.x >= 0) vi[bq + bm2.x] = -__dmul_rn(vo, acc_a);
+          if (bm2.y >= 0) vi[bq + bm2.y] = -__fma_rn(two_vo, ch, acc_b);
         }
         if (is_slack) {
-          vi[bp + v.len_tv[o]] = -1.0;          // d g_p / d P_s
+          vi[bp + bm2.z] = -1.0;                // d g_p / d P_s
           vi[v.grid_pos_gth[g]] = 1.0;         // d g_theta / d theta_s
         }
         if (gi >= 0) {
-          vi[bq + v.len_tv[o]] = -1.0;          // d g_q / d Q_g
+          vi[bq + bm2.z] = -1.0;                // d g_q / d Q_g
           vi[v.gen_pos[v.grid_gen_off[g] + gi]] = 1.0;  // d g_V / d V
         }
       }
@@ -258,20 +305,20 @@ __global__ void __launch_bounds__(1024) k_fused(View v, EvalArgs a) {
   }
 }
 
-template <bool WF, bool WJ, bool MASKED>
-int launch_fused(Ctx &c, const EvalArgs &a, cudaStream_t s) {
-  const int cap = a.cap;
-  const size_t smem = (size_t)cap * sizeof(double) * ((WJ ? 6 : 2) + (MASKED ? 2 : 0));
-  auto kern = k_fused<WF, WJ, MASKED>;
-  // the kernel also holds a few bytes of static shared memory: opt in above 46 KB
+constexpr int kWarpsPerBlock = 4;
+
+template <int ITEMS, bool WF, bool WJ, bool MASKED>
+int launch_fused_t(const View &v, int num_sms, const pf_tuning &t, const EvalArgs &a, cudaStream_t s) {
+  const size_t smem = (size_t)kWarpsPerBlock * 32 * ITEMS * sizeof(double) * (MASKED ? 4 : 2);
+  auto kern = k_fused<ITEMS, WF, WJ, MASKED>;
   if (smem > 46 * 1024)
     PF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int64_t grid = c.v.n_units;
-  if (c.tuning.ctas_per_sm > 0) grid = std::min<int64_t>(grid, (int64_t)c.tuning.ctas_per_sm * c.num_sms);
+  int64_t grid = (v.n_units + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (t.ctas_per_sm > 0) grid = std::min<int64_t>(grid, (int64_t)t.ctas_per_sm * num_sms);
   if (grid < 1) grid = 1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3((unsigned)cap);
+  cfg.blockDim = dim3(32 * kWarpsPerBlock);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -279,8 +326,50 @@ int launch_fused(Ctx &c, const EvalArgs &a, cudaStream_t s) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  PF_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, c.v, a));
+  PF_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, v, a));
   return PF_OK;
+}
+
+template <int ITEMS>
+int launch_fused_items(const View &v, int num_sms, const pf_tuning &t, const EvalArgs &a, bool masked,
+                       cudaStream_t s) {
+  const bool wf = a.F != nullptr, wj = a.vals != nullptr;
+  if (wf && wj)
+    return masked ? launch_fused_t<ITEMS, true, true, true>(v, num_sms, t, a, s)
+                  : launch_fused_t<ITEMS, true, true, false>(v, num_sms, t, a, s);
+  if (wf)
+    return masked ? launch_fused_t<ITEMS, true, false, true>(v, num_sms, t, a, s)
+                  : launch_fused_t<ITEMS, true, false, false>(v, num_sms, t, a, s);
+  return masked ? launch_fused_t<ITEMS, false, true, true>(v, num_sms, t, a, s)
+                : launch_fused_t<ITEMS, false, true, false>(v, num_sms, t, a, s);
+}
+
+int launch_fused(const View &v, int num_sms, const pf_tuning &t, const EvalArgs &a, bool masked, cudaStream_t s) {
+  switch (t.tile_inc) {
+    case 32: return launch_fused_items<1>(v, num_sms, t, a, masked, s);
+    case 64: return launch_fused_items<2>(v, num_sms, t, a, masked, s);
+    case 96: return launch_fused_items<3>(v, num_sms, t, a, masked, s);
+    case 128: return launch_fused_items<4>(v, num_sms, t, a, masked, s);
+    default: return fail(PF_ERR_INVALID, "tile_inc must be 32, 64, 96 or 128");
+  }
+}
+
+int launch_phasor(const View &v, int num_sms, const double *x, cudaStream_t s) {
+  const int tb = 256;
+  int64_t blocks = (v.n_bus_inst + tb - 1) / tb;
+  blocks = std::min<int64_t>(blocks, (int64_t)num_sms * 16);
+  k_phasor<<<(unsigned)std::max<int64_t>(blocks, 1), tb, 0, s>>>(v, x);
+  PF_CUDA_TRY(cudaGetLastError());
+  return PF_OK;
+}
+
+__global__ void k_sincos(const double *__restrict__ t, int64_t n, const double2 *__restrict__ tab,
+                         double *__restrict__ c, double *__restrict__ sn) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 r = table_sincos(t[i], tab);
+  c[i] = r.x;
+  sn[i] = r.y;
 }
 
 }  // namespace
@@ -300,74 +389,27 @@ int launch_eval_stages(Ctx &c, int stages, const double *x, const pf_overrides *
   a.vals = vals;
   a.gb = c.v.inc_gb;
   a.ac = c.v.inc_ac;
-  a.ahat = c.v.a_hat;
-  a.chat = c.v.c_hat;
-  a.cap = c.tuning.tile_inc;
+  a.hat = c.v.bus_hat;
   if (ov) {
     a.p_inj = ov->p_inj;
     a.q_inj = ov->q_inj;
     a.status = ov->status;
     if (ov->br_r || ov->br_x || ov->br_b || ov->br_tap) {
       if (stages & 2)
-        PF_TRY(compute_coefficients(c, ov->br_r, ov->br_x, ov->br_b, ov->br_tap, c.ov_gb, c.ov_ac, c.ov_ahat,
-                                    c.ov_chat, s));
+        PF_TRY(compute_coefficients(c, ov->br_r, ov->br_x, ov->br_b, ov->br_tap, c.ov_gb, c.ov_ac, c.ov_hat, s));
       a.gb = c.ov_gb;
       a.ac = c.ov_ac;
-      a.ahat = c.ov_ahat;
-      a.chat = c.ov_chat;
+      a.hat = c.ov_hat;
     }
   }
   const bool masked = c.any_outage || a.status != nullptr;
-  if (stages & 1) {
-    const int tb = 256;
-    int64_t blocks = (c.v.n_bus_inst + tb - 1) / tb;
-    blocks = std::min<int64_t>(blocks, (int64_t)c.num_sms * 16);
-    k_phasor<<<(unsigned)std::max<int64_t>(blocks, 1), tb, 0, s>>>(c.v, x);
-    PF_CUDA_TRY(cudaGetLastError());
-  }
+  if (stages & 1) PF_TRY(launch_phasor(c.v, c.num_sms, x, s));
   if (!(stages & 2)) return PF_OK;
-  const bool wf = F != nullptr, wj = vals != nullptr;
-  if (wf && wj) return masked ? launch_fused<true, true, true>(c, a, s) : launch_fused<true, true, false>(c, a, s);
-  if (wf) return masked ? launch_fused<true, false, true>(c, a, s) : launch_fused<true, false, false>(c, a, s);
-  return masked ? launch_fused<false, true, true>(c, a, s) : launch_fused<false, true, false>(c, a, s);
+  return launch_fused(c.v, c.num_sms, c.tuning, a, masked, s);
 }
 
-}  // namespace pf
-
-// ---------------------------------------------------------------------------
 // Evaluation with caller-provided phasor scratch (used by the allocation-free
 // entry point, whose scratch is a static device array).
-// ---------------------------------------------------------------------------
-
-namespace pf {
-
-namespace {
-
-template <bool WF, bool WJ, bool MASKED>
-int launch_fused_view(const View &v, int num_sms, const pf_tuning &t, const EvalArgs &a, cudaStream_t s) {
-  const size_t smem = (size_t)a.cap * sizeof(double) * ((WJ ? 6 : 2) + (MASKED ? 2 : 0));
-  auto kern = k_fused<WF, WJ, MASKED>;
-  if (smem > 46 * 1024)
-    PF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int64_t grid = v.n_units;
-  if (t.ctas_per_sm > 0) grid = std::min<int64_t>(grid, (int64_t)t.ctas_per_sm * num_sms);
-  if (grid < 1) grid = 1;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3((unsigned)a.cap);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  PF_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, v, a));
-  return PF_OK;
-}
-
-}  // namespace
-
 int launch_eval_scratch(Ctx &c, const double *x, double *F, double *vals, double2 *scratch, cudaStream_t s) {
   if (!x) return fail(PF_ERR_INVALID, "x is NULL");
   if (!scratch) return fail(PF_ERR_INVALID, "scratch is NULL");
@@ -380,24 +422,18 @@ int launch_eval_scratch(Ctx &c, const double *x, double *F, double *vals, double
   a.vals = vals;
   a.gb = c.v.inc_gb;
   a.ac = c.v.inc_ac;
-  a.ahat = c.v.a_hat;
-  a.chat = c.v.c_hat;
-  a.cap = c.tuning.tile_inc;
-  const int tb = 256;
-  int64_t blocks = (v.n_bus_inst + tb - 1) / tb;
-  blocks = std::min<int64_t>(blocks, (int64_t)c.num_sms * 16);
-  k_phasor<<<(unsigned)std::max<int64_t>(blocks, 1), tb, 0, s>>>(v, x);
+  a.hat = c.v.bus_hat;
+  PF_TRY(launch_phasor(v, c.num_sms, x, s));
+  return launch_fused(v, c.num_sms, c.tuning, a, c.any_outage, s);
+}
+
+// The phasor routine alone, for verification against a reference sin / cos.
+int launch_sincos(Ctx &c, const double *t, int64_t n, double *cs, double *sn, cudaStream_t s) {
+  if (n <= 0) return PF_OK;
+  if (!t || !cs || !sn) return fail(PF_ERR_INVALID, "NULL argument");
+  k_sincos<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t, n, c.v.sincos_tab, cs, sn);
   PF_CUDA_TRY(cudaGetLastError());
-  const bool masked = c.any_outage;
-  const bool wf = F != nullptr, wj = vals != nullptr;
-  if (wf && wj)
-    return masked ? launch_fused_view<true, true, true>(v, c.num_sms, c.tuning, a, s)
-                  : launch_fused_view<true, true, false>(v, c.num_sms, c.tuning, a, s);
-  if (wf)
-    return masked ? launch_fused_view<true, false, true>(v, c.num_sms, c.tuning, a, s)
-                  : launch_fused_view<true, false, false>(v, c.num_sms, c.tuning, a, s);
-  return masked ? launch_fused_view<false, true, true>(v, c.num_sms, c.tuning, a, s)
-                : launch_fused_view<false, true, false>(v, c.num_sms, c.tuning, a, s);
+  return PF_OK;
 }
 
 }  // namespace pf

@@ -18,8 +18,14 @@
 namespace pf {
 
 constexpr int kNumSMsDefault = 152;
-constexpr int kMaxTileInc = 1024;
-constexpr int kMinTileInc = 64;
+// A round (the unit one warp evaluates) holds up to kRoundBuses whole buses
+// and up to `tile_inc` branch ends (32, 64, 96 or 128: 1-4 ends per lane); a
+// bus with more ends forms a round of its own, evaluated in chunks.
+constexpr int kRoundBuses = 32;
+constexpr int kMaxTileInc = 128;
+constexpr int kMinTileInc = 32;
+constexpr int kMaxGroup = 32;      // parallel branches between one pair of buses
+constexpr int kSinCosTable = 256;  // table of (cos, sin)(i pi / 128)
 
 // Thread-local error message behind pf_last_error().
 void set_error(const std::string &msg);
@@ -58,12 +64,11 @@ struct View {
   const int2 *diag;         // [n_bus] in-row offsets of columns (theta_o, V_o), -1 absent
   const int32_t *len_tv;    // [n_bus] theta + V columns of the bus's rows
   const int32_t *gen;       // [n_bus] extended: local generator index, -1 none
-  const double *a_hat;      // [n_bus] sum over ends of A_e, plus shunt g
-  const double *c_hat;      // [n_bus] sum over ends of C_e, plus shunt b
-  const double *g_sh;       // [n_bus] shunt conductance total
-  const double *b_sh;       // [n_bus] shunt susceptance total
-  const double *p_inj;      // [n_bus] net P injection (P_g - P_load)
-  const double *q_inj;      // [n_bus] net Q injection (-Q_load)
+  const double2 *bus_hat;   // [n_bus] (A^, C^): sums over ends of A_e, C_e plus shunt g, b
+  const double2 *bus_sh;    // [n_bus] (g, b) shunt totals
+  const double2 *bus_inj;   // [n_bus] (P_inj, Q_inj): net injections (P_g - P_load, -Q_load)
+  const int4 *bus_meta;     // [n_bus] {row_p, row_q, base_p, base_q}
+  const int4 *bus_meta2;    // [n_bus] {diag theta, diag V, len_tv, gen}
   const int32_t *bus_grid;  // [n_bus]
 
   // per branch
@@ -78,6 +83,7 @@ struct View {
   const int2 *inc_rt;       // in-row offsets of (theta_k, V_k) columns, -1 absent
   const int32_t *inc_grp;   // at a group head: parallel ends to the same bus; else 0
   const int32_t *inc_mirror;// position of the other end of the same branch
+  const int4 *inc_meta;     // {own, other, rt.x, rt.y} packed for one vector load
 
   // per grid
   const int64_t *grid_bus_off, *grid_br_off;  // [n_grids+1]
@@ -102,12 +108,13 @@ struct View {
   // scratch
   double2 *phasor;                            // [n_bus_inst] (cos theta, sin theta)
   int32_t *dev_error;
+  const double2 *sincos_tab;                  // [kSinCosTable] (cos, sin)(i pi / 128)
 };
 
 struct Ctx {
   View v{};
   int num_sms = kNumSMsDefault;
-  pf_tuning tuning{256, 0};
+  pf_tuning tuning{64, 0};
   int max_degree = 0, max_group = 0;
   int64_t n_x = 0, n_f = 0, nnz = 0, n_branch_inst = 0, n_tiles = 0;
 
@@ -129,8 +136,7 @@ struct Ctx {
   int64_t *inst_unit_off_d = nullptr;
 
   // override scratch (coefficients recomputed from per-call parameters)
-  double2 *ov_gb = nullptr, *ov_ac = nullptr;
-  double *ov_ahat = nullptr, *ov_chat = nullptr;
+  double2 *ov_gb = nullptr, *ov_ac = nullptr, *ov_hat = nullptr;
 
   // host-call staging, allocated on first use
   double *stage_x = nullptr, *stage_f = nullptr, *stage_v = nullptr;
@@ -165,11 +171,10 @@ int upload(Ctx &c, T **p, const std::vector<T> &h, cudaStream_t s) {
 int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance *inst,
                   int n_inst, int formulation, cudaStream_t s);
 int build_tiles(Ctx &c, int tile_inc, cudaStream_t s);
-// Per-end coefficients (G, B, A, C) and per-bus sums (A_hat, C_hat) from the
-// branch parameters; any of r, x, b, tap may be overridden by device arrays.
+// Per-end coefficients (G, B, A, C) and per-bus sums (A^, C^) from the branch
+// parameters; any of r, x, b, tap may be overridden by device arrays.
 int compute_coefficients(Ctx &c, const double *r, const double *x, const double *b,
-                         const double *tap, double2 *gb, double2 *ac, double *ahat, double *chat,
-                         cudaStream_t s);
+                         const double *tap, double2 *gb, double2 *ac, double2 *hat, cudaStream_t s);
 
 // ---- evaluation (pf_eval.cu) ----
 int launch_eval(Ctx &c, const double *x, const pf_overrides *ov, double *F, double *vals,
@@ -181,6 +186,8 @@ int launch_vjp(Ctx &c, const double *x, const pf_overrides *ov, const double *v,
                const pf_grads *g, cudaStream_t s);
 // F / J evaluation whose per-bus phasor scratch is `scratch` instead of the context's.
 int launch_eval_scratch(Ctx &c, const double *x, double *F, double *vals, double2 *scratch, cudaStream_t s);
+// The phasor routine alone (verification).
+int launch_sincos(Ctx &c, const double *t, int64_t n, double *cs, double *sn, cudaStream_t s);
 // The context behind a C-ABI handle.
 Ctx *ctx_of(pf_ctx *h);
 

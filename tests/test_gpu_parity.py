@@ -119,8 +119,8 @@ def test_deterministic_across_runs_and_tunings(P, name):
     for _ in range(3):
         F1, v1 = ctx.residual_jacobian(x)
         assert torch.equal(F0, F1) and torch.equal(v0, v1)
-    for tile in (64, 96, 128, 512, 1024):
-        for ctas in (0, 1, 3):
+    for tile in (32, 64, 96, 128):
+        for ctas in (0, 1, 3, 16):
             ctx.set_tuning(tile, ctas)
             F1, v1 = ctx.residual_jacobian(x)
             assert torch.equal(F0, F1) and torch.equal(v0, v1), (tile, ctas)
@@ -134,7 +134,7 @@ def test_autotune_keeps_results(P):
     F0, v0 = ctx.residual_jacobian(x)
     F, v = torch.empty_like(F0), torch.empty_like(v0)
     t = ctx.autotune(x, F, v)
-    assert t["tile_inc"] in (128, 256, 512)
+    assert t["tile_inc"] in (32, 64, 96, 128)
     F1, v1 = ctx.residual_jacobian(x)
     assert torch.equal(F0, F1) and torch.equal(v0, v1)
 
@@ -188,3 +188,20 @@ def test_full_70k_against_oracle(P):
         assert_tol(F.cpu().numpy(), oracle.residual(sys, xn), f"70k F {k}")
         assert_tol(v.cpu().numpy(), oracle.jacobian(sys, xn)[2], f"70k J {k}")
     ctx.check_device()
+
+
+def test_phasor_routine_against_libm(P):
+    """The table-driven sin / cos of the phasor kernel vs the host libm (numpy),
+    including arguments past the table's reduction range."""
+    ctx = P.Context(GRIDS["three_bus"])
+    rng = np.random.default_rng(0)
+    th = np.concatenate([np.linspace(-7, 7, 400001), rng.uniform(-1e4, 1e4, 100000),
+                         [0.0, -0.0, np.pi, -np.pi, 1e5, -3e6, 65535.9, 65536.0]])
+    c, s = ctx.sincos(torch.from_numpy(th).cuda())
+    c, s = c.cpu().numpy(), s.cpu().numpy()
+    small = np.abs(th) <= 7
+    assert np.max(np.abs(c - np.cos(th))[small]) <= 4.5e-16
+    assert np.max(np.abs(s - np.sin(th))[small]) <= 4.5e-16
+    # larger arguments: the reduction error grows with |theta| (ulp of theta)
+    assert np.max(np.abs(c - np.cos(th))) <= 1e-12
+    assert np.max(np.abs(s - np.sin(th))) <= 1e-12
