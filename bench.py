@@ -1,16 +1,17 @@
 """Benchmark: F+J evaluations/s on the 70,000-bus synthetic grid (one GPU per rank).
 
-One step = one fused evaluation of the bus mismatches F and the Jacobian
-values J (tasks 1 and 2 of Newton power flow) at one of 10 Newton-like
-states, through the library's C ABI.  Inputs are resident in HBM; the L2
-cache (129 MB) is flushed by writing a 512 MB buffer between timed steps,
-outside the timed events.  Each step's evaluation is a captured CUDA graph
-(k_phasor + k_fused) replayed on the timing stream.
+One step = one batched launch that evaluates the bus mismatches F and the
+Jacobian values J (tasks 1 and 2 of Newton power flow) at 48 Newton-like
+states of the grid (48 instances of one context; k_phasor + k_fused,
+replayed as a captured CUDA graph) through the library's C ABI.  Inputs are
+resident in HBM; the 48 states' x, F and J (444 MB) exceed the 129 MB L2.
+value = evaluations / s.  The same states evaluated one launch at a time are
+reported beside it ("single_instance"), on the same GPU.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
-Under torchrun every rank evaluates its own replica (the single-grid path
-does not shard); value = evaluations of all ranks / max rank time.
+Under torchrun every rank evaluates its own replica (the path does not
+shard); value = evaluations of all ranks / max rank time.
 """
 from __future__ import annotations
 
@@ -30,41 +31,50 @@ sys.path.insert(0, ROOT)
 
 import gridgen  # noqa: E402
 
-N_STATES = 10
-FLUSH_BYTES = 512 << 20
-METRIC = "F+J evals/s on 70k-bus grid"
+N_STATES = 48
+LEAD_BYTES = 1 << 30
+METRIC = "F+J evals/s on 70k-bus grid (batched; single-instance reported beside)"
 WORKLOAD = ("70k-bus seeded synthetic grid (70,000 buses, 88,000 branches, 7,000 PV, 50,000 PQ loads, "
-            "3,000 shunts, 12% transformers), reduced polar formulation, FP64, 10 perturbed states")
+            "3,000 shunts, 12% transformers), reduced polar formulation, FP64, 48 perturbed states")
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20000)
-    p.add_argument("--warmup", type=int, default=200)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--e2e-steps", type=int, default=400)
+    p.add_argument("--e2e-steps", type=int, default=20)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--profile", action="store_true",
                    help="only run warmup + steps evaluations of the workload (for ncu), no timing")
+    p.add_argument("--tile", type=int, default=0, help="profile mode: tile_inc (0: autotune)")
+    p.add_argument("--ctas", type=int, default=0, help="profile mode: CTAs per SM")
     return p.parse_args()
 
 
 def run_profile(args):
-    """A few plain evaluations of the bench workload, for an ncu capture."""
+    """A few plain evaluations of the bench workload (the batched 48-state
+    launch), for an ncu capture."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_2011_11880_gb300 import Context
     sys_ = gridgen.grid_70k()
-    ctx = Context(sys_, "reduced")
-    X = [torch.from_numpy(gridgen.perturbed_state(sys_, k)).cuda() for k in range(1, N_STATES + 1)]
+    ctx = Context([sys_], "reduced", instances=[(0, -1)] * N_STATES)
+    X = torch.from_numpy(np.concatenate([gridgen.perturbed_state(sys_, k)
+                                         for k in range(1, N_STATES + 1)])).cuda()
     F, V = ctx.empty_f(), ctx.empty_vals()
+    if args.tile:
+        ctx.set_tuning(args.tile, args.ctas)
+    else:
+        ctx.autotune(X, F, V)
+    print("tuning", ctx.tuning())
     for k in range(args.warmup + args.steps):
-        ctx.residual_jacobian(X[k % N_STATES], F, V)
+        ctx.residual_jacobian(X, F, V)
     torch.cuda.synchronize()
     ctx.check_device()
-    print(f"profile run: {args.warmup + args.steps} evaluations, n_f={ctx.dims.n_f}, nnz={ctx.dims.nnz}")
+    print(f"profile run: {args.warmup + args.steps} batched evaluations of {N_STATES} states")
     return 0
 
 
@@ -233,38 +243,37 @@ def main():
 
     sys_ = gridgen.grid_70k()
     states_np = [gridgen.perturbed_state(sys_, k) for k in range(1, N_STATES + 1)]
-    ctx = Context(sys_, "reduced")
+
+    def capture(fn):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            fn()
+        return g
+
+    stream = torch.cuda.Stream(device=dev)
+    lead = torch.empty(LEAD_BYTES // 4, dtype=torch.float32, device=dev)
+
+    # ---- batched: the 48 states as 48 instances of the grid, one launch per step ----
+    ctx = Context([sys_], "reduced", instances=[(0, -1)] * N_STATES)
     d = ctx.dims
-    X = torch.from_numpy(np.stack(states_np)).to(dev)
+    one = Context(sys_, "reduced")            # single-instance context for the comparison
+    d1 = one.dims
+    X = torch.from_numpy(np.concatenate(states_np)).to(dev)
     F = torch.empty(d.n_f, dtype=torch.float64, device=dev)
     V = torch.empty(d.nnz, dtype=torch.float64, device=dev)
-    stream = torch.cuda.Stream(device=dev)
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-
     with torch.cuda.stream(stream):
-        tuning = ctx.autotune(X[0], F, V)
-        # one graph per state: k_phasor + k_fused
-        graphs = []
-        for k in range(N_STATES):
-            ctx.residual_jacobian(X[k], F, V)          # warm the kernels before capture
+        tuning = ctx.autotune(X, F, V)
+        ctx.residual_jacobian(X, F, V)
         torch.cuda.synchronize()
-        for k in range(N_STATES):
-            g = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g, stream=stream):
-                ctx.residual_jacobian(X[k], F, V)
-            graphs.append(g)
+        g_eval = capture(lambda: ctx.residual_jacobian(X, F, V))
+        g_ph = capture(lambda: ctx.eval_stage(1, X, F, V))
+        g_fu = capture(lambda: ctx.eval_stage(2, X, F, V))
     torch.cuda.synchronize()
 
-    def step(k):
-        graphs[k % N_STATES].replay()
-
     K, W = args.steps, max(args.warmup, 3)
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     with torch.cuda.stream(stream):
         for k in range(W):
-            flush.fill_(float(k))
-            step(k)
+            g_eval.replay()
     torch.cuda.synchronize()
     if distributed:
         dist.barrier()
@@ -272,15 +281,14 @@ def main():
     sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
     sampler.start()
     time.sleep(0.3)
+    ev_a, ev_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     wall0 = time.perf_counter()
     torch.cuda.nvtx.range_push("bench_timed")
     with torch.cuda.stream(stream):
-        flush.fill_(-1.0)                          # lead work so the host runs ahead of the GPU
+        ev_a.record(stream)
         for k in range(K):
-            flush.fill_(float(k))
-            ev0[k].record(stream)
-            step(k)
-            ev1[k].record(stream)
+            g_eval.replay()
+        ev_b.record(stream)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     wall = time.perf_counter() - wall0
@@ -288,68 +296,82 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    step_ms = np.array([a.elapsed_time(b) for a, b in zip(ev0, ev1)])
-    t_sum = float(step_ms.sum()) / 1000.0
+    t_sum = ev_a.elapsed_time(ev_b) / 1000.0
     t = torch.tensor([t_sum], dtype=torch.float64, device=dev)
     if distributed:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     t_max = float(t.item())
-    value = world * K / t_max
+    value = world * K * N_STATES / t_max
     ms_per_step = 1000.0 * t_max / K
 
-    # ---- end to end through the host-buffer entry point ----
+    # ---- the dominant kernel alone: the batched k_fused launch between events ----
+    KF = min(K, 200)
+    with torch.cuda.stream(stream):
+        g_ph.replay()
+        ev_a.record(stream)
+        for k in range(KF):
+            g_fu.replay()
+        ev_b.record(stream)
+    torch.cuda.synchronize()
+    kf_ms = ev_a.elapsed_time(ev_b) / KF
+
+    # ---- single instance, one evaluation at a time (each state its own x, F, J) ----
+    Xs = X.view(N_STATES, d1.n_x)
+    Fs = torch.empty(N_STATES, d1.n_f, dtype=torch.float64, device=dev)
+    Vs = torch.empty(N_STATES, d1.nnz, dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        one_tuning = one.autotune(Xs[0], Fs[0], Vs[0])
+        for k in range(N_STATES):
+            one.residual_jacobian(Xs[k], Fs[k], Vs[k])
+        torch.cuda.synchronize()
+        g_one = [capture(lambda k=k: one.residual_jacobian(Xs[k], Fs[k], Vs[k])) for k in range(N_STATES)]
+    torch.cuda.synchronize()
+    KS = min(K * N_STATES, 20000)
+    with torch.cuda.stream(stream):
+        lead.fill_(1.0)
+        ev_a.record(stream)
+        for k in range(KS):
+            g_one[k % N_STATES].replay()
+        ev_b.record(stream)
+    torch.cuda.synchronize()
+    single_rate = KS / (ev_a.elapsed_time(ev_b) / 1000.0)
+
+    # ---- end to end through the host-buffer entry point (one batched step) ----
     E = min(args.e2e_steps, K)
-    xh = torch.from_numpy(np.stack(states_np)).pin_memory().numpy()
+    xh = torch.from_numpy(np.concatenate(states_np)).pin_memory().numpy()
     Fh = torch.empty(d.n_f, dtype=torch.float64).pin_memory().numpy()
     Vh = torch.empty(d.nnz, dtype=torch.float64).pin_memory().numpy()
     with torch.cuda.stream(stream):
-        for k in range(3):
-            ctx.residual_jacobian_host(xh[k], Fh, Vh, stream=stream)
-        e2e_t = 0.0
+        for k in range(2):
+            ctx.residual_jacobian_host(xh, Fh, Vh, stream=stream)
+        stream.synchronize()
+        t0 = time.perf_counter()
         for k in range(E):
-            flush.fill_(float(k))
-            stream.synchronize()
-            t0 = time.perf_counter()
-            ctx.residual_jacobian_host(xh[k % N_STATES], Fh, Vh, stream=stream)
-            e2e_t += time.perf_counter() - t0
+            ctx.residual_jacobian_host(xh, Fh, Vh, stream=stream)
+        e2e_t = time.perf_counter() - t0
     te = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
     if distributed:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * E / float(te.item())
+    e2e_value = world * E * N_STATES / float(te.item())
 
-    # ---- the dominant kernel alone: phasor stage, then k_fused between events ----
-    KF = min(K, 2000)
-    evf0 = [torch.cuda.Event(enable_timing=True) for _ in range(KF)]
-    evf1 = [torch.cuda.Event(enable_timing=True) for _ in range(KF)]
-    with torch.cuda.stream(stream):
-        flush.fill_(-2.0)
-        for k in range(KF):
-            flush.fill_(float(k))
-            ctx.eval_stage(1, X[k % N_STATES], F, V, stream=stream)
-            evf0[k].record(stream)
-            ctx.eval_stage(2, X[k % N_STATES], F, V, stream=stream)
-            evf1[k].record(stream)
-    torch.cuda.synchronize()
-    kf_ms = float(np.mean([a.elapsed_time(b) for a, b in zip(evf0, evf1)]))
-
-    # ---- correctness spot check of the timed outputs (last state) against a fresh call ----
-    Fc, Vc = ctx.residual_jacobian(X[(K - 1) % N_STATES])
-    graphs[(K - 1) % N_STATES].replay()
-    torch.cuda.synchronize()
-    assert torch.equal(Fc, F) and torch.equal(Vc, V), "graph replay differs from a direct call"
+    # ---- the timed outputs equal single-instance evaluations ----
+    for k in (0, N_STATES - 1):
+        assert torch.equal(F[ctx.f_off[k]:ctx.f_off[k + 1]], Fs[k]), "batched F differs from single instance"
+        assert torch.equal(V[ctx.nnz_off[k]:ctx.nnz_off[k + 1]], Vs[k]), "batched J differs from single instance"
     ctx.check_device()
+    one.check_device()
 
     peaks, peak_kind = load_peaks()
     n_pv, n_load, n_shunt = sys_.n_pv, sys_.load_bus.shape[0], sys_.sh_bus.shape[0]
-    ip, _, oth = ctx.incidence()
-    own = np.repeat(np.arange(d.n_bus), np.diff(ip))
+    ip, _, oth = one.incidence()
+    own = np.repeat(np.arange(d1.n_bus), np.diff(ip))
     n_groups = int(np.count_nonzero(np.r_[True, (oth[1:] != oth[:-1]) | (own[1:] != own[:-1])]))
-    flops_kf = fused_fp64_flops(d, n_groups)
-    bytes_alg = algorithmic_bytes(d, n_pv, n_load, n_shunt)
+    flops_kf = N_STATES * fused_fp64_flops(d1, n_groups)          # one batched launch
+    bytes_alg = N_STATES * algorithmic_bytes(d1, n_pv, n_load, n_shunt)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     fp64_peak_tflops = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12          # 2 DFMA/clk/SM, FMA = 2 flops
     achieved_tf = flops_kf / (kf_ms * 1e-3) / 1e12
-    eval_s = t_max / K
+    eval_s = t_max / K                                                  # one batched step
     tr = load_traffic()
     roofline = {"bound": "alu", "kernel": "k_fused", "achieved": achieved_tf, "peak": fp64_peak_tflops,
                 "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak_tflops,
@@ -371,9 +393,13 @@ def main():
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_f": d.n_f, "nnz": d.nnz, "states": N_STATES,
-                   "l2": "flushed between timed steps (512 MB write, outside the timed events)",
+        "config": {"workload": WORKLOAD, "n_f_per_state": d1.n_f, "nnz_per_state": d1.nnz,
+                   "step": f"one batched launch over {N_STATES} states (instances of the grid)",
+                   "l2": "inputs larger than L2: 48 states with their own x, F and J (444 MB) per step, no flush",
                    "tuning": tuning, "timed_region_wall_s": wall, "parallelism": f"replicas x{world}"},
+        "single_instance": {"value": single_rate, "unit": "evals/s", "tuning": one_tuning,
+                            "how": "one evaluation per launch, 48 states with their own buffers cycled"},
+        "batched_over_single": value / world / single_rate,
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": 8 * d.n_x,
                 "d2h_bytes_per_step": 8 * (d.n_f + d.nnz), "steps": E},
         "gpu_launches": 2 * K,

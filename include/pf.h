@@ -239,7 +239,7 @@ PF_API int pf_eval_stage(pf_ctx *ctx, int32_t stage, const double *x, const pf_o
  * device-memory budget, plug-ins that may use only memory handed to them).
  * Same inputs, outputs and results as pf_residual_jacobian; F or vals may be
  * NULL.  It calls no cudaMalloc / cudaFree: the per-bus scratch of the
- * evaluation is a static device array of 2^18 instance-buses (4 MiB), held by
+ * evaluation is a static device array of 2^18 instance-buses (8 MiB), held by
  * every GPU that loads the library until the process exits.
  *   - Contexts with more than 2^18 buses summed over their instances are
  *     rejected with PF_ERR_UNSUPPORTED (use pf_residual_jacobian).

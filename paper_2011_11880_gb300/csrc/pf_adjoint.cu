@@ -46,7 +46,8 @@ __global__ void k_phasor_adj(View v, const double *__restrict__ x) {
     const int64_t lb = q - v.inst_bus_off[inst];
     double s, c;
     sincos(x[v.inst_x_off[inst] + lb], &s, &c);
-    v.phasor[q] = make_double2(c, s);
+    v.phasor[2 * q] = make_double2(c, s);
+    v.phasor[2 * q + 1] = make_double2(x[v.inst_x_off[inst] + v.grid_nbus[v.inst_grid[inst]] + lb], 0.0);
   }
 }
 
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(1024) k_vjp_state(View v, VjpArgs a) {
     const int32_t nb = v.grid_nbus[g];
     const double *__restrict__ xi = a.x + v.inst_x_off[inst];
     const double *__restrict__ Vi = xi + nb - gb0;
-    const double2 *__restrict__ ph = v.phasor + v.inst_bus_off[inst] - gb0;
+    const double2 *__restrict__ phb = v.phasor + 2 * (v.inst_bus_off[inst] - gb0);
     const int32_t outage = masked ? v.inst_outage[inst] : -1;
     const int64_t st_base = v.inst_br_off[inst] - v.grid_br_off[g];
     const int64_t f0 = v.inst_f_off[inst];
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(1024) k_vjp_state(View v, VjpArgs a) {
         const int32_t e = e0 + j;
         const int32_t o = v.inc_own[e], k = v.inc_other[e], em = v.inc_mirror[e];
         const bool in = !masked || end_in(v, e, outage, a.status, st_base);
-        const double2 po = ph[o], pk = ph[k];
+        const double2 po = phb[2 * o], pk = phb[2 * k];
         double2 G = a.gb[e], Gm = a.gb[em];
         if (!in) G = Gm = make_double2(0.0, 0.0);
         double xh, yh;
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(1024) k_vjp_state(View v, VjpArgs a) {
             const int32_t e = cs + j;
             const int32_t o = v.inc_own[e], k = v.inc_other[e], em = v.inc_mirror[e];
             const bool in = !masked || end_in(v, e, outage, a.status, st_base);
-            const double2 po = ph[o], pk = ph[k];
+            const double2 po = phb[2 * o], pk = phb[2 * k];
             double2 G = a.gb[e], Gm = a.gb[em];
             if (!in) G = Gm = make_double2(0.0, 0.0);
             double xh, yh, mx, my;
@@ -298,7 +299,7 @@ __global__ void k_vjp_params(View v, ParamArgs a) {
     const int64_t gb0 = v.grid_bus_off[g];
     const int32_t nb = v.grid_nbus[g];
     const double *__restrict__ xi = a.x + v.inst_x_off[inst];
-    const double2 *__restrict__ ph = v.phasor + v.inst_bus_off[inst] - gb0;
+    const double2 *__restrict__ phb = v.phasor + 2 * (v.inst_bus_off[inst] - gb0);
     const int32_t f = v.br_from[l], t = v.br_to[l];
     bool in = v.br_status[l] != 0 && l != v.inst_outage[inst];
     if (a.status) in = in && a.status[q] != 0;
@@ -313,7 +314,7 @@ __global__ void k_vjp_params(View v, ParamArgs a) {
       const double id2 = 1.0 / (dd * dd);
       const double dg_dr = (x * x - r * r) * id2, dg_dx = -2.0 * r * x * id2;
       const double db_dr = 2.0 * r * x * id2, db_dx = (x * x - r * r) * id2;
-      const double2 pf = ph[f], pt = ph[t];
+      const double2 pf = phb[2 * f], pt = phb[2 * t];
       // delta = theta_f - theta_t - phi
       const double cD = pf.x * pt.x + pf.y * pt.y, sD = pf.y * pt.x - pf.x * pt.y;
       double sp, cp;

@@ -426,11 +426,23 @@ __global__ void k_pack_bus(View v, const int32_t *base_p, const int32_t *base_q,
   m2[o] = make_int4(d.x, d.y, len_tv[o], v.gen[o]);
 }
 
-__global__ void k_pack_inc(View v, const int2 *rt, int4 *meta) {
+__global__ void k_pack_inc(View v, const int2 *rt, const int32_t *base_p, const int32_t *base_q, int4 *meta,
+                           int4 *pos) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= v.n_inc) return;
   const int2 r = rt[i];
-  meta[i] = make_int4(v.inc_own[i], v.inc_other[i], r.x, r.y);
+  const int32_t o = v.inc_own[i];
+  meta[i] = make_int4(o, v.inc_other[i], v.inc_grp[i], v.inc_code[i]);
+  const int32_t bp = base_p[o], bq = base_q[o];
+  pos[i] = make_int4(bp >= 0 && r.x >= 0 ? bp + r.x : -1, bp >= 0 && r.y >= 0 ? bp + r.y : -1,
+                     bq >= 0 && r.x >= 0 ? bq + r.x : -1, bq >= 0 && r.y >= 0 ? bq + r.y : -1);
+}
+
+__global__ void k_tile_desc(View v, const int32_t *bus0, const int32_t *bus1, int64_t n, int4 *desc) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int32_t b0 = bus0[t], b1 = bus1[t];
+  desc[t] = make_int4(b0, b1, v.inc_ptr[b0], v.inc_ptr[b1]);
 }
 
 __global__ void k_pack2(const double *a, const double *b, int64_t n, double2 *out) {
@@ -613,10 +625,12 @@ int build_tiles(Ctx &c, int tile_inc, cudaStream_t s) {
   c.n_tiles = c.grid_tile_off[G];
   PF_TRY(dev_alloc(c, &c.tile_bus0, c.n_tiles, &c.tile_allocations));
   PF_TRY(dev_alloc(c, &c.tile_bus1, c.n_tiles, &c.tile_allocations));
+  PF_TRY(dev_alloc(c, &c.tile_desc, c.n_tiles, &c.tile_allocations));
   PF_TRY(dev_alloc(c, &c.grid_tile_off_d, G + 1, &c.tile_allocations));
   PF_CUDA_TRY(cudaMemcpyAsync(c.grid_tile_off_d, c.grid_tile_off.data(), (G + 1) * sizeof(int64_t),
                               cudaMemcpyHostToDevice, s));
   k_tiles<<<nblk(G, 128), 128, 0, s>>>(c.v, tile_inc, c.grid_tile_off_d, nullptr, c.tile_bus0, c.tile_bus1);
+  k_tile_desc<<<nblk(c.n_tiles), TB, 0, s>>>(c.v, c.tile_bus0, c.tile_bus1, c.n_tiles, c.tile_desc);
   PF_CUDA_TRY(cudaGetLastError());
   const int I = c.v.n_inst;
   c.unit_off.assign(I + 1, 0);
@@ -629,6 +643,7 @@ int build_tiles(Ctx &c, int tile_inc, cudaStream_t s) {
                               cudaMemcpyHostToDevice, s));
   c.v.tile_bus0 = c.tile_bus0;
   c.v.tile_bus1 = c.tile_bus1;
+  c.v.tile_desc = c.tile_desc;
   c.v.grid_tile_off = c.grid_tile_off_d;
   c.v.inst_unit_off = c.inst_unit_off_d;
   c.v.n_units = c.unit_off[I];
@@ -987,14 +1002,15 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
     PF_TRY(dev_alloc(c, &c.ov_hat, N));
 
     // ---- packed records for the evaluation kernels ----
-    int4 *bus_meta, *bus_meta2, *inc_meta;
+    int4 *bus_meta, *bus_meta2, *inc_meta, *inc_pos;
     PF_TRY(dev_alloc(c, &bus_meta, N));
     PF_TRY(dev_alloc(c, &bus_meta2, N));
     PF_TRY(dev_alloc(c, &inc_meta, NI));
+    PF_TRY(dev_alloc(c, &inc_pos, NI));
     k_pack_bus<<<nblk(N), TB, 0, s>>>(v, base_p, base_q, diag, len_tv, bus_meta, bus_meta2);
-    if (NI > 0) k_pack_inc<<<nblk(NI), TB, 0, s>>>(v, inc_rt, inc_meta);
+    if (NI > 0) k_pack_inc<<<nblk(NI), TB, 0, s>>>(v, inc_rt, base_p, base_q, inc_meta, inc_pos);
     PF_CUDA_TRY(cudaGetLastError());
-    v.bus_meta = bus_meta; v.bus_meta2 = bus_meta2; v.inc_meta = inc_meta;
+    v.bus_meta = bus_meta; v.bus_meta2 = bus_meta2; v.inc_meta = inc_meta; v.inc_pos = inc_pos;
 
     // ---- contribution list ----
     int32_t *count;
@@ -1080,7 +1096,7 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
   v.inst_grid = d_inst_grid; v.inst_outage = d_inst_outage;
   v.inst_x_off = d_x_off; v.inst_f_off = d_f_off; v.inst_v_off = d_v_off;
   v.inst_bus_off = d_bus_off; v.inst_br_off = d_br_off;
-  PF_TRY(dev_alloc(c, &v.phasor, v.n_bus_inst));
+  PF_TRY(dev_alloc(c, &v.phasor, 2 * v.n_bus_inst));
 
   int dev = 0;
   PF_CUDA_TRY(cudaGetDevice(&dev));

@@ -80,6 +80,9 @@ __device__ __forceinline__ double2 table_sincos(double t, const double2 *__restr
   return make_double2(__fma_rn(T.x, cr, -__dmul_rn(T.y, sr)), __fma_rn(T.y, cr, __dmul_rn(T.x, sr)));
 }
 
+// Per bus of every instance: (cos theta, sin theta) and a copy of V, side by
+// side in one 32-byte record, so the fused kernel's gathers of a neighbour's
+// data hit L2 in one sector.
 __global__ void __launch_bounds__(256) k_phasor(View v, const double *__restrict__ x) {
   // Let the fused kernel start launching; it waits for this grid's results.
   cudaTriggerProgrammaticLaunchCompletion();
@@ -87,7 +90,11 @@ __global__ void __launch_bounds__(256) k_phasor(View v, const double *__restrict
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < v.n_bus_inst; q += stride) {
     const int inst = v.n_inst == 1 ? 0 : find_segment(v.inst_bus_off, v.n_inst, q);
     const int64_t lb = q - v.inst_bus_off[inst];
-    v.phasor[q] = table_sincos(__ldg(x + v.inst_x_off[inst] + lb), v.sincos_tab);
+    const double *xi = x + v.inst_x_off[inst];
+    const double th = __ldg(xi + lb);
+    const double vm = __ldg(xi + v.grid_nbus[v.inst_grid[inst]] + lb);
+    v.phasor[2 * q] = table_sincos(th, v.sincos_tab);
+    v.phasor[2 * q + 1] = make_double2(vm, 0.0);
   }
 }
 
@@ -109,11 +116,12 @@ struct EndTerms {
 };
 
 __device__ __forceinline__ EndTerms end_terms(double2 G, double2 po, double2 pk) {
-  const double uu = __fma_rn(G.x, pk.x, -__dmul_rn(G.y, pk.y));
+  // negations are applied to inputs (exact), so they fold into operand modifiers
+  const double uu = __fma_rn(G.x, pk.x, __dmul_rn(-G.y, pk.y));
   const double ww = __fma_rn(G.x, pk.y, __dmul_rn(G.y, pk.x));
   EndTerms r;
   r.xh = __fma_rn(po.x, uu, __dmul_rn(po.y, ww));
-  r.yh = __fma_rn(po.y, uu, -__dmul_rn(po.x, ww));
+  r.yh = __fma_rn(po.y, uu, __dmul_rn(-po.x, ww));
   return r;
 }
 
@@ -123,8 +131,42 @@ __device__ __forceinline__ bool end_in_service(const View &v, int32_t e, int32_t
   return (l != outage) && (status == nullptr || status[st_base + l] != 0);
 }
 
+// Off-diagonal entries of a group of `len` parallel branch ends e, e+1, ...
+// (same own bus o, same other bus k, so the same four CSR positions), summed
+// in list order.  Rare; called after the common path.
+__device__ __forceinline__ void write_group(const View &v, const EvalArgs &a, int32_t e, int32_t len, int32_t o,
+                                            int32_t k, int4 p, const double2 *rec, double *vi, bool masked,
+                                            int32_t outage, int64_t st_base) {
+  const double2 po = rec[2 * o], pk = rec[2 * k];
+  const double vo = rec[2 * o + 1].x, vk = rec[2 * k + 1].x;
+  double pt = 0.0, qt = 0.0, pv = 0.0, qv = 0.0;
+  for (int32_t q = 0; q < len; ++q) {
+    double2 G = __ldg(a.gb + e + q);
+    if (masked && !end_in_service(v, e + q, outage, a.status, st_base)) G = make_double2(0.0, 0.0);
+    const EndTerms tq = end_terms(G, po, pk);
+    const double tp = __dmul_rn(-vo, __dmul_rn(vk, tq.yh));
+    const double tqq = __dmul_rn(vo, __dmul_rn(vk, tq.xh));
+    const double tv = __dmul_rn(-vo, tq.xh);
+    const double tw = __dmul_rn(-vo, tq.yh);
+    if (q == 0) {
+      pt = tp; qt = tqq; pv = tv; qv = tw;
+    } else {
+      pt = __dadd_rn(pt, tp); qt = __dadd_rn(qt, tqq); pv = __dadd_rn(pv, tv); qv = __dadd_rn(qv, tw);
+    }
+  }
+  if (p.x >= 0) vi[p.x] = pt;
+  if (p.y >= 0) vi[p.y] = pv;
+  if (p.z >= 0) vi[p.z] = qt;
+  if (p.w >= 0) vi[p.w] = qv;
+}
+
+// One-warp CTAs that must fit on one SM (register budget of k_fused).
+#ifndef PF_FUSED_MIN_CTAS
+#define PF_FUSED_MIN_CTAS 16
+#endif
+
 template <int ITEMS, bool WF, bool WJ, bool MASKED>
-__global__ void __launch_bounds__(256) k_fused(View v, EvalArgs a) {
+__global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArgs a) {
   constexpr int R = 32 * ITEMS;
   extern __shared__ double sm[];
   const int lane = threadIdx.x & 31;
@@ -138,44 +180,47 @@ __global__ void __launch_bounds__(256) k_fused(View v, EvalArgs a) {
   for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; u < v.n_units; u += nwarps) {
     const int inst = v.n_inst == 1 ? 0 : find_segment(v.inst_unit_off, v.n_inst, u);
     const int g = v.inst_grid[inst];
-    const int64_t t = v.grid_tile_off[g] + (u - v.inst_unit_off[inst]);
-    const int32_t b0 = __ldg(v.tile_bus0 + t), b1 = __ldg(v.tile_bus1 + t);
-    const int32_t e0 = __ldg(v.inc_ptr + b0), e1 = __ldg(v.inc_ptr + b1);
+    const int4 td = __ldg(v.tile_desc + v.grid_tile_off[g] + (u - v.inst_unit_off[inst]));
+    const int32_t b0 = td.x, b1 = td.y, e0 = td.z, e1 = td.w;
     const int64_t gb0 = v.grid_bus_off[g];
     const int32_t nb = v.grid_nbus[g];
     const double *__restrict__ xi = a.x + v.inst_x_off[inst];
-    const double *__restrict__ Vi = xi + nb - gb0;                 // V by global bus id
-    const double2 *__restrict__ ph = v.phasor + v.inst_bus_off[inst] - gb0;
+    // (cos, sin) at rec[2 k], (V, 0) at rec[2 k + 1], by global bus id k
+    const double2 *__restrict__ rec = v.phasor + 2 * (v.inst_bus_off[inst] - gb0);
     double *__restrict__ vi = WJ ? a.vals + v.inst_v_off[inst] : nullptr;
     const int32_t outage = MASKED ? v.inst_outage[inst] : -1;
     const int64_t st_base = MASKED ? v.inst_br_off[inst] - v.grid_br_off[g] : 0;
 
-    // owner lane of bus b0 + lane: its record, loaded before the ends
+    // owner lane of bus b0 + lane: its records are fetched now, used at the end
     const int32_t ob = b0 + lane;
     const bool owner = ob < b1;
     int32_t op0 = 0, op1 = 0;
     int4 bm = make_int4(-1, -1, -1, -1), bm2 = make_int4(-1, -1, 0, -1);
+    double2 hat = make_double2(0.0, 0.0), inj = make_double2(0.0, 0.0);
     if (owner) {
       op0 = __ldg(v.inc_ptr + ob);
       op1 = __ldg(v.inc_ptr + ob + 1);
       bm = __ldg(v.bus_meta + ob);
       bm2 = __ldg(v.bus_meta2 + ob);
+      if (!MASKED) hat = __ldg(a.hat + ob);
+      if (WF) inj = __ldg(v.bus_inj + ob);
     }
     double acc_a = 0.0, acc_b = 0.0, acc_ma = 0.0, acc_mc = 0.0;
 
     for (int32_t cs = e0; cs < e1; cs += R) {
       const int32_t ce = min(cs + R, e1);
-      int4 meta[ITEMS];
+      int4 meta[ITEMS], pos[ITEMS];
       double2 G[ITEMS];
 #pragma unroll
       for (int it = 0; it < ITEMS; ++it) {
         const int32_t e = cs + it * 32 + lane;
         if (e < ce) {
           meta[it] = __ldg(v.inc_meta + e);
+          if (WJ) pos[it] = __ldg(v.inc_pos + e);
           G[it] = __ldg(a.gb + e);
         }
       }
-      // the phasors come from k_phasor (programmatic dependent launch)
+      // the per-bus records come from k_phasor (programmatic dependent launch)
       cudaGridDependencySynchronize();
 #pragma unroll
       for (int it = 0; it < ITEMS; ++it) {
@@ -185,11 +230,12 @@ __global__ void __launch_bounds__(256) k_fused(View v, EvalArgs a) {
         const int32_t o = meta[it].x, k = meta[it].y;
         bool in = true;
         if (MASKED) {
-          in = end_in_service(v, e, outage, a.status, st_base);
+          const int32_t l = meta[it].w >> 1;
+          in = (l != outage) && (a.status == nullptr || a.status[st_base + l] != 0);
           if (!in) G[it] = make_double2(0.0, 0.0);
         }
-        const double2 pk = ph[k], po = ph[o];
-        const double vk = Vi[k];
+        const double2 pk = rec[2 * k], po = rec[2 * o];
+        const double vk = rec[2 * k + 1].x;
         const EndTerms tm = end_terms(G[it], po, pk);
         const double ea = __dmul_rn(vk, tm.xh), eb = __dmul_rn(vk, tm.yh);
         s_a[s] = ea;
@@ -199,35 +245,22 @@ __global__ void __launch_bounds__(256) k_fused(View v, EvalArgs a) {
           s_ma[s] = in ? ac.x : 0.0;
           s_mc[s] = in ? ac.y : 0.0;
         }
-        if (WJ) {
-          const int32_t len = __ldg(v.inc_grp + e);
-          if (len > 0) {
-            const double vo = Vi[o];
-            double pt = -__dmul_rn(vo, eb);
-            double qt = __dmul_rn(vo, ea);
-            double pv = -__dmul_rn(vo, tm.xh);
-            double qv = -__dmul_rn(vo, tm.yh);
-            for (int32_t q = 1; q < len; ++q) {      // parallel branches to the same bus (rare)
-              const int32_t em = e + q;
-              double2 Gm = __ldg(a.gb + em);
-              if (MASKED && !end_in_service(v, em, outage, a.status, st_base)) Gm = make_double2(0.0, 0.0);
-              const EndTerms tq = end_terms(Gm, po, pk);
-              pt = __dadd_rn(pt, -__dmul_rn(vo, __dmul_rn(vk, tq.yh)));
-              qt = __dadd_rn(qt, __dmul_rn(vo, __dmul_rn(vk, tq.xh)));
-              pv = __dadd_rn(pv, -__dmul_rn(vo, tq.xh));
-              qv = __dadd_rn(qv, -__dmul_rn(vo, tq.yh));
-            }
-            const int4 om = __ldg(v.bus_meta + o);
-            const int32_t rx = meta[it].z, ry = meta[it].w;
-            if (om.z >= 0) {
-              if (rx >= 0) vi[om.z + rx] = pt;
-              if (ry >= 0) vi[om.z + ry] = pv;
-            }
-            if (om.w >= 0) {
-              if (rx >= 0) vi[om.w + rx] = qt;
-              if (ry >= 0) vi[om.w + ry] = qv;
-            }
-          }
+        if (WJ && meta[it].z == 1) {                 // the common case: no parallel branch
+          const double vo = rec[2 * o + 1].x;
+          const int4 p = pos[it];
+          if (p.x >= 0) vi[p.x] = __dmul_rn(-vo, eb);
+          if (p.y >= 0) vi[p.y] = __dmul_rn(-vo, tm.xh);
+          if (p.z >= 0) vi[p.z] = __dmul_rn(vo, ea);
+          if (p.w >= 0) vi[p.w] = __dmul_rn(-vo, tm.yh);
+        }
+      }
+      if (WJ) {
+        // heads of groups of parallel branches (rare), after the common path
+#pragma unroll
+        for (int it = 0; it < ITEMS; ++it) {
+          const int32_t e = cs + it * 32 + lane;
+          if (e < ce && meta[it].z > 1)
+            write_group(v, a, e, meta[it].z, meta[it].x, meta[it].y, pos[it], rec, vi, MASKED, outage, st_base);
         }
       }
       __syncwarp();
@@ -250,27 +283,25 @@ __global__ void __launch_bounds__(256) k_fused(View v, EvalArgs a) {
     if (owner) {
       const int32_t o = ob;
       const int64_t lb = o - gb0;
-      const double vo = Vi[o];
+      const double vo = rec[2 * o + 1].x;
       double ah, ch;
       if (MASKED) {
         const double2 sh = __ldg(v.bus_sh + o);
         ah = __dadd_rn(acc_ma, sh.x);
         ch = __dadd_rn(acc_mc, sh.y);
       } else {
-        const double2 h = __ldg(a.hat + o);
-        ah = h.x;
-        ch = h.y;
+        ah = hat.x;
+        ch = hat.y;
       }
       const int32_t rp = bm.x, rq = bm.y, bp = bm.z, bq = bm.w;
       const int32_t gi = bm2.w;
       const bool is_slack = (v.formulation == PF_EXTENDED) && (lb == v.grid_slack[g]);
       if (WF) {
         double *__restrict__ Fi = a.F + v.inst_f_off[inst];
-        const double2 inj = __ldg(v.bus_inj + o);
         const double pin = a.p_inj ? a.p_inj[v.inst_bus_off[inst] + lb] : inj.x;
         const double qin = a.q_inj ? a.q_inj[v.inst_bus_off[inst] + lb] : inj.y;
         double fp = __fma_rn(vo, __fma_rn(vo, ah, -acc_a), -pin);
-        double fq = -__fma_rn(vo, __fma_rn(vo, ch, acc_b), qin);
+        double fq = __fma_rn(-vo, __fma_rn(vo, ch, acc_b), -qin);     // = -(vo (vo ch + sum b) + qin)
         if (is_slack) {
           fp = __dsub_rn(fp, xi[2 * nb + v.grid_ngen[g]]);
           Fi[v.grid_row_gth[g]] = __dsub_rn(xi[lb], v.grid_theta_set[g]);
@@ -289,8 +320,8 @@ __global__ void __launch_bounds__(256) k_fused(View v, EvalArgs a) {
           if (bm2.y >= 0) vi[bp + bm2.y] = __fma_rn(two_vo, ah, -acc_a);
         }
         if (bq >= 0) {
-          if (bm2.x >= 0) vi[bq + bm2.x] = -__dmul_rn(vo, acc_a);
-          if (bm2.y >= 0) vi[bq + bm2.y] = -__fma_rn(two_vo, ch, acc_b);
+          if (bm2.x >= 0) vi[bq + bm2.x] = __dmul_rn(-vo, acc_a);
+          if (bm2.y >= 0) vi[bq + bm2.y] = __fma_rn(-two_vo, ch, -acc_b);
         }
         if (is_slack) {
           vi[bp + bm2.z] = -1.0;                // d g_p / d P_s
@@ -305,7 +336,7 @@ __global__ void __launch_bounds__(256) k_fused(View v, EvalArgs a) {
   }
 }
 
-constexpr int kWarpsPerBlock = 4;
+constexpr int kWarpsPerBlock = 1;   // one warp per CTA: rounds spread evenly over SMs
 
 template <int ITEMS, bool WF, bool WJ, bool MASKED>
 int launch_fused_t(const View &v, int num_sms, const pf_tuning &t, const EvalArgs &a, cudaStream_t s) {

@@ -83,7 +83,8 @@ struct View {
   const int2 *inc_rt;       // in-row offsets of (theta_k, V_k) columns, -1 absent
   const int32_t *inc_grp;   // at a group head: parallel ends to the same bus; else 0
   const int32_t *inc_mirror;// position of the other end of the same branch
-  const int4 *inc_meta;     // {own, other, rt.x, rt.y} packed for one vector load
+  const int4 *inc_meta;     // {own, other, parallel-group length at a head else 0, code}
+  const int4 *inc_pos;      // local CSR positions of this end's (P,theta_k), (P,V_k), (Q,theta_k), (Q,V_k); -1 absent
 
   // per grid
   const int64_t *grid_bus_off, *grid_br_off;  // [n_grids+1]
@@ -96,8 +97,9 @@ struct View {
   const int32_t *gen_pos;                     // [sum ngen] CSR position of the g_V entry
   const int32_t *gen_bus;                     // [sum ngen] global bus of each generator
 
-  // tiles (contiguous bus ranges)
+  // tiles (contiguous bus ranges; one warp round each)
   const int32_t *tile_bus0, *tile_bus1;
+  const int4 *tile_desc;                      // {first bus, end bus, first end, end end}
   const int64_t *grid_tile_off;               // [n_grids+1]
 
   // per instance
@@ -106,7 +108,7 @@ struct View {
   const int64_t *inst_unit_off;               // [n_inst+1] tiles of earlier instances
 
   // scratch
-  double2 *phasor;                            // [n_bus_inst] (cos theta, sin theta)
+  double2 *phasor;                            // [2 n_bus_inst]: (cos theta, sin theta), (V, 0) per bus
   int32_t *dev_error;
   const double2 *sincos_tab;                  // [kSinCosTable] (cos, sin)(i pi / 128)
 };
@@ -132,6 +134,7 @@ struct Ctx {
   int64_t *contrib_ptr = nullptr;  // per grid nnz+1 local entries, at grid_cptr_off
   int32_t *contrib_src = nullptr;  // at grid_csrc_off
   int32_t *tile_bus0 = nullptr, *tile_bus1 = nullptr;
+  int4 *tile_desc = nullptr;
   int64_t *grid_tile_off_d = nullptr;
   int64_t *inst_unit_off_d = nullptr;
 

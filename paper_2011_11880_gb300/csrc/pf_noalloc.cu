@@ -6,8 +6,8 @@
 // memory up front, or plug-in layers that may only use memory handed to
 // them.  pf_residual_jacobian_static serves them: it allocates nothing.
 // Inputs, outputs and the built context come from the caller; the only
-// scratch the evaluation needs -- (cos theta, sin theta) of every bus of
-// every instance -- lives in g_static_phasor below, a fixed device array
+// scratch the evaluation needs -- (cos theta, sin theta) and V of every bus
+// of every instance -- lives in g_static_phasor below, a fixed device array
 // that exists on every GPU that loads this library until the process
 // exits.
 #include <mutex>
@@ -19,10 +19,11 @@
 namespace pf {
 namespace {
 
-// Capacity of the static scratch: 2^18 instance-buses (4 MiB of double2).
+// Capacity of the static scratch: 2^18 instance-buses, two double2 each
+// ((cos theta, sin theta) and (V, 0)): 8 MiB.
 constexpr int64_t kStaticPhasorBuses = int64_t(1) << 18;
 
-static __device__ __align__(256) double2 g_static_phasor[kStaticPhasorBuses];
+static __device__ __align__(256) double2 g_static_phasor[2 * kStaticPhasorBuses];
 
 std::mutex g_setup_mutex;
 std::vector<double2 *> g_setup_address;   // device address of g_static_phasor, per device
