@@ -547,6 +547,130 @@ __global__ void k_tiles(View v, int cap, const int64_t *tile_off, int32_t *count
   if (count) count[g] = n;
 }
 
+
+// ---- rounds of the fused kernel ----------------------------------------------------
+
+// sort key: grid, then degree class (degree, or kLaneMaxDegree + 1 for a bus
+// with more ends), then bus id
+__global__ void k_round_keys(View v, uint64_t *keys, uint32_t *vals) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= v.n_bus) return;
+  const int32_t d = v.inc_ptr[b + 1] - v.inc_ptr[b];
+  const uint64_t cls = d > kLaneMaxDegree ? kLaneMaxDegree + 1 : d;
+  keys[b] = ((uint64_t)v.bus_grid[b] << 37) | (cls << 31) | (uint64_t)b;
+  vals[b] = (uint32_t)b;
+}
+
+__global__ void k_count_large(View v, int32_t *n_large) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= v.n_bus) return;
+  if (v.inc_ptr[b + 1] - v.inc_ptr[b] > kLaneMaxDegree) atomicAdd(n_large + v.bus_grid[b], 1);
+}
+
+// one thread per round: its buses and items per lane
+__global__ void k_round_fill(View v, const uint32_t *sorted, const int64_t *grid_round_off, const int32_t *n_large,
+                             int64_t n_rounds, int32_t *rbus, int4 *desc, int32_t *slots) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rounds) return;
+  const int g = find_segment(grid_round_off, v.n_grids, r);
+  const int64_t rl = r - grid_round_off[g];
+  const int64_t gb0 = v.grid_bus_off[g];
+  const int64_t n_norm = v.grid_nbus[g] - n_large[g];
+  const int64_t n_norm_rounds = (n_norm + 31) / 32;
+  if (rl < n_norm_rounds) {
+    int32_t nb = 0, dmax = 0;
+    for (int l = 0; l < 32; ++l) {
+      const int64_t i = 32 * rl + l;
+      int32_t b = -1;
+      if (i < n_norm) {
+        b = (int32_t)sorted[gb0 + i];
+        dmax = max(dmax, v.inc_ptr[b + 1] - v.inc_ptr[b]);
+        ++nb;
+      }
+      rbus[32 * r + l] = b;
+    }
+    desc[r] = make_int4(0, dmax, nb, 0);
+    slots[r] = 32 * dmax;
+  } else {
+    const int32_t b = (int32_t)sorted[gb0 + n_norm + (rl - n_norm_rounds)];
+    for (int l = 0; l < 32; ++l) rbus[32 * r + l] = l == 0 ? b : -1;
+    desc[r] = make_int4(0, v.inc_ptr[b + 1] - v.inc_ptr[b], 1, 1);
+    slots[r] = 0;
+  }
+}
+
+__global__ void k_round_base(const int64_t *S, int64_t n_rounds, int4 *desc, int32_t *err) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rounds) return;
+  if (S[r] > 0x7fffffffLL) atomicOr(err, kErrMap);
+  desc[r].x = (int32_t)S[r];
+}
+
+// one thread per slot: end j of lane l of its round (or padding)
+__global__ void k_slot_fill(View v, const int64_t *S, int64_t n_rounds, int64_t n_slots, const int4 *desc,
+                            const int32_t *rbus, int4 *smeta, int4 *spos, double2 *sgb, double2 *sac) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_slots) return;
+  const int64_t r = [&] {
+    int64_t lo = 0, hi = n_rounds - 1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) >> 1;
+      if (S[mid] <= q) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  }();
+  const int64_t rel = q - S[r];
+  const int j = (int)(rel / 32), l = (int)(rel % 32);
+  const int32_t b = rbus[32 * r + l];
+  const int32_t deg = b >= 0 ? v.inc_ptr[b + 1] - v.inc_ptr[b] : 0;
+  if (b >= 0 && j < deg) {
+    const int32_t e = v.inc_ptr[b] + j;
+    smeta[q] = make_int4(v.inc_other[e], v.inc_grp[e], v.inc_code[e], e);
+    spos[q] = v.inc_pos[e];
+    sgb[q] = v.inc_gb[e];
+    sac[q] = v.inc_ac[e];
+  } else {
+    smeta[q] = make_int4(0, -1, 0, 0);
+    spos[q] = make_int4(-1, -1, -1, -1);
+    sgb[q] = make_double2(0.0, 0.0);
+    sac[q] = make_double2(0.0, 0.0);
+  }
+  (void)desc;
+}
+
+// bus records in round order (and, for per-call overrides, the coefficients)
+__global__ void k_rbus_fill(View v, int64_t n, const int32_t *rbus, const double2 *hat, int4 *m1, int4 *m2,
+                            double2 *rh, double2 *ri) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t b = rbus[i];
+  if (b >= 0) {
+    if (m1) m1[i] = v.bus_meta[b];
+    if (m2) m2[i] = v.bus_meta2[b];
+    rh[i] = hat[b];
+    if (ri) ri[i] = v.bus_inj[b];
+  } else {
+    if (m1) m1[i] = make_int4(-1, -1, -1, -1);
+    if (m2) m2[i] = make_int4(-1, -1, 0, -1);
+    rh[i] = make_double2(0.0, 0.0);
+    if (ri) ri[i] = make_double2(0.0, 0.0);
+  }
+}
+
+__global__ void k_slot_coeff(int64_t n_slots, const int4 *smeta, const double2 *gb, const double2 *ac, double2 *sgb,
+                             double2 *sac) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_slots) return;
+  const int4 m = smeta[q];
+  if (m.y >= 0) {
+    sgb[q] = gb[m.w];
+    sac[q] = ac[m.w];
+  } else {
+    sgb[q] = make_double2(0.0, 0.0);
+    sac[q] = make_double2(0.0, 0.0);
+  }
+}
+
 template <class T>
 std::vector<T> to_host(const T *d, size_t n, cudaStream_t s, int *rc) {
   std::vector<T> h(n);
@@ -649,6 +773,115 @@ int build_tiles(Ctx &c, int tile_inc, cudaStream_t s) {
   c.v.n_units = c.unit_off[I];
   c.tuning.tile_inc = tile_inc;
   PF_CUDA_TRY(cudaStreamSynchronize(s));
+  return PF_OK;
+}
+
+
+// ---- rounds of the fused kernel: buses sorted by degree, 32 per round ---------------
+
+int build_rounds(Ctx &c, cudaStream_t s) {
+  View &v = c.v;
+  const int G = v.n_grids;
+  const int64_t N = v.n_bus;
+  TempList tmp;
+  const int64_t np = sort_padded(N);
+  uint64_t *keys;
+  uint32_t *vals;
+  int32_t *n_large;
+  PF_TRY(tmp.alloc(&keys, np));
+  PF_TRY(tmp.alloc(&vals, np));
+  PF_TRY(tmp.alloc(&n_large, G));
+  PF_CUDA_TRY(cudaMemsetAsync(n_large, 0, G * sizeof(int32_t), s));
+  k_round_keys<<<nblk(N), TB, 0, s>>>(v, keys, vals);
+  k_count_large<<<nblk(N), TB, 0, s>>>(v, n_large);
+  PF_CUDA_TRY(cudaGetLastError());
+  PF_TRY(bitonic_sort_pairs(keys, vals, N, s));
+  int rc = PF_OK;
+  std::vector<int32_t> h_large = to_host(n_large, G, s, &rc);
+  if (rc) return rc;
+  c.grid_round_off.assign(G + 1, 0);
+  for (int g = 0; g < G; ++g) {
+    const int64_t n_norm = c.grid_bus_off[g + 1] - c.grid_bus_off[g] - h_large[g];
+    c.grid_round_off[g + 1] = c.grid_round_off[g] + (n_norm + 31) / 32 + h_large[g];
+  }
+  const int64_t R = c.grid_round_off[G];
+  c.n_rounds = R;
+  int64_t *d_round_off, *S, *stmp;
+  int32_t *rbus, *slots, *err;
+  int4 *desc;
+  PF_TRY(upload(c, &d_round_off, c.grid_round_off, s));
+  PF_TRY(dev_alloc(c, &rbus, 32 * R));
+  PF_TRY(dev_alloc(c, &desc, R));
+  PF_TRY(tmp.alloc(&slots, R));
+  PF_TRY(tmp.alloc(&S, R + 1));
+  PF_TRY(tmp.alloc(&stmp, scan_tmp_elems(R) + 1));
+  PF_TRY(tmp.alloc(&err, 1));
+  PF_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
+  k_round_fill<<<nblk(R), TB, 0, s>>>(v, vals, d_round_off, n_large, R, rbus, desc, slots);
+  PF_CUDA_TRY(cudaGetLastError());
+  PF_TRY(exclusive_scan<int32_t>(slots, S, R, stmp, s));
+  k_round_base<<<nblk(R), TB, 0, s>>>(S, R, desc, err);
+  PF_CUDA_TRY(cudaGetLastError());
+  std::vector<int64_t> total = to_host(S + R, 1, s, &rc);
+  if (rc) return rc;
+  std::vector<int32_t> herr = to_host(err, 1, s, &rc);
+  if (rc) return rc;
+  if (herr[0]) return fail(PF_ERR_UNSUPPORTED, "more than 2^31 evaluation slots");
+  const int64_t NS = total[0];
+  c.n_slots = NS;
+  int4 *smeta, *spos, *m1, *m2;
+  double2 *sgb, *sac, *rh, *ri;
+  PF_TRY(dev_alloc(c, &smeta, NS));
+  PF_TRY(dev_alloc(c, &spos, NS));
+  PF_TRY(dev_alloc(c, &sgb, NS));
+  PF_TRY(dev_alloc(c, &sac, NS));
+  PF_TRY(dev_alloc(c, &m1, 32 * R));
+  PF_TRY(dev_alloc(c, &m2, 32 * R));
+  PF_TRY(dev_alloc(c, &rh, 32 * R));
+  PF_TRY(dev_alloc(c, &ri, 32 * R));
+  PF_TRY(dev_alloc(c, &c.ov_slot_gb, NS));
+  PF_TRY(dev_alloc(c, &c.ov_slot_ac, NS));
+  PF_TRY(dev_alloc(c, &c.ov_rbus_hat, 32 * R));
+  if (NS > 0) {
+    k_slot_fill<<<nblk(NS), TB, 0, s>>>(v, S, R, NS, desc, rbus, smeta, spos, sgb, sac);
+    PF_CUDA_TRY(cudaGetLastError());
+  }
+  k_rbus_fill<<<nblk(32 * R), TB, 0, s>>>(v, 32 * R, rbus, v.bus_hat, m1, m2, rh, ri);
+  PF_CUDA_TRY(cudaGetLastError());
+  v.grid_round_off = d_round_off;
+  v.round_desc = desc;
+  v.rbus = rbus;
+  v.rbus_meta = m1;
+  v.rbus_meta2 = m2;
+  v.rbus_hat = rh;
+  v.rbus_inj = ri;
+  v.slot_meta = smeta;
+  v.slot_pos = spos;
+  v.slot_gb = sgb;
+  v.slot_ac = sac;
+  const int I = v.n_inst;
+  c.round_off.assign(I + 1, 0);
+  for (int i = 0; i < I; ++i) {
+    const int g = c.inst_grid[i];
+    c.round_off[i + 1] = c.round_off[i] + (c.grid_round_off[g + 1] - c.grid_round_off[g]);
+  }
+  int64_t *d_inst_round_off;
+  PF_TRY(upload(c, &d_inst_round_off, c.round_off, s));
+  v.inst_round_off = d_inst_round_off;
+  v.n_round_units = c.round_off[I];
+  PF_CUDA_TRY(cudaStreamSynchronize(s));
+  return PF_OK;
+}
+
+int permute_overrides(Ctx &c, cudaStream_t s) {
+  if (c.n_slots > 0) {
+    k_slot_coeff<<<nblk(c.n_slots), TB, 0, s>>>(c.n_slots, c.v.slot_meta, c.ov_gb, c.ov_ac, c.ov_slot_gb,
+                                                c.ov_slot_ac);
+    PF_CUDA_TRY(cudaGetLastError());
+  }
+  k_rbus_fill<<<nblk(32 * c.n_rounds), TB, 0, s>>>(c.v, 32 * c.n_rounds, c.v.rbus, c.ov_hat, nullptr, nullptr,
+                                                   c.ov_rbus_hat, nullptr);
+  PF_CUDA_TRY(cudaGetLastError());
   return PF_OK;
 }
 
@@ -1116,6 +1349,7 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
     v.sincos_tab = d_tab;
   }
   PF_TRY(build_tiles(c, 64, s));
+  PF_TRY(build_rounds(c, s));
   PF_CUDA_TRY(cudaStreamSynchronize(s));
   return PF_OK;
 }

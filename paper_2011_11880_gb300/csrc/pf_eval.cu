@@ -20,14 +20,15 @@
 // where A^ = sum A + shunt g and C^ = sum C + shunt b.  No division; 14
 // FP64 operations per branch end plus two adds into its bus's sums.
 //
-// Work decomposition.  One warp evaluates one round: up to 32 whole
-// consecutive buses with up to R = 32 * ITEMS branch ends (ITEMS ends per
-// lane); a bus with more than R ends is a round of its own, evaluated in
-// chunks of R.  Lanes compute the ends, owner lanes (one per bus) sum their
-// bus's ends and write the bus's F rows and diagonal J entries; the head end
-// of a group of parallel branches writes the group's off-diagonal entries
-// (its members are recomputed, which is rare and keeps groups independent of
-// chunking).
+// Work decomposition.  The buses of each grid are sorted by degree (number
+// of branch ends) and cut into rounds of 32; one warp evaluates one round,
+// one bus per lane.  A lane walks its bus's ends in incidence-list order,
+// computes each end's terms, writes the end's off-diagonal J entries (a group
+// of parallel branches is summed in list order and written at its last end),
+// keeps the bus sums in registers, and finally writes the bus's F rows and
+// diagonal J entries.  Because the buses of a round have the same degree,
+// nearly every lane does useful FP64 work at every step.  A bus with more
+// than 32 ends is a round of its own, evaluated by the whole warp in chunks.
 //
 // Determinism: every operation is an explicitly rounded intrinsic and every
 // sum runs in incidence-list order, so results are bit-identical run to run,
@@ -102,9 +103,12 @@ struct EvalArgs {
   const double *x;
   double *F;
   double *vals;
-  const double2 *gb;
+  const double2 *gb;        // per end, incidence order
   const double2 *ac;
-  const double2 *hat;
+  const double2 *hat;       // per bus
+  const double2 *sgb;       // per end, slot order of the rounds
+  const double2 *sac;
+  const double2 *rhat;      // per bus, round order
   const double *p_inj;     // per-instance-bus override or nullptr
   const double *q_inj;
   const uint8_t *status;   // per-instance-branch mask or nullptr
@@ -160,28 +164,162 @@ __device__ __forceinline__ void write_group(const View &v, const EvalArgs &a, in
   if (p.w >= 0) vi[p.w] = qv;
 }
 
+// F rows, the extended formulation's extra rows and the diagonal of J for
+// bus o (global id) of one instance, from the sums over its ends.
+template <bool WF, bool WJ>
+__device__ __forceinline__ void finalize_bus(const View &v, const EvalArgs &a, int inst, int g, int32_t o,
+                                             int64_t gb0, int32_t nb, const double *xi, double *vi, double vo,
+                                             double acc_a, double acc_b, double ah, double ch, int4 bm, int4 bm2,
+                                             double2 inj) {
+  const int64_t lb = o - gb0;
+  const int32_t rp = bm.x, rq = bm.y, bp = bm.z, bq = bm.w;
+  const int32_t gi = bm2.w;
+  const bool is_slack = (v.formulation == PF_EXTENDED) && (lb == v.grid_slack[g]);
+  if (WF) {
+    double *__restrict__ Fi = a.F + v.inst_f_off[inst];
+    const double pin = a.p_inj ? a.p_inj[v.inst_bus_off[inst] + lb] : inj.x;
+    const double qin = a.q_inj ? a.q_inj[v.inst_bus_off[inst] + lb] : inj.y;
+    double fp = __fma_rn(vo, __fma_rn(vo, ah, -acc_a), -pin);
+    double fq = __fma_rn(-vo, __fma_rn(vo, ch, acc_b), -qin);     // = -(vo (vo ch + sum b) + qin)
+    if (is_slack) {
+      fp = __dsub_rn(fp, xi[2 * nb + v.grid_ngen[g]]);
+      Fi[v.grid_row_gth[g]] = __dsub_rn(xi[lb], v.grid_theta_set[g]);
+    }
+    if (gi >= 0) {
+      fq = __dsub_rn(fq, xi[2 * nb + gi]);
+      Fi[2 * nb + gi] = __dsub_rn(vo, v.gen_vset[v.grid_gen_off[g] + gi]);
+    }
+    if (rp >= 0) Fi[rp] = fp;
+    if (rq >= 0) Fi[rq] = fq;
+  }
+  if (WJ) {
+    const double two_vo = __dadd_rn(vo, vo);
+    if (bp >= 0) {
+      if (bm2.x >= 0) vi[bp + bm2.x] = __dmul_rn(vo, acc_b);
+      if (bm2.y >= 0) vi[bp + bm2.y] = __fma_rn(two_vo, ah, -acc_a);
+    }
+    if (bq >= 0) {
+      if (bm2.x >= 0) vi[bq + bm2.x] = __dmul_rn(-vo, acc_a);
+      if (bm2.y >= 0) vi[bq + bm2.y] = __fma_rn(-two_vo, ch, -acc_b);
+    }
+    if (is_slack) {
+      vi[bp + bm2.z] = -1.0;                // d g_p / d P_s
+      vi[v.grid_pos_gth[g]] = 1.0;         // d g_theta / d theta_s
+    }
+    if (gi >= 0) {
+      vi[bq + bm2.z] = -1.0;                // d g_q / d Q_g
+      vi[v.gen_pos[v.grid_gen_off[g] + gi]] = 1.0;  // d g_V / d V
+    }
+  }
+}
+
+// One bus with more than 32 ends, evaluated by the whole warp in chunks of
+// R = 32 ITEMS ends (incidence order): lanes compute the ends and write the
+// off-diagonal entries, lane 0 sums the chunk in list order.
+template <int ITEMS, bool WF, bool WJ, bool MASKED>
+__device__ __noinline__ void large_bus_round(const View &v, const EvalArgs &a, int inst, int g, int32_t o,
+                                             const double2 *__restrict__ rec, double *__restrict__ vi,
+                                             const double *__restrict__ xi, int32_t outage, int64_t st_base) {
+  constexpr int R = 32 * ITEMS;
+  extern __shared__ double sm[];
+  double *__restrict__ s_a = sm;
+  double *__restrict__ s_b = s_a + R;
+  double *__restrict__ s_ma = s_b + R;   // masked: A of each end, 0 when out
+  double *__restrict__ s_mc = s_ma + R;
+  const int lane = threadIdx.x & 31;
+  const int32_t e0 = __ldg(v.inc_ptr + o), e1 = __ldg(v.inc_ptr + o + 1);
+  double acc_a = 0.0, acc_b = 0.0, acc_ma = 0.0, acc_mc = 0.0;
+  cudaGridDependencySynchronize();
+  const double2 po = rec[2 * o];
+  const double vo = rec[2 * o + 1].x;
+  for (int32_t cs = e0; cs < e1; cs += R) {
+    const int32_t ce = min(cs + R, e1);
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+      const int s = it * 32 + lane;
+      const int32_t e = cs + s;
+      if (e >= ce) continue;
+      const int4 meta = __ldg(v.inc_meta + e);
+      double2 G = __ldg(a.gb + e);
+      bool in = true;
+      if (MASKED) {
+        const int32_t l = meta.w >> 1;
+        in = (l != outage) && (a.status == nullptr || a.status[st_base + l] != 0);
+        if (!in) G = make_double2(0.0, 0.0);
+      }
+      const int32_t k = meta.y;
+      const double2 pk = rec[2 * k];
+      const double vk = rec[2 * k + 1].x;
+      const EndTerms tm = end_terms(G, po, pk);
+      const double ea = __dmul_rn(vk, tm.xh), eb = __dmul_rn(vk, tm.yh);
+      s_a[s] = ea;
+      s_b[s] = eb;
+      if (MASKED) {
+        const double2 ac = __ldg(a.ac + e);
+        s_ma[s] = in ? ac.x : 0.0;
+        s_mc[s] = in ? ac.y : 0.0;
+      }
+      if (WJ) {
+        const int4 p = __ldg(v.inc_pos + e);
+        if (meta.z == 1) {
+          if (p.x >= 0) vi[p.x] = __dmul_rn(-vo, eb);
+          if (p.y >= 0) vi[p.y] = __dmul_rn(-vo, tm.xh);
+          if (p.z >= 0) vi[p.z] = __dmul_rn(vo, ea);
+          if (p.w >= 0) vi[p.w] = __dmul_rn(-vo, tm.yh);
+        } else if (meta.z > 1) {
+          write_group(v, a, e, meta.z, o, k, p, rec, vi, MASKED, outage, st_base);
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      for (int32_t e = cs; e < ce; ++e) {
+        acc_a = __dadd_rn(acc_a, s_a[e - cs]);
+        acc_b = __dadd_rn(acc_b, s_b[e - cs]);
+        if (MASKED) {
+          acc_ma = __dadd_rn(acc_ma, s_ma[e - cs]);
+          acc_mc = __dadd_rn(acc_mc, s_mc[e - cs]);
+        }
+      }
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    double ah, ch;
+    if (MASKED) {
+      const double2 sh = __ldg(v.bus_sh + o);
+      ah = __dadd_rn(acc_ma, sh.x);
+      ch = __dadd_rn(acc_mc, sh.y);
+    } else {
+      const double2 hat = __ldg(a.hat + o);
+      ah = hat.x;
+      ch = hat.y;
+    }
+    const double2 inj = WF ? __ldg(v.bus_inj + o) : make_double2(0.0, 0.0);
+    finalize_bus<WF, WJ>(v, a, inst, g, o, v.grid_bus_off[g], v.grid_nbus[g], xi, vi, vo, acc_a, acc_b, ah, ch,
+                         __ldg(v.bus_meta + o), __ldg(v.bus_meta2 + o), inj);
+  }
+}
+
 // One-warp CTAs that must fit on one SM (register budget of k_fused).
 #ifndef PF_FUSED_MIN_CTAS
 #define PF_FUSED_MIN_CTAS 16
 #endif
 
+// One warp per round.  A round holds up to 32 buses of equal (or adjacent)
+// degree, one per lane; lane l walks the ends of its bus in incidence order
+// (slot first + 32 j + l holds end j, so every fetch of the round's end data
+// is coalesced), keeps the bus sums in registers and writes the off-diagonal
+// entries of each end, summing a group of parallel branches in list order
+// before it writes the group's entries.  Ends are fetched ITEMS at a time.
 template <int ITEMS, bool WF, bool WJ, bool MASKED>
 __global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArgs a) {
-  constexpr int R = 32 * ITEMS;
-  extern __shared__ double sm[];
   const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  double *__restrict__ s_a = sm + (size_t)wib * R * (MASKED ? 4 : 2);
-  double *__restrict__ s_b = s_a + R;
-  double *__restrict__ s_ma = s_b + R;   // masked: A of each end, 0 when out
-  double *__restrict__ s_mc = s_ma + R;
-  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-
-  for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; u < v.n_units; u += nwarps) {
-    const int inst = v.n_inst == 1 ? 0 : find_segment(v.inst_unit_off, v.n_inst, u);
+  for (int64_t u = blockIdx.x; u < v.n_round_units; u += gridDim.x) {
+    const int inst = v.n_inst == 1 ? 0 : find_segment(v.inst_round_off, v.n_inst, u);
     const int g = v.inst_grid[inst];
-    const int4 td = __ldg(v.tile_desc + v.grid_tile_off[g] + (u - v.inst_unit_off[inst]));
-    const int32_t b0 = td.x, b1 = td.y, e0 = td.z, e1 = td.w;
+    const int64_t r = v.grid_round_off[g] + (u - v.inst_round_off[inst]);
+    const int4 rd = __ldg(v.round_desc + r);     // {first slot, items per lane, buses, large}
     const int64_t gb0 = v.grid_bus_off[g];
     const int32_t nb = v.grid_nbus[g];
     const double *__restrict__ xi = a.x + v.inst_x_off[inst];
@@ -190,100 +328,104 @@ __global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArg
     double *__restrict__ vi = WJ ? a.vals + v.inst_v_off[inst] : nullptr;
     const int32_t outage = MASKED ? v.inst_outage[inst] : -1;
     const int64_t st_base = MASKED ? v.inst_br_off[inst] - v.grid_br_off[g] : 0;
+    if (rd.w) {
+      large_bus_round<ITEMS, WF, WJ, MASKED>(v, a, inst, g, __ldg(v.rbus + 32 * r), rec, vi, xi, outage, st_base);
+      continue;
+    }
 
-    // owner lane of bus b0 + lane: its records are fetched now, used at the end
-    const int32_t ob = b0 + lane;
-    const bool owner = ob < b1;
-    int32_t op0 = 0, op1 = 0;
+    // this lane's bus: records in round order, fetched before the wait
+    const int64_t rb = 32 * r + lane;
+    const bool owner = lane < rd.z;
+    int32_t o = 0;
     int4 bm = make_int4(-1, -1, -1, -1), bm2 = make_int4(-1, -1, 0, -1);
     double2 hat = make_double2(0.0, 0.0), inj = make_double2(0.0, 0.0);
     if (owner) {
-      op0 = __ldg(v.inc_ptr + ob);
-      op1 = __ldg(v.inc_ptr + ob + 1);
-      bm = __ldg(v.bus_meta + ob);
-      bm2 = __ldg(v.bus_meta2 + ob);
-      if (!MASKED) hat = __ldg(a.hat + ob);
-      if (WF) inj = __ldg(v.bus_inj + ob);
+      o = __ldg(v.rbus + rb);
+      bm = __ldg(v.rbus_meta + rb);
+      bm2 = __ldg(v.rbus_meta2 + rb);
+      if (!MASKED) hat = __ldg(a.rhat + rb);
+      if (WF) inj = __ldg(v.rbus_inj + rb);
     }
     double acc_a = 0.0, acc_b = 0.0, acc_ma = 0.0, acc_mc = 0.0;
+    // running sums of a group of parallel branches, written at its last end
+    double gpt = 0.0, gqt = 0.0, gpv = 0.0, gqv = 0.0;
+    int4 gpos = make_int4(-1, -1, -1, -1);
+    int32_t grem = 0;
+    double2 po = make_double2(0.0, 0.0);
+    double vo = 0.0;
+    const int32_t D = rd.y;
+    const int64_t q0 = (int64_t)rd.x + lane;
 
-    for (int32_t cs = e0; cs < e1; cs += R) {
-      const int32_t ce = min(cs + R, e1);
+    for (int32_t j0 = 0; j0 < D; j0 += ITEMS) {
       int4 meta[ITEMS], pos[ITEMS];
-      double2 G[ITEMS];
+      double2 G[ITEMS], AC[ITEMS];
 #pragma unroll
       for (int it = 0; it < ITEMS; ++it) {
-        const int32_t e = cs + it * 32 + lane;
-        if (e < ce) {
-          meta[it] = __ldg(v.inc_meta + e);
-          if (WJ) pos[it] = __ldg(v.inc_pos + e);
-          G[it] = __ldg(a.gb + e);
+        meta[it] = make_int4(0, -1, 0, 0);
+        if (j0 + it < D) {
+          const int64_t q = q0 + 32 * (j0 + it);
+          meta[it] = __ldg(v.slot_meta + q);
+          if (WJ) pos[it] = __ldg(v.slot_pos + q);
+          G[it] = __ldg(a.sgb + q);
+          if (MASKED) AC[it] = __ldg(a.sac + q);
         }
       }
-      // the per-bus records come from k_phasor (programmatic dependent launch)
-      cudaGridDependencySynchronize();
+      if (j0 == 0) {
+        // the per-bus records come from k_phasor (programmatic dependent launch)
+        cudaGridDependencySynchronize();
+        if (owner) {
+          po = rec[2 * o];
+          vo = rec[2 * o + 1].x;
+        }
+      }
 #pragma unroll
       for (int it = 0; it < ITEMS; ++it) {
-        const int s = it * 32 + lane;
-        const int32_t e = cs + s;
-        if (e >= ce) continue;
-        const int32_t o = meta[it].x, k = meta[it].y;
+        const int32_t grp = meta[it].y;        // group length at a head, 0 for a member, -1 padding
+        if (grp < 0) continue;
+        const int32_t k = meta[it].x;
+        double2 Gi = G[it];
         bool in = true;
         if (MASKED) {
-          const int32_t l = meta[it].w >> 1;
+          const int32_t l = meta[it].z >> 1;
           in = (l != outage) && (a.status == nullptr || a.status[st_base + l] != 0);
-          if (!in) G[it] = make_double2(0.0, 0.0);
+          if (!in) Gi = make_double2(0.0, 0.0);
         }
-        const double2 pk = rec[2 * k], po = rec[2 * o];
+        const double2 pk = rec[2 * k];
         const double vk = rec[2 * k + 1].x;
-        const EndTerms tm = end_terms(G[it], po, pk);
+        const EndTerms tm = end_terms(Gi, po, pk);
         const double ea = __dmul_rn(vk, tm.xh), eb = __dmul_rn(vk, tm.yh);
-        s_a[s] = ea;
-        s_b[s] = eb;
+        acc_a = __dadd_rn(acc_a, ea);
+        acc_b = __dadd_rn(acc_b, eb);
         if (MASKED) {
-          const double2 ac = __ldg(a.ac + e);
-          s_ma[s] = in ? ac.x : 0.0;
-          s_mc[s] = in ? ac.y : 0.0;
+          acc_ma = __dadd_rn(acc_ma, in ? AC[it].x : 0.0);
+          acc_mc = __dadd_rn(acc_mc, in ? AC[it].y : 0.0);
         }
-        if (WJ && meta[it].z == 1) {                 // the common case: no parallel branch
-          const double vo = rec[2 * o + 1].x;
-          const int4 p = pos[it];
-          if (p.x >= 0) vi[p.x] = __dmul_rn(-vo, eb);
-          if (p.y >= 0) vi[p.y] = __dmul_rn(-vo, tm.xh);
-          if (p.z >= 0) vi[p.z] = __dmul_rn(vo, ea);
-          if (p.w >= 0) vi[p.w] = __dmul_rn(-vo, tm.yh);
-        }
-      }
-      if (WJ) {
-        // heads of groups of parallel branches (rare), after the common path
-#pragma unroll
-        for (int it = 0; it < ITEMS; ++it) {
-          const int32_t e = cs + it * 32 + lane;
-          if (e < ce && meta[it].z > 1)
-            write_group(v, a, e, meta[it].z, meta[it].x, meta[it].y, pos[it], rec, vi, MASKED, outage, st_base);
-        }
-      }
-      __syncwarp();
-      if (owner) {
-        const int32_t lo = max(op0, cs), hi = min(op1, ce);
-        for (int32_t e = lo; e < hi; ++e) {
-          acc_a = __dadd_rn(acc_a, s_a[e - cs]);
-          acc_b = __dadd_rn(acc_b, s_b[e - cs]);
-          if (MASKED) {
-            acc_ma = __dadd_rn(acc_ma, s_ma[e - cs]);
-            acc_mc = __dadd_rn(acc_mc, s_mc[e - cs]);
+        if (WJ) {
+          const double tp = __dmul_rn(-vo, eb), tv = __dmul_rn(-vo, tm.xh);
+          const double tq = __dmul_rn(vo, ea), tw = __dmul_rn(-vo, tm.yh);
+          if (grp > 0) {
+            gpt = tp; gqt = tq; gpv = tv; gqv = tw;
+            gpos = pos[it];
+            grem = grp - 1;
+          } else {                               // a further branch of the group (rare)
+            gpt = __dadd_rn(gpt, tp); gqt = __dadd_rn(gqt, tq);
+            gpv = __dadd_rn(gpv, tv); gqv = __dadd_rn(gqv, tw);
+            --grem;
+          }
+          if (grem == 0) {
+            if (gpos.x >= 0) vi[gpos.x] = gpt;
+            if (gpos.y >= 0) vi[gpos.y] = gpv;
+            if (gpos.z >= 0) vi[gpos.z] = gqt;
+            if (gpos.w >= 0) vi[gpos.w] = gqv;
           }
         }
       }
-      __syncwarp();
     }
-    if (e0 == e1) cudaGridDependencySynchronize();   // a round of isolated buses only
-
-    // ---- per-bus results: F rows and the diagonal of J ----
+    if (D == 0) {                                // a round of isolated buses only
+      cudaGridDependencySynchronize();
+      if (owner) vo = rec[2 * o + 1].x;
+    }
     if (owner) {
-      const int32_t o = ob;
-      const int64_t lb = o - gb0;
-      const double vo = rec[2 * o + 1].x;
       double ah, ch;
       if (MASKED) {
         const double2 sh = __ldg(v.bus_sh + o);
@@ -293,45 +435,7 @@ __global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArg
         ah = hat.x;
         ch = hat.y;
       }
-      const int32_t rp = bm.x, rq = bm.y, bp = bm.z, bq = bm.w;
-      const int32_t gi = bm2.w;
-      const bool is_slack = (v.formulation == PF_EXTENDED) && (lb == v.grid_slack[g]);
-      if (WF) {
-        double *__restrict__ Fi = a.F + v.inst_f_off[inst];
-        const double pin = a.p_inj ? a.p_inj[v.inst_bus_off[inst] + lb] : inj.x;
-        const double qin = a.q_inj ? a.q_inj[v.inst_bus_off[inst] + lb] : inj.y;
-        double fp = __fma_rn(vo, __fma_rn(vo, ah, -acc_a), -pin);
-        double fq = __fma_rn(-vo, __fma_rn(vo, ch, acc_b), -qin);     // = -(vo (vo ch + sum b) + qin)
-        if (is_slack) {
-          fp = __dsub_rn(fp, xi[2 * nb + v.grid_ngen[g]]);
-          Fi[v.grid_row_gth[g]] = __dsub_rn(xi[lb], v.grid_theta_set[g]);
-        }
-        if (gi >= 0) {
-          fq = __dsub_rn(fq, xi[2 * nb + gi]);
-          Fi[2 * nb + gi] = __dsub_rn(vo, v.gen_vset[v.grid_gen_off[g] + gi]);
-        }
-        if (rp >= 0) Fi[rp] = fp;
-        if (rq >= 0) Fi[rq] = fq;
-      }
-      if (WJ) {
-        const double two_vo = __dadd_rn(vo, vo);
-        if (bp >= 0) {
-          if (bm2.x >= 0) vi[bp + bm2.x] = __dmul_rn(vo, acc_b);
-          if (bm2.y >= 0) vi[bp + bm2.y] = __fma_rn(two_vo, ah, -acc_a);
-        }
-        if (bq >= 0) {
-          if (bm2.x >= 0) vi[bq + bm2.x] = __dmul_rn(-vo, acc_a);
-          if (bm2.y >= 0) vi[bq + bm2.y] = __fma_rn(-two_vo, ch, -acc_b);
-        }
-        if (is_slack) {
-          vi[bp + bm2.z] = -1.0;                // d g_p / d P_s
-          vi[v.grid_pos_gth[g]] = 1.0;         // d g_theta / d theta_s
-        }
-        if (gi >= 0) {
-          vi[bq + bm2.z] = -1.0;                // d g_q / d Q_g
-          vi[v.gen_pos[v.grid_gen_off[g] + gi]] = 1.0;  // d g_V / d V
-        }
-      }
+      finalize_bus<WF, WJ>(v, a, inst, g, o, gb0, nb, xi, vi, vo, acc_a, acc_b, ah, ch, bm, bm2, inj);
     }
   }
 }
@@ -340,11 +444,12 @@ constexpr int kWarpsPerBlock = 1;   // one warp per CTA: rounds spread evenly ov
 
 template <int ITEMS, bool WF, bool WJ, bool MASKED>
 int launch_fused_t(const View &v, int num_sms, const pf_tuning &t, const EvalArgs &a, cudaStream_t s) {
+  // shared memory: the chunk sums of a large-bus round
   const size_t smem = (size_t)kWarpsPerBlock * 32 * ITEMS * sizeof(double) * (MASKED ? 4 : 2);
   auto kern = k_fused<ITEMS, WF, WJ, MASKED>;
   if (smem > 46 * 1024)
     PF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int64_t grid = (v.n_units + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  int64_t grid = (v.n_round_units + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (t.ctas_per_sm > 0) grid = std::min<int64_t>(grid, (int64_t)t.ctas_per_sm * num_sms);
   if (grid < 1) grid = 1;
   cudaLaunchConfig_t cfg = {};
@@ -385,6 +490,15 @@ int launch_fused(const View &v, int num_sms, const pf_tuning &t, const EvalArgs 
   }
 }
 
+void built_coefficients(const View &v, EvalArgs &a) {
+  a.gb = v.inc_gb;
+  a.ac = v.inc_ac;
+  a.hat = v.bus_hat;
+  a.sgb = v.slot_gb;
+  a.sac = v.slot_ac;
+  a.rhat = v.rbus_hat;
+}
+
 int launch_phasor(const View &v, int num_sms, const double *x, cudaStream_t s) {
   const int tb = 256;
   int64_t blocks = (v.n_bus_inst + tb - 1) / tb;
@@ -418,19 +532,22 @@ int launch_eval_stages(Ctx &c, int stages, const double *x, const pf_overrides *
   a.x = x;
   a.F = F;
   a.vals = vals;
-  a.gb = c.v.inc_gb;
-  a.ac = c.v.inc_ac;
-  a.hat = c.v.bus_hat;
+  built_coefficients(c.v, a);
   if (ov) {
     a.p_inj = ov->p_inj;
     a.q_inj = ov->q_inj;
     a.status = ov->status;
     if (ov->br_r || ov->br_x || ov->br_b || ov->br_tap) {
-      if (stages & 2)
+      if (stages & 2) {
         PF_TRY(compute_coefficients(c, ov->br_r, ov->br_x, ov->br_b, ov->br_tap, c.ov_gb, c.ov_ac, c.ov_hat, s));
+        PF_TRY(permute_overrides(c, s));
+      }
       a.gb = c.ov_gb;
       a.ac = c.ov_ac;
       a.hat = c.ov_hat;
+      a.sgb = c.ov_slot_gb;
+      a.sac = c.ov_slot_ac;
+      a.rhat = c.ov_rbus_hat;
     }
   }
   const bool masked = c.any_outage || a.status != nullptr;
@@ -451,9 +568,7 @@ int launch_eval_scratch(Ctx &c, const double *x, double *F, double *vals, double
   a.x = x;
   a.F = F;
   a.vals = vals;
-  a.gb = c.v.inc_gb;
-  a.ac = c.v.inc_ac;
-  a.hat = c.v.bus_hat;
+  built_coefficients(c.v, a);
   PF_TRY(launch_phasor(v, c.num_sms, x, s));
   return launch_fused(v, c.num_sms, c.tuning, a, c.any_outage, s);
 }

@@ -25,6 +25,10 @@ constexpr int kRoundBuses = 32;
 constexpr int kMaxTileInc = 128;
 constexpr int kMinTileInc = 32;
 constexpr int kMaxGroup = 32;      // parallel branches between one pair of buses
+// The fused kernel evaluates rounds of 32 buses of equal (or adjacent)
+// degree, one bus per lane; a bus with more than kLaneMaxDegree ends forms a
+// round of its own, evaluated by the whole warp.
+constexpr int kLaneMaxDegree = 32;
 constexpr int kSinCosTable = 256;  // table of (cos, sin)(i pi / 128)
 
 // Thread-local error message behind pf_last_error().
@@ -54,6 +58,7 @@ struct View {
   int formulation;
   int n_grids, n_inst;
   int64_t n_bus, n_branch, n_inc, n_units, n_bus_inst;
+  int64_t n_round_units;    // sum over instances of the rounds of its grid
 
   // per bus
   const int32_t *inc_ptr;   // [n_bus+1] first incidence of each bus
@@ -102,6 +107,18 @@ struct View {
   const int4 *tile_desc;                      // {first bus, end bus, first end, end end}
   const int64_t *grid_tile_off;               // [n_grids+1]
 
+  // rounds of the fused kernel (per grid, buses sorted by degree)
+  const int64_t *grid_round_off;              // [n_grids+1]
+  const int64_t *inst_round_off;              // [n_inst+1] rounds of earlier instances
+  const int4 *round_desc;                     // {first slot, items per lane, buses, flags (1 = one large bus)}
+  const int32_t *rbus;                        // [32 per round] global bus id, -1 padding
+  const int4 *rbus_meta, *rbus_meta2;         // bus records in round order
+  const double2 *rbus_hat, *rbus_inj;
+  const int4 *slot_meta;                      // end j of lane l at slot first + 32 j + l:
+                                              //   {other bus, group length at a head / 0 / -1 padding, code, end index}
+  const int4 *slot_pos;                       // the end's four CSR positions
+  const double2 *slot_gb, *slot_ac;           // the end's coefficients
+
   // per instance
   const int32_t *inst_grid, *inst_outage;     // outage: global branch id or -1
   const int64_t *inst_x_off, *inst_f_off, *inst_v_off, *inst_bus_off, *inst_br_off;
@@ -138,8 +155,12 @@ struct Ctx {
   int64_t *grid_tile_off_d = nullptr;
   int64_t *inst_unit_off_d = nullptr;
 
-  // override scratch (coefficients recomputed from per-call parameters)
+  // override scratch (coefficients recomputed from per-call parameters), in
+  // incidence order and permuted to slot / round order
   double2 *ov_gb = nullptr, *ov_ac = nullptr, *ov_hat = nullptr;
+  double2 *ov_slot_gb = nullptr, *ov_slot_ac = nullptr, *ov_rbus_hat = nullptr;
+  int64_t n_slots = 0, n_rounds = 0;
+  std::vector<int64_t> grid_round_off, round_off;
 
   // host-call staging, allocated on first use
   double *stage_x = nullptr, *stage_f = nullptr, *stage_v = nullptr;
@@ -174,6 +195,8 @@ int upload(Ctx &c, T **p, const std::vector<T> &h, cudaStream_t s) {
 int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance *inst,
                   int n_inst, int formulation, cudaStream_t s);
 int build_tiles(Ctx &c, int tile_inc, cudaStream_t s);
+// Copies per-call coefficients (incidence / bus order) into slot / round order.
+int permute_overrides(Ctx &c, cudaStream_t s);
 // Per-end coefficients (G, B, A, C) and per-bus sums (A^, C^) from the branch
 // parameters; any of r, x, b, tap may be overridden by device arrays.
 int compute_coefficients(Ctx &c, const double *r, const double *x, const double *b,
