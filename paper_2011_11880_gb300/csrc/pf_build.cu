@@ -404,17 +404,62 @@ __global__ void k_coeff(View v, const double *r_ov, const double *x_ov, const do
 // A^ = (sum of A_e over the bus's ends, in list order) + shunt g; same for C^.
 // The evaluation's masked path accumulates in the same order, so a mask of
 // all ones gives the same bits.
+// A^ and C^ of every bus: the sum of its ends' A, C plus the shunt, in the
+// order the evaluation kernels use when they sum under a mask, so that a
+// masked evaluation with every branch in service gives the same bits:
+// groups of parallel branches merged in incidence order and summed in list
+// order for a bus with up to 32 groups; for a larger bus, 32 lane-strided
+// partial sums over its ends combined by the butterfly of k_fused_large.
 __global__ void k_hat(View v, const double2 *ac, double2 *hat) {
   const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= v.n_bus) return;
+  const int32_t e0 = v.inc_ptr[o], e1 = v.inc_ptr[o + 1];
   double sa = 0.0, sc = 0.0;
-  for (int32_t e = v.inc_ptr[o]; e < v.inc_ptr[o + 1]; ++e) {
-    const double2 t = ac[e];
-    sa = __dadd_rn(sa, t.x);
-    sc = __dadd_rn(sc, t.y);
+  if (v.bus_npair[o] <= kLaneMaxDegree) {
+    for (int32_t e = e0; e < e1;) {
+      const int32_t len = v.inc_grp[e];
+      double2 t = ac[e];
+      for (int32_t i = 1; i < len; ++i)
+        t = make_double2(__dadd_rn(t.x, ac[e + i].x), __dadd_rn(t.y, ac[e + i].y));
+      sa = __dadd_rn(sa, t.x);
+      sc = __dadd_rn(sc, t.y);
+      e += len;
+    }
+  } else {
+    double pa[32], pc[32];
+    for (int l = 0; l < 32; ++l) {
+      pa[l] = 0.0;
+      pc[l] = 0.0;
+      for (int32_t e = e0 + l; e < e1; e += 32) {
+        pa[l] = __dadd_rn(pa[l], ac[e].x);
+        pc[l] = __dadd_rn(pc[l], ac[e].y);
+      }
+    }
+    for (int m = 16; m >= 1; m >>= 1) {
+      double qa[32], qc[32];
+      for (int l = 0; l < 32; ++l) {
+        qa[l] = __dadd_rn(pa[l], pa[l ^ m]);
+        qc[l] = __dadd_rn(pc[l], pc[l ^ m]);
+      }
+      for (int l = 0; l < 32; ++l) {
+        pa[l] = qa[l];
+        pc[l] = qc[l];
+      }
+    }
+    sa = pa[0];
+    sc = pc[0];
   }
   const double2 sh = v.bus_sh[o];
   hat[o] = make_double2(__dadd_rn(sa, sh.x), __dadd_rn(sc, sh.y));
+}
+
+// per bus: the number of groups of parallel branches (distinct neighbours)
+__global__ void k_npair(View v, int32_t *npair) {
+  const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= v.n_bus) return;
+  int32_t n = 0;
+  for (int32_t e = v.inc_ptr[o]; e < v.inc_ptr[o + 1]; ++e) n += v.inc_grp[e] > 0;
+  npair[o] = n;
 }
 
 __global__ void k_pack_bus(View v, const int32_t *base_p, const int32_t *base_q, const int2 *diag,
@@ -555,7 +600,7 @@ __global__ void k_tiles(View v, int cap, const int64_t *tile_off, int32_t *count
 __global__ void k_round_keys(View v, uint64_t *keys, uint32_t *vals) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= v.n_bus) return;
-  const int32_t d = v.inc_ptr[b + 1] - v.inc_ptr[b];
+  const int32_t d = v.bus_npair[b];
   const uint64_t cls = d > kLaneMaxDegree ? kLaneMaxDegree + 1 : d;
   keys[b] = ((uint64_t)v.bus_grid[b] << 37) | (cls << 31) | (uint64_t)b;
   vals[b] = (uint32_t)b;
@@ -564,7 +609,7 @@ __global__ void k_round_keys(View v, uint64_t *keys, uint32_t *vals) {
 __global__ void k_count_large(View v, int32_t *n_large) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= v.n_bus) return;
-  if (v.inc_ptr[b + 1] - v.inc_ptr[b] > kLaneMaxDegree) atomicAdd(n_large + v.bus_grid[b], 1);
+  if (v.bus_npair[b] > kLaneMaxDegree) atomicAdd(n_large + v.bus_grid[b], 1);
 }
 
 // one thread per round: its buses and items per lane
@@ -584,7 +629,7 @@ __global__ void k_round_fill(View v, const uint32_t *sorted, const int64_t *grid
       int32_t b = -1;
       if (i < n_norm) {
         b = (int32_t)sorted[gb0 + i];
-        dmax = max(dmax, v.inc_ptr[b + 1] - v.inc_ptr[b]);
+        dmax = max(dmax, v.bus_npair[b]);
         ++nb;
       }
       rbus[32 * r + l] = b;
@@ -594,7 +639,7 @@ __global__ void k_round_fill(View v, const uint32_t *sorted, const int64_t *grid
   } else {
     const int32_t b = (int32_t)sorted[gb0 + n_norm + (rl - n_norm_rounds)];
     for (int l = 0; l < 32; ++l) rbus[32 * r + l] = l == 0 ? b : -1;
-    desc[r] = make_int4(0, v.inc_ptr[b + 1] - v.inc_ptr[b], 1, 1);
+    desc[r] = make_int4(0, v.bus_npair[b], 1, 1);
     slots[r] = 0;
   }
 }
@@ -606,36 +651,33 @@ __global__ void k_round_base(const int64_t *S, int64_t n_rounds, int4 *desc, int
   desc[r].x = (int32_t)S[r];
 }
 
-// one thread per slot: end j of lane l of its round (or padding)
-__global__ void k_slot_fill(View v, const int64_t *S, int64_t n_rounds, int64_t n_slots, const int4 *desc,
-                            const int32_t *rbus, int4 *smeta, int4 *spos, double2 *sgb, double2 *sac) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n_slots) return;
-  const int64_t r = [&] {
-    int64_t lo = 0, hi = n_rounds - 1;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi + 1) >> 1;
-      if (S[mid] <= q) lo = mid; else hi = mid - 1;
+// one thread per (round, lane): the slots of the lane's bus, one per group of
+// parallel branches (pair of buses) in incidence order, then padding
+__global__ void k_slot_fill(View v, int64_t n_rounds, const int4 *desc, const int32_t *rbus, int4 *smeta,
+                            int4 *spos) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 32 * n_rounds) return;
+  const int64_t r = t >> 5;
+  const int l = (int)(t & 31);
+  const int4 d = desc[r];
+  if (d.w) return;                               // a large bus: no slots
+  const int32_t b = rbus[t];
+  int j = 0;
+  if (b >= 0) {
+    for (int32_t e = v.inc_ptr[b]; e < v.inc_ptr[b + 1]; ++e) {
+      const int32_t len = v.inc_grp[e];
+      if (len == 0) continue;
+      const int64_t q = (int64_t)d.x + 32 * j + l;
+      smeta[q] = make_int4(v.inc_other[e], len, v.inc_code[e], e);
+      spos[q] = v.inc_pos[e];
+      ++j;
     }
-    return lo;
-  }();
-  const int64_t rel = q - S[r];
-  const int j = (int)(rel / 32), l = (int)(rel % 32);
-  const int32_t b = rbus[32 * r + l];
-  const int32_t deg = b >= 0 ? v.inc_ptr[b + 1] - v.inc_ptr[b] : 0;
-  if (b >= 0 && j < deg) {
-    const int32_t e = v.inc_ptr[b] + j;
-    smeta[q] = make_int4(v.inc_other[e], v.inc_grp[e], v.inc_code[e], e);
-    spos[q] = v.inc_pos[e];
-    sgb[q] = v.inc_gb[e];
-    sac[q] = v.inc_ac[e];
-  } else {
+  }
+  for (; j < d.y; ++j) {
+    const int64_t q = (int64_t)d.x + 32 * j + l;
     smeta[q] = make_int4(0, -1, 0, 0);
     spos[q] = make_int4(-1, -1, -1, -1);
-    sgb[q] = make_double2(0.0, 0.0);
-    sac[q] = make_double2(0.0, 0.0);
   }
-  (void)desc;
 }
 
 // bus records in round order (and, for per-call overrides, the coefficients)
@@ -657,14 +699,50 @@ __global__ void k_rbus_fill(View v, int64_t n, const int32_t *rbus, const double
   }
 }
 
+// per round of 32 buses of every instance: its instance, round and descriptor
+__global__ void k_unit_fill(View v, const int64_t *lane_off, int4 *unit) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= v.n_lane_units) return;
+  const int inst = find_segment(lane_off, v.n_inst, u);
+  const int g = v.inst_grid[inst];
+  const int64_t r = v.grid_round_off[g] + (u - lane_off[inst]);
+  const int4 d = v.round_desc[r];
+  unit[u] = make_int4(inst, (int32_t)r, d.x, d.y | (d.z << 8));
+}
+
+// per large bus of every instance: its instance and bus (the rounds after
+// the grid's rounds of 32 buses hold one large bus each)
+__global__ void k_large_fill(View v, const int64_t *large_off, const int64_t *lane_rounds, int2 *out) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= v.n_large_units) return;
+  const int inst = find_segment(large_off, v.n_inst, u);
+  const int g = v.inst_grid[inst];
+  const int64_t r = v.grid_round_off[g] + lane_rounds[g] + (u - large_off[inst]);
+  out[u] = make_int2(inst, v.rbus[32 * r]);
+}
+
+__global__ void k_rec_base(View v, int64_t *base) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= v.n_inst) return;
+  base[i] = v.inst_bus_off[i] - v.grid_bus_off[v.inst_grid[i]];
+}
+
+// per slot: the coefficients of its group of parallel branches, summed in
+// incidence order (the merged branch end of the pair of buses)
 __global__ void k_slot_coeff(int64_t n_slots, const int4 *smeta, const double2 *gb, const double2 *ac, double2 *sgb,
                              double2 *sac) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n_slots) return;
   const int4 m = smeta[q];
-  if (m.y >= 0) {
-    sgb[q] = gb[m.w];
-    sac[q] = ac[m.w];
+  if (m.y > 0) {
+    double2 g = gb[m.w], a = ac[m.w];
+    for (int32_t i = 1; i < m.y; ++i) {
+      const double2 gi = gb[m.w + i], ai = ac[m.w + i];
+      g = make_double2(__dadd_rn(g.x, gi.x), __dadd_rn(g.y, gi.y));
+      a = make_double2(__dadd_rn(a.x, ai.x), __dadd_rn(a.y, ai.y));
+    }
+    sgb[q] = g;
+    sac[q] = a;
   } else {
     sgb[q] = make_double2(0.0, 0.0);
     sac[q] = make_double2(0.0, 0.0);
@@ -843,7 +921,8 @@ int build_rounds(Ctx &c, cudaStream_t s) {
   PF_TRY(dev_alloc(c, &c.ov_slot_ac, NS));
   PF_TRY(dev_alloc(c, &c.ov_rbus_hat, 32 * R));
   if (NS > 0) {
-    k_slot_fill<<<nblk(NS), TB, 0, s>>>(v, S, R, NS, desc, rbus, smeta, spos, sgb, sac);
+    k_slot_fill<<<nblk(32 * R), TB, 0, s>>>(v, R, desc, rbus, smeta, spos);
+    k_slot_coeff<<<nblk(NS), TB, 0, s>>>(NS, smeta, v.inc_gb, v.inc_ac, sgb, sac);
     PF_CUDA_TRY(cudaGetLastError());
   }
   k_rbus_fill<<<nblk(32 * R), TB, 0, s>>>(v, 32 * R, rbus, v.bus_hat, m1, m2, rh, ri);
@@ -859,16 +938,34 @@ int build_rounds(Ctx &c, cudaStream_t s) {
   v.slot_pos = spos;
   v.slot_gb = sgb;
   v.slot_ac = sac;
+  if (c.n_rounds >= 0x7fffffffLL / 32) return fail(PF_ERR_UNSUPPORTED, "too many evaluation rounds");
+  // units of work: the rounds of 32 buses and the large buses of every instance
   const int I = v.n_inst;
-  c.round_off.assign(I + 1, 0);
+  std::vector<int64_t> lane_rounds(G), lane_off(I + 1, 0), large_off(I + 1, 0);
+  for (int g = 0; g < G; ++g) lane_rounds[g] = c.grid_round_off[g + 1] - c.grid_round_off[g] - h_large[g];
   for (int i = 0; i < I; ++i) {
     const int g = c.inst_grid[i];
-    c.round_off[i + 1] = c.round_off[i] + (c.grid_round_off[g + 1] - c.grid_round_off[g]);
+    lane_off[i + 1] = lane_off[i] + lane_rounds[g];
+    large_off[i + 1] = large_off[i] + h_large[g];
   }
-  int64_t *d_inst_round_off;
-  PF_TRY(upload(c, &d_inst_round_off, c.round_off, s));
-  v.inst_round_off = d_inst_round_off;
-  v.n_round_units = c.round_off[I];
+  v.n_lane_units = lane_off[I];
+  v.n_large_units = large_off[I];
+  int64_t *d_lane_off, *d_large_off, *d_lane_rounds, *rec_base;
+  int4 *unit;
+  int2 *large;
+  PF_TRY(upload(c, &d_lane_off, lane_off, s));
+  PF_TRY(upload(c, &d_large_off, large_off, s));
+  PF_TRY(upload(c, &d_lane_rounds, lane_rounds, s));
+  PF_TRY(dev_alloc(c, &unit, v.n_lane_units));
+  PF_TRY(dev_alloc(c, &large, v.n_large_units));
+  PF_TRY(dev_alloc(c, &rec_base, I));
+  if (v.n_lane_units > 0) k_unit_fill<<<nblk(v.n_lane_units), TB, 0, s>>>(v, d_lane_off, unit);
+  if (v.n_large_units > 0) k_large_fill<<<nblk(v.n_large_units), TB, 0, s>>>(v, d_large_off, d_lane_rounds, large);
+  k_rec_base<<<nblk(I), TB, 0, s>>>(v, rec_base);
+  PF_CUDA_TRY(cudaGetLastError());
+  v.unit_rec = unit;
+  v.large_rec = large;
+  v.inst_rec_base = rec_base;
   PF_CUDA_TRY(cudaStreamSynchronize(s));
   return PF_OK;
 }
@@ -1147,6 +1244,13 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
       PF_CUDA_TRY(cudaGetLastError());
     }
     v.inc_mirror = mirror; v.inc_grp = grp;
+    {
+      int32_t *npair;
+      PF_TRY(dev_alloc(c, &npair, N));
+      k_npair<<<nblk(N), TB, 0, s>>>(v, npair);
+      PF_CUDA_TRY(cudaGetLastError());
+      v.bus_npair = npair;
+    }
     int rc = PF_OK;
     std::vector<int32_t> hstats = to_host(stats, 4, s, &rc);
     if (rc) return rc;
@@ -1335,13 +1439,13 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
   PF_CUDA_TRY(cudaGetDevice(&dev));
   PF_CUDA_TRY(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev));
 
-  // (cos, sin) of i pi / 128 for the table-driven phasor routine, evaluated in
+  // (cos, sin) of i pi / 512 for the table-driven phasor routine, evaluated in
   // long double on the host and rounded once to double.
   {
     std::vector<double2> tab(kSinCosTable);
     const long double pi = 3.14159265358979323846264338327950288419716939937510L;
     for (int i = 0; i < kSinCosTable; ++i) {
-      const long double a = pi * (long double)i / 128.0L;
+      const long double a = pi * (long double)i / (long double)(kSinCosTable / 2);
       tab[i] = make_double2((double)cosl(a), (double)sinl(a));
     }
     double2 *d_tab;

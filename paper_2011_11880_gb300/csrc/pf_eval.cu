@@ -28,11 +28,13 @@
 // keeps the bus sums in registers, and finally writes the bus's F rows and
 // diagonal J entries.  Because the buses of a round have the same degree,
 // nearly every lane does useful FP64 work at every step.  A bus with more
-// than 32 ends is a round of its own, evaluated by the whole warp in chunks.
+// than 32 ends is evaluated by a whole warp in a second kernel.
 //
 // Determinism: every operation is an explicitly rounded intrinsic and every
-// sum runs in incidence-list order, so results are bit-identical run to run,
-// across code paths and for every tuning.
+// sum runs in a fixed order -- incidence-list order for a bus with up to 32
+// ends and for every group of parallel branches, lane-strided partial sums
+// combined by a fixed butterfly for a bus with more ends -- so results are
+// bit-identical run to run, across code paths and for every tuning.
 #include <algorithm>
 
 #include "pf_internal.cuh"
@@ -42,23 +44,26 @@ namespace pf {
 namespace {
 
 // ---------------------------------------------------------------------------
-// (cos t, sin t) by table-driven argument reduction (angle addition):
-//   t = k pi/128 + r, |r| <= pi/256, k = nearest integer to t 128/pi;
-//   r from a two-constant Cody-Waite split of pi/128 (the high part has 30
-//   significant bits, so k * STEP_HI is exact for |k| < 2^22);
-//   cos r, sin r by their Taylor series to degree 6 / 7 (truncation below
-//   1e-19 for |r| <= pi/256);
+// (cos t, sin t) by table-driven argument reduction (angle addition, after
+// P. T. P. Tang's table-driven elementary functions):
+//   t = k pi/512 + r, |r| <= pi/1024, k = nearest integer to t 512/pi;
+//   r from a two-constant Cody-Waite split of pi/512 (the high part has 27
+//   significant bits, so k * STEP_HI is exact for |k| < 2^26);
+//   cos r, sin r by their Taylor series to degree 4 / 5 (the first omitted
+//   terms, r^6/720 and r^7/5040, are below 1.2e-18 and 6e-22 for
+//   |r| <= pi/1024);
 //   cos t = C_k cos r - S_k sin r, sin t = S_k cos r + C_k sin r with the
-//   table (C_k, S_k) = (cos, sin)(k pi / 128) computed on the host in long
-//   double.  16 FP64 operations.  Arguments beyond |t| = 2^16 use sincos().
+//   table (C_k, S_k) = (cos, sin)(k pi / 512) computed on the host in long
+//   double.  14 FP64 operations.  Arguments beyond |t| = 2^16 use sincos().
 // ---------------------------------------------------------------------------
-constexpr double kInvStep = 0x1.45f306dc9c883p+5;     // 128 / pi
-constexpr double kStepHi = 0x1.921fb54000000p-6;      // pi / 128, high 30 bits
-constexpr double kStepLo = 0x1.10b4611a62633p-36;     // pi / 128 - kStepHi
+constexpr double kInvStep = 0x1.45f306dc9c883p+7;     // 512 / pi
+constexpr double kStepHi = 0x1.921fb54000000p-8;      // pi / 512, high 27 bits
+constexpr double kStepLo = 0x1.10b4611a62633p-38;     // pi / 512 - kStepHi
 constexpr double kRoundMagic = 6755399441055744.0;    // 1.5 * 2^52
 
 __device__ __forceinline__ double2 table_sincos(double t, const double2 *__restrict__ tab) {
-  if (!(fabs(t) < 65536.0)) {
+  // |t| >= 2^16 or NaN, tested on the high word (integer pipe)
+  if ((__double2hiint(t) & 0x7fffffff) >= 0x40f00000) {
     double s, c;
     sincos(t, &s, &c);
     return make_double2(c, s);
@@ -69,14 +74,11 @@ __device__ __forceinline__ double2 table_sincos(double t, const double2 *__restr
   double r = __fma_rn(-kd, kStepHi, t);
   r = __fma_rn(-kd, kStepLo, r);
   const double z = __dmul_rn(r, r);
-  // sin r = r + r z (-1/6 + z (1/120 - z / 5040))
-  double ps = __fma_rn(z, -1.0 / 5040.0, 1.0 / 120.0);
-  ps = __fma_rn(z, ps, -1.0 / 6.0);
+  // sin r = r + r z (-1/6 + z / 120)
+  const double ps = __fma_rn(z, 1.0 / 120.0, -1.0 / 6.0);
   const double sr = __fma_rn(__dmul_rn(r, z), ps, r);
-  // cos r = 1 + z (-1/2 + z (1/24 - z / 720))
-  double pc = __fma_rn(z, -1.0 / 720.0, 1.0 / 24.0);
-  pc = __fma_rn(z, pc, -0.5);
-  const double cr = __fma_rn(z, pc, 1.0);
+  // cos r = 1 + z (-1/2 + z / 24)
+  const double cr = __fma_rn(z, __fma_rn(z, 1.0 / 24.0, -0.5), 1.0);
   const double2 T = __ldg(tab + (ki & (kSinCosTable - 1)));
   return make_double2(__fma_rn(T.x, cr, -__dmul_rn(T.y, sr)), __fma_rn(T.y, cr, __dmul_rn(T.x, sr)));
 }
@@ -135,33 +137,60 @@ __device__ __forceinline__ bool end_in_service(const View &v, int32_t e, int32_t
   return (l != outage) && (status == nullptr || status[st_base + l] != 0);
 }
 
+__device__ __forceinline__ int64_t gb0_of(const View &v, int g) { return __ldg(v.grid_bus_off + g); }
+
 // Off-diagonal entries of a group of `len` parallel branch ends e, e+1, ...
-// (same own bus o, same other bus k, so the same four CSR positions), summed
-// in list order.  Rare; called after the common path.
+// (same own bus o, same other bus k, so the same four CSR positions): with
+// X = sum xh and Y = sum yh over the group in list order,
+//   dP/dt_k = -V_o (V_k Y),  dP/dV_k = -V_o X,  dQ/dt_k = V_o (V_k X),  dQ/dV_k = -V_o Y.
+// For a group of one branch these are the single end's terms.
 __device__ __forceinline__ void write_group(const View &v, const EvalArgs &a, int32_t e, int32_t len, int32_t o,
                                             int32_t k, int4 p, const double2 *rec, double *vi, bool masked,
                                             int32_t outage, int64_t st_base) {
   const double2 po = rec[2 * o], pk = rec[2 * k];
   const double vo = rec[2 * o + 1].x, vk = rec[2 * k + 1].x;
-  double pt = 0.0, qt = 0.0, pv = 0.0, qv = 0.0;
+  double X = 0.0, Y = 0.0;
   for (int32_t q = 0; q < len; ++q) {
     double2 G = __ldg(a.gb + e + q);
     if (masked && !end_in_service(v, e + q, outage, a.status, st_base)) G = make_double2(0.0, 0.0);
     const EndTerms tq = end_terms(G, po, pk);
-    const double tp = __dmul_rn(-vo, __dmul_rn(vk, tq.yh));
-    const double tqq = __dmul_rn(vo, __dmul_rn(vk, tq.xh));
-    const double tv = __dmul_rn(-vo, tq.xh);
-    const double tw = __dmul_rn(-vo, tq.yh);
     if (q == 0) {
-      pt = tp; qt = tqq; pv = tv; qv = tw;
+      X = tq.xh; Y = tq.yh;
     } else {
-      pt = __dadd_rn(pt, tp); qt = __dadd_rn(qt, tqq); pv = __dadd_rn(pv, tv); qv = __dadd_rn(qv, tw);
+      X = __dadd_rn(X, tq.xh); Y = __dadd_rn(Y, tq.yh);
     }
   }
-  if (p.x >= 0) vi[p.x] = pt;
-  if (p.y >= 0) vi[p.y] = pv;
-  if (p.z >= 0) vi[p.z] = qt;
-  if (p.w >= 0) vi[p.w] = qv;
+  const double A = __dmul_rn(vk, X), B = __dmul_rn(vk, Y);
+  if (p.x >= 0) vi[p.x] = __dmul_rn(-vo, B);
+  if (p.y >= 0) vi[p.y] = __dmul_rn(-vo, X);
+  if (p.z >= 0) vi[p.z] = __dmul_rn(vo, A);
+  if (p.w >= 0) vi[p.w] = __dmul_rn(-vo, Y);
+}
+
+// Under an outage mask: the coefficients of the branches in service of the
+// group of `len` parallel branch ends e, e+1, ..., summed in incidence order
+// (zero when none is in service).
+struct GroupCoeff {
+  double2 gb, ac;
+};
+
+__device__ __forceinline__ GroupCoeff masked_group(const View &v, const EvalArgs &a, int32_t e, int32_t len,
+                                                   int32_t outage, int64_t st_base) {
+  GroupCoeff r{make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+  bool first = true;
+  for (int32_t i = 0; i < len; ++i) {
+    if (!end_in_service(v, e + i, outage, a.status, st_base)) continue;
+    const double2 gi = __ldg(a.gb + e + i), ci = __ldg(a.ac + e + i);
+    if (first) {
+      r.gb = gi;
+      r.ac = ci;
+      first = false;
+    } else {
+      r.gb = make_double2(__dadd_rn(r.gb.x, gi.x), __dadd_rn(r.gb.y, gi.y));
+      r.ac = make_double2(__dadd_rn(r.ac.x, ci.x), __dadd_rn(r.ac.y, ci.y));
+    }
+  }
+  return r;
 }
 
 // F rows, the extended formulation's extra rows and the diagonal of J for
@@ -213,129 +242,38 @@ __device__ __forceinline__ void finalize_bus(const View &v, const EvalArgs &a, i
   }
 }
 
-// One bus with more than 32 ends, evaluated by the whole warp in chunks of
-// R = 32 ITEMS ends (incidence order): lanes compute the ends and write the
-// off-diagonal entries, lane 0 sums the chunk in list order.
-template <int ITEMS, bool WF, bool WJ, bool MASKED>
-__device__ __noinline__ void large_bus_round(const View &v, const EvalArgs &a, int inst, int g, int32_t o,
-                                             const double2 *__restrict__ rec, double *__restrict__ vi,
-                                             const double *__restrict__ xi, int32_t outage, int64_t st_base) {
-  constexpr int R = 32 * ITEMS;
-  extern __shared__ double sm[];
-  double *__restrict__ s_a = sm;
-  double *__restrict__ s_b = s_a + R;
-  double *__restrict__ s_ma = s_b + R;   // masked: A of each end, 0 when out
-  double *__restrict__ s_mc = s_ma + R;
-  const int lane = threadIdx.x & 31;
-  const int32_t e0 = __ldg(v.inc_ptr + o), e1 = __ldg(v.inc_ptr + o + 1);
-  double acc_a = 0.0, acc_b = 0.0, acc_ma = 0.0, acc_mc = 0.0;
-  cudaGridDependencySynchronize();
-  const double2 po = rec[2 * o];
-  const double vo = rec[2 * o + 1].x;
-  for (int32_t cs = e0; cs < e1; cs += R) {
-    const int32_t ce = min(cs + R, e1);
-#pragma unroll
-    for (int it = 0; it < ITEMS; ++it) {
-      const int s = it * 32 + lane;
-      const int32_t e = cs + s;
-      if (e >= ce) continue;
-      const int4 meta = __ldg(v.inc_meta + e);
-      double2 G = __ldg(a.gb + e);
-      bool in = true;
-      if (MASKED) {
-        const int32_t l = meta.w >> 1;
-        in = (l != outage) && (a.status == nullptr || a.status[st_base + l] != 0);
-        if (!in) G = make_double2(0.0, 0.0);
-      }
-      const int32_t k = meta.y;
-      const double2 pk = rec[2 * k];
-      const double vk = rec[2 * k + 1].x;
-      const EndTerms tm = end_terms(G, po, pk);
-      const double ea = __dmul_rn(vk, tm.xh), eb = __dmul_rn(vk, tm.yh);
-      s_a[s] = ea;
-      s_b[s] = eb;
-      if (MASKED) {
-        const double2 ac = __ldg(a.ac + e);
-        s_ma[s] = in ? ac.x : 0.0;
-        s_mc[s] = in ? ac.y : 0.0;
-      }
-      if (WJ) {
-        const int4 p = __ldg(v.inc_pos + e);
-        if (meta.z == 1) {
-          if (p.x >= 0) vi[p.x] = __dmul_rn(-vo, eb);
-          if (p.y >= 0) vi[p.y] = __dmul_rn(-vo, tm.xh);
-          if (p.z >= 0) vi[p.z] = __dmul_rn(vo, ea);
-          if (p.w >= 0) vi[p.w] = __dmul_rn(-vo, tm.yh);
-        } else if (meta.z > 1) {
-          write_group(v, a, e, meta.z, o, k, p, rec, vi, MASKED, outage, st_base);
-        }
-      }
-    }
-    __syncwarp();
-    if (lane == 0) {
-      for (int32_t e = cs; e < ce; ++e) {
-        acc_a = __dadd_rn(acc_a, s_a[e - cs]);
-        acc_b = __dadd_rn(acc_b, s_b[e - cs]);
-        if (MASKED) {
-          acc_ma = __dadd_rn(acc_ma, s_ma[e - cs]);
-          acc_mc = __dadd_rn(acc_mc, s_mc[e - cs]);
-        }
-      }
-    }
-    __syncwarp();
-  }
-  if (lane == 0) {
-    double ah, ch;
-    if (MASKED) {
-      const double2 sh = __ldg(v.bus_sh + o);
-      ah = __dadd_rn(acc_ma, sh.x);
-      ch = __dadd_rn(acc_mc, sh.y);
-    } else {
-      const double2 hat = __ldg(a.hat + o);
-      ah = hat.x;
-      ch = hat.y;
-    }
-    const double2 inj = WF ? __ldg(v.bus_inj + o) : make_double2(0.0, 0.0);
-    finalize_bus<WF, WJ>(v, a, inst, g, o, v.grid_bus_off[g], v.grid_nbus[g], xi, vi, vo, acc_a, acc_b, ah, ch,
-                         __ldg(v.bus_meta + o), __ldg(v.bus_meta2 + o), inj);
-  }
-}
-
 // One-warp CTAs that must fit on one SM (register budget of k_fused).
 #ifndef PF_FUSED_MIN_CTAS
 #define PF_FUSED_MIN_CTAS 16
 #endif
 
-// One warp per round.  A round holds up to 32 buses of equal (or adjacent)
-// degree, one per lane; lane l walks the ends of its bus in incidence order
-// (slot first + 32 j + l holds end j, so every fetch of the round's end data
-// is coalesced), keeps the bus sums in registers and writes the off-diagonal
-// entries of each end, summing a group of parallel branches in list order
-// before it writes the group's entries.  Ends are fetched ITEMS at a time.
+// One warp per round.  A round holds up to 32 buses with equal (or
+// adjacent) numbers of neighbours, one per lane; lane l walks its bus's
+// groups of parallel branches in incidence order (slot first + 32 j + l holds
+// group j, so every fetch of the round's data is coalesced), keeps the bus
+// sums in registers and writes the group's four off-diagonal entries.  A
+// group's coefficients are summed at build time, so a pair of buses joined by
+// several branches costs one merged branch end.  Under an outage mask a
+// group with more than one branch re-sums the coefficients of its branches in
+// service.  Slots are fetched ITEMS at a time.
 template <int ITEMS, bool WF, bool WJ, bool MASKED>
 __global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArgs a) {
   const int lane = threadIdx.x & 31;
-  for (int64_t u = blockIdx.x; u < v.n_round_units; u += gridDim.x) {
-    const int inst = v.n_inst == 1 ? 0 : find_segment(v.inst_round_off, v.n_inst, u);
-    const int g = v.inst_grid[inst];
-    const int64_t r = v.grid_round_off[g] + (u - v.inst_round_off[inst]);
-    const int4 rd = __ldg(v.round_desc + r);     // {first slot, items per lane, buses, large}
-    const int64_t gb0 = v.grid_bus_off[g];
-    const int32_t nb = v.grid_nbus[g];
-    const double *__restrict__ xi = a.x + v.inst_x_off[inst];
+  for (int64_t u = blockIdx.x; u < v.n_lane_units; u += gridDim.x) {
+    const int4 ur = __ldg(v.unit_rec + u);        // {instance, round, first slot, D | buses << 8}
+    const int inst = ur.x;
+    const int64_t r = ur.y;
+    const int g = __ldg(v.inst_grid + inst);
+    const double *__restrict__ xi = a.x + __ldg(v.inst_x_off + inst);
     // (cos, sin) at rec[2 k], (V, 0) at rec[2 k + 1], by global bus id k
-    const double2 *__restrict__ rec = v.phasor + 2 * (v.inst_bus_off[inst] - gb0);
-    double *__restrict__ vi = WJ ? a.vals + v.inst_v_off[inst] : nullptr;
+    const double2 *__restrict__ rec = v.phasor + 2 * __ldg(v.inst_rec_base + inst);
+    double *__restrict__ vi = WJ ? a.vals + __ldg(v.inst_v_off + inst) : nullptr;
     const int32_t outage = MASKED ? v.inst_outage[inst] : -1;
     const int64_t st_base = MASKED ? v.inst_br_off[inst] - v.grid_br_off[g] : 0;
-    if (rd.w) {
-      large_bus_round<ITEMS, WF, WJ, MASKED>(v, a, inst, g, __ldg(v.rbus + 32 * r), rec, vi, xi, outage, st_base);
-      continue;
-    }
 
     // this lane's bus: records in round order, fetched before the wait
     const int64_t rb = 32 * r + lane;
-    const bool owner = lane < rd.z;
+    const bool owner = lane < (ur.w >> 8);
     int32_t o = 0;
     int4 bm = make_int4(-1, -1, -1, -1), bm2 = make_int4(-1, -1, 0, -1);
     double2 hat = make_double2(0.0, 0.0), inj = make_double2(0.0, 0.0);
@@ -347,14 +285,10 @@ __global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArg
       if (WF) inj = __ldg(v.rbus_inj + rb);
     }
     double acc_a = 0.0, acc_b = 0.0, acc_ma = 0.0, acc_mc = 0.0;
-    // running sums of a group of parallel branches, written at its last end
-    double gpt = 0.0, gqt = 0.0, gpv = 0.0, gqv = 0.0;
-    int4 gpos = make_int4(-1, -1, -1, -1);
-    int32_t grem = 0;
     double2 po = make_double2(0.0, 0.0);
     double vo = 0.0;
-    const int32_t D = rd.y;
-    const int64_t q0 = (int64_t)rd.x + lane;
+    const int32_t D = ur.w & 0xff;
+    const int64_t q0 = (int64_t)ur.z + lane;
 
     for (int32_t j0 = 0; j0 < D; j0 += ITEMS) {
       int4 meta[ITEMS], pos[ITEMS];
@@ -380,15 +314,22 @@ __global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArg
       }
 #pragma unroll
       for (int it = 0; it < ITEMS; ++it) {
-        const int32_t grp = meta[it].y;        // group length at a head, 0 for a member, -1 padding
-        if (grp < 0) continue;
+        const int32_t len = meta[it].y;          // branches in the group, -1 padding
+        if (len < 0) continue;
         const int32_t k = meta[it].x;
         double2 Gi = G[it];
-        bool in = true;
         if (MASKED) {
-          const int32_t l = meta[it].z >> 1;
-          in = (l != outage) && (a.status == nullptr || a.status[st_base + l] != 0);
-          if (!in) Gi = make_double2(0.0, 0.0);
+          if (len == 1) {
+            const int32_t l = meta[it].z >> 1;
+            if (l == outage || (a.status != nullptr && a.status[st_base + l] == 0)) {
+              Gi = make_double2(0.0, 0.0);
+              AC[it] = make_double2(0.0, 0.0);
+            }
+          } else {
+            const GroupCoeff mg = masked_group(v, a, meta[it].w, len, outage, st_base);
+            Gi = mg.gb;
+            AC[it] = mg.ac;
+          }
         }
         const double2 pk = rec[2 * k];
         const double vk = rec[2 * k + 1].x;
@@ -397,27 +338,15 @@ __global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArg
         acc_a = __dadd_rn(acc_a, ea);
         acc_b = __dadd_rn(acc_b, eb);
         if (MASKED) {
-          acc_ma = __dadd_rn(acc_ma, in ? AC[it].x : 0.0);
-          acc_mc = __dadd_rn(acc_mc, in ? AC[it].y : 0.0);
+          acc_ma = __dadd_rn(acc_ma, AC[it].x);
+          acc_mc = __dadd_rn(acc_mc, AC[it].y);
         }
         if (WJ) {
-          const double tp = __dmul_rn(-vo, eb), tv = __dmul_rn(-vo, tm.xh);
-          const double tq = __dmul_rn(vo, ea), tw = __dmul_rn(-vo, tm.yh);
-          if (grp > 0) {
-            gpt = tp; gqt = tq; gpv = tv; gqv = tw;
-            gpos = pos[it];
-            grem = grp - 1;
-          } else {                               // a further branch of the group (rare)
-            gpt = __dadd_rn(gpt, tp); gqt = __dadd_rn(gqt, tq);
-            gpv = __dadd_rn(gpv, tv); gqv = __dadd_rn(gqv, tw);
-            --grem;
-          }
-          if (grem == 0) {
-            if (gpos.x >= 0) vi[gpos.x] = gpt;
-            if (gpos.y >= 0) vi[gpos.y] = gpv;
-            if (gpos.z >= 0) vi[gpos.z] = gqt;
-            if (gpos.w >= 0) vi[gpos.w] = gqv;
-          }
+          const int4 p = pos[it];
+          if (p.x >= 0) vi[p.x] = __dmul_rn(-vo, eb);
+          if (p.y >= 0) vi[p.y] = __dmul_rn(-vo, tm.xh);
+          if (p.z >= 0) vi[p.z] = __dmul_rn(vo, ea);
+          if (p.w >= 0) vi[p.w] = __dmul_rn(-vo, tm.yh);
         }
       }
     }
@@ -435,34 +364,132 @@ __global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArg
         ah = hat.x;
         ch = hat.y;
       }
-      finalize_bus<WF, WJ>(v, a, inst, g, o, gb0, nb, xi, vi, vo, acc_a, acc_b, ah, ch, bm, bm2, inj);
+      finalize_bus<WF, WJ>(v, a, inst, g, o, gb0_of(v, g), v.grid_nbus[g], xi, vi, vo, acc_a, acc_b, ah, ch, bm,
+                           bm2, inj);
     }
   }
 }
 
-constexpr int kWarpsPerBlock = 1;   // one warp per CTA: rounds spread evenly over SMs
+// Buses with more than 32 ends, one warp each (launched after k_fused, so the
+// phasor records are complete).  Lane l takes ends l, l + 32, l + 64, ... of
+// the bus's list and sums them in that order; the 32 partial sums are then
+// combined by a fixed butterfly, so the result depends on neither the
+// tuning nor the schedule.  Off-diagonal entries as in k_fused.
+template <int ITEMS, bool WF, bool WJ, bool MASKED>
+__global__ void __launch_bounds__(32) k_fused_large(View v, EvalArgs a) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t u = blockIdx.x; u < v.n_large_units; u += gridDim.x) {
+    const int2 lr = __ldg(v.large_rec + u);       // {instance, bus}
+    const int inst = lr.x;
+    const int32_t o = lr.y;
+    const int g = __ldg(v.inst_grid + inst);
+    const double *__restrict__ xi = a.x + __ldg(v.inst_x_off + inst);
+    const double2 *__restrict__ rec = v.phasor + 2 * __ldg(v.inst_rec_base + inst);
+    double *__restrict__ vi = WJ ? a.vals + __ldg(v.inst_v_off + inst) : nullptr;
+    const int32_t outage = MASKED ? v.inst_outage[inst] : -1;
+    const int64_t st_base = MASKED ? v.inst_br_off[inst] - v.grid_br_off[g] : 0;
+    const int32_t e0 = __ldg(v.inc_ptr + o), e1 = __ldg(v.inc_ptr + o + 1);
+    const double2 po = rec[2 * o];
+    const double vo = rec[2 * o + 1].x;
+    double acc_a = 0.0, acc_b = 0.0, acc_ma = 0.0, acc_mc = 0.0;
+    for (int32_t cs = e0; cs < e1; cs += 32 * ITEMS) {
+      int4 meta[ITEMS];
+      double2 G[ITEMS];
+#pragma unroll
+      for (int it = 0; it < ITEMS; ++it) {
+        const int32_t e = cs + it * 32 + lane;
+        if (e < e1) {
+          meta[it] = __ldg(v.inc_meta + e);
+          G[it] = __ldg(a.gb + e);
+        }
+      }
+#pragma unroll
+      for (int it = 0; it < ITEMS; ++it) {
+        const int32_t e = cs + it * 32 + lane;
+        if (e >= e1) continue;
+        double2 Gi = G[it];
+        bool in = true;
+        if (MASKED) {
+          const int32_t l = meta[it].w >> 1;
+          in = (l != outage) && (a.status == nullptr || a.status[st_base + l] != 0);
+          if (!in) Gi = make_double2(0.0, 0.0);
+        }
+        const int32_t k = meta[it].y;
+        const double2 pk = rec[2 * k];
+        const double vk = rec[2 * k + 1].x;
+        const EndTerms tm = end_terms(Gi, po, pk);
+        const double ea = __dmul_rn(vk, tm.xh), eb = __dmul_rn(vk, tm.yh);
+        acc_a = __dadd_rn(acc_a, ea);
+        acc_b = __dadd_rn(acc_b, eb);
+        if (MASKED) {
+          const double2 ac = __ldg(a.ac + e);
+          acc_ma = __dadd_rn(acc_ma, in ? ac.x : 0.0);
+          acc_mc = __dadd_rn(acc_mc, in ? ac.y : 0.0);
+        }
+        if (WJ) {
+          const int4 p = __ldg(v.inc_pos + e);
+          if (meta[it].z == 1) {
+            if (p.x >= 0) vi[p.x] = __dmul_rn(-vo, eb);
+            if (p.y >= 0) vi[p.y] = __dmul_rn(-vo, tm.xh);
+            if (p.z >= 0) vi[p.z] = __dmul_rn(vo, ea);
+            if (p.w >= 0) vi[p.w] = __dmul_rn(-vo, tm.yh);
+          } else if (meta[it].z > 1) {
+            write_group(v, a, e, meta[it].z, o, k, p, rec, vi, MASKED, outage, st_base);
+          }
+        }
+      }
+    }
+    // fixed butterfly: every lane ends with the same sums
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+      acc_a = __dadd_rn(acc_a, __shfl_xor_sync(0xffffffffu, acc_a, m));
+      acc_b = __dadd_rn(acc_b, __shfl_xor_sync(0xffffffffu, acc_b, m));
+      if (MASKED) {
+        acc_ma = __dadd_rn(acc_ma, __shfl_xor_sync(0xffffffffu, acc_ma, m));
+        acc_mc = __dadd_rn(acc_mc, __shfl_xor_sync(0xffffffffu, acc_mc, m));
+      }
+    }
+    if (lane == 0) {
+      double ah, ch;
+      if (MASKED) {
+        const double2 sh = __ldg(v.bus_sh + o);
+        ah = __dadd_rn(acc_ma, sh.x);
+        ch = __dadd_rn(acc_mc, sh.y);
+      } else {
+        const double2 hat = __ldg(a.hat + o);
+        ah = hat.x;
+        ch = hat.y;
+      }
+      const double2 inj = WF ? __ldg(v.bus_inj + o) : make_double2(0.0, 0.0);
+      finalize_bus<WF, WJ>(v, a, inst, g, o, gb0_of(v, g), v.grid_nbus[g], xi, vi, vo, acc_a, acc_b, ah, ch,
+                           __ldg(v.bus_meta + o), __ldg(v.bus_meta2 + o), inj);
+    }
+  }
+}
 
 template <int ITEMS, bool WF, bool WJ, bool MASKED>
 int launch_fused_t(const View &v, int num_sms, const pf_tuning &t, const EvalArgs &a, cudaStream_t s) {
-  // shared memory: the chunk sums of a large-bus round
-  const size_t smem = (size_t)kWarpsPerBlock * 32 * ITEMS * sizeof(double) * (MASKED ? 4 : 2);
-  auto kern = k_fused<ITEMS, WF, WJ, MASKED>;
-  if (smem > 46 * 1024)
-    PF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int64_t grid = (v.n_round_units + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  if (t.ctas_per_sm > 0) grid = std::min<int64_t>(grid, (int64_t)t.ctas_per_sm * num_sms);
-  if (grid < 1) grid = 1;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3(32 * kWarpsPerBlock);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  PF_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, v, a));
+  if (v.n_lane_units > 0) {
+    int64_t grid = v.n_lane_units;
+    if (t.ctas_per_sm > 0) grid = std::min<int64_t>(grid, (int64_t)t.ctas_per_sm * num_sms);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(32);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    PF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_fused<ITEMS, WF, WJ, MASKED>, v, a));
+  }
+  if (v.n_large_units > 0) {
+    int64_t grid = v.n_large_units;
+    if (t.ctas_per_sm > 0) grid = std::min<int64_t>(grid, (int64_t)t.ctas_per_sm * num_sms);
+    k_fused_large<ITEMS, WF, WJ, MASKED><<<(unsigned)grid, 32, 0, s>>>(v, a);
+    PF_CUDA_TRY(cudaGetLastError());
+  }
   return PF_OK;
 }
 

@@ -29,7 +29,7 @@ constexpr int kMaxGroup = 32;      // parallel branches between one pair of buse
 // degree, one bus per lane; a bus with more than kLaneMaxDegree ends forms a
 // round of its own, evaluated by the whole warp.
 constexpr int kLaneMaxDegree = 32;
-constexpr int kSinCosTable = 256;  // table of (cos, sin)(i pi / 128)
+constexpr int kSinCosTable = 1024;  // table of (cos, sin)(i pi / 512)
 
 // Thread-local error message behind pf_last_error().
 void set_error(const std::string &msg);
@@ -58,7 +58,8 @@ struct View {
   int formulation;
   int n_grids, n_inst;
   int64_t n_bus, n_branch, n_inc, n_units, n_bus_inst;
-  int64_t n_round_units;    // sum over instances of the rounds of its grid
+  int64_t n_lane_units;     // sum over instances of the rounds of 32 buses of its grid
+  int64_t n_large_units;    // sum over instances of the buses with more than 32 ends
 
   // per bus
   const int32_t *inc_ptr;   // [n_bus+1] first incidence of each bus
@@ -109,15 +110,19 @@ struct View {
 
   // rounds of the fused kernel (per grid, buses sorted by degree)
   const int64_t *grid_round_off;              // [n_grids+1]
-  const int64_t *inst_round_off;              // [n_inst+1] rounds of earlier instances
+  const int4 *unit_rec;                       // per round of 32 buses of every instance:
+                                              //   {instance, round, first slot, items per lane | buses << 8}
+  const int2 *large_rec;                      // per large bus of every instance: {instance, bus}
+  const int64_t *inst_rec_base;               // per instance: inst_bus_off - grid_bus_off of its grid
   const int4 *round_desc;                     // {first slot, items per lane, buses, flags (1 = one large bus)}
   const int32_t *rbus;                        // [32 per round] global bus id, -1 padding
   const int4 *rbus_meta, *rbus_meta2;         // bus records in round order
   const double2 *rbus_hat, *rbus_inj;
-  const int4 *slot_meta;                      // end j of lane l at slot first + 32 j + l:
-                                              //   {other bus, group length at a head / 0 / -1 padding, code, end index}
-  const int4 *slot_pos;                       // the end's four CSR positions
-  const double2 *slot_gb, *slot_ac;           // the end's coefficients
+  const int32_t *bus_npair;                   // per bus: groups of parallel branches (distinct neighbours)
+  const int4 *slot_meta;                      // group j of lane l at slot first + 32 j + l:
+                                              //   {other bus, group length (-1 padding), code and index of its first end}
+  const int4 *slot_pos;                       // the group's four CSR positions
+  const double2 *slot_gb, *slot_ac;           // the group's coefficients summed in incidence order
 
   // per instance
   const int32_t *inst_grid, *inst_outage;     // outage: global branch id or -1
@@ -127,7 +132,7 @@ struct View {
   // scratch
   double2 *phasor;                            // [2 n_bus_inst]: (cos theta, sin theta), (V, 0) per bus
   int32_t *dev_error;
-  const double2 *sincos_tab;                  // [kSinCosTable] (cos, sin)(i pi / 128)
+  const double2 *sincos_tab;                  // [kSinCosTable] (cos, sin)(i pi / 512)
 };
 
 struct Ctx {
@@ -160,7 +165,7 @@ struct Ctx {
   double2 *ov_gb = nullptr, *ov_ac = nullptr, *ov_hat = nullptr;
   double2 *ov_slot_gb = nullptr, *ov_slot_ac = nullptr, *ov_rbus_hat = nullptr;
   int64_t n_slots = 0, n_rounds = 0;
-  std::vector<int64_t> grid_round_off, round_off;
+  std::vector<int64_t> grid_round_off;
 
   // host-call staging, allocated on first use
   double *stage_x = nullptr, *stage_f = nullptr, *stage_v = nullptr;
