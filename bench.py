@@ -154,20 +154,24 @@ def algorithmic_bytes(d, n_pv, n_load, n_shunt):
     return read + write
 
 
-def fused_fp64_flops(d, n_groups):
-    """Algorithmic FP64 flops of one k_fused launch (F and J, no mask), an
-    FMA counting 2: per branch end 20 (the rotated terms u, w, xh, yh: 4
-    multiplies + 4 FMAs; the six products a, b, dP/dt_k, dQ/dt_k, dP/dV_k,
-    dQ/dV_k; 2 adds into the bus sums), per extra end of a parallel group 4
-    adds, per bus 16 (F_P, F_Q: 2 FMAs each; the four diagonal entries)."""
-    return d.n_inc * 20 + 4 * (d.n_inc - n_groups) + d.n_bus * 16
+def fused_fp64_ops(d, n_pairs):
+    """FP64 operations (an FMA, a multiply or an add each count one: each
+    takes one issue of the FP64 pipe) of one instance in k_fused, F and J,
+    no mask: per pair of connected buses (parallel branches merged) 12 -- the
+    rotated terms u, w, xh, yh (4 multiplies + 4 FMAs), a = V_k xh, b = V_k yh,
+    2 adds into the bus sums -- plus one multiply per J value written (every
+    off-diagonal value, and the diagonal values: 2 multiplies + 2 FMAs per
+    bus), plus per bus 5: F_P and F_Q (2 FMAs each) and 2 V_o."""
+    return 12 * n_pairs + d.nnz + 5 * d.n_bus
 
 
 def source_hash():
+    """Hash of the sources that decide k_fused's memory traffic (kernel and data layout)."""
     import hashlib
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2011_11880_gb300", "csrc", "pf_eval.cu"), "rb") as fh:
-        h.update(fh.read())
+    for f in ("pf_eval.cu", "pf_build.cu", "pf_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2011_11880_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -365,20 +369,20 @@ def main():
     n_pv, n_load, n_shunt = sys_.n_pv, sys_.load_bus.shape[0], sys_.sh_bus.shape[0]
     ip, _, oth = one.incidence()
     own = np.repeat(np.arange(d1.n_bus), np.diff(ip))
-    n_groups = int(np.count_nonzero(np.r_[True, (oth[1:] != oth[:-1]) | (own[1:] != own[:-1])]))
-    flops_kf = N_STATES * fused_fp64_flops(d1, n_groups)          # one batched launch
+    n_pairs = int(np.count_nonzero(np.r_[True, (oth[1:] != oth[:-1]) | (own[1:] != own[:-1])]))
+    ops_kf = N_STATES * fused_fp64_ops(d1, n_pairs)                # one batched launch
     bytes_alg = N_STATES * algorithmic_bytes(d1, n_pv, n_load, n_shunt)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    fp64_peak_tflops = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12          # 2 DFMA/clk/SM, FMA = 2 flops
-    achieved_tf = flops_kf / (kf_ms * 1e-3) / 1e12
+    fp64_peak_gops = 152 * 2 * sm_mhz * 1e6 / 1e9                 # 2 FP64 operations / clk / SM
+    achieved_gops = ops_kf / (kf_ms * 1e-3) / 1e9
     eval_s = t_max / K                                                  # one batched step
     tr = load_traffic()
-    roofline = {"bound": "alu", "kernel": "k_fused", "achieved": achieved_tf, "peak": fp64_peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved_tf / fp64_peak_tflops,
+    roofline = {"bound": "alu", "kernel": "k_fused", "achieved": achieved_gops, "peak": fp64_peak_gops,
+                "unit": "G FP64 op/s", "frac": achieved_gops / fp64_peak_gops,
                 "traffic": tr.get("dram_bytes_per_launch") if tr else None,
-                "kernel_ms": kf_ms, "algorithmic_flops": flops_kf,
-                "peak_kind": "FP64 derived from unit counts and clock: 152 SMs x 2 DFMA/clk x 2 flops x "
-                             f"{sm_mhz:.0f} MHz",
+                "kernel_ms": kf_ms, "algorithmic_fp64_ops": ops_kf,
+                "peak_kind": "FP64 pipe derived from unit counts and clock: 152 SMs x 2 FP64 operations/clk x "
+                             f"{sm_mhz:.0f} MHz (= the 1.25 TFLOP/s FP64 FMA rate / 2)",
                 "evaluation_hbm_view": {"algorithmic_bytes": bytes_alg, "achieved_gbs": bytes_alg / eval_s / 1e9,
                                         "peak_gbs": peaks["hbm_gbs"], "peak_kind": peak_kind,
                                         "frac": bytes_alg / eval_s / 1e9 / peaks["hbm_gbs"]}}
@@ -424,7 +428,7 @@ def load_traffic():
             rec = json.load(fh)
     except Exception:
         return None
-    return rec if rec.get("pf_eval_cu_sha256_16") == source_hash() else None
+    return rec if rec.get("source_sha256_16") == source_hash() else None
 
 
 if __name__ == "__main__":
