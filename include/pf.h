@@ -154,8 +154,9 @@ typedef struct pf_grads {
 } pf_grads;
 
 typedef struct pf_tuning {
-  int32_t tile_inc;              /* branch ends per warp round: 32, 64, 96 or 128 (1-4 per lane) */
-  int32_t ctas_per_sm;           /* persistent CTAs per SM; 0 = enough CTAs for every round */
+  int32_t tile_inc;              /* 32, 64, 96 or 128: each lane fetches tile_inc / 32 pairs of
+                                    connected buses ahead (the chunk of a bus with > 32 neighbours) */
+  int32_t ctas_per_sm;           /* persistent CTAs per SM; 0 = one CTA for every round */
 } pf_tuning;
 
 /* ---- build (once) -------------------------------------------------------- */
@@ -269,17 +270,18 @@ PF_API int pf_vjp(pf_ctx *ctx, const double *x, const pf_overrides *ov, const do
 /* ---- tuning ------------------------------------------------------------------ */
 
 PF_API int pf_get_tuning(const pf_ctx *ctx, pf_tuning *t);
-/* Re-tiles the context (device work on `stream`, synchronised).  Never
- * changes results.  PF_ERR_INVALID for values outside the documented range. */
+/* Sets the launch parameters of the evaluation kernels (synchronises
+ * `stream` first).  Never changes results.  PF_ERR_INVALID for values
+ * outside the documented range. */
 PF_API int pf_set_tuning(pf_ctx *ctx, const pf_tuning *t, void *stream);
-/* Times the fused evaluation at x for each candidate tiling, keeps the
+/* Times the fused evaluation at x for each candidate tuning, keeps the
  * fastest and returns it in *chosen.  x, F, vals: device buffers used as
  * scratch for the timing runs. */
 PF_API int pf_autotune(pf_ctx *ctx, const double *x, double *F, double *vals, void *stream,
                 pf_tuning *chosen);
 
 /* The per-bus trigonometric routine of the evaluation (table-driven reduction
- * by multiples of pi/128 and short Taylor polynomials), exposed so it can be
+ * by multiples of pi/512 and short Taylor polynomials), exposed so it can be
  * checked against a reference sin / cos: cos_out[i], sin_out[i] of theta[i],
  * n device entries each, asynchronous on `stream`. */
 PF_API int pf_sincos(pf_ctx *ctx, const double *theta, int64_t n, double *cos_out, double *sin_out,

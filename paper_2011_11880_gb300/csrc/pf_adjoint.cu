@@ -1,17 +1,19 @@
 // Adjoint: vector-Jacobian products v^T dF/d(x, P_inj, Q_inj, r, x, b_c, tau)
-// for a batch of cotangents.  Trigonometric terms are recomputed (one sincos
-// per bus in k_phasor, shared with the forward kernel), nothing from a
-// forward call is kept.
+// for a batch of cotangents.  Trigonometric terms are recomputed (the forward
+// kernels' phasor records, one sincos per bus), nothing from a forward call
+// is kept.
 //
-// State part.  For bus o with branch ends e (other bus k) and mirror ends e'
-// (the same branch seen from k), using the rotated form of pf_eval.cu:
-//   dL/dtheta_o = v_P(o) V_o sum_e b_e - v_Q(o) V_o sum_e a_e
-//               + sum_e [ -v_P(k) Y_e' + v_Q(k) X_e' ]
+// State part.  For bus o with pairs (o, k) (parallel branches merged) the
+// gradient gathers the column of J^T at theta_o and V_o:
+//   dL/dtheta_o = v_P(o) V_o sum b - v_Q(o) V_o sum a
+//               + sum_k [ v_P(k) dP_k/dtheta_o + v_Q(k) dQ_k/dtheta_o ]
 //   dL/dV_o     = v_P(o) (2 V_o A^ - sum a) - v_Q(o) (2 V_o C^ + sum b)
-//               + sum_e [ -v_P(k) V_k xh_e' - v_Q(k) V_k yh_e' ]
-// plus the +-1 terms of the extended rows.  Sums run in incidence-list order
-// (deterministic).  The terms of one end are computed once per tile and
-// reused for every cotangent.
+//               + sum_k [ v_P(k) dP_k/dV_o + v_Q(k) dQ_k/dV_o ]
+// (a, b as in the forward kernels; the mirror partials from the merged
+// coefficients of the ends at k towards o), plus the +-1 terms of the
+// extended rows.  One lane per bus on the forward kernel's rounds; the
+// cotangents run in chunks whose sums stay in registers, the mirror partials
+// are recomputed per chunk.
 //
 // Parameter part.  One thread per (instance, branch): the partials of the
 // four terminal powers with respect to g, b, b_c and tau, chained to r and x
@@ -25,30 +27,45 @@ namespace pf {
 
 namespace {
 
+// From this many cotangents on, they are read from a transposed copy.
+constexpr int kVjpTransposeMin = 16;
+
 struct VjpArgs {
   const double *x;
   const double *v;        // [n_cot][n_f]
+  const double *vt;       // [n_f][n_cot] transposed copy, or nullptr
   int n_cot;
-  int64_t n_f;
-  const double2 *gb;
-  const double2 *ac;
-  const double2 *hat;
+  int64_t n_f, n_x;
+  const double2 *gb, *ac, *hat;       // per end (incidence order) / per bus
+  const double2 *sgb, *sgbm, *sac;    // per slot: merged own and mirror coefficients, own A, C
+  const double2 *rhat;                // per bus in round order
   const uint8_t *status;
   double *gx;             // [n_cot][n_x]
-  int64_t n_x;
-  int cap;
 };
 
-__global__ void k_phasor_adj(View v, const double *__restrict__ x) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < v.n_bus_inst; q += stride) {
-    const int inst = v.n_inst == 1 ? 0 : find_segment(v.inst_bus_off, v.n_inst, q);
-    const int64_t lb = q - v.inst_bus_off[inst];
-    double s, c;
-    sincos(x[v.inst_x_off[inst] + lb], &s, &c);
-    v.phasor[2 * q] = make_double2(c, s);
-    v.phasor[2 * q + 1] = make_double2(x[v.inst_x_off[inst] + v.grid_nbus[v.inst_grid[inst]] + lb], 0.0);
-  }
+// Cotangent c at row `row` (instance-offset) in either layout.
+__device__ __forceinline__ double cot_at(const double *v, const double *vt, int n_cot, int64_t n_f, int c,
+                                         int64_t row) {
+  return vt ? __ldg(vt + row * n_cot + c) : __ldg(v + (int64_t)c * n_f + row);
+}
+
+__device__ __forceinline__ double cot_row(const VjpArgs &a, int c, int64_t f0, int32_t row) {
+  return row >= 0 ? cot_at(a.v, a.vt, a.n_cot, a.n_f, c, f0 + row) : 0.0;
+}
+
+// Rotated terms of one branch end (own phasor po, other phasor pk), as in the
+// forward kernels.
+struct Terms {
+  double xh, yh;
+};
+
+__device__ __forceinline__ Terms rotated(double2 G, double2 po, double2 pk) {
+  const double uu = __fma_rn(G.x, pk.x, __dmul_rn(-G.y, pk.y));
+  const double ww = __fma_rn(G.x, pk.y, __dmul_rn(G.y, pk.x));
+  Terms r;
+  r.xh = __fma_rn(po.x, uu, __dmul_rn(po.y, ww));
+  r.yh = __fma_rn(po.y, uu, __dmul_rn(-po.x, ww));
+  return r;
 }
 
 __device__ __forceinline__ bool end_in(const View &v, int32_t e, int32_t outage, const uint8_t *status,
@@ -57,220 +74,282 @@ __device__ __forceinline__ bool end_in(const View &v, int32_t e, int32_t outage,
   return (l != outage) && (status == nullptr || status[st_base + l] != 0);
 }
 
-// Rotated terms of end e (own bus o, other bus k): xh, yh.
-__device__ __forceinline__ void rotated(double2 G, double2 po, double2 pk, double &xh, double &yh) {
-  const double uu = G.x * pk.x - G.y * pk.y;
-  const double ww = G.x * pk.y + G.y * pk.x;
-  xh = po.x * uu + po.y * ww;
-  yh = po.y * uu - po.x * ww;
+// Under an outage mask: own coefficients, own A, C and mirror coefficients of
+// the branches in service of a group of `len` parallel ends e, e+1, ...,
+// each summed in incidence order (zero when none is in service).
+struct PairCoeff {
+  double2 gb, ac, gbm;
+};
+
+__device__ __forceinline__ PairCoeff masked_pair(const View &v, const VjpArgs &a, int32_t e, int32_t len,
+                                                 int32_t outage, int64_t st_base) {
+  PairCoeff r{make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+  bool first = true;
+  for (int32_t i = 0; i < len; ++i) {
+    if (!end_in(v, e + i, outage, a.status, st_base)) continue;
+    const double2 g = __ldg(a.gb + e + i), c = __ldg(a.ac + e + i), m = __ldg(a.gb + v.inc_mirror[e + i]);
+    if (first) {
+      r.gb = g; r.ac = c; r.gbm = m;
+      first = false;
+    } else {
+      r.gb = make_double2(__dadd_rn(r.gb.x, g.x), __dadd_rn(r.gb.y, g.y));
+      r.ac = make_double2(__dadd_rn(r.ac.x, c.x), __dadd_rn(r.ac.y, c.y));
+      r.gbm = make_double2(__dadd_rn(r.gbm.x, m.x), __dadd_rn(r.gbm.y, m.y));
+    }
+  }
+  return r;
 }
 
-__global__ void __launch_bounds__(1024) k_vjp_state(View v, VjpArgs a) {
-  extern __shared__ double sm[];
-  const int cap = a.cap;
-  double *s_a = sm, *s_b = sm + cap, *s_g = sm + 2 * cap, *s_h = sm + 3 * cap;
-  double *s_ma = sm + 4 * cap, *s_mc = sm + 5 * cap;
-  __shared__ int s_cut;
-  const bool masked = a.status != nullptr || v.inst_outage != nullptr;
+// The partials of bus k's P and Q rows with respect to theta_o and V_o, for
+// the (merged) branch end at k towards o with coefficients Gm:
+//   dP_k/dt_o = -V_k b',  dQ_k/dt_o = V_k a',  dP_k/dV_o = -V_k xh',  dQ_k/dV_o = -V_k yh',
+// with xh', yh' the rotated terms of that end and a' = V_o xh', b' = V_o yh'.
+struct Mirror {
+  double pt, qt, pv, qv;
+};
 
-  for (int64_t u = blockIdx.x; u < v.n_units; u += gridDim.x) {
-    const int inst = v.n_inst == 1 ? 0 : find_segment(v.inst_unit_off, v.n_inst, u);
-    const int g = v.inst_grid[inst];
-    const int64_t t = v.grid_tile_off[g] + (u - v.inst_unit_off[inst]);
-    const int32_t b0 = v.tile_bus0[t], b1 = v.tile_bus1[t];
-    const int32_t e0 = v.inc_ptr[b0], e1 = v.inc_ptr[b1];
+__device__ __forceinline__ Mirror mirror_partials(double2 Gm, double2 po, double vo, double2 pk, double vk) {
+  const Terms t = rotated(Gm, pk, po);
+  Mirror m;
+  m.pt = __dmul_rn(-vk, __dmul_rn(vo, t.yh));
+  m.qt = __dmul_rn(vk, __dmul_rn(vo, t.xh));
+  m.pv = __dmul_rn(-vk, t.xh);
+  m.qv = __dmul_rn(-vk, t.yh);
+  return m;
+}
+
+
+// Writes dL/dtheta_o, dL/dV_o (and, in the extended formulation, the
+// gradients of the generator / slack unknowns) of cotangent c.
+__device__ __forceinline__ void write_state_grad(const View &v, const VjpArgs &a, int inst, int g, int64_t lb,
+                                                 int32_t nb, int32_t gi, int32_t rp, int32_t rq, int c, double gt,
+                                                 double gvv) {
+  const int64_t f0 = v.inst_f_off[inst];
+  double *__restrict__ gx = a.gx + (int64_t)c * a.n_x + v.inst_x_off[inst];
+  if (v.formulation == PF_EXTENDED) {
+    if (lb == v.grid_slack[g]) {
+      gt = __dadd_rn(gt, cot_row(a, c, f0, v.grid_row_gth[g]));   // d g_theta / d theta_s = 1
+      gx[2 * nb + v.grid_ngen[g]] = -cot_row(a, c, f0, rp);        // d g_p / d P_s = -1
+    }
+    if (gi >= 0) {
+      gvv = __dadd_rn(gvv, cot_row(a, c, f0, 2 * nb + gi));       // d g_V / d V = 1
+      gx[2 * nb + gi] = -cot_row(a, c, f0, rq);                    // d g_q / d Q_g = -1
+    }
+  }
+  gx[lb] = gt;
+  gx[nb + lb] = gvv;
+}
+
+// State part, one warp per round of 32 buses, one bus per lane (the forward
+// kernel's rounds and slots).  For the lane's bus o:
+//   dL/dtheta_o = v_P(o) dP_o/dt_o + v_Q(o) dQ_o/dt_o + sum over pairs (o,k) [v_P(k) dP_k/dt_o + v_Q(k) dQ_k/dt_o]
+//   dL/dV_o     = the same with V_o,
+// the diagonal partials from the bus sums (as in the forward kernel) and the
+// mirror partials recomputed per chunk of CH cotangents, whose sums are kept
+// in registers.  Sums in a fixed order: own rows, then pairs in list order.
+template <int CH, bool MASKED>
+__global__ void __launch_bounds__(32) k_vjp_lane(View v, VjpArgs a) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t u = blockIdx.x; u < v.n_lane_units; u += gridDim.x) {
+    const int4 ur = __ldg(v.unit_rec + u);
+    const int inst = ur.x;
+    const int64_t r = ur.y;
+    const int g = __ldg(v.inst_grid + inst);
+    const double2 *__restrict__ rec = v.phasor + 2 * __ldg(v.inst_rec_base + inst);
+    const int32_t outage = MASKED ? v.inst_outage[inst] : -1;
+    const int64_t st_base = MASKED ? v.inst_br_off[inst] - v.grid_br_off[g] : 0;
+    const int64_t f0 = v.inst_f_off[inst];
+    const int64_t rb = 32 * r + lane;
+    if (lane >= (ur.w >> 8)) continue;           // no bus on this lane (no warp-wide operation follows)
+    const int32_t o = __ldg(v.rbus + rb);
+    const int4 bm = __ldg(v.rbus_meta + rb);
+    const int32_t gi = __ldg(v.rbus_meta2 + rb).w;
     const int64_t gb0 = v.grid_bus_off[g];
     const int32_t nb = v.grid_nbus[g];
-    const double *__restrict__ xi = a.x + v.inst_x_off[inst];
-    const double *__restrict__ Vi = xi + nb - gb0;
-    const double2 *__restrict__ phb = v.phasor + 2 * (v.inst_bus_off[inst] - gb0);
-    const int32_t outage = masked ? v.inst_outage[inst] : -1;
-    const int64_t st_base = v.inst_br_off[inst] - v.grid_br_off[g];
-    const int64_t f0 = v.inst_f_off[inst];
-    const int32_t ob = b0 + (int32_t)threadIdx.x;
-    const bool owner = ob < b1;
-    const bool single = (e1 - e0) <= cap;
+    const int32_t D = ur.w & 0xff;
+    const int64_t q0 = (int64_t)ur.z + lane;
+    const double2 po = rec[2 * o];
+    const double vo = rec[2 * o + 1].x;
 
-    if (single) {
-      // own and mirror terms of this thread's end, kept for every cotangent
-      const int j = threadIdx.x;
-      const int n = e1 - e0;
-      double mx = 0.0, my = 0.0, vk = 0.0;
-      int32_t rpk = -1, rqk = -1;
-      if (j < n) {
-        const int32_t e = e0 + j;
-        const int32_t o = v.inc_own[e], k = v.inc_other[e], em = v.inc_mirror[e];
-        const bool in = !masked || end_in(v, e, outage, a.status, st_base);
-        const double2 po = phb[2 * o], pk = phb[2 * k];
-        double2 G = a.gb[e], Gm = a.gb[em];
-        if (!in) G = Gm = make_double2(0.0, 0.0);
-        double xh, yh;
-        rotated(G, po, pk, xh, yh);
-        vk = Vi[k];
-        s_a[j] = vk * xh;
-        s_b[j] = vk * yh;
-        rotated(Gm, pk, po, mx, my);
-        rpk = v.row_p[k];
-        rqk = v.row_q[k];
-        if (masked) {
-          const double2 ac = a.ac[e];
-          s_ma[j] = in ? ac.x : 0.0;
-          s_mc[j] = in ? ac.y : 0.0;
+    // bus sums over the own ends (the forward kernel's a, b; A^, C^ under a mask)
+    double sa = 0.0, sb = 0.0, sma = 0.0, smc = 0.0;
+    for (int32_t j = 0; j < D; ++j) {
+      const int64_t q = q0 + 32 * j;
+      const int4 meta = __ldg(v.slot_meta + q);
+      if (meta.y < 0) continue;
+      double2 G = __ldg(a.sgb + q), AC = make_double2(0.0, 0.0);
+      if (MASKED) {
+        AC = __ldg(a.sac + q);
+        if (meta.y == 1) {
+          if (!end_in(v, meta.w, outage, a.status, st_base)) G = AC = make_double2(0.0, 0.0);
+        } else {
+          const PairCoeff pc = masked_pair(v, a, meta.w, meta.y, outage, st_base);
+          G = pc.gb;
+          AC = pc.ac;
         }
       }
-      __syncthreads();
-      double sa = 0.0, sb = 0.0, ma = 0.0, mc = 0.0;
-      int32_t op0 = 0, op1 = 0;
-      if (owner) {
-        op0 = v.inc_ptr[ob];
-        op1 = v.inc_ptr[ob + 1];
-        for (int32_t e = op0; e < op1; ++e) {
-          sa += s_a[e - e0];
-          sb += s_b[e - e0];
-          if (masked) {
-            ma += s_ma[e - e0];
-            mc += s_mc[e - e0];
-          }
-        }
+      const int32_t k = meta.x;
+      const double2 pk = rec[2 * k];
+      const double vk = rec[2 * k + 1].x;
+      const Terms t = rotated(G, po, pk);
+      sa = __dadd_rn(sa, __dmul_rn(vk, t.xh));
+      sb = __dadd_rn(sb, __dmul_rn(vk, t.yh));
+      if (MASKED) {
+        sma = __dadd_rn(sma, AC.x);
+        smc = __dadd_rn(smc, AC.y);
       }
-      for (int c = 0; c < a.n_cot; ++c) {
-        const double *__restrict__ vc = a.v + (int64_t)c * a.n_f + f0;
-        if (j < n) {
-          const int32_t o = v.inc_own[e0 + j];
-          const double vo = Vi[o];
-          const double vpk = rpk >= 0 ? vc[rpk] : 0.0;
-          const double vqk = rqk >= 0 ? vc[rqk] : 0.0;
-          // X' = V_k V_o mx, Y' = V_k V_o my
-          const double vv = vk * vo;
-          s_g[j] = -vpk * (vv * my) + vqk * (vv * mx);
-          s_h[j] = -vpk * (vk * mx) - vqk * (vk * my);
-        }
-        __syncthreads();
-        if (owner) {
-          double gt = 0.0, gv = 0.0;
-          for (int32_t e = op0; e < op1; ++e) {
-            gt += s_g[e - e0];
-            gv += s_h[e - e0];
-          }
-          const int32_t o = ob;
-          const int64_t lb = o - gb0;
-          const double vo = Vi[o];
-          const double ah = masked ? ma + v.bus_sh[o].x : a.hat[o].x;
-          const double ch = masked ? mc + v.bus_sh[o].y : a.hat[o].y;
-          const int32_t rp = v.row_p[o], rq = v.row_q[o];
-          const double vp = rp >= 0 ? vc[rp] : 0.0;
-          const double vq = rq >= 0 ? vc[rq] : 0.0;
-          double dth = vp * (vo * sb) - vq * (vo * sa) + gt;
-          double dv = vp * (2.0 * vo * ah - sa) - vq * (2.0 * vo * ch + sb) + gv;
-          double *__restrict__ gx = a.gx + (int64_t)c * a.n_x + v.inst_x_off[inst];
-          if (v.formulation == PF_EXTENDED) {
-            const int32_t gi = v.gen[o];
-            if (lb == v.grid_slack[g]) {
-              dth += vc[v.grid_row_gth[g]];
-              gx[2 * nb + v.grid_ngen[g]] = -vp;        // P_s
-            }
-            if (gi >= 0) {
-              dv += vc[2 * nb + gi];
-              gx[2 * nb + gi] = -vq;                    // Q_g
-            }
-          }
-          gx[lb] = dth;
-          gx[nb + lb] = dv;
-        }
-        __syncthreads();
-      }
+    }
+    double ah, ch;
+    if (MASKED) {
+      const double2 sh = __ldg(v.bus_sh + o);
+      ah = __dadd_rn(sma, sh.x);
+      ch = __dadd_rn(smc, sh.y);
     } else {
-      // A bus with more ends than `cap`: chunk over its ends for every
-      // cotangent, recomputing the rotated terms.
-      for (int c = 0; c < a.n_cot; ++c) {
-        const double *__restrict__ vc = a.v + (int64_t)c * a.n_f + f0;
-        double sa = 0.0, sb = 0.0, ma = 0.0, mc = 0.0, gt = 0.0, gv = 0.0;
-        for (int32_t cs = e0; cs < e1;) {
-          int32_t ce = min(cs + cap, e1);
-          if (ce < e1) {
-            if (threadIdx.x == 0) s_cut = cs;
-            __syncthreads();
-            for (int j = threadIdx.x; j < cap; j += blockDim.x) {
-              const int32_t p = cs + 1 + j;
-              if (p <= ce && v.inc_grp[p] > 0) atomicMax(&s_cut, p);
-            }
-            __syncthreads();
-            const int32_t cut = s_cut;
-            __syncthreads();
-            if (cut == cs) {
-              if (threadIdx.x == 0) atomicOr(v.dev_error, kErrChunk);
-              break;
-            }
-            ce = cut;
-          }
-          const int n = ce - cs;
-          for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            const int32_t e = cs + j;
-            const int32_t o = v.inc_own[e], k = v.inc_other[e], em = v.inc_mirror[e];
-            const bool in = !masked || end_in(v, e, outage, a.status, st_base);
-            const double2 po = phb[2 * o], pk = phb[2 * k];
-            double2 G = a.gb[e], Gm = a.gb[em];
-            if (!in) G = Gm = make_double2(0.0, 0.0);
-            double xh, yh, mx, my;
-            rotated(G, po, pk, xh, yh);
-            rotated(Gm, pk, po, mx, my);
-            const double vk = Vi[k], vo = Vi[o];
-            s_a[j] = vk * xh;
-            s_b[j] = vk * yh;
-            const int32_t rpk = v.row_p[k], rqk = v.row_q[k];
-            const double vpk = rpk >= 0 ? vc[rpk] : 0.0;
-            const double vqk = rqk >= 0 ? vc[rqk] : 0.0;
-            const double vv = vk * vo;
-            s_g[j] = -vpk * (vv * my) + vqk * (vv * mx);
-            s_h[j] = -vpk * (vk * mx) - vqk * (vk * my);
-            if (masked) {
-              const double2 ac = a.ac[e];
-              s_ma[j] = in ? ac.x : 0.0;
-              s_mc[j] = in ? ac.y : 0.0;
-            }
-          }
-          __syncthreads();
-          if (owner) {
-            const int32_t lo = max(v.inc_ptr[ob], cs), hi = min(v.inc_ptr[ob + 1], ce);
-            for (int32_t e = lo; e < hi; ++e) {
-              sa += s_a[e - cs];
-              sb += s_b[e - cs];
-              gt += s_g[e - cs];
-              gv += s_h[e - cs];
-              if (masked) {
-                ma += s_ma[e - cs];
-                mc += s_mc[e - cs];
-              }
-            }
-          }
-          __syncthreads();
-          cs = ce;
+      const double2 h = __ldg(a.rhat + rb);
+      ah = h.x;
+      ch = h.y;
+    }
+    const double two_vo = __dadd_rn(vo, vo);
+    const double d_pt = __dmul_rn(vo, sb), d_qt = __dmul_rn(-vo, sa);
+    const double d_pv = __fma_rn(two_vo, ah, -sa), d_qv = __fma_rn(-two_vo, ch, -sb);
+
+    for (int c0 = 0; c0 < a.n_cot; c0 += CH) {
+      double gt[CH], gvv[CH];
+#pragma unroll
+      for (int i = 0; i < CH; ++i) {
+        gt[i] = 0.0;
+        gvv[i] = 0.0;
+        if (c0 + i < a.n_cot) {
+          const double vp = cot_row(a, c0 + i, f0, bm.x), vq = cot_row(a, c0 + i, f0, bm.y);
+          gt[i] = __fma_rn(d_pt, vp, __dmul_rn(d_qt, vq));
+          gvv[i] = __fma_rn(d_pv, vp, __dmul_rn(d_qv, vq));
         }
-        if (owner) {
-          const int32_t o = ob;
-          const int64_t lb = o - gb0;
-          const double vo = Vi[o];
-          const double ah = masked ? ma + v.bus_sh[o].x : a.hat[o].x;
-          const double ch = masked ? mc + v.bus_sh[o].y : a.hat[o].y;
-          const int32_t rp = v.row_p[o], rq = v.row_q[o];
-          const double vp = rp >= 0 ? vc[rp] : 0.0;
-          const double vq = rq >= 0 ? vc[rq] : 0.0;
-          double dth = vp * (vo * sb) - vq * (vo * sa) + gt;
-          double dv = vp * (2.0 * vo * ah - sa) - vq * (2.0 * vo * ch + sb) + gv;
-          double *__restrict__ gx = a.gx + (int64_t)c * a.n_x + v.inst_x_off[inst];
-          if (v.formulation == PF_EXTENDED) {
-            const int32_t gi = v.gen[o];
-            if (lb == v.grid_slack[g]) {
-              dth += vc[v.grid_row_gth[g]];
-              gx[2 * nb + v.grid_ngen[g]] = -vp;
-            }
-            if (gi >= 0) {
-              dv += vc[2 * nb + gi];
-              gx[2 * nb + gi] = -vq;
-            }
+      }
+      for (int32_t j = 0; j < D; ++j) {
+        const int64_t q = q0 + 32 * j;
+        const int4 meta = __ldg(v.slot_meta + q);
+        if (meta.y < 0) continue;
+        double2 Gm = __ldg(a.sgbm + q);
+        if (MASKED) {
+          if (meta.y == 1) {
+            if (!end_in(v, meta.w, outage, a.status, st_base)) Gm = make_double2(0.0, 0.0);
+          } else {
+            Gm = masked_pair(v, a, meta.w, meta.y, outage, st_base).gbm;
           }
-          gx[lb] = dth;
-          gx[nb + lb] = dv;
+        }
+        const int32_t k = meta.x;
+        const double2 pk = rec[2 * k];
+        const double vk = rec[2 * k + 1].x;
+        const Mirror m = mirror_partials(Gm, po, vo, pk, vk);
+        const int4 bk = __ldg(v.bus_meta + k);
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+          if (c0 + i < a.n_cot) {
+            const double vp = cot_row(a, c0 + i, f0, bk.x), vq = cot_row(a, c0 + i, f0, bk.y);
+            gt[i] = __fma_rn(m.qt, vq, __fma_rn(m.pt, vp, gt[i]));
+            gvv[i] = __fma_rn(m.qv, vq, __fma_rn(m.pv, vp, gvv[i]));
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < CH; ++i)
+        if (c0 + i < a.n_cot) write_state_grad(v, a, inst, g, o - gb0, nb, gi, bm.x, bm.y, c0 + i, gt[i], gvv[i]);
+    }
+  }
+}
+
+// State part for a bus with more than 32 neighbours, one warp per bus: lane l
+// takes ends l, l + 32, ... (per end, not merged), partial sums are combined
+// by a fixed butterfly.
+template <int CH, bool MASKED>
+__global__ void __launch_bounds__(32) k_vjp_large(View v, VjpArgs a) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t u = blockIdx.x; u < v.n_large_units; u += gridDim.x) {
+    const int2 lr = __ldg(v.large_rec + u);
+    const int inst = lr.x;
+    const int32_t o = lr.y;
+    const int g = __ldg(v.inst_grid + inst);
+    const double2 *__restrict__ rec = v.phasor + 2 * __ldg(v.inst_rec_base + inst);
+    const int32_t outage = MASKED ? v.inst_outage[inst] : -1;
+    const int64_t st_base = MASKED ? v.inst_br_off[inst] - v.grid_br_off[g] : 0;
+    const int64_t f0 = v.inst_f_off[inst];
+    const int32_t e0 = __ldg(v.inc_ptr + o), e1 = __ldg(v.inc_ptr + o + 1);
+    const int4 bm = __ldg(v.bus_meta + o);
+    const int32_t gi = __ldg(v.bus_meta2 + o).w;
+    const double2 po = rec[2 * o];
+    const double vo = rec[2 * o + 1].x;
+    double sa = 0.0, sb = 0.0, sma = 0.0, smc = 0.0;
+    for (int32_t e = e0 + lane; e < e1; e += 32) {
+      double2 G = __ldg(a.gb + e), AC = __ldg(a.ac + e);
+      if (MASKED && !end_in(v, e, outage, a.status, st_base)) G = AC = make_double2(0.0, 0.0);
+      const int32_t k = __ldg(v.inc_other + e);
+      const Terms t = rotated(G, po, rec[2 * k]);
+      const double vk = rec[2 * k + 1].x;
+      sa = __dadd_rn(sa, __dmul_rn(vk, t.xh));
+      sb = __dadd_rn(sb, __dmul_rn(vk, t.yh));
+      if (MASKED) {
+        sma = __dadd_rn(sma, AC.x);
+        smc = __dadd_rn(smc, AC.y);
+      }
+    }
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+      sa = __dadd_rn(sa, __shfl_xor_sync(0xffffffffu, sa, m));
+      sb = __dadd_rn(sb, __shfl_xor_sync(0xffffffffu, sb, m));
+      if (MASKED) {
+        sma = __dadd_rn(sma, __shfl_xor_sync(0xffffffffu, sma, m));
+        smc = __dadd_rn(smc, __shfl_xor_sync(0xffffffffu, smc, m));
+      }
+    }
+    double ah, ch;
+    if (MASKED) {
+      const double2 sh = __ldg(v.bus_sh + o);
+      ah = __dadd_rn(sma, sh.x);
+      ch = __dadd_rn(smc, sh.y);
+    } else {
+      const double2 h = __ldg(a.hat + o);
+      ah = h.x;
+      ch = h.y;
+    }
+    const double two_vo = __dadd_rn(vo, vo);
+    const double d_pt = __dmul_rn(vo, sb), d_qt = __dmul_rn(-vo, sa);
+    const double d_pv = __fma_rn(two_vo, ah, -sa), d_qv = __fma_rn(-two_vo, ch, -sb);
+    for (int c0 = 0; c0 < a.n_cot; c0 += CH) {
+      double gt[CH], gvv[CH];
+#pragma unroll
+      for (int i = 0; i < CH; ++i) gt[i] = gvv[i] = 0.0;
+      for (int32_t e = e0 + lane; e < e1; e += 32) {
+        double2 Gm = __ldg(a.gb + __ldg(v.inc_mirror + e));
+        if (MASKED && !end_in(v, e, outage, a.status, st_base)) Gm = make_double2(0.0, 0.0);
+        const int32_t k = __ldg(v.inc_other + e);
+        const Mirror m = mirror_partials(Gm, po, vo, rec[2 * k], rec[2 * k + 1].x);
+        const int4 bk = __ldg(v.bus_meta + k);
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+          if (c0 + i < a.n_cot) {
+            const double vp = cot_row(a, c0 + i, f0, bk.x), vq = cot_row(a, c0 + i, f0, bk.y);
+            gt[i] = __fma_rn(m.qt, vq, __fma_rn(m.pt, vp, gt[i]));
+            gvv[i] = __fma_rn(m.qv, vq, __fma_rn(m.pv, vp, gvv[i]));
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < CH; ++i) {
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1) {
+          gt[i] = __dadd_rn(gt[i], __shfl_xor_sync(0xffffffffu, gt[i], m));
+          gvv[i] = __dadd_rn(gvv[i], __shfl_xor_sync(0xffffffffu, gvv[i], m));
+        }
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+          if (c0 + i < a.n_cot) {
+            const double vp = cot_row(a, c0 + i, f0, bm.x), vq = cot_row(a, c0 + i, f0, bm.y);
+            const double t = __fma_rn(d_qt, vq, __fma_rn(d_pt, vp, gt[i]));
+            const double w = __fma_rn(d_qv, vq, __fma_rn(d_pv, vp, gvv[i]));
+            write_state_grad(v, a, inst, g, o - v.grid_bus_off[g], v.grid_nbus[g], gi, bm.x, bm.y, c0 + i, t, w);
+          }
         }
       }
     }
@@ -278,100 +357,149 @@ __global__ void __launch_bounds__(1024) k_vjp_state(View v, VjpArgs a) {
 }
 
 struct ParamArgs {
-  const double *x;
-  const double *v;
+  const double *v;            // [n_cot][n_f], or
+  const double *vt;           // [n_f][n_cot] (transposed copy) when not nullptr
   int n_cot;
   int64_t n_f, n_bi;          // n_bi: branches summed over instances
   const double *r, *xr, *b, *tap;   // overrides or nullptr
   const uint8_t *status;
   double *gr, *gxr, *gb, *gtap;
-  double *gp, *gq;            // injection grads
-  int64_t n_busi;
 };
 
-// one thread per (instance, branch)
+// One thread per (instance, branch).  With the branch's constants
+//   g + j b_s = 1 / (r + j x),  alpha = (x^2 - r^2)/D^2,  beta = 2 r x / D^2  (D = r^2 + x^2),
+// so that dg/dr = db_s/dx = alpha and db_s/dr = -dg/dx = beta, and the state's
+//   cos / sin of delta = theta_f - theta_t - phi,  vv = V_f V_t / tau,
+// the derivatives of the four terminal powers (P_f, Q_f, P_t, Q_t) with
+// respect to g, b_s, b_c and tau are formed once and dotted with the
+// cotangent entries of the four rows for every cotangent.  OVR: the
+// constants come from per-call parameters instead of the build.
+template <bool OVR>
 __global__ void k_vjp_params(View v, ParamArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.n_bi; q += stride) {
     const int inst = v.n_inst == 1 ? 0 : find_segment(v.inst_br_off, v.n_inst, q);
     const int g = v.inst_grid[inst];
     const int64_t l = v.grid_br_off[g] + (q - v.inst_br_off[inst]);   // global branch
-    const int64_t gb0 = v.grid_bus_off[g];
-    const int32_t nb = v.grid_nbus[g];
-    const double *__restrict__ xi = a.x + v.inst_x_off[inst];
-    const double2 *__restrict__ phb = v.phasor + 2 * (v.inst_bus_off[inst] - gb0);
+    const double2 *__restrict__ rec = v.phasor + 2 * __ldg(v.inst_rec_base + inst);
     const int32_t f = v.br_from[l], t = v.br_to[l];
     bool in = v.br_status[l] != 0 && l != v.inst_outage[inst];
     if (a.status) in = in && a.status[q] != 0;
-    double d_r[4], d_x[4], d_b[4], d_t[4];   // order: P_f, Q_f, P_t, Q_t
+    double d_r[4], d_x[4], d_t[4], db1 = 0.0, db3 = 0.0;   // rows: P_f, Q_f, P_t, Q_t
     if (in) {
-      const double r = a.r ? a.r[l] : v.br_r[l];
-      const double x = a.xr ? a.xr[l] : v.br_x[l];
-      const double bc = a.b ? a.b[l] : v.br_b[l];
-      const double tau = a.tap ? a.tap[l] : v.br_tap[l];
-      const double dd = r * r + x * x;
-      const double g_ = r / dd, b_ = -x / dd;
-      const double id2 = 1.0 / (dd * dd);
-      const double dg_dr = (x * x - r * r) * id2, dg_dx = -2.0 * r * x * id2;
-      const double db_dr = 2.0 * r * x * id2, db_dx = (x * x - r * r) * id2;
-      const double2 pf = phb[2 * f], pt = phb[2 * t];
-      // delta = theta_f - theta_t - phi
+      double gs, bs, al, be, it, bc;
+      const double2 ph = __ldg(v.br_k_ph + l);             // (cos phi, sin phi)
+      if (OVR) {
+        const double r = a.r ? a.r[l] : v.br_r[l];
+        const double x = a.xr ? a.xr[l] : v.br_x[l];
+        const double dd = r * r + x * x;
+        const double inv = 1.0 / dd;
+        gs = r * inv;
+        bs = -x * inv;
+        al = (x * x - r * r) * (inv * inv);
+        be = 2.0 * r * x * (inv * inv);
+        it = 1.0 / (a.tap ? a.tap[l] : v.br_tap[l]);
+        bc = a.b ? a.b[l] : v.br_b[l];
+      } else {
+        const double2 k1 = __ldg(v.br_k_gb + l), k2 = __ldg(v.br_k_ab + l), k3 = __ldg(v.br_k_tc + l);
+        gs = k1.x; bs = k1.y; al = k2.x; be = k2.y; it = k3.x; bc = k3.y;
+      }
+      const double2 pf = rec[2 * f], pt = rec[2 * t];
+      const double vf = rec[2 * f + 1].x, vt = rec[2 * t + 1].x;
       const double cD = pf.x * pt.x + pf.y * pt.y, sD = pf.y * pt.x - pf.x * pt.y;
-      double sp, cp;
-      sincos(v.br_shift[l], &sp, &cp);
-      const double cd = cD * cp + sD * sp, sd = sD * cp - cD * sp;
-      const double vf = xi[nb + (f - gb0)], vt = xi[nb + (t - gb0)];
-      const double it = 1.0 / tau;
-      const double vv = vf * vt * it;
-      const double vf2t = vf * vf * it * it, vt2 = vt * vt;
-      const double Pf_g = vf2t - vv * cd, Pf_b = -vv * sd;
-      const double Qf_g = -vv * sd, Qf_b = -vf2t + vv * cd;
-      const double Pt_g = vt2 - vv * cd, Pt_b = vv * sd;
-      const double Qt_g = vv * sd, Qt_b = -vt2 + vv * cd;
-      d_r[0] = Pf_g * dg_dr + Pf_b * db_dr; d_x[0] = Pf_g * dg_dx + Pf_b * db_dx;
-      d_r[1] = Qf_g * dg_dr + Qf_b * db_dr; d_x[1] = Qf_g * dg_dx + Qf_b * db_dx;
-      d_r[2] = Pt_g * dg_dr + Pt_b * db_dr; d_x[2] = Pt_g * dg_dx + Pt_b * db_dx;
-      d_r[3] = Qt_g * dg_dr + Qt_b * db_dr; d_x[3] = Qt_g * dg_dx + Qt_b * db_dx;
-      d_b[0] = 0.0; d_b[1] = -0.5 * vf2t; d_b[2] = 0.0; d_b[3] = -0.5 * vt2;
-      const double vv2 = vv * it;
-      d_t[0] = -2.0 * vf2t * it * (g_ + v.br_gfr[l]) + vv2 * (g_ * cd + b_ * sd);
-      d_t[1] = 2.0 * vf2t * it * (b_ + 0.5 * bc) + vv2 * (g_ * sd - b_ * cd);
-      d_t[2] = vv2 * (g_ * cd - b_ * sd);
-      d_t[3] = -vv2 * (g_ * sd + b_ * cd);
+      const double cd = cD * ph.x + sD * ph.y, sd = sD * ph.x - cD * ph.y;
+      const double vfi = vf * it;
+      const double vv = vfi * vt, vf2t = vfi * vfi, vt2 = vt * vt;
+      const double pgc = vv * cd, pgs = vv * sd;
+      // d/dg and d/db_s of each row
+      const double Fg[4] = {vf2t - pgc, -pgs, vt2 - pgc, pgs};
+      const double Fb[4] = {-pgs, pgc - vf2t, pgs, pgc - vt2};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        d_r[i] = Fg[i] * al + Fb[i] * be;
+        d_x[i] = Fb[i] * al - Fg[i] * be;
+      }
+      db1 = -0.5 * vf2t;
+      db3 = -0.5 * vt2;
+      const double gc = gs * cd, bsd = bs * sd, gsd = gs * sd, bcd = bs * cd;
+      const double tv = it * vv, tf = 2.0 * it * vf2t;
+      d_t[0] = tv * (gc + bsd) - tf * (gs + v.br_gfr[l]);
+      d_t[1] = tf * (bs + 0.5 * bc) + tv * (gsd - bcd);
+      d_t[2] = tv * (gc - bsd);
+      d_t[3] = -tv * (gsd + bcd);
     } else {
-      for (int i = 0; i < 4; ++i) d_r[i] = d_x[i] = d_b[i] = d_t[i] = 0.0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) d_r[i] = d_x[i] = d_t[i] = 0.0;
     }
-    const int32_t rows[4] = {v.row_p[f], v.row_q[f], v.row_p[t], v.row_q[t]};
+    const int4 mf = __ldg(v.bus_meta + f), mt = __ldg(v.bus_meta + t);
+    const int32_t rows[4] = {mf.x, mf.y, mt.x, mt.y};
     const int64_t f0 = v.inst_f_off[inst];
+#pragma unroll 4
     for (int c = 0; c < a.n_cot; ++c) {
-      const double *__restrict__ vc = a.v + (int64_t)c * a.n_f + f0;
       double w[4];
-      for (int i = 0; i < 4; ++i) w[i] = rows[i] >= 0 ? vc[rows[i]] : 0.0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) w[i] = rows[i] >= 0 ? cot_at(a.v, a.vt, a.n_cot, a.n_f, c, f0 + rows[i]) : 0.0;
       const int64_t o = (int64_t)c * a.n_bi + q;
       if (a.gr) a.gr[o] = w[0] * d_r[0] + w[1] * d_r[1] + w[2] * d_r[2] + w[3] * d_r[3];
       if (a.gxr) a.gxr[o] = w[0] * d_x[0] + w[1] * d_x[1] + w[2] * d_x[2] + w[3] * d_x[3];
-      if (a.gb) a.gb[o] = w[0] * d_b[0] + w[1] * d_b[1] + w[2] * d_b[2] + w[3] * d_b[3];
+      if (a.gb) a.gb[o] = w[1] * db1 + w[3] * db3;
       if (a.gtap) a.gtap[o] = w[0] * d_t[0] + w[1] * d_t[1] + w[2] * d_t[2] + w[3] * d_t[3];
     }
   }
 }
 
-// one thread per (instance, bus): dF_P/dP_inj = -1, dF_Q/dQ_inj = -1
+// v [n_cot][n_f] -> vt [n_f][n_cot], 32 x 32 tiles through shared memory
+__global__ void __launch_bounds__(256) k_transpose(const double *__restrict__ v, int n_cot, int64_t n_f,
+                                                   double *__restrict__ vt) {
+  __shared__ double tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.x * 32;    // rows of F
+  const int c0 = blockIdx.y * 32;                  // cotangents
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int c = c0 + j;
+    const int64_t r = r0 + threadIdx.x;
+    if (c < n_cot && r < n_f) tile[j][threadIdx.x] = v[(int64_t)c * n_f + r];
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int64_t r = r0 + j;
+    const int c = c0 + threadIdx.x;
+    if (c < n_cot && r < n_f) vt[r * n_cot + c] = tile[threadIdx.x][j];
+  }
+}
+
+// one thread per (cotangent, instance bus): dF_P/dP_inj = -1, dF_Q/dQ_inj = -1
 __global__ void k_vjp_inj(View v, const double *__restrict__ vv, int n_cot, int64_t n_f, double *gp, double *gq) {
+  const int64_t n = (int64_t)n_cot * v.n_bus_inst;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < v.n_bus_inst; q += stride) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+    const int64_t c = t / v.n_bus_inst, q = t - c * v.n_bus_inst;
     const int inst = v.n_inst == 1 ? 0 : find_segment(v.inst_bus_off, v.n_inst, q);
     const int g = v.inst_grid[inst];
     const int64_t b = v.grid_bus_off[g] + (q - v.inst_bus_off[inst]);
-    const int32_t rp = v.row_p[b], rq = v.row_q[b];
-    const int64_t f0 = v.inst_f_off[inst];
-    for (int c = 0; c < n_cot; ++c) {
-      const double *__restrict__ vc = vv + (int64_t)c * n_f + f0;
-      const int64_t o = (int64_t)c * v.n_bus_inst + q;
-      if (gp) gp[o] = rp >= 0 ? -vc[rp] : 0.0;
-      if (gq) gq[o] = rq >= 0 ? -vc[rq] : 0.0;
-    }
+    const int4 bm = __ldg(v.bus_meta + b);
+    const double *__restrict__ vc = vv + c * n_f + v.inst_f_off[inst];
+    if (gp) gp[t] = bm.x >= 0 ? -vc[bm.x] : 0.0;
+    if (gq) gq[t] = bm.y >= 0 ? -vc[bm.y] : 0.0;
   }
+}
+
+template <int CH, bool MASKED>
+int launch_state(const Ctx &c, const VjpArgs &a, cudaStream_t s) {
+  const int64_t cap = c.tuning.ctas_per_sm > 0 ? (int64_t)c.tuning.ctas_per_sm * c.num_sms : INT64_MAX;
+  if (c.v.n_lane_units > 0) {
+    k_vjp_lane<CH, MASKED><<<(unsigned)std::min<int64_t>(c.v.n_lane_units, cap), 32, 0, s>>>(c.v, a);
+    PF_CUDA_TRY(cudaGetLastError());
+  }
+  if (c.v.n_large_units > 0) {
+    k_vjp_large<CH, MASKED><<<(unsigned)std::min<int64_t>(c.v.n_large_units, cap), 32, 0, s>>>(c.v, a);
+    PF_CUDA_TRY(cudaGetLastError());
+  }
+  return PF_OK;
+}
+
+template <int CH>
+int launch_state_ch(const Ctx &c, const VjpArgs &a, bool masked, cudaStream_t s) {
+  return masked ? launch_state<CH, true>(c, a, s) : launch_state<CH, false>(c, a, s);
 }
 
 }  // namespace
@@ -382,44 +510,61 @@ int launch_vjp(Ctx &c, const double *x, const pf_overrides *ov, const double *v,
   if (n_cot <= 0) return fail(PF_ERR_INVALID, "n_cot must be positive");
   const int tb = 256;
   const int64_t cap_blocks = (int64_t)c.num_sms * 16;
-  k_phasor_adj<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((c.v.n_bus_inst + tb - 1) / tb, cap_blocks)),
-                 tb, 0, s>>>(c.v, x);
-  PF_CUDA_TRY(cudaGetLastError());
-  const double2 *gb = c.v.inc_gb, *ac = c.v.inc_ac, *hat = c.v.bus_hat;
-  const uint8_t *status = ov ? ov->status : nullptr;
+  // (cos, sin) and V of every bus: the forward kernels' phasor records
+  PF_TRY(launch_phasor(c.v, c.num_sms, x, s));
+  VjpArgs a{};
+  a.x = x; a.v = v; a.n_cot = n_cot; a.n_f = c.n_f; a.n_x = c.n_x;
+  a.gb = c.v.inc_gb; a.ac = c.v.inc_ac; a.hat = c.v.bus_hat;
+  a.sgb = c.v.slot_gb; a.sgbm = c.v.slot_gbm; a.sac = c.v.slot_ac; a.rhat = c.v.rbus_hat;
+  a.status = ov ? ov->status : nullptr;
   const double *r = nullptr, *xr = nullptr, *b = nullptr, *tap = nullptr;
   if (ov && (ov->br_r || ov->br_x || ov->br_b || ov->br_tap)) {
     r = ov->br_r; xr = ov->br_x; b = ov->br_b; tap = ov->br_tap;
     PF_TRY(compute_coefficients(c, r, xr, b, tap, c.ov_gb, c.ov_ac, c.ov_hat, s));
-    gb = c.ov_gb;
-    ac = c.ov_ac;
-    hat = c.ov_hat;
+    PF_TRY(permute_overrides(c, s));
+    a.gb = c.ov_gb; a.ac = c.ov_ac; a.hat = c.ov_hat;
+    a.sgb = c.ov_slot_gb; a.sgbm = c.ov_slot_gbm; a.sac = c.ov_slot_ac; a.rhat = c.ov_rbus_hat;
+  }
+  // many cotangents: read them from a transposed copy, so that one row's
+  // cotangents are contiguous for the per-bus and per-branch loops
+  if (n_cot >= kVjpTransposeMin && (g->x || g->br_r || g->br_x || g->br_b || g->br_tap)) {
+    const int64_t need = c.n_f * (int64_t)n_cot;
+    if (c.vt_cap < need) {
+      if (c.vt_scratch) cudaFree(c.vt_scratch);
+      c.vt_scratch = nullptr;
+      c.vt_cap = 0;
+      cudaError_t e = cudaMalloc(&c.vt_scratch, need * sizeof(double));
+      if (e != cudaSuccess)
+        return fail(e == cudaErrorMemoryAllocation ? PF_ERR_OOM : PF_ERR_CUDA,
+                    std::string("pf_vjp: allocating the transposed cotangents (make the first call with this "
+                                "many cotangents outside stream capture): ") + cudaGetErrorString(e));
+      c.vt_cap = need;
+    }
+    const dim3 grid((unsigned)((c.n_f + 31) / 32), (unsigned)((n_cot + 31) / 32));
+    k_transpose<<<grid, dim3(32, 8), 0, s>>>(v, n_cot, c.n_f, c.vt_scratch);
+    PF_CUDA_TRY(cudaGetLastError());
+    a.vt = c.vt_scratch;
   }
   if (g->x) {
-    VjpArgs a{};
-    a.x = x; a.v = v; a.n_cot = n_cot; a.n_f = c.n_f; a.gb = gb; a.ac = ac; a.hat = hat;
-    a.status = status; a.gx = g->x; a.n_x = c.n_x; a.cap = c.tuning.tile_inc;
-    View vv = c.v;
-    if (!c.any_outage) vv.inst_outage = nullptr;   // unmasked fast path unless outages exist
-    const size_t smem = (size_t)a.cap * sizeof(double) * 6;
-    if (smem > 46 * 1024)
-      PF_CUDA_TRY(cudaFuncSetAttribute(k_vjp_state, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int64_t grid = c.v.n_units;
-    if (c.tuning.ctas_per_sm > 0) grid = std::min<int64_t>(grid, (int64_t)c.tuning.ctas_per_sm * c.num_sms);
-    k_vjp_state<<<(unsigned)std::max<int64_t>(grid, 1), a.cap, smem, s>>>(vv, a);
-    PF_CUDA_TRY(cudaGetLastError());
+    a.gx = g->x;
+    const bool masked = c.any_outage || a.status != nullptr;
+    if (n_cot >= 16) PF_TRY(launch_state_ch<8>(c, a, masked, s));
+    else if (n_cot >= 4) PF_TRY(launch_state_ch<4>(c, a, masked, s));
+    else PF_TRY(launch_state_ch<1>(c, a, masked, s));
   }
   if (g->br_r || g->br_x || g->br_b || g->br_tap) {
     ParamArgs p{};
-    p.x = x; p.v = v; p.n_cot = n_cot; p.n_f = c.n_f; p.n_bi = c.n_branch_inst;
-    p.r = r; p.xr = xr; p.b = b; p.tap = tap; p.status = status;
+    p.v = v; p.vt = a.vt; p.n_cot = n_cot; p.n_f = c.n_f; p.n_bi = c.n_branch_inst;
+    p.r = r; p.xr = xr; p.b = b; p.tap = tap; p.status = a.status;
     p.gr = g->br_r; p.gxr = g->br_x; p.gb = g->br_b; p.gtap = g->br_tap;
     const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((c.n_branch_inst + tb - 1) / tb, cap_blocks));
-    k_vjp_params<<<(unsigned)blocks, tb, 0, s>>>(c.v, p);
+    if (r || xr || b || tap) k_vjp_params<true><<<(unsigned)blocks, tb, 0, s>>>(c.v, p);
+    else k_vjp_params<false><<<(unsigned)blocks, tb, 0, s>>>(c.v, p);
     PF_CUDA_TRY(cudaGetLastError());
   }
   if (g->p_inj || g->q_inj) {
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((c.v.n_bus_inst + tb - 1) / tb, cap_blocks));
+    const int64_t n = (int64_t)n_cot * c.v.n_bus_inst;
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n + tb - 1) / tb, cap_blocks));
     k_vjp_inj<<<(unsigned)blocks, tb, 0, s>>>(c.v, v, n_cot, c.n_f, g->p_inj, g->q_inj);
     PF_CUDA_TRY(cudaGetLastError());
   }

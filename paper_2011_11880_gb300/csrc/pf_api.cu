@@ -35,8 +35,8 @@ cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
 void free_ctx(pf_ctx *ctx) {
   if (!ctx) return;
   for (void *p : ctx->c.allocations) cudaFree(p);
-  for (void *p : ctx->c.tile_allocations) cudaFree(p);
   if (ctx->c.stage_x) cudaFree(ctx->c.stage_x);
+  if (ctx->c.vt_scratch) cudaFree(ctx->c.vt_scratch);
   if (ctx->c.stage_f) cudaFree(ctx->c.stage_f);
   if (ctx->c.stage_v) cudaFree(ctx->c.stage_v);
   delete ctx;
@@ -234,7 +234,7 @@ int pf_set_tuning(pf_ctx *ctx, const pf_tuning *t, void *stream) {
   if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return fail(PF_ERR_INVALID, "ctas_per_sm must be in [0, 32]");
   cudaStream_t s = as_stream(stream);
   PF_CUDA_TRY(cudaStreamSynchronize(s));
-  if (t->tile_inc != ctx->c.tuning.tile_inc) PF_TRY(pf::build_tiles(ctx->c, t->tile_inc, s));
+  ctx->c.tuning.tile_inc = t->tile_inc;
   ctx->c.tuning.ctas_per_sm = t->ctas_per_sm;
   return PF_OK;
 }

@@ -372,6 +372,24 @@ __global__ void k_net_injection(const double *pg, const double *pl, const double
 }
 
 // per-end coefficients of the rotated branch form (see the evaluation kernel)
+// Per branch, for the adjoint: the series admittance g + j b_s = 1/(r + jx),
+// its derivative with respect to r (dg/dr = (x^2 - r^2)/D^2, db_s/dr = 2 r x/D^2,
+// D = r^2 + x^2; the x-derivatives follow from the Cauchy-Riemann relations),
+// 1/tau, b_c and (cos phi, sin phi).
+__global__ void k_branch_consts(View v, double2 *kgb, double2 *kab, double2 *ktc, double2 *kph) {
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= v.n_branch) return;
+  const double r = v.br_r[l], x = v.br_x[l];
+  const double d = r * r + x * x;
+  const double inv = 1.0 / d;
+  kgb[l] = make_double2(r * inv, -x * inv);
+  kab[l] = make_double2((x * x - r * r) * (inv * inv), 2.0 * r * x * (inv * inv));
+  ktc[l] = make_double2(1.0 / v.br_tap[l], v.br_b[l]);
+  double sp, cp;
+  sincos(v.br_shift[l], &sp, &cp);
+  kph[l] = make_double2(cp, sp);
+}
+
 __global__ void k_coeff(View v, const double *r_ov, const double *x_ov, const double *b_ov, const double *tap_ov,
                         double2 *gb, double2 *ac) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -483,13 +501,6 @@ __global__ void k_pack_inc(View v, const int2 *rt, const int32_t *base_p, const 
                      bq >= 0 && r.x >= 0 ? bq + r.x : -1, bq >= 0 && r.y >= 0 ? bq + r.y : -1);
 }
 
-__global__ void k_tile_desc(View v, const int32_t *bus0, const int32_t *bus1, int64_t n, int4 *desc) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const int32_t b0 = bus0[t], b1 = bus1[t];
-  desc[t] = make_int4(b0, b1, v.inc_ptr[b0], v.inc_ptr[b1]);
-}
-
 __global__ void k_pack2(const double *a, const double *b, int64_t n, double2 *out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = make_double2(a[i], b[i]);
@@ -565,38 +576,10 @@ __global__ void k_cptr(const int64_t *S, const int64_t *grid_nnz_off, const int6
   if (q + 1 == grid_cptr_off[g + 1]) src_len[g] = cptr[q];
 }
 
-// greedy packing of consecutive buses into rounds of at most `cap` branch ends
-// and kRoundBuses buses; a bus with more ends than `cap` forms a round alone.
-__global__ void k_tiles(View v, int cap, const int64_t *tile_off, int32_t *count, int32_t *bus0, int32_t *bus1) {
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= v.n_grids) return;
-  const int64_t b0 = v.grid_bus_off[g], b1 = v.grid_bus_off[g + 1];
-  int64_t t = tile_off ? tile_off[g] : 0;
-  int32_t n = 0;
-  int64_t start = b0;
-  int32_t inc = 0, nb = 0;
-  for (int64_t b = b0; b < b1; ++b) {
-    const int32_t d = v.inc_ptr[b + 1] - v.inc_ptr[b];
-    if (nb > 0 && (inc + d > cap || nb + 1 > kRoundBuses)) {
-      if (bus0) { bus0[t] = (int32_t)start; bus1[t] = (int32_t)b; ++t; }
-      ++n;
-      start = b;
-      inc = 0;
-      nb = 0;
-    }
-    inc += d;
-    ++nb;
-  }
-  if (bus0) { bus0[t] = (int32_t)start; bus1[t] = (int32_t)b1; }
-  ++n;
-  if (count) count[g] = n;
-}
+// ---- rounds of the evaluation kernels ----------------------------------------------------
 
-
-// ---- rounds of the fused kernel ----------------------------------------------------
-
-// sort key: grid, then degree class (degree, or kLaneMaxDegree + 1 for a bus
-// with more ends), then bus id
+// sort key: grid, then class (number of neighbours, or kLaneMaxDegree + 1
+// for a bus with more), then bus id
 __global__ void k_round_keys(View v, uint64_t *keys, uint32_t *vals) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= v.n_bus) return;
@@ -729,23 +712,26 @@ __global__ void k_rec_base(View v, int64_t *base) {
 
 // per slot: the coefficients of its group of parallel branches, summed in
 // incidence order (the merged branch end of the pair of buses)
-__global__ void k_slot_coeff(int64_t n_slots, const int4 *smeta, const double2 *gb, const double2 *ac, double2 *sgb,
-                             double2 *sac) {
+__global__ void k_slot_coeff(View v, int64_t n_slots, const int4 *smeta, const double2 *gb, const double2 *ac,
+                             double2 *sgb, double2 *sac, double2 *sgbm) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n_slots) return;
   const int4 m = smeta[q];
   if (m.y > 0) {
-    double2 g = gb[m.w], a = ac[m.w];
+    double2 g = gb[m.w], a = ac[m.w], gm = gb[v.inc_mirror[m.w]];
     for (int32_t i = 1; i < m.y; ++i) {
-      const double2 gi = gb[m.w + i], ai = ac[m.w + i];
+      const double2 gi = gb[m.w + i], ai = ac[m.w + i], mi = gb[v.inc_mirror[m.w + i]];
       g = make_double2(__dadd_rn(g.x, gi.x), __dadd_rn(g.y, gi.y));
       a = make_double2(__dadd_rn(a.x, ai.x), __dadd_rn(a.y, ai.y));
+      gm = make_double2(__dadd_rn(gm.x, mi.x), __dadd_rn(gm.y, mi.y));
     }
     sgb[q] = g;
     sac[q] = a;
+    sgbm[q] = gm;
   } else {
     sgb[q] = make_double2(0.0, 0.0);
     sac[q] = make_double2(0.0, 0.0);
+    sgbm[q] = make_double2(0.0, 0.0);
   }
 }
 
@@ -806,55 +792,6 @@ int compute_coefficients(Ctx &c, const double *r, const double *x, const double 
   return PF_OK;
 }
 
-// --------------------------------------------------------------------------
-// tiles
-// --------------------------------------------------------------------------
-
-int build_tiles(Ctx &c, int tile_inc, cudaStream_t s) {
-  const int G = c.v.n_grids;
-  int32_t *cnt;
-  TempList tmp;
-  PF_TRY(tmp.alloc(&cnt, G));
-  k_tiles<<<nblk(G, 128), 128, 0, s>>>(c.v, tile_inc, nullptr, cnt, nullptr, nullptr);
-  PF_CUDA_TRY(cudaGetLastError());
-  int rc = PF_OK;
-  std::vector<int32_t> hc = to_host(cnt, G, s, &rc);
-  if (rc) return rc;
-  for (void *p : c.tile_allocations) cudaFree(p);
-  c.tile_allocations.clear();
-  c.grid_tile_off.assign(G + 1, 0);
-  for (int g = 0; g < G; ++g) c.grid_tile_off[g + 1] = c.grid_tile_off[g] + hc[g];
-  c.n_tiles = c.grid_tile_off[G];
-  PF_TRY(dev_alloc(c, &c.tile_bus0, c.n_tiles, &c.tile_allocations));
-  PF_TRY(dev_alloc(c, &c.tile_bus1, c.n_tiles, &c.tile_allocations));
-  PF_TRY(dev_alloc(c, &c.tile_desc, c.n_tiles, &c.tile_allocations));
-  PF_TRY(dev_alloc(c, &c.grid_tile_off_d, G + 1, &c.tile_allocations));
-  PF_CUDA_TRY(cudaMemcpyAsync(c.grid_tile_off_d, c.grid_tile_off.data(), (G + 1) * sizeof(int64_t),
-                              cudaMemcpyHostToDevice, s));
-  k_tiles<<<nblk(G, 128), 128, 0, s>>>(c.v, tile_inc, c.grid_tile_off_d, nullptr, c.tile_bus0, c.tile_bus1);
-  k_tile_desc<<<nblk(c.n_tiles), TB, 0, s>>>(c.v, c.tile_bus0, c.tile_bus1, c.n_tiles, c.tile_desc);
-  PF_CUDA_TRY(cudaGetLastError());
-  const int I = c.v.n_inst;
-  c.unit_off.assign(I + 1, 0);
-  for (int i = 0; i < I; ++i) {
-    const int g = c.inst_grid[i];
-    c.unit_off[i + 1] = c.unit_off[i] + (c.grid_tile_off[g + 1] - c.grid_tile_off[g]);
-  }
-  PF_TRY(dev_alloc(c, &c.inst_unit_off_d, I + 1, &c.tile_allocations));
-  PF_CUDA_TRY(cudaMemcpyAsync(c.inst_unit_off_d, c.unit_off.data(), (I + 1) * sizeof(int64_t),
-                              cudaMemcpyHostToDevice, s));
-  c.v.tile_bus0 = c.tile_bus0;
-  c.v.tile_bus1 = c.tile_bus1;
-  c.v.tile_desc = c.tile_desc;
-  c.v.grid_tile_off = c.grid_tile_off_d;
-  c.v.inst_unit_off = c.inst_unit_off_d;
-  c.v.n_units = c.unit_off[I];
-  c.tuning.tile_inc = tile_inc;
-  PF_CUDA_TRY(cudaStreamSynchronize(s));
-  return PF_OK;
-}
-
-
 // ---- rounds of the fused kernel: buses sorted by degree, 32 per round ---------------
 
 int build_rounds(Ctx &c, cudaStream_t s) {
@@ -908,11 +845,13 @@ int build_rounds(Ctx &c, cudaStream_t s) {
   const int64_t NS = total[0];
   c.n_slots = NS;
   int4 *smeta, *spos, *m1, *m2;
-  double2 *sgb, *sac, *rh, *ri;
+  double2 *sgb, *sac, *sgbm, *rh, *ri;
   PF_TRY(dev_alloc(c, &smeta, NS));
   PF_TRY(dev_alloc(c, &spos, NS));
   PF_TRY(dev_alloc(c, &sgb, NS));
   PF_TRY(dev_alloc(c, &sac, NS));
+  PF_TRY(dev_alloc(c, &sgbm, NS));
+  PF_TRY(dev_alloc(c, &c.ov_slot_gbm, NS));
   PF_TRY(dev_alloc(c, &m1, 32 * R));
   PF_TRY(dev_alloc(c, &m2, 32 * R));
   PF_TRY(dev_alloc(c, &rh, 32 * R));
@@ -922,7 +861,7 @@ int build_rounds(Ctx &c, cudaStream_t s) {
   PF_TRY(dev_alloc(c, &c.ov_rbus_hat, 32 * R));
   if (NS > 0) {
     k_slot_fill<<<nblk(32 * R), TB, 0, s>>>(v, R, desc, rbus, smeta, spos);
-    k_slot_coeff<<<nblk(NS), TB, 0, s>>>(NS, smeta, v.inc_gb, v.inc_ac, sgb, sac);
+    k_slot_coeff<<<nblk(NS), TB, 0, s>>>(v, NS, smeta, v.inc_gb, v.inc_ac, sgb, sac, sgbm);
     PF_CUDA_TRY(cudaGetLastError());
   }
   k_rbus_fill<<<nblk(32 * R), TB, 0, s>>>(v, 32 * R, rbus, v.bus_hat, m1, m2, rh, ri);
@@ -938,6 +877,7 @@ int build_rounds(Ctx &c, cudaStream_t s) {
   v.slot_pos = spos;
   v.slot_gb = sgb;
   v.slot_ac = sac;
+  v.slot_gbm = sgbm;
   if (c.n_rounds >= 0x7fffffffLL / 32) return fail(PF_ERR_UNSUPPORTED, "too many evaluation rounds");
   // units of work: the rounds of 32 buses and the large buses of every instance
   const int I = v.n_inst;
@@ -972,8 +912,8 @@ int build_rounds(Ctx &c, cudaStream_t s) {
 
 int permute_overrides(Ctx &c, cudaStream_t s) {
   if (c.n_slots > 0) {
-    k_slot_coeff<<<nblk(c.n_slots), TB, 0, s>>>(c.n_slots, c.v.slot_meta, c.ov_gb, c.ov_ac, c.ov_slot_gb,
-                                                c.ov_slot_ac);
+    k_slot_coeff<<<nblk(c.n_slots), TB, 0, s>>>(c.v, c.n_slots, c.v.slot_meta, c.ov_gb, c.ov_ac, c.ov_slot_gb,
+                                                c.ov_slot_ac, c.ov_slot_gbm);
     PF_CUDA_TRY(cudaGetLastError());
   }
   k_rbus_fill<<<nblk(32 * c.n_rounds), TB, 0, s>>>(c.v, 32 * c.n_rounds, c.v.rbus, c.ov_hat, nullptr, nullptr,
@@ -1452,7 +1392,19 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
     PF_TRY(upload(c, &d_tab, tab, s));
     v.sincos_tab = d_tab;
   }
-  PF_TRY(build_tiles(c, 64, s));
+  {
+    const int64_t M = v.n_branch;
+    double2 *kgb, *kab, *ktc, *kph;
+    PF_TRY(dev_alloc(c, &kgb, M));
+    PF_TRY(dev_alloc(c, &kab, M));
+    PF_TRY(dev_alloc(c, &ktc, M));
+    PF_TRY(dev_alloc(c, &kph, M));
+    if (M > 0) {
+      k_branch_consts<<<nblk(M), TB, 0, s>>>(v, kgb, kab, ktc, kph);
+      PF_CUDA_TRY(cudaGetLastError());
+    }
+    v.br_k_gb = kgb; v.br_k_ab = kab; v.br_k_tc = ktc; v.br_k_ph = kph;
+  }
   PF_TRY(build_rounds(c, s));
   PF_CUDA_TRY(cudaStreamSynchronize(s));
   return PF_OK;

@@ -526,15 +526,6 @@ void built_coefficients(const View &v, EvalArgs &a) {
   a.rhat = v.rbus_hat;
 }
 
-int launch_phasor(const View &v, int num_sms, const double *x, cudaStream_t s) {
-  const int tb = 256;
-  int64_t blocks = (v.n_bus_inst + tb - 1) / tb;
-  blocks = std::min<int64_t>(blocks, (int64_t)num_sms * 16);
-  k_phasor<<<(unsigned)std::max<int64_t>(blocks, 1), tb, 0, s>>>(v, x);
-  PF_CUDA_TRY(cudaGetLastError());
-  return PF_OK;
-}
-
 __global__ void k_sincos(const double *__restrict__ t, int64_t n, const double2 *__restrict__ tab,
                          double *__restrict__ c, double *__restrict__ sn) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -545,6 +536,15 @@ __global__ void k_sincos(const double *__restrict__ t, int64_t n, const double2 
 }
 
 }  // namespace
+
+int launch_phasor(const View &v, int num_sms, const double *x, cudaStream_t s) {
+  const int tb = 256;
+  int64_t blocks = (v.n_bus_inst + tb - 1) / tb;
+  blocks = std::min<int64_t>(blocks, (int64_t)num_sms * 16);
+  k_phasor<<<(unsigned)std::max<int64_t>(blocks, 1), tb, 0, s>>>(v, x);
+  PF_CUDA_TRY(cudaGetLastError());
+  return PF_OK;
+}
 
 int launch_eval(Ctx &c, const double *x, const pf_overrides *ov, double *F, double *vals, cudaStream_t s) {
   return launch_eval_stages(c, 3, x, ov, F, vals, s);

@@ -18,16 +18,14 @@
 namespace pf {
 
 constexpr int kNumSMsDefault = 152;
-// A round (the unit one warp evaluates) holds up to kRoundBuses whole buses
-// and up to `tile_inc` branch ends (32, 64, 96 or 128: 1-4 ends per lane); a
-// bus with more ends forms a round of its own, evaluated in chunks.
-constexpr int kRoundBuses = 32;
+// `tile_inc` (32, 64, 96 or 128) sets how many slots each lane of the fused
+// kernel fetches ahead (tile_inc / 32) and the chunk of a large bus.
 constexpr int kMaxTileInc = 128;
 constexpr int kMinTileInc = 32;
 constexpr int kMaxGroup = 32;      // parallel branches between one pair of buses
-// The fused kernel evaluates rounds of 32 buses of equal (or adjacent)
-// degree, one bus per lane; a bus with more than kLaneMaxDegree ends forms a
-// round of its own, evaluated by the whole warp.
+// The evaluation kernels work on rounds of 32 buses with equal (or adjacent)
+// numbers of neighbours, one bus per lane; a bus with more than
+// kLaneMaxDegree neighbours is evaluated by a whole warp.
 constexpr int kLaneMaxDegree = 32;
 constexpr int kSinCosTable = 1024;  // table of (cos, sin)(i pi / 512)
 
@@ -52,12 +50,11 @@ int fail(int code, const std::string &msg);
 // Device error flag bits (set with integer atomics).
 constexpr int kErrMap = 1;      // an index-map entry failed a consistency check
 constexpr int kErrTimeout = 2;  // a bounded wait gave up
-constexpr int kErrChunk = 4;    // a tile could not be cut at a parallel-group boundary
 
 struct View {
   int formulation;
   int n_grids, n_inst;
-  int64_t n_bus, n_branch, n_inc, n_units, n_bus_inst;
+  int64_t n_bus, n_branch, n_inc, n_bus_inst;
   int64_t n_lane_units;     // sum over instances of the rounds of 32 buses of its grid
   int64_t n_large_units;    // sum over instances of the buses with more than 32 ends
 
@@ -80,6 +77,9 @@ struct View {
   // per branch
   const int32_t *br_from, *br_to;   // global bus ids
   const double *br_r, *br_x, *br_b, *br_tap, *br_shift, *br_gfr, *br_gto;
+  // per branch, for the adjoint: (g, b_s) = 1/(r + jx), (alpha, beta) = d(g, b_s)/dr,
+  // (1/tau, b_c), (cos phi, sin phi)
+  const double2 *br_k_gb, *br_k_ab, *br_k_tc, *br_k_ph;
   const uint8_t *br_status;
 
   // per incidence, sorted by (own bus, other bus, branch)
@@ -103,11 +103,6 @@ struct View {
   const int32_t *gen_pos;                     // [sum ngen] CSR position of the g_V entry
   const int32_t *gen_bus;                     // [sum ngen] global bus of each generator
 
-  // tiles (contiguous bus ranges; one warp round each)
-  const int32_t *tile_bus0, *tile_bus1;
-  const int4 *tile_desc;                      // {first bus, end bus, first end, end end}
-  const int64_t *grid_tile_off;               // [n_grids+1]
-
   // rounds of the fused kernel (per grid, buses sorted by degree)
   const int64_t *grid_round_off;              // [n_grids+1]
   const int4 *unit_rec;                       // per round of 32 buses of every instance:
@@ -123,11 +118,11 @@ struct View {
                                               //   {other bus, group length (-1 padding), code and index of its first end}
   const int4 *slot_pos;                       // the group's four CSR positions
   const double2 *slot_gb, *slot_ac;           // the group's coefficients summed in incidence order
+  const double2 *slot_gbm;                    // the same for the group's mirror ends (at the other bus)
 
   // per instance
   const int32_t *inst_grid, *inst_outage;     // outage: global branch id or -1
   const int64_t *inst_x_off, *inst_f_off, *inst_v_off, *inst_bus_off, *inst_br_off;
-  const int64_t *inst_unit_off;               // [n_inst+1] tiles of earlier instances
 
   // scratch
   double2 *phasor;                            // [2 n_bus_inst]: (cos theta, sin theta), (V, 0) per bus
@@ -140,14 +135,14 @@ struct Ctx {
   int num_sms = kNumSMsDefault;
   pf_tuning tuning{64, 0};
   int max_degree = 0, max_group = 0;
-  int64_t n_x = 0, n_f = 0, nnz = 0, n_branch_inst = 0, n_tiles = 0;
+  int64_t n_x = 0, n_f = 0, nnz = 0, n_branch_inst = 0;
 
   // host copies of per-grid / per-instance layout
   std::vector<int64_t> grid_bus_off, grid_br_off, grid_row_off, grid_nnz_off, grid_cptr_off,
-      grid_csrc_off, grid_sh_off, grid_tile_off;
+      grid_csrc_off, grid_sh_off;
   std::vector<int32_t> grid_nf, grid_nnz, grid_nx, grid_nshunt;
   std::vector<int32_t> inst_grid, inst_outage;
-  std::vector<int64_t> x_off, f_off, v_off, bus_off, br_off, unit_off;
+  std::vector<int64_t> x_off, f_off, v_off, bus_off, br_off;
   bool any_outage = false;
 
   // device arrays not in View
@@ -155,23 +150,21 @@ struct Ctx {
   int32_t *colind = nullptr;       // per grid nnz entries, at grid_nnz_off
   int64_t *contrib_ptr = nullptr;  // per grid nnz+1 local entries, at grid_cptr_off
   int32_t *contrib_src = nullptr;  // at grid_csrc_off
-  int32_t *tile_bus0 = nullptr, *tile_bus1 = nullptr;
-  int4 *tile_desc = nullptr;
-  int64_t *grid_tile_off_d = nullptr;
-  int64_t *inst_unit_off_d = nullptr;
 
   // override scratch (coefficients recomputed from per-call parameters), in
   // incidence order and permuted to slot / round order
   double2 *ov_gb = nullptr, *ov_ac = nullptr, *ov_hat = nullptr;
-  double2 *ov_slot_gb = nullptr, *ov_slot_ac = nullptr, *ov_rbus_hat = nullptr;
+  double2 *ov_slot_gb = nullptr, *ov_slot_ac = nullptr, *ov_slot_gbm = nullptr, *ov_rbus_hat = nullptr;
   int64_t n_slots = 0, n_rounds = 0;
   std::vector<int64_t> grid_round_off;
 
   // host-call staging, allocated on first use
   double *stage_x = nullptr, *stage_f = nullptr, *stage_v = nullptr;
+  // transposed cotangents of pf_vjp, allocated on first use and grown
+  double *vt_scratch = nullptr;
+  int64_t vt_cap = 0;
 
   std::vector<void *> allocations;
-  std::vector<void *> tile_allocations;
 };
 
 template <class T>
@@ -199,9 +192,10 @@ int upload(Ctx &c, T **p, const std::vector<T> &h, cudaStream_t s) {
 // ---- build (pf_build.cu) ----
 int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance *inst,
                   int n_inst, int formulation, cudaStream_t s);
-int build_tiles(Ctx &c, int tile_inc, cudaStream_t s);
 // Copies per-call coefficients (incidence / bus order) into slot / round order.
 int permute_overrides(Ctx &c, cudaStream_t s);
+// (cos theta, sin theta) and V of every instance bus into v.phasor (pf_eval.cu).
+int launch_phasor(const View &v, int num_sms, const double *x, cudaStream_t s);
 // Per-end coefficients (G, B, A, C) and per-bus sums (A^, C^) from the branch
 // parameters; any of r, x, b, tap may be overridden by device arrays.
 int compute_coefficients(Ctx &c, const double *r, const double *x, const double *b,
