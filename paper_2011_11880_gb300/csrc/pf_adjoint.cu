@@ -79,14 +79,18 @@ __device__ __forceinline__ bool end_in(const View &v, int32_t e, int32_t outage,
 // each summed in incidence order (zero when none is in service).
 struct PairCoeff {
   double2 gb, ac, gbm;
+  bool any_out;
 };
 
 __device__ __forceinline__ PairCoeff masked_pair(const View &v, const VjpArgs &a, int32_t e, int32_t len,
                                                  int32_t outage, int64_t st_base) {
-  PairCoeff r{make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+  PairCoeff r{make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0), false};
   bool first = true;
   for (int32_t i = 0; i < len; ++i) {
-    if (!end_in(v, e + i, outage, a.status, st_base)) continue;
+    if (!end_in(v, e + i, outage, a.status, st_base)) {
+      r.any_out = true;
+      continue;
+    }
     const double2 g = __ldg(a.gb + e + i), c = __ldg(a.ac + e + i), m = __ldg(a.gb + v.inc_mirror[e + i]);
     if (first) {
       r.gb = g; r.ac = c; r.gbm = m;
@@ -150,7 +154,12 @@ __device__ __forceinline__ void write_state_grad(const View &v, const VjpArgs &a
 template <int CH, bool MASKED>
 __global__ void __launch_bounds__(32) k_vjp_lane(View v, VjpArgs a) {
   const int lane = threadIdx.x & 31;
-  for (int64_t u = blockIdx.x; u < v.n_lane_units; u += gridDim.x) {
+  const int n_chunks = (a.n_cot + CH - 1) / CH;
+  const int64_t n_work = v.n_lane_units * n_chunks;
+  for (int64_t w = blockIdx.x; w < n_work; w += gridDim.x) {
+    // unit of work: one round and one chunk of CH cotangents
+    const int64_t u = w % v.n_lane_units;
+    const int c0 = (int)(w / v.n_lane_units) * CH;
     const int4 ur = __ldg(v.unit_rec + u);
     const int inst = ur.x;
     const int64_t r = ur.y;
@@ -171,21 +180,24 @@ __global__ void __launch_bounds__(32) k_vjp_lane(View v, VjpArgs a) {
     const double2 po = rec[2 * o];
     const double vo = rec[2 * o + 1].x;
 
-    // bus sums over the own ends (the forward kernel's a, b; A^, C^ under a mask)
-    double sa = 0.0, sb = 0.0, sma = 0.0, smc = 0.0;
+    // bus sums over the own ends (the forward kernel's a, b)
+    double sa = 0.0, sb = 0.0;
+    bool any_out = false;                        // masked: an end of this bus is out of service
     for (int32_t j = 0; j < D; ++j) {
       const int64_t q = q0 + 32 * j;
       const int4 meta = __ldg(v.slot_meta + q);
       if (meta.y < 0) continue;
-      double2 G = __ldg(a.sgb + q), AC = make_double2(0.0, 0.0);
+      double2 G = __ldg(a.sgb + q);
       if (MASKED) {
-        AC = __ldg(a.sac + q);
         if (meta.y == 1) {
-          if (!end_in(v, meta.w, outage, a.status, st_base)) G = AC = make_double2(0.0, 0.0);
+          if (!end_in(v, meta.w, outage, a.status, st_base)) {
+            G = make_double2(0.0, 0.0);
+            any_out = true;
+          }
         } else {
           const PairCoeff pc = masked_pair(v, a, meta.w, meta.y, outage, st_base);
           G = pc.gb;
-          AC = pc.ac;
+          any_out |= pc.any_out;
         }
       }
       const int32_t k = meta.x;
@@ -194,26 +206,32 @@ __global__ void __launch_bounds__(32) k_vjp_lane(View v, VjpArgs a) {
       const Terms t = rotated(G, po, pk);
       sa = __dadd_rn(sa, __dmul_rn(vk, t.xh));
       sb = __dadd_rn(sb, __dmul_rn(vk, t.yh));
-      if (MASKED) {
-        sma = __dadd_rn(sma, AC.x);
-        smc = __dadd_rn(smc, AC.y);
+    }
+    // A^, C^: built, or re-summed over the ends in service in the built order
+    double2 hat = __ldg(a.rhat + rb);
+    if (MASKED && any_out) {
+      double ma = 0.0, mc = 0.0;
+      for (int32_t j = 0; j < D; ++j) {
+        const int64_t q = q0 + 32 * j;
+        const int4 meta = __ldg(v.slot_meta + q);
+        if (meta.y < 0) continue;
+        double2 AC;
+        if (meta.y == 1)
+          AC = end_in(v, meta.w, outage, a.status, st_base) ? __ldg(a.sac + q) : make_double2(0.0, 0.0);
+        else
+          AC = masked_pair(v, a, meta.w, meta.y, outage, st_base).ac;
+        ma = __dadd_rn(ma, AC.x);
+        mc = __dadd_rn(mc, AC.y);
       }
-    }
-    double ah, ch;
-    if (MASKED) {
       const double2 sh = __ldg(v.bus_sh + o);
-      ah = __dadd_rn(sma, sh.x);
-      ch = __dadd_rn(smc, sh.y);
-    } else {
-      const double2 h = __ldg(a.rhat + rb);
-      ah = h.x;
-      ch = h.y;
+      hat = make_double2(__dadd_rn(ma, sh.x), __dadd_rn(mc, sh.y));
     }
+    const double ah = hat.x, ch = hat.y;
     const double two_vo = __dadd_rn(vo, vo);
     const double d_pt = __dmul_rn(vo, sb), d_qt = __dmul_rn(-vo, sa);
     const double d_pv = __fma_rn(two_vo, ah, -sa), d_qv = __fma_rn(-two_vo, ch, -sb);
 
-    for (int c0 = 0; c0 < a.n_cot; c0 += CH) {
+    {
       double gt[CH], gvv[CH];
 #pragma unroll
       for (int i = 0; i < CH; ++i) {
@@ -374,10 +392,17 @@ struct ParamArgs {
 // respect to g, b_s, b_c and tau are formed once and dotted with the
 // cotangent entries of the four rows for every cotangent.  OVR: the
 // constants come from per-call parameters instead of the build.
+constexpr int kParamChunk = 16;   // cotangents per thread of k_vjp_params
+
 template <bool OVR>
-__global__ void k_vjp_params(View v, ParamArgs a) {
+__global__ void __launch_bounds__(128) k_vjp_params(View v, ParamArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.n_bi; q += stride) {
+  const int n_chunks = (a.n_cot + kParamChunk - 1) / kParamChunk;
+  const int64_t n_work = a.n_bi * n_chunks;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_work; w += stride) {
+    const int64_t q = w % a.n_bi;
+    const int c0 = (int)(w / a.n_bi) * kParamChunk;
+    const int c1 = min(a.n_cot, c0 + kParamChunk);
     const int inst = v.n_inst == 1 ? 0 : find_segment(v.inst_br_off, v.n_inst, q);
     const int g = v.inst_grid[inst];
     const int64_t l = v.grid_br_off[g] + (q - v.inst_br_off[inst]);   // global branch
@@ -435,7 +460,7 @@ __global__ void k_vjp_params(View v, ParamArgs a) {
     const int32_t rows[4] = {mf.x, mf.y, mt.x, mt.y};
     const int64_t f0 = v.inst_f_off[inst];
 #pragma unroll 4
-    for (int c = 0; c < a.n_cot; ++c) {
+    for (int c = c0; c < c1; ++c) {
       double w[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) w[i] = rows[i] >= 0 ? cot_at(a.v, a.vt, a.n_cot, a.n_f, c, f0 + rows[i]) : 0.0;
@@ -469,10 +494,10 @@ __global__ void __launch_bounds__(256) k_transpose(const double *__restrict__ v,
 
 // one thread per (cotangent, instance bus): dF_P/dP_inj = -1, dF_Q/dQ_inj = -1
 __global__ void k_vjp_inj(View v, const double *__restrict__ vv, int n_cot, int64_t n_f, double *gp, double *gq) {
-  const int64_t n = (int64_t)n_cot * v.n_bus_inst;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
-    const int64_t c = t / v.n_bus_inst, q = t - c * v.n_bus_inst;
+  for (int c = blockIdx.y; c < n_cot; c += gridDim.y)
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < v.n_bus_inst; q += stride) {
+    const int64_t t = (int64_t)c * v.n_bus_inst + q;
     const int inst = v.n_inst == 1 ? 0 : find_segment(v.inst_bus_off, v.n_inst, q);
     const int g = v.inst_grid[inst];
     const int64_t b = v.grid_bus_off[g] + (q - v.inst_bus_off[inst]);
@@ -487,7 +512,8 @@ template <int CH, bool MASKED>
 int launch_state(const Ctx &c, const VjpArgs &a, cudaStream_t s) {
   const int64_t cap = c.tuning.ctas_per_sm > 0 ? (int64_t)c.tuning.ctas_per_sm * c.num_sms : INT64_MAX;
   if (c.v.n_lane_units > 0) {
-    k_vjp_lane<CH, MASKED><<<(unsigned)std::min<int64_t>(c.v.n_lane_units, cap), 32, 0, s>>>(c.v, a);
+    const int64_t work = c.v.n_lane_units * ((a.n_cot + CH - 1) / CH);
+    k_vjp_lane<CH, MASKED><<<(unsigned)std::min<int64_t>(work, cap), 32, 0, s>>>(c.v, a);
     PF_CUDA_TRY(cudaGetLastError());
   }
   if (c.v.n_large_units > 0) {
@@ -557,15 +583,16 @@ int launch_vjp(Ctx &c, const double *x, const pf_overrides *ov, const double *v,
     p.v = v; p.vt = a.vt; p.n_cot = n_cot; p.n_f = c.n_f; p.n_bi = c.n_branch_inst;
     p.r = r; p.xr = xr; p.b = b; p.tap = tap; p.status = a.status;
     p.gr = g->br_r; p.gxr = g->br_x; p.gb = g->br_b; p.gtap = g->br_tap;
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((c.n_branch_inst + tb - 1) / tb, cap_blocks));
-    if (r || xr || b || tap) k_vjp_params<true><<<(unsigned)blocks, tb, 0, s>>>(c.v, p);
-    else k_vjp_params<false><<<(unsigned)blocks, tb, 0, s>>>(c.v, p);
+    const int64_t work = c.n_branch_inst * ((n_cot + kParamChunk - 1) / kParamChunk);
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((work + 127) / 128, cap_blocks * 2));
+    if (r || xr || b || tap) k_vjp_params<true><<<(unsigned)blocks, 128, 0, s>>>(c.v, p);
+    else k_vjp_params<false><<<(unsigned)blocks, 128, 0, s>>>(c.v, p);
     PF_CUDA_TRY(cudaGetLastError());
   }
   if (g->p_inj || g->q_inj) {
-    const int64_t n = (int64_t)n_cot * c.v.n_bus_inst;
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n + tb - 1) / tb, cap_blocks));
-    k_vjp_inj<<<(unsigned)blocks, tb, 0, s>>>(c.v, v, n_cot, c.n_f, g->p_inj, g->q_inj);
+    const int64_t bx = std::max<int64_t>(1, std::min<int64_t>((c.v.n_bus_inst + tb - 1) / tb, cap_blocks));
+    const int by = (int)std::min<int64_t>(n_cot, std::max<int64_t>(1, cap_blocks / bx));
+    k_vjp_inj<<<dim3((unsigned)bx, (unsigned)by), tb, 0, s>>>(c.v, v, n_cot, c.n_f, g->p_inj, g->q_inj);
     PF_CUDA_TRY(cudaGetLastError());
   }
   return PF_OK;

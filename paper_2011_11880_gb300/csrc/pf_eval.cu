@@ -172,14 +172,18 @@ __device__ __forceinline__ void write_group(const View &v, const EvalArgs &a, in
 // (zero when none is in service).
 struct GroupCoeff {
   double2 gb, ac;
+  bool any_out;
 };
 
 __device__ __forceinline__ GroupCoeff masked_group(const View &v, const EvalArgs &a, int32_t e, int32_t len,
                                                    int32_t outage, int64_t st_base) {
-  GroupCoeff r{make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+  GroupCoeff r{make_double2(0.0, 0.0), make_double2(0.0, 0.0), false};
   bool first = true;
   for (int32_t i = 0; i < len; ++i) {
-    if (!end_in_service(v, e + i, outage, a.status, st_base)) continue;
+    if (!end_in_service(v, e + i, outage, a.status, st_base)) {
+      r.any_out = true;
+      continue;
+    }
     const double2 gi = __ldg(a.gb + e + i), ci = __ldg(a.ac + e + i);
     if (first) {
       r.gb = gi;
@@ -191,6 +195,29 @@ __device__ __forceinline__ GroupCoeff masked_group(const View &v, const EvalArgs
     }
   }
   return r;
+}
+
+// Under an outage mask, for a bus (lane slots q0 + 32 j, j < D) with an end
+// out of service: A^ and C^ summed over its groups' ends in service (groups
+// merged in incidence order, then summed in list order, as k_hat builds
+// them), plus the shunt.
+__device__ __forceinline__ double2 masked_hat(const View &v, const EvalArgs &a, int64_t q0, int32_t D,
+                                           int32_t outage, int64_t st_base, int32_t o) {
+  double sa = 0.0, sc = 0.0;
+  for (int32_t j = 0; j < D; ++j) {
+    const int4 m = __ldg(v.slot_meta + q0 + 32 * j);
+    if (m.y < 0) continue;
+    double2 ac;
+    if (m.y == 1) {
+      ac = end_in_service(v, m.w, outage, a.status, st_base) ? __ldg(a.sac + q0 + 32 * j) : make_double2(0.0, 0.0);
+    } else {
+      ac = masked_group(v, a, m.w, m.y, outage, st_base).ac;
+    }
+    sa = __dadd_rn(sa, ac.x);
+    sc = __dadd_rn(sc, ac.y);
+  }
+  const double2 sh = __ldg(v.bus_sh + o);
+  return make_double2(__dadd_rn(sa, sh.x), __dadd_rn(sc, sh.y));
 }
 
 // F rows, the extended formulation's extra rows and the diagonal of J for
@@ -281,10 +308,11 @@ __global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArg
       o = __ldg(v.rbus + rb);
       bm = __ldg(v.rbus_meta + rb);
       bm2 = __ldg(v.rbus_meta2 + rb);
-      if (!MASKED) hat = __ldg(a.rhat + rb);
+      hat = __ldg(a.rhat + rb);
       if (WF) inj = __ldg(v.rbus_inj + rb);
     }
-    double acc_a = 0.0, acc_b = 0.0, acc_ma = 0.0, acc_mc = 0.0;
+    double acc_a = 0.0, acc_b = 0.0;
+    bool any_out = false;                        // masked: an end of this bus is out of service
     double2 po = make_double2(0.0, 0.0);
     double vo = 0.0;
     const int32_t D = ur.w & 0xff;
@@ -292,7 +320,7 @@ __global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArg
 
     for (int32_t j0 = 0; j0 < D; j0 += ITEMS) {
       int4 meta[ITEMS], pos[ITEMS];
-      double2 G[ITEMS], AC[ITEMS];
+      double2 G[ITEMS];
 #pragma unroll
       for (int it = 0; it < ITEMS; ++it) {
         meta[it] = make_int4(0, -1, 0, 0);
@@ -301,7 +329,6 @@ __global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArg
           meta[it] = __ldg(v.slot_meta + q);
           if (WJ) pos[it] = __ldg(v.slot_pos + q);
           G[it] = __ldg(a.sgb + q);
-          if (MASKED) AC[it] = __ldg(a.sac + q);
         }
       }
       if (j0 == 0) {
@@ -323,12 +350,12 @@ __global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArg
             const int32_t l = meta[it].z >> 1;
             if (l == outage || (a.status != nullptr && a.status[st_base + l] == 0)) {
               Gi = make_double2(0.0, 0.0);
-              AC[it] = make_double2(0.0, 0.0);
+              any_out = true;
             }
           } else {
             const GroupCoeff mg = masked_group(v, a, meta[it].w, len, outage, st_base);
             Gi = mg.gb;
-            AC[it] = mg.ac;
+            any_out |= mg.any_out;
           }
         }
         const double2 pk = rec[2 * k];
@@ -337,10 +364,6 @@ __global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArg
         const double ea = __dmul_rn(vk, tm.xh), eb = __dmul_rn(vk, tm.yh);
         acc_a = __dadd_rn(acc_a, ea);
         acc_b = __dadd_rn(acc_b, eb);
-        if (MASKED) {
-          acc_ma = __dadd_rn(acc_ma, AC[it].x);
-          acc_mc = __dadd_rn(acc_mc, AC[it].y);
-        }
         if (WJ) {
           const int4 p = pos[it];
           if (p.x >= 0) vi[p.x] = __dmul_rn(-vo, eb);
@@ -355,17 +378,11 @@ __global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArg
       if (owner) vo = rec[2 * o + 1].x;
     }
     if (owner) {
-      double ah, ch;
-      if (MASKED) {
-        const double2 sh = __ldg(v.bus_sh + o);
-        ah = __dadd_rn(acc_ma, sh.x);
-        ch = __dadd_rn(acc_mc, sh.y);
-      } else {
-        ah = hat.x;
-        ch = hat.y;
-      }
-      finalize_bus<WF, WJ>(v, a, inst, g, o, gb0_of(v, g), v.grid_nbus[g], xi, vi, vo, acc_a, acc_b, ah, ch, bm,
-                           bm2, inj);
+      // A^, C^: built (every end in service), else re-summed over the ends in
+      // service in the same order as the built value
+      if (MASKED && any_out) hat = masked_hat(v, a, q0, D, outage, st_base, o);
+      finalize_bus<WF, WJ>(v, a, inst, g, o, gb0_of(v, g), v.grid_nbus[g], xi, vi, vo, acc_a, acc_b, hat.x, hat.y,
+                           bm, bm2, inj);
     }
   }
 }
