@@ -81,6 +81,23 @@ def run_profile(args):
     return 0
 
 
+def max_over_ranks(seconds, distributed, device):
+    """The slowest rank's time (the timing every rank reports is its own
+    CUDA-event time; the whole job's time is the maximum)."""
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    if distributed:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, t_max):
+    """Whole-job throughput of `world` replicas that each processed
+    `units_per_rank` units, the slowest in t_max seconds."""
+    return world * units_per_rank / t_max
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -306,11 +323,8 @@ def main():
     torch.cuda.synchronize()
     clocks = sampler.stop()
     t_sum = ev_a.elapsed_time(ev_b) / 1000.0
-    t = torch.tensor([t_sum], dtype=torch.float64, device=dev)
-    if distributed:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_max = float(t.item())
-    value = world * K * N_STATES / t_max
+    t_max = max_over_ranks(t_sum, distributed, dev)
+    value = job_throughput(world, K * N_STATES, t_max)
     ms_per_step = 1000.0 * t_max / K
 
     # ---- the dominant kernel alone: the batched k_fused launch between events ----
@@ -358,10 +372,7 @@ def main():
         for k in range(E):
             ctx.residual_jacobian_host(xh, Fh, Vh, stream=stream)
         e2e_t = time.perf_counter() - t0
-    te = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
-    if distributed:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * E * N_STATES / float(te.item())
+    e2e_value = job_throughput(world, E * N_STATES, max_over_ranks(e2e_t, distributed, dev))
 
     # ---- the timed outputs equal single-instance evaluations ----
     for k in (0, N_STATES - 1):
