@@ -50,7 +50,7 @@ def parse():
                    help="only run warmup + steps evaluations of the workload (for ncu), no timing")
     p.add_argument("--tile", type=int, default=0, help="profile mode: tile_inc (0: autotune)")
     p.add_argument("--ctas", type=int, default=0, help="profile mode: CTAs per SM")
-    p.add_argument("--workload", default="70k", choices=["70k", "contingency", "adjoint", "mixed"],
+    p.add_argument("--workload", default="70k", choices=["70k", "contingency", "adjoint", "mixed", "newton"],
                    help="70k: the headline line (default); the others measure the batched-contingency, "
                         "adjoint and mixed-scenario workloads on one GPU and print their own line")
     return p.parse_args()
@@ -564,6 +564,45 @@ def run_workload(args):
                                "output_bytes": out_bytes},
                     "cpu_baseline": {"value": m / el, "unit": "cotangents/s", "cores": 1, "kind": "oracle",
                                      "sample": f"{m} oracle VJPs in {el:.1f} s"}})
+    elif args.workload == "newton":
+        # flat-start Newton power flow (F, J, convergence test and update in this library's
+        # kernels; the sparse solve in cuSOLVER).  The synthetic grids have a flat-start Newton
+        # solution only at light load at these sizes (a CPU sparse Newton agrees), so the loads are
+        # scaled down: 2,000 buses x 0.2, 10,000 buses x 0.1.
+        runs = []
+        for n_bus, seed, load in ((2000, 3000, 0.2), (10000, 3001, 0.1)):
+            sk = gridgen.synthetic_grid(n_bus, seed, load_scale=load)
+            ctx = Context(sk)
+            x0 = torch.from_numpy(gridgen.flat_state(sk)).cuda()
+            x = x0.clone()
+            ctx.newton(x, tol=1e-8, max_iter=15)                      # warm-up (allocations)
+            ts = []
+            for _ in range(max(1, min(args.steps, 3))):
+                x.copy_(x0)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                info = ctx.newton(x, tol=1e-8, max_iter=15)
+                ts.append(time.perf_counter() - t0)
+            runs.append({"n_bus": n_bus, "load_scale": load, "seconds": float(np.median(ts)), **info})
+            ctx.close()
+        clocks = {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled (host-synchronous loop)"],
+                  "samples": 0}
+        t = runs[-1]["seconds"]
+        s2 = gridgen.synthetic_grid(2000, 3000, load_scale=0.2)
+        t0, m = time.perf_counter(), 0
+        while time.perf_counter() - t0 < args.cpu_seconds and m < 3:
+            oracle.newton_dense(s2, gridgen.flat_state(s2), tol=1e-8)
+            m += 1
+        el = time.perf_counter() - t0
+        out.update({"metric": "flat-start Newton power flow, seconds per solve (10,000-bus grid)", "value": t,
+                    "unit": "s", "higher_is_better": False, "ms_per_step": 1e3 * t,
+                    "config": {"workload": "seeded synthetic 2,000-bus (load x 0.2) and 10,000-bus (load x 0.1) "
+                                           "grids, reduced formulation, flat start, max |F| <= 1e-8",
+                               "solver": "cuSOLVER sparse QR (METIS ordering) per iteration"},
+                    "runs": runs,
+                    "cpu_baseline": {"value": el / max(m, 1), "unit": "s", "cores": 1, "kind": "oracle",
+                                     "sample": f"{m} dense-Newton solves of the 2,000-bus grid in {el:.1f} s "
+                                               "(dense LU)"}})
     else:
         grids, insts = gridgen.mixed_batch()
         ctx = Context(grids, instances=[(k, -1) for k in range(len(grids))])
@@ -608,7 +647,7 @@ def run_workload(args):
                                "buses": int(sum(gg.n_bus for gg in grids)), "tuning": tuning},
                     "cpu_baseline": {"value": m / el, "unit": "iterations/s", "cores": 1, "kind": "oracle",
                                      "sample": f"{m} instance iterations in {el:.1f} s"}})
-    per_step = {"contingency": 2, "adjoint": 5, "mixed": 5}[args.workload]
+    per_step = {"contingency": 2, "adjoint": 5, "mixed": 5, "newton": 0}[args.workload]
     out["breakdown"] = breakdown
     out["clocks"] = clocks
     out["gpu_launches"] = per_step * K

@@ -68,6 +68,7 @@ extern "C" {
 #define PF_ERR_TIMEOUT 4      /* a bounded device wait gave up             */
 #define PF_ERR_UNSUPPORTED 5  /* valid input outside the library's limits  */
 #define PF_ERR_DEVICE 6       /* a kernel raised the context's error flag  */
+#define PF_ERR_NUMERIC 7      /* Newton: J numerically singular            */
 
 /* ---- formulations (Sec. II-A) ------------------------------------------- */
 #define PF_REDUCED 0          /* classic: P/theta non-slack, Q/V PQ buses  */
@@ -266,6 +267,37 @@ PF_API int pf_residual_jacobian_host(pf_ctx *ctx, const double *x_host, double *
  * forward call is stored.  ov may be NULL. */
 PF_API int pf_vjp(pf_ctx *ctx, const double *x, const pf_overrides *ov, const double *v,
            int32_t n_cot, const pf_grads *g, void *stream);
+
+/* ---- Newton iterations around the hot path (tasks 3 and 4 of Sec. I) ---------- */
+
+typedef struct pf_newton_info {
+  int32_t iterations;            /* Newton updates applied                              */
+  int32_t converged;             /* 1 when every instance reached max |F| <= tol        */
+  double max_mismatch;           /* max over instances of max |F| at the last evaluation */
+  double eval_ms;                /* host wall time in F + J evaluation and the norm     */
+  double solve_ms;               /* ... in the sparse solves (task 3)                   */
+  double update_ms;              /* ... in the updates (task 4)                         */
+} pf_newton_info;
+
+/* Newton power flow on every instance: repeat { F, J at x (this library's
+ * kernels); stop when max |F| <= tol for every instance; per instance that
+ * has not converged, solve J dx = F (cuSOLVER sparse QR with METIS
+ * ordering: a library solve, outside the hot path); x <- x - dx on the
+ * unknowns (task 4, on the device) } for at most max_iter updates.  x: the
+ * instances' states ([n_x], device), updated in place.  Synchronises `stream`
+ * every iteration (the convergence test is read on the host).  Device
+ * scratch (F, J values, dx) is allocated on the first call.  Errors:
+ * PF_ERR_INVALID (NULL x, max_iter < 0, tol < 0 or NaN), PF_ERR_NUMERIC (a
+ * singular J), PF_ERR_CUDA.  info may be NULL. */
+PF_API int pf_newton(pf_ctx *ctx, double *x, double tol, int32_t max_iter, void *stream, pf_newton_info *info);
+
+/* Convergence test of task (4): norms[i] = max |F| over the rows of instance
+ * i (device, [n_inst] doubles), exact in any order (a maximum). */
+PF_API int pf_mismatch_norm(pf_ctx *ctx, const double *F, double *norms, void *stream);
+
+/* Task (4): x <- x - dx on the unknowns of every instance (dx in the row /
+ * column order of J, [n_f] device; x [n_x] device, in place). */
+PF_API int pf_newton_update(pf_ctx *ctx, double *x, const double *dx, void *stream);
 
 /* ---- tuning ------------------------------------------------------------------ */
 

@@ -64,6 +64,11 @@ class PfTuning(ctypes.Structure):
 
 
 # name -> (restype, argtypes); every symbol include/pf.h declares
+class PfNewtonInfo(ctypes.Structure):
+    _fields_ = [("iterations", c_int32), ("converged", c_int32), ("max_mismatch", ctypes.c_double),
+                ("eval_ms", ctypes.c_double), ("solve_ms", ctypes.c_double), ("update_ms", ctypes.c_double)]
+
+
 SIGNATURES = {
     "pf_build": (c_int32, [P(PfSystem), c_int32, c_void_p, P(c_void_p)]),
     "pf_build_batch": (c_int32, [P(PfSystem), c_int32, P(PfInstance), c_int32, c_int32, c_void_p, P(c_void_p)]),
@@ -82,6 +87,9 @@ SIGNATURES = {
     "pf_residual_jacobian_static": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pf_residual_jacobian_host": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pf_vjp": (c_int32, [c_void_p, c_void_p, P(PfOverrides), c_void_p, c_int32, P(PfGrads), c_void_p]),
+    "pf_newton": (c_int32, [c_void_p, c_void_p, ctypes.c_double, c_int32, c_void_p, P(PfNewtonInfo)]),
+    "pf_mismatch_norm": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "pf_newton_update": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "pf_get_tuning": (c_int32, [c_void_p, P(PfTuning)]),
     "pf_set_tuning": (c_int32, [c_void_p, P(PfTuning), c_void_p]),
     "pf_autotune": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, P(PfTuning)]),

@@ -16,10 +16,15 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpf.so")
-SOURCES = ["pf_api.cu", "pf_build.cu", "pf_eval.cu", "pf_adjoint.cu", "pf_sort_scan.cu", "pf_noalloc.cu"]
+SOURCES = ["pf_api.cu", "pf_build.cu", "pf_eval.cu", "pf_adjoint.cu", "pf_sort_scan.cu", "pf_noalloc.cu",
+           "pf_newton.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]
+
+
+def cuda_lib_dir() -> str:
+    return os.path.join(os.path.dirname(os.path.dirname(nvcc())), "lib64")
 
 
 def nvcc() -> str:
@@ -54,7 +59,10 @@ def build(verbose_ptxas: bool = False, force: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
+    # cuSOLVER / cuSPARSE serve the Newton loop's sparse solve (outside the hot path)
+    libdir = cuda_lib_dir()
+    cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-L" + libdir, "-lcusolver", "-lcusparse",
+           "-Xlinker", "-rpath," + libdir]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

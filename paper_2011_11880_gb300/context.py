@@ -10,7 +10,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import PfDims, PfGrads, PfInstance, PfOverrides, PfSystem, PfTuning, check
+from ._lib import PfDims, PfGrads, PfInstance, PfNewtonInfo, PfOverrides, PfSystem, PfTuning, check
 
 FORMULATIONS = {"reduced": _lib.PF_REDUCED, "extended": _lib.PF_EXTENDED}
 
@@ -259,6 +259,29 @@ class Context:
         check(self._lib.pf_vjp(self._h, xp, ctypes.byref(ov) if ov is not None else None, vp, int(n_cot),
                                ctypes.byref(g), _stream(stream)), "pf_vjp")
         return out
+
+    # ---- Newton iterations around the evaluation (tasks 3 and 4) ----
+    def newton(self, x, tol: float = 1e-10, max_iter: int = 20, stream=None):
+        """Newton power flow on every instance, x updated in place; returns
+        {iterations, converged, max_mismatch, eval_ms, solve_ms, update_ms}."""
+        info = PfNewtonInfo()
+        check(self._lib.pf_newton(self._h, _ptr(x, numel=self.dims.n_x, name="x"), float(tol), int(max_iter),
+                                  _stream(stream), ctypes.byref(info)), "pf_newton")
+        return {k: getattr(info, k) for k, _ in PfNewtonInfo._fields_}
+
+    def mismatch_norm(self, F, stream=None):
+        """max |F| per instance ([n_inst] float64 CUDA tensor)."""
+        out = torch.empty(self.dims.n_instances, dtype=torch.float64, device=F.device)
+        check(self._lib.pf_mismatch_norm(self._h, _ptr(F, numel=self.dims.n_f, name="F"), _ptr(out),
+                                         _stream(stream)), "pf_mismatch_norm")
+        return out
+
+    def newton_update(self, x, dx, stream=None):
+        """x <- x - dx on the unknowns (dx in J's column order), in place."""
+        check(self._lib.pf_newton_update(self._h, _ptr(x, numel=self.dims.n_x, name="x"),
+                                         _ptr(dx, numel=self.dims.n_f, name="dx"), _stream(stream)),
+              "pf_newton_update")
+        return x
 
     # ---- tuning / errors ----
     def tuning(self):

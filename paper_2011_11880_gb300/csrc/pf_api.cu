@@ -37,6 +37,7 @@ void free_ctx(pf_ctx *ctx) {
   for (void *p : ctx->c.allocations) cudaFree(p);
   if (ctx->c.stage_x) cudaFree(ctx->c.stage_x);
   if (ctx->c.vt_scratch) cudaFree(ctx->c.vt_scratch);
+  if (ctx->c.newton && ctx->c.newton_free) ctx->c.newton_free(ctx->c.newton);
   if (ctx->c.stage_f) cudaFree(ctx->c.stage_f);
   if (ctx->c.stage_v) cudaFree(ctx->c.stage_v);
   delete ctx;
@@ -221,6 +222,21 @@ int pf_vjp(pf_ctx *ctx, const double *x, const pf_overrides *ov, const double *v
   return pf::launch_vjp(ctx->c, x, ov, v, n_cot, g, as_stream(stream));
 }
 
+int pf_newton(pf_ctx *ctx, double *x, double tol, int32_t max_iter, void *stream, pf_newton_info *info) {
+  if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
+  return pf::newton(ctx->c, x, tol, max_iter, as_stream(stream), info);
+}
+
+int pf_mismatch_norm(pf_ctx *ctx, const double *F, double *norms, void *stream) {
+  if (!ctx || !F || !norms) return fail(PF_ERR_INVALID, "NULL argument");
+  return pf::newton_norms(ctx->c, F, norms, as_stream(stream));
+}
+
+int pf_newton_update(pf_ctx *ctx, double *x, const double *dx, void *stream) {
+  if (!ctx || !x || !dx) return fail(PF_ERR_INVALID, "NULL argument");
+  return pf::newton_update(ctx->c, x, dx, as_stream(stream));
+}
+
 int pf_get_tuning(const pf_ctx *ctx, pf_tuning *t) {
   if (!ctx || !t) return fail(PF_ERR_INVALID, "NULL argument");
   *t = ctx->c.tuning;
@@ -294,6 +310,7 @@ const char *pf_error_string(int32_t code) {
     case PF_ERR_TIMEOUT: return "bounded device wait timed out";
     case PF_ERR_UNSUPPORTED: return "outside the library's limits";
     case PF_ERR_DEVICE: return "device-side consistency check failed";
+    case PF_ERR_NUMERIC: return "numerically singular Jacobian";
     default: return "unknown error code";
   }
 }

@@ -163,6 +163,9 @@ struct Ctx {
   // transposed cotangents of pf_vjp, allocated on first use and grown
   double *vt_scratch = nullptr;
   int64_t vt_cap = 0;
+  // Newton-iteration state (pf_newton.cu), created on first use
+  void *newton = nullptr;
+  void (*newton_free)(void *) = nullptr;
 
   std::vector<void *> allocations;
 };
@@ -194,6 +197,10 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
                   int n_inst, int formulation, cudaStream_t s);
 // Copies per-call coefficients (incidence / bus order) into slot / round order.
 int permute_overrides(Ctx &c, cudaStream_t s);
+// Newton iterations (pf_newton.cu).
+int newton(Ctx &c, double *x, double tol, int max_iter, cudaStream_t s, pf_newton_info *info);
+int newton_norms(Ctx &c, const double *F, double *norms, cudaStream_t s);
+int newton_update(Ctx &c, double *x, const double *dx, cudaStream_t s);
 // (cos theta, sin theta) and V of every instance bus into v.phasor (pf_eval.cu).
 int launch_phasor(const View &v, int num_sms, const double *x, cudaStream_t s);
 // Per-end coefficients (G, B, A, C) and per-bus sums (A^, C^) from the branch

@@ -1,0 +1,188 @@
+// Newton iterations around the hot path: tasks (3) and (4) of Newton power
+// flow (Sec. I).  Every iteration evaluates F and J with the library's
+// kernels, checks convergence (max |F| per instance, on the device), solves
+// J dx = F per instance with cuSOLVER's sparse QR (a library call: the linear
+// solve is outside the hot path) and updates the unknowns, x <- x - dx, on
+// the device.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#define DISABLE_CUSOLVER_DEPRECATED
+#include <cusolverSp.h>
+#include <cusparse.h>
+
+#include "pf_internal.cuh"
+
+namespace pf {
+namespace {
+
+// max |F| over the rows of each instance.  |F| is non-negative, so its bit
+// pattern orders like the value and an integer atomicMax gives the exact
+// maximum in any order (a NaN, positive after fabs, wins over every number).
+__global__ void k_mismatch_norm(View v, const int64_t *__restrict__ f_off, int64_t n_f, const double *__restrict__ F,
+                                unsigned long long *__restrict__ norm) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_f; r += stride) {
+    const int inst = v.n_inst == 1 ? 0 : find_segment(f_off, v.n_inst, r);
+    atomicMax(norm + inst, (unsigned long long)__double_as_longlong(fabs(F[r])));
+  }
+}
+
+// Task (4): x <- x - dx on the unknowns of every instance.  Reduced
+// formulation: theta of a bus with a P row (the slack has none) and V of a
+// bus with a Q row (PQ-type buses), at the bus's row index; extended: the
+// columns are numbered like x itself.
+__global__ void k_newton_update(View v, double *__restrict__ x, const double *__restrict__ dx) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < v.n_bus_inst; q += stride) {
+    const int inst = v.n_inst == 1 ? 0 : find_segment(v.inst_bus_off, v.n_inst, q);
+    const int g = v.inst_grid[inst];
+    const int64_t lb = q - v.inst_bus_off[inst];
+    const int64_t b = v.grid_bus_off[g] + lb;
+    const int32_t nb = v.grid_nbus[g];
+    double *__restrict__ xi = x + v.inst_x_off[inst];
+    const double *__restrict__ di = dx + v.inst_f_off[inst];
+    const int4 m = v.bus_meta[b];                       // {row_p, row_q, ...}
+    if (m.x >= 0) xi[lb] = __dsub_rn(xi[lb], di[m.x]);
+    if (m.y >= 0) xi[nb + lb] = __dsub_rn(xi[nb + lb], di[m.y]);
+    if (v.formulation == PF_EXTENDED && lb == 0) {     // generator Q_g and slack P_s columns
+      const int32_t extra = v.grid_ngen[g] + 1;
+      for (int32_t j = 0; j < extra; ++j) xi[2 * nb + j] = __dsub_rn(xi[2 * nb + j], di[2 * nb + j]);
+    }
+  }
+}
+
+struct Solver {
+  cusolverSpHandle_t sp = nullptr;
+  cusparseMatDescr_t descr = nullptr;
+  double *F = nullptr, *vals = nullptr, *dx = nullptr;
+  unsigned long long *norm = nullptr;
+  int64_t *f_off = nullptr;
+};
+
+int make_solver(Ctx &c, Solver **out) {
+  if (c.newton) {
+    *out = static_cast<Solver *>(c.newton);
+    return PF_OK;
+  }
+  Solver *S = new Solver();
+  c.newton = S;
+  c.newton_free = [](void *p) {
+    Solver *s = static_cast<Solver *>(p);
+    if (s->sp) cusolverSpDestroy(s->sp);
+    if (s->descr) cusparseDestroyMatDescr(s->descr);
+    delete s;
+  };
+  if (cusolverSpCreate(&S->sp) != CUSOLVER_STATUS_SUCCESS) return fail(PF_ERR_CUDA, "cusolverSpCreate failed");
+  if (cusparseCreateMatDescr(&S->descr) != CUSPARSE_STATUS_SUCCESS)
+    return fail(PF_ERR_CUDA, "cusparseCreateMatDescr failed");
+  cusparseSetMatType(S->descr, CUSPARSE_MATRIX_TYPE_GENERAL);
+  cusparseSetMatIndexBase(S->descr, CUSPARSE_INDEX_BASE_ZERO);
+  PF_TRY(dev_alloc(c, &S->F, c.n_f));
+  PF_TRY(dev_alloc(c, &S->vals, c.nnz));
+  PF_TRY(dev_alloc(c, &S->dx, c.n_f));
+  PF_TRY(dev_alloc(c, &S->norm, c.v.n_inst));
+  PF_TRY(upload(c, &S->f_off, c.f_off, nullptr));
+  *out = S;
+  return PF_OK;
+}
+
+int launch_norm(Ctx &c, const int64_t *f_off, const double *F, unsigned long long *norm, cudaStream_t s) {
+  PF_CUDA_TRY(cudaMemsetAsync(norm, 0, c.v.n_inst * sizeof(unsigned long long), s));
+  if (c.n_f > 0) {
+    const int64_t blocks = std::min<int64_t>((c.n_f + 255) / 256, (int64_t)c.num_sms * 16);
+    k_mismatch_norm<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(c.v, f_off, c.n_f, F, norm);
+    PF_CUDA_TRY(cudaGetLastError());
+  }
+  return PF_OK;
+}
+
+int launch_update(Ctx &c, double *x, const double *dx, cudaStream_t s) {
+  const int64_t blocks = std::min<int64_t>((c.v.n_bus_inst + 255) / 256, (int64_t)c.num_sms * 16);
+  k_newton_update<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(c.v, x, dx);
+  PF_CUDA_TRY(cudaGetLastError());
+  return PF_OK;
+}
+
+double ms_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+
+int newton_norms(Ctx &c, const double *F, double *norms, cudaStream_t s) {
+  Solver *S;
+  PF_TRY(make_solver(c, &S));
+  PF_TRY(launch_norm(c, S->f_off, F, reinterpret_cast<unsigned long long *>(norms), s));
+  return PF_OK;
+}
+
+int newton_update(Ctx &c, double *x, const double *dx, cudaStream_t s) { return launch_update(c, x, dx, s); }
+
+int newton(Ctx &c, double *x, double tol, int max_iter, cudaStream_t s, pf_newton_info *info) {
+  if (!x) return fail(PF_ERR_INVALID, "x is NULL");
+  if (max_iter < 0 || !(tol >= 0.0)) return fail(PF_ERR_INVALID, "max_iter must be >= 0 and tol >= 0");
+  Solver *S;
+  PF_TRY(make_solver(c, &S));
+  if (cusolverSpSetStream(S->sp, s) != CUSOLVER_STATUS_SUCCESS) return fail(PF_ERR_CUDA, "cusolverSpSetStream failed");
+  pf_newton_info r{};
+  const int I = c.v.n_inst;
+  std::vector<unsigned long long> h_norm(I);
+  for (int it = 0;; ++it) {
+    auto t0 = std::chrono::steady_clock::now();
+    PF_TRY(launch_eval(c, x, nullptr, S->F, S->vals, s));
+    PF_TRY(launch_norm(c, S->f_off, S->F, S->norm, s));
+    PF_CUDA_TRY(cudaMemcpyAsync(h_norm.data(), S->norm, I * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    PF_CUDA_TRY(cudaStreamSynchronize(s));
+    r.eval_ms += ms_since(t0);
+    double worst = 0.0;
+    bool done = true;
+    std::vector<char> active(I, 0);
+    for (int i = 0; i < I; ++i) {
+      double n;
+      std::memcpy(&n, &h_norm[i], sizeof(double));
+      if (!(n <= worst)) worst = n;            // NaN propagates
+      active[i] = !(n <= tol);
+      done = done && !active[i];
+    }
+    r.max_mismatch = worst;
+    if (done) {
+      r.converged = 1;
+      break;
+    }
+    if (it >= max_iter || worst != worst) break;
+    // task (3): J dx = F per instance that has not converged (dx = 0 for the others)
+    t0 = std::chrono::steady_clock::now();
+    PF_CUDA_TRY(cudaMemsetAsync(S->dx, 0, c.n_f * sizeof(double), s));
+    for (int i = 0; i < I; ++i) {
+      if (!active[i]) continue;
+      const int g = c.inst_grid[i];
+      const int n = c.grid_nf[g], nnz = c.grid_nnz[g];
+      if (n == 0) continue;
+      int singular = -1;
+      const cusolverStatus_t st = cusolverSpDcsrlsvqr(
+          S->sp, n, nnz, S->descr, S->vals + c.v_off[i], c.rowptr + c.grid_row_off[g], c.colind + c.grid_nnz_off[g],
+          S->F + c.f_off[i], 1e-14, /*reorder: METIS nested dissection*/ 3, S->dx + c.f_off[i], &singular);
+      if (st != CUSOLVER_STATUS_SUCCESS)
+        return fail(PF_ERR_CUDA, "cusolverSpDcsrlsvqr failed with status " + std::to_string((int)st));
+      if (singular >= 0)
+        return fail(PF_ERR_NUMERIC, "J is singular (instance " + std::to_string(i) + ", iteration " +
+                                        std::to_string(it) + ", pivot " + std::to_string(singular) + ")");
+    }
+    PF_CUDA_TRY(cudaStreamSynchronize(s));
+    r.solve_ms += ms_since(t0);
+    // task (4)
+    t0 = std::chrono::steady_clock::now();
+    PF_TRY(launch_update(c, x, S->dx, s));
+    PF_CUDA_TRY(cudaStreamSynchronize(s));
+    r.update_ms += ms_since(t0);
+    r.iterations = it + 1;
+  }
+  if (info) *info = r;
+  return PF_OK;
+}
+
+}  // namespace pf

@@ -1,0 +1,108 @@
+"""Newton iterations around the hot path (pf_newton: this library's F, J,
+convergence test and update kernels; cuSOLVER's sparse QR for the solve)
+against the oracle's dense Newton and the 2-bus closed form.  GPU only."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import gridgen
+import oracle
+from oracle import EXTENDED, REDUCED
+from tests.gpu_common import assert_tol, two_bus, with_outage
+
+pytestmark = pytest.mark.gpu
+MNAME = {REDUCED: "reduced", EXTENDED: "extended"}
+
+
+@pytest.fixture(scope="module")
+def P():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2011_11880_gb300 as p
+    return p
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("mode", [REDUCED, EXTENDED])
+def test_newton_200bus_matches_oracle_newton(P, mode):
+    sys = gridgen.grid_200()
+    x0 = gridgen.flat_state(sys, mode == EXTENDED)
+    xo, hist = oracle.newton_dense(sys, x0, mode)
+    assert hist[-1] <= 1e-10
+    ctx = P.Context(sys, MNAME[mode])
+    x = cuda(x0)
+    info = ctx.newton(x, tol=1e-10, max_iter=20)
+    assert info["converged"] == 1 and info["max_mismatch"] <= 1e-10
+    assert abs(info["iterations"] - (len(hist) - 1)) <= 1, (info, len(hist))
+    # both iterate to max |F| <= 1e-10: the same solution to well within 1e-8
+    assert np.max(np.abs(x.cpu().numpy() - xo)) <= 1e-8
+    assert np.max(np.abs(oracle.residual(sys, x.cpu().numpy(), mode))) <= 1e-10
+
+
+def test_newton_two_bus_closed_form(P):
+    """Slack (V = 1, theta = 0) - lossless line (x = 0.1) - PQ load 0.5 + j0.2:
+    V^2 = [1 - 2 Q x + sqrt((1 - 2 Q x)^2 - 4 x^2 (P^2 + Q^2))] / 2,
+    sin theta = -P x / V."""
+    sys = two_bus()
+    ctx = P.Context(sys)
+    x = cuda(gridgen.flat_state(sys))
+    info = ctx.newton(x, tol=1e-13, max_iter=20)
+    assert info["converged"] == 1
+    Pl, Ql, xl = 0.5, 0.2, 0.1
+    a = 1 - 2 * Ql * xl
+    v2 = math.sqrt((a + math.sqrt(a * a - 4 * xl * xl * (Pl * Pl + Ql * Ql))) / 2)
+    th2 = math.asin(-Pl * xl / v2)
+    xs = x.cpu().numpy()
+    assert abs(xs[3] - v2) <= 1e-12 and abs(xs[1] - th2) <= 1e-12
+
+
+def test_newton_batched_outages(P):
+    sys = gridgen.grid_200()
+    x0 = gridgen.flat_state(sys)
+    # outages for which the oracle's Newton converges (the grid stays solvable)
+    outs = []
+    for l in range(0, sys.n_branch, 7):
+        xo, hist = oracle.newton_dense(with_outage(sys, l), x0, max_iter=12)
+        if hist[-1] <= 1e-10:
+            outs.append((l, xo))
+        if len(outs) == 6:
+            break
+    assert len(outs) == 6
+    ctx = P.Context([sys], instances=[(0, l) for l, _ in outs])
+    x = cuda(np.concatenate([x0] * len(outs)))
+    info = ctx.newton(x, tol=1e-10, max_iter=20)
+    assert info["converged"] == 1
+    xs = x.cpu().numpy()
+    for k, (l, xo) in enumerate(outs):
+        assert np.max(np.abs(xs[ctx.x_off[k]:ctx.x_off[k + 1]] - xo)) <= 1e-8, l
+
+
+def test_mismatch_norm_and_update(P):
+    grids = [gridgen.synthetic_grid(300, 4), gridgen.grid_200()]
+    ctx = P.Context(grids, instances=[(0, -1), (1, -1), (0, 5)])
+    xs = [gridgen.perturbed_state(grids[g], k + 1) for k, g in enumerate((0, 1, 0))]
+    x = cuda(np.concatenate(xs))
+    F = ctx.residual(x)
+    norms = ctx.mismatch_norm(F).cpu().numpy()
+    Fh = F.cpu().numpy()
+    for k in range(3):
+        assert norms[k] == np.max(np.abs(Fh[ctx.f_off[k]:ctx.f_off[k + 1]]))
+    # update: x - dx on the unknowns, in J's column order, as the oracle's Newton does
+    rng = np.random.default_rng(3)
+    dx = rng.standard_normal(ctx.dims.n_f)
+    x2 = ctx.newton_update(x.clone(), cuda(dx)).cpu().numpy()
+    for k, g in enumerate((0, 1, 0)):
+        fm = oracle.Formulation(grids[g], REDUCED)
+        n = grids[g].n_bus
+        want = xs[k].copy()
+        d = dx[ctx.f_off[k]:ctx.f_off[k + 1]]
+        ok = fm.col_th >= 0
+        want[np.arange(n)[ok]] -= d[fm.col_th[ok]]
+        ok = fm.col_v >= 0
+        want[n + np.arange(n)[ok]] -= d[fm.col_v[ok]]
+        assert np.array_equal(x2[ctx.x_off[k]:ctx.x_off[k + 1]], want)
