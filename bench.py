@@ -584,7 +584,9 @@ def run_workload(args):
                 info = ctx.newton(x, tol=1e-8, max_iter=15)
                 ts.append(time.perf_counter() - t0)
             runs.append({"n_bus": n_bus, "load_scale": load, "seconds": float(np.median(ts)), **info})
+            ctx.check_device()
             ctx.close()
+        ctx = None
         clocks = {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled (host-synchronous loop)"],
                   "samples": 0}
         t = runs[-1]["seconds"]
@@ -651,7 +653,8 @@ def run_workload(args):
     out["breakdown"] = breakdown
     out["clocks"] = clocks
     out["gpu_launches"] = per_step * K
-    ctx.check_device()
+    if ctx is not None:
+        ctx.check_device()
     print(json.dumps(out), flush=True)
     return 0
 
