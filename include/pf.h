@@ -313,7 +313,7 @@ PF_API int pf_autotune(pf_ctx *ctx, const double *x, double *F, double *vals, vo
                 pf_tuning *chosen);
 
 /* The per-bus trigonometric routine of the evaluation (table-driven reduction
- * by multiples of pi/512 and short Taylor polynomials), exposed so it can be
+ * by multiples of pi/16384 and short Taylor polynomials), exposed so it can be
  * checked against a reference sin / cos: cos_out[i], sin_out[i] of theta[i],
  * n device entries each, asynchronous on `stream`. */
 PF_API int pf_sincos(pf_ctx *ctx, const double *theta, int64_t n, double *cos_out, double *sin_out,

@@ -1379,7 +1379,7 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
   PF_CUDA_TRY(cudaGetDevice(&dev));
   PF_CUDA_TRY(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev));
 
-  // (cos, sin) of i pi / 512 for the table-driven phasor routine, evaluated in
+  // (cos, sin) of i pi / 16384 for the table-driven phasor routine, evaluated in
   // long double on the host and rounded once to double.
   {
     std::vector<double2> tab(kSinCosTable);

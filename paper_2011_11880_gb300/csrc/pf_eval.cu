@@ -46,19 +46,19 @@ namespace {
 // ---------------------------------------------------------------------------
 // (cos t, sin t) by table-driven argument reduction (angle addition, after
 // P. T. P. Tang's table-driven elementary functions):
-//   t = k pi/512 + r, |r| <= pi/1024, k = nearest integer to t 512/pi;
-//   r from a two-constant Cody-Waite split of pi/512 (the high part has 27
-//   significant bits, so k * STEP_HI is exact for |k| < 2^26);
-//   cos r, sin r by their Taylor series to degree 4 / 5 (the first omitted
-//   terms, r^6/720 and r^7/5040, are below 1.2e-18 and 6e-22 for
-//   |r| <= pi/1024);
+//   t = k pi/16384 + r, |r| <= pi/32768, k = nearest integer to t 16384/pi;
+//   r from a two-constant Cody-Waite split of pi/16384 (the high part has 24
+//   significant bits, so k * STEP_HI is exact for |k| < 2^29, i.e. |t| < 2^16);
+//   cos r = 1 - r^2/2 and sin r = r - r^3/6 (the first omitted terms, r^4/24
+//   and r^5/120, are below 3.6e-18 and 7e-23 for |r| <= pi/32768);
 //   cos t = C_k cos r - S_k sin r, sin t = S_k cos r + C_k sin r with the
-//   table (C_k, S_k) = (cos, sin)(k pi / 512) computed on the host in long
-//   double.  14 FP64 operations.  Arguments beyond |t| = 2^16 use sincos().
+//   table (C_k, S_k) = (cos, sin)(k pi / 16384) (32768 entries, 512 KB,
+//   computed on the host in long double).  12 FP64 operations.  Arguments
+//   beyond |t| = 2^16 use sincos().
 // ---------------------------------------------------------------------------
-constexpr double kInvStep = 0x1.45f306dc9c883p+7;     // 512 / pi
-constexpr double kStepHi = 0x1.921fb54000000p-8;      // pi / 512, high 27 bits
-constexpr double kStepLo = 0x1.10b4611a62633p-38;     // pi / 512 - kStepHi
+constexpr double kInvStep = 0x1.45f306dc9c883p+12;    // 16384 / pi
+constexpr double kStepHi = 0x1.921fb60000000p-13;     // pi / 16384, high 24 bits
+constexpr double kStepLo = -0x1.777a5cf72cecep-38;    // pi / 16384 - kStepHi
 constexpr double kRoundMagic = 6755399441055744.0;    // 1.5 * 2^52
 
 __device__ __forceinline__ double2 table_sincos(double t, const double2 *__restrict__ tab) {
@@ -74,11 +74,8 @@ __device__ __forceinline__ double2 table_sincos(double t, const double2 *__restr
   double r = __fma_rn(-kd, kStepHi, t);
   r = __fma_rn(-kd, kStepLo, r);
   const double z = __dmul_rn(r, r);
-  // sin r = r + r z (-1/6 + z / 120)
-  const double ps = __fma_rn(z, 1.0 / 120.0, -1.0 / 6.0);
-  const double sr = __fma_rn(__dmul_rn(r, z), ps, r);
-  // cos r = 1 + z (-1/2 + z / 24)
-  const double cr = __fma_rn(z, __fma_rn(z, 1.0 / 24.0, -0.5), 1.0);
+  const double cr = __fma_rn(z, -0.5, 1.0);                         // cos r
+  const double sr = __fma_rn(__dmul_rn(r, z), -1.0 / 6.0, r);       // sin r
   const double2 T = __ldg(tab + (ki & (kSinCosTable - 1)));
   return make_double2(__fma_rn(T.x, cr, -__dmul_rn(T.y, sr)), __fma_rn(T.y, cr, __dmul_rn(T.x, sr)));
 }

@@ -27,7 +27,7 @@ constexpr int kMaxGroup = 32;      // parallel branches between one pair of buse
 // numbers of neighbours, one bus per lane; a bus with more than
 // kLaneMaxDegree neighbours is evaluated by a whole warp.
 constexpr int kLaneMaxDegree = 32;
-constexpr int kSinCosTable = 1024;  // table of (cos, sin)(i pi / 512)
+constexpr int kSinCosTable = 32768;  // table of (cos, sin)(i pi / 16384)
 
 // Thread-local error message behind pf_last_error().
 void set_error(const std::string &msg);
@@ -127,7 +127,7 @@ struct View {
   // scratch
   double2 *phasor;                            // [2 n_bus_inst]: (cos theta, sin theta), (V, 0) per bus
   int32_t *dev_error;
-  const double2 *sincos_tab;                  // [kSinCosTable] (cos, sin)(i pi / 512)
+  const double2 *sincos_tab;                  // [kSinCosTable] (cos, sin)(i pi / 16384)
 };
 
 struct Ctx {
