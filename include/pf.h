@@ -175,7 +175,7 @@ typedef struct pf_tuning {
 PF_API int pf_build(const pf_system *sys, int32_t formulation, void *stream, pf_ctx **out);
 
 /* Batched form: n_grids networks and n_inst instances over them, evaluated
- * together by one persistent launch.  Instance k owns the k-th block of x, F
+ * together by one launch of each kernel.  Instance k owns the k-th block of x, F
  * and J values (offsets from pf_offsets).  Same errors as pf_build, plus
  * PF_ERR_INVALID for a bad grid index or outage branch. */
 PF_API int pf_build_batch(const pf_system *grids, int32_t n_grids, const pf_instance *inst,
@@ -263,8 +263,14 @@ PF_API int pf_residual_jacobian_host(pf_ctx *ctx, const double *x_host, double *
 
 /* Adjoint (differentiation of F): for n_cot cotangents v
  * ([n_cot][n_f], device), the vector-Jacobian products v^T dF/d(x, P_inj,
- * Q_inj, r, x, b_c, tau).  Trigonometric terms are recomputed, nothing from a
- * forward call is stored.  ov may be NULL. */
+ * Q_inj, r, x, b_c, tau) into the non-NULL arrays of g.  Trigonometric terms
+ * are recomputed, nothing from a forward call is stored.  ov may be NULL.
+ * Sums run in a fixed order: every cotangent of a batch gives the bits of a
+ * single-cotangent call.  With 16 or more cotangents they are first copied
+ * to a transposed device buffer owned by the context, allocated by the first
+ * call with that many (or more) cotangents: make that call outside stream
+ * capture.  Errors: PF_ERR_INVALID (NULL x / v / g, n_cot <= 0), PF_ERR_OOM,
+ * PF_ERR_CUDA. */
 PF_API int pf_vjp(pf_ctx *ctx, const double *x, const pf_overrides *ov, const double *v,
            int32_t n_cot, const pf_grads *g, void *stream);
 
