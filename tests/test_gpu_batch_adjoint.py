@@ -167,3 +167,38 @@ def test_autograd_function_single_and_batched(P):
         goc = oracle.vjp(sys, xn, V[c])
         assert_tol(gxb[c].cpu().numpy(), goc["x"], f"batched dx {c}")
         assert_tol(grb[c].cpu().numpy(), goc["r"], f"batched dr {c}")
+
+
+def test_many_tiny_grids_in_one_batch(P):
+    """2,000 instances of 2- to 40-bus grids (rounds mostly partly filled), each its own grid."""
+    rng = np.random.default_rng(8)
+    grids = [gridgen.synthetic_grid(int(n), 100 + k) for k, n in enumerate(rng.integers(2, 41, 2000))]
+    ctx = P.Context(grids, instances=[(k, -1) for k in range(len(grids))])
+    xs = [gridgen.perturbed_state(g, k + 1) for k, g in enumerate(grids)]
+    F, V = ctx.residual_jacobian(cuda(np.concatenate(xs)))
+    Fh, Vh = F.cpu().numpy(), V.cpu().numpy()
+    for k in list(range(0, 2000, 97)) + [1999]:
+        assert_tol(Fh[ctx.f_off[k]:ctx.f_off[k + 1]], oracle.residual(grids[k], xs[k]), f"grid {k} F")
+        assert_tol(Vh[ctx.nnz_off[k]:ctx.nnz_off[k + 1]], oracle.jacobian(grids[k], xs[k])[2], f"grid {k} J")
+    ctx.check_device()
+
+
+@pytest.mark.parametrize("mode", [REDUCED, EXTENDED])
+def test_every_branch_out_of_service(P, mode):
+    """Degenerate network: no branch in service (F is the injections and shunts alone), built
+    plain and as a masked batch instance."""
+    sys = gridgen.grid_200()
+    dead = sys.copy()
+    dead.br_status = np.zeros_like(sys.br_status)
+    x = gridgen.perturbed_state(sys, 3, mode == EXTENDED)
+    F0 = oracle.residual(dead, x, mode)
+    J0 = oracle.jacobian(dead, x, mode)[2]
+    ctx = P.Context(dead, MNAME[mode])
+    F, V = ctx.residual_jacobian(cuda(x))
+    assert_tol(F.cpu().numpy(), F0, "F")
+    assert_tol(V.cpu().numpy(), J0, "J")
+    status = torch.zeros(sys.n_branch, dtype=torch.uint8, device="cuda")
+    ctx2 = P.Context(sys, MNAME[mode])
+    F2, V2 = ctx2.eval(cuda(x), ctx2.empty_f(), ctx2.empty_vals(), status=status)
+    assert_tol(F2.cpu().numpy(), F0, "F masked")
+    assert_tol(V2.cpu().numpy(), J0, "J masked")
