@@ -256,8 +256,12 @@ PF_API int pf_residual_jacobian_static(pf_ctx *ctx, const double *x, double *F, 
 
 /* End-to-end form for callers holding host memory: copies x (host) in,
  * evaluates, copies F and vals (host; either may be NULL) out and
- * synchronises `stream`.  Page-locked host buffers give the full copy rate.
- * Device staging buffers are allocated on the first call and kept. */
+ * synchronises `stream`.  With several instances the work is pipelined over
+ * up to 8 chunks of instances on internal streams (copy in, evaluate, copy
+ * out overlap; the calls wait for `stream`'s earlier work first).
+ * Page-locked host buffers give the full copy rate and the overlap.  Device
+ * staging buffers, streams and events are created on the first call and
+ * kept. */
 PF_API int pf_residual_jacobian_host(pf_ctx *ctx, const double *x_host, double *F_host,
                               double *vals_host, void *stream);
 

@@ -32,8 +32,14 @@ namespace {
 
 cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
 
+// Chunks of instances of the pipelined host-buffer evaluation.
+constexpr int kHostChunks = 8;
+
 void free_ctx(pf_ctx *ctx) {
   if (!ctx) return;
+  for (auto &q : ctx->c.pipe_stream)
+    if (q) cudaStreamDestroy(q);
+  for (auto &e : ctx->c.pipe_events) cudaEventDestroy(e);
   for (void *p : ctx->c.allocations) cudaFree(p);
   if (ctx->c.stage_x) cudaFree(ctx->c.stage_x);
   if (ctx->c.vt_scratch) cudaFree(ctx->c.vt_scratch);
@@ -207,11 +213,52 @@ int pf_residual_jacobian_host(pf_ctx *ctx, const double *x_host, double *F_host,
     PF_CUDA_TRY(cudaMalloc(&c.stage_f, std::max<int64_t>(c.n_f, 1) * sizeof(double)));
     PF_CUDA_TRY(cudaMalloc(&c.stage_v, std::max<int64_t>(c.nnz, 1) * sizeof(double)));
   }
-  PF_CUDA_TRY(cudaMemcpyAsync(c.stage_x, x_host, c.n_x * sizeof(double), cudaMemcpyHostToDevice, s));
-  PF_TRY(pf::launch_eval(c, c.stage_x, nullptr, F_host ? c.stage_f : nullptr, vals_host ? c.stage_v : nullptr, s));
-  if (F_host) PF_CUDA_TRY(cudaMemcpyAsync(F_host, c.stage_f, c.n_f * sizeof(double), cudaMemcpyDeviceToHost, s));
-  if (vals_host)
-    PF_CUDA_TRY(cudaMemcpyAsync(vals_host, c.stage_v, c.nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
+  double *F_dev = F_host ? c.stage_f : nullptr, *v_dev = vals_host ? c.stage_v : nullptr;
+  const int I = c.v.n_inst;
+  const int C = std::min(I, kHostChunks);
+  if (C <= 1) {
+    PF_CUDA_TRY(cudaMemcpyAsync(c.stage_x, x_host, c.n_x * sizeof(double), cudaMemcpyHostToDevice, s));
+    PF_TRY(pf::launch_eval(c, c.stage_x, nullptr, F_dev, v_dev, s));
+    if (F_host) PF_CUDA_TRY(cudaMemcpyAsync(F_host, c.stage_f, c.n_f * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (vals_host)
+      PF_CUDA_TRY(cudaMemcpyAsync(vals_host, c.stage_v, c.nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PF_CUDA_TRY(cudaStreamSynchronize(s));
+    return PF_OK;
+  }
+  // Pipeline over chunks of instances: copy in (stream 0), evaluate (stream 1) and copy
+  // out (stream 2) overlap, so the time approaches that of the largest of the three.
+  if (!c.pipe_stream[0]) {
+    for (auto &q : c.pipe_stream) PF_CUDA_TRY(cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking));
+    c.pipe_events.resize(2 * kHostChunks + 2);
+    for (auto &e : c.pipe_events) PF_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  cudaStream_t s_in = c.pipe_stream[0], s_ev = c.pipe_stream[1], s_out = c.pipe_stream[2];
+  cudaEvent_t ev_start = c.pipe_events[2 * kHostChunks], ev_end = c.pipe_events[2 * kHostChunks + 1];
+  PF_CUDA_TRY(cudaEventRecord(ev_start, s));                  // after the caller's earlier work
+  PF_CUDA_TRY(cudaStreamWaitEvent(s_in, ev_start, 0));
+  PF_CUDA_TRY(cudaStreamWaitEvent(s_ev, ev_start, 0));
+  PF_CUDA_TRY(cudaStreamWaitEvent(s_out, ev_start, 0));
+  for (int k = 0; k < C; ++k) {
+    const int i0 = (int)((int64_t)I * k / C), i1 = (int)((int64_t)I * (k + 1) / C);
+    cudaEvent_t ev_in = c.pipe_events[2 * k], ev_done = c.pipe_events[2 * k + 1];
+    const int64_t x0 = c.x_off[i0], nx = c.x_off[i1] - x0;
+    PF_CUDA_TRY(cudaMemcpyAsync(c.stage_x + x0, x_host + x0, nx * sizeof(double), cudaMemcpyHostToDevice, s_in));
+    PF_CUDA_TRY(cudaEventRecord(ev_in, s_in));
+    PF_CUDA_TRY(cudaStreamWaitEvent(s_ev, ev_in, 0));
+    PF_TRY(pf::launch_eval_range(c, i0, i1, c.stage_x, F_dev, v_dev, s_ev));
+    PF_CUDA_TRY(cudaEventRecord(ev_done, s_ev));
+    PF_CUDA_TRY(cudaStreamWaitEvent(s_out, ev_done, 0));
+    if (F_host) {
+      const int64_t f0 = c.f_off[i0], nf = c.f_off[i1] - f0;
+      PF_CUDA_TRY(cudaMemcpyAsync(F_host + f0, c.stage_f + f0, nf * sizeof(double), cudaMemcpyDeviceToHost, s_out));
+    }
+    if (vals_host) {
+      const int64_t v0 = c.v_off[i0], nv = c.v_off[i1] - v0;
+      PF_CUDA_TRY(cudaMemcpyAsync(vals_host + v0, c.stage_v + v0, nv * sizeof(double), cudaMemcpyDeviceToHost, s_out));
+    }
+  }
+  PF_CUDA_TRY(cudaEventRecord(ev_end, s_out));
+  PF_CUDA_TRY(cudaStreamWaitEvent(s, ev_end, 0));
   PF_CUDA_TRY(cudaStreamSynchronize(s));
   return PF_OK;
 }

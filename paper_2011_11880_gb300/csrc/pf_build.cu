@@ -890,6 +890,8 @@ int build_rounds(Ctx &c, cudaStream_t s) {
   }
   v.n_lane_units = lane_off[I];
   v.n_large_units = large_off[I];
+  c.lane_off = lane_off;
+  c.large_off = large_off;
   int64_t *d_lane_off, *d_large_off, *d_lane_rounds, *rec_base;
   int4 *unit;
   int2 *large;

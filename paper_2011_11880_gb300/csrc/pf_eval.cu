@@ -87,7 +87,8 @@ __global__ void __launch_bounds__(256) k_phasor(View v, const double *__restrict
   // Let the fused kernel start launching; it waits for this grid's results.
   cudaTriggerProgrammaticLaunchCompletion();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < v.n_bus_inst; q += stride) {
+  for (int64_t q = v.bus_inst_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < v.n_bus_inst;
+       q += stride) {
     const int inst = v.n_inst == 1 ? 0 : find_segment(v.inst_bus_off, v.n_inst, q);
     const int64_t lb = q - v.inst_bus_off[inst];
     const double *xi = x + v.inst_x_off[inst];
@@ -553,7 +554,7 @@ __global__ void k_sincos(const double *__restrict__ t, int64_t n, const double2 
 
 int launch_phasor(const View &v, int num_sms, const double *x, cudaStream_t s) {
   const int tb = 256;
-  int64_t blocks = (v.n_bus_inst + tb - 1) / tb;
+  int64_t blocks = (v.n_bus_inst - v.bus_inst_begin + tb - 1) / tb;
   blocks = std::min<int64_t>(blocks, (int64_t)num_sms * 16);
   k_phasor<<<(unsigned)std::max<int64_t>(blocks, 1), tb, 0, s>>>(v, x);
   PF_CUDA_TRY(cudaGetLastError());
@@ -595,6 +596,28 @@ int launch_eval_stages(Ctx &c, int stages, const double *x, const pf_overrides *
   if (stages & 1) PF_TRY(launch_phasor(c.v, c.num_sms, x, s));
   if (!(stages & 2)) return PF_OK;
   return launch_fused(c.v, c.num_sms, c.tuning, a, masked, s);
+}
+
+// F and J of the instances [i0, i1): the units of those instances are
+// contiguous in the unit lists, their buses contiguous in the phasor scratch.
+int launch_eval_range(Ctx &c, int i0, int i1, const double *x, double *F, double *vals, cudaStream_t s) {
+  if (!x) return fail(PF_ERR_INVALID, "x is NULL");
+  if (i0 < 0 || i1 > c.v.n_inst || i0 >= i1) return fail(PF_ERR_INVALID, "bad instance range");
+  if (!F && !vals) return PF_OK;
+  View v = c.v;
+  v.unit_rec = c.v.unit_rec + c.lane_off[i0];
+  v.n_lane_units = c.lane_off[i1] - c.lane_off[i0];
+  v.large_rec = c.v.large_rec + c.large_off[i0];
+  v.n_large_units = c.large_off[i1] - c.large_off[i0];
+  v.bus_inst_begin = c.bus_off[i0];
+  v.n_bus_inst = c.bus_off[i1];
+  EvalArgs a{};
+  a.x = x;
+  a.F = F;
+  a.vals = vals;
+  built_coefficients(c.v, a);
+  PF_TRY(launch_phasor(v, c.num_sms, x, s));
+  return launch_fused(v, c.num_sms, c.tuning, a, c.any_outage, s);
 }
 
 // Evaluation with caller-provided phasor scratch (used by the allocation-free

@@ -55,6 +55,7 @@ struct View {
   int formulation;
   int n_grids, n_inst;
   int64_t n_bus, n_branch, n_inc, n_bus_inst;
+  int64_t bus_inst_begin;   // first instance bus of k_phasor (0; later for an instance range)
   int64_t n_lane_units;     // sum over instances of the rounds of 32 buses of its grid
   int64_t n_large_units;    // sum over instances of the buses with more than 32 ends
 
@@ -157,12 +158,16 @@ struct Ctx {
   double2 *ov_slot_gb = nullptr, *ov_slot_ac = nullptr, *ov_slot_gbm = nullptr, *ov_rbus_hat = nullptr;
   int64_t n_slots = 0, n_rounds = 0;
   std::vector<int64_t> grid_round_off;
+  std::vector<int64_t> lane_off, large_off;   // per instance: first unit of k_fused / k_fused_large
 
   // host-call staging, allocated on first use
   double *stage_x = nullptr, *stage_f = nullptr, *stage_v = nullptr;
   // transposed cotangents of pf_vjp, allocated on first use and grown
   double *vt_scratch = nullptr;
   int64_t vt_cap = 0;
+  // pipelined host-buffer evaluation: internal streams and events, created on first use
+  cudaStream_t pipe_stream[3] = {nullptr, nullptr, nullptr};
+  std::vector<cudaEvent_t> pipe_events;
   // Newton-iteration state (pf_newton.cu), created on first use
   void *newton = nullptr;
   void (*newton_free)(void *) = nullptr;
@@ -201,6 +206,8 @@ int permute_overrides(Ctx &c, cudaStream_t s);
 int newton(Ctx &c, double *x, double tol, int max_iter, cudaStream_t s, pf_newton_info *info);
 int newton_norms(Ctx &c, const double *F, double *norms, cudaStream_t s);
 int newton_update(Ctx &c, double *x, const double *dx, cudaStream_t s);
+// F and J of the instances [i0, i1) only (pf_eval.cu; built coefficients, no overrides).
+int launch_eval_range(Ctx &c, int i0, int i1, const double *x, double *F, double *vals, cudaStream_t s);
 // (cos theta, sin theta) and V of every instance bus into v.phasor (pf_eval.cu).
 int launch_phasor(const View &v, int num_sms, const double *x, cudaStream_t s);
 // Per-end coefficients (G, B, A, C) and per-bus sums (A^, C^) from the branch

@@ -202,3 +202,27 @@ def test_every_branch_out_of_service(P, mode):
     F2, V2 = ctx2.eval(cuda(x), ctx2.empty_f(), ctx2.empty_vals(), status=status)
     assert_tol(F2.cpu().numpy(), F0, "F masked")
     assert_tol(V2.cpu().numpy(), J0, "J masked")
+
+
+def test_host_buffers_pipelined_batch(P):
+    """pf_residual_jacobian_host on a batch (pipelined over chunks of instances) gives the
+    device path's bits, from pageable and from page-locked host buffers."""
+    grids = [gridgen.synthetic_grid(300, 2), gridgen.synthetic_grid(1100, 3), gridgen.grid_200()]
+    rng = np.random.default_rng(12)
+    inst = [(int(g), int(rng.integers(-1, 200))) for g in rng.integers(0, 3, 21)]
+    ctx = P.Context(grids, instances=inst)
+    xn = np.concatenate([gridgen.perturbed_state(grids[g], k + 1) for k, (g, _) in enumerate(inst)])
+    F_d, v_d = ctx.residual_jacobian(cuda(xn))
+    F_d, v_d = F_d.cpu().numpy(), v_d.cpu().numpy()
+    for pinned in (False, True):
+        if pinned:
+            xh = torch.from_numpy(xn).pin_memory().numpy()
+            F_h = torch.empty(ctx.dims.n_f, dtype=torch.float64).pin_memory().numpy()
+            v_h = torch.empty(ctx.dims.nnz, dtype=torch.float64).pin_memory().numpy()
+        else:
+            xh, F_h, v_h = xn.copy(), np.empty(ctx.dims.n_f), np.empty(ctx.dims.nnz)
+        ctx.residual_jacobian_host(xh, F_h, v_h)
+        assert np.array_equal(F_h, F_d) and np.array_equal(v_h, v_d), pinned
+        F_only = np.empty(ctx.dims.n_f)
+        ctx.residual_jacobian_host(xh, F_only, None)
+        assert np.array_equal(F_only, F_d)
