@@ -127,6 +127,8 @@ typedef struct pf_dims {
   int64_t nnz;                   /* sum over instances: length of J values   */
   int64_t n_bus_inst;            /* sum over instances of N (p_inj / q_inj length) */
   int64_t n_branch_inst;         /* sum over instances of M (status override length) */
+  int64_t n_gen_inst;            /* extended: sum over instances of the generators (PV units,
+                                    then the slack) -- the length of gen_mode / gen_qlim */
 } pf_dims;
 
 /* Per-call overrides (device pointers; every field may be NULL). */
@@ -140,6 +142,12 @@ typedef struct pf_overrides {
   const double *br_x;            /*   branch model (adjoint / sensitivity use);   */
   const double *br_b;            /*   each NULL keeps the built value             */
   const double *br_tap;
+  const uint8_t *gen_mode;       /* extended, [n_gen_inst]: 0 = voltage control (g_V = V - Vset);
+                                    otherwise the generator is held at a reactive limit and
+                                    g_V = Q_g - gen_qlim (Sec. II-A: PV -> PQ switching in the
+                                    same formulation; the J pattern carries both entries of
+                                    every g_V row, so switching never changes it) */
+  const double *gen_qlim;        /* [n_gen_inst] the held reactive output (read where mode != 0) */
 } pf_overrides;
 
 /* Gradients of a vector-Jacobian product (device pointers; NULL skips).
@@ -300,6 +308,20 @@ typedef struct pf_newton_info {
  * PF_ERR_INVALID (NULL x, max_iter < 0, tol < 0 or NaN), PF_ERR_NUMERIC (a
  * singular J), PF_ERR_CUDA.  info may be NULL. */
 PF_API int pf_newton(pf_ctx *ctx, double *x, double tol, int32_t max_iter, void *stream, pf_newton_info *info);
+
+/* Newton power flow with reactive limits (extended formulation; Sec. II-A):
+ * pf_newton's iterations with the generators' modes of gen_mode; after each
+ * converged solve, every generator in voltage control whose Q_g lies above
+ * q_max or below q_min is switched to that limit (gen_mode 1 or 2, gen_qlim
+ * set) and the solve is repeated, until no switch happens (at most
+ * max_rounds solves).  q_min, q_max: [n_gen_inst] device; gen_mode
+ * (uint8) and gen_qlim: [n_gen_inst] device, read as the starting modes and
+ * updated in place (all zero = every generator in voltage control).
+ * info->iterations counts the Newton updates of all solves; *rounds (may be
+ * NULL) the solves.  PF_ERR_INVALID for the reduced formulation. */
+PF_API int pf_newton_qlim(pf_ctx *ctx, double *x, const double *q_min, const double *q_max, uint8_t *gen_mode,
+                          double *gen_qlim, double tol, int32_t max_iter, int32_t max_rounds, void *stream,
+                          pf_newton_info *info, int32_t *rounds);
 
 /* Convergence test of task (4): norms[i] = max |F| over the rows of instance
  * i (device, [n_inst] doubles), exact in any order (a maximum). */

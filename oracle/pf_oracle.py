@@ -26,6 +26,12 @@ of the branch model, Eq. 4):
   * Extended formulation (Eqs. 1-3): rows [g_p(N), g_q(N), g_V(gens), g_theta],
     columns [theta(N), V(N), Q_g(gens), P_s]; generators are the PV units in
     input order followed by the slack; g_V = V - Vset, g_theta = theta_s - theta_set.
+  * Reactive limits in the extended formulation (Sec. II-A: the same
+    formulation serves before and after a PV generator switches to a PQ
+    load): a generator in voltage control has g_V = V - Vset; one held at a
+    reactive limit has g_V = Q_g - Q_lim instead.  Its g_V row always carries
+    both entries, dg_V/dV and dg_V/dQ_g (one of them an explicit zero), so
+    switching never changes the pattern.
   * Reduced (classic) formulation: rows/columns [P/theta of non-slack buses,
     Q/V of PQ-type buses], each in ascending bus order.
   * Jacobian pattern: the structural union of all model contributions; the
@@ -260,12 +266,13 @@ def split_state(sys, x, mode):
     return theta, V, None, None
 
 
-def residual(sys, x, mode=REDUCED, p_inj=None, q_inj=None, **branch_params):
+def residual(sys, x, mode=REDUCED, p_inj=None, q_inj=None, gen_mode=None, gen_qlim=None, **branch_params):
     """Task (1): the residual vector F in the formulation's row order.
 
     ``x`` is the full state [theta(N), V(N)] (+ [Q_g, P_s] extended); in the
     reduced formulation the slack angle and the PV / slack magnitudes are read
-    from x as fixed values.
+    from x as fixed values.  Extended formulation: ``gen_mode[i]`` != 0 holds
+    generator i at the reactive output ``gen_qlim[i]`` (g_V = Q_g - Q_lim).
     """
     fm = Formulation(sys, mode)
     theta, V, qg, ps = split_state(sys, x, mode)
@@ -279,6 +286,9 @@ def residual(sys, x, mode=REDUCED, p_inj=None, q_inj=None, **branch_params):
         np.add.at(fq, fm.gens, -qg)
         vset = np.concatenate([sys.pv_vset, [sys.slack_vset]])
         out[fm.row_gv] = V[fm.gens] - vset
+        if gen_mode is not None:
+            held = np.asarray(gen_mode) != 0
+            out[fm.row_gv[held]] = qg[held] - np.asarray(gen_qlim)[held]
         out[fm.row_gth] = theta[sys.slack_bus] - sys.slack_theta
     hp = fm.row_p >= 0
     hq = fm.row_q >= 0
@@ -291,7 +301,7 @@ def residual(sys, x, mode=REDUCED, p_inj=None, q_inj=None, **branch_params):
 # Jacobian (task 2)
 # ---------------------------------------------------------------------------
 
-def _triplets(sys, x, mode, state_columns):
+def _triplets(sys, x, mode, state_columns, gen_mode=None):
     """All (row, col, value) contributions of every model.
 
     ``state_columns``: columns are positions in x (theta_b -> b, V_b -> N+b,
@@ -343,7 +353,9 @@ def _triplets(sys, x, mode, state_columns):
         one = np.ones(ng)
         put(fm.row_q[fm.gens], cqg, -one)                   # g_q gets -Q_g
         put([fm.row_p[sys.slack_bus]], [cps], [-1.0])        # g_p at slack gets -P_s
-        put(fm.row_gv, cv[fm.gens], one)                     # g_V = V - Vset
+        held = np.zeros(ng, bool) if gen_mode is None else np.asarray(gen_mode) != 0
+        put(fm.row_gv, cv[fm.gens], np.where(held, 0.0, 1.0))   # g_V = V - Vset
+        put(fm.row_gv, cqg, np.where(held, 1.0, 0.0))           # g_V = Q_g - Q_lim when held
         put([fm.row_gth], [cth[sys.slack_bus]], [1.0])       # g_theta = theta_s - theta_set
     return (np.concatenate(rows), np.concatenate(cols),
             np.concatenate([np.asarray(v) for v in vals]))
@@ -363,18 +375,18 @@ def _coo_to_csr(rows, cols, vals, n_rows, n_cols):
     return rowptr, colind, data
 
 
-def jacobian(sys, x, mode=REDUCED):
+def jacobian(sys, x, mode=REDUCED, gen_mode=None):
     """Task (2): CSR (rowptr, colind, values) of dF/d(unknowns), ascending columns."""
     fm = Formulation(sys, mode)
-    r, c, v = _triplets(sys, x, mode, state_columns=False)
+    r, c, v = _triplets(sys, x, mode, state_columns=False, gen_mode=gen_mode)
     return _coo_to_csr(r, c, v, fm.n_rows, fm.n_cols)
 
 
-def jacobian_state(sys, x, mode=REDUCED):
+def jacobian_state(sys, x, mode=REDUCED, gen_mode=None):
     """CSR of dF/dx over every entry of the state vector x (all theta, all V,
     and the extended extras), used for vector-Jacobian products."""
     fm = Formulation(sys, mode)
-    r, c, v = _triplets(sys, x, mode, state_columns=True)
+    r, c, v = _triplets(sys, x, mode, state_columns=True, gen_mode=gen_mode)
     n_x = x.shape[0]
     return _coo_to_csr(r, c, v, fm.n_rows, n_x)
 
@@ -399,7 +411,7 @@ def csr_matvec_t(rowptr, colind, vals, v, n_cols):
 # vector-Jacobian products (adjoint)
 # ---------------------------------------------------------------------------
 
-def vjp(sys, x, v, mode=REDUCED):
+def vjp(sys, x, v, mode=REDUCED, gen_mode=None):
     """v^T dF/d(x, P_inj, Q_inj, r, x_branch, b_c, tap).
 
     Returns dict with 'x' (len(x)), 'p_inj', 'q_inj' (N) and 'r', 'reac',
@@ -407,7 +419,7 @@ def vjp(sys, x, v, mode=REDUCED):
     """
     fm = Formulation(sys, mode)
     n = sys.n_bus
-    rp, ci, jv = jacobian_state(sys, x, mode)
+    rp, ci, jv = jacobian_state(sys, x, mode, gen_mode)
     out = {"x": csr_matvec_t(rp, ci, jv, v, x.shape[0])}
     vp = np.zeros(n)
     vq = np.zeros(n)
@@ -511,7 +523,7 @@ def contribution_lists(sys, mode=REDUCED):
 # dense Newton (tiny grids only; task (3) by a library dense solve)
 # ---------------------------------------------------------------------------
 
-def newton_dense(sys, x0, mode=REDUCED, tol=1e-10, max_iter=30):
+def newton_dense(sys, x0, mode=REDUCED, tol=1e-10, max_iter=30, gen_mode=None, gen_qlim=None):
     """Newton iterations on the formulation's unknowns with a dense solve.
 
     Returns (x, history of ||F||_inf).  Stops when ||F||_inf <= tol.
@@ -530,11 +542,45 @@ def newton_dense(sys, x0, mode=REDUCED, tol=1e-10, max_iter=30):
         col_x[fm.col_ps] = 2 * n + fm.gens.shape[0]
     hist = []
     for _ in range(max_iter):
-        F = residual(sys, x, mode)
+        F = residual(sys, x, mode, gen_mode=gen_mode, gen_qlim=gen_qlim)
         hist.append(float(np.max(np.abs(F))) if F.size else 0.0)
         if hist[-1] <= tol:
             break
-        rp, ci, jv = jacobian(sys, x, mode)
+        rp, ci, jv = jacobian(sys, x, mode, gen_mode)
         J = csr_to_dense(rp, ci, jv, fm.n_cols)
         x[col_x] -= np.linalg.solve(J, F)
     return x, hist
+
+
+def newton_qlim(sys, x0, q_min, q_max, tol=1e-10, max_iter=30, max_switch_rounds=20):
+    """Extended-formulation Newton with reactive limits (Sec. II-A: limits are
+    checked between solves and a generator that violates one is held at it,
+    the formulation unchanged).  Generators in voltage control whose Q_g ends
+    above q_max or below q_min are switched to that limit and the system is
+    solved again, until no generator in voltage control violates a limit.
+    Generators are the PV units in input order, then the slack.
+
+    Returns (x, gen_mode, gen_qlim, rounds): gen_mode 0 = voltage control,
+    1 = held at q_max, 2 = held at q_min.
+    """
+    n = sys.n_bus
+    ng = sys.n_pv + 1
+    q_min = np.asarray(q_min, float)
+    q_max = np.asarray(q_max, float)
+    gen_mode = np.zeros(ng, np.int8)
+    gen_qlim = np.zeros(ng)
+    x = np.array(x0, dtype=float)
+    for rounds in range(1, max_switch_rounds + 1):
+        x, hist = newton_dense(sys, x, EXTENDED, tol, max_iter, gen_mode, gen_qlim)
+        if hist[-1] > tol:
+            raise RuntimeError("Newton did not converge")
+        qg = x[2 * n:2 * n + ng]
+        hi = (gen_mode == 0) & (qg > q_max)
+        lo = (gen_mode == 0) & (qg < q_min)
+        if not (hi.any() or lo.any()):
+            return x, gen_mode, gen_qlim, rounds
+        gen_mode[hi] = 1
+        gen_qlim[hi] = q_max[hi]
+        gen_mode[lo] = 2
+        gen_qlim[lo] = q_min[lo]
+    raise RuntimeError("reactive-limit switching did not settle")

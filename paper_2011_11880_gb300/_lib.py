@@ -46,12 +46,14 @@ class PfDims(ctypes.Structure):
         ("formulation", c_int32), ("n_grids", c_int32), ("n_instances", c_int32), ("max_degree", c_int32),
         ("n_bus", c_int64), ("n_branch", c_int64), ("n_inc", c_int64), ("n_x", c_int64),
         ("n_f", c_int64), ("nnz", c_int64), ("n_bus_inst", c_int64), ("n_branch_inst", c_int64),
+        ("n_gen_inst", c_int64),
     ]
 
 
 class PfOverrides(ctypes.Structure):
     _fields_ = [("p_inj", c_void_p), ("q_inj", c_void_p), ("status", c_void_p),
-                ("br_r", c_void_p), ("br_x", c_void_p), ("br_b", c_void_p), ("br_tap", c_void_p)]
+                ("br_r", c_void_p), ("br_x", c_void_p), ("br_b", c_void_p), ("br_tap", c_void_p),
+                ("gen_mode", c_void_p), ("gen_qlim", c_void_p)]
 
 
 class PfGrads(ctypes.Structure):
@@ -63,11 +65,12 @@ class PfTuning(ctypes.Structure):
     _fields_ = [("tile_inc", c_int32), ("ctas_per_sm", c_int32)]
 
 
-# name -> (restype, argtypes); every symbol include/pf.h declares
 class PfNewtonInfo(ctypes.Structure):
     _fields_ = [("iterations", c_int32), ("converged", c_int32), ("max_mismatch", ctypes.c_double),
                 ("eval_ms", ctypes.c_double), ("solve_ms", ctypes.c_double), ("update_ms", ctypes.c_double)]
 
+
+# name -> (restype, argtypes); every symbol include/pf.h declares
 
 SIGNATURES = {
     "pf_build": (c_int32, [P(PfSystem), c_int32, c_void_p, P(c_void_p)]),
@@ -88,6 +91,8 @@ SIGNATURES = {
     "pf_residual_jacobian_host": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "pf_vjp": (c_int32, [c_void_p, c_void_p, P(PfOverrides), c_void_p, c_int32, P(PfGrads), c_void_p]),
     "pf_newton": (c_int32, [c_void_p, c_void_p, ctypes.c_double, c_int32, c_void_p, P(PfNewtonInfo)]),
+    "pf_newton_qlim": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_double,
+                                 c_int32, c_int32, c_void_p, P(PfNewtonInfo), P(c_int32)]),
     "pf_mismatch_norm": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "pf_newton_update": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "pf_get_tuning": (c_int32, [c_void_p, P(PfTuning)]),

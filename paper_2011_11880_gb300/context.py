@@ -82,6 +82,7 @@ class Dims:
     nnz: int
     n_bus_inst: int
     n_branch_inst: int
+    n_gen_inst: int
 
 
 class Context:
@@ -177,8 +178,9 @@ class Context:
         return torch.empty(self.dims.nnz, dtype=torch.float64, device=device or "cuda")
 
     # ---- evaluation ----
-    def _overrides(self, p_inj=None, q_inj=None, status=None, br_r=None, br_x=None, br_b=None, br_tap=None):
-        if all(v is None for v in (p_inj, q_inj, status, br_r, br_x, br_b, br_tap)):
+    def _overrides(self, p_inj=None, q_inj=None, status=None, br_r=None, br_x=None, br_b=None, br_tap=None,
+                   gen_mode=None, gen_qlim=None):
+        if all(v is None for v in (p_inj, q_inj, status, br_r, br_x, br_b, br_tap, gen_mode, gen_qlim)):
             return None
         d = self.dims
         ov = PfOverrides()
@@ -189,6 +191,8 @@ class Context:
         ov.br_x = _ptr(br_x, numel=d.n_branch, name="br_x")
         ov.br_b = _ptr(br_b, numel=d.n_branch, name="br_b")
         ov.br_tap = _ptr(br_tap, numel=d.n_branch, name="br_tap")
+        ov.gen_mode = _ptr(gen_mode, torch.uint8, d.n_gen_inst, "gen_mode")
+        ov.gen_qlim = _ptr(gen_qlim, numel=d.n_gen_inst, name="gen_qlim")
         return ov
 
     def eval(self, x, F=None, vals=None, stream=None, **overrides):
@@ -268,6 +272,26 @@ class Context:
         check(self._lib.pf_newton(self._h, _ptr(x, numel=self.dims.n_x, name="x"), float(tol), int(max_iter),
                                   _stream(stream), ctypes.byref(info)), "pf_newton")
         return {k: getattr(info, k) for k, _ in PfNewtonInfo._fields_}
+
+    def newton_qlim(self, x, q_min, q_max, gen_mode=None, gen_qlim=None, tol: float = 1e-10, max_iter: int = 20,
+                    max_rounds: int = 20, stream=None):
+        """Extended-formulation Newton with reactive limits, x updated in place.
+        gen_mode (uint8) / gen_qlim: starting modes (default all zero: voltage
+        control), updated in place.  Returns (info dict, rounds, gen_mode, gen_qlim)."""
+        d = self.dims
+        if gen_mode is None:
+            gen_mode = torch.zeros(d.n_gen_inst, dtype=torch.uint8, device=x.device)
+        if gen_qlim is None:
+            gen_qlim = torch.zeros(d.n_gen_inst, dtype=torch.float64, device=x.device)
+        info = PfNewtonInfo()
+        rounds = ctypes.c_int32(0)
+        check(self._lib.pf_newton_qlim(self._h, _ptr(x, numel=d.n_x, name="x"), _ptr(q_min, numel=d.n_gen_inst,
+                                       name="q_min"), _ptr(q_max, numel=d.n_gen_inst, name="q_max"),
+                                       _ptr(gen_mode, torch.uint8, d.n_gen_inst, "gen_mode"),
+                                       _ptr(gen_qlim, numel=d.n_gen_inst, name="gen_qlim"), float(tol),
+                                       int(max_iter), int(max_rounds), _stream(stream), ctypes.byref(info),
+                                       ctypes.byref(rounds)), "pf_newton_qlim")
+        return {k: getattr(info, k) for k, _ in PfNewtonInfo._fields_}, rounds.value, gen_mode, gen_qlim
 
     def mismatch_norm(self, F, stream=None):
         """max |F| per instance ([n_inst] float64 CUDA tensor)."""

@@ -40,6 +40,7 @@ struct VjpArgs {
   const double2 *sgb, *sgbm, *sac;    // per slot: merged own and mirror coefficients, own A, C
   const double2 *rhat;                // per bus in round order
   const uint8_t *status;
+  const uint8_t *gen_mode;  // extended, per instance-generator: != 0 held at a reactive limit
   double *gx;             // [n_cot][n_x]
 };
 
@@ -136,8 +137,13 @@ __device__ __forceinline__ void write_state_grad(const View &v, const VjpArgs &a
       gx[2 * nb + v.grid_ngen[g]] = -cot_row(a, c, f0, rp);        // d g_p / d P_s = -1
     }
     if (gi >= 0) {
-      gvv = __dadd_rn(gvv, cot_row(a, c, f0, 2 * nb + gi));       // d g_V / d V = 1
-      gx[2 * nb + gi] = -cot_row(a, c, f0, rq);                    // d g_q / d Q_g = -1
+      const double vgv = cot_row(a, c, f0, 2 * nb + gi);
+      if (a.gen_mode && a.gen_mode[v.inst_gen_off[inst] + gi]) {
+        gx[2 * nb + gi] = __dsub_rn(vgv, cot_row(a, c, f0, rq));   // d g_V / d Q_g = 1, d g_q / d Q_g = -1
+      } else {
+        gvv = __dadd_rn(gvv, vgv);                                // d g_V / d V = 1
+        gx[2 * nb + gi] = -cot_row(a, c, f0, rq);                  // d g_q / d Q_g = -1
+      }
     }
   }
   gx[lb] = gt;
@@ -543,6 +549,7 @@ int launch_vjp(Ctx &c, const double *x, const pf_overrides *ov, const double *v,
   a.gb = c.v.inc_gb; a.ac = c.v.inc_ac; a.hat = c.v.bus_hat;
   a.sgb = c.v.slot_gb; a.sgbm = c.v.slot_gbm; a.sac = c.v.slot_ac; a.rhat = c.v.rbus_hat;
   a.status = ov ? ov->status : nullptr;
+  a.gen_mode = ov ? ov->gen_mode : nullptr;
   const double *r = nullptr, *xr = nullptr, *b = nullptr, *tap = nullptr;
   if (ov && (ov->br_r || ov->br_x || ov->br_b || ov->br_tap)) {
     r = ov->br_r; xr = ov->br_x; b = ov->br_b; tap = ov->br_tap;

@@ -102,6 +102,7 @@ int pf_get_dims(const pf_ctx *ctx, pf_dims *d) {
   d->n_grids = c.v.n_grids;
   d->n_instances = c.v.n_inst;
   d->max_degree = c.max_degree;
+  d->n_gen_inst = c.n_gen_inst;
   d->n_bus = c.v.n_bus;
   d->n_branch = c.v.n_branch;
   d->n_inc = c.v.n_inc;
@@ -272,6 +273,17 @@ int pf_vjp(pf_ctx *ctx, const double *x, const pf_overrides *ov, const double *v
 int pf_newton(pf_ctx *ctx, double *x, double tol, int32_t max_iter, void *stream, pf_newton_info *info) {
   if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
   return pf::newton(ctx->c, x, tol, max_iter, as_stream(stream), info);
+}
+
+int pf_newton_qlim(pf_ctx *ctx, double *x, const double *q_min, const double *q_max, uint8_t *gen_mode,
+                   double *gen_qlim, double tol, int32_t max_iter, int32_t max_rounds, void *stream,
+                   pf_newton_info *info, int32_t *rounds) {
+  if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
+  int r = 0;
+  PF_TRY(pf::newton_qlim(ctx->c, x, q_min, q_max, gen_mode, gen_qlim, tol, max_iter, max_rounds,
+                         as_stream(stream), info, &r));
+  if (rounds) *rounds = r;
+  return PF_OK;
 }
 
 int pf_mismatch_norm(pf_ctx *ctx, const double *F, double *norms, void *stream) {

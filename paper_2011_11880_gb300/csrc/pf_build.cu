@@ -256,14 +256,16 @@ __global__ void k_row_struct(View v, const int64_t *grid_f_off, int2 *inc_rt, in
   if (v.row_q[o] >= 0) rowlen[grid_f_off[g] + v.row_q[o]] = nth + nv + ((ext && v.gen[o] >= 0) ? 1 : 0);
 }
 
-// extended: one-entry rows g_V (per generator) and g_theta (per grid)
+// extended: rows g_V (per generator: entries at V_b and at Q_g, so that the
+// row serves voltage control and a held reactive limit alike) and g_theta
+// (per grid, one entry)
 __global__ void k_gen_rowlen(View v, const int64_t *grid_f_off, int32_t *rowlen, int64_t n_gen_tot) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n_gen_tot) {
     const int32_t b = v.gen_bus[i];
     const int g = v.bus_grid[b];
     const int64_t gi = i - v.grid_gen_off[g];
-    rowlen[grid_f_off[g] + 2 * (int64_t)v.grid_nbus[g] + gi] = 1;
+    rowlen[grid_f_off[g] + 2 * (int64_t)v.grid_nbus[g] + gi] = 2;
   }
   if (i < v.n_grids) {
     const int g = (int)i;
@@ -323,8 +325,9 @@ __global__ void k_gen_cols(View v, const int32_t *rowptr, const int64_t *grid_ro
     const int64_t gi = i - v.grid_gen_off[g];
     const int32_t row = 2 * v.grid_nbus[g] + (int32_t)gi;
     const int32_t pos = rowptr[grid_row_off[g] + row];
-    colind[grid_nnz_off[g] + pos] = v.row_q[b];
-    gen_pos[i] = pos;
+    colind[grid_nnz_off[g] + pos] = v.row_q[b];                    // V_b column (< 2 N)
+    colind[grid_nnz_off[g] + pos + 1] = 2 * v.grid_nbus[g] + (int32_t)gi;   // Q_g column
+    gen_pos[i] = pos;                                              // the Q_g entry is at pos + 1
   }
   if (i < v.n_grids) {
     const int g = (int)i;
@@ -561,7 +564,10 @@ __global__ void k_contrib_const(View v, int pass, const int64_t *grid_nnz_off, c
     if (pass == 0) count[grid_nnz_off[g] + pos] = 1;
     else src[grid_csrc_off[g] + cptr[grid_cptr_off[g] + pos]] = -1;
   };
-  if (i < n_gen_tot) put(v.bus_grid[v.gen_bus[i]], gen_pos[i]);
+  if (i < n_gen_tot) {
+    put(v.bus_grid[v.gen_bus[i]], gen_pos[i]);
+    put(v.bus_grid[v.gen_bus[i]], gen_pos[i] + 1);
+  }
   if (i < v.n_grids) put((int)i, grid_pos_gth[i]);
 }
 
@@ -1346,6 +1352,7 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
   c.v_off.assign(n_inst + 1, 0);
   c.bus_off.assign(n_inst + 1, 0);
   c.br_off.assign(n_inst + 1, 0);
+  c.gen_off.assign(n_inst + 1, 0);
   c.any_outage = false;
   for (int i = 0; i < n_inst; ++i) {
     const int g = inst[i].grid;
@@ -1357,14 +1364,16 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
     c.v_off[i + 1] = c.v_off[i] + c.grid_nnz[g];
     c.bus_off[i + 1] = c.bus_off[i] + h_grid_nbus[g];
     c.br_off[i + 1] = c.br_off[i] + h_grid_nbr[g];
+    c.gen_off[i + 1] = c.gen_off[i] + h_grid_ngen[g];
   }
+  c.n_gen_inst = c.gen_off[n_inst];
   c.n_x = c.x_off[n_inst];
   c.n_f = c.f_off[n_inst];
   c.nnz = c.v_off[n_inst];
   v.n_bus_inst = c.bus_off[n_inst];
   c.n_branch_inst = c.br_off[n_inst];
   int32_t *d_inst_grid, *d_inst_outage;
-  int64_t *d_x_off, *d_f_off, *d_v_off, *d_bus_off, *d_br_off;
+  int64_t *d_x_off, *d_f_off, *d_v_off, *d_bus_off, *d_br_off, *d_gen_off;
   PF_TRY(upload(c, &d_inst_grid, c.inst_grid, s));
   PF_TRY(upload(c, &d_inst_outage, c.inst_outage, s));
   PF_TRY(upload(c, &d_x_off, c.x_off, s));
@@ -1372,9 +1381,10 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
   PF_TRY(upload(c, &d_v_off, c.v_off, s));
   PF_TRY(upload(c, &d_bus_off, c.bus_off, s));
   PF_TRY(upload(c, &d_br_off, c.br_off, s));
+  PF_TRY(upload(c, &d_gen_off, c.gen_off, s));
   v.inst_grid = d_inst_grid; v.inst_outage = d_inst_outage;
   v.inst_x_off = d_x_off; v.inst_f_off = d_f_off; v.inst_v_off = d_v_off;
-  v.inst_bus_off = d_bus_off; v.inst_br_off = d_br_off;
+  v.inst_bus_off = d_bus_off; v.inst_br_off = d_br_off; v.inst_gen_off = d_gen_off;
   PF_TRY(dev_alloc(c, &v.phasor, 2 * v.n_bus_inst));
 
   int dev = 0;

@@ -112,6 +112,8 @@ struct EvalArgs {
   const double *p_inj;     // per-instance-bus override or nullptr
   const double *q_inj;
   const uint8_t *status;   // per-instance-branch mask or nullptr
+  const uint8_t *gen_mode; // extended, per instance-generator: != 0 holds Q_g at gen_qlim, or nullptr
+  const double *gen_qlim;
 };
 
 // Rotated terms of one branch end (own phasor po, other phasor pk).
@@ -240,8 +242,11 @@ __device__ __forceinline__ void finalize_bus(const View &v, const EvalArgs &a, i
       Fi[v.grid_row_gth[g]] = __dsub_rn(xi[lb], v.grid_theta_set[g]);
     }
     if (gi >= 0) {
-      fq = __dsub_rn(fq, xi[2 * nb + gi]);
-      Fi[2 * nb + gi] = __dsub_rn(vo, v.gen_vset[v.grid_gen_off[g] + gi]);
+      const double qg = xi[2 * nb + gi];
+      fq = __dsub_rn(fq, qg);
+      const int64_t gq = v.inst_gen_off[inst] + gi;
+      Fi[2 * nb + gi] = (a.gen_mode && a.gen_mode[gq]) ? __dsub_rn(qg, a.gen_qlim[gq])       // held at a limit
+                                                       : __dsub_rn(vo, v.gen_vset[v.grid_gen_off[g] + gi]);
     }
     if (rp >= 0) Fi[rp] = fp;
     if (rq >= 0) Fi[rq] = fq;
@@ -262,7 +267,10 @@ __device__ __forceinline__ void finalize_bus(const View &v, const EvalArgs &a, i
     }
     if (gi >= 0) {
       vi[bq + bm2.z] = -1.0;                // d g_q / d Q_g
-      vi[v.gen_pos[v.grid_gen_off[g] + gi]] = 1.0;  // d g_V / d V
+      const bool held = a.gen_mode && a.gen_mode[v.inst_gen_off[inst] + gi];
+      const int32_t p = v.gen_pos[v.grid_gen_off[g] + gi];
+      vi[p] = held ? 0.0 : 1.0;             // d g_V / d V
+      vi[p + 1] = held ? 1.0 : 0.0;         // d g_V / d Q_g
     }
   }
 }
@@ -579,6 +587,9 @@ int launch_eval_stages(Ctx &c, int stages, const double *x, const pf_overrides *
     a.p_inj = ov->p_inj;
     a.q_inj = ov->q_inj;
     a.status = ov->status;
+    a.gen_mode = ov->gen_mode;
+    a.gen_qlim = ov->gen_qlim;
+    if (ov->gen_mode && !ov->gen_qlim) return fail(PF_ERR_INVALID, "gen_mode needs gen_qlim");
     if (ov->br_r || ov->br_x || ov->br_b || ov->br_tap) {
       if (stages & 2) {
         PF_TRY(compute_coefficients(c, ov->br_r, ov->br_x, ov->br_b, ov->br_tap, c.ov_gb, c.ov_ac, c.ov_hat, s));

@@ -124,6 +124,7 @@ struct View {
   // per instance
   const int32_t *inst_grid, *inst_outage;     // outage: global branch id or -1
   const int64_t *inst_x_off, *inst_f_off, *inst_v_off, *inst_bus_off, *inst_br_off;
+  const int64_t *inst_gen_off;                // extended: generators of earlier instances
 
   // scratch
   double2 *phasor;                            // [2 n_bus_inst]: (cos theta, sin theta), (V, 0) per bus
@@ -143,7 +144,8 @@ struct Ctx {
       grid_csrc_off, grid_sh_off;
   std::vector<int32_t> grid_nf, grid_nnz, grid_nx, grid_nshunt;
   std::vector<int32_t> inst_grid, inst_outage;
-  std::vector<int64_t> x_off, f_off, v_off, bus_off, br_off;
+  std::vector<int64_t> x_off, f_off, v_off, bus_off, br_off, gen_off;
+  int64_t n_gen_inst = 0;
   bool any_outage = false;
 
   // device arrays not in View
@@ -203,7 +205,10 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
 // Copies per-call coefficients (incidence / bus order) into slot / round order.
 int permute_overrides(Ctx &c, cudaStream_t s);
 // Newton iterations (pf_newton.cu).
-int newton(Ctx &c, double *x, double tol, int max_iter, cudaStream_t s, pf_newton_info *info);
+int newton(Ctx &c, double *x, double tol, int max_iter, cudaStream_t s, pf_newton_info *info,
+           const pf_overrides *ov = nullptr);
+int newton_qlim(Ctx &c, double *x, const double *q_min, const double *q_max, uint8_t *mode, double *qlim, double tol,
+                int max_iter, int max_rounds, cudaStream_t s, pf_newton_info *info, int *rounds);
 int newton_norms(Ctx &c, const double *F, double *norms, cudaStream_t s);
 int newton_update(Ctx &c, double *x, const double *dx, cudaStream_t s);
 // F and J of the instances [i0, i1) only (pf_eval.cu; built coefficients, no overrides).

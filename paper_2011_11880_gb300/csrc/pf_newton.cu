@@ -55,12 +55,38 @@ __global__ void k_newton_update(View v, double *__restrict__ x, const double *__
   }
 }
 
+// Reactive limits (Sec. II-A): a generator in voltage control whose Q_g lies
+// above q_max or below q_min is switched to that limit.  One thread per
+// instance-generator; counts the switches.
+__global__ void k_qlim_check(View v, const double *__restrict__ x, const double *__restrict__ q_min,
+                             const double *__restrict__ q_max, uint8_t *__restrict__ mode, double *__restrict__ qlim,
+                             int64_t n_gen_inst, unsigned int *__restrict__ switched) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_gen_inst; q += stride) {
+    if (mode[q] != 0) continue;
+    const int inst = v.n_inst == 1 ? 0 : find_segment(v.inst_gen_off, v.n_inst, q);
+    const int g = v.inst_grid[inst];
+    const int64_t gi = q - v.inst_gen_off[inst];
+    const double qg = x[v.inst_x_off[inst] + 2 * (int64_t)v.grid_nbus[g] + gi];
+    if (qg > q_max[q]) {
+      mode[q] = 1;
+      qlim[q] = q_max[q];
+      atomicAdd(switched, 1u);
+    } else if (qg < q_min[q]) {
+      mode[q] = 2;
+      qlim[q] = q_min[q];
+      atomicAdd(switched, 1u);
+    }
+  }
+}
+
 struct Solver {
   cusolverSpHandle_t sp = nullptr;
   cusparseMatDescr_t descr = nullptr;
   double *F = nullptr, *vals = nullptr, *dx = nullptr;
   unsigned long long *norm = nullptr;
   int64_t *f_off = nullptr;
+  unsigned int *switched = nullptr;
 };
 
 int make_solver(Ctx &c, Solver **out) {
@@ -85,6 +111,7 @@ int make_solver(Ctx &c, Solver **out) {
   PF_TRY(dev_alloc(c, &S->vals, c.nnz));
   PF_TRY(dev_alloc(c, &S->dx, c.n_f));
   PF_TRY(dev_alloc(c, &S->norm, c.v.n_inst));
+  PF_TRY(dev_alloc(c, &S->switched, 1));
   PF_TRY(upload(c, &S->f_off, c.f_off, nullptr));
   *out = S;
   return PF_OK;
@@ -122,7 +149,8 @@ int newton_norms(Ctx &c, const double *F, double *norms, cudaStream_t s) {
 
 int newton_update(Ctx &c, double *x, const double *dx, cudaStream_t s) { return launch_update(c, x, dx, s); }
 
-int newton(Ctx &c, double *x, double tol, int max_iter, cudaStream_t s, pf_newton_info *info) {
+int newton(Ctx &c, double *x, double tol, int max_iter, cudaStream_t s, pf_newton_info *info,
+           const pf_overrides *ov) {
   if (!x) return fail(PF_ERR_INVALID, "x is NULL");
   if (max_iter < 0 || !(tol >= 0.0)) return fail(PF_ERR_INVALID, "max_iter must be >= 0 and tol >= 0");
   Solver *S;
@@ -133,7 +161,7 @@ int newton(Ctx &c, double *x, double tol, int max_iter, cudaStream_t s, pf_newto
   std::vector<unsigned long long> h_norm(I);
   for (int it = 0;; ++it) {
     auto t0 = std::chrono::steady_clock::now();
-    PF_TRY(launch_eval(c, x, nullptr, S->F, S->vals, s));
+    PF_TRY(launch_eval(c, x, ov, S->F, S->vals, s));
     PF_TRY(launch_norm(c, S->f_off, S->F, S->norm, s));
     PF_CUDA_TRY(cudaMemcpyAsync(h_norm.data(), S->norm, I * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     PF_CUDA_TRY(cudaStreamSynchronize(s));
@@ -182,6 +210,49 @@ int newton(Ctx &c, double *x, double tol, int max_iter, cudaStream_t s, pf_newto
     r.iterations = it + 1;
   }
   if (info) *info = r;
+  return PF_OK;
+}
+
+int newton_qlim(Ctx &c, double *x, const double *q_min, const double *q_max, uint8_t *mode, double *qlim, double tol,
+                int max_iter, int max_rounds, cudaStream_t s, pf_newton_info *info, int *rounds) {
+  if (c.v.formulation != PF_EXTENDED) return fail(PF_ERR_INVALID, "reactive limits need the extended formulation");
+  if (!x || !mode || !qlim || ((!q_min || !q_max) && c.n_gen_inst > 0))
+    return fail(PF_ERR_INVALID, "x, q_min, q_max, gen_mode and gen_qlim must not be NULL");
+  if (max_rounds < 1) return fail(PF_ERR_INVALID, "max_rounds must be >= 1");
+  Solver *S;
+  PF_TRY(make_solver(c, &S));
+  pf_overrides ov{};
+  ov.gen_mode = mode;
+  ov.gen_qlim = qlim;
+  pf_newton_info total{};
+  int r = 0;
+  for (r = 1; r <= max_rounds; ++r) {
+    pf_newton_info one{};
+    PF_TRY(newton(c, x, tol, max_iter, s, &one, &ov));
+    total.iterations += one.iterations;
+    total.eval_ms += one.eval_ms;
+    total.solve_ms += one.solve_ms;
+    total.update_ms += one.update_ms;
+    total.max_mismatch = one.max_mismatch;
+    total.converged = 0;
+    if (!one.converged) break;
+    unsigned int h_switched = 0;
+    if (c.n_gen_inst > 0) {
+      PF_CUDA_TRY(cudaMemsetAsync(S->switched, 0, sizeof(unsigned int), s));
+      const int64_t blocks = std::min<int64_t>((c.n_gen_inst + 255) / 256, (int64_t)c.num_sms * 16);
+      k_qlim_check<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(c.v, x, q_min, q_max, mode, qlim,
+                                                                         c.n_gen_inst, S->switched);
+      PF_CUDA_TRY(cudaGetLastError());
+      PF_CUDA_TRY(cudaMemcpyAsync(&h_switched, S->switched, sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+      PF_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    if (h_switched == 0) {
+      total.converged = 1;
+      break;
+    }
+  }
+  if (info) *info = total;
+  if (rounds) *rounds = std::min(r, max_rounds);
   return PF_OK;
 }
 

@@ -121,6 +121,7 @@ def structural_pattern(sys, fm):
         for gi, b in enumerate(fm.gens):
             P[fm.row_q[b], fm.col_qg[gi]] = True
             P[fm.row_gv[gi], fm.col_v[b]] = True
+            P[fm.row_gv[gi], fm.col_qg[gi]] = True     # g_V held at a reactive limit: Q_g - Q_lim
         P[fm.row_p[sys.slack_bus], fm.col_ps] = True
         P[fm.row_gth, fm.col_th[sys.slack_bus]] = True
     return P

@@ -106,3 +106,68 @@ def test_mismatch_norm_and_update(P):
         ok = fm.col_v >= 0
         want[n + np.arange(n)[ok]] -= d[fm.col_v[ok]]
         assert np.array_equal(x2[ctx.x_off[k]:ctx.x_off[k + 1]], want)
+
+
+def _modes(sys, seed):
+    rng = np.random.default_rng(seed)
+    ng = sys.n_pv + 1
+    return rng.integers(0, 3, ng).astype(np.uint8), rng.uniform(-0.5, 0.8, ng)
+
+
+def test_generator_modes_match_oracle(P):
+    """Extended formulation with generators held at reactive limits (F, J and the VJP), in a
+    batch where every instance has its own modes."""
+    grids = [gridgen.synthetic_grid(30, 7, n_branch=39, cluster=10), gridgen.grid_200()]
+    inst = [(0, -1), (1, -1), (1, 11), (0, 4)]
+    ctx = P.Context(grids, "extended", instances=inst)
+    xs, modes, qlims = [], [], []
+    for k, (g, _) in enumerate(inst):
+        xs.append(gridgen.perturbed_state(grids[g], k + 1, True))
+        m, q = _modes(grids[g], 20 + k)
+        modes.append(m)
+        qlims.append(q)
+    assert ctx.dims.n_gen_inst == sum(m.shape[0] for m in modes)
+    X = cuda(np.concatenate(xs))
+    gm = torch.from_numpy(np.concatenate(modes)).cuda()
+    gq = cuda(np.concatenate(qlims))
+    F, V = ctx.eval(X, ctx.empty_f(), ctx.empty_vals(), gen_mode=gm, gen_qlim=gq)
+    Fh, Vh = F.cpu().numpy(), V.cpu().numpy()
+    v = gridgen.gaussian_cotangents(ctx.dims.n_f, 1)[0]
+    gx = ctx.vjp(X, cuda(v), 1, want=("x",), gen_mode=gm, gen_qlim=gq)["x"][0].cpu().numpy()
+    for k, (g, out) in enumerate(inst):
+        sysk = with_outage(grids[g], out)
+        f = Fh[ctx.f_off[k]:ctx.f_off[k + 1]]
+        assert_tol(f, oracle.residual(sysk, xs[k], EXTENDED, gen_mode=modes[k], gen_qlim=qlims[k]), f"F {k}")
+        assert_tol(Vh[ctx.nnz_off[k]:ctx.nnz_off[k + 1]],
+                   oracle.jacobian(sysk, xs[k], EXTENDED, gen_mode=modes[k])[2], f"J {k}")
+        vk = v[ctx.f_off[k]:ctx.f_off[k + 1]]
+        assert_tol(gx[ctx.x_off[k]:ctx.x_off[k + 1]],
+                   oracle.vjp(sysk, xs[k], vk, EXTENDED, gen_mode=modes[k])["x"], f"v^T J {k}")
+    # without modes every generator is in voltage control: the held entries are explicit zeros
+    F0, V0 = ctx.residual_jacobian(X)
+    for k, (g, out) in enumerate(inst):
+        sysk = with_outage(grids[g], out)
+        assert_tol(V0[ctx.nnz_off[k]:ctx.nnz_off[k + 1]].cpu().numpy(),
+                   oracle.jacobian(sysk, xs[k], EXTENDED)[2], f"J voltage control {k}")
+
+
+def test_newton_with_reactive_limits_matches_oracle(P):
+    sys = gridgen.grid_200()
+    n = sys.n_bus
+    ng = sys.n_pv + 1
+    x0 = gridgen.flat_state(sys, True)
+    xe, _ = oracle.newton_dense(sys, x0, EXTENDED)
+    q0 = xe[2 * n:2 * n + ng]
+    q_max = np.full(ng, 1e30)
+    q_min = np.full(ng, -1e30)
+    q_max[[2, 9, 21]] = q0[[2, 9, 21]] - 0.05
+    q_min[[5, 30]] = q0[[5, 30]] + 0.05
+    xo, mo, qo, ro = oracle.newton_qlim(sys, x0, q_min, q_max)
+    ctx = P.Context(sys, "extended")
+    x = cuda(x0)
+    info, rounds, gm, gq = ctx.newton_qlim(x, cuda(q_min), cuda(q_max), tol=1e-10)
+    assert info["converged"] == 1 and rounds == ro
+    assert np.array_equal(gm.cpu().numpy(), mo)
+    assert np.max(np.abs(x.cpu().numpy() - xo)) <= 1e-8
+    held = mo != 0
+    assert np.array_equal(gq.cpu().numpy()[held], qo[held])
