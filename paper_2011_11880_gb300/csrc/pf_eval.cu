@@ -17,24 +17,26 @@
 //     F_P = V_o (V_o A^ - sum a) - P_inj,    F_Q = -V_o (V_o C^ + sum b) - Q_inj,
 //     dF_P/dt_o = V_o sum b,   dF_Q/dt_o = -V_o sum a,
 //     dF_P/dV_o = 2 V_o A^ - sum a,   dF_Q/dV_o = -2 V_o C^ - sum b,
-// where A^ = sum A + shunt g and C^ = sum C + shunt b.  No division; 14
-// FP64 operations per branch end plus two adds into its bus's sums.
+// where A^ = sum A + shunt g and C^ = sum C + shunt b.  No division; per
+// pair of connected buses (parallel branches merged into one end with their
+// coefficients summed) 8 FP64 operations for u, w, xh, yh, 2 for a and b, 2
+// adds into the bus sums and one multiply per J value.
 //
-// Work decomposition.  The buses of each grid are sorted by degree (number
-// of branch ends) and cut into rounds of 32; one warp evaluates one round,
-// one bus per lane.  A lane walks its bus's ends in incidence-list order,
-// computes each end's terms, writes the end's off-diagonal J entries (a group
-// of parallel branches is summed in list order and written at its last end),
-// keeps the bus sums in registers, and finally writes the bus's F rows and
-// diagonal J entries.  Because the buses of a round have the same degree,
+// Work decomposition.  The buses of each grid are sorted by their number of
+// neighbours and cut into rounds of 32; one warp evaluates one round, one bus
+// per lane.  A lane walks its bus's pairs in incidence-list order, computes
+// each pair's terms, writes the pair's four off-diagonal J entries, keeps the
+// bus sums in registers, and finally writes the bus's F rows and diagonal J
+// entries.  Because the buses of a round have the same number of pairs,
 // nearly every lane does useful FP64 work at every step.  A bus with more
-// than 32 ends is evaluated by a whole warp in a second kernel.
+// than 32 neighbours is evaluated by a whole warp in a second kernel.
 //
 // Determinism: every operation is an explicitly rounded intrinsic and every
-// sum runs in a fixed order -- incidence-list order for a bus with up to 32
-// ends and for every group of parallel branches, lane-strided partial sums
-// combined by a fixed butterfly for a bus with more ends -- so results are
-// bit-identical run to run, across code paths and for every tuning.
+// sum runs in a fixed order -- a group's coefficients and a bus's pairs in
+// incidence-list order for a bus with up to 32 neighbours, lane-strided
+// partial sums over its ends combined by a fixed butterfly for a larger bus
+// -- so results are bit-identical run to run, across code paths and for every
+// tuning.
 #include <algorithm>
 
 #include "pf_internal.cuh"
