@@ -186,12 +186,17 @@ def fused_fp64_ops(d, n_pairs):
 
 
 def source_hash():
-    """Hash of the sources that decide k_fused's memory traffic (kernel and data layout)."""
+    """Hash of the code (comments and blank space removed) of the sources that
+    decide k_fused's memory traffic: the kernel and the data layout."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ("pf_eval.cu", "pf_build.cu", "pf_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2011_11880_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2011_11880_gb300", "csrc", f)) as fh:
+            code = fh.read()
+        code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
+        code = re.sub(r"//[^\n]*", " ", code)
+        h.update(" ".join(code.split()).encode())
     return h.hexdigest()[:16]
 
 
