@@ -226,3 +226,32 @@ def test_host_buffers_pipelined_batch(P):
         F_only = np.empty(ctx.dims.n_f)
         ctx.residual_jacobian_host(xh, F_only, None)
         assert np.array_equal(F_only, F_d)
+
+
+@pytest.mark.parametrize("mode", [REDUCED, EXTENDED])
+def test_large_bus_under_outages_and_modes(P, mode):
+    """The warp-per-bus kernel (a hub with 1,500 neighbours) under branch outages, with a PV
+    unit on the hub held at a reactive limit in the extended formulation."""
+    sys = star_grid(1500)
+    sys.pv_bus = sys.pv_bus.copy()
+    sys.pv_bus[0] = 0                                   # a generator on the hub
+    inst = [(0, -1), (0, 0), (0, 1), (0, 1503)]          # outages of hub branches and of a parallel one
+    ctx = P.Context([sys], MNAME[mode], instances=inst)
+    xs = [gridgen.perturbed_state(sys, k + 1, mode == EXTENDED) for k in range(len(inst))]
+    ov = {}
+    gm = None
+    if mode == EXTENDED:
+        ng = sys.n_pv + 1
+        gm = np.zeros(ng, np.uint8)
+        gm[0] = 1
+        gq = np.full(ng, 0.25)
+        ov = dict(gen_mode=torch.from_numpy(np.tile(gm, len(inst))).cuda(), gen_qlim=cuda(np.tile(gq, len(inst))))
+    F, V = ctx.eval(cuda(np.concatenate(xs)), ctx.empty_f(), ctx.empty_vals(), **ov)
+    Fh, Vh = F.cpu().numpy(), V.cpu().numpy()
+    for k, (_, out) in enumerate(inst):
+        sk = with_outage(sys, out)
+        kw = dict(gen_mode=gm, gen_qlim=np.full(sys.n_pv + 1, 0.25)) if mode == EXTENDED else {}
+        assert_tol(Fh[ctx.f_off[k]:ctx.f_off[k + 1]], oracle.residual(sk, xs[k], mode, **kw), f"F {k}")
+        jkw = dict(gen_mode=gm) if mode == EXTENDED else {}
+        assert_tol(Vh[ctx.nnz_off[k]:ctx.nnz_off[k + 1]], oracle.jacobian(sk, xs[k], mode, **jkw)[2], f"J {k}")
+    ctx.check_device()
