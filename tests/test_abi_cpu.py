@@ -72,8 +72,9 @@ def test_struct_layout_matches_c(tmp_path):
 
 
 def test_error_strings(lib):
-    for code in range(7):
-        assert lib.pf_error_string(code)
+    for code in range(8):
+        assert lib.pf_error_string(code) and lib.pf_error_string(code) != b"unknown error code"
+    assert lib.pf_error_string(99) == b"unknown error code"
 
 
 def _build(lib, sys, formulation=0):
@@ -130,3 +131,27 @@ def test_null_arguments(lib):
     assert lib.pf_residual(None, None, None, None) == 1
     assert lib.pf_get_dims(None, None) == 1
     lib.pf_destroy(None)
+
+
+def _build_batch(lib, systems, instances, formulation=0):
+    from paper_2011_11880_gb300._lib import PfInstance, PfSystem
+    from paper_2011_11880_gb300.context import _SystemArrays
+    arrs = [_SystemArrays(x) for x in systems]
+    grids = (PfSystem * len(arrs))(*[a.struct for a in arrs])
+    inst = (PfInstance * max(len(instances), 1))(*[PfInstance(g, o) for g, o in instances])
+    h = ctypes.c_void_p()
+    rc = lib.pf_build_batch(grids, len(arrs), inst if instances else None, len(instances), formulation, None,
+                            ctypes.byref(h))
+    return rc, (lib.pf_last_error() or b"").decode(), h
+
+
+@pytest.mark.parametrize("instances,expect", [
+    ([], "no instances"),
+    ([(0, -1), (1, -1)], "grid index out of range"),
+    ([(0, 2)], "outage branch out of range"),
+    ([(0, -2)], "outage branch out of range"),
+])
+def test_batch_validation_rejects(lib, instances, expect):
+    rc, msg, h = _build_batch(lib, [base_system()], instances)
+    assert rc == 1 and expect in msg, (rc, msg)
+    assert not h.value
