@@ -297,11 +297,19 @@ typedef struct pf_newton_info {
   double update_ms;              /* ... in the updates (task 4)                         */
 } pf_newton_info;
 
+/* Linear solver of the Newton loop (a library solve, outside the hot path). */
+#define PF_SOLVER_LU 0        /* default: LU refactorization -- a host LU of the first J (METIS
+                                 ordering, partial pivoting) fixes the ordering, pivots and
+                                 factor patterns; cuSOLVER-Rf refactors every later J and solves
+                                 on the device */
+#define PF_SOLVER_QR 1        /* cuSOLVER's device sparse QR, from scratch every iteration */
+PF_API int pf_set_newton_solver(pf_ctx *ctx, int32_t solver);
+
 /* Newton power flow on every instance: repeat { F, J at x (this library's
  * kernels); stop when max |F| <= tol for every instance; per instance that
- * has not converged, solve J dx = F (cuSOLVER sparse QR with METIS
- * ordering: a library solve, outside the hot path); x <- x - dx on the
- * unknowns (task 4, on the device) } for at most max_iter updates.  x: the
+ * has not converged, solve J dx = F with the chosen solver;
+ * x <- x - dx on the unknowns (task 4, on the device) } for at most max_iter
+ * updates.  x: the
  * instances' states ([n_x], device), updated in place.  Synchronises `stream`
  * every iteration (the convergence test is read on the host).  Device
  * scratch (F, J values, dx) is allocated on the first call.  Errors:

@@ -273,6 +273,10 @@ class Context:
                                   _stream(stream), ctypes.byref(info)), "pf_newton")
         return {k: getattr(info, k) for k, _ in PfNewtonInfo._fields_}
 
+    def set_newton_solver(self, solver: str = "lu"):
+        """Linear solver of the Newton loop: "lu" (refactorization, default) or "qr"."""
+        check(self._lib.pf_set_newton_solver(self._h, {"lu": 0, "qr": 1}[solver]), "pf_set_newton_solver")
+
     def newton_qlim(self, x, q_min, q_max, gen_mode=None, gen_qlim=None, tol: float = 1e-10, max_iter: int = 20,
                     max_rounds: int = 20, stream=None):
         """Extended-formulation Newton with reactive limits, x updated in place.

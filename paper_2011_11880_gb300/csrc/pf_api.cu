@@ -286,6 +286,14 @@ int pf_newton_qlim(pf_ctx *ctx, double *x, const double *q_min, const double *q_
   return PF_OK;
 }
 
+int pf_set_newton_solver(pf_ctx *ctx, int32_t solver) {
+  if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
+  if (solver != PF_SOLVER_LU && solver != PF_SOLVER_QR)
+    return fail(PF_ERR_INVALID, "solver must be PF_SOLVER_LU or PF_SOLVER_QR");
+  ctx->c.newton_solver = solver;
+  return PF_OK;
+}
+
 int pf_mismatch_norm(pf_ctx *ctx, const double *F, double *norms, void *stream) {
   if (!ctx || !F || !norms) return fail(PF_ERR_INVALID, "NULL argument");
   return pf::newton_norms(ctx->c, F, norms, as_stream(stream));

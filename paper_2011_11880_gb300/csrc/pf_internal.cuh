@@ -171,6 +171,7 @@ struct Ctx {
   cudaStream_t pipe_stream[3] = {nullptr, nullptr, nullptr};
   std::vector<cudaEvent_t> pipe_events;
   // Newton-iteration state (pf_newton.cu), created on first use
+  int newton_solver = PF_SOLVER_LU;
   void *newton = nullptr;
   void (*newton_free)(void *) = nullptr;
 

@@ -11,7 +11,9 @@
 #include <vector>
 
 #define DISABLE_CUSOLVER_DEPRECATED
+#include <cusolverRf.h>
 #include <cusolverSp.h>
+#include <cusolverSp_LOWLEVEL_PREVIEW.h>
 #include <cusparse.h>
 
 #include "pf_internal.cuh"
@@ -80,9 +82,22 @@ __global__ void k_qlim_check(View v, const double *__restrict__ x, const double 
   }
 }
 
+// LU refactorization of one instance's J (the pattern is fixed, so the
+// ordering and pivoting of a first LU are reused): a host LU of the first J
+// with a METIS fill-reducing ordering and partial pivoting gives P, Q, L, U
+// (P A Q^T = L U); cuSOLVER-Rf then refactors every later J on the device and
+// solves with the factors.
+struct RfInst {
+  cusolverRfHandle_t rf = nullptr;
+  int *dP = nullptr, *dQ = nullptr;
+  double *dT = nullptr;
+};
+
 struct Solver {
   cusolverSpHandle_t sp = nullptr;
   cusparseMatDescr_t descr = nullptr;
+  std::vector<RfInst> rf;                 // per instance, created on first use
+  std::vector<std::vector<int>> h_rowptr, h_colind;   // per grid, host copies of the pattern
   double *F = nullptr, *vals = nullptr, *dx = nullptr;
   unsigned long long *norm = nullptr;
   int64_t *f_off = nullptr;
@@ -98,6 +113,12 @@ int make_solver(Ctx &c, Solver **out) {
   c.newton = S;
   c.newton_free = [](void *p) {
     Solver *s = static_cast<Solver *>(p);
+    for (RfInst &r : s->rf) {
+      if (r.rf) cusolverRfDestroy(r.rf);
+      if (r.dP) cudaFree(r.dP);
+      if (r.dQ) cudaFree(r.dQ);
+      if (r.dT) cudaFree(r.dT);
+    }
     if (s->sp) cusolverSpDestroy(s->sp);
     if (s->descr) cusparseDestroyMatDescr(s->descr);
     delete s;
@@ -131,6 +152,115 @@ int launch_update(Ctx &c, double *x, const double *dx, cudaStream_t s) {
   const int64_t blocks = std::min<int64_t>((c.v.n_bus_inst + 255) / 256, (int64_t)c.num_sms * 16);
   k_newton_update<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(c.v, x, dx);
   PF_CUDA_TRY(cudaGetLastError());
+  return PF_OK;
+}
+
+#define PF_SOLVER_TRY(expr, what)                                                             \
+  do {                                                                                        \
+    const cusolverStatus_t _st = (expr);                                                     \
+    if (_st != CUSOLVER_STATUS_SUCCESS)                                                      \
+      return fail(PF_ERR_CUDA, std::string(what) + " failed with status " + std::to_string((int)_st)); \
+  } while (0)
+
+// First factorization of instance i: host LU of its current J, then the
+// device refactorization object.
+int rf_setup(Ctx &c, Solver *S, int i, cudaStream_t s) {
+  const int g = c.inst_grid[i];
+  const int n = c.grid_nf[g], nnz = c.grid_nnz[g];
+  if (S->h_rowptr.empty()) {
+    S->h_rowptr.resize(c.v.n_grids);
+    S->h_colind.resize(c.v.n_grids);
+  }
+  std::vector<int> &rp = S->h_rowptr[g], &ci = S->h_colind[g];
+  if (rp.empty()) {
+    rp.resize(n + 1);
+    ci.resize(nnz);
+    PF_CUDA_TRY(cudaMemcpy(rp.data(), c.rowptr + c.grid_row_off[g], (n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+    PF_CUDA_TRY(cudaMemcpy(ci.data(), c.colind + c.grid_nnz_off[g], nnz * sizeof(int), cudaMemcpyDeviceToHost));
+  }
+  std::vector<double> va(nnz);
+  PF_CUDA_TRY(cudaMemcpyAsync(va.data(), S->vals + c.v_off[i], nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
+  PF_CUDA_TRY(cudaStreamSynchronize(s));
+  // fill-reducing symmetric ordering r, B = A(r, r)
+  std::vector<int> r(n), rpB(rp), ciB(ci), map(nnz);
+  PF_SOLVER_TRY(cusolverSpXcsrmetisndHost(S->sp, n, nnz, S->descr, rp.data(), ci.data(), nullptr, r.data()),
+                "cusolverSpXcsrmetisndHost");
+  size_t bytes = 0;
+  PF_SOLVER_TRY(cusolverSpXcsrperm_bufferSizeHost(S->sp, n, n, nnz, S->descr, rpB.data(), ciB.data(), r.data(),
+                                                  r.data(), &bytes), "cusolverSpXcsrperm_bufferSizeHost");
+  std::vector<char> buf(bytes + 1);
+  for (int k = 0; k < nnz; ++k) map[k] = k;
+  PF_SOLVER_TRY(cusolverSpXcsrpermHost(S->sp, n, n, nnz, S->descr, rpB.data(), ciB.data(), r.data(), r.data(),
+                                       map.data(), buf.data()), "cusolverSpXcsrpermHost");
+  std::vector<double> vb(nnz);
+  for (int k = 0; k < nnz; ++k) vb[k] = va[map[k]];
+  // host LU with partial pivoting
+  csrluInfoHost_t info = nullptr;
+  PF_SOLVER_TRY(cusolverSpCreateCsrluInfoHost(&info), "cusolverSpCreateCsrluInfoHost");
+  struct InfoGuard {
+    csrluInfoHost_t p;
+    ~InfoGuard() { cusolverSpDestroyCsrluInfoHost(p); }
+  } guard{info};
+  PF_SOLVER_TRY(cusolverSpXcsrluAnalysisHost(S->sp, n, nnz, S->descr, rpB.data(), ciB.data(), info),
+                "cusolverSpXcsrluAnalysisHost");
+  size_t internal = 0, work = 0;
+  PF_SOLVER_TRY(cusolverSpDcsrluBufferInfoHost(S->sp, n, nnz, S->descr, vb.data(), rpB.data(), ciB.data(), info,
+                                               &internal, &work), "cusolverSpDcsrluBufferInfoHost");
+  std::vector<char> wbuf(work + 1);
+  PF_SOLVER_TRY(cusolverSpDcsrluFactorHost(S->sp, n, nnz, S->descr, vb.data(), rpB.data(), ciB.data(), info, 1.0,
+                                           wbuf.data()), "cusolverSpDcsrluFactorHost");
+  int singular = -1;
+  PF_SOLVER_TRY(cusolverSpDcsrluZeroPivotHost(S->sp, info, 1e-14, &singular), "cusolverSpDcsrluZeroPivotHost");
+  if (singular >= 0)
+    return fail(PF_ERR_NUMERIC, "J is singular (instance " + std::to_string(i) + ", pivot " +
+                                    std::to_string(singular) + ")");
+  int nnzL = 0, nnzU = 0;
+  PF_SOLVER_TRY(cusolverSpXcsrluNnzHost(S->sp, &nnzL, &nnzU, info), "cusolverSpXcsrluNnzHost");
+  std::vector<int> Plu(n), Qlu(n), rpL(n + 1), ciL(nnzL), rpU(n + 1), ciU(nnzU);
+  std::vector<double> vL(nnzL), vU(nnzU);
+  PF_SOLVER_TRY(cusolverSpDcsrluExtractHost(S->sp, Plu.data(), Qlu.data(), S->descr, vL.data(), rpL.data(),
+                                            ciL.data(), S->descr, vU.data(), rpU.data(), ciU.data(), info,
+                                            wbuf.data()), "cusolverSpDcsrluExtractHost");
+  // permutations relative to A: the ordering composed with the pivoting
+  std::vector<int> P(n), Q(n);
+  for (int j = 0; j < n; ++j) {
+    P[j] = r[Plu[j]];
+    Q[j] = r[Qlu[j]];
+  }
+  RfInst &R = S->rf[i];
+  PF_SOLVER_TRY(cusolverRfCreate(&R.rf), "cusolverRfCreate");
+  PF_SOLVER_TRY(cusolverRfSetResetValuesFastMode(R.rf, CUSOLVERRF_RESET_VALUES_FAST_MODE_ON),
+                "cusolverRfSetResetValuesFastMode");
+  PF_SOLVER_TRY(cusolverRfSetMatrixFormat(R.rf, CUSOLVERRF_MATRIX_FORMAT_CSR, CUSOLVERRF_UNIT_DIAGONAL_ASSUMED_L),
+                "cusolverRfSetMatrixFormat");
+  PF_SOLVER_TRY(cusolverRfSetAlgs(R.rf, CUSOLVERRF_FACTORIZATION_ALG0, CUSOLVERRF_TRIANGULAR_SOLVE_ALG1),
+                "cusolverRfSetAlgs");
+  PF_SOLVER_TRY(cusolverRfSetupHost(n, nnz, rp.data(), ci.data(), va.data(), nnzL, rpL.data(), ciL.data(),
+                                    vL.data(), nnzU, rpU.data(), ciU.data(), vU.data(), P.data(), Q.data(), R.rf),
+                "cusolverRfSetupHost");
+  PF_SOLVER_TRY(cusolverRfAnalyze(R.rf), "cusolverRfAnalyze");
+  PF_CUDA_TRY(cudaMalloc(&R.dP, n * sizeof(int)));
+  PF_CUDA_TRY(cudaMalloc(&R.dQ, n * sizeof(int)));
+  PF_CUDA_TRY(cudaMalloc(&R.dT, n * sizeof(double)));
+  PF_CUDA_TRY(cudaMemcpy(R.dP, P.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+  PF_CUDA_TRY(cudaMemcpy(R.dQ, Q.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+  return PF_OK;
+}
+
+// J dx = F for instance i by LU refactorization (S->dx[i] = S->F[i] on entry).
+int rf_solve(Ctx &c, Solver *S, int i, cudaStream_t s) {
+  const int g = c.inst_grid[i];
+  const int n = c.grid_nf[g], nnz = c.grid_nnz[g];
+  if (S->rf.empty()) S->rf.resize(c.v.n_inst);
+  RfInst &R = S->rf[i];
+  if (!R.rf) PF_TRY(rf_setup(c, S, i, s));
+  {
+    // the factors are computed by the refactorization (after the setup, too)
+    PF_SOLVER_TRY(cusolverRfResetValues(n, nnz, c.rowptr + c.grid_row_off[g], c.colind + c.grid_nnz_off[g],
+                                        S->vals + c.v_off[i], R.dP, R.dQ, R.rf), "cusolverRfResetValues");
+    PF_SOLVER_TRY(cusolverRfRefactor(R.rf), "cusolverRfRefactor");
+  }
+  PF_SOLVER_TRY(cusolverRfSolve(R.rf, R.dP, R.dQ, 1, R.dT, n, S->dx + c.f_off[i], n), "cusolverRfSolve");
   return PF_OK;
 }
 
@@ -190,6 +320,13 @@ int newton(Ctx &c, double *x, double tol, int max_iter, cudaStream_t s, pf_newto
       const int g = c.inst_grid[i];
       const int n = c.grid_nf[g], nnz = c.grid_nnz[g];
       if (n == 0) continue;
+      if (c.newton_solver == PF_SOLVER_LU) {
+        PF_CUDA_TRY(cudaMemcpyAsync(S->dx + c.f_off[i], S->F + c.f_off[i], n * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, s));
+        PF_CUDA_TRY(cudaStreamSynchronize(s));
+        PF_TRY(rf_solve(c, S, i, s));
+        continue;
+      }
       int singular = -1;
       const cusolverStatus_t st = cusolverSpDcsrlsvqr(
           S->sp, n, nnz, S->descr, S->vals + c.v_off[i], c.rowptr + c.grid_row_off[g], c.colind + c.grid_nnz_off[g],
@@ -200,6 +337,8 @@ int newton(Ctx &c, double *x, double tol, int max_iter, cudaStream_t s, pf_newto
         return fail(PF_ERR_NUMERIC, "J is singular (instance " + std::to_string(i) + ", iteration " +
                                         std::to_string(it) + ", pivot " + std::to_string(singular) + ")");
     }
+    // cuSOLVER-Rf works on the legacy default stream: wait for all of it
+    if (c.newton_solver == PF_SOLVER_LU) PF_CUDA_TRY(cudaDeviceSynchronize());
     PF_CUDA_TRY(cudaStreamSynchronize(s));
     r.solve_ms += ms_since(t0);
     // task (4)

@@ -28,13 +28,15 @@ def cuda(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
+@pytest.mark.parametrize("solver", ["lu", "qr"])
 @pytest.mark.parametrize("mode", [REDUCED, EXTENDED])
-def test_newton_200bus_matches_oracle_newton(P, mode):
+def test_newton_200bus_matches_oracle_newton(P, mode, solver):
     sys = gridgen.grid_200()
     x0 = gridgen.flat_state(sys, mode == EXTENDED)
     xo, hist = oracle.newton_dense(sys, x0, mode)
     assert hist[-1] <= 1e-10
     ctx = P.Context(sys, MNAME[mode])
+    ctx.set_newton_solver(solver)
     x = cuda(x0)
     info = ctx.newton(x, tol=1e-10, max_iter=20)
     assert info["converged"] == 1 and info["max_mismatch"] <= 1e-10
@@ -61,7 +63,8 @@ def test_newton_two_bus_closed_form(P):
     assert abs(xs[3] - v2) <= 1e-12 and abs(xs[1] - th2) <= 1e-12
 
 
-def test_newton_batched_outages(P):
+@pytest.mark.parametrize("solver", ["lu", "qr"])
+def test_newton_batched_outages(P, solver):
     sys = gridgen.grid_200()
     x0 = gridgen.flat_state(sys)
     # outages for which the oracle's Newton converges (the grid stays solvable)
@@ -74,6 +77,7 @@ def test_newton_batched_outages(P):
             break
     assert len(outs) == 6
     ctx = P.Context([sys], instances=[(0, l) for l, _ in outs])
+    ctx.set_newton_solver(solver)
     x = cuda(np.concatenate([x0] * len(outs)))
     info = ctx.newton(x, tol=1e-10, max_iter=20)
     assert info["converged"] == 1
