@@ -584,3 +584,68 @@ def newton_qlim(sys, x0, q_min, q_max, tol=1e-10, max_iter=30, max_switch_rounds
         gen_mode[lo] = 2
         gen_qlim[lo] = q_min[lo]
     raise RuntimeError("reactive-limit switching did not settle")
+
+
+# ---------------------------------------------------------------------------
+# fast decoupled iterations (Sec. V names the Fast Decoupled method as future
+# work; the XB variant of Stott and Alsac, with van Amerongen's choice of
+# which matrix drops the resistances)
+# ---------------------------------------------------------------------------
+
+def fdlf_matrices(sys):
+    """(B', B'') of the XB fast decoupled method, dense, reduced-formulation order.
+
+    B' (rows / columns: non-slack buses): built from 1/x of every in-service
+    branch only (resistance, charging, taps, shifts and shunts ignored);
+    B'' (rows / columns: PQ-type buses): -Im(Y_bus) with phase shifts set to
+    zero (series admittance, charging, taps and shunts kept).
+    """
+    fm = Formulation(sys, REDUCED)
+    n = sys.n_bus
+    on = np.asarray(sys.br_status) != 0
+    f = np.asarray(sys.br_from, np.int64)[on]
+    t = np.asarray(sys.br_to, np.int64)[on]
+    x = np.asarray(sys.br_x, float)[on]
+    r = np.asarray(sys.br_r, float)[on]
+    bc = np.asarray(sys.br_b, float)[on]
+    tau = np.asarray(sys.br_tap, float)[on]
+    B1 = np.zeros((n, n))
+    y1 = 1.0 / x
+    np.add.at(B1, (f, f), y1)
+    np.add.at(B1, (t, t), y1)
+    np.add.at(B1, (f, t), -y1)
+    np.add.at(B1, (t, f), -y1)
+    bs = -x / (r * r + x * x)                          # Im of the series admittance 1 / (r + jx)
+    B2 = np.zeros((n, n))
+    np.add.at(B2, (f, f), -(bs + bc / 2) / (tau * tau))
+    np.add.at(B2, (t, t), -(bs + bc / 2))
+    np.add.at(B2, (f, t), bs / tau)
+    np.add.at(B2, (t, f), bs / tau)
+    np.add.at(B2, (np.asarray(sys.sh_bus, np.int64), np.asarray(sys.sh_bus, np.int64)), -np.asarray(sys.sh_b))
+    ns = np.argsort(np.where(fm.row_p >= 0, fm.row_p, n + 1))[: int(np.sum(fm.row_p >= 0))]
+    pq = np.argsort(np.where(fm.row_q >= 0, fm.row_q, 2 * n + 1))[: int(np.sum(fm.row_q >= 0))]
+    return B1[np.ix_(ns, ns)], B2[np.ix_(pq, pq)], ns, pq
+
+
+def fdlf(sys, x0, tol=1e-10, max_iter=100):
+    """Fast decoupled iterations (reduced formulation): with the mismatches
+    F = P_out - P_spec (this module's sign), each iteration solves
+    B' dtheta = -F_P / V and updates theta, re-evaluates F, solves
+    B'' dV = -F_Q / V and updates V.  Returns (x, history of ||F||_inf), the
+    norm taken before each iteration; stops at ||F||_inf <= tol.
+    """
+    n = sys.n_bus
+    fm = Formulation(sys, REDUCED)
+    B1, B2, ns, pq = fdlf_matrices(sys)
+    x = np.array(x0, dtype=float)
+    hist = []
+    for _ in range(max_iter):
+        F = residual(sys, x)
+        hist.append(float(np.max(np.abs(F))) if F.size else 0.0)
+        if hist[-1] <= tol:
+            break
+        x[ns] += np.linalg.solve(B1, -F[fm.row_p[ns]] / x[n + ns])
+        F = residual(sys, x)
+        x[n + pq] += np.linalg.solve(B2, -F[fm.row_q[pq]] / x[n + pq])
+    return x, hist
+
