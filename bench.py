@@ -593,14 +593,30 @@ def run_workload(args):
                     t0 = time.perf_counter()
                     info = ctx.newton(x, tol=1e-8, max_iter=15)
                     ts.append(time.perf_counter() - t0)
-                runs.append({"n_bus": n_bus, "load_scale": load, "solver": solver,
+                runs.append({"n_bus": n_bus, "load_scale": load, "method": "newton", "solver": solver,
                              "seconds": float(np.median(ts)), "seconds_first_call": t_first, **info})
                 ctx.check_device()
                 ctx.close()
+            # fast decoupled iterations (B', B'' factored once, on the first call)
+            ctx = Context(sk)
+            x0 = torch.from_numpy(gridgen.flat_state(sk)).cuda()
+            x = x0.clone()
+            ctx.fdlf(x, tol=1e-8, max_iter=100)
+            ts = []
+            for _ in range(max(1, min(args.steps, 3))):
+                x.copy_(x0)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                info = ctx.fdlf(x, tol=1e-8, max_iter=100)
+                ts.append(time.perf_counter() - t0)
+            runs.append({"n_bus": n_bus, "load_scale": load, "method": "fast decoupled", "solver": "lu",
+                         "seconds": float(np.median(ts)), **info})
+            ctx.check_device()
+            ctx.close()
         ctx = None
         clocks = {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled (host-synchronous loop)"],
                   "samples": 0}
-        t = [r for r in runs if r["n_bus"] == 10000 and r["solver"] == "lu"][0]["seconds"]
+        t = [r for r in runs if r["n_bus"] == 10000 and r["method"] == "newton" and r["solver"] == "lu"][0]["seconds"]
         s2 = gridgen.synthetic_grid(2000, 3000, load_scale=0.2)
         t0, m = time.perf_counter(), 0
         while time.perf_counter() - t0 < args.cpu_seconds and m < 3:

@@ -331,6 +331,19 @@ PF_API int pf_newton_qlim(pf_ctx *ctx, double *x, const double *q_min, const dou
                           double *gen_qlim, double tol, int32_t max_iter, int32_t max_rounds, void *stream,
                           pf_newton_info *info, int32_t *rounds);
 
+/* Fast decoupled power flow (the method Sec. V names as future work; XB
+ * variant of Stott and Alsac, reduced formulation): B' from 1/x of the
+ * branches (non-slack rows), B'' = -Im(Y_bus) without phase shifts (PQ
+ * rows), each built on the host from the context and factored once
+ * (host LU, cuSOLVER-Rf); every iteration solves B' dtheta = -F_P / V with
+ * F from this library's kernels, updates theta, re-evaluates F and solves
+ * B'' dV = -F_Q / V.  An instance's outage branch is left out of its
+ * matrices (one factored pair per distinct grid and outage; per-call status
+ * masks are not applied to them).  Stops when max |F| <= tol for every
+ * instance or after max_iter iterations; x updated in place.  PF_ERR_INVALID
+ * for the extended formulation. */
+PF_API int pf_fdlf(pf_ctx *ctx, double *x, double tol, int32_t max_iter, void *stream, pf_newton_info *info);
+
 /* Convergence test of task (4): norms[i] = max |F| over the rows of instance
  * i (device, [n_inst] doubles), exact in any order (a maximum). */
 PF_API int pf_mismatch_norm(pf_ctx *ctx, const double *F, double *norms, void *stream);

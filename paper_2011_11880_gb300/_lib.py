@@ -94,6 +94,7 @@ SIGNATURES = {
     "pf_newton_qlim": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_double,
                                  c_int32, c_int32, c_void_p, P(PfNewtonInfo), P(c_int32)]),
     "pf_set_newton_solver": (c_int32, [c_void_p, c_int32]),
+    "pf_fdlf": (c_int32, [c_void_p, c_void_p, ctypes.c_double, c_int32, c_void_p, P(PfNewtonInfo)]),
     "pf_mismatch_norm": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "pf_newton_update": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "pf_get_tuning": (c_int32, [c_void_p, P(PfTuning)]),

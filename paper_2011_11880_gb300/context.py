@@ -273,6 +273,13 @@ class Context:
                                   _stream(stream), ctypes.byref(info)), "pf_newton")
         return {k: getattr(info, k) for k, _ in PfNewtonInfo._fields_}
 
+    def fdlf(self, x, tol: float = 1e-10, max_iter: int = 100, stream=None):
+        """Fast decoupled power flow (reduced formulation), x updated in place."""
+        info = PfNewtonInfo()
+        check(self._lib.pf_fdlf(self._h, _ptr(x, numel=self.dims.n_x, name="x"), float(tol), int(max_iter),
+                                _stream(stream), ctypes.byref(info)), "pf_fdlf")
+        return {k: getattr(info, k) for k, _ in PfNewtonInfo._fields_}
+
     def set_newton_solver(self, solver: str = "lu"):
         """Linear solver of the Newton loop: "lu" (refactorization, default) or "qr"."""
         check(self._lib.pf_set_newton_solver(self._h, {"lu": 0, "qr": 1}[solver]), "pf_set_newton_solver")

@@ -286,6 +286,11 @@ int pf_newton_qlim(pf_ctx *ctx, double *x, const double *q_min, const double *q_
   return PF_OK;
 }
 
+int pf_fdlf(pf_ctx *ctx, double *x, double tol, int32_t max_iter, void *stream, pf_newton_info *info) {
+  if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
+  return pf::fdlf(ctx->c, x, tol, max_iter, as_stream(stream), info);
+}
+
 int pf_set_newton_solver(pf_ctx *ctx, int32_t solver) {
   if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
   if (solver != PF_SOLVER_LU && solver != PF_SOLVER_QR)

@@ -211,6 +211,7 @@ int newton(Ctx &c, double *x, double tol, int max_iter, cudaStream_t s, pf_newto
 int newton_qlim(Ctx &c, double *x, const double *q_min, const double *q_max, uint8_t *mode, double *qlim, double tol,
                 int max_iter, int max_rounds, cudaStream_t s, pf_newton_info *info, int *rounds);
 int newton_norms(Ctx &c, const double *F, double *norms, cudaStream_t s);
+int fdlf(Ctx &c, double *x, double tol, int max_iter, cudaStream_t s, pf_newton_info *info);
 int newton_update(Ctx &c, double *x, const double *dx, cudaStream_t s);
 // F and J of the instances [i0, i1) only (pf_eval.cu; built coefficients, no overrides).
 int launch_eval_range(Ctx &c, int i0, int i1, const double *x, double *F, double *vals, cudaStream_t s);

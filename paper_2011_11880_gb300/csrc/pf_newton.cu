@@ -93,10 +93,47 @@ struct RfInst {
   double *dT = nullptr;
 };
 
+// Fast decoupled half-iteration, per instance bus with a row of the half
+// (P for half 0, Q for half 1): rhs = -F / V at the bus's row.
+__global__ void k_fdlf_rhs(View v, const double *__restrict__ F, const double *__restrict__ x,
+                           double *__restrict__ rhs, int half) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < v.n_bus_inst; q += stride) {
+    const int inst = v.n_inst == 1 ? 0 : find_segment(v.inst_bus_off, v.n_inst, q);
+    const int g = v.inst_grid[inst];
+    const int64_t lb = q - v.inst_bus_off[inst];
+    const int4 m = v.bus_meta[v.grid_bus_off[g] + lb];
+    const int32_t row = half == 0 ? m.x : m.y;
+    if (row < 0) continue;
+    const int64_t f0 = v.inst_f_off[inst];
+    const double V = x[v.inst_x_off[inst] + v.grid_nbus[g] + lb];
+    rhs[f0 + row] = -F[f0 + row] / V;
+  }
+}
+
+// ... then theta (half 0) or V (half 1) += the solution at the bus's row.
+__global__ void k_fdlf_update(View v, double *__restrict__ x, const double *__restrict__ d, int half) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < v.n_bus_inst; q += stride) {
+    const int inst = v.n_inst == 1 ? 0 : find_segment(v.inst_bus_off, v.n_inst, q);
+    const int g = v.inst_grid[inst];
+    const int64_t lb = q - v.inst_bus_off[inst];
+    const int4 m = v.bus_meta[v.grid_bus_off[g] + lb];
+    const int32_t row = half == 0 ? m.x : m.y;
+    if (row < 0) continue;
+    const int64_t xi = v.inst_x_off[inst] + (half == 0 ? 0 : v.grid_nbus[g]) + lb;
+    x[xi] = __dadd_rn(x[xi], d[v.inst_f_off[inst] + row]);
+  }
+}
+
 struct Solver {
   cusolverSpHandle_t sp = nullptr;
   cusparseMatDescr_t descr = nullptr;
   std::vector<RfInst> rf;                 // per instance, created on first use
+  std::vector<RfInst> fd1, fd2;           // fast decoupled: B' and B'' per (grid, outage) pair
+  std::vector<int> fd_n1;                 // per pair: rows of B' (the rows of B'' follow)
+  std::vector<int> fd_of_inst;            // per instance: its pair
+  double *rhs = nullptr;                  // fast decoupled right-hand sides, [n_f]
   std::vector<std::vector<int>> h_rowptr, h_colind;   // per grid, host copies of the pattern
   double *F = nullptr, *vals = nullptr, *dx = nullptr;
   unsigned long long *norm = nullptr;
@@ -113,12 +150,13 @@ int make_solver(Ctx &c, Solver **out) {
   c.newton = S;
   c.newton_free = [](void *p) {
     Solver *s = static_cast<Solver *>(p);
-    for (RfInst &r : s->rf) {
-      if (r.rf) cusolverRfDestroy(r.rf);
-      if (r.dP) cudaFree(r.dP);
-      if (r.dQ) cudaFree(r.dQ);
-      if (r.dT) cudaFree(r.dT);
-    }
+    for (auto *list : {&s->rf, &s->fd1, &s->fd2})
+      for (RfInst &r : *list) {
+        if (r.rf) cusolverRfDestroy(r.rf);
+        if (r.dP) cudaFree(r.dP);
+        if (r.dQ) cudaFree(r.dQ);
+        if (r.dT) cudaFree(r.dT);
+      }
     if (s->sp) cusolverSpDestroy(s->sp);
     if (s->descr) cusparseDestroyMatDescr(s->descr);
     delete s;
@@ -162,25 +200,12 @@ int launch_update(Ctx &c, double *x, const double *dx, cudaStream_t s) {
       return fail(PF_ERR_CUDA, std::string(what) + " failed with status " + std::to_string((int)_st)); \
   } while (0)
 
-// First factorization of instance i: host LU of its current J, then the
-// device refactorization object.
-int rf_setup(Ctx &c, Solver *S, int i, cudaStream_t s) {
-  const int g = c.inst_grid[i];
-  const int n = c.grid_nf[g], nnz = c.grid_nnz[g];
-  if (S->h_rowptr.empty()) {
-    S->h_rowptr.resize(c.v.n_grids);
-    S->h_colind.resize(c.v.n_grids);
-  }
-  std::vector<int> &rp = S->h_rowptr[g], &ci = S->h_colind[g];
-  if (rp.empty()) {
-    rp.resize(n + 1);
-    ci.resize(nnz);
-    PF_CUDA_TRY(cudaMemcpy(rp.data(), c.rowptr + c.grid_row_off[g], (n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
-    PF_CUDA_TRY(cudaMemcpy(ci.data(), c.colind + c.grid_nnz_off[g], nnz * sizeof(int), cudaMemcpyDeviceToHost));
-  }
-  std::vector<double> va(nnz);
-  PF_CUDA_TRY(cudaMemcpyAsync(va.data(), S->vals + c.v_off[i], nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
-  PF_CUDA_TRY(cudaStreamSynchronize(s));
+// Host LU of a CSR matrix (rp, ci, va; n rows) with a METIS fill-reducing
+// ordering and partial pivoting, handed to a cuSOLVER-Rf object that
+// refactors later values of the same pattern on the device.
+int rf_factor_host(Solver *S, int n, const std::vector<int> &rp, const std::vector<int> &ci,
+                   const std::vector<double> &va, RfInst &R, const std::string &what) {
+  const int nnz = rp[n];
   // fill-reducing symmetric ordering r, B = A(r, r)
   std::vector<int> r(n), rpB(rp), ciB(ci), map(nnz);
   PF_SOLVER_TRY(cusolverSpXcsrmetisndHost(S->sp, n, nnz, S->descr, rp.data(), ci.data(), nullptr, r.data()),
@@ -212,8 +237,7 @@ int rf_setup(Ctx &c, Solver *S, int i, cudaStream_t s) {
   int singular = -1;
   PF_SOLVER_TRY(cusolverSpDcsrluZeroPivotHost(S->sp, info, 1e-14, &singular), "cusolverSpDcsrluZeroPivotHost");
   if (singular >= 0)
-    return fail(PF_ERR_NUMERIC, "J is singular (instance " + std::to_string(i) + ", pivot " +
-                                    std::to_string(singular) + ")");
+    return fail(PF_ERR_NUMERIC, what + " is singular (pivot " + std::to_string(singular) + ")");
   int nnzL = 0, nnzU = 0;
   PF_SOLVER_TRY(cusolverSpXcsrluNnzHost(S->sp, &nnzL, &nnzU, info), "cusolverSpXcsrluNnzHost");
   std::vector<int> Plu(n), Qlu(n), rpL(n + 1), ciL(nnzL), rpU(n + 1), ciU(nnzU);
@@ -227,7 +251,6 @@ int rf_setup(Ctx &c, Solver *S, int i, cudaStream_t s) {
     P[j] = r[Plu[j]];
     Q[j] = r[Qlu[j]];
   }
-  RfInst &R = S->rf[i];
   PF_SOLVER_TRY(cusolverRfCreate(&R.rf), "cusolverRfCreate");
   PF_SOLVER_TRY(cusolverRfSetResetValuesFastMode(R.rf, CUSOLVERRF_RESET_VALUES_FAST_MODE_ON),
                 "cusolverRfSetResetValuesFastMode");
@@ -235,7 +258,8 @@ int rf_setup(Ctx &c, Solver *S, int i, cudaStream_t s) {
                 "cusolverRfSetMatrixFormat");
   PF_SOLVER_TRY(cusolverRfSetAlgs(R.rf, CUSOLVERRF_FACTORIZATION_ALG0, CUSOLVERRF_TRIANGULAR_SOLVE_ALG1),
                 "cusolverRfSetAlgs");
-  PF_SOLVER_TRY(cusolverRfSetupHost(n, nnz, rp.data(), ci.data(), va.data(), nnzL, rpL.data(), ciL.data(),
+  PF_SOLVER_TRY(cusolverRfSetupHost(n, nnz, const_cast<int *>(rp.data()), const_cast<int *>(ci.data()),
+                                    const_cast<double *>(va.data()), nnzL, rpL.data(), ciL.data(),
                                     vL.data(), nnzU, rpU.data(), ciU.data(), vU.data(), P.data(), Q.data(), R.rf),
                 "cusolverRfSetupHost");
   PF_SOLVER_TRY(cusolverRfAnalyze(R.rf), "cusolverRfAnalyze");
@@ -245,6 +269,27 @@ int rf_setup(Ctx &c, Solver *S, int i, cudaStream_t s) {
   PF_CUDA_TRY(cudaMemcpy(R.dP, P.data(), n * sizeof(int), cudaMemcpyHostToDevice));
   PF_CUDA_TRY(cudaMemcpy(R.dQ, Q.data(), n * sizeof(int), cudaMemcpyHostToDevice));
   return PF_OK;
+}
+
+// First factorization of instance i: host LU of its current J.
+int rf_setup(Ctx &c, Solver *S, int i, cudaStream_t s) {
+  const int g = c.inst_grid[i];
+  const int n = c.grid_nf[g], nnz = c.grid_nnz[g];
+  if (S->h_rowptr.empty()) {
+    S->h_rowptr.resize(c.v.n_grids);
+    S->h_colind.resize(c.v.n_grids);
+  }
+  std::vector<int> &rp = S->h_rowptr[g], &ci = S->h_colind[g];
+  if (rp.empty()) {
+    rp.resize(n + 1);
+    ci.resize(nnz);
+    PF_CUDA_TRY(cudaMemcpy(rp.data(), c.rowptr + c.grid_row_off[g], (n + 1) * sizeof(int), cudaMemcpyDeviceToHost));
+    PF_CUDA_TRY(cudaMemcpy(ci.data(), c.colind + c.grid_nnz_off[g], nnz * sizeof(int), cudaMemcpyDeviceToHost));
+  }
+  std::vector<double> va(nnz);
+  PF_CUDA_TRY(cudaMemcpyAsync(va.data(), S->vals + c.v_off[i], nnz * sizeof(double), cudaMemcpyDeviceToHost, s));
+  PF_CUDA_TRY(cudaStreamSynchronize(s));
+  return rf_factor_host(S, n, rp, ci, va, S->rf[i], "J of instance " + std::to_string(i));
 }
 
 // J dx = F for instance i by LU refactorization (S->dx[i] = S->F[i] on entry).
@@ -392,6 +437,198 @@ int newton_qlim(Ctx &c, double *x, const double *q_min, const double *q_max, uin
   }
   if (info) *info = total;
   if (rounds) *rounds = std::min(r, max_rounds);
+  return PF_OK;
+}
+
+namespace {
+
+// CSR (sorted columns, duplicates summed in insertion order) of triplets.
+void triplets_to_csr(int n, std::vector<std::pair<int64_t, double>> &t, std::vector<int> &rp, std::vector<int> &ci,
+                     std::vector<double> &va) {
+  std::stable_sort(t.begin(), t.end(), [](const auto &a, const auto &b) { return a.first < b.first; });
+  rp.assign(n + 1, 0);
+  ci.clear();
+  va.clear();
+  for (size_t k = 0; k < t.size();) {
+    const int64_t key = t[k].first;
+    double sum = t[k].second;
+    size_t j = k + 1;
+    for (; j < t.size() && t[j].first == key; ++j) sum += t[j].second;
+    const int row = (int)(key / n), col = (int)(key % n);
+    ci.push_back(col);
+    va.push_back(sum);
+    rp[row + 1]++;
+    k = j;
+  }
+  for (int i = 0; i < n; ++i) rp[i + 1] += rp[i];
+}
+
+// B' and B'' of grid g with global branch `outage` out of service (-1:
+// none), XB variant, built on the host from the device copies of the grid's
+// data and factored once into slot k.
+int fdlf_setup(Ctx &c, Solver *S, int g, int32_t outage, int k) {
+  const View &v = c.v;
+  const int64_t b0 = c.grid_bus_off[g], nb = c.grid_bus_off[g + 1] - b0;
+  const int64_t l0 = c.grid_br_off[g], nl = c.grid_br_off[g + 1] - l0;
+  std::vector<int32_t> from(nl), to(nl);
+  std::vector<double> r(nl), x(nl), bc(nl), tap(nl);
+  std::vector<uint8_t> st(nl);
+  std::vector<double2> sh(nb);
+  std::vector<int4> meta(nb);
+  PF_CUDA_TRY(cudaMemcpy(from.data(), v.br_from + l0, nl * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  PF_CUDA_TRY(cudaMemcpy(to.data(), v.br_to + l0, nl * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  PF_CUDA_TRY(cudaMemcpy(r.data(), v.br_r + l0, nl * sizeof(double), cudaMemcpyDeviceToHost));
+  PF_CUDA_TRY(cudaMemcpy(x.data(), v.br_x + l0, nl * sizeof(double), cudaMemcpyDeviceToHost));
+  PF_CUDA_TRY(cudaMemcpy(bc.data(), v.br_b + l0, nl * sizeof(double), cudaMemcpyDeviceToHost));
+  PF_CUDA_TRY(cudaMemcpy(tap.data(), v.br_tap + l0, nl * sizeof(double), cudaMemcpyDeviceToHost));
+  PF_CUDA_TRY(cudaMemcpy(st.data(), v.br_status + l0, nl * sizeof(uint8_t), cudaMemcpyDeviceToHost));
+  PF_CUDA_TRY(cudaMemcpy(sh.data(), v.bus_sh + b0, nb * sizeof(double2), cudaMemcpyDeviceToHost));
+  PF_CUDA_TRY(cudaMemcpy(meta.data(), v.bus_meta + b0, nb * sizeof(int4), cudaMemcpyDeviceToHost));
+  int n1 = 0, n2 = 0;
+  for (const int4 &m : meta) {
+    n1 += m.x >= 0;
+    n2 += m.y >= 0;
+  }
+  // rows: P row of a bus (0..n1), Q row minus n1 (0..n2)
+  std::vector<std::pair<int64_t, double>> t1, t2;
+  auto put = [](std::vector<std::pair<int64_t, double>> &t, int n, int i, int j, double val) {
+    if (i >= 0 && j >= 0) t.push_back({(int64_t)i * n + j, val});
+  };
+  for (int64_t b = 0; b < nb; ++b) {               // keep every diagonal in the pattern
+    put(t1, n1, meta[b].x, meta[b].x, 0.0);
+    if (meta[b].y >= 0) put(t2, n2, meta[b].y - n1, meta[b].y - n1, 0.0);
+  }
+  for (int64_t l = 0; l < nl; ++l) {
+    if (!st[l] || l0 + l == outage) continue;
+    const int64_t f = from[l] - b0, t = to[l] - b0;
+    const int pf = meta[f].x, pt = meta[t].x;
+    const int qf = meta[f].y >= 0 ? meta[f].y - n1 : -1, qt = meta[t].y >= 0 ? meta[t].y - n1 : -1;
+    const double y1 = 1.0 / x[l];
+    put(t1, n1, pf, pf, y1);
+    put(t1, n1, pt, pt, y1);
+    put(t1, n1, pf, pt, -y1);
+    put(t1, n1, pt, pf, -y1);
+    const double bs = -x[l] / (r[l] * r[l] + x[l] * x[l]);
+    put(t2, n2, qf, qf, -(bs + 0.5 * bc[l]) / (tap[l] * tap[l]));
+    put(t2, n2, qt, qt, -(bs + 0.5 * bc[l]));
+    put(t2, n2, qf, qt, bs / tap[l]);
+    put(t2, n2, qt, qf, bs / tap[l]);
+  }
+  for (int64_t b = 0; b < nb; ++b)
+    if (meta[b].y >= 0) put(t2, n2, meta[b].y - n1, meta[b].y - n1, -sh[b].y);
+  S->fd_n1[k] = n1;
+  for (int which = 0; which < 2; ++which) {
+    const int n = which == 0 ? n1 : n2;
+    if (n == 0) continue;
+    std::vector<int> rp, ci;
+    std::vector<double> va;
+    triplets_to_csr(n, which == 0 ? t1 : t2, rp, ci, va);
+    RfInst &R = which == 0 ? S->fd1[k] : S->fd2[k];
+    PF_TRY(rf_factor_host(S, n, rp, ci, va, R, which == 0 ? "B'" : "B''"));
+    // the factors come from a refactorization of the same values
+    int *drp, *dci;
+    double *dva;
+    PF_CUDA_TRY(cudaMalloc(&drp, (n + 1) * sizeof(int)));
+    PF_CUDA_TRY(cudaMalloc(&dci, rp[n] * sizeof(int)));
+    PF_CUDA_TRY(cudaMalloc(&dva, rp[n] * sizeof(double)));
+    PF_CUDA_TRY(cudaMemcpy(drp, rp.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice));
+    PF_CUDA_TRY(cudaMemcpy(dci, ci.data(), rp[n] * sizeof(int), cudaMemcpyHostToDevice));
+    PF_CUDA_TRY(cudaMemcpy(dva, va.data(), rp[n] * sizeof(double), cudaMemcpyHostToDevice));
+    const cusolverStatus_t s1 = cusolverRfResetValues(n, rp[n], drp, dci, dva, R.dP, R.dQ, R.rf);
+    const cusolverStatus_t s2 = s1 == CUSOLVER_STATUS_SUCCESS ? cusolverRfRefactor(R.rf) : s1;
+    cudaDeviceSynchronize();
+    cudaFree(drp);
+    cudaFree(dci);
+    cudaFree(dva);
+    if (s2 != CUSOLVER_STATUS_SUCCESS)
+      return fail(PF_ERR_CUDA, "cuSOLVER-Rf refactorization of the fast decoupled matrices failed");
+  }
+  return PF_OK;
+}
+
+}  // namespace
+
+int fdlf(Ctx &c, double *x, double tol, int max_iter, cudaStream_t s, pf_newton_info *info) {
+  if (c.v.formulation != PF_REDUCED) return fail(PF_ERR_INVALID, "the fast decoupled method uses the reduced formulation");
+  if (!x) return fail(PF_ERR_INVALID, "x is NULL");
+  if (max_iter < 0 || !(tol >= 0.0)) return fail(PF_ERR_INVALID, "max_iter must be >= 0 and tol >= 0");
+  Solver *S;
+  PF_TRY(make_solver(c, &S));
+  const int I = c.v.n_inst;
+  if (S->fd_of_inst.empty()) {
+    // one pair of factored matrices per distinct (grid, outage) of the instances
+    std::vector<std::pair<int, int32_t>> keys;
+    S->fd_of_inst.assign(I, -1);
+    for (int i = 0; i < I; ++i) {
+      const std::pair<int, int32_t> key{c.inst_grid[i], c.inst_outage[i]};
+      int k = -1;
+      for (size_t j = 0; j < keys.size(); ++j)
+        if (keys[j] == key) k = (int)j;
+      if (k < 0) {
+        k = (int)keys.size();
+        keys.push_back(key);
+      }
+      S->fd_of_inst[i] = k;
+    }
+    S->fd1.resize(keys.size());
+    S->fd2.resize(keys.size());
+    S->fd_n1.assign(keys.size(), 0);
+    PF_TRY(dev_alloc(c, &S->rhs, c.n_f));
+    for (size_t k = 0; k < keys.size(); ++k) PF_TRY(fdlf_setup(c, S, keys[k].first, keys[k].second, (int)k));
+  }
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((c.v.n_bus_inst + 255) / 256, (int64_t)c.num_sms * 16));
+  pf_newton_info r{};
+  std::vector<unsigned long long> h_norm(I);
+  for (int it = 0;; ++it) {
+    auto t0 = std::chrono::steady_clock::now();
+    PF_TRY(launch_eval(c, x, nullptr, S->F, nullptr, s));
+    PF_TRY(launch_norm(c, S->f_off, S->F, S->norm, s));
+    PF_CUDA_TRY(cudaMemcpyAsync(h_norm.data(), S->norm, I * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    PF_CUDA_TRY(cudaStreamSynchronize(s));
+    r.eval_ms += ms_since(t0);
+    double worst = 0.0;
+    for (int i = 0; i < I; ++i) {
+      double nrm;
+      std::memcpy(&nrm, &h_norm[i], sizeof(double));
+      if (!(nrm <= worst)) worst = nrm;
+    }
+    r.max_mismatch = worst;
+    if (worst <= tol) {
+      r.converged = 1;
+      break;
+    }
+    if (it >= max_iter || worst != worst) break;
+    for (int half = 0; half < 2; ++half) {
+      if (half == 1) {                                   // F at the updated angles
+        t0 = std::chrono::steady_clock::now();
+        PF_TRY(launch_eval(c, x, nullptr, S->F, nullptr, s));
+        PF_CUDA_TRY(cudaStreamSynchronize(s));
+        r.eval_ms += ms_since(t0);
+      }
+      t0 = std::chrono::steady_clock::now();
+      PF_CUDA_TRY(cudaMemsetAsync(S->rhs, 0, c.n_f * sizeof(double), s));
+      k_fdlf_rhs<<<(unsigned)blocks, 256, 0, s>>>(c.v, S->F, x, S->rhs, half);
+      PF_CUDA_TRY(cudaGetLastError());
+      PF_CUDA_TRY(cudaStreamSynchronize(s));
+      for (int i = 0; i < I; ++i) {
+        const int g = c.inst_grid[i], k = S->fd_of_inst[i];
+        const int n1 = S->fd_n1[k], n = half == 0 ? n1 : c.grid_nf[g] - n1;
+        if (n == 0) continue;
+        RfInst &R = half == 0 ? S->fd1[k] : S->fd2[k];
+        double *b = S->rhs + c.f_off[i] + (half == 0 ? 0 : n1);
+        PF_SOLVER_TRY(cusolverRfSolve(R.rf, R.dP, R.dQ, 1, R.dT, n, b, n), "cusolverRfSolve");
+      }
+      PF_CUDA_TRY(cudaDeviceSynchronize());            // cuSOLVER-Rf works on the legacy default stream
+      r.solve_ms += ms_since(t0);
+      t0 = std::chrono::steady_clock::now();
+      k_fdlf_update<<<(unsigned)blocks, 256, 0, s>>>(c.v, x, S->rhs, half);
+      PF_CUDA_TRY(cudaGetLastError());
+      PF_CUDA_TRY(cudaStreamSynchronize(s));
+      r.update_ms += ms_since(t0);
+    }
+    r.iterations = it + 1;
+  }
+  if (info) *info = r;
   return PF_OK;
 }
 

@@ -175,3 +175,32 @@ def test_newton_with_reactive_limits_matches_oracle(P):
     assert np.max(np.abs(x.cpu().numpy() - xo)) <= 1e-8
     held = mo != 0
     assert np.array_equal(gq.cpu().numpy()[held], qo[held])
+
+
+def test_fast_decoupled_matches_oracle(P):
+    """Fast decoupled iterations (B', B'' factored once) vs the oracle's, on the 200-bus case and on a
+    batch of outage instances; the fixed point is the Newton solution."""
+    sys = gridgen.grid_200()
+    x0 = gridgen.flat_state(sys)
+    xo, ho = oracle.fdlf(sys, x0)
+    xn, _ = oracle.newton_dense(sys, x0)
+    ctx = P.Context(sys)
+    x = cuda(x0)
+    info = ctx.fdlf(x, tol=1e-10, max_iter=100)
+    assert info["converged"] == 1 and abs(info["iterations"] - (len(ho) - 1)) <= 1, (info, len(ho))
+    xs = x.cpu().numpy()
+    assert np.max(np.abs(xs - xo)) <= 1e-8 and np.max(np.abs(xs - xn)) <= 1e-8
+    outs = []
+    for l in range(3, sys.n_branch, 11):
+        xl, hl = oracle.fdlf(with_outage(sys, l), x0, max_iter=60)
+        if hl[-1] <= 1e-10:
+            outs.append((l, xl))
+        if len(outs) == 4:
+            break
+    ctxb = P.Context([sys], instances=[(0, l) for l, _ in outs])
+    xb = cuda(np.concatenate([x0] * len(outs)))
+    info = ctxb.fdlf(xb, tol=1e-10, max_iter=100)
+    assert info["converged"] == 1
+    xbs = xb.cpu().numpy()
+    for k, (l, xl) in enumerate(outs):
+        assert np.max(np.abs(xbs[ctxb.x_off[k]:ctxb.x_off[k + 1]] - xl)) <= 1e-8, l
