@@ -174,15 +174,25 @@ def algorithmic_bytes(d, n_pv, n_load, n_shunt):
     return read + write
 
 
-def fused_fp64_ops(d, n_pairs):
+def fused_fp64_ops(d, n_pairs, pattern):
     """FP64 operations (an FMA, a multiply or an add each count one: each
     takes one issue of the FP64 pipe) of one instance in k_fused, F and J,
-    no mask: per pair of connected buses (parallel branches merged) 12 -- the
-    rotated terms u, w, xh, yh (4 multiplies + 4 FMAs), a = V_k xh, b = V_k yh,
-    2 adds into the bus sums -- plus one multiply per J value written (every
-    off-diagonal value, and the diagonal values: 2 multiplies + 2 FMAs per
-    bus), plus per bus 5: F_P and F_Q (2 FMAs each) and 2 V_o."""
-    return 12 * n_pairs + d.nnz + 5 * d.n_bus
+    no mask: per pair of connected buses (parallel branches merged) 10 -- the
+    terms u, w, X, Y from the rectangular voltages (4 multiplies + 4 FMAs) and
+    2 adds into the bus sums; per value in a V column of a P or Q row one
+    multiply by 1/V (a theta-column value is X or -Y itself), plus one more
+    FMA for each diagonal V value; per bus 5: V_o^2, V_o^2 A^ - S_X,
+    V_o^2 C^ + S_Y and the two F rows."""
+    n = d.n_bus
+    rp, ci = pattern
+    if d.formulation == 0:                   # reduced: theta columns of the n - 1 non-slack buses first
+        n_v = int(np.count_nonzero(ci >= n - 1))
+        n_vdiag = 2 * (d.n_f - (n - 1))      # P and Q rows of each PQ bus
+    else:                                    # extended: g_p, g_q rows and V columns of every bus
+        row = np.repeat(np.arange(rp.shape[0] - 1), np.diff(rp))
+        n_v = int(np.count_nonzero((row < 2 * n) & (ci >= n) & (ci < 2 * n)))
+        n_vdiag = 2 * n
+    return 10 * n_pairs + n_v + n_vdiag + 5 * n
 
 
 def source_hash():
@@ -391,7 +401,7 @@ def main():
     ip, _, oth = one.incidence()
     own = np.repeat(np.arange(d1.n_bus), np.diff(ip))
     n_pairs = int(np.count_nonzero(np.r_[True, (oth[1:] != oth[:-1]) | (own[1:] != own[:-1])]))
-    ops_kf = N_STATES * fused_fp64_ops(d1, n_pairs)                # one batched launch
+    ops_kf = N_STATES * fused_fp64_ops(d1, n_pairs, one.pattern())  # one batched launch
     bytes_alg = N_STATES * algorithmic_bytes(d1, n_pv, n_load, n_shunt)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     fp64_peak_gops = 152 * 2 * sm_mhz * 1e6 / 1e9                 # 2 FP64 operations / clk / SM

@@ -372,6 +372,16 @@ PF_API int pf_autotune(pf_ctx *ctx, const double *x, double *F, double *vals, vo
 PF_API int pf_sincos(pf_ctx *ctx, const double *theta, int64_t n, double *cos_out, double *sin_out,
                      void *stream);
 
+/* The per-bus records of the evaluation's first stage, exposed so they can be
+ * checked: for every bus of every instance (instance-bus order, as p_inj),
+ * four doubles (V cos theta, V sin theta, V, 1/V) -- the bus voltage in
+ * rectangular form (the sin / cos of pf_sincos times V) and the reciprocal
+ * of V by one cubically convergent correction of the hardware approximation.
+ * A bus with |V| < 2^-500 gets 2^-600 in place of V in the first, second and
+ * fourth entries.  x: device, length n_x; rec: device, 4 n_bus_inst doubles,
+ * caller-owned.  Asynchronous on `stream`. */
+PF_API int pf_voltage_records(pf_ctx *ctx, const double *x, double *rec, void *stream);
+
 /* ---- errors --------------------------------------------------------------------- */
 
 PF_API const char *pf_error_string(int32_t code);

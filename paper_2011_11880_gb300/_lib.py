@@ -101,6 +101,7 @@ SIGNATURES = {
     "pf_set_tuning": (c_int32, [c_void_p, P(PfTuning), c_void_p]),
     "pf_autotune": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, P(PfTuning)]),
     "pf_sincos": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
+    "pf_voltage_records": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "pf_error_string": (ctypes.c_char_p, [c_int32]),
     "pf_last_error": (ctypes.c_char_p, []),
     "pf_check_device": (c_int32, [c_void_p, c_void_p]),

@@ -345,5 +345,13 @@ class Context:
                                   _stream(stream)), "pf_sincos")
         return c, s
 
+    def voltage_records(self, x, stream=None):
+        """[n_bus_inst, 4] float64 CUDA tensor of the evaluation's per-bus records
+        (V cos theta, V sin theta, V, 1/V) at state x."""
+        rec = torch.empty((self.dims.n_bus_inst, 4), dtype=torch.float64, device=x.device)
+        check(self._lib.pf_voltage_records(self._h, _ptr(x, numel=self.dims.n_x, name="x"), _ptr(rec),
+                                           _stream(stream)), "pf_voltage_records")
+        return rec
+
     def check_device(self, stream=None):
         check(self._lib.pf_check_device(self._h, _stream(stream)), "pf_check_device")

@@ -5,13 +5,13 @@
 //
 // State part.  For bus o with pairs (o, k) (parallel branches merged) the
 // gradient gathers the column of J^T at theta_o and V_o:
-//   dL/dtheta_o = v_P(o) V_o sum b - v_Q(o) V_o sum a
+//   dL/dtheta_o = v_P(o) S_Y - v_Q(o) S_X
 //               + sum_k [ v_P(k) dP_k/dtheta_o + v_Q(k) dQ_k/dtheta_o ]
-//   dL/dV_o     = v_P(o) (2 V_o A^ - sum a) - v_Q(o) (2 V_o C^ + sum b)
+//   dL/dV_o     = v_P(o) (2 V_o^2 A^ - S_X) / V_o - v_Q(o) (2 V_o^2 C^ + S_Y) / V_o
 //               + sum_k [ v_P(k) dP_k/dV_o + v_Q(k) dQ_k/dV_o ]
-// (a, b as in the forward kernels; the mirror partials from the merged
-// coefficients of the ends at k towards o), plus the +-1 terms of the
-// extended rows.  One lane per bus on the forward kernel's rounds; the
+// (S_X, S_Y as in the forward kernels, from the rectangular voltages; the
+// mirror partials from the merged coefficients of the ends at k towards o),
+// plus the +-1 terms of the extended rows.  One lane per bus on the forward kernel's rounds; the
 // cotangents run in chunks whose sums stay in registers, the mirror partials
 // are recomputed per chunk.
 //
@@ -54,19 +54,39 @@ __device__ __forceinline__ double cot_row(const VjpArgs &a, int c, int64_t f0, i
   return row >= 0 ? cot_at(a.v, a.vt, a.n_cot, a.n_f, c, f0 + row) : 0.0;
 }
 
-// Rotated terms of one branch end (own phasor po, other phasor pk), as in the
-// forward kernels.
+// X and Y of one branch end (own voltage Eo, other voltage Ek, rectangular),
+// as in the forward kernels.
 struct Terms {
-  double xh, yh;
+  double X, Y;
 };
 
-__device__ __forceinline__ Terms rotated(double2 G, double2 po, double2 pk) {
-  const double uu = __fma_rn(G.x, pk.x, __dmul_rn(-G.y, pk.y));
-  const double ww = __fma_rn(G.x, pk.y, __dmul_rn(G.y, pk.x));
+__device__ __forceinline__ Terms rotated(double2 G, double2 Eo, double2 Ek) {
+  const double uu = __fma_rn(G.x, Ek.x, __dmul_rn(-G.y, Ek.y));
+  const double ww = __fma_rn(G.x, Ek.y, __dmul_rn(G.y, Ek.x));
   Terms r;
-  r.xh = __fma_rn(po.x, uu, __dmul_rn(po.y, ww));
-  r.yh = __fma_rn(po.y, uu, __dmul_rn(-po.x, ww));
+  r.X = __fma_rn(Eo.x, uu, __dmul_rn(Eo.y, ww));
+  r.Y = __fma_rn(Eo.y, uu, __dmul_rn(-Eo.x, ww));
   return r;
+}
+
+// -x, by flipping the sign bit on the integer pipe (exact, no FP64 issue).
+__device__ __forceinline__ double neg(double x) {
+  return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
+}
+
+// Diagonal partials of bus o from its sums S_X, S_Y, V_o, 1/V_o, A^ and C^.
+struct Diag {
+  double pt, qt, pv, qv;
+};
+
+__device__ __forceinline__ Diag diag_partials(double sx, double sy, double vo, double rvo, double ah, double ch) {
+  const double v2 = __dmul_rn(vo, vo);
+  Diag d;
+  d.pt = sy;
+  d.qt = neg(sx);
+  d.pv = __dmul_rn(__fma_rn(v2, ah, __fma_rn(v2, ah, -sx)), rvo);
+  d.qv = __dmul_rn(__fma_rn(v2, ch, __fma_rn(v2, ch, sy)), -rvo);
+  return d;
 }
 
 __device__ __forceinline__ bool end_in(const View &v, int32_t e, int32_t outage, const uint8_t *status,
@@ -107,19 +127,19 @@ __device__ __forceinline__ PairCoeff masked_pair(const View &v, const VjpArgs &a
 
 // The partials of bus k's P and Q rows with respect to theta_o and V_o, for
 // the (merged) branch end at k towards o with coefficients Gm:
-//   dP_k/dt_o = -V_k b',  dQ_k/dt_o = V_k a',  dP_k/dV_o = -V_k xh',  dQ_k/dV_o = -V_k yh',
-// with xh', yh' the rotated terms of that end and a' = V_o xh', b' = V_o yh'.
+//   dP_k/dt_o = -Y',  dQ_k/dt_o = X',  dP_k/dV_o = -X' / V_o,  dQ_k/dV_o = -Y' / V_o,
+// with X', Y' the terms of that end (own voltage E_k, other voltage E_o).
 struct Mirror {
   double pt, qt, pv, qv;
 };
 
-__device__ __forceinline__ Mirror mirror_partials(double2 Gm, double2 po, double vo, double2 pk, double vk) {
-  const Terms t = rotated(Gm, pk, po);
+__device__ __forceinline__ Mirror mirror_partials(double2 Gm, double2 Eo, double rvo, double2 Ek) {
+  const Terms t = rotated(Gm, Ek, Eo);
   Mirror m;
-  m.pt = __dmul_rn(-vk, __dmul_rn(vo, t.yh));
-  m.qt = __dmul_rn(vk, __dmul_rn(vo, t.xh));
-  m.pv = __dmul_rn(-vk, t.xh);
-  m.qv = __dmul_rn(-vk, t.yh);
+  m.pt = neg(t.Y);
+  m.qt = t.X;
+  m.pv = __dmul_rn(-t.X, rvo);
+  m.qv = __dmul_rn(-t.Y, rvo);
   return m;
 }
 
@@ -183,11 +203,11 @@ __global__ void __launch_bounds__(32) k_vjp_lane(View v, VjpArgs a) {
     const int32_t nb = v.grid_nbus[g];
     const int32_t D = ur.w & 0xff;
     const int64_t q0 = (int64_t)ur.z + lane;
-    const double2 po = rec[2 * o];
-    const double vo = rec[2 * o + 1].x;
+    const double2 Eo = rec[2 * o];
+    const double2 vr = rec[2 * o + 1];             // (V_o, 1/V_o)
 
-    // bus sums over the own ends (the forward kernel's a, b)
-    double sa = 0.0, sb = 0.0;
+    // bus sums over the own ends (the forward kernel's S_X, S_Y)
+    double sx = 0.0, sy = 0.0;
     bool any_out = false;                        // masked: an end of this bus is out of service
     for (int32_t j = 0; j < D; ++j) {
       const int64_t q = q0 + 32 * j;
@@ -206,12 +226,9 @@ __global__ void __launch_bounds__(32) k_vjp_lane(View v, VjpArgs a) {
           any_out |= pc.any_out;
         }
       }
-      const int32_t k = meta.x;
-      const double2 pk = rec[2 * k];
-      const double vk = rec[2 * k + 1].x;
-      const Terms t = rotated(G, po, pk);
-      sa = __dadd_rn(sa, __dmul_rn(vk, t.xh));
-      sb = __dadd_rn(sb, __dmul_rn(vk, t.yh));
+      const Terms t = rotated(G, Eo, rec[2 * meta.x]);
+      sx = __dadd_rn(sx, t.X);
+      sy = __dadd_rn(sy, t.Y);
     }
     // A^, C^: built, or re-summed over the ends in service in the built order
     double2 hat = __ldg(a.rhat + rb);
@@ -232,10 +249,7 @@ __global__ void __launch_bounds__(32) k_vjp_lane(View v, VjpArgs a) {
       const double2 sh = __ldg(v.bus_sh + o);
       hat = make_double2(__dadd_rn(ma, sh.x), __dadd_rn(mc, sh.y));
     }
-    const double ah = hat.x, ch = hat.y;
-    const double two_vo = __dadd_rn(vo, vo);
-    const double d_pt = __dmul_rn(vo, sb), d_qt = __dmul_rn(-vo, sa);
-    const double d_pv = __fma_rn(two_vo, ah, -sa), d_qv = __fma_rn(-two_vo, ch, -sb);
+    const Diag d = diag_partials(sx, sy, vr.x, vr.y, hat.x, hat.y);
 
     {
       double gt[CH], gvv[CH];
@@ -245,8 +259,8 @@ __global__ void __launch_bounds__(32) k_vjp_lane(View v, VjpArgs a) {
         gvv[i] = 0.0;
         if (c0 + i < a.n_cot) {
           const double vp = cot_row(a, c0 + i, f0, bm.x), vq = cot_row(a, c0 + i, f0, bm.y);
-          gt[i] = __fma_rn(d_pt, vp, __dmul_rn(d_qt, vq));
-          gvv[i] = __fma_rn(d_pv, vp, __dmul_rn(d_qv, vq));
+          gt[i] = __fma_rn(d.pt, vp, __dmul_rn(d.qt, vq));
+          gvv[i] = __fma_rn(d.pv, vp, __dmul_rn(d.qv, vq));
         }
       }
       for (int32_t j = 0; j < D; ++j) {
@@ -262,9 +276,7 @@ __global__ void __launch_bounds__(32) k_vjp_lane(View v, VjpArgs a) {
           }
         }
         const int32_t k = meta.x;
-        const double2 pk = rec[2 * k];
-        const double vk = rec[2 * k + 1].x;
-        const Mirror m = mirror_partials(Gm, po, vo, pk, vk);
+        const Mirror m = mirror_partials(Gm, Eo, vr.y, rec[2 * k]);
         const int4 bk = __ldg(v.bus_meta + k);
 #pragma unroll
         for (int i = 0; i < CH; ++i) {
@@ -300,17 +312,16 @@ __global__ void __launch_bounds__(32) k_vjp_large(View v, VjpArgs a) {
     const int32_t e0 = __ldg(v.inc_ptr + o), e1 = __ldg(v.inc_ptr + o + 1);
     const int4 bm = __ldg(v.bus_meta + o);
     const int32_t gi = __ldg(v.bus_meta2 + o).w;
-    const double2 po = rec[2 * o];
-    const double vo = rec[2 * o + 1].x;
-    double sa = 0.0, sb = 0.0, sma = 0.0, smc = 0.0;
+    const double2 Eo = rec[2 * o];
+    const double2 vr = rec[2 * o + 1];             // (V_o, 1/V_o)
+    double sx = 0.0, sy = 0.0, sma = 0.0, smc = 0.0;
     for (int32_t e = e0 + lane; e < e1; e += 32) {
       double2 G = __ldg(a.gb + e), AC = __ldg(a.ac + e);
       if (MASKED && !end_in(v, e, outage, a.status, st_base)) G = AC = make_double2(0.0, 0.0);
       const int32_t k = __ldg(v.inc_other + e);
-      const Terms t = rotated(G, po, rec[2 * k]);
-      const double vk = rec[2 * k + 1].x;
-      sa = __dadd_rn(sa, __dmul_rn(vk, t.xh));
-      sb = __dadd_rn(sb, __dmul_rn(vk, t.yh));
+      const Terms t = rotated(G, Eo, rec[2 * k]);
+      sx = __dadd_rn(sx, t.X);
+      sy = __dadd_rn(sy, t.Y);
       if (MASKED) {
         sma = __dadd_rn(sma, AC.x);
         smc = __dadd_rn(smc, AC.y);
@@ -318,8 +329,8 @@ __global__ void __launch_bounds__(32) k_vjp_large(View v, VjpArgs a) {
     }
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) {
-      sa = __dadd_rn(sa, __shfl_xor_sync(0xffffffffu, sa, m));
-      sb = __dadd_rn(sb, __shfl_xor_sync(0xffffffffu, sb, m));
+      sx = __dadd_rn(sx, __shfl_xor_sync(0xffffffffu, sx, m));
+      sy = __dadd_rn(sy, __shfl_xor_sync(0xffffffffu, sy, m));
       if (MASKED) {
         sma = __dadd_rn(sma, __shfl_xor_sync(0xffffffffu, sma, m));
         smc = __dadd_rn(smc, __shfl_xor_sync(0xffffffffu, smc, m));
@@ -335,9 +346,7 @@ __global__ void __launch_bounds__(32) k_vjp_large(View v, VjpArgs a) {
       ah = h.x;
       ch = h.y;
     }
-    const double two_vo = __dadd_rn(vo, vo);
-    const double d_pt = __dmul_rn(vo, sb), d_qt = __dmul_rn(-vo, sa);
-    const double d_pv = __fma_rn(two_vo, ah, -sa), d_qv = __fma_rn(-two_vo, ch, -sb);
+    const Diag d = diag_partials(sx, sy, vr.x, vr.y, ah, ch);
     for (int c0 = 0; c0 < a.n_cot; c0 += CH) {
       double gt[CH], gvv[CH];
 #pragma unroll
@@ -346,7 +355,7 @@ __global__ void __launch_bounds__(32) k_vjp_large(View v, VjpArgs a) {
         double2 Gm = __ldg(a.gb + __ldg(v.inc_mirror + e));
         if (MASKED && !end_in(v, e, outage, a.status, st_base)) Gm = make_double2(0.0, 0.0);
         const int32_t k = __ldg(v.inc_other + e);
-        const Mirror m = mirror_partials(Gm, po, vo, rec[2 * k], rec[2 * k + 1].x);
+        const Mirror m = mirror_partials(Gm, Eo, vr.y, rec[2 * k]);
         const int4 bk = __ldg(v.bus_meta + k);
 #pragma unroll
         for (int i = 0; i < CH; ++i) {
@@ -370,8 +379,8 @@ __global__ void __launch_bounds__(32) k_vjp_large(View v, VjpArgs a) {
         for (int i = 0; i < CH; ++i) {
           if (c0 + i < a.n_cot) {
             const double vp = cot_row(a, c0 + i, f0, bm.x), vq = cot_row(a, c0 + i, f0, bm.y);
-            const double t = __fma_rn(d_qt, vq, __fma_rn(d_pt, vp, gt[i]));
-            const double w = __fma_rn(d_qv, vq, __fma_rn(d_pv, vp, gvv[i]));
+            const double t = __fma_rn(d.qt, vq, __fma_rn(d.pt, vp, gt[i]));
+            const double w = __fma_rn(d.qv, vq, __fma_rn(d.pv, vp, gvv[i]));
             write_state_grad(v, a, inst, g, o - v.grid_bus_off[g], v.grid_nbus[g], gi, bm.x, bm.y, c0 + i, t, w);
           }
         }
@@ -393,7 +402,7 @@ struct ParamArgs {
 // One thread per (instance, branch).  With the branch's constants
 //   g + j b_s = 1 / (r + j x),  alpha = (x^2 - r^2)/D^2,  beta = 2 r x / D^2  (D = r^2 + x^2),
 // so that dg/dr = db_s/dx = alpha and db_s/dr = -dg/dx = beta, and the state's
-//   cos / sin of delta = theta_f - theta_t - phi,  vv = V_f V_t / tau,
+//   (V_f V_t / tau) cos / sin of delta = theta_f - theta_t - phi (from E_f conj(E_t)),
 // the derivatives of the four terminal powers (P_f, Q_f, P_t, Q_t) with
 // respect to g, b_s, b_c and tau are formed once and dotted with the
 // cotangent entries of the four rows for every cotangent.  OVR: the
@@ -435,13 +444,13 @@ __global__ void __launch_bounds__(128) k_vjp_params(View v, ParamArgs a) {
         const double2 k1 = __ldg(v.br_k_gb + l), k2 = __ldg(v.br_k_ab + l), k3 = __ldg(v.br_k_tc + l);
         gs = k1.x; bs = k1.y; al = k2.x; be = k2.y; it = k3.x; bc = k3.y;
       }
-      const double2 pf = rec[2 * f], pt = rec[2 * t];
+      const double2 Ef = rec[2 * f], Et = rec[2 * t];
       const double vf = rec[2 * f + 1].x, vt = rec[2 * t + 1].x;
-      const double cD = pf.x * pt.x + pf.y * pt.y, sD = pf.y * pt.x - pf.x * pt.y;
-      const double cd = cD * ph.x + sD * ph.y, sd = sD * ph.x - cD * ph.y;
+      // V_f V_t (cos, sin)(theta_f - theta_t), then rotated by -phi and divided by tau
+      const double cD = Ef.x * Et.x + Ef.y * Et.y, sD = Ef.y * Et.x - Ef.x * Et.y;
+      const double pgc = (cD * ph.x + sD * ph.y) * it, pgs = (sD * ph.x - cD * ph.y) * it;
       const double vfi = vf * it;
-      const double vv = vfi * vt, vf2t = vfi * vfi, vt2 = vt * vt;
-      const double pgc = vv * cd, pgs = vv * sd;
+      const double vf2t = vfi * vfi, vt2 = vt * vt;
       // d/dg and d/db_s of each row
       const double Fg[4] = {vf2t - pgc, -pgs, vt2 - pgc, pgs};
       const double Fb[4] = {-pgs, pgc - vf2t, pgs, pgc - vt2};
@@ -452,12 +461,13 @@ __global__ void __launch_bounds__(128) k_vjp_params(View v, ParamArgs a) {
       }
       db1 = -0.5 * vf2t;
       db3 = -0.5 * vt2;
-      const double gc = gs * cd, bsd = bs * sd, gsd = gs * sd, bcd = bs * cd;
-      const double tv = it * vv, tf = 2.0 * it * vf2t;
-      d_t[0] = tv * (gc + bsd) - tf * (gs + v.br_gfr[l]);
-      d_t[1] = tf * (bs + 0.5 * bc) + tv * (gsd - bcd);
-      d_t[2] = tv * (gc - bsd);
-      d_t[3] = -tv * (gsd + bcd);
+      // tau-derivatives: the V_f V_t terms scale with 1/tau, the V_f^2 terms with 1/tau^2
+      const double gc = gs * pgc, bsd = bs * pgs, gsd = gs * pgs, bcd = bs * pgc;
+      const double tf = 2.0 * it * vf2t;
+      d_t[0] = it * (gc + bsd) - tf * (gs + v.br_gfr[l]);
+      d_t[1] = tf * (bs + 0.5 * bc) + it * (gsd - bcd);
+      d_t[2] = it * (gc - bsd);
+      d_t[3] = -it * (gsd + bcd);
     } else {
 #pragma unroll
       for (int i = 0; i < 4; ++i) d_r[i] = d_x[i] = d_t[i] = 0.0;

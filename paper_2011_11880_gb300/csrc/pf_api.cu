@@ -373,6 +373,16 @@ int pf_sincos(pf_ctx *ctx, const double *theta, int64_t n, double *cos_out, doub
   return pf::launch_sincos(ctx->c, theta, n, cos_out, sin_out, as_stream(stream));
 }
 
+int pf_voltage_records(pf_ctx *ctx, const double *x, double *rec, void *stream) {
+  if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
+  if (!x || !rec) return fail(PF_ERR_INVALID, "x or rec is NULL");
+  const cudaStream_t s = as_stream(stream);
+  PF_TRY(pf::launch_phasor(ctx->c.v, ctx->c.num_sms, x, s));
+  PF_CUDA_TRY(cudaMemcpyAsync(rec, ctx->c.v.phasor, sizeof(double) * 4 * (size_t)ctx->c.v.n_bus_inst,
+                              cudaMemcpyDeviceToDevice, s));
+  return PF_OK;
+}
+
 const char *pf_error_string(int32_t code) {
   switch (code) {
     case PF_OK: return "ok";

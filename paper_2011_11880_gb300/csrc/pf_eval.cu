@@ -4,23 +4,25 @@
 // Arithmetic form.  For a branch end at bus o whose other end is bus k, with
 // per-end coefficients (G, B, A, C) built once from the branch model (see
 // k_coeff in pf_build.cu), the terminal powers of Eq. (4) extended with Q,
-// tap and shift are
+// tap and shift are, with the bus voltages in rectangular form
+// E = V (cos t, sin t) = (e, f),
 //     P_o =  A V_o^2 - X,   Q_o = -C V_o^2 - Y,
-//     X = V_o V_k xh,       Y = V_o V_k yh,
-//     xh = cos(t_o) u + sin(t_o) w,   yh = sin(t_o) u - cos(t_o) w,
-//     u  = G cos(t_k) - B sin(t_k),   w  = G sin(t_k) + B cos(t_k),
-// which is the polar form with the angle difference expanded, so that the
-// only trigonometry is one sin/cos pair per bus (k_phasor).  The partials
-// follow from the same expansion:
-//     dP_o/dt_k = -Y,  dQ_o/dt_k = X,  dP_o/dV_k = -V_o xh,  dQ_o/dV_k = -V_o yh,
-// and, summed over the ends of bus o with a = V_k xh, b = V_k yh,
-//     F_P = V_o (V_o A^ - sum a) - P_inj,    F_Q = -V_o (V_o C^ + sum b) - Q_inj,
-//     dF_P/dt_o = V_o sum b,   dF_Q/dt_o = -V_o sum a,
-//     dF_P/dV_o = 2 V_o A^ - sum a,   dF_Q/dV_o = -2 V_o C^ - sum b,
-// where A^ = sum A + shunt g and C^ = sum C + shunt b.  No division; per
-// pair of connected buses (parallel branches merged into one end with their
-// coefficients summed) 8 FP64 operations for u, w, xh, yh, 2 for a and b, 2
-// adds into the bus sums and one multiply per J value.
+//     X = e_o u + f_o w,    Y = f_o u - e_o w,
+//     u = G e_k - B f_k,    w = G f_k + B e_k,
+// which is the polar form with the angle difference expanded (X = V_o V_k
+// times the rotated cosine term), so that the only trigonometry is one
+// sin/cos pair per bus (k_phasor).  The partials follow from the same
+// expansion:
+//     dP_o/dt_k = -Y,  dQ_o/dt_k = X,  dP_o/dV_k = -X / V_k,  dQ_o/dV_k = -Y / V_k,
+// and, with S_X = sum X and S_Y = sum Y over the ends of bus o,
+//     F_P = V_o^2 A^ - S_X - P_inj,    F_Q = -(V_o^2 C^ + S_Y) - Q_inj,
+//     dF_P/dt_o = S_Y,   dF_Q/dt_o = -S_X,
+//     dF_P/dV_o = (2 V_o^2 A^ - S_X) / V_o,   dF_Q/dV_o = -(2 V_o^2 C^ + S_Y) / V_o,
+// where A^ = sum A + shunt g and C^ = sum C + shunt b.  1/V is formed once
+// per bus by k_phasor.  Per pair of connected buses (parallel branches merged
+// into one end with their coefficients summed): 8 FP64 operations for u, w,
+// X, Y, 2 adds into the bus sums, no operation for a theta-column J value (a
+// sign flip on the integer pipe) and one multiply for a V-column J value.
 //
 // Work decomposition.  The buses of each grid are sorted by their number of
 // neighbours and cut into rounds of 32; one warp evaluates one round, one bus
@@ -82,9 +84,31 @@ __device__ __forceinline__ double2 table_sincos(double t, const double2 *__restr
   return make_double2(__fma_rn(T.x, cr, -__dmul_rn(T.y, sr)), __fma_rn(T.y, cr, __dmul_rn(T.x, sr)));
 }
 
-// Per bus of every instance: (cos theta, sin theta) and a copy of V, side by
-// side in one 32-byte record, so the fused kernel's gathers of a neighbour's
-// data hit L2 in one sector.
+// -x, by flipping the sign bit on the integer pipe (exact, no FP64 issue).
+__device__ __forceinline__ double neg(double x) {
+  return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
+}
+
+// 1/s by one Householder step of order 2 (cubic convergence) from the
+// hardware's approximate reciprocal r0: with e = 1 - s r0,
+// 1/s = r0 / (1 - e) = r0 (1 + e + e^2 + ...), so r1 = r0 + r0 (e + e^2) has
+// relative error e^3.  3 FP64 operations.
+__device__ __forceinline__ double recip(double s) {
+  double r0;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r0) : "d"(s));
+  const double e = __fma_rn(-s, r0, 1.0);
+  return __fma_rn(r0, __fma_rn(e, e, e), r0);
+}
+
+// Per bus of every instance: the voltage in rectangular form
+// E = V (cos theta, sin theta), then V and 1/V, side by side in one 32-byte
+// record, so the fused kernel's gathers of a neighbour's data hit L2 in one
+// sector.  A voltage below 2^-500 in magnitude (a dead bus) is replaced by
+// 2^-600 in E and 1/V: every term then carries a factor of at most 2^-600
+// where it should carry V (terms that are zero to far below any tolerance),
+// and the dF/dV values, which divide that factor out again, stay exact.
+constexpr double kDeadV = 0x1p-600;
+
 __global__ void __launch_bounds__(256) k_phasor(View v, const double *__restrict__ x) {
   // Let the fused kernel start launching; it waits for this grid's results.
   cudaTriggerProgrammaticLaunchCompletion();
@@ -96,8 +120,10 @@ __global__ void __launch_bounds__(256) k_phasor(View v, const double *__restrict
     const double *xi = x + v.inst_x_off[inst];
     const double th = __ldg(xi + lb);
     const double vm = __ldg(xi + v.grid_nbus[v.inst_grid[inst]] + lb);
-    v.phasor[2 * q] = table_sincos(th, v.sincos_tab);
-    v.phasor[2 * q + 1] = make_double2(vm, 0.0);
+    const double2 cs = table_sincos(th, v.sincos_tab);
+    const double sv = (__double2hiint(vm) & 0x7ff00000) < 0x20b00000 ? kDeadV : vm;   // |V| < 2^-500
+    v.phasor[2 * q] = make_double2(__dmul_rn(sv, cs.x), __dmul_rn(sv, cs.y));
+    v.phasor[2 * q + 1] = make_double2(vm, recip(sv));
   }
 }
 
@@ -118,19 +144,28 @@ struct EvalArgs {
   const double *gen_qlim;
 };
 
-// Rotated terms of one branch end (own phasor po, other phasor pk).
+// X and Y of one branch end (own voltage Eo, other voltage Ek, rectangular).
 struct EndTerms {
-  double xh, yh;
+  double X, Y;
 };
 
-__device__ __forceinline__ EndTerms end_terms(double2 G, double2 po, double2 pk) {
+__device__ __forceinline__ EndTerms end_terms(double2 G, double2 Eo, double2 Ek) {
   // negations are applied to inputs (exact), so they fold into operand modifiers
-  const double uu = __fma_rn(G.x, pk.x, __dmul_rn(-G.y, pk.y));
-  const double ww = __fma_rn(G.x, pk.y, __dmul_rn(G.y, pk.x));
+  const double uu = __fma_rn(G.x, Ek.x, __dmul_rn(-G.y, Ek.y));
+  const double ww = __fma_rn(G.x, Ek.y, __dmul_rn(G.y, Ek.x));
   EndTerms r;
-  r.xh = __fma_rn(po.x, uu, __dmul_rn(po.y, ww));
-  r.yh = __fma_rn(po.y, uu, __dmul_rn(-po.x, ww));
+  r.X = __fma_rn(Eo.x, uu, __dmul_rn(Eo.y, ww));
+  r.Y = __fma_rn(Eo.y, uu, __dmul_rn(-Eo.x, ww));
   return r;
+}
+
+// The four off-diagonal values of a pair (CSR positions p, -1 where the
+// formulation has no such entry) from its X, Y and 1/V_k.
+__device__ __forceinline__ void write_pair(double *vi, int4 p, double X, double Y, double rvk) {
+  if (p.x >= 0) vi[p.x] = neg(Y);                    // dP_o / dtheta_k
+  if (p.y >= 0) vi[p.y] = __dmul_rn(-X, rvk);        // dP_o / dV_k
+  if (p.z >= 0) vi[p.z] = X;                         // dQ_o / dtheta_k
+  if (p.w >= 0) vi[p.w] = __dmul_rn(-Y, rvk);        // dQ_o / dV_k
 }
 
 __device__ __forceinline__ bool end_in_service(const View &v, int32_t e, int32_t outage, const uint8_t *status,
@@ -142,31 +177,26 @@ __device__ __forceinline__ bool end_in_service(const View &v, int32_t e, int32_t
 __device__ __forceinline__ int64_t gb0_of(const View &v, int g) { return __ldg(v.grid_bus_off + g); }
 
 // Off-diagonal entries of a group of `len` parallel branch ends e, e+1, ...
-// (same own bus o, same other bus k, so the same four CSR positions): with
-// X = sum xh and Y = sum yh over the group in list order,
-//   dP/dt_k = -V_o (V_k Y),  dP/dV_k = -V_o X,  dQ/dt_k = V_o (V_k X),  dQ/dV_k = -V_o Y.
-// For a group of one branch these are the single end's terms.
+// (same own bus o, same other bus k, so the same four CSR positions), from
+// X and Y summed over the group in list order.  For a group of one branch
+// these are the single end's terms.
 __device__ __forceinline__ void write_group(const View &v, const EvalArgs &a, int32_t e, int32_t len, int32_t o,
                                             int32_t k, int4 p, const double2 *rec, double *vi, bool masked,
                                             int32_t outage, int64_t st_base) {
-  const double2 po = rec[2 * o], pk = rec[2 * k];
-  const double vo = rec[2 * o + 1].x, vk = rec[2 * k + 1].x;
+  const double2 Eo = rec[2 * o], Ek = rec[2 * k];
+  const double rvk = rec[2 * k + 1].y;
   double X = 0.0, Y = 0.0;
   for (int32_t q = 0; q < len; ++q) {
     double2 G = __ldg(a.gb + e + q);
     if (masked && !end_in_service(v, e + q, outage, a.status, st_base)) G = make_double2(0.0, 0.0);
-    const EndTerms tq = end_terms(G, po, pk);
+    const EndTerms tq = end_terms(G, Eo, Ek);
     if (q == 0) {
-      X = tq.xh; Y = tq.yh;
+      X = tq.X; Y = tq.Y;
     } else {
-      X = __dadd_rn(X, tq.xh); Y = __dadd_rn(Y, tq.yh);
+      X = __dadd_rn(X, tq.X); Y = __dadd_rn(Y, tq.Y);
     }
   }
-  const double A = __dmul_rn(vk, X), B = __dmul_rn(vk, Y);
-  if (p.x >= 0) vi[p.x] = __dmul_rn(-vo, B);
-  if (p.y >= 0) vi[p.y] = __dmul_rn(-vo, X);
-  if (p.z >= 0) vi[p.z] = __dmul_rn(vo, A);
-  if (p.w >= 0) vi[p.w] = __dmul_rn(-vo, Y);
+  write_pair(vi, p, X, Y, rvk);
 }
 
 // Under an outage mask: the coefficients of the branches in service of the
@@ -227,18 +257,21 @@ __device__ __forceinline__ double2 masked_hat(const View &v, const EvalArgs &a, 
 template <bool WF, bool WJ>
 __device__ __forceinline__ void finalize_bus(const View &v, const EvalArgs &a, int inst, int g, int32_t o,
                                              int64_t gb0, int32_t nb, const double *xi, double *vi, double vo,
-                                             double acc_a, double acc_b, double ah, double ch, int4 bm, int4 bm2,
-                                             double2 inj) {
+                                             double rvo, double sx, double sy, double ah, double ch, int4 bm,
+                                             int4 bm2, double2 inj) {
   const int64_t lb = o - gb0;
   const int32_t rp = bm.x, rq = bm.y, bp = bm.z, bq = bm.w;
   const int32_t gi = bm2.w;
   const bool is_slack = (v.formulation == PF_EXTENDED) && (lb == v.grid_slack[g]);
+  const double v2 = __dmul_rn(vo, vo);
+  const double tp = __fma_rn(v2, ah, -sx);          // V_o^2 A^ - S_X
+  const double tq = __fma_rn(v2, ch, sy);           // V_o^2 C^ + S_Y
   if (WF) {
     double *__restrict__ Fi = a.F + v.inst_f_off[inst];
     const double pin = a.p_inj ? a.p_inj[v.inst_bus_off[inst] + lb] : inj.x;
     const double qin = a.q_inj ? a.q_inj[v.inst_bus_off[inst] + lb] : inj.y;
-    double fp = __fma_rn(vo, __fma_rn(vo, ah, -acc_a), -pin);
-    double fq = __fma_rn(-vo, __fma_rn(vo, ch, acc_b), -qin);     // = -(vo (vo ch + sum b) + qin)
+    double fp = __dsub_rn(tp, pin);
+    double fq = __dadd_rn(-tq, -qin);
     if (is_slack) {
       fp = __dsub_rn(fp, xi[2 * nb + v.grid_ngen[g]]);
       Fi[v.grid_row_gth[g]] = __dsub_rn(xi[lb], v.grid_theta_set[g]);
@@ -254,14 +287,13 @@ __device__ __forceinline__ void finalize_bus(const View &v, const EvalArgs &a, i
     if (rq >= 0) Fi[rq] = fq;
   }
   if (WJ) {
-    const double two_vo = __dadd_rn(vo, vo);
     if (bp >= 0) {
-      if (bm2.x >= 0) vi[bp + bm2.x] = __dmul_rn(vo, acc_b);
-      if (bm2.y >= 0) vi[bp + bm2.y] = __fma_rn(two_vo, ah, -acc_a);
+      if (bm2.x >= 0) vi[bp + bm2.x] = sy;
+      if (bm2.y >= 0) vi[bp + bm2.y] = __dmul_rn(__fma_rn(v2, ah, tp), rvo);
     }
     if (bq >= 0) {
-      if (bm2.x >= 0) vi[bq + bm2.x] = __dmul_rn(-vo, acc_a);
-      if (bm2.y >= 0) vi[bq + bm2.y] = __fma_rn(-two_vo, ch, -acc_b);
+      if (bm2.x >= 0) vi[bq + bm2.x] = neg(sx);
+      if (bm2.y >= 0) vi[bq + bm2.y] = __dmul_rn(__fma_rn(v2, ch, tq), -rvo);
     }
     if (is_slack) {
       vi[bp + bm2.z] = -1.0;                // d g_p / d P_s
@@ -300,7 +332,7 @@ __global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArg
     const int64_t r = ur.y;
     const int g = __ldg(v.inst_grid + inst);
     const double *__restrict__ xi = a.x + __ldg(v.inst_x_off + inst);
-    // (cos, sin) at rec[2 k], (V, 0) at rec[2 k + 1], by global bus id k
+    // E = V (cos, sin) at rec[2 k], (V, 1/V) at rec[2 k + 1], by global bus id k
     const double2 *__restrict__ rec = v.phasor + 2 * __ldg(v.inst_rec_base + inst);
     double *__restrict__ vi = WJ ? a.vals + __ldg(v.inst_v_off + inst) : nullptr;
     const int32_t outage = MASKED ? v.inst_outage[inst] : -1;
@@ -319,10 +351,9 @@ __global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArg
       hat = __ldg(a.rhat + rb);
       if (WF) inj = __ldg(v.rbus_inj + rb);
     }
-    double acc_a = 0.0, acc_b = 0.0;
+    double sx = 0.0, sy = 0.0;
     bool any_out = false;                        // masked: an end of this bus is out of service
-    double2 po = make_double2(0.0, 0.0);
-    double vo = 0.0;
+    double2 Eo = make_double2(0.0, 0.0), vr = make_double2(0.0, 0.0);
     const int32_t D = ur.w & 0xff;
     const int64_t q0 = (int64_t)ur.z + lane;
 
@@ -343,8 +374,8 @@ __global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArg
         // the per-bus records come from k_phasor (programmatic dependent launch)
         cudaGridDependencySynchronize();
         if (owner) {
-          po = rec[2 * o];
-          vo = rec[2 * o + 1].x;
+          Eo = rec[2 * o];
+          vr = rec[2 * o + 1];
         }
       }
 #pragma unroll
@@ -366,31 +397,23 @@ __global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArg
             any_out |= mg.any_out;
           }
         }
-        const double2 pk = rec[2 * k];
-        const double vk = rec[2 * k + 1].x;
-        const EndTerms tm = end_terms(Gi, po, pk);
-        const double ea = __dmul_rn(vk, tm.xh), eb = __dmul_rn(vk, tm.yh);
-        acc_a = __dadd_rn(acc_a, ea);
-        acc_b = __dadd_rn(acc_b, eb);
-        if (WJ) {
-          const int4 p = pos[it];
-          if (p.x >= 0) vi[p.x] = __dmul_rn(-vo, eb);
-          if (p.y >= 0) vi[p.y] = __dmul_rn(-vo, tm.xh);
-          if (p.z >= 0) vi[p.z] = __dmul_rn(vo, ea);
-          if (p.w >= 0) vi[p.w] = __dmul_rn(-vo, tm.yh);
-        }
+        const double2 Ek = rec[2 * k];
+        const EndTerms tm = end_terms(Gi, Eo, Ek);
+        sx = __dadd_rn(sx, tm.X);
+        sy = __dadd_rn(sy, tm.Y);
+        if (WJ) write_pair(vi, pos[it], tm.X, tm.Y, rec[2 * k + 1].y);
       }
     }
     if (D == 0) {                                // a round of isolated buses only
       cudaGridDependencySynchronize();
-      if (owner) vo = rec[2 * o + 1].x;
+      if (owner) vr = rec[2 * o + 1];
     }
     if (owner) {
       // A^, C^: built (every end in service), else re-summed over the ends in
       // service in the same order as the built value
       if (MASKED && any_out) hat = masked_hat(v, a, q0, D, outage, st_base, o);
-      finalize_bus<WF, WJ>(v, a, inst, g, o, gb0_of(v, g), v.grid_nbus[g], xi, vi, vo, acc_a, acc_b, hat.x, hat.y,
-                           bm, bm2, inj);
+      finalize_bus<WF, WJ>(v, a, inst, g, o, gb0_of(v, g), v.grid_nbus[g], xi, vi, vr.x, vr.y, sx, sy, hat.x,
+                           hat.y, bm, bm2, inj);
     }
   }
 }
@@ -414,9 +437,9 @@ __global__ void __launch_bounds__(32) k_fused_large(View v, EvalArgs a) {
     const int32_t outage = MASKED ? v.inst_outage[inst] : -1;
     const int64_t st_base = MASKED ? v.inst_br_off[inst] - v.grid_br_off[g] : 0;
     const int32_t e0 = __ldg(v.inc_ptr + o), e1 = __ldg(v.inc_ptr + o + 1);
-    const double2 po = rec[2 * o];
-    const double vo = rec[2 * o + 1].x;
-    double acc_a = 0.0, acc_b = 0.0, acc_ma = 0.0, acc_mc = 0.0;
+    const double2 Eo = rec[2 * o];
+    const double2 vr = rec[2 * o + 1];
+    double sx = 0.0, sy = 0.0, acc_ma = 0.0, acc_mc = 0.0;
     for (int32_t cs = e0; cs < e1; cs += 32 * ITEMS) {
       int4 meta[ITEMS];
       double2 G[ITEMS];
@@ -440,12 +463,9 @@ __global__ void __launch_bounds__(32) k_fused_large(View v, EvalArgs a) {
           if (!in) Gi = make_double2(0.0, 0.0);
         }
         const int32_t k = meta[it].y;
-        const double2 pk = rec[2 * k];
-        const double vk = rec[2 * k + 1].x;
-        const EndTerms tm = end_terms(Gi, po, pk);
-        const double ea = __dmul_rn(vk, tm.xh), eb = __dmul_rn(vk, tm.yh);
-        acc_a = __dadd_rn(acc_a, ea);
-        acc_b = __dadd_rn(acc_b, eb);
+        const EndTerms tm = end_terms(Gi, Eo, rec[2 * k]);
+        sx = __dadd_rn(sx, tm.X);
+        sy = __dadd_rn(sy, tm.Y);
         if (MASKED) {
           const double2 ac = __ldg(a.ac + e);
           acc_ma = __dadd_rn(acc_ma, in ? ac.x : 0.0);
@@ -454,10 +474,7 @@ __global__ void __launch_bounds__(32) k_fused_large(View v, EvalArgs a) {
         if (WJ) {
           const int4 p = __ldg(v.inc_pos + e);
           if (meta[it].z == 1) {
-            if (p.x >= 0) vi[p.x] = __dmul_rn(-vo, eb);
-            if (p.y >= 0) vi[p.y] = __dmul_rn(-vo, tm.xh);
-            if (p.z >= 0) vi[p.z] = __dmul_rn(vo, ea);
-            if (p.w >= 0) vi[p.w] = __dmul_rn(-vo, tm.yh);
+            write_pair(vi, p, tm.X, tm.Y, rec[2 * k + 1].y);
           } else if (meta[it].z > 1) {
             write_group(v, a, e, meta[it].z, o, k, p, rec, vi, MASKED, outage, st_base);
           }
@@ -467,8 +484,8 @@ __global__ void __launch_bounds__(32) k_fused_large(View v, EvalArgs a) {
     // fixed butterfly: every lane ends with the same sums
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) {
-      acc_a = __dadd_rn(acc_a, __shfl_xor_sync(0xffffffffu, acc_a, m));
-      acc_b = __dadd_rn(acc_b, __shfl_xor_sync(0xffffffffu, acc_b, m));
+      sx = __dadd_rn(sx, __shfl_xor_sync(0xffffffffu, sx, m));
+      sy = __dadd_rn(sy, __shfl_xor_sync(0xffffffffu, sy, m));
       if (MASKED) {
         acc_ma = __dadd_rn(acc_ma, __shfl_xor_sync(0xffffffffu, acc_ma, m));
         acc_mc = __dadd_rn(acc_mc, __shfl_xor_sync(0xffffffffu, acc_mc, m));
@@ -486,7 +503,7 @@ __global__ void __launch_bounds__(32) k_fused_large(View v, EvalArgs a) {
         ch = hat.y;
       }
       const double2 inj = WF ? __ldg(v.bus_inj + o) : make_double2(0.0, 0.0);
-      finalize_bus<WF, WJ>(v, a, inst, g, o, gb0_of(v, g), v.grid_nbus[g], xi, vi, vo, acc_a, acc_b, ah, ch,
+      finalize_bus<WF, WJ>(v, a, inst, g, o, gb0_of(v, g), v.grid_nbus[g], xi, vi, vr.x, vr.y, sx, sy, ah, ch,
                            __ldg(v.bus_meta + o), __ldg(v.bus_meta2 + o), inj);
     }
   }

@@ -205,3 +205,42 @@ def test_phasor_routine_against_libm(P):
     # larger arguments: the reduction error grows with |theta| (ulp of theta)
     assert np.max(np.abs(c - np.cos(th))) <= 1e-12
     assert np.max(np.abs(s - np.sin(th))) <= 1e-12
+
+
+def test_voltage_records_against_libm(P):
+    """The per-bus records (V cos theta, V sin theta, V, 1/V) vs numpy, over a wide range of V,
+    and the dead-bus substitution (|V| < 2^-500: 2^-600 in place of V)."""
+    sys = GRIDS["grid2000"]
+    ctx = P.Context(sys)
+    n = sys.n_bus
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.uniform(-7, 7, n), np.exp(rng.uniform(-40, 40, n))])
+    x[n + 1::7] *= -1.0                                      # negative magnitudes too
+    x[n + 3], x[n + 4], x[n + 5] = 0.0, 1e-200, 2.0 ** -499
+    rec = ctx.voltage_records(torch.from_numpy(x).cuda()).cpu().numpy()
+    th, vm = x[:n], x[n:]
+    dead = np.abs(vm) < 2.0 ** -500
+    assert dead.sum() == 2 and np.array_equal(rec[:, 2], vm)
+    sv = np.where(dead, 2.0 ** -600, vm)
+    # products of the phasor routine (|error| <= 4.5e-16) and V, rounded once
+    assert np.all(np.abs(rec[:, 0] - sv * np.cos(th)) <= 8e-16 * np.abs(sv))
+    assert np.all(np.abs(rec[:, 1] - sv * np.sin(th)) <= 8e-16 * np.abs(sv))
+    # 1/V within one ulp
+    r = 1.0 / sv
+    assert np.all(np.abs(rec[:, 3] - r) <= np.spacing(np.abs(r)))
+    assert np.array_equal(rec[dead, 3], np.full(2, 2.0 ** 600))
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_dead_bus_matches_oracle(P, mode):
+    """A PQ bus at V = 0 (and one at 1e-300): F and J (whose dF/dV values divide that factor
+    out again) still match the oracle."""
+    sys = GRIDS["grid200"]
+    n = sys.n_bus
+    x = state(sys, 2, mode == EXTENDED).copy()
+    pq = [b for b in range(n) if b not in set(sys.pv_bus.tolist()) | {sys.slack_bus}]
+    x[n + pq[3]] = 0.0
+    x[n + pq[10]] = 1e-300
+    ctx, F, v = gpu_eval(P, sys, x, mode)
+    assert_tol(F, oracle.residual(sys, x, mode), "F dead bus")
+    assert_tol(v, oracle.jacobian(sys, x, mode)[2], "J dead bus")
