@@ -47,57 +47,125 @@ namespace pf {
 
 namespace {
 
-// ---------------------------------------------------------------------------
-// (cos t, sin t) by table-driven argument reduction (angle addition, after
-// P. T. P. Tang's table-driven elementary functions):
-//   t = k pi/16384 + r, |r| <= pi/32768, k = nearest integer to t 16384/pi;
-//   r from a two-constant Cody-Waite split of pi/16384 (the high part has 24
-//   significant bits, so k * STEP_HI is exact for |k| < 2^29, i.e. |t| < 2^16);
-//   cos r = 1 - r^2/2 and sin r = r - r^3/6 (the first omitted terms, r^4/24
-//   and r^5/120, are below 3.6e-18 and 7e-23 for |r| <= pi/32768);
-//   cos t = C_k cos r - S_k sin r, sin t = S_k cos r + C_k sin r with the
-//   table (C_k, S_k) = (cos, sin)(k pi / 16384) (32768 entries, 512 KB,
-//   computed on the host in long double).  12 FP64 operations.  Arguments
-//   beyond |t| = 2^16 use sincos().
-// ---------------------------------------------------------------------------
-constexpr double kInvStep = 0x1.45f306dc9c883p+12;    // 16384 / pi
-constexpr double kStepHi = 0x1.921fb60000000p-13;     // pi / 16384, high 24 bits
-constexpr double kStepLo = -0x1.777a5cf72cecep-38;    // pi / 16384 - kStepHi
-constexpr double kRoundMagic = 6755399441055744.0;    // 1.5 * 2^52
-
-__device__ __forceinline__ double2 table_sincos(double t, const double2 *__restrict__ tab) {
-  // |t| >= 2^16 or NaN, tested on the high word (integer pipe)
-  if ((__double2hiint(t) & 0x7fffffff) >= 0x40f00000) {
-    double s, c;
-    sincos(t, &s, &c);
-    return make_double2(c, s);
-  }
-  const double km = __fma_rn(t, kInvStep, kRoundMagic);
-  const int ki = __double2loint(km);                  // nearest integer, two's complement
-  const double kd = __dsub_rn(km, kRoundMagic);
-  double r = __fma_rn(-kd, kStepHi, t);
-  r = __fma_rn(-kd, kStepLo, r);
-  const double z = __dmul_rn(r, r);
-  const double cr = __fma_rn(z, -0.5, 1.0);                         // cos r
-  const double sr = __fma_rn(__dmul_rn(r, z), -1.0 / 6.0, r);       // sin r
-  const double2 T = __ldg(tab + (ki & (kSinCosTable - 1)));
-  return make_double2(__fma_rn(T.x, cr, -__dmul_rn(T.y, sr)), __fma_rn(T.y, cr, __dmul_rn(T.x, sr)));
-}
-
 // -x, by flipping the sign bit on the integer pipe (exact, no FP64 issue).
 __device__ __forceinline__ double neg(double x) {
   return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
 }
 
-// 1/s by one Householder step of order 2 (cubic convergence) from the
-// hardware's approximate reciprocal r0: with e = 1 - s r0,
-// 1/s = r0 / (1 - e) = r0 (1 + e + e^2 + ...), so r1 = r0 + r0 (e + e^2) has
-// relative error e^3.  3 FP64 operations.
-__device__ __forceinline__ double recip(double s) {
-  double r0;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r0) : "d"(s));
-  const double e = __fma_rn(-s, r0, 1.0);
-  return __fma_rn(r0, __fma_rn(e, e, e), r0);
+// ---------------------------------------------------------------------------
+// Per-bus voltage records on the integer pipe.  GB300 issues FP64 arithmetic
+// at 2 operations per clock per SM, 64-bit integer multiplies many times
+// faster, so the trigonometric routine and the reciprocal run in 64-bit fixed
+// point and leave one FP64 FMA per output.
+//
+// (cos t, sin t) for |t| < 32, by table-driven argument reduction (after
+// P. T. P. Tang's table-driven elementary functions):
+//   |t| = U 2^-57 (exact for |t| >= 2^-5, truncated at 2^-57 below);
+//   y = |t| 16384/pi from the 128-bit product U * round(2^65/pi), k = nearest
+//   integer to y, r = (y - k) pi/16384 from (y - k) 2^64 * round(pi 2^61),
+//   so |r| <= pi/32768 with an error below 2^-58;
+//   h = 1 - cos r = r^2/2 and sin r = r - r^3/6 in fixed point (the first
+//   omitted terms, r^4/24 and r^5/120, are below 3.6e-18 and 7e-23);
+//   cos t = C_k - (C_k h + S_k sin r),  sin t = S_k + (C_k sin r - S_k h)
+//   with the table (C_k, S_k) = (cos, sin)(k pi/16384) (32768 entries, as
+//   doubles and as 2^62-scaled integers, from long double on the host).
+// The corrections d are at most 1e-4 in magnitude and carry 2^-73 absolute
+// precision; V (C_k + d) is fma(V, C_k, V d) with the product V d formed and
+// rounded on the integer pipe.  1/V: a single-precision hardware
+// approximation y0 of 1/m (V = m 2^e, 1 <= m < 2), then one Householder step
+// of order 2 in 64-bit fixed point, y1 = y0 (1 + e + e^2) with e = 1 - m y0
+// (relative error e^3 < 2^-60), rounded to nearest.  Arguments |t| >= 32, and
+// V non-finite or of magnitude >= 2^977, use sincos() and FP64 arithmetic.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kInvStepFix = 0xa2f9836e4e44152aULL;   // round(2^65 / pi)
+constexpr long long kStepFix = 0x6487ed5110b4611aLL;                // round(pi 2^61)
+constexpr long long kSixthFix = 0x2aaaaaaaaaaaaaabLL;               // round(2^64 / 6)
+
+// v * d 2^-73 as a double, rounded to nearest (ties away), for a finite
+// normal v with 2^-600 <= |v| < 2^977 and |d| < 2^62: the 53-bit significand
+// of v times the normalised |d| in one 64 x 64 -> high-64 product.
+__device__ __forceinline__ double mul_fix73(double v, long long d) {
+  if (d == 0) return 0.0;
+  const unsigned long long vb = (unsigned long long)__double_as_longlong(v);
+  const int ev = (int)((vb >> 52) & 0x7ff);
+  const unsigned long long vm = ((vb & 0xfffffffffffffULL) | (1ULL << 52)) << 11;    // top bit 63
+  const unsigned long long a = d < 0 ? 0ULL - (unsigned long long)d : (unsigned long long)d;
+  const int lz = __clzll((long long)a);
+  unsigned long long p = __umul64hi(vm, a << lz);                                   // in [2^62, 2^64)
+  int e = ev + 64 - lz - 73;                    // biased exponent when bit 63 of p is set
+  if (!(p >> 63)) {
+    p <<= 1;
+    e -= 1;
+  }
+  const unsigned long long sign = (vb ^ (unsigned long long)d) & 0x8000000000000000ULL;
+  const unsigned long long mag = ((unsigned long long)e << 52) + ((p >> 11) & 0xfffffffffffffULL) + ((p >> 10) & 1);
+  return __longlong_as_double((long long)(sign | mag));
+}
+
+// 1/v for a finite normal v with 2^-600 <= |v| < 2^977.
+__device__ __forceinline__ double recip_fix(double v) {
+  const unsigned long long vb = (unsigned long long)__double_as_longlong(v);
+  const int ev = (int)((vb >> 52) & 0x7ff);
+  const unsigned long long frac = vb & 0xfffffffffffffULL;
+  const unsigned long long M = (frac | (1ULL << 52)) << 10;                         // m 2^62
+  float y0f;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0f) : "f"(__uint_as_float(0x3f800000u | (unsigned)(frac >> 29))));
+  const unsigned u = __float_as_uint(y0f);                                           // y0 in (0.5, 1]
+  const int ef = (int)((u >> 23) & 0xff) - 127;                                      // -1 or 0
+  const long long Y = (long long)((unsigned long long)(0x800000u | (u & 0x7fffffu)) << (39 + ef));   // y0 2^62
+  const long long E = (long long)(1ULL << 60) - (long long)__umul64hi(M, (unsigned long long)Y);    // e 2^60
+  const long long T = E + (__mul64hi(E << 22, E << 22) >> 40);                      // (e + e^2) 2^60
+  const unsigned long long Y1 = (unsigned long long)(Y + (__mul64hi(Y, T << 20) >> 16));            // y1 2^62
+  const int lz = __clzll((long long)Y1);
+  const unsigned long long n = Y1 << lz;
+  const unsigned long long mag =
+      ((unsigned long long)(2047 - ev - lz) << 52) + ((n >> 11) & 0xfffffffffffffULL) + ((n >> 10) & 1);
+  return __longlong_as_double((long long)((vb & 0x8000000000000000ULL) | mag));
+}
+
+// (V cos t, V sin t) and 1/V of a per-bus record; sv is V after the dead-bus
+// substitution.
+struct RectV {
+  double2 E;
+  double rv;
+};
+
+__device__ __forceinline__ RectV rect_voltage(double t, double sv, const double2 *__restrict__ tab,
+                                              const longlong2 *__restrict__ tabf) {
+  RectV o;
+  if ((__double2hiint(t) & 0x7fffffff) >= 0x40400000 || (__double2hiint(sv) & 0x7ff00000) >= 0x7d000000) {
+    double sn, cs;
+    sincos(t, &sn, &cs);
+    o.E = make_double2(__dmul_rn(sv, cs), __dmul_rn(sv, sn));
+    o.rv = __drcp_rn(sv);
+    return o;
+  }
+  const unsigned long long tb = (unsigned long long)__double_as_longlong(t);
+  const int et = (int)((tb >> 52) & 0x7ff);
+  const unsigned long long mt = (tb & 0xfffffffffffffULL) | (et ? (1ULL << 52) : 0ULL);
+  const int sh = et - 1018;                                   // |t| 2^57 = mt 2^(et - 1018)
+  const unsigned long long U = sh >= 0 ? mt << sh : (sh > -64 ? mt >> -sh : 0ULL);
+  // y 2^108 = U * kInvStepFix; k = round(y), f = y - k
+  const unsigned long long wh = __umul64hi(U, kInvStepFix), wl = U * kInvStepFix;
+  const unsigned long long tr = wh + (1ULL << 43);
+  const unsigned k = (unsigned)(tr >> 44);
+  const long long fk = (long long)(tr & ((1ULL << 44) - 1)) - (1LL << 43);          // f 2^44
+  const long long F = (long long)(((unsigned long long)fk << 20) | (wl >> 44));      // f 2^64
+  const long long R = __mul64hi(F, kStepFix);                                        // r 2^75
+  const long long R2 = __mul64hi(R, R);                                              // r^2 2^86
+  const long long S6 = __mul64hi(__mul64hi(R2, R), kSixthFix);                       // r^3/6 2^97
+  const long long SR = R - (S6 >> 22);                                               // sin r 2^75
+  const long long H = R2 >> 12;                                                      // r^2/2 2^75
+  const int idx = (int)(k & (kSinCosTable - 1));
+  const double2 T = __ldg(tab + idx);
+  const longlong2 Tf = __ldg(tabf + idx);                                            // (C, S) 2^62
+  const long long dc = -(__mul64hi(Tf.x, H) + __mul64hi(Tf.y, SR));                  // 2^73
+  const long long ds = __mul64hi(Tf.x, SR) - __mul64hi(Tf.y, H);
+  const double ex = __fma_rn(sv, T.x, mul_fix73(sv, dc));
+  const double ey = __fma_rn(sv, T.y, mul_fix73(sv, ds));
+  o.E = make_double2(ex, (long long)tb < 0 ? neg(ey) : ey);                         // sin is odd
+  o.rv = recip_fix(sv);
+  return o;
 }
 
 // Per bus of every instance: the voltage in rectangular form
@@ -120,10 +188,10 @@ __global__ void __launch_bounds__(256) k_phasor(View v, const double *__restrict
     const double *xi = x + v.inst_x_off[inst];
     const double th = __ldg(xi + lb);
     const double vm = __ldg(xi + v.grid_nbus[v.inst_grid[inst]] + lb);
-    const double2 cs = table_sincos(th, v.sincos_tab);
     const double sv = (__double2hiint(vm) & 0x7ff00000) < 0x20b00000 ? kDeadV : vm;   // |V| < 2^-500
-    v.phasor[2 * q] = make_double2(__dmul_rn(sv, cs.x), __dmul_rn(sv, cs.y));
-    v.phasor[2 * q + 1] = make_double2(vm, recip(sv));
+    const RectV r = rect_voltage(th, sv, v.sincos_tab, v.sincos_fix);
+    v.phasor[2 * q] = r.E;
+    v.phasor[2 * q + 1] = make_double2(vm, r.rv);
   }
 }
 
@@ -569,12 +637,12 @@ void built_coefficients(const View &v, EvalArgs &a) {
 }
 
 __global__ void k_sincos(const double *__restrict__ t, int64_t n, const double2 *__restrict__ tab,
-                         double *__restrict__ c, double *__restrict__ sn) {
+                         const longlong2 *__restrict__ tabf, double *__restrict__ c, double *__restrict__ sn) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double2 r = table_sincos(t[i], tab);
-  c[i] = r.x;
-  sn[i] = r.y;
+  const RectV r = rect_voltage(t[i], 1.0, tab, tabf);
+  c[i] = r.E.x;
+  sn[i] = r.E.y;
 }
 
 }  // namespace
@@ -671,7 +739,7 @@ int launch_eval_scratch(Ctx &c, const double *x, double *F, double *vals, double
 int launch_sincos(Ctx &c, const double *t, int64_t n, double *cs, double *sn, cudaStream_t s) {
   if (n <= 0) return PF_OK;
   if (!t || !cs || !sn) return fail(PF_ERR_INVALID, "NULL argument");
-  k_sincos<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t, n, c.v.sincos_tab, cs, sn);
+  k_sincos<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t, n, c.v.sincos_tab, c.v.sincos_fix, cs, sn);
   PF_CUDA_TRY(cudaGetLastError());
   return PF_OK;
 }
