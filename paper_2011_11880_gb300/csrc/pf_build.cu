@@ -688,13 +688,18 @@ __global__ void k_rbus_fill(View v, int64_t n, const int32_t *rbus, const double
   }
 }
 
-// per round of 32 buses of every instance: its instance, round and descriptor
+// per round of 32 buses of every instance: its instance, round and
+// descriptor.  The rounds of a grid ascend in neighbour count; an instance's
+// units take them heaviest and lightest alternately (n-1, 0, n-2, 1, ...), so
+// the CTAs that run side by side -- all of them, when one instance fills less
+// than a wave -- carry a mix of long and short rounds.
 __global__ void k_unit_fill(View v, const int64_t *lane_off, int4 *unit) {
   const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= v.n_lane_units) return;
   const int inst = find_segment(lane_off, v.n_inst, u);
   const int g = v.inst_grid[inst];
-  const int64_t r = v.grid_round_off[g] + (u - lane_off[inst]);
+  const int64_t j = u - lane_off[inst], n = lane_off[inst + 1] - lane_off[inst];
+  const int64_t r = v.grid_round_off[g] + ((j & 1) ? (j >> 1) : n - 1 - (j >> 1));
   const int4 d = v.round_desc[r];
   unit[u] = make_int4(inst, (int32_t)r, d.x, d.y | (d.z << 8));
 }
