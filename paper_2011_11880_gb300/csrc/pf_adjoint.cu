@@ -591,7 +591,8 @@ int launch_vjp(Ctx &c, const double *x, const pf_overrides *ov, const double *v,
   if (g->x) {
     a.gx = g->x;
     const bool masked = c.any_outage || a.status != nullptr;
-    if (n_cot >= 16) PF_TRY(launch_state_ch<8>(c, a, masked, s));
+    if (n_cot >= 32) PF_TRY(launch_state_ch<16>(c, a, masked, s));
+    else if (n_cot >= 16) PF_TRY(launch_state_ch<8>(c, a, masked, s));
     else if (n_cot >= 4) PF_TRY(launch_state_ch<4>(c, a, masked, s));
     else PF_TRY(launch_state_ch<1>(c, a, masked, s));
   }
