@@ -65,7 +65,8 @@ __device__ __forceinline__ double neg(double x) {
 //   integer to y, r = (y - k) pi/16384 from (y - k) 2^64 * round(pi 2^61),
 //   so |r| <= pi/32768 with an error below 2^-58;
 //   h = 1 - cos r = r^2/2 and sin r = r - r^3/6 in fixed point (the first
-//   omitted terms, r^4/24 and r^5/120, are below 3.6e-18 and 7e-23);
+//   omitted terms, r^4/24 and r^5/120, are below 3.6e-18 and 7e-23; r^3/6,
+//   C_k h and S_k h from 32-bit factors, to 2^-57);
 //   cos t = C_k - (C_k h + S_k sin r),  sin t = S_k + (C_k sin r - S_k h)
 //   with the table (C_k, S_k) = (cos, sin)(k pi/16384) (32768 entries, as
 //   doubles and as 2^62-scaled integers, from long double on the host).
@@ -79,7 +80,7 @@ __device__ __forceinline__ double neg(double x) {
 // ---------------------------------------------------------------------------
 constexpr unsigned long long kInvStepFix = 0xa2f9836e4e44152aULL;   // round(2^65 / pi)
 constexpr long long kStepFix = 0x6487ed5110b4611aLL;                // round(pi 2^61)
-constexpr long long kSixthFix = 0x2aaaaaaaaaaaaaabLL;               // round(2^64 / 6)
+constexpr int kSixth32 = 0x2aaaaaab;                                 // round(2^32 / 6)
 
 // v * d 2^-73 as a double, rounded to nearest (ties away), for a finite
 // normal v with 2^-600 <= |v| < 2^977 and |d| < 2^62: the 53-bit significand
@@ -114,7 +115,8 @@ __device__ __forceinline__ double recip_fix(double v) {
   const int ef = (int)((u >> 23) & 0xff) - 127;                                      // -1 or 0
   const long long Y = (long long)((unsigned long long)(0x800000u | (u & 0x7fffffu)) << (39 + ef));   // y0 2^62
   const long long E = (long long)(1ULL << 60) - (long long)__umul64hi(M, (unsigned long long)Y);    // e 2^60
-  const long long T = E + (__mul64hi(E << 22, E << 22) >> 40);                      // (e + e^2) 2^60
+  const long long Es = E >> 8;                                                       // |e| < 2^-21: 32 bits
+  const long long T = E + ((Es * Es) >> 44);                                         // (e + e^2) 2^60
   const unsigned long long Y1 = (unsigned long long)(Y + (__mul64hi(Y, T << 20) >> 16));            // y1 2^62
   const int lz = __clzll((long long)Y1);
   const unsigned long long n = Y1 << lz;
@@ -153,14 +155,17 @@ __device__ __forceinline__ RectV rect_voltage(double t, double sv, const double2
   const long long F = (long long)(((unsigned long long)fk << 20) | (wl >> 44));      // f 2^64
   const long long R = __mul64hi(F, kStepFix);                                        // r 2^75
   const long long R2 = __mul64hi(R, R);                                              // r^2 2^86
-  const long long S6 = __mul64hi(__mul64hi(R2, R), kSixthFix);                       // r^3/6 2^97
-  const long long SR = R - (S6 >> 22);                                               // sin r 2^75
+  // r^3/6 (< 2^-42.6) needs only 32-bit factors: r 2^43 and r^2 2^54
+  const int r3 = __mulhi(__mulhi((int)(R2 >> 32), (int)(R >> 32)), kSixth32);       // r^3/6 2^65
+  const long long SR = R - ((long long)r3 << 10);                                    // sin r 2^75
   const long long H = R2 >> 12;                                                      // r^2/2 2^75
   const int idx = (int)(k & (kSinCosTable - 1));
   const double2 T = __ldg(tab + idx);
   const longlong2 Tf = __ldg(tabf + idx);                                            // (C, S) 2^62
-  const long long dc = -(__mul64hi(Tf.x, H) + __mul64hi(Tf.y, SR));                  // 2^73
-  const long long ds = __mul64hi(Tf.x, SR) - __mul64hi(Tf.y, H);
+  // h < 2^-27.7: C h and S h from 32-bit factors (C 2^30, h 2^58) to 2^-57
+  const int h32 = (int)(H >> 17), c32 = (int)(Tf.x >> 32), s32 = (int)(Tf.y >> 32);
+  const long long dc = -(((long long)c32 * h32) >> 15) - __mul64hi(Tf.y, SR);          // 2^73
+  const long long ds = __mul64hi(Tf.x, SR) - (((long long)s32 * h32) >> 15);
   const double ex = __fma_rn(sv, T.x, mul_fix73(sv, dc));
   const double ey = __fma_rn(sv, T.y, mul_fix73(sv, ds));
   o.E = make_double2(ex, (long long)tb < 0 ? neg(ey) : ey);                         // sin is odd
@@ -177,13 +182,22 @@ __device__ __forceinline__ RectV rect_voltage(double t, double sv, const double2
 // and the dF/dV values, which divide that factor out again, stay exact.
 constexpr double kDeadV = 0x1p-600;
 
+// One thread per instance-bus; the block looks up the instances of its
+// first and last bus once, a thread searches only between them.
 __global__ void __launch_bounds__(256) k_phasor(View v, const double *__restrict__ x) {
   // Let the fused kernel start launching; it waits for this grid's results.
   cudaTriggerProgrammaticLaunchCompletion();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q = v.bus_inst_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < v.n_bus_inst;
-       q += stride) {
-    const int inst = v.n_inst == 1 ? 0 : find_segment(v.inst_bus_off, v.n_inst, q);
+  __shared__ int s_inst[2];
+  const int64_t q0 = v.bus_inst_begin + (int64_t)blockIdx.x * blockDim.x;
+  const int64_t q = q0 + threadIdx.x;
+  if (v.n_inst > 1 && threadIdx.x < 2) {
+    const int64_t key = threadIdx.x == 0 ? q0 : min(q0 + (int64_t)blockDim.x, v.n_bus_inst) - 1;
+    s_inst[threadIdx.x] = find_segment(v.inst_bus_off, v.n_inst, key);
+  }
+  __syncthreads();
+  if (q < v.n_bus_inst) {
+    const int i0 = v.n_inst > 1 ? s_inst[0] : 0, i1 = v.n_inst > 1 ? s_inst[1] : 0;
+    const int inst = i0 == i1 ? i0 : i0 + find_segment(v.inst_bus_off + i0, i1 - i0 + 1, q);
     const int64_t lb = q - v.inst_bus_off[inst];
     const double *xi = x + v.inst_x_off[inst];
     const double th = __ldg(xi + lb);
@@ -648,10 +662,11 @@ __global__ void k_sincos(const double *__restrict__ t, int64_t n, const double2 
 }  // namespace
 
 int launch_phasor(const View &v, int num_sms, const double *x, cudaStream_t s) {
+  (void)num_sms;
   const int tb = 256;
-  int64_t blocks = (v.n_bus_inst - v.bus_inst_begin + tb - 1) / tb;
-  blocks = std::min<int64_t>(blocks, (int64_t)num_sms * 16);
-  k_phasor<<<(unsigned)std::max<int64_t>(blocks, 1), tb, 0, s>>>(v, x);
+  const int64_t blocks = (v.n_bus_inst - v.bus_inst_begin + tb - 1) / tb;
+  if (blocks <= 0) return PF_OK;
+  k_phasor<<<(unsigned)blocks, tb, 0, s>>>(v, x);
   PF_CUDA_TRY(cudaGetLastError());
   return PF_OK;
 }
