@@ -191,15 +191,23 @@ def test_full_70k_against_oracle(P):
 
 
 def test_phasor_routine_against_libm(P):
-    """The table-driven sin / cos of the phasor kernel vs the host libm (numpy),
-    including arguments past the table's reduction range."""
+    """The table-driven sin / cos of the phasor kernel vs the host libm (numpy): the fixed-point
+    path (|t| < 32) on a grid, at and between table points, near the switch to sincos() at 32, on
+    tiny and subnormal angles; and arguments past it."""
     ctx = P.Context(GRIDS["three_bus"])
     rng = np.random.default_rng(0)
+    steps = np.arange(-3000, 3001) * (np.pi / 16384)           # table points and the midpoints between
     th = np.concatenate([np.linspace(-7, 7, 400001), rng.uniform(-1e4, 1e4, 100000),
+                         rng.uniform(-32, 32, 100000), steps, steps + np.pi / 32768,
+                         np.nextafter(32.0, 0.0) * np.array([1.0, -1.0]), [32.0, -32.0],
+                         2.0 ** -np.arange(1, 1075, 7.0), -(2.0 ** -np.arange(1, 1075, 11.0)), [5e-324],
                          [0.0, -0.0, np.pi, -np.pi, 1e5, -3e6, 65535.9, 65536.0]])
     c, s = ctx.sincos(torch.from_numpy(th).cuda())
     c, s = c.cpu().numpy(), s.cpu().numpy()
-    small = np.abs(th) <= 7
+    small = np.abs(th) <= 32
+    # sin is odd: the sign of a tiny or zero angle is kept
+    tiny = np.abs(th) < 1e-300
+    assert np.array_equal(np.signbit(s[tiny]), np.signbit(th[tiny]))
     assert np.max(np.abs(c - np.cos(th))[small]) <= 4.5e-16
     assert np.max(np.abs(s - np.sin(th))[small]) <= 4.5e-16
     # larger arguments: the reduction error grows with |theta| (ulp of theta)
