@@ -177,12 +177,12 @@ def algorithmic_bytes(d, n_pv, n_load, n_shunt):
 def fused_fp64_ops(d, n_pairs, pattern):
     """FP64 operations (an FMA, a multiply or an add each count one: each
     takes one issue of the FP64 pipe) of one instance in k_fused, F and J,
-    no mask: per pair of connected buses (parallel branches merged) 10 -- the
-    terms u, w, X, Y from the rectangular voltages (4 multiplies + 4 FMAs) and
-    2 adds into the bus sums; per value in a V column of a P or Q row one
-    multiply by 1/V (a theta-column value is X or -Y itself), plus one more
-    FMA for each diagonal V value; per bus 5: V_o^2, V_o^2 A^ - S_X,
-    V_o^2 C^ + S_Y and the two F rows."""
+    no mask: per pair of connected buses (parallel branches merged) 8 -- the
+    terms u, w, X, Y from the rectangular voltages (4 multiplies + 4 FMAs;
+    the bus sums of X and Y are exact integer sums on the integer pipe); per
+    value in a V column of a P or Q row one multiply by 1/V (a theta-column
+    value is X or -Y itself), plus one more FMA for each diagonal V value; per
+    bus 5: V_o^2, V_o^2 A^ - S_X, V_o^2 C^ + S_Y and the two F rows."""
     n = d.n_bus
     rp, ci = pattern
     if d.formulation == 0:                   # reduced: theta columns of the n - 1 non-slack buses first
@@ -192,7 +192,7 @@ def fused_fp64_ops(d, n_pairs, pattern):
         row = np.repeat(np.arange(rp.shape[0] - 1), np.diff(rp))
         n_v = int(np.count_nonzero((row < 2 * n) & (ci >= n) & (ci < 2 * n)))
         n_vdiag = 2 * n
-    return 10 * n_pairs + n_v + n_vdiag + 5 * n
+    return 8 * n_pairs + n_v + n_vdiag + 5 * n
 
 
 def source_hash():

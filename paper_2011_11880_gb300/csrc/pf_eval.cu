@@ -21,8 +21,9 @@
 // where A^ = sum A + shunt g and C^ = sum C + shunt b.  1/V is formed once
 // per bus by k_phasor.  Per pair of connected buses (parallel branches merged
 // into one end with their coefficients summed): 8 FP64 operations for u, w,
-// X, Y, 2 adds into the bus sums, no operation for a theta-column J value (a
-// sign flip on the integer pipe) and one multiply for a V-column J value.
+// X, Y, no operation for a theta-column J value (a sign flip on the integer
+// pipe) and one multiply for a V-column J value; the sums S_X, S_Y are exact,
+// in 128-bit fixed point on the integer pipe, rounded once.
 //
 // Work decomposition.  The buses of each grid are sorted by their number of
 // neighbours and cut into rounds of 32; one warp evaluates one round, one bus
@@ -33,12 +34,13 @@
 // nearly every lane does useful FP64 work at every step.  A bus with more
 // than 32 neighbours is evaluated by a whole warp in a second kernel.
 //
-// Determinism: every operation is an explicitly rounded intrinsic and every
-// sum runs in a fixed order -- a group's coefficients and a bus's pairs in
-// incidence-list order for a bus with up to 32 neighbours, lane-strided
-// partial sums over its ends combined by a fixed butterfly for a larger bus
-// -- so results are bit-identical run to run, across code paths and for every
-// tuning.
+// Determinism: every operation is an explicitly rounded intrinsic, the bus
+// sums of a bus with up to 32 neighbours are exact (so independent of the
+// order of the terms), and every other sum runs in a fixed order -- a group's
+// coefficients in incidence-list order, the FP64 fallback of the bus sums in
+// list order, lane-strided partial sums over the ends combined by a fixed
+// butterfly for a larger bus -- so results are bit-identical run to run,
+// across code paths and for every tuning.
 #include <algorithm>
 
 #include "pf_internal.cuh"
@@ -207,6 +209,72 @@ __global__ void __launch_bounds__(256) k_phasor(View v, const double *__restrict
     v.phasor[2 * q] = r.E;
     v.phasor[2 * q + 1] = make_double2(vm, r.rv);
   }
+}
+
+// Exact sums of FP64 terms on the integer pipe: a 128-bit two's-complement
+// accumulator with 64 fraction bits (|term| < 2^57; bits below 2^-64 are
+// dropped, an absolute error below 2^-64 per term).  The sum is exact up to
+// that, so it does not depend on the order of the terms, and it is rounded
+// to a double once (to nearest, ties away from zero).
+struct Acc128 {
+  unsigned long long lo;
+  long long hi;
+};
+
+// Adds x; clears `ok` when |x| >= 2^57 or x is not finite (the caller then
+// sums in FP64 instead).
+__device__ __forceinline__ void acc_add(Acc128 &a, double x, bool &ok) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  ok = ok && e < 1080;                        // |x| < 2^57: 32 terms stay below 2^62
+  const unsigned long long m = (b & 0xfffffffffffffULL) | (e ? (1ULL << 52) : 0ULL);
+  const int s = e - 1011;                      // x = m 2^(e - 1075) = (m 2^s) 2^-64
+  unsigned long long lo, hi;
+  if (s >= 64) {
+    hi = m << min(s - 64, 63);
+    lo = 0ULL;
+  } else if (s > 0) {
+    hi = m >> (64 - s);
+    lo = m << s;
+  } else {
+    hi = 0ULL;
+    lo = s > -64 ? m >> -s : 0ULL;
+  }
+  if (b >> 63) {                               // subtract
+    const unsigned long long nlo = a.lo - lo;
+    a.hi = (long long)((unsigned long long)a.hi - hi - (a.lo < lo ? 1ULL : 0ULL));
+    a.lo = nlo;
+  } else {
+    const unsigned long long nlo = a.lo + lo;
+    a.hi = (long long)((unsigned long long)a.hi + hi + (nlo < lo ? 1ULL : 0ULL));
+    a.lo = nlo;
+  }
+}
+
+__device__ __forceinline__ double acc_value(const Acc128 &a) {
+  unsigned long long hi = (unsigned long long)a.hi, lo = a.lo;
+  const unsigned long long sign = hi & 0x8000000000000000ULL;
+  if (sign) {                                  // magnitude
+    lo = 0ULL - lo;
+    hi = ~hi + (lo == 0ULL ? 1ULL : 0ULL);
+  }
+  if ((hi | lo) == 0ULL) return 0.0;
+  // normalise the 128-bit magnitude so that its top bit is bit 63 of n
+  const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+  const int sh = lz & 63;
+  unsigned long long n, rest;
+  if (lz < 64) {
+    n = sh ? (hi << sh) | (lo >> (64 - sh)) : hi;
+    rest = lo << sh;                           // bits below n (only the rounding bit matters)
+  } else {
+    n = lo << sh;
+    rest = 0ULL;
+  }
+  (void)rest;
+  const int p = 127 - lz;                      // value = 2^(p - 64) * (n / 2^63)
+  const unsigned long long mag =
+      ((unsigned long long)(p - 64 + 1023) << 52) + ((n >> 11) & 0xfffffffffffffULL) + ((n >> 10) & 1ULL);
+  return __longlong_as_double((long long)(sign | mag));
 }
 
 struct EvalArgs {
@@ -391,9 +459,29 @@ __device__ __forceinline__ void finalize_bus(const View &v, const EvalArgs &a, i
   }
 }
 
+// The merged coefficients (G, B) of slot q (meta: its slot_meta entry) as
+// the mask leaves them: the built value, zero for a single branch out of
+// service, or the re-summed branches in service of a group.
+template <bool MASKED>
+__device__ __forceinline__ double2 slot_gb(const View &v, const EvalArgs &a, int4 meta, double2 G, int32_t outage,
+                                           int64_t st_base, bool &any_out) {
+  if (!MASKED) return G;
+  if (meta.y == 1) {
+    const int32_t l = meta.z >> 1;
+    if (l == outage || (a.status != nullptr && a.status[st_base + l] == 0)) {
+      any_out = true;
+      return make_double2(0.0, 0.0);
+    }
+    return G;
+  }
+  const GroupCoeff mg = masked_group(v, a, meta.w, meta.y, outage, st_base);
+  any_out |= mg.any_out;
+  return mg.gb;
+}
+
 // One-warp CTAs that must fit on one SM (register budget of k_fused).
 #ifndef PF_FUSED_MIN_CTAS
-#define PF_FUSED_MIN_CTAS 16
+#define PF_FUSED_MIN_CTAS 24
 #endif
 
 // One warp per round.  A round holds up to 32 buses with equal (or
@@ -433,7 +521,8 @@ __global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArg
       hat = __ldg(a.rhat + rb);
       if (WF) inj = __ldg(v.rbus_inj + rb);
     }
-    double sx = 0.0, sy = 0.0;
+    Acc128 ax{0ULL, 0LL}, ay{0ULL, 0LL};       // exact S_X, S_Y
+    bool exact = true;
     bool any_out = false;                        // masked: an end of this bus is out of service
     double2 Eo = make_double2(0.0, 0.0), vr = make_double2(0.0, 0.0);
     const int32_t D = ur.w & 0xff;
@@ -465,24 +554,11 @@ __global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArg
         const int32_t len = meta[it].y;          // branches in the group, -1 padding
         if (len < 0) continue;
         const int32_t k = meta[it].x;
-        double2 Gi = G[it];
-        if (MASKED) {
-          if (len == 1) {
-            const int32_t l = meta[it].z >> 1;
-            if (l == outage || (a.status != nullptr && a.status[st_base + l] == 0)) {
-              Gi = make_double2(0.0, 0.0);
-              any_out = true;
-            }
-          } else {
-            const GroupCoeff mg = masked_group(v, a, meta[it].w, len, outage, st_base);
-            Gi = mg.gb;
-            any_out |= mg.any_out;
-          }
-        }
+        const double2 Gi = slot_gb<MASKED>(v, a, meta[it], G[it], outage, st_base, any_out);
         const double2 Ek = rec[2 * k];
         const EndTerms tm = end_terms(Gi, Eo, Ek);
-        sx = __dadd_rn(sx, tm.X);
-        sy = __dadd_rn(sy, tm.Y);
+        acc_add(ax, tm.X, exact);
+        acc_add(ay, tm.Y, exact);
         if (WJ) write_pair(vi, pos[it], tm.X, tm.Y, rec[2 * k + 1].y);
       }
     }
@@ -491,6 +567,27 @@ __global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArg
       if (owner) vr = rec[2 * o + 1];
     }
     if (owner) {
+      // S_X, S_Y: the exact sums, rounded once; in FP64, in list order, when a
+      // term is out of the accumulator's range or the bus is dead (its terms
+      // carry the 2^-600 factor that 1/V divides out again)
+      double sx, sy;
+      if (exact && (__double2hiint(vr.x) & 0x7ff00000) >= 0x20b00000) {
+        sx = acc_value(ax);
+        sy = acc_value(ay);
+      } else {
+        sx = 0.0;
+        sy = 0.0;
+        bool unused = false;
+        for (int32_t j = 0; j < D; ++j) {
+          const int64_t q = q0 + 32 * j;
+          const int4 m = __ldg(v.slot_meta + q);
+          if (m.y < 0) continue;
+          const double2 Gi = slot_gb<MASKED>(v, a, m, __ldg(a.sgb + q), outage, st_base, unused);
+          const EndTerms tm = end_terms(Gi, Eo, rec[2 * m.x]);
+          sx = __dadd_rn(sx, tm.X);
+          sy = __dadd_rn(sy, tm.Y);
+        }
+      }
       // A^, C^: built (every end in service), else re-summed over the ends in
       // service in the same order as the built value
       if (MASKED && any_out) hat = masked_hat(v, a, q0, D, outage, st_base, o);
