@@ -174,15 +174,16 @@ def algorithmic_bytes(d, n_pv, n_load, n_shunt):
     return read + write
 
 
-def fused_fp64_ops(d, n_pairs, pattern):
-    """FP64 operations (an FMA, a multiply or an add each count one: each
-    takes one issue of the FP64 pipe) of one instance in k_fused, F and J,
-    no mask: per pair of connected buses (parallel branches merged) 8 -- the
-    terms u, w, X, Y from the rectangular voltages (4 multiplies + 4 FMAs;
-    the bus sums of X and Y are exact integer sums on the integer pipe); per
-    value in a V column of a P or Q row one multiply by 1/V (a theta-column
-    value is X or -Y itself), plus one more FMA for each diagonal V value; per
-    bus 5: V_o^2, V_o^2 A^ - S_X, V_o^2 C^ + S_Y and the two F rows."""
+def fused_fp64_ops(d, n_pairs, pattern, executed=False):
+    """Algorithmic operations (an FMA, a multiply or an add each count one) of
+    one instance's F and J in the rectangular-voltage form k_fused evaluates,
+    no mask: per pair of connected buses (parallel branches merged) 10 -- the
+    terms u, w, X, Y (4 multiplies + 4 FMAs) and the two adds into the bus
+    sums; per value in a V column of a P or Q row one multiply by 1/V (a
+    theta-column value is X or -Y itself), plus one more FMA for each
+    diagonal V value; per bus 5: V_o^2, V_o^2 A^ - S_X, V_o^2 C^ + S_Y and the
+    two F rows.  k_fused executes the bus sums as exact integer sums on the
+    ALU pipe, so its FP64 pipe executes 2 per pair fewer (`executed`)."""
     n = d.n_bus
     rp, ci = pattern
     if d.formulation == 0:                   # reduced: theta columns of the n - 1 non-slack buses first
@@ -192,7 +193,7 @@ def fused_fp64_ops(d, n_pairs, pattern):
         row = np.repeat(np.arange(rp.shape[0] - 1), np.diff(rp))
         n_v = int(np.count_nonzero((row < 2 * n) & (ci >= n) & (ci < 2 * n)))
         n_vdiag = 2 * n
-    return 8 * n_pairs + n_v + n_vdiag + 5 * n
+    return (8 if executed else 10) * n_pairs + n_v + n_vdiag + 5 * n
 
 
 def source_hash():
@@ -403,7 +404,9 @@ def main():
     ip, _, oth = one.incidence()
     own = np.repeat(np.arange(d1.n_bus), np.diff(ip))
     n_pairs = int(np.count_nonzero(np.r_[True, (oth[1:] != oth[:-1]) | (own[1:] != own[:-1])]))
-    ops_kf = N_STATES * fused_fp64_ops(d1, n_pairs, one.pattern())  # one batched launch
+    pattern = one.pattern()
+    ops_kf = N_STATES * fused_fp64_ops(d1, n_pairs, pattern)        # one batched launch
+    ops_exec = N_STATES * fused_fp64_ops(d1, n_pairs, pattern, executed=True)
     bytes_alg = N_STATES * algorithmic_bytes(d1, n_pv, n_load, n_shunt)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     fp64_peak_gops = 152 * 2 * sm_mhz * 1e6 / 1e9                 # 2 FP64 operations / clk / SM
@@ -413,7 +416,8 @@ def main():
     roofline = {"bound": "alu", "kernel": "k_fused", "achieved": achieved_gops, "peak": fp64_peak_gops,
                 "unit": "G FP64 op/s", "frac": achieved_gops / fp64_peak_gops,
                 "traffic": tr.get("dram_bytes_per_launch") if tr else None,
-                "kernel_ms": kf_ms, "algorithmic_fp64_ops": ops_kf,
+                "kernel_ms": kf_ms, "algorithmic_fp64_ops": ops_kf, "executed_fp64_ops": ops_exec,
+                "fp64_pipe_frac": ops_exec / (kf_ms * 1e-3) / 1e9 / fp64_peak_gops,
                 "peak_kind": "FP64 pipe derived from unit counts and clock: 152 SMs x 2 FP64 operations/clk x "
                              f"{sm_mhz:.0f} MHz (= the 1.25 TFLOP/s FP64 FMA rate / 2)",
                 "evaluation_hbm_view": {"algorithmic_bytes": bytes_alg, "achieved_gbs": bytes_alg / eval_s / 1e9,

@@ -252,3 +252,19 @@ def test_dead_bus_matches_oracle(P, mode):
     ctx, F, v = gpu_eval(P, sys, x, mode)
     assert_tol(F, oracle.residual(sys, x, mode), "F dead bus")
     assert_tol(v, oracle.jacobian(sys, x, mode)[2], "J dead bus")
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_out_of_range_terms_match_oracle(P, mode):
+    """Two connected buses at V = 1e10 make the pair terms X, Y about 1e20, beyond the exact
+    integer bus sums' range (2^57): those buses sum in FP64; F and J still match the oracle."""
+    sys = GRIDS["grid200"]
+    n = sys.n_bus
+    x = state(sys, 3, mode == EXTENDED).copy()
+    a, b = int(sys.br_from[0]), int(sys.br_to[0])
+    x[n + a] = 1e10
+    x[n + b] = -2e10
+    ctx, F, v = gpu_eval(P, sys, x, mode)
+    assert np.max(np.abs(F)) > 2.0 ** 57
+    assert_tol(F, oracle.residual(sys, x, mode), "F out of range")
+    assert_tol(v, oracle.jacobian(sys, x, mode)[2], "J out of range")
