@@ -479,10 +479,15 @@ __device__ __forceinline__ double2 slot_gb(const View &v, const EvalArgs &a, int
   return mg.gb;
 }
 
-// One-warp CTAs that must fit on one SM (register budget of k_fused).
-#ifndef PF_FUSED_MIN_CTAS
-#define PF_FUSED_MIN_CTAS 24
-#endif
+// One-warp CTAs that must fit on one SM (the register budget of k_fused):
+// the largest count each variant compiles to without spilling -- for the
+// unmasked F + J evaluation 64 registers with one slot per fetch, 80 with
+// two; fewer CTAs for the other variants and for deeper fetches.
+template <int ITEMS, bool WF, bool WJ, bool MASKED>
+struct FusedMinCtas {
+  static constexpr bool plain = WF && WJ && !MASKED;     // the F + J evaluation without a mask
+  static constexpr int value = ITEMS == 1 ? (plain ? 32 : 28) : ITEMS == 2 ? (plain ? 24 : 20) : 16;
+};
 
 // One warp per round.  A round holds up to 32 buses with equal (or
 // adjacent) numbers of neighbours, one per lane; lane l walks its bus's
@@ -494,7 +499,7 @@ __device__ __forceinline__ double2 slot_gb(const View &v, const EvalArgs &a, int
 // group with more than one branch re-sums the coefficients of its branches in
 // service.  Slots are fetched ITEMS at a time.
 template <int ITEMS, bool WF, bool WJ, bool MASKED>
-__global__ void __launch_bounds__(32, PF_FUSED_MIN_CTAS) k_fused(View v, EvalArgs a) {
+__global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED>::value)) k_fused(View v, EvalArgs a) {
   const int lane = threadIdx.x & 31;
   for (int64_t u = blockIdx.x; u < v.n_lane_units; u += gridDim.x) {
     const int4 ur = __ldg(v.unit_rec + u);        // {instance, round, first slot, D | buses << 8}
