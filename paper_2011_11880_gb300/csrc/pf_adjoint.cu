@@ -11,9 +11,11 @@
 //               + sum_k [ v_P(k) dP_k/dV_o + v_Q(k) dQ_k/dV_o ]
 // (S_X, S_Y as in the forward kernels, from the rectangular voltages; the
 // mirror partials from the merged coefficients of the ends at k towards o),
-// plus the +-1 terms of the extended rows.  One lane per bus on the forward kernel's rounds; the
-// cotangents run in chunks whose sums stay in registers, the mirror partials
-// are recomputed per chunk.
+// plus the +-1 terms of the extended rows.  One lane per bus on the forward
+// kernel's rounds; the cotangents run in chunks whose sums stay in
+// registers; per chunk, one pass over the bus's pairs forms W = conj(E_o) E_k
+// once for the own terms and the mirror partials (12 FP64 operations per pair
+// instead of 16).
 //
 // Parameter part.  One thread per (instance, branch): the partials of the
 // four terminal powers with respect to g, b, b_c and tau, chained to r and x
@@ -176,7 +178,7 @@ __device__ __forceinline__ void write_state_grad(const View &v, const VjpArgs &a
 //   dL/dV_o     = the same with V_o,
 // the diagonal partials from the bus sums (as in the forward kernel) and the
 // mirror partials recomputed per chunk of CH cotangents, whose sums are kept
-// in registers.  Sums in a fixed order: own rows, then pairs in list order.
+// in registers.  Sums in a fixed order: pairs in list order, then own rows.
 template <int CH, bool MASKED>
 __global__ void __launch_bounds__(32) k_vjp_lane(View v, VjpArgs a) {
   const int lane = threadIdx.x & 31;
@@ -206,29 +208,56 @@ __global__ void __launch_bounds__(32) k_vjp_lane(View v, VjpArgs a) {
     const double2 Eo = rec[2 * o];
     const double2 vr = rec[2 * o + 1];             // (V_o, 1/V_o)
 
-    // bus sums over the own ends (the forward kernel's S_X, S_Y)
+    // One pass over the pairs: W = conj(E_o) E_k gives both the own terms
+    // (X - jY = y W, summed into S_X, S_Y for the diagonal partials) and the
+    // mirror partials of bus k's rows at theta_o, V_o (X' - jY' = y_m conj(W)),
+    // which meet the cotangents of k's rows at once.  The own rows'
+    // contributions are added after the pairs.
     double sx = 0.0, sy = 0.0;
     bool any_out = false;                        // masked: an end of this bus is out of service
+    double gt[CH], gvv[CH];
+#pragma unroll
+    for (int i = 0; i < CH; ++i) gt[i] = gvv[i] = 0.0;
     for (int32_t j = 0; j < D; ++j) {
       const int64_t q = q0 + 32 * j;
       const int4 meta = __ldg(v.slot_meta + q);
       if (meta.y < 0) continue;
-      double2 G = __ldg(a.sgb + q);
+      double2 G = __ldg(a.sgb + q), Gm = __ldg(a.sgbm + q);
       if (MASKED) {
         if (meta.y == 1) {
           if (!end_in(v, meta.w, outage, a.status, st_base)) {
-            G = make_double2(0.0, 0.0);
+            G = Gm = make_double2(0.0, 0.0);
             any_out = true;
           }
         } else {
           const PairCoeff pc = masked_pair(v, a, meta.w, meta.y, outage, st_base);
           G = pc.gb;
+          Gm = pc.gbm;
           any_out |= pc.any_out;
         }
       }
-      const Terms t = rotated(G, Eo, rec[2 * meta.x]);
-      sx = __dadd_rn(sx, t.X);
-      sy = __dadd_rn(sy, t.Y);
+      const int32_t k = meta.x;
+      const double2 Ek = rec[2 * k];
+      const double wr = __fma_rn(Eo.x, Ek.x, __dmul_rn(Eo.y, Ek.y));       // W = conj(E_o) E_k
+      const double wi = __fma_rn(Eo.x, Ek.y, __dmul_rn(-Eo.y, Ek.x));
+      sx = __dadd_rn(sx, __fma_rn(G.x, wr, __dmul_rn(-G.y, wi)));          // X
+      sy = __dadd_rn(sy, __fma_rn(-G.x, wi, __dmul_rn(-G.y, wr)));         // Y = -(G wi + B wr)
+      const double xm = __fma_rn(Gm.x, wr, __dmul_rn(Gm.y, wi));           // X'
+      const double ym = __fma_rn(Gm.x, wi, __dmul_rn(-Gm.y, wr));          // Y'
+      Mirror m;
+      m.pt = neg(ym);
+      m.qt = xm;
+      m.pv = __dmul_rn(-xm, vr.y);
+      m.qv = __dmul_rn(-ym, vr.y);
+      const int4 bk = __ldg(v.bus_meta + k);
+#pragma unroll
+      for (int i = 0; i < CH; ++i) {
+        if (c0 + i < a.n_cot) {
+          const double vp = cot_row(a, c0 + i, f0, bk.x), vq = cot_row(a, c0 + i, f0, bk.y);
+          gt[i] = __fma_rn(m.qt, vq, __fma_rn(m.pt, vp, gt[i]));
+          gvv[i] = __fma_rn(m.qv, vq, __fma_rn(m.pv, vp, gvv[i]));
+        }
+      }
     }
     // A^, C^: built, or re-summed over the ends in service in the built order
     double2 hat = __ldg(a.rhat + rb);
@@ -250,53 +279,18 @@ __global__ void __launch_bounds__(32) k_vjp_lane(View v, VjpArgs a) {
       hat = make_double2(__dadd_rn(ma, sh.x), __dadd_rn(mc, sh.y));
     }
     const Diag d = diag_partials(sx, sy, vr.x, vr.y, hat.x, hat.y);
-
-    {
-      double gt[CH], gvv[CH];
 #pragma unroll
-      for (int i = 0; i < CH; ++i) {
-        gt[i] = 0.0;
-        gvv[i] = 0.0;
-        if (c0 + i < a.n_cot) {
-          const double vp = cot_row(a, c0 + i, f0, bm.x), vq = cot_row(a, c0 + i, f0, bm.y);
-          gt[i] = __fma_rn(d.pt, vp, __dmul_rn(d.qt, vq));
-          gvv[i] = __fma_rn(d.pv, vp, __dmul_rn(d.qv, vq));
-        }
+    for (int i = 0; i < CH; ++i) {
+      if (c0 + i < a.n_cot) {
+        const double vp = cot_row(a, c0 + i, f0, bm.x), vq = cot_row(a, c0 + i, f0, bm.y);
+        const double t = __fma_rn(d.qt, vq, __fma_rn(d.pt, vp, gt[i]));
+        const double w = __fma_rn(d.qv, vq, __fma_rn(d.pv, vp, gvv[i]));
+        write_state_grad(v, a, inst, g, o - gb0, nb, gi, bm.x, bm.y, c0 + i, t, w);
       }
-      for (int32_t j = 0; j < D; ++j) {
-        const int64_t q = q0 + 32 * j;
-        const int4 meta = __ldg(v.slot_meta + q);
-        if (meta.y < 0) continue;
-        double2 Gm = __ldg(a.sgbm + q);
-        if (MASKED) {
-          if (meta.y == 1) {
-            if (!end_in(v, meta.w, outage, a.status, st_base)) Gm = make_double2(0.0, 0.0);
-          } else {
-            Gm = masked_pair(v, a, meta.w, meta.y, outage, st_base).gbm;
-          }
-        }
-        const int32_t k = meta.x;
-        const Mirror m = mirror_partials(Gm, Eo, vr.y, rec[2 * k]);
-        const int4 bk = __ldg(v.bus_meta + k);
-#pragma unroll
-        for (int i = 0; i < CH; ++i) {
-          if (c0 + i < a.n_cot) {
-            const double vp = cot_row(a, c0 + i, f0, bk.x), vq = cot_row(a, c0 + i, f0, bk.y);
-            gt[i] = __fma_rn(m.qt, vq, __fma_rn(m.pt, vp, gt[i]));
-            gvv[i] = __fma_rn(m.qv, vq, __fma_rn(m.pv, vp, gvv[i]));
-          }
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < CH; ++i)
-        if (c0 + i < a.n_cot) write_state_grad(v, a, inst, g, o - gb0, nb, gi, bm.x, bm.y, c0 + i, gt[i], gvv[i]);
     }
   }
 }
 
-// State part for a bus with more than 32 neighbours, one warp per bus: lane l
-// takes ends l, l + 32, ... (per end, not merged), partial sums are combined
-// by a fixed butterfly.
 template <int CH, bool MASKED>
 __global__ void __launch_bounds__(32) k_vjp_large(View v, VjpArgs a) {
   const int lane = threadIdx.x & 31;

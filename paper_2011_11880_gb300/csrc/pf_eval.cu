@@ -262,15 +262,8 @@ __device__ __forceinline__ double acc_value(const Acc128 &a) {
   // normalise the 128-bit magnitude so that its top bit is bit 63 of n
   const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
   const int sh = lz & 63;
-  unsigned long long n, rest;
-  if (lz < 64) {
-    n = sh ? (hi << sh) | (lo >> (64 - sh)) : hi;
-    rest = lo << sh;                           // bits below n (only the rounding bit matters)
-  } else {
-    n = lo << sh;
-    rest = 0ULL;
-  }
-  (void)rest;
+  // (bits below n's 11 lowest are dropped: the rounding uses bit 10 of n)
+  const unsigned long long n = lz < 64 ? (sh ? (hi << sh) | (lo >> (64 - sh)) : hi) : lo << sh;
   const int p = 127 - lz;                      // value = 2^(p - 64) * (n / 2^63)
   const unsigned long long mag =
       ((unsigned long long)(p - 64 + 1023) << 52) + ((n >> 11) & 0xfffffffffffffULL) + ((n >> 10) & 1ULL);
