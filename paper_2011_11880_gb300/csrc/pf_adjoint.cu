@@ -401,7 +401,7 @@ struct ParamArgs {
 // respect to g, b_s, b_c and tau are formed once and dotted with the
 // cotangent entries of the four rows for every cotangent.  OVR: the
 // constants come from per-call parameters instead of the build.
-constexpr int kParamChunk = 16;   // cotangents per thread of k_vjp_params
+constexpr int kParamChunk = 32;   // cotangents per thread of k_vjp_params
 
 template <bool OVR>
 __global__ void __launch_bounds__(128) k_vjp_params(View v, ParamArgs a) {
