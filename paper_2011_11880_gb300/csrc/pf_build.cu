@@ -1397,23 +1397,17 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
   PF_CUDA_TRY(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev));
 
   // (cos, sin) of i pi / 16384 for the table-driven phasor routine, evaluated in
-  // long double on the host and rounded once to double and to 2^-62.
+  // long double on the host and rounded once to 2^-62.
   {
-    std::vector<double2> tab(kSinCosTable);
     std::vector<longlong2> tabf(kSinCosTable);
     const long double pi = 3.14159265358979323846264338327950288419716939937510L;
     const long double two62 = 4611686018427387904.0L;
     for (int i = 0; i < kSinCosTable; ++i) {
       const long double a = pi * (long double)i / (long double)(kSinCosTable / 2);
-      const long double ca = cosl(a), sa = sinl(a);
-      tab[i] = make_double2((double)ca, (double)sa);
-      tabf[i] = make_longlong2(llroundl(ca * two62), llroundl(sa * two62));
+      tabf[i] = make_longlong2(llroundl(cosl(a) * two62), llroundl(sinl(a) * two62));
     }
-    double2 *d_tab;
     longlong2 *d_tabf;
-    PF_TRY(upload(c, &d_tab, tab, s));
     PF_TRY(upload(c, &d_tabf, tabf, s));
-    v.sincos_tab = d_tab;
     v.sincos_fix = d_tabf;
   }
   {

@@ -55,10 +55,11 @@ __device__ __forceinline__ double neg(double x) {
 }
 
 // ---------------------------------------------------------------------------
-// Per-bus voltage records on the integer pipe.  GB300 issues FP64 arithmetic
-// at 2 operations per clock per SM, 64-bit integer multiplies many times
-// faster, so the trigonometric routine and the reciprocal run in 64-bit fixed
-// point and leave one FP64 FMA per output.
+// Per-bus voltage records, split between the integer and the FP64 pipes.
+// GB300 issues FP64 arithmetic at 2 operations per clock per SM and 64-bit
+// integer work many times faster, on separate pipes; the trigonometric
+// routine runs in 64-bit fixed point, the products with V and the
+// reciprocal 1/V on the FP64 pipe.
 //
 // (cos t, sin t) for |t| < 32, by table-driven argument reduction (after
 // P. T. P. Tang's table-driven elementary functions):
@@ -70,61 +71,37 @@ __device__ __forceinline__ double neg(double x) {
 //   omitted terms, r^4/24 and r^5/120, are below 3.6e-18 and 7e-23; r^3/6,
 //   C_k h and S_k h from 32-bit factors, to 2^-57);
 //   cos t = C_k - (C_k h + S_k sin r),  sin t = S_k + (C_k sin r - S_k h)
-//   with the table (C_k, S_k) = (cos, sin)(k pi/16384) (32768 entries, as
-//   doubles and as 2^62-scaled integers, from long double on the host).
-// The corrections d are at most 1e-4 in magnitude and carry 2^-73 absolute
-// precision; V (C_k + d) is fma(V, C_k, V d) with the product V d formed and
-// rounded on the integer pipe.  1/V: a single-precision hardware
-// approximation y0 of 1/m (V = m 2^e, 1 <= m < 2), then one Householder step
-// of order 2 in 64-bit fixed point, y1 = y0 (1 + e + e^2) with e = 1 - m y0
-// (relative error e^3 < 2^-60), rounded to nearest.  Arguments |t| >= 32, and
-// V non-finite or of magnitude >= 2^977, use sincos() and FP64 arithmetic.
+//   with the table (C_k, S_k) = (cos, sin)(k pi/16384) as 2^62-scaled
+//   integers (32768 entries, from long double on the host); the sums are
+//   formed in 2^-62 fixed point and rounded once to double.
+// Then E = V (cos t, sin t) by two FP64 multiplies, and 1/V by the hardware's
+// approximate reciprocal r0 and one Householder step of order 2: with
+// e = 1 - V r0, 1/V = r0 (1 + e + e^2 + ...), so r1 = r0 + r0 (e + e^2) has
+// relative error e^3 (3 FP64 operations).  Arguments |t| >= 32, and V
+// non-finite or of magnitude >= 2^977, use sincos() and FP64 arithmetic.
 // ---------------------------------------------------------------------------
 constexpr unsigned long long kInvStepFix = 0xa2f9836e4e44152aULL;   // round(2^65 / pi)
 constexpr long long kStepFix = 0x6487ed5110b4611aLL;                // round(pi 2^61)
 constexpr int kSixth32 = 0x2aaaaaab;                                 // round(2^32 / 6)
 
-// v * d 2^-73 as a double, rounded to nearest (ties away), for a finite
-// normal v with 2^-600 <= |v| < 2^977 and |d| < 2^62: the 53-bit significand
-// of v times the normalised |d| in one 64 x 64 -> high-64 product.
-__device__ __forceinline__ double mul_fix73(double v, long long d) {
-  if (d == 0) return 0.0;
-  const unsigned long long vb = (unsigned long long)__double_as_longlong(v);
-  const int ev = (int)((vb >> 52) & 0x7ff);
-  const unsigned long long vm = ((vb & 0xfffffffffffffULL) | (1ULL << 52)) << 11;    // top bit 63
-  const unsigned long long a = d < 0 ? 0ULL - (unsigned long long)d : (unsigned long long)d;
+// z 2^-62 as a double, rounded to nearest (ties away from zero).
+__device__ __forceinline__ double fix62_to_double(long long z) {
+  if (z == 0) return 0.0;
+  const unsigned long long sign = (unsigned long long)z & 0x8000000000000000ULL;
+  const unsigned long long a = sign ? 0ULL - (unsigned long long)z : (unsigned long long)z;
   const int lz = __clzll((long long)a);
-  unsigned long long p = __umul64hi(vm, a << lz);                                   // in [2^62, 2^64)
-  int e = ev + 64 - lz - 73;                    // biased exponent when bit 63 of p is set
-  if (!(p >> 63)) {
-    p <<= 1;
-    e -= 1;
-  }
-  const unsigned long long sign = (vb ^ (unsigned long long)d) & 0x8000000000000000ULL;
-  const unsigned long long mag = ((unsigned long long)e << 52) + ((p >> 11) & 0xfffffffffffffULL) + ((p >> 10) & 1);
+  const unsigned long long n = a << lz;                                              // top bit 63
+  const unsigned long long mag =
+      ((unsigned long long)(1024 - lz) << 52) + ((n >> 11) & 0xfffffffffffffULL) + ((n >> 10) & 1ULL);
   return __longlong_as_double((long long)(sign | mag));
 }
 
-// 1/v for a finite normal v with 2^-600 <= |v| < 2^977.
-__device__ __forceinline__ double recip_fix(double v) {
-  const unsigned long long vb = (unsigned long long)__double_as_longlong(v);
-  const int ev = (int)((vb >> 52) & 0x7ff);
-  const unsigned long long frac = vb & 0xfffffffffffffULL;
-  const unsigned long long M = (frac | (1ULL << 52)) << 10;                         // m 2^62
-  float y0f;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0f) : "f"(__uint_as_float(0x3f800000u | (unsigned)(frac >> 29))));
-  const unsigned u = __float_as_uint(y0f);                                           // y0 in (0.5, 1]
-  const int ef = (int)((u >> 23) & 0xff) - 127;                                      // -1 or 0
-  const long long Y = (long long)((unsigned long long)(0x800000u | (u & 0x7fffffu)) << (39 + ef));   // y0 2^62
-  const long long E = (long long)(1ULL << 60) - (long long)__umul64hi(M, (unsigned long long)Y);    // e 2^60
-  const long long Es = E >> 8;                                                       // |e| < 2^-21: 32 bits
-  const long long T = E + ((Es * Es) >> 44);                                         // (e + e^2) 2^60
-  const unsigned long long Y1 = (unsigned long long)(Y + (__mul64hi(Y, T << 20) >> 16));            // y1 2^62
-  const int lz = __clzll((long long)Y1);
-  const unsigned long long n = Y1 << lz;
-  const unsigned long long mag =
-      ((unsigned long long)(2047 - ev - lz) << 52) + ((n >> 11) & 0xfffffffffffffULL) + ((n >> 10) & 1);
-  return __longlong_as_double((long long)((vb & 0x8000000000000000ULL) | mag));
+// 1/s for a finite normal s with 2^-600 <= |s| < 2^977 (see above).
+__device__ __forceinline__ double recip(double s) {
+  double r0;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r0) : "d"(s));
+  const double e = __fma_rn(-s, r0, 1.0);
+  return __fma_rn(r0, __fma_rn(e, e, e), r0);
 }
 
 // (V cos t, V sin t) and 1/V of a per-bus record; sv is V after the dead-bus
@@ -134,8 +111,7 @@ struct RectV {
   double rv;
 };
 
-__device__ __forceinline__ RectV rect_voltage(double t, double sv, const double2 *__restrict__ tab,
-                                              const longlong2 *__restrict__ tabf) {
+__device__ __forceinline__ RectV rect_voltage(double t, double sv, const longlong2 *__restrict__ tabf) {
   RectV o;
   if ((__double2hiint(t) & 0x7fffffff) >= 0x40400000 || (__double2hiint(sv) & 0x7ff00000) >= 0x7d000000) {
     double sn, cs;
@@ -162,16 +138,16 @@ __device__ __forceinline__ RectV rect_voltage(double t, double sv, const double2
   const long long SR = R - ((long long)r3 << 10);                                    // sin r 2^75
   const long long H = R2 >> 12;                                                      // r^2/2 2^75
   const int idx = (int)(k & (kSinCosTable - 1));
-  const double2 T = __ldg(tab + idx);
   const longlong2 Tf = __ldg(tabf + idx);                                            // (C, S) 2^62
   // h < 2^-27.7: C h and S h from 32-bit factors (C 2^30, h 2^58) to 2^-57
   const int h32 = (int)(H >> 17), c32 = (int)(Tf.x >> 32), s32 = (int)(Tf.y >> 32);
   const long long dc = -(((long long)c32 * h32) >> 15) - __mul64hi(Tf.y, SR);          // 2^73
   const long long ds = __mul64hi(Tf.x, SR) - (((long long)s32 * h32) >> 15);
-  const double ex = __fma_rn(sv, T.x, mul_fix73(sv, dc));
-  const double ey = __fma_rn(sv, T.y, mul_fix73(sv, ds));
-  o.E = make_double2(ex, (long long)tb < 0 ? neg(ey) : ey);                         // sin is odd
-  o.rv = recip_fix(sv);
+  const double ct = fix62_to_double(Tf.x + (dc >> 11));                              // cos t
+  const double st = fix62_to_double(Tf.y + (ds >> 11));                              // sin |t|
+  const double ey = __dmul_rn(sv, st);
+  o.E = make_double2(__dmul_rn(sv, ct), (long long)tb < 0 ? neg(ey) : ey);          // sin is odd
+  o.rv = recip(sv);
   return o;
 }
 
@@ -205,7 +181,7 @@ __global__ void __launch_bounds__(256) k_phasor(View v, const double *__restrict
     const double th = __ldg(xi + lb);
     const double vm = __ldg(xi + v.grid_nbus[v.inst_grid[inst]] + lb);
     const double sv = (__double2hiint(vm) & 0x7ff00000) < 0x20b00000 ? kDeadV : vm;   // |V| < 2^-500
-    const RectV r = rect_voltage(th, sv, v.sincos_tab, v.sincos_fix);
+    const RectV r = rect_voltage(th, sv, v.sincos_fix);
     v.phasor[2 * q] = r.E;
     v.phasor[2 * q + 1] = make_double2(vm, r.rv);
   }
@@ -745,11 +721,11 @@ void built_coefficients(const View &v, EvalArgs &a) {
   a.rhat = v.rbus_hat;
 }
 
-__global__ void k_sincos(const double *__restrict__ t, int64_t n, const double2 *__restrict__ tab,
-                         const longlong2 *__restrict__ tabf, double *__restrict__ c, double *__restrict__ sn) {
+__global__ void k_sincos(const double *__restrict__ t, int64_t n, const longlong2 *__restrict__ tabf,
+                         double *__restrict__ c, double *__restrict__ sn) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const RectV r = rect_voltage(t[i], 1.0, tab, tabf);
+  const RectV r = rect_voltage(t[i], 1.0, tabf);
   c[i] = r.E.x;
   sn[i] = r.E.y;
 }
@@ -849,7 +825,7 @@ int launch_eval_scratch(Ctx &c, const double *x, double *F, double *vals, double
 int launch_sincos(Ctx &c, const double *t, int64_t n, double *cs, double *sn, cudaStream_t s) {
   if (n <= 0) return PF_OK;
   if (!t || !cs || !sn) return fail(PF_ERR_INVALID, "NULL argument");
-  k_sincos<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t, n, c.v.sincos_tab, c.v.sincos_fix, cs, sn);
+  k_sincos<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t, n, c.v.sincos_fix, cs, sn);
   PF_CUDA_TRY(cudaGetLastError());
   return PF_OK;
 }

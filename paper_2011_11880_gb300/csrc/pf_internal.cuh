@@ -129,8 +129,7 @@ struct View {
   // scratch
   double2 *phasor;                            // [2 n_bus_inst]: (cos theta, sin theta), (V, 0) per bus
   int32_t *dev_error;
-  const double2 *sincos_tab;                  // [kSinCosTable] (cos, sin)(i pi / 16384)
-  const longlong2 *sincos_fix;                // [kSinCosTable] the same, times 2^62, rounded to integers
+  const longlong2 *sincos_fix;                // [kSinCosTable] (cos, sin)(i pi / 16384) times 2^62, rounded
 };
 
 struct Ctx {
