@@ -166,6 +166,9 @@ typedef struct pf_tuning {
   int32_t tile_inc;              /* 32, 64, 96 or 128: each lane fetches tile_inc / 32 pairs of
                                     connected buses ahead (the chunk of a bus with > 32 neighbours) */
   int32_t ctas_per_sm;           /* persistent CTAs per SM; 0 = one CTA for every round */
+  int32_t split_rounds;          /* 1: a warp takes half a round, two lanes per bus (each every
+                                    other pair; twice the warps, for contexts that fill less than
+                                    a wave); 0: one lane per bus.  Results are bit-identical. */
 } pf_tuning;
 
 /* ---- build (once) -------------------------------------------------------- */

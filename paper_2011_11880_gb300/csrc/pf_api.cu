@@ -320,10 +320,12 @@ int pf_set_tuning(pf_ctx *ctx, const pf_tuning *t, void *stream) {
   if (t->tile_inc < pf::kMinTileInc || t->tile_inc > pf::kMaxTileInc || t->tile_inc % 32 != 0)
     return fail(PF_ERR_INVALID, "tile_inc must be 32, 64, 96 or 128");
   if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return fail(PF_ERR_INVALID, "ctas_per_sm must be in [0, 32]");
+  if (t->split_rounds != 0 && t->split_rounds != 1) return fail(PF_ERR_INVALID, "split_rounds must be 0 or 1");
   cudaStream_t s = as_stream(stream);
   PF_CUDA_TRY(cudaStreamSynchronize(s));
   ctx->c.tuning.tile_inc = t->tile_inc;
   ctx->c.tuning.ctas_per_sm = t->ctas_per_sm;
+  ctx->c.tuning.split_rounds = t->split_rounds;
   return PF_OK;
 }
 
@@ -338,27 +340,24 @@ int pf_autotune(pf_ctx *ctx, const double *x, double *F, double *vals, void *str
   PF_CUDA_TRY(cudaEventCreate(&e0));
   PF_CUDA_TRY(cudaEventCreate(&e1));
   int rc = PF_OK;
-  for (int ti : tiles) {
-    for (int ca : ctas) {
-      pf_tuning t{ti, ca};
-      rc = pf_set_tuning(ctx, &t, stream);
-      if (rc) break;
-      for (int w = 0; w < 2 && !rc; ++w) rc = pf::launch_eval(ctx->c, x, nullptr, F, vals, s);
-      if (rc) break;
-      const int reps = 5;
-      cudaEventRecord(e0, s);
-      for (int r = 0; r < reps && !rc; ++r) rc = pf::launch_eval(ctx->c, x, nullptr, F, vals, s);
-      cudaEventRecord(e1, s);
-      if (rc) break;
-      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(PF_ERR_CUDA, "autotune timing"); break; }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = t;
-      }
-    }
+  for (int k = 0; k < 2 * 4 * 3 && !rc; ++k) {       // split rounds x tiles x CTAs per SM
+    const pf_tuning t{tiles[(k / 3) % 4], ctas[k % 3], k / 12};
+    rc = pf_set_tuning(ctx, &t, stream);
     if (rc) break;
+    for (int w = 0; w < 2 && !rc; ++w) rc = pf::launch_eval(ctx->c, x, nullptr, F, vals, s);
+    if (rc) break;
+    const int reps = 5;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && !rc; ++r) rc = pf::launch_eval(ctx->c, x, nullptr, F, vals, s);
+    cudaEventRecord(e1, s);
+    if (rc) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(PF_ERR_CUDA, "autotune timing"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

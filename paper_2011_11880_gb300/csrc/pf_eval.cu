@@ -227,6 +227,13 @@ __device__ __forceinline__ void acc_add(Acc128 &a, double x, bool &ok) {
   }
 }
 
+// Adds another accumulator's value (lo, hi).
+__device__ __forceinline__ void acc_merge(Acc128 &a, unsigned long long lo, long long hi) {
+  const unsigned long long nlo = a.lo + lo;
+  a.hi = (long long)((unsigned long long)a.hi + (unsigned long long)hi + (nlo < lo ? 1ULL : 0ULL));
+  a.lo = nlo;
+}
+
 __device__ __forceinline__ double acc_value(const Acc128 &a) {
   unsigned long long hi = (unsigned long long)a.hi, lo = a.lo;
   const unsigned long long sign = hi & 0x8000000000000000ULL;
@@ -261,6 +268,7 @@ struct EvalArgs {
   const uint8_t *status;   // per-instance-branch mask or nullptr
   const uint8_t *gen_mode; // extended, per instance-generator: != 0 holds Q_g at gen_qlim, or nullptr
   const double *gen_qlim;
+  int split;               // 1: half a round per warp, two lanes per bus
 };
 
 // X and Y of one branch end (own voltage Eo, other voltage Ek, rectangular).
@@ -470,8 +478,15 @@ struct FusedMinCtas {
 template <int ITEMS, bool WF, bool WJ, bool MASKED>
 __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED>::value)) k_fused(View v, EvalArgs a) {
   const int lane = threadIdx.x & 31;
-  for (int64_t u = blockIdx.x; u < v.n_lane_units; u += gridDim.x) {
-    const int4 ur = __ldg(v.unit_rec + u);        // {instance, round, first slot, D | buses << 8}
+  // split rounds: a warp takes half a round (16 buses), two lanes per bus,
+  // lane l the pairs l >> 4, (l >> 4) + 2, ... of bus l & 15
+  const int split = a.split;
+  const int64_t n_units = v.n_lane_units << split;
+  const int bl0 = split ? (lane & 15) : lane;    // bus lane within the (half) round
+  const int par = split ? (lane >> 4) : 0;       // this lane's first pair
+  const int step = 1 + split;                    // and its stride
+  for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
+    const int4 ur = __ldg(v.unit_rec + (u >> split));   // {instance, round, first slot, D | buses << 8}
     const int inst = ur.x;
     const int64_t r = ur.y;
     const int g = __ldg(v.inst_grid + inst);
@@ -483,13 +498,15 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED>::valu
     const int64_t st_base = MASKED ? v.inst_br_off[inst] - v.grid_br_off[g] : 0;
 
     // this lane's bus: records in round order, fetched before the wait
-    const int64_t rb = 32 * r + lane;
-    const bool owner = lane < (ur.w >> 8);
+    const int bl = bl0 + (split ? 16 * (int)(u & 1) : 0);
+    const int64_t rb = 32 * r + bl;
+    const bool owner = bl < (ur.w >> 8);
+    const bool lead = owner && par == 0;         // the lane that finishes the bus
     int32_t o = 0;
     int4 bm = make_int4(-1, -1, -1, -1), bm2 = make_int4(-1, -1, 0, -1);
     double2 hat = make_double2(0.0, 0.0), inj = make_double2(0.0, 0.0);
-    if (owner) {
-      o = __ldg(v.rbus + rb);
+    if (owner) o = __ldg(v.rbus + rb);
+    if (lead) {
       bm = __ldg(v.rbus_meta + rb);
       bm2 = __ldg(v.rbus_meta2 + rb);
       hat = __ldg(a.rhat + rb);
@@ -500,22 +517,23 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED>::valu
     bool any_out = false;                        // masked: an end of this bus is out of service
     double2 Eo = make_double2(0.0, 0.0), vr = make_double2(0.0, 0.0);
     const int32_t D = ur.w & 0xff;
-    const int64_t q0 = (int64_t)ur.z + lane;
+    const int64_t q0 = (int64_t)ur.z + bl;
 
-    for (int32_t j0 = 0; j0 < D; j0 += ITEMS) {
+    for (int32_t j0 = par; j0 < D; j0 += ITEMS * step) {
       int4 meta[ITEMS], pos[ITEMS];
       double2 G[ITEMS];
 #pragma unroll
       for (int it = 0; it < ITEMS; ++it) {
         meta[it] = make_int4(0, -1, 0, 0);
-        if (j0 + it < D) {
-          const int64_t q = q0 + 32 * (j0 + it);
+        const int32_t j = j0 + it * step;
+        if (j < D) {
+          const int64_t q = q0 + 32 * j;
           meta[it] = __ldg(v.slot_meta + q);
           if (WJ) pos[it] = __ldg(v.slot_pos + q);
           G[it] = __ldg(a.sgb + q);
         }
       }
-      if (j0 == 0) {
+      if (j0 == par) {
         // the per-bus records come from k_phasor (programmatic dependent launch)
         cudaGridDependencySynchronize();
         if (owner) {
@@ -536,11 +554,22 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED>::valu
         if (WJ) write_pair(vi, pos[it], tm.X, tm.Y, rec[2 * k + 1].y);
       }
     }
-    if (D == 0) {                                // a round of isolated buses only
+    if (D <= par) {                              // no pair on this lane (a round of isolated buses)
       cudaGridDependencySynchronize();
-      if (owner) vr = rec[2 * o + 1];
+      if (owner) {
+        Eo = rec[2 * o];
+        vr = rec[2 * o + 1];
+      }
     }
-    if (owner) {
+    if (split) {
+      // the second lane of each bus hands its partial sums to the first: the
+      // sums are exact, so the result is the unsplit one, bit for bit
+      acc_merge(ax, __shfl_down_sync(0xffffffffu, ax.lo, 16), __shfl_down_sync(0xffffffffu, ax.hi, 16));
+      acc_merge(ay, __shfl_down_sync(0xffffffffu, ay.lo, 16), __shfl_down_sync(0xffffffffu, ay.hi, 16));
+      exact = __shfl_down_sync(0xffffffffu, (int)exact, 16) != 0 && exact;
+      any_out = __shfl_down_sync(0xffffffffu, (int)any_out, 16) != 0 || any_out;
+    }
+    if (lead) {
       // S_X, S_Y: the exact sums, rounded once; in FP64, in list order, when a
       // term is out of the accumulator's range or the bus is dead (its terms
       // carry the 2^-600 factor that 1/V divides out again)
@@ -665,7 +694,7 @@ __global__ void __launch_bounds__(32) k_fused_large(View v, EvalArgs a) {
 template <int ITEMS, bool WF, bool WJ, bool MASKED>
 int launch_fused_t(const View &v, int num_sms, const pf_tuning &t, const EvalArgs &a, cudaStream_t s) {
   if (v.n_lane_units > 0) {
-    int64_t grid = v.n_lane_units;
+    int64_t grid = v.n_lane_units << a.split;
     if (t.ctas_per_sm > 0) grid = std::min<int64_t>(grid, (int64_t)t.ctas_per_sm * num_sms);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
@@ -755,6 +784,7 @@ int launch_eval_stages(Ctx &c, int stages, const double *x, const pf_overrides *
   a.x = x;
   a.F = F;
   a.vals = vals;
+  a.split = c.tuning.split_rounds ? 1 : 0;
   built_coefficients(c.v, a);
   if (ov) {
     a.p_inj = ov->p_inj;
@@ -799,6 +829,7 @@ int launch_eval_range(Ctx &c, int i0, int i1, const double *x, double *F, double
   a.x = x;
   a.F = F;
   a.vals = vals;
+  a.split = c.tuning.split_rounds ? 1 : 0;
   built_coefficients(c.v, a);
   PF_TRY(launch_phasor(v, c.num_sms, x, s));
   return launch_fused(v, c.num_sms, c.tuning, a, c.any_outage, s);
@@ -816,6 +847,7 @@ int launch_eval_scratch(Ctx &c, const double *x, double *F, double *vals, double
   a.x = x;
   a.F = F;
   a.vals = vals;
+  a.split = c.tuning.split_rounds ? 1 : 0;
   built_coefficients(c.v, a);
   PF_TRY(launch_phasor(v, c.num_sms, x, s));
   return launch_fused(v, c.num_sms, c.tuning, a, c.any_outage, s);

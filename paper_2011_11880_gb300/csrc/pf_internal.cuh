@@ -135,7 +135,7 @@ struct View {
 struct Ctx {
   View v{};
   int num_sms = kNumSMsDefault;
-  pf_tuning tuning{64, 0};
+  pf_tuning tuning{64, 0, 0};
   int max_degree = 0, max_group = 0;
   int64_t n_x = 0, n_f = 0, nnz = 0, n_branch_inst = 0;
 

@@ -119,11 +119,14 @@ def test_deterministic_across_runs_and_tunings(P, name):
     for _ in range(3):
         F1, v1 = ctx.residual_jacobian(x)
         assert torch.equal(F0, F1) and torch.equal(v0, v1)
-    for tile in (32, 64, 96, 128):
-        for ctas in (0, 1, 3, 16):
-            ctx.set_tuning(tile, ctas)
-            F1, v1 = ctx.residual_jacobian(x)
-            assert torch.equal(F0, F1) and torch.equal(v0, v1), (tile, ctas)
+    for split in (0, 1):
+        for tile in (32, 64, 96, 128):
+            for ctas in (0, 1, 3, 16):
+                ctx.set_tuning(tile, ctas, split)
+                F1, v1 = ctx.residual_jacobian(x)
+                assert torch.equal(F0, F1) and torch.equal(v0, v1), (tile, ctas, split)
+                F2 = ctx.residual(x)                   # F alone takes the same sums
+                assert torch.equal(F0, F2), (tile, ctas, split)
     ctx.check_device()
 
 
