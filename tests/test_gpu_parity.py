@@ -271,3 +271,30 @@ def test_out_of_range_terms_match_oracle(P, mode):
     assert np.max(np.abs(F)) > 2.0 ** 57
     assert_tol(F, oracle.residual(sys, x, mode), "F out of range")
     assert_tol(v, oracle.jacobian(sys, x, mode)[2], "J out of range")
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_split_rounds_bit_identical_under_masks(P, mode):
+    """Two lanes per bus (split rounds) give the one-lane results bit for bit: a batch with
+    outage instances, a per-call status mask, and (extended) generators held at limits."""
+    grids = [GRIDS["grid200"], GRIDS["grid30"], GRIDS["edge300"]]
+    inst = [(0, -1), (0, 7), (1, 3), (2, -1), (2, 11), (1, -1)]
+    ctx = P.Context(grids, MNAME[mode], instances=inst)
+    x = torch.from_numpy(np.concatenate([state(grids[g], k + 1, mode == EXTENDED)
+                                         for k, (g, _) in enumerate(inst)])).cuda()
+    rng = np.random.default_rng(8)
+    status = torch.from_numpy((rng.random(ctx.dims.n_branch_inst) > 0.05).astype(np.uint8)).cuda()
+    kw = {"status": status}
+    if mode == EXTENDED:
+        kw["gen_mode"] = torch.from_numpy(rng.integers(0, 3, ctx.dims.n_gen_inst).astype(np.uint8)).cuda()
+        kw["gen_qlim"] = torch.from_numpy(rng.uniform(-0.5, 0.8, ctx.dims.n_gen_inst)).cuda()
+    outs = []
+    for split in (0, 1):
+        for tile in (32, 128):
+            ctx.set_tuning(tile, 0, split)
+            outs.append(ctx.eval(x, ctx.empty_f(), ctx.empty_vals(), **kw))
+            outs.append(ctx.residual_jacobian(x))
+    for k in range(2, len(outs), 2):
+        assert torch.equal(outs[0][0], outs[k][0]) and torch.equal(outs[0][1], outs[k][1]), k
+        assert torch.equal(outs[1][0], outs[k + 1][0]) and torch.equal(outs[1][1], outs[k + 1][1]), k
+    ctx.check_device()
