@@ -35,9 +35,12 @@
  *     ascending columns, parallel branches merged, the four diagonal
  *     entries of a bus always present when their row and column exist,
  *     out-of-service / masked branches kept as explicit zeros.
- *   - Results are deterministic: every F row and J value is a sum in a fixed
- *     order (no floating-point atomics), identical run to run and for every
- *     tuning choice.
+ *   - Results are deterministic (no floating-point atomics): a bus's sums
+ *     over its branch ends are exact integer sums rounded once (or, for a
+ *     bus with more than 32 neighbours or an out-of-range term, FP64 sums in
+ *     a fixed order), every other sum runs in a fixed order, so F and J are
+ *     identical run to run, for every tuning choice, and between a batch and
+ *     the single-instance evaluation of each of its instances.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Evaluation calls are asynchronous on that stream, allocate
  *     nothing and may be captured in a CUDA graph; device buffers passed to
@@ -236,7 +239,8 @@ PF_API int pf_eval(pf_ctx *ctx, const double *x, const pf_overrides *ov, double 
             void *stream);
 
 /* The two kernels of an evaluation, one at a time: PF_STAGE_PHASOR computes
- * (cos theta, sin theta) of every bus into the context's scratch;
+ * the per-bus records (the bus voltage V (cos theta, sin theta), V and 1/V,
+ * as pf_voltage_records returns them) into the context's scratch;
  * PF_STAGE_FUSED runs the fused F / J kernel, reading that scratch (a
  * PF_STAGE_PHASOR call at the same x must precede it on the stream).
  * pf_eval runs both.  For timing each kernel and for overlapping the stages
