@@ -390,6 +390,11 @@ PF_API int pf_sincos(pf_ctx *ctx, const double *theta, int64_t n, double *cos_ou
 PF_API int pf_voltage_records(pf_ctx *ctx, const double *x, double *rec, void *stream);
 
 /* ---- errors --------------------------------------------------------------------- */
+/* Test hook: with the environment variable PF_FAIL_ALLOC=<n> set when
+ * pf_build / pf_build_batch starts, the n-th device allocation of that build
+ * (counted from 0) fails without allocating: the build returns PF_ERR_OOM and
+ * frees everything it had allocated.  For exercising the error path without a
+ * GPU fault; unset in normal use. */
 
 PF_API const char *pf_error_string(int32_t code);
 PF_API const char *pf_last_error(void);

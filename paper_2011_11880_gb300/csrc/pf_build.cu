@@ -31,6 +31,7 @@ struct TempList {
   template <class T>
   int alloc(T **out, size_t n) {
     if (n == 0) n = 1;
+    if (alloc_fault()) return fail(PF_ERR_OOM, "device allocation failed (PF_FAIL_ALLOC, build scratch)");
     void *q = nullptr;
     cudaError_t e = cudaMalloc(&q, n * sizeof(T));
     if (e != cudaSuccess)
@@ -941,6 +942,7 @@ int permute_overrides(Ctx &c, cudaStream_t s) {
 
 int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance *inst, int n_inst,
                   int formulation, cudaStream_t s) {
+  const BuildAllocScope fault_scope;
   if (formulation != PF_REDUCED && formulation != PF_EXTENDED)
     return fail(PF_ERR_INVALID, "formulation must be PF_REDUCED or PF_EXTENDED");
   if (n_grids <= 0 || !grids) return fail(PF_ERR_INVALID, "no grids");

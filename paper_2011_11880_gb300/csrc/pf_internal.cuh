@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
+#include <cstdlib>
 #include <vector>
 
 #include "../../include/pf.h"
@@ -178,10 +179,33 @@ struct Ctx {
   std::vector<void *> allocations;
 };
 
+// Host-side fault injection for tests: with PF_FAIL_ALLOC=<n> in the
+// environment when a build starts, the n-th device allocation of that build
+// (counted from 0) reports failure without allocating, so that the error path
+// (PF_ERR_OOM, everything allocated so far freed) can be exercised without any
+// GPU fault.  BuildAllocScope reads the variable for the span of one build;
+// alloc_fault() counts.
+inline thread_local long long g_alloc_count = 0, g_alloc_fail_at = -1;
+
+inline void begin_build_allocs() {
+  const char *e = std::getenv("PF_FAIL_ALLOC");
+  g_alloc_count = 0;
+  g_alloc_fail_at = (e && *e) ? std::atoll(e) : -1;
+}
+
+inline bool alloc_fault() { return g_alloc_fail_at >= 0 && g_alloc_count++ == g_alloc_fail_at; }
+
+// Arms the hook for one build and disarms it when the build returns.
+struct BuildAllocScope {
+  BuildAllocScope() { begin_build_allocs(); }
+  ~BuildAllocScope() { g_alloc_fail_at = -1; }
+};
+
 template <class T>
 int dev_alloc(Ctx &c, T **p, size_t n, std::vector<void *> *list = nullptr) {
   *p = nullptr;
   if (n == 0) n = 1;
+  if (alloc_fault()) return fail(PF_ERR_OOM, "device allocation failed (PF_FAIL_ALLOC)");
   void *q = nullptr;
   cudaError_t e = cudaMalloc(&q, n * sizeof(T));
   if (e != cudaSuccess)
