@@ -546,7 +546,7 @@ int launch_vjp(Ctx &c, const double *x, const pf_overrides *ov, const double *v,
   if (n_cot <= 0) return fail(PF_ERR_INVALID, "n_cot must be positive");
   const int tb = 256;
   const int64_t cap_blocks = (int64_t)c.num_sms * 16;
-  // (cos, sin) and V of every bus: the forward kernels' phasor records
+  // E = V (cos, sin), V and 1/V of every bus: the forward kernels' per-bus records
   PF_TRY(launch_phasor(c.v, c.num_sms, x, s));
   VjpArgs a{};
   a.x = x; a.v = v; a.n_cot = n_cot; a.n_f = c.n_f; a.n_x = c.n_x;

@@ -32,7 +32,9 @@
 // bus sums in registers, and finally writes the bus's F rows and diagonal J
 // entries.  Because the buses of a round have the same number of pairs,
 // nearly every lane does useful FP64 work at every step.  A bus with more
-// than 32 neighbours is evaluated by a whole warp in a second kernel.
+// than 32 neighbours is evaluated by a whole warp in a second kernel.  With
+// split rounds (a tuning choice) a warp takes half a round, two lanes per bus
+// taking alternate pairs, their exact partial sums merged by a shuffle.
 //
 // Determinism: every operation is an explicitly rounded intrinsic, the bus
 // sums of a bus with up to 32 neighbours are exact (so independent of the

@@ -128,7 +128,7 @@ struct View {
   const int64_t *inst_gen_off;                // extended: generators of earlier instances
 
   // scratch
-  double2 *phasor;                            // [2 n_bus_inst]: (cos theta, sin theta), (V, 0) per bus
+  double2 *phasor;                            // [2 n_bus_inst]: (V cos theta, V sin theta), (V, 1/V) per bus
   int32_t *dev_error;
   const longlong2 *sincos_fix;                // [kSinCosTable] (cos, sin)(i pi / 16384) times 2^62, rounded
 };
