@@ -35,7 +35,7 @@ N_STATES = 48
 LEAD_BYTES = 1 << 30
 METRIC = "F+J evals/s on 70k-bus grid (batched; single-instance reported beside)"
 WORKLOAD = ("70k-bus seeded synthetic grid (70,000 buses, 88,000 branches, 7,000 PV, 50,000 PQ loads, "
-            "3,000 shunts, 12% transformers), reduced polar formulation, FP64, 48 perturbed states")
+            "3,000 shunts, 12% transformers), reduced polar formulation, FP64, {} perturbed states")
 
 
 def parse():
@@ -50,6 +50,8 @@ def parse():
                    help="only run warmup + steps evaluations of the workload (for ncu), no timing")
     p.add_argument("--tile", type=int, default=0, help="profile mode: tile_inc (0: autotune)")
     p.add_argument("--ctas", type=int, default=0, help="profile mode: CTAs per SM")
+    p.add_argument("--states", type=int, default=48,
+                   help="70k workload: states evaluated per batched launch (48 = the headline configuration)")
     p.add_argument("--workload", default="70k", choices=["70k", "contingency", "adjoint", "mixed", "newton"],
                    help="70k: the headline line (default); the others measure the batched-contingency, "
                         "adjoint and mixed-scenario workloads on one GPU and print their own line")
@@ -174,6 +176,15 @@ def algorithmic_bytes(d, n_pv, n_load, n_shunt):
     return read + write
 
 
+def l2_note(step_bytes):
+    """How the timed region relates to the 129 MB L2 (the timing rule: inputs
+    larger than L2, or a flush between steps)."""
+    if step_bytes > 129e6:
+        return f"inputs larger than L2: every state's own x, F and J ({step_bytes / 1e6:.0f} MB) per step, no flush"
+    return (f"x, F and J of the step ({step_bytes / 1e6:.0f} MB) fit in L2, so steps after the first may hit it: "
+            "a batch-size sweep point, not the headline configuration")
+
+
 def fused_fp64_ops(d, n_pairs, pattern, executed=False):
     """Algorithmic operations (an FMA, a multiply or an add each count one) of
     one instance's F and J in the rectangular-voltage form k_fused evaluates,
@@ -241,7 +252,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "evals/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / rate,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "sample": f"{n} oracle F+J evaluations"},
+        "data": "synthetic", "config": {"workload": WORKLOAD.format(N_STATES), "sample": f"{n} oracle F+J evaluations"},
         "e2e": {"value": rate, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "cpu_baseline": {"value": rate, "unit": "evals/s", "cores": 1, "kind": "oracle",
                          "sample": f"{n} F+J evaluations of the 70k grid ({el:.1f} s, numpy FP64, "
@@ -256,7 +267,11 @@ def run_reference(args, rank, world):
 # --------------------------------------------------------------------------
 
 def main():
+    global N_STATES
     args = parse()
+    if args.states < 1:
+        raise SystemExit("--states must be positive")
+    N_STATES = args.states
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -295,7 +310,7 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     lead = torch.empty(LEAD_BYTES // 4, dtype=torch.float32, device=dev)
 
-    # ---- batched: the 48 states as 48 instances of the grid, one launch per step ----
+    # ---- batched: the states as instances of the grid, one launch per step ----
     ctx = Context([sys_], "reduced", instances=[(0, -1)] * N_STATES)
     d = ctx.dims
     one = Context(sys_, "reduced")            # single-instance context for the comparison
@@ -434,12 +449,12 @@ def main():
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_f_per_state": d1.n_f, "nnz_per_state": d1.nnz,
+        "config": {"workload": WORKLOAD.format(N_STATES), "n_f_per_state": d1.n_f, "nnz_per_state": d1.nnz,
                    "step": f"one batched launch over {N_STATES} states (instances of the grid)",
-                   "l2": "inputs larger than L2: 48 states with their own x, F and J (444 MB) per step, no flush",
+                   "l2": l2_note(N_STATES * 8 * (d1.n_x + d1.n_f + d1.nnz)),
                    "tuning": tuning, "timed_region_wall_s": wall, "parallelism": f"replicas x{world}"},
         "single_instance": {"value": single_rate, "unit": "evals/s", "tuning": one_tuning,
-                            "how": "one evaluation per launch pair (k_phasor, k_fused), 48 states with their "
+                            "how": f"one evaluation per launch pair (k_phasor, k_fused), {N_STATES} states with their "
                                    "own buffers evaluated one after the other from one CUDA graph"},
         "batched_over_single": value / world / single_rate,
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": 8 * d.n_x,
