@@ -207,6 +207,12 @@ def fused_fp64_ops(d, n_pairs, pattern, executed=False):
     return (8 if executed else 10) * n_pairs + n_v + n_vdiag + 5 * n
 
 
+def launches_per_eval(ctx):
+    """Kernels one evaluation of the context launches: k_phasor and k_fused, and
+    k_fused_large where a bus has more than 32 neighbours."""
+    return 2 + (1 if ctx.dims.max_degree > 32 else 0)
+
+
 def source_hash():
     """Hash of the code (comments and blank space removed) of the sources that
     decide k_fused's memory traffic: the kernel and the data layout."""
@@ -433,6 +439,8 @@ def main():
                 "traffic": tr.get("dram_bytes_per_launch") if tr else None,
                 "kernel_ms": kf_ms, "algorithmic_fp64_ops": ops_kf, "executed_fp64_ops": ops_exec,
                 "fp64_pipe_frac": ops_exec / (kf_ms * 1e-3) / 1e9 / fp64_peak_gops,
+                # the whole step: k_fused's executed operations plus k_phasor's 5 per bus, over the step time
+                "step_fp64_pipe_frac": (ops_exec + 5 * d.n_bus_inst) / eval_s / 1e9 / fp64_peak_gops,
                 "peak_kind": "FP64 pipe derived from unit counts and clock: 152 SMs x 2 FP64 operations/clk x "
                              f"{sm_mhz:.0f} MHz (= the 1.25 TFLOP/s FP64 FMA rate / 2)",
                 "evaluation_hbm_view": {"algorithmic_bytes": bytes_alg, "achieved_gbs": bytes_alg / eval_s / 1e9,
@@ -459,7 +467,7 @@ def main():
         "batched_over_single": value / world / single_rate,
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": 8 * d.n_x,
                 "d2h_bytes_per_step": 8 * (d.n_f + d.nnz), "steps": E},
-        "gpu_launches": 2 * K,
+        "gpu_launches": launches_per_eval(ctx) * K,
         "roofline": roofline,
         "clocks": clocks,
         "cpu_baseline": cpu,
@@ -711,6 +719,8 @@ def run_workload(args):
                     "cpu_baseline": {"value": m / el, "unit": "iterations/s", "cores": 1, "kind": "oracle",
                                      "sample": f"{m} instance iterations in {el:.1f} s"}})
     per_step = {"contingency": 2, "adjoint": 5, "mixed": 5, "newton": 0}[args.workload]
+    if args.workload in ("contingency", "mixed"):
+        per_step += launches_per_eval(ctx) - 2
     out["breakdown"] = breakdown
     out["clocks"] = clocks
     out["gpu_launches"] = per_step * K

@@ -168,7 +168,9 @@ typedef struct pf_grads {
 typedef struct pf_tuning {
   int32_t tile_inc;              /* 32, 64, 96 or 128: each lane fetches tile_inc / 32 pairs of
                                     connected buses ahead (the chunk of a bus with > 32 neighbours) */
-  int32_t ctas_per_sm;           /* persistent CTAs per SM; 0 = one CTA for every round */
+  int32_t ctas_per_sm;           /* persistent CTAs per SM of the fused kernels and the adjoint
+                                    state kernel (the fused kernel's warps then claim rounds
+                                    from a counter); 0 = one CTA for every round */
   int32_t split_rounds;          /* 1: a warp takes half a round, two lanes per bus (each every
                                     other pair; twice the warps, for contexts that fill less than
                                     a wave); 0: one lane per bus.  Results are bit-identical. */
@@ -363,8 +365,10 @@ PF_API int pf_newton_update(pf_ctx *ctx, double *x, const double *dx, void *stre
 
 PF_API int pf_get_tuning(const pf_ctx *ctx, pf_tuning *t);
 /* Sets the launch parameters of the evaluation kernels (synchronises
- * `stream` first).  Never changes results.  PF_ERR_INVALID for values
- * outside the documented range. */
+ * `stream` first; allocates the schedule counters of ctas_per_sm > 0 on
+ * first use).  Never changes results.  PF_ERR_INVALID for values outside
+ * the documented range (tile_inc 32/64/96/128, ctas_per_sm 0..32,
+ * split_rounds 0/1). */
 PF_API int pf_set_tuning(pf_ctx *ctx, const pf_tuning *t, void *stream);
 /* Times the fused evaluation at x for each candidate tuning, keeps the
  * fastest and returns it in *chosen.  x, F, vals: device buffers used as
@@ -399,8 +403,9 @@ PF_API int pf_voltage_records(pf_ctx *ctx, const double *x, double *rec, void *s
 PF_API const char *pf_error_string(int32_t code);
 PF_API const char *pf_last_error(void);
 /* Reads and clears the context's device error flag (a kernel found an
- * inconsistent map or a bounded wait ran out).  Synchronises `stream`.
- * Returns PF_OK or PF_ERR_DEVICE / PF_ERR_TIMEOUT. */
+ * inconsistent map or a bounded wait ran out), and checks that the schedule
+ * counters of persistent fused grids (ctas_per_sm > 0) are back at zero.
+ * Synchronises `stream`.  Returns PF_OK or PF_ERR_DEVICE / PF_ERR_TIMEOUT. */
 PF_API int pf_check_device(pf_ctx *ctx, void *stream);
 
 #ifdef __cplusplus

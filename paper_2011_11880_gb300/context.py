@@ -319,10 +319,14 @@ class Context:
         return x
 
     # ---- tuning / errors ----
+    @staticmethod
+    def _tuning_dict(t):
+        return {"tile_inc": t.tile_inc, "ctas_per_sm": t.ctas_per_sm, "split_rounds": t.split_rounds}
+
     def tuning(self):
         t = PfTuning()
         check(self._lib.pf_get_tuning(self._h, ctypes.byref(t)), "pf_get_tuning")
-        return {"tile_inc": t.tile_inc, "ctas_per_sm": t.ctas_per_sm, "split_rounds": t.split_rounds}
+        return self._tuning_dict(t)
 
     def set_tuning(self, tile_inc: int, ctas_per_sm: int = 0, split_rounds: int = 0, stream=None):
         t = PfTuning(int(tile_inc), int(ctas_per_sm), int(split_rounds))
@@ -334,7 +338,7 @@ class Context:
                                     _ptr(F, numel=self.dims.n_f, name="F"),
                                     _ptr(vals, numel=self.dims.nnz, name="vals"), _stream(stream),
                                     ctypes.byref(t)), "pf_autotune")
-        return {"tile_inc": t.tile_inc, "ctas_per_sm": t.ctas_per_sm, "split_rounds": t.split_rounds}
+        return self._tuning_dict(t)
 
     def sincos(self, theta, stream=None):
         """(cos, sin) of a float64 CUDA tensor by the evaluation's phasor routine."""

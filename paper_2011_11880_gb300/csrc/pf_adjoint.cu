@@ -520,14 +520,14 @@ __global__ void k_vjp_inj(View v, const double *__restrict__ vv, int n_cot, int6
 
 template <int CH, bool MASKED>
 int launch_state(const Ctx &c, const VjpArgs &a, cudaStream_t s) {
-  const int64_t cap = c.tuning.ctas_per_sm > 0 ? (int64_t)c.tuning.ctas_per_sm * c.num_sms : INT64_MAX;
+  const int cps = c.tuning.ctas_per_sm;
   if (c.v.n_lane_units > 0) {
     const int64_t work = c.v.n_lane_units * ((a.n_cot + CH - 1) / CH);
-    k_vjp_lane<CH, MASKED><<<(unsigned)std::min<int64_t>(work, cap), 32, 0, s>>>(c.v, a);
+    k_vjp_lane<CH, MASKED><<<(unsigned)capped_grid(work, cps, c.num_sms), 32, 0, s>>>(c.v, a);
     PF_CUDA_TRY(cudaGetLastError());
   }
   if (c.v.n_large_units > 0) {
-    k_vjp_large<CH, MASKED><<<(unsigned)std::min<int64_t>(c.v.n_large_units, cap), 32, 0, s>>>(c.v, a);
+    k_vjp_large<CH, MASKED><<<(unsigned)capped_grid(c.v.n_large_units, cps, c.num_sms), 32, 0, s>>>(c.v, a);
     PF_CUDA_TRY(cudaGetLastError());
   }
   return PF_OK;

@@ -323,9 +323,18 @@ int pf_set_tuning(pf_ctx *ctx, const pf_tuning *t, void *stream) {
   if (t->split_rounds != 0 && t->split_rounds != 1) return fail(PF_ERR_INVALID, "split_rounds must be 0 or 1");
   cudaStream_t s = as_stream(stream);
   PF_CUDA_TRY(cudaStreamSynchronize(s));
-  ctx->c.tuning.tile_inc = t->tile_inc;
-  ctx->c.tuning.ctas_per_sm = t->ctas_per_sm;
-  ctx->c.tuning.split_rounds = t->split_rounds;
+  pf::Ctx &c = ctx->c;
+  if (t->ctas_per_sm > 0 && !c.work_ctr) {
+    void *p = nullptr;
+    const size_t bytes = 2 * sizeof(unsigned long long);
+    if (cudaMalloc(&p, bytes) != cudaSuccess) return fail(PF_ERR_OOM, "cudaMalloc of the schedule counters");
+    c.allocations.push_back(p);
+    PF_CUDA_TRY(cudaMemset(p, 0, bytes));
+    c.work_ctr = static_cast<unsigned long long *>(p);
+  }
+  c.tuning.tile_inc = t->tile_inc;
+  c.tuning.ctas_per_sm = t->ctas_per_sm;
+  c.tuning.split_rounds = t->split_rounds;
   return PF_OK;
 }
 
@@ -408,6 +417,14 @@ int pf_check_device(pf_ctx *ctx, void *stream) {
   PF_CUDA_TRY(cudaStreamSynchronize(s));
   if (h & pf::kErrTimeout) return fail(PF_ERR_TIMEOUT, "a bounded device wait gave up");
   if (h) return fail(PF_ERR_DEVICE, "device error flag " + std::to_string(h));
+  if (ctx->c.work_ctr) {
+    // the schedule counters of persistent k_fused grids are zero between launches
+    unsigned long long w[2];
+    PF_CUDA_TRY(cudaMemcpyAsync(w, ctx->c.work_ctr, sizeof(w), cudaMemcpyDeviceToHost, s));
+    PF_CUDA_TRY(cudaStreamSynchronize(s));
+    for (unsigned long long x : w)
+      if (x) return fail(PF_ERR_DEVICE, "schedule counter not reset");
+  }
   return PF_OK;
 }
 

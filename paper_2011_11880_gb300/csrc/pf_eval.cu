@@ -271,6 +271,10 @@ struct EvalArgs {
   const uint8_t *gen_mode; // extended, per instance-generator: != 0 holds Q_g at gen_qlim, or nullptr
   const double *gen_qlim;
   int split;               // 1: half a round per warp, two lanes per bus
+  // a persistent (capped) k_fused grid: {next unit, CTAs done} counters of
+  // its dynamic schedule, zero at launch and reset by the grid's last CTA;
+  // nullptr: CTA b takes units b, b + grid, ...
+  unsigned long long *work;
 };
 
 // X and Y of one branch end (own voltage Eo, other voltage Ek, rectangular).
@@ -462,10 +466,15 @@ __device__ __forceinline__ double2 slot_gb(const View &v, const EvalArgs &a, int
 // the largest count each variant compiles to without spilling -- for the
 // unmasked F + J evaluation 64 registers with one slot per fetch, 80 with
 // two; fewer CTAs for the other variants and for deeper fetches.
-template <int ITEMS, bool WF, bool WJ, bool MASKED>
+// The persistent variants (DYN: dynamic schedule) keep a claimed unit index
+// live across the loop, and a persistent grid holds fewer CTAs per SM: a
+// bound of 4 (one slot per fetch: 12) fewer CTAs leaves them room without
+// spilling.
+template <int ITEMS, bool WF, bool WJ, bool MASKED, bool DYN>
 struct FusedMinCtas {
   static constexpr bool plain = WF && WJ && !MASKED;     // the F + J evaluation without a mask
-  static constexpr int value = ITEMS == 1 ? (plain ? 32 : 28) : ITEMS == 2 ? (plain ? 24 : 20) : 16;
+  static constexpr int base = ITEMS == 1 ? (plain ? 32 : 28) : ITEMS == 2 ? (plain ? 24 : 20) : 16;
+  static constexpr int value = DYN ? base - (ITEMS == 1 ? 12 : 4) : base;
 };
 
 // One warp per round.  A round holds up to 32 buses with equal (or
@@ -477,8 +486,8 @@ struct FusedMinCtas {
 // several branches costs one merged branch end.  Under an outage mask a
 // group with more than one branch re-sums the coefficients of its branches in
 // service.  Slots are fetched ITEMS at a time.
-template <int ITEMS, bool WF, bool WJ, bool MASKED>
-__global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED>::value)) k_fused(View v, EvalArgs a) {
+template <int ITEMS, bool WF, bool WJ, bool MASKED, bool DYN>
+__global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED, DYN>::value)) k_fused(View v, EvalArgs a) {
   const int lane = threadIdx.x & 31;
   // split rounds: a warp takes half a round (16 buses), two lanes per bus,
   // lane l the pairs l >> 4, (l >> 4) + 2, ... of bus l & 15
@@ -487,7 +496,22 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED>::valu
   const int bl0 = split ? (lane & 15) : lane;    // bus lane within the (half) round
   const int par = split ? (lane >> 4) : 0;       // this lane's first pair
   const int step = 1 + split;                    // and its stride
-  for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
+  // Dynamic schedule of a persistent grid: lane 0 claims the warp's next unit
+  // from a counter as it starts a unit, so the claim's latency hides behind
+  // the unit's work; units of uneven weight then even out over the CTAs.
+  unsigned long long *const work = DYN ? a.work : nullptr;
+  int64_t u = blockIdx.x;
+  unsigned long long claim = 0;
+  if (work) {
+    // The counters were reset by the previous launch's last CTA; as a
+    // programmatic dependent this grid may start before that write is
+    // visible, so it waits for its prerequisite grids before the first claim.
+    cudaGridDependencySynchronize();
+    if (lane == 0) claim = atomicAdd(work, 1ULL);
+    u = (int64_t)__shfl_sync(0xffffffffu, claim, 0);
+  }
+  for (; u < n_units; u = work ? (int64_t)__shfl_sync(0xffffffffu, claim, 0) : u + gridDim.x) {
+    if (work && lane == 0) claim = atomicAdd(work, 1ULL);
     const int4 ur = __ldg(v.unit_rec + (u >> split));   // {instance, round, first slot, D | buses << 8}
     const int inst = ur.x;
     const int64_t r = ur.y;
@@ -600,6 +624,15 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED>::valu
                            hat.y, bm, bm2, inj);
     }
   }
+  // Every CTA leaves the loop once, after a claim past the last unit; the last
+  // one to leave resets both counters for the next launch.
+  if (work && lane == 0) {
+    __threadfence();
+    if (atomicAdd(work + 1, 1ULL) == gridDim.x - 1) {
+      work[0] = 0ULL;
+      work[1] = 0ULL;
+    }
+  }
 }
 
 // Buses with more than 32 ends, one warp each (launched after k_fused, so the
@@ -693,11 +726,18 @@ __global__ void __launch_bounds__(32) k_fused_large(View v, EvalArgs a) {
   }
 }
 
+// pdl: k_fused is launched as a programmatic dependent of the stream's
+// previous kernel (k_phasor), so its CTAs start before that grid ends and
+// load the static maps and the branch coefficients ahead of their wait for
+// it; set only where no kernel that wrote those coefficients comes directly
+// before it.
 template <int ITEMS, bool WF, bool WJ, bool MASKED>
-int launch_fused_t(const View &v, int num_sms, const pf_tuning &t, const EvalArgs &a, cudaStream_t s) {
+int launch_fused_t(const View &v, int num_sms, const pf_tuning &t, const EvalArgs &a, bool pdl, cudaStream_t s) {
   if (v.n_lane_units > 0) {
-    int64_t grid = v.n_lane_units << a.split;
-    if (t.ctas_per_sm > 0) grid = std::min<int64_t>(grid, (int64_t)t.ctas_per_sm * num_sms);
+    const int64_t n_units = v.n_lane_units << a.split;
+    const int64_t grid = capped_grid(n_units, t.ctas_per_sm, num_sms);
+    EvalArgs ak = a;
+    if (grid == n_units) ak.work = nullptr;       // one CTA per unit: the hardware schedules them
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(32);
@@ -707,12 +747,12 @@ int launch_fused_t(const View &v, int num_sms, const pf_tuning &t, const EvalArg
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    PF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_fused<ITEMS, WF, WJ, MASKED>, v, a));
+    cfg.numAttrs = pdl ? 1 : 0;
+    if (ak.work) PF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_fused<ITEMS, WF, WJ, MASKED, true>, v, ak));
+    else PF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_fused<ITEMS, WF, WJ, MASKED, false>, v, ak));
   }
   if (v.n_large_units > 0) {
-    int64_t grid = v.n_large_units;
-    if (t.ctas_per_sm > 0) grid = std::min<int64_t>(grid, (int64_t)t.ctas_per_sm * num_sms);
+    const int64_t grid = capped_grid(v.n_large_units, t.ctas_per_sm, num_sms);
     k_fused_large<ITEMS, WF, WJ, MASKED><<<(unsigned)grid, 32, 0, s>>>(v, a);
     PF_CUDA_TRY(cudaGetLastError());
   }
@@ -720,27 +760,41 @@ int launch_fused_t(const View &v, int num_sms, const pf_tuning &t, const EvalArg
 }
 
 template <int ITEMS>
-int launch_fused_items(const View &v, int num_sms, const pf_tuning &t, const EvalArgs &a, bool masked,
+int launch_fused_items(const View &v, int num_sms, const pf_tuning &t, const EvalArgs &a, bool masked, bool pdl,
                        cudaStream_t s) {
   const bool wf = a.F != nullptr, wj = a.vals != nullptr;
   if (wf && wj)
-    return masked ? launch_fused_t<ITEMS, true, true, true>(v, num_sms, t, a, s)
-                  : launch_fused_t<ITEMS, true, true, false>(v, num_sms, t, a, s);
+    return masked ? launch_fused_t<ITEMS, true, true, true>(v, num_sms, t, a, pdl, s)
+                  : launch_fused_t<ITEMS, true, true, false>(v, num_sms, t, a, pdl, s);
   if (wf)
-    return masked ? launch_fused_t<ITEMS, true, false, true>(v, num_sms, t, a, s)
-                  : launch_fused_t<ITEMS, true, false, false>(v, num_sms, t, a, s);
-  return masked ? launch_fused_t<ITEMS, false, true, true>(v, num_sms, t, a, s)
-                : launch_fused_t<ITEMS, false, true, false>(v, num_sms, t, a, s);
+    return masked ? launch_fused_t<ITEMS, true, false, true>(v, num_sms, t, a, pdl, s)
+                  : launch_fused_t<ITEMS, true, false, false>(v, num_sms, t, a, pdl, s);
+  return masked ? launch_fused_t<ITEMS, false, true, true>(v, num_sms, t, a, pdl, s)
+                : launch_fused_t<ITEMS, false, true, false>(v, num_sms, t, a, pdl, s);
 }
 
-int launch_fused(const View &v, int num_sms, const pf_tuning &t, const EvalArgs &a, bool masked, cudaStream_t s) {
+int launch_fused(const View &v, int num_sms, const pf_tuning &t, const EvalArgs &a, bool masked, cudaStream_t s,
+                 bool pdl = true) {
   switch (t.tile_inc) {
-    case 32: return launch_fused_items<1>(v, num_sms, t, a, masked, s);
-    case 64: return launch_fused_items<2>(v, num_sms, t, a, masked, s);
-    case 96: return launch_fused_items<3>(v, num_sms, t, a, masked, s);
-    case 128: return launch_fused_items<4>(v, num_sms, t, a, masked, s);
+    case 32: return launch_fused_items<1>(v, num_sms, t, a, masked, pdl, s);
+    case 64: return launch_fused_items<2>(v, num_sms, t, a, masked, pdl, s);
+    case 96: return launch_fused_items<3>(v, num_sms, t, a, masked, pdl, s);
+    case 128: return launch_fused_items<4>(v, num_sms, t, a, masked, pdl, s);
     default: return fail(PF_ERR_INVALID, "tile_inc must be 32, 64, 96 or 128");
   }
+}
+
+// The view of the instances [i0, i1): their units are contiguous in the unit
+// lists and their buses in the phasor scratch; every other index stays global.
+View range_view(const Ctx &c, int i0, int i1) {
+  View v = c.v;
+  v.unit_rec = c.v.unit_rec + c.lane_off[i0];
+  v.n_lane_units = c.lane_off[i1] - c.lane_off[i0];
+  v.large_rec = c.v.large_rec + c.large_off[i0];
+  v.n_large_units = c.large_off[i1] - c.large_off[i0];
+  v.bus_inst_begin = c.bus_off[i0];
+  v.n_bus_inst = c.bus_off[i1];
+  return v;
 }
 
 void built_coefficients(const View &v, EvalArgs &a) {
@@ -787,7 +841,9 @@ int launch_eval_stages(Ctx &c, int stages, const double *x, const pf_overrides *
   a.F = F;
   a.vals = vals;
   a.split = c.tuning.split_rounds ? 1 : 0;
+  a.work = c.work_ctr;
   built_coefficients(c.v, a);
+  bool params = false;                           // per-call branch parameters
   if (ov) {
     a.p_inj = ov->p_inj;
     a.q_inj = ov->q_inj;
@@ -796,6 +852,7 @@ int launch_eval_stages(Ctx &c, int stages, const double *x, const pf_overrides *
     a.gen_qlim = ov->gen_qlim;
     if (ov->gen_mode && !ov->gen_qlim) return fail(PF_ERR_INVALID, "gen_mode needs gen_qlim");
     if (ov->br_r || ov->br_x || ov->br_b || ov->br_tap) {
+      params = true;
       if (stages & 2) {
         PF_TRY(compute_coefficients(c, ov->br_r, ov->br_x, ov->br_b, ov->br_tap, c.ov_gb, c.ov_ac, c.ov_hat, s));
         PF_TRY(permute_overrides(c, s));
@@ -811,7 +868,9 @@ int launch_eval_stages(Ctx &c, int stages, const double *x, const pf_overrides *
   const bool masked = c.any_outage || a.status != nullptr;
   if (stages & 1) PF_TRY(launch_phasor(c.v, c.num_sms, x, s));
   if (!(stages & 2)) return PF_OK;
-  return launch_fused(c.v, c.num_sms, c.tuning, a, masked, s);
+  // the fused stage alone with per-call branch parameters: the kernel that
+  // wrote its coefficients comes directly before it
+  return launch_fused(c.v, c.num_sms, c.tuning, a, masked, s, !(params && stages == 2));
 }
 
 // F and J of the instances [i0, i1): the units of those instances are
@@ -820,18 +879,13 @@ int launch_eval_range(Ctx &c, int i0, int i1, const double *x, double *F, double
   if (!x) return fail(PF_ERR_INVALID, "x is NULL");
   if (i0 < 0 || i1 > c.v.n_inst || i0 >= i1) return fail(PF_ERR_INVALID, "bad instance range");
   if (!F && !vals) return PF_OK;
-  View v = c.v;
-  v.unit_rec = c.v.unit_rec + c.lane_off[i0];
-  v.n_lane_units = c.lane_off[i1] - c.lane_off[i0];
-  v.large_rec = c.v.large_rec + c.large_off[i0];
-  v.n_large_units = c.large_off[i1] - c.large_off[i0];
-  v.bus_inst_begin = c.bus_off[i0];
-  v.n_bus_inst = c.bus_off[i1];
+  const View v = range_view(c, i0, i1);
   EvalArgs a{};
   a.x = x;
   a.F = F;
   a.vals = vals;
   a.split = c.tuning.split_rounds ? 1 : 0;
+  a.work = c.work_ctr;
   built_coefficients(c.v, a);
   PF_TRY(launch_phasor(v, c.num_sms, x, s));
   return launch_fused(v, c.num_sms, c.tuning, a, c.any_outage, s);
@@ -850,6 +904,7 @@ int launch_eval_scratch(Ctx &c, const double *x, double *F, double *vals, double
   a.F = F;
   a.vals = vals;
   a.split = c.tuning.split_rounds ? 1 : 0;
+  a.work = c.work_ctr;
   built_coefficients(c.v, a);
   PF_TRY(launch_phasor(v, c.num_sms, x, s));
   return launch_fused(v, c.num_sms, c.tuning, a, c.any_outage, s);

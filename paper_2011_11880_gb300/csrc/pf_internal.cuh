@@ -30,6 +30,16 @@ constexpr int kMaxGroup = 32;      // parallel branches between one pair of buse
 constexpr int kLaneMaxDegree = 32;
 constexpr int kSinCosTable = 32768;  // table of (cos, sin)(i pi / 16384)
 
+// Grid of a kernel whose CTAs walk `work` units with a grid-stride loop,
+// capped at ctas_per_sm CTAs per SM when that is set.  The units of a grid
+// alternate between heavy and light rounds, so a capped grid is made odd:
+// with an even stride every CTA would take only heavy or only light rounds.
+inline int64_t capped_grid(int64_t work, int ctas_per_sm, int num_sms) {
+  const int64_t cap = (int64_t)ctas_per_sm * num_sms;
+  if (ctas_per_sm <= 0 || work <= cap) return work;
+  return (cap & 1) ? cap : cap - 1;
+}
+
 // Thread-local error message behind pf_last_error().
 void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
@@ -171,6 +181,9 @@ struct Ctx {
   // pipelined host-buffer evaluation: internal streams and events, created on first use
   cudaStream_t pipe_stream[3] = {nullptr, nullptr, nullptr};
   std::vector<cudaEvent_t> pipe_events;
+  // dynamic schedule of a persistent k_fused grid (tuning.ctas_per_sm > 0):
+  // {next unit, CTAs done}, zero between launches; allocated by pf_set_tuning
+  unsigned long long *work_ctr = nullptr;
   // Newton-iteration state (pf_newton.cu), created on first use
   int newton_solver = PF_SOLVER_LU;
   void *newton = nullptr;

@@ -119,15 +119,17 @@ def test_deterministic_across_runs_and_tunings(P, name):
     for _ in range(3):
         F1, v1 = ctx.residual_jacobian(x)
         assert torch.equal(F0, F1) and torch.equal(v0, v1)
+    nan = float("nan")
     for split in (0, 1):
         for tile in (32, 64, 96, 128):
             for ctas in (0, 1, 3, 16):
                 ctx.set_tuning(tile, ctas, split)
-                F1, v1 = ctx.residual_jacobian(x)
-                assert torch.equal(F0, F1) and torch.equal(v0, v1), (tile, ctas, split)
-                F2 = ctx.residual(x)                   # F alone takes the same sums
+                for _ in range(2):                     # a persistent grid's counters are reused
+                    F1, v1 = ctx.residual_jacobian(x, ctx.empty_f().fill_(nan), ctx.empty_vals().fill_(nan))
+                    assert torch.equal(F0, F1) and torch.equal(v0, v1), (tile, ctas, split)
+                F2 = ctx.residual(x, ctx.empty_f().fill_(nan))   # F alone takes the same sums
                 assert torch.equal(F0, F2), (tile, ctas, split)
-    ctx.check_device()
+                ctx.check_device()
 
 
 def test_autotune_keeps_results(P):
@@ -297,4 +299,65 @@ def test_split_rounds_bit_identical_under_masks(P, mode):
     for k in range(2, len(outs), 2):
         assert torch.equal(outs[0][0], outs[k][0]) and torch.equal(outs[0][1], outs[k][1]), k
         assert torch.equal(outs[1][0], outs[k + 1][0]) and torch.equal(outs[1][1], outs[k + 1][1]), k
+    ctx.check_device()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_persistent_schedule_bit_identical(P, mode):
+    """Persistent fused grids (ctas_per_sm > 0), whose warps claim rounds from a counter, give
+    the one-CTA-per-round results bit for bit over a batch: outage instances, a status mask,
+    branch-parameter overrides, buses with more than 32 neighbours (the warp-per-bus kernel),
+    F or J alone, repeated launches (the counters are reset by each grid), the fused stage
+    launched alone, and replays of a captured CUDA graph."""
+    grids = [GRIDS["grid200"], GRIDS["star"], GRIDS["edge300"]]
+    inst = [(0, -1), (1, -1), (0, 7), (2, -1), (1, 5), (2, 11), (0, 3)]
+    ctx = P.Context(grids, MNAME[mode], instances=inst)
+    d = ctx.dims
+    x = torch.from_numpy(np.concatenate([state(grids[g], k + 2, mode == EXTENDED)
+                                         for k, (g, _) in enumerate(inst)])).cuda()
+    rng = np.random.default_rng(21)
+    r0 = np.concatenate([g.br_r for g in grids])
+    assert r0.size == d.n_branch
+    kw = {"status": torch.from_numpy((rng.random(d.n_branch_inst) > 0.05).astype(np.uint8)).cuda(),
+          "br_r": torch.from_numpy(r0 * rng.uniform(0.9, 1.1, r0.size)).cuda()}
+    if mode == EXTENDED:
+        kw["gen_mode"] = torch.from_numpy(rng.integers(0, 3, d.n_gen_inst).astype(np.uint8)).cuda()
+        kw["gen_qlim"] = torch.from_numpy(rng.uniform(-0.5, 0.8, d.n_gen_inst)).cuda()
+    nan = float("nan")
+
+    def run():   # outputs start as NaN, so a round left out cannot pass for a written one
+        F, V = ctx.empty_f().fill_(nan), ctx.empty_vals().fill_(nan)
+        ctx.eval_stage(1, x, F, V)
+        ctx.eval_stage(2, x, F, V)
+        return (ctx.eval(x, ctx.empty_f().fill_(nan), ctx.empty_vals().fill_(nan), **kw),
+                ctx.residual_jacobian(x, ctx.empty_f().fill_(nan), ctx.empty_vals().fill_(nan)),
+                ctx.residual(x, ctx.empty_f().fill_(nan)), ctx.jacobian(x, ctx.empty_vals().fill_(nan)),
+                (F, V))
+
+    ctx.set_tuning(64, 0, 0)
+    ref = run()
+    for tile, cps, split in ((64, 16, 0), (64, 20, 0), (32, 1, 0), (128, 16, 1), (96, 3, 1)):
+        ctx.set_tuning(tile, cps, split)
+        for _ in range(2):
+            got = run()
+            for k in (0, 1, 4):
+                assert torch.equal(ref[k][0], got[k][0]) and torch.equal(ref[k][1], got[k][1]), (k, tile, cps)
+            assert torch.equal(ref[2], got[2]) and torch.equal(ref[3], got[3]), (tile, cps)
+        ctx.check_device()                     # the schedule counters are back at zero
+    s = torch.cuda.Stream()
+    F, V = ctx.empty_f(), ctx.empty_vals()
+    ctx.set_tuning(64, 16, 0)
+    with torch.cuda.stream(s):
+        ctx.residual_jacobian(x, F, V, stream=s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ctx.residual_jacobian(x, F, V, stream=s)
+    for _ in range(3):
+        F.fill_(nan)
+        V.fill_(nan)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(F, ref[1][0]) and torch.equal(V, ref[1][1])
     ctx.check_device()
