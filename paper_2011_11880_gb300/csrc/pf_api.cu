@@ -32,8 +32,18 @@ namespace {
 
 cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
 
-// Chunks of instances of the pipelined host-buffer evaluation.
+// Chunks of instances of the pipelined host-buffer evaluation.  The copy out
+// of F and J is the slowest stage, so the chunks grow: chunk k ends at
+// instance max(k + 1, I (k+1)^2 / C^2), and the first copy out starts after a
+// small chunk's copy in and evaluation.
 constexpr int kHostChunks = 8;
+constexpr bool kHostGrowingChunks = true;
+
+int host_chunk_end(int I, int C, int k) {
+  const int64_t n = (int64_t)(k + 1);
+  if (!kHostGrowingChunks) return (int)((int64_t)I * n / C);
+  return (int)std::max<int64_t>(n, (int64_t)I * n * n / ((int64_t)C * C));
+}
 
 void free_ctx(pf_ctx *ctx) {
   if (!ctx) return;
@@ -240,7 +250,8 @@ int pf_residual_jacobian_host(pf_ctx *ctx, const double *x_host, double *F_host,
   PF_CUDA_TRY(cudaStreamWaitEvent(s_ev, ev_start, 0));
   PF_CUDA_TRY(cudaStreamWaitEvent(s_out, ev_start, 0));
   for (int k = 0; k < C; ++k) {
-    const int i0 = (int)((int64_t)I * k / C), i1 = (int)((int64_t)I * (k + 1) / C);
+    const int i0 = k ? host_chunk_end(I, C, k - 1) : 0, i1 = host_chunk_end(I, C, k);
+    if (i0 == i1) continue;                                   // an empty leading chunk
     cudaEvent_t ev_in = c.pipe_events[2 * k], ev_done = c.pipe_events[2 * k + 1];
     const int64_t x0 = c.x_off[i0], nx = c.x_off[i1] - x0;
     PF_CUDA_TRY(cudaMemcpyAsync(c.stage_x + x0, x_host + x0, nx * sizeof(double), cudaMemcpyHostToDevice, s_in));
