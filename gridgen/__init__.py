@@ -339,30 +339,41 @@ class Instance:
 
 
 def contingency_batch(seed: int = 3000, n_small: int = 2048, n_large: int = 256,
-                      small_bus: int = 2000, large_bus: int = 10000):
+                      small_bus: int = 2000, large_bus: int = 10000, only=None):
     """2,048 instances of a 2,000-bus grid plus 256 of a 10,000-bus grid; each
-    instance has its own seeded perturbed state and one seeded branch outage."""
+    instance has its own seeded perturbed state and one seeded branch outage.
+    only: indices of the instances to generate (the others are left out of the
+    returned list; each generated one equals its entry in the full batch)."""
     grids = [synthetic_grid(small_bus, seed), synthetic_grid(large_bus, seed + 1)]
     rng = np.random.default_rng(seed + 2)
+    keep = None if only is None else set(int(i) for i in only)
     insts = []
+    j = 0
     for gi, count in ((0, n_small), (1, n_large)):
         g = grids[gi]
         outs = rng.integers(0, g.n_branch, size=count)
         for k in range(count):
-            insts.append(Instance(grid=gi, x=perturbed_state(g, seed * 7919 + 1000003 * gi + k),
-                                  outage=int(outs[k])))
+            if keep is None or j in keep:
+                insts.append(Instance(grid=gi, x=perturbed_state(g, seed * 7919 + 1000003 * gi + k),
+                                      outage=int(outs[k])))
+            j += 1
     return grids, insts
 
 
-def mixed_batch(n_inst: int = 4096, seed: int = 5000, n_min: int = 500, n_max: int = 20000):
+def mixed_batch(n_inst: int = 4096, seed: int = 5000, n_min: int = 500, n_max: int = 20000, only=None):
     """Mixed-scenario batch: every instance has its own grid with a log-uniform
     size in [n_min, n_max]; PV outputs scaled per generator by U[0.5, 1.5] and
     loads by one U[0.8, 1.2] factor per instance, given as net-injection
-    overrides."""
+    overrides.  only: indices of the instances to generate (grid k of a
+    generated instance k is the full batch's grid k; `grid` then indexes the
+    returned list)."""
     rng = np.random.default_rng(seed)
     sizes = np.exp(rng.uniform(math.log(n_min), math.log(n_max), n_inst)).round().astype(int)
+    keep = None if only is None else set(int(i) for i in only)
     grids, insts = [], []
     for k, n in enumerate(sizes):
+        if keep is not None and k not in keep:
+            continue
         g = synthetic_grid(int(n), seed + 17 * k + 1)
         r = np.random.default_rng(seed * 31 + k)
         pv_scale = r.uniform(0.5, 1.5, g.n_pv)
@@ -373,5 +384,5 @@ def mixed_batch(n_inst: int = 4096, seed: int = 5000, n_min: int = 500, n_max: i
         np.add.at(p, g.load_bus, -g.load_p * load_scale)
         np.add.at(q, g.load_bus, -g.load_q * load_scale)
         grids.append(g)
-        insts.append(Instance(grid=k, x=perturbed_state(g, seed * 131 + k), p_inj=p, q_inj=q))
+        insts.append(Instance(grid=len(grids) - 1, x=perturbed_state(g, seed * 131 + k), p_inj=p, q_inj=q))
     return grids, insts

@@ -65,3 +65,14 @@ def test_reference_arm_runs_on_rank_zero_only(rank, expect_line):
         assert rec["e2e"]["h2d_bytes_per_step"] == 0 and rec["cpu_baseline"]["kind"] == "oracle"
     else:
         assert lines == []
+
+
+def test_oracle_pool_runs_one_process_per_core():
+    """The batched CPU baseline spreads the oracle over one spawned process per host core,
+    each on its own share of the instances, and counts every process's instances."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for kind, n in (("contingency", 2304), ("mixed", 4096)):
+        rate, m, el, cores = bench.oracle_pool(kind, n, 0.3)
+        assert cores == len(os.sched_getaffinity(0))
+        assert m >= cores and el >= 0.3 and rate == pytest.approx(m / el)
