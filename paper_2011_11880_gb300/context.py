@@ -206,10 +206,13 @@ class Context:
                                 _stream(stream)), "pf_eval")
         return F, vals
 
-    def eval_stage(self, stage: int, x, F=None, vals=None, stream=None):
-        """One kernel of an evaluation: stage 1 (phasors) or 2 (fused F/J; needs a preceding stage 1)."""
+    def eval_stage(self, stage: int, x, F=None, vals=None, stream=None, **overrides):
+        """One kernel of an evaluation: stage 1 (phasors) or 2 (fused F/J; needs a preceding stage 1),
+        with the per-call overrides of `eval`."""
         d = self.dims
-        check(self._lib.pf_eval_stage(self._h, int(stage), _ptr(x, numel=d.n_x, name="x"), None,
+        ov = self._overrides(**overrides)
+        check(self._lib.pf_eval_stage(self._h, int(stage), _ptr(x, numel=d.n_x, name="x"),
+                                      ctypes.byref(ov) if ov is not None else None,
                                       _ptr(F, numel=d.n_f, name="F"), _ptr(vals, numel=d.nnz, name="vals"),
                                       _stream(stream)), "pf_eval_stage")
         return F, vals

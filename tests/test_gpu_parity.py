@@ -329,18 +329,24 @@ def test_persistent_schedule_bit_identical(P, mode):
         F, V = ctx.empty_f().fill_(nan), ctx.empty_vals().fill_(nan)
         ctx.eval_stage(1, x, F, V)
         ctx.eval_stage(2, x, F, V)
+        # the fused stage alone right after the kernels that write the per-call coefficients
+        Fo, Vo = ctx.empty_f().fill_(nan), ctx.empty_vals().fill_(nan)
+        ctx.eval_stage(1, x, Fo, Vo, **kw)
+        ctx.eval_stage(2, x, Fo, Vo, **kw)
         return (ctx.eval(x, ctx.empty_f().fill_(nan), ctx.empty_vals().fill_(nan), **kw),
                 ctx.residual_jacobian(x, ctx.empty_f().fill_(nan), ctx.empty_vals().fill_(nan)),
                 ctx.residual(x, ctx.empty_f().fill_(nan)), ctx.jacobian(x, ctx.empty_vals().fill_(nan)),
-                (F, V))
+                (F, V), (Fo, Vo))
 
     ctx.set_tuning(64, 0, 0)
     ref = run()
+    assert torch.equal(ref[5][0], ref[0][0]) and torch.equal(ref[5][1], ref[0][1])   # stages == one call
+    assert torch.equal(ref[4][0], ref[1][0]) and torch.equal(ref[4][1], ref[1][1])
     for tile, cps, split in ((64, 16, 0), (64, 20, 0), (32, 1, 0), (128, 16, 1), (96, 3, 1)):
         ctx.set_tuning(tile, cps, split)
         for _ in range(2):
             got = run()
-            for k in (0, 1, 4):
+            for k in (0, 1, 4, 5):
                 assert torch.equal(ref[k][0], got[k][0]) and torch.equal(ref[k][1], got[k][1]), (k, tile, cps)
             assert torch.equal(ref[2], got[2]) and torch.equal(ref[3], got[3]), (tile, cps)
         ctx.check_device()                     # the schedule counters are back at zero
