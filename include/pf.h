@@ -370,9 +370,10 @@ PF_API int pf_get_tuning(const pf_ctx *ctx, pf_tuning *t);
  * the documented range (tile_inc 32/64/96/128, ctas_per_sm 0..32,
  * split_rounds 0/1). */
 PF_API int pf_set_tuning(pf_ctx *ctx, const pf_tuning *t, void *stream);
-/* Times the fused evaluation at x for each candidate tuning, keeps the
- * fastest and returns it in *chosen.  x, F, vals: device buffers used as
- * scratch for the timing runs. */
+/* Times the fused evaluation at x for each candidate tuning (a batch of
+ * about 2 ms of back-to-back evaluations, 5 to 200, the faster of two
+ * batches), keeps the fastest and returns it in *chosen.  x, F, vals: device
+ * buffers used as scratch for the timing runs. */
 PF_API int pf_autotune(pf_ctx *ctx, const double *x, double *F, double *vals, void *stream,
                 pf_tuning *chosen);
 

@@ -1,5 +1,6 @@
 // C ABI of libpf.so (declarations and contracts in include/pf.h).
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <cstring>
 #include <string>
@@ -359,21 +360,32 @@ int pf_autotune(pf_ctx *ctx, const double *x, double *F, double *vals, void *str
   cudaEvent_t e0, e1;
   PF_CUDA_TRY(cudaEventCreate(&e0));
   PF_CUDA_TRY(cudaEventCreate(&e1));
+  // milliseconds per evaluation over `reps` evaluations back to back
+  auto time_evals = [&](int reps, float *per_eval) -> int {
+    PF_CUDA_TRY(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps; ++r) PF_TRY(pf::launch_eval(ctx->c, x, nullptr, F, vals, s));
+    PF_CUDA_TRY(cudaEventRecord(e1, s));
+    PF_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    PF_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    *per_eval = ms / reps;
+    return PF_OK;
+  };
   int rc = PF_OK;
   for (int k = 0; k < 2 * 4 * 3 && !rc; ++k) {       // split rounds x tiles x CTAs per SM
     const pf_tuning t{tiles[(k / 3) % 4], ctas[k % 3], k / 12};
     rc = pf_set_tuning(ctx, &t, stream);
     if (rc) break;
     for (int w = 0; w < 2 && !rc; ++w) rc = pf::launch_eval(ctx->c, x, nullptr, F, vals, s);
+    // a batch of about 2 ms (5 to 200 evaluations), timed twice, the faster kept: short
+    // evaluations are otherwise compared on the noise of a few microseconds
+    float probe = 0.f, t1 = 0.f, t2 = 0.f;
+    if (!rc) rc = time_evals(3, &probe);
+    const int reps = std::max(5, std::min(200, (int)std::ceil(2.0f / std::max(probe, 1e-4f))));
+    if (!rc) rc = time_evals(reps, &t1);
+    if (!rc) rc = time_evals(reps, &t2);
     if (rc) break;
-    const int reps = 5;
-    cudaEventRecord(e0, s);
-    for (int r = 0; r < reps && !rc; ++r) rc = pf::launch_eval(ctx->c, x, nullptr, F, vals, s);
-    cudaEventRecord(e1, s);
-    if (rc) break;
-    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(PF_ERR_CUDA, "autotune timing"); break; }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    const float ms = std::min(t1, t2);
     if (ms < best_ms) {
       best_ms = ms;
       best = t;
