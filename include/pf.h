@@ -376,6 +376,20 @@ PF_API int pf_set_tuning(pf_ctx *ctx, const pf_tuning *t, void *stream);
  * buffers used as scratch for the timing runs. */
 PF_API int pf_autotune(pf_ctx *ctx, const double *x, double *F, double *vals, void *stream,
                 pf_tuning *chosen);
+/* pf_autotune with a tuning cache, so that a process does not time again
+ * what an earlier one chose.  `path` names a text file of tunings, one per
+ * line, keyed by the GPU (name, SM count) and the context (formulation,
+ * numbers of grids, instances, buses, branches, rounds and J nonzeros, and a
+ * hash of the per-grid round counts and of the instance list).  A valid
+ * entry for this context is applied without any timing (*from_cache = 1);
+ * otherwise pf_autotune runs and its choice is appended to the file
+ * (*from_cache = 0).  A file that is missing or unreadable, or holds lines
+ * that do not parse or values outside pf_set_tuning's ranges, is treated as
+ * holding no entry; a file that cannot be written leaves the chosen tuning
+ * set and still returns PF_OK.  Never changes results.  from_cache may be
+ * NULL.  Errors: those of pf_autotune; PF_ERR_INVALID for a NULL path. */
+PF_API int pf_autotune_cache(pf_ctx *ctx, const char *path, const double *x, double *F, double *vals,
+                             void *stream, pf_tuning *chosen, int32_t *from_cache);
 
 /* The per-bus trigonometric routine of the evaluation (table-driven reduction
  * by multiples of pi/16384 and short Taylor polynomials), exposed so it can be

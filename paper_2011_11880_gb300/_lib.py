@@ -100,6 +100,8 @@ SIGNATURES = {
     "pf_get_tuning": (c_int32, [c_void_p, P(PfTuning)]),
     "pf_set_tuning": (c_int32, [c_void_p, P(PfTuning), c_void_p]),
     "pf_autotune": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, P(PfTuning)]),
+    "pf_autotune_cache": (c_int32, [c_void_p, ctypes.c_char_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                    P(PfTuning), P(c_int32)]),
     "pf_sincos": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
     "pf_voltage_records": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "pf_error_string": (ctypes.c_char_p, [c_int32]),

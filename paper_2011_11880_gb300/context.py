@@ -4,6 +4,7 @@ CUDA stream to the C ABI.  All arithmetic runs in the library's kernels."""
 from __future__ import annotations
 
 import ctypes
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -335,13 +336,21 @@ class Context:
         t = PfTuning(int(tile_inc), int(ctas_per_sm), int(split_rounds))
         check(self._lib.pf_set_tuning(self._h, ctypes.byref(t), _stream(stream)), "pf_set_tuning")
 
-    def autotune(self, x, F, vals, stream=None):
+    def autotune(self, x, F, vals, stream=None, cache=None):
+        """Times the candidate tunings at x (F, vals: scratch outputs) and keeps the fastest.
+        cache: path of a tuning file; an entry for this GPU and context shape is applied
+        without timing ("from_cache" in the returned dict), else the choice is appended."""
         t = PfTuning()
-        check(self._lib.pf_autotune(self._h, _ptr(x, numel=self.dims.n_x, name="x"),
-                                    _ptr(F, numel=self.dims.n_f, name="F"),
-                                    _ptr(vals, numel=self.dims.nnz, name="vals"), _stream(stream),
-                                    ctypes.byref(t)), "pf_autotune")
-        return self._tuning_dict(t)
+        xp = _ptr(x, numel=self.dims.n_x, name="x")
+        fp = _ptr(F, numel=self.dims.n_f, name="F")
+        vp = _ptr(vals, numel=self.dims.nnz, name="vals")
+        if cache is None:
+            check(self._lib.pf_autotune(self._h, xp, fp, vp, _stream(stream), ctypes.byref(t)), "pf_autotune")
+            return self._tuning_dict(t)
+        hit = ctypes.c_int32(0)
+        check(self._lib.pf_autotune_cache(self._h, os.fsencode(cache), xp, fp, vp, _stream(stream),
+                                          ctypes.byref(t), ctypes.byref(hit)), "pf_autotune_cache")
+        return dict(self._tuning_dict(t), from_cache=bool(hit.value))
 
     def sincos(self, theta, stream=None):
         """(cos, sin) of a float64 CUDA tensor by the evaluation's phasor routine."""

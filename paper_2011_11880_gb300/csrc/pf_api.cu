@@ -3,6 +3,8 @@
 #include <cmath>
 #include <chrono>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -32,6 +34,42 @@ pf::Ctx *pf::ctx_of(pf_ctx *h) { return h ? &h->c : nullptr; }
 namespace {
 
 cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+// Tuning cache: a line is "<tag> <key> <tile_inc> <ctas_per_sm> <split_rounds>".
+constexpr const char *kTuningTag = "pf-tuning-v1";
+
+bool tuning_valid(const pf_tuning &t) {
+  return t.tile_inc >= pf::kMinTileInc && t.tile_inc <= pf::kMaxTileInc && t.tile_inc % 32 == 0 &&
+         t.ctas_per_sm >= 0 && t.ctas_per_sm <= 32 && (t.split_rounds == 0 || t.split_rounds == 1);
+}
+
+// 64-bit FNV-1a over the bytes of v.
+template <class T>
+uint64_t fnv1a(uint64_t h, const std::vector<T> &v) {
+  const unsigned char *p = reinterpret_cast<const unsigned char *>(v.data());
+  for (size_t i = 0; i < v.size() * sizeof(T); ++i) h = (h ^ p[i]) * 0x100000001b3ULL;
+  return h;
+}
+
+// The GPU and the shape of the context, without blanks; empty if the device
+// cannot be queried.
+std::string tuning_key(const pf::Ctx &c) {
+  int dev = 0;
+  cudaDeviceProp prop{};
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "";
+  std::string name(prop.name);
+  for (char &ch : name)
+    if (ch == ' ' || ch == '\t') ch = '_';
+  uint64_t h = 0xcbf29ce484222325ULL;
+  h = fnv1a(h, c.grid_round_off);
+  h = fnv1a(h, c.inst_grid);
+  h = fnv1a(h, c.inst_outage);
+  std::ostringstream k;
+  k << name << ":sm" << prop.multiProcessorCount << ":f" << c.v.formulation << ":g" << c.v.n_grids << ":i"
+    << c.v.n_inst << ":b" << c.v.n_bus << ":br" << c.v.n_branch << ":r" << c.n_rounds << ":nnz" << c.nnz << ":h"
+    << std::hex << h;
+  return k.str();
+}
 
 // Chunks of instances of the pipelined host-buffer evaluation.  The copy out
 // of F and J is the slowest stage, so the chunks grow: chunk k ends at
@@ -396,6 +434,42 @@ int pf_autotune(pf_ctx *ctx, const double *x, double *F, double *vals, void *str
   if (rc) return rc;
   PF_TRY(pf_set_tuning(ctx, &best, stream));
   if (chosen) *chosen = best;
+  return PF_OK;
+}
+
+int pf_autotune_cache(pf_ctx *ctx, const char *path, const double *x, double *F, double *vals, void *stream,
+                      pf_tuning *chosen, int32_t *from_cache) {
+  if (!ctx || !path) return fail(PF_ERR_INVALID, "NULL argument");
+  if (from_cache) *from_cache = 0;
+  const std::string key = tuning_key(ctx->c);
+  if (key.empty()) return fail(PF_ERR_CUDA, "cannot query the device for the tuning key");
+  {
+    std::ifstream in(path);
+    std::string line;
+    pf_tuning found{};
+    bool have = false;
+    while (in && std::getline(in, line)) {             // the last valid entry for the key wins
+      std::istringstream ls(line);
+      std::string tag, k;
+      pf_tuning t{};
+      if (ls >> tag >> k >> t.tile_inc >> t.ctas_per_sm >> t.split_rounds && tag == kTuningTag && k == key &&
+          tuning_valid(t)) {
+        found = t;
+        have = true;
+      }
+    }
+    if (have) {
+      PF_TRY(pf_set_tuning(ctx, &found, stream));
+      if (chosen) *chosen = found;
+      if (from_cache) *from_cache = 1;
+      return PF_OK;
+    }
+  }
+  pf_tuning t{};
+  PF_TRY(pf_autotune(ctx, x, F, vals, stream, &t));
+  std::ofstream out(path, std::ios::app);
+  if (out) out << kTuningTag << ' ' << key << ' ' << t.tile_inc << ' ' << t.ctas_per_sm << ' ' << t.split_rounds << '\n';
+  if (chosen) *chosen = t;
   return PF_OK;
 }
 

@@ -367,3 +367,44 @@ def test_persistent_schedule_bit_identical(P, mode):
         torch.cuda.synchronize()
         assert torch.equal(F, ref[1][0]) and torch.equal(V, ref[1][1])
     ctx.check_device()
+
+
+def test_autotune_cache(P, tmp_path):
+    """pf_autotune_cache: the first context times and appends its choice; a second context of
+    the same shape takes it from the file without timing; another instance list is another key;
+    lines that do not parse or hold out-of-range values are ignored.  Results never change."""
+    sys = gridgen.synthetic_grid(2000, 5)
+    path = tmp_path / "tuning.txt"
+    x1 = np.concatenate([state(sys, 1), state(sys, 2)])
+    x = torch.from_numpy(x1).cuda()
+
+    def ctx_of(inst):
+        c = P.Context([sys], instances=inst)
+        return c, c.empty_f(), c.empty_vals()
+
+    c1, F1, V1 = ctx_of([(0, -1), (0, 3)])
+    t1 = c1.autotune(x, F1, V1, cache=str(path))
+    assert t1["from_cache"] is False
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1 and lines[0].startswith("pf-tuning-v1 ")
+    c2, F2, V2 = ctx_of([(0, -1), (0, 3)])
+    t2 = c2.autotune(x, F2, V2, cache=str(path))
+    assert t2["from_cache"] is True and {k: t2[k] for k in t1 if k != "from_cache"} == \
+        {k: t1[k] for k in t1 if k != "from_cache"}
+    assert c2.tuning() == {k: t1[k] for k in t1 if k != "from_cache"}
+    assert len(path.read_text().splitlines()) == 1
+    a1, b1 = c1.residual_jacobian(x)
+    a2, b2 = c2.residual_jacobian(x)
+    assert torch.equal(a1, a2) and torch.equal(b1, b2)
+    c3, F3, V3 = ctx_of([(0, -1), (0, 4)])             # another outage: another key
+    assert c3.autotune(x, F3, V3, cache=str(path))["from_cache"] is False
+    assert len(path.read_text().splitlines()) == 2
+    key = lines[0].split()[1]
+    path.write_text(f"garbage line\npf-tuning-v1 {key} 48 0 0\npf-tuning-v1 {key} 64 99 0\n")
+    c4, F4, V4 = ctx_of([(0, -1), (0, 3)])
+    assert c4.autotune(x, F4, V4, cache=str(path))["from_cache"] is False   # nothing valid: timed again
+    assert len(path.read_text().splitlines()) == 4
+    c5, F5, V5 = ctx_of([(0, -1), (0, 3)])
+    assert c5.autotune(x, F5, V5, cache=str(path))["from_cache"] is True
+    for c in (c1, c2, c3, c4, c5):
+        c.check_device()
