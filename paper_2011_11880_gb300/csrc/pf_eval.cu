@@ -34,7 +34,9 @@
 // nearly every lane does useful FP64 work at every step.  A bus with more
 // than 32 neighbours is evaluated by a whole warp in a second kernel.  With
 // split rounds (a tuning choice) a warp takes half a round, two lanes per bus
-// taking alternate pairs, their exact partial sums merged by a shuffle.
+// taking alternate pairs, their exact partial sums merged by a shuffle.  The
+// launch has one one-warp CTA per round, or (ctas_per_sm > 0) a persistent
+// grid whose warps claim rounds from a counter.
 //
 // Determinism: every operation is an explicitly rounded intrinsic, the bus
 // sums of a bus with up to 32 neighbours are exact (so independent of the
