@@ -255,3 +255,37 @@ def test_large_bus_under_outages_and_modes(P, mode):
         jkw = dict(gen_mode=gm) if mode == EXTENDED else {}
         assert_tol(Vh[ctx.nnz_off[k]:ctx.nnz_off[k + 1]], oracle.jacobian(sk, xs[k], mode, **jkw)[2], f"J {k}")
     ctx.check_device()
+
+
+@pytest.mark.parametrize("mode", [REDUCED, EXTENDED])
+def test_branchless_buses_and_smallest_grids(P, mode):
+    """Degenerate grids: buses without any branch (a grid whose only branch is taken out by
+    the outage has no pair at all), a two-bus grid of a slack and a PV unit (one row in the
+    reduced formulation), alone and in one batch with a normal grid.  (A one-bus grid is
+    refused by pf_build's host validation.)"""
+    bare = gridgen.PowerSystem.build(2, branches=[(0, 1, 0.01, 0.1, 0.02)], slack=(0, 1.02, 0.1),
+                                     pvs=[(1, 0.2, 1.01)], shunts=[(0, 0.01, 0.2)])
+    islands = gridgen.PowerSystem.build(4, branches=[(0, 1, 0.01, 0.1, 0.02)], loads=[(2, 0.3, 0.1), (3, 0.2, 0.0)],
+                                        slack=(0, 1.0, 0.0), shunts=[(3, 0.0, 0.1)])
+    grids = [bare, islands, three_bus()]
+    ext = mode == EXTENDED
+    for g in grids[:2]:
+        ctx = P.Context(g, "extended" if ext else "reduced")
+        x_np = gridgen.perturbed_state(g, 2, ext)
+        F, v = ctx.residual_jacobian(torch.from_numpy(x_np).cuda())
+        rp, ci, jo = oracle.jacobian(g, x_np, mode)
+        assert F.numel() == len(rp) - 1 and v.numel() == len(ci)
+        assert_tol(F.cpu().numpy(), oracle.residual(g, x_np, mode), "F degenerate")
+        assert_tol(v.cpu().numpy(), jo, "J degenerate")
+        ctx.check_device()
+    inst = [(0, -1), (1, -1), (2, 3), (0, 0), (1, 0)]
+    ctx = P.Context(grids, "extended" if ext else "reduced", instances=inst)
+    xs = [gridgen.perturbed_state(grids[g], k + 1, ext) for k, (g, _) in enumerate(inst)]
+    x = torch.from_numpy(np.concatenate(xs)).cuda()
+    F, v = ctx.residual_jacobian(x)
+    fo, vo = ctx.f_off, ctx.nnz_off
+    for k, (g, out) in enumerate(inst):
+        sk = grids[g] if out < 0 else with_outage(grids[g], out)
+        assert_tol(F[fo[k]:fo[k + 1]].cpu().numpy(), oracle.residual(sk, xs[k], mode), f"F inst {k}")
+        assert_tol(v[vo[k]:vo[k + 1]].cpu().numpy(), oracle.jacobian(sk, xs[k], mode)[2], f"J inst {k}")
+    ctx.check_device()
