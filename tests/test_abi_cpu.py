@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -155,3 +156,18 @@ def test_batch_validation_rejects(lib, instances, expect):
     rc, msg, h = _build_batch(lib, [base_system()], instances)
     assert rc == 1 and expect in msg, (rc, msg)
     assert not h.value
+
+
+def test_package_refuses_to_load_without_the_library(tmp_path):
+    """No CPU fallback: a copy of the package without libpf.so fails to import."""
+    import shutil
+    src = os.path.join(ROOT, "paper_2011_11880_gb300")
+    dst = tmp_path / "paper_2011_11880_gb300"
+    dst.mkdir()
+    for f in os.listdir(src):
+        if f.endswith(".py"):
+            shutil.copy(os.path.join(src, f), dst / f)
+    r = subprocess.run([sys.executable, "-c", "import paper_2011_11880_gb300"], cwd=tmp_path,
+                       capture_output=True, text=True)
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "libpf.so not found" in r.stderr
