@@ -282,6 +282,22 @@ def oracle_pool(kind, n_inst, seconds):
     return m / el, m, el, cores
 
 
+def host_cpu():
+    """The host the oracle ran on: architecture, model name where the OS gives one, logical CPUs."""
+    import platform
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    cpus = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return f"{platform.machine()}{', ' + model if model else ''}, {cpus} logical CPUs"
+
+
 def launches_per_eval(ctx):
     """Kernels one evaluation of the context launches: k_phasor and k_fused, and
     k_fused_large where a bus has more than 32 neighbours."""
@@ -335,7 +351,7 @@ def run_reference(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD.format(N_STATES), "sample": f"{n} oracle F+J evaluations"},
         "e2e": {"value": rate, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "cpu_baseline": {"value": rate, "unit": "evals/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": rate, "unit": "evals/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
                          "sample": f"{n} F+J evaluations of the 70k grid ({el:.1f} s, numpy FP64, "
                                    f"one thread; requested {total_steps} steps bounded to {budget:.0f} s)"},
     }
@@ -525,7 +541,7 @@ def main():
     cpu = None
     if rank == 0:
         rate, n, el = time_oracle(sys_, states_np, args.cpu_seconds)
-        cpu = {"value": rate, "unit": "evals/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": rate, "unit": "evals/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
                "sample": f"{n} F+J evaluations of the 70k grid in {el:.1f} s (numpy FP64, one thread)"}
 
     line = {
@@ -640,7 +656,7 @@ def run_workload(args):
                     "hbm_view": {"algorithmic_bytes": bytes_alg, "achieved_gbs": bytes_alg / t / 1e9,
                                  "peak_gbs": peaks["hbm_gbs"], "frac": bytes_alg / t / 1e9 / peaks["hbm_gbs"],
                                  "peak_kind": peak_kind},
-                    "cpu_baseline": {"value": cpu_rate, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                    "cpu_baseline": {"value": cpu_rate, "unit": "evals/s", "cores": cores, "kind": "oracle", "host": host_cpu(),
                                      "sample": f"{m} instance F+J evaluations in {el:.1f} s, one process per "
                                                f"host core ({cores}), each cycling over its 1/{cores} of the "
                                                "2,304 instances"}})
@@ -675,7 +691,7 @@ def run_workload(args):
                     "config": {"workload": "70k-bus seeded synthetic grid, 64 Gaussian cotangents (seeds 4000+k), "
                                            "v^T dF/d(theta, V, P_inj, Q_inj, r, x, b_c, tau), one call",
                                "output_bytes": out_bytes},
-                    "cpu_baseline": {"value": m / el, "unit": "cotangents/s", "cores": 1, "kind": "oracle",
+                    "cpu_baseline": {"value": m / el, "unit": "cotangents/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
                                      "sample": f"{m} oracle VJPs in {el:.1f} s"}})
     elif args.workload == "newton":
         # flat-start Newton power flow (F, J, convergence test and update in this library's
@@ -739,7 +755,7 @@ def run_workload(args):
                                          "device after it; later solves reuse it) and, for comparison, "
                                          "cuSOLVER sparse QR every iteration"},
                     "runs": runs,
-                    "cpu_baseline": {"value": el / max(m, 1), "unit": "s", "cores": 1, "kind": "oracle",
+                    "cpu_baseline": {"value": el / max(m, 1), "unit": "s", "cores": 1, "kind": "oracle", "host": host_cpu(),
                                      "sample": f"{m} dense-Newton solves of the 2,000-bus grid in {el:.1f} s "
                                                "(dense LU)"}})
     else:
@@ -776,7 +792,7 @@ def run_workload(args):
                                            "PV output x U[0.5,1.5], load x U[0.8,1.2] as injection overrides, "
                                            "F + J then v^T dF/d(x, P_inj, Q_inj) with v = F, one captured graph",
                                "buses": int(sum(gg.n_bus for gg in grids)), "tuning": tuning},
-                    "cpu_baseline": {"value": cpu_rate, "unit": "iterations/s", "cores": cores, "kind": "oracle",
+                    "cpu_baseline": {"value": cpu_rate, "unit": "iterations/s", "cores": cores, "kind": "oracle", "host": host_cpu(),
                                      "sample": f"{m} instance iterations in {el:.1f} s, one process per host core "
                                                f"({cores}), each cycling over its 1/{cores} of the 4,096 "
                                                "instances"}})
