@@ -45,6 +45,9 @@
  *     stream).  Evaluation calls are asynchronous on that stream, allocate
  *     nothing and may be captured in a CUDA graph; device buffers passed to
  *     them must stay valid until the stream reaches the call.
+ *   - A context belongs to the device that was current when it was built.
+ *     Every call on it makes that device current for its duration and
+ *     restores the caller's device afterwards; `stream` must belong to it.
  *   - Every function returns PF_OK (0) or an error code; pf_last_error()
  *     returns a message for the calling thread's last failure.
  */

@@ -140,6 +140,7 @@ int pf_build(const pf_system *sys, int32_t formulation, void *stream, pf_ctx **o
 
 void pf_destroy(pf_ctx *ctx) {
   if (!ctx) return;
+  const pf::DeviceGuard on_device(ctx->c.device);
   cudaDeviceSynchronize();
   free_ctx(ctx);
 }
@@ -183,6 +184,7 @@ int pf_grid_sizes(const pf_ctx *ctx, int32_t grid, int32_t *n_f, int32_t *nnz, i
 
 int pf_pattern(const pf_ctx *ctx, int32_t grid, int32_t *rowptr, int32_t *colind) {
   PF_TRY(check_grid(ctx, grid));
+  PF_ON_DEVICE(ctx->c);
   const pf::Ctx &c = ctx->c;
   if (rowptr) PF_TRY(copy_out(rowptr, c.rowptr + c.grid_row_off[grid], (size_t)c.grid_nf[grid] + 1));
   if (colind) PF_TRY(copy_out(colind, c.colind + c.grid_nnz_off[grid], (size_t)c.grid_nnz[grid]));
@@ -191,6 +193,7 @@ int pf_pattern(const pf_ctx *ctx, int32_t grid, int32_t *rowptr, int32_t *colind
 
 int pf_incidence(const pf_ctx *ctx, int32_t grid, int32_t *ptr, int32_t *code, int32_t *other) {
   PF_TRY(check_grid(ctx, grid));
+  PF_ON_DEVICE(ctx->c);
   const pf::Ctx &c = ctx->c;
   const int64_t b0 = c.grid_bus_off[grid], b1 = c.grid_bus_off[grid + 1];
   const int64_t l0 = c.grid_br_off[grid], l1 = c.grid_br_off[grid + 1];
@@ -218,6 +221,7 @@ int pf_incidence(const pf_ctx *ctx, int32_t grid, int32_t *ptr, int32_t *code, i
 
 int pf_contributions(const pf_ctx *ctx, int32_t grid, int64_t *ptr, int32_t *src) {
   PF_TRY(check_grid(ctx, grid));
+  PF_ON_DEVICE(ctx->c);
   const pf::Ctx &c = ctx->c;
   if (ptr) PF_TRY(copy_out(ptr, c.contrib_ptr + c.grid_cptr_off[grid], (size_t)c.grid_nnz[grid] + 1));
   if (src)
@@ -228,12 +232,14 @@ int pf_contributions(const pf_ctx *ctx, int32_t grid, int64_t *ptr, int32_t *src
 
 int pf_eval(pf_ctx *ctx, const double *x, const pf_overrides *ov, double *F, double *vals, void *stream) {
   if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
+  PF_ON_DEVICE(ctx->c);
   return pf::launch_eval(ctx->c, x, ov, F, vals, as_stream(stream));
 }
 
 int pf_eval_stage(pf_ctx *ctx, int32_t stage, const double *x, const pf_overrides *ov, double *F, double *vals,
                   void *stream) {
   if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
+  PF_ON_DEVICE(ctx->c);
   if (stage != PF_STAGE_PHASOR && stage != PF_STAGE_FUSED)
     return fail(PF_ERR_INVALID, "stage must be PF_STAGE_PHASOR or PF_STAGE_FUSED");
   return pf::launch_eval_stages(ctx->c, stage, x, ov, F, vals, as_stream(stream));
@@ -256,6 +262,7 @@ int pf_residual_jacobian(pf_ctx *ctx, const double *x, double *F, double *vals, 
 int pf_residual_jacobian_host(pf_ctx *ctx, const double *x_host, double *F_host, double *vals_host,
                               void *stream) {
   if (!ctx || !x_host) return fail(PF_ERR_INVALID, "NULL argument");
+  PF_ON_DEVICE(ctx->c);
   pf::Ctx &c = ctx->c;
   cudaStream_t s = as_stream(stream);
   if (!c.stage_x) {
@@ -317,11 +324,13 @@ int pf_residual_jacobian_host(pf_ctx *ctx, const double *x_host, double *F_host,
 int pf_vjp(pf_ctx *ctx, const double *x, const pf_overrides *ov, const double *v, int32_t n_cot,
            const pf_grads *g, void *stream) {
   if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
+  PF_ON_DEVICE(ctx->c);
   return pf::launch_vjp(ctx->c, x, ov, v, n_cot, g, as_stream(stream));
 }
 
 int pf_newton(pf_ctx *ctx, double *x, double tol, int32_t max_iter, void *stream, pf_newton_info *info) {
   if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
+  PF_ON_DEVICE(ctx->c);
   return pf::newton(ctx->c, x, tol, max_iter, as_stream(stream), info);
 }
 
@@ -329,6 +338,7 @@ int pf_newton_qlim(pf_ctx *ctx, double *x, const double *q_min, const double *q_
                    double *gen_qlim, double tol, int32_t max_iter, int32_t max_rounds, void *stream,
                    pf_newton_info *info, int32_t *rounds) {
   if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
+  PF_ON_DEVICE(ctx->c);
   int r = 0;
   PF_TRY(pf::newton_qlim(ctx->c, x, q_min, q_max, gen_mode, gen_qlim, tol, max_iter, max_rounds,
                          as_stream(stream), info, &r));
@@ -338,11 +348,13 @@ int pf_newton_qlim(pf_ctx *ctx, double *x, const double *q_min, const double *q_
 
 int pf_fdlf(pf_ctx *ctx, double *x, double tol, int32_t max_iter, void *stream, pf_newton_info *info) {
   if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
+  PF_ON_DEVICE(ctx->c);
   return pf::fdlf(ctx->c, x, tol, max_iter, as_stream(stream), info);
 }
 
 int pf_set_newton_solver(pf_ctx *ctx, int32_t solver) {
   if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
+  PF_ON_DEVICE(ctx->c);
   if (solver != PF_SOLVER_LU && solver != PF_SOLVER_QR)
     return fail(PF_ERR_INVALID, "solver must be PF_SOLVER_LU or PF_SOLVER_QR");
   ctx->c.newton_solver = solver;
@@ -351,11 +363,13 @@ int pf_set_newton_solver(pf_ctx *ctx, int32_t solver) {
 
 int pf_mismatch_norm(pf_ctx *ctx, const double *F, double *norms, void *stream) {
   if (!ctx || !F || !norms) return fail(PF_ERR_INVALID, "NULL argument");
+  PF_ON_DEVICE(ctx->c);
   return pf::newton_norms(ctx->c, F, norms, as_stream(stream));
 }
 
 int pf_newton_update(pf_ctx *ctx, double *x, const double *dx, void *stream) {
   if (!ctx || !x || !dx) return fail(PF_ERR_INVALID, "NULL argument");
+  PF_ON_DEVICE(ctx->c);
   return pf::newton_update(ctx->c, x, dx, as_stream(stream));
 }
 
@@ -367,6 +381,7 @@ int pf_get_tuning(const pf_ctx *ctx, pf_tuning *t) {
 
 int pf_set_tuning(pf_ctx *ctx, const pf_tuning *t, void *stream) {
   if (!ctx || !t) return fail(PF_ERR_INVALID, "NULL argument");
+  PF_ON_DEVICE(ctx->c);
   if (t->tile_inc < pf::kMinTileInc || t->tile_inc > pf::kMaxTileInc || t->tile_inc % 32 != 0)
     return fail(PF_ERR_INVALID, "tile_inc must be 32, 64, 96 or 128");
   if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return fail(PF_ERR_INVALID, "ctas_per_sm must be in [0, 32]");
@@ -390,6 +405,7 @@ int pf_set_tuning(pf_ctx *ctx, const pf_tuning *t, void *stream) {
 
 int pf_autotune(pf_ctx *ctx, const double *x, double *F, double *vals, void *stream, pf_tuning *chosen) {
   if (!ctx || !x) return fail(PF_ERR_INVALID, "NULL argument");
+  PF_ON_DEVICE(ctx->c);
   cudaStream_t s = as_stream(stream);
   const int tiles[] = {32, 64, 96, 128};
   const int ctas[] = {0, 8, 16};
@@ -440,6 +456,7 @@ int pf_autotune(pf_ctx *ctx, const double *x, double *F, double *vals, void *str
 int pf_autotune_cache(pf_ctx *ctx, const char *path, const double *x, double *F, double *vals, void *stream,
                       pf_tuning *chosen, int32_t *from_cache) {
   if (!ctx || !path) return fail(PF_ERR_INVALID, "NULL argument");
+  PF_ON_DEVICE(ctx->c);
   if (from_cache) *from_cache = 0;
   const std::string key = tuning_key(ctx->c);
   if (key.empty()) return fail(PF_ERR_CUDA, "cannot query the device for the tuning key");
@@ -475,11 +492,13 @@ int pf_autotune_cache(pf_ctx *ctx, const char *path, const double *x, double *F,
 
 int pf_sincos(pf_ctx *ctx, const double *theta, int64_t n, double *cos_out, double *sin_out, void *stream) {
   if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
+  PF_ON_DEVICE(ctx->c);
   return pf::launch_sincos(ctx->c, theta, n, cos_out, sin_out, as_stream(stream));
 }
 
 int pf_voltage_records(pf_ctx *ctx, const double *x, double *rec, void *stream) {
   if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
+  PF_ON_DEVICE(ctx->c);
   if (!x || !rec) return fail(PF_ERR_INVALID, "x or rec is NULL");
   const cudaStream_t s = as_stream(stream);
   PF_TRY(pf::launch_phasor(ctx->c.v, ctx->c.num_sms, x, s));
@@ -506,6 +525,7 @@ const char *pf_last_error(void) { return pf::g_last_error.c_str(); }
 
 int pf_check_device(pf_ctx *ctx, void *stream) {
   if (!ctx) return fail(PF_ERR_INVALID, "ctx is NULL");
+  PF_ON_DEVICE(ctx->c);
   int32_t h = 0;
   cudaStream_t s = as_stream(stream);
   PF_CUDA_TRY(cudaMemcpyAsync(&h, ctx->c.v.dev_error, sizeof(int32_t), cudaMemcpyDeviceToHost, s));

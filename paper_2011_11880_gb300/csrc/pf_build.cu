@@ -1396,6 +1396,7 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
 
   int dev = 0;
   PF_CUDA_TRY(cudaGetDevice(&dev));
+  c.device = dev;
   PF_CUDA_TRY(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, dev));
 
   // (cos, sin) of i pi / 16384 for the table-driven phasor routine, evaluated in

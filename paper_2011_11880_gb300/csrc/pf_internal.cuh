@@ -145,6 +145,7 @@ struct View {
 
 struct Ctx {
   View v{};
+  int device = 0;                  // the device current at pf_build: every call runs on it
   int num_sms = kNumSMsDefault;
   pf_tuning tuning{64, 0, 0};
   int max_degree = 0, max_group = 0;
@@ -191,6 +192,29 @@ struct Ctx {
 
   std::vector<void *> allocations;
 };
+
+// Makes a context's device current for the span of a call and restores the
+// caller's device afterwards (nothing is switched when it is current already).
+struct DeviceGuard {
+  int prev = -1;
+  int status = 0;                  // the cudaError_t of the switch
+  explicit DeviceGuard(int dev) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != dev) {
+      status = (int)cudaSetDevice(dev);
+      if (status == 0) prev = cur;
+    }
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  DeviceGuard(const DeviceGuard &) = delete;
+  DeviceGuard &operator=(const DeviceGuard &) = delete;
+};
+
+#define PF_ON_DEVICE(ctxref)                                                       \
+  const ::pf::DeviceGuard pf_device_guard_((ctxref).device);                       \
+  if (pf_device_guard_.status) return ::pf::fail(PF_ERR_CUDA, "cannot make the context's device current")
 
 // Host-side fault injection for tests: with PF_FAIL_ALLOC=<n> in the
 // environment when a build starts, the n-th device allocation of that build

@@ -53,6 +53,7 @@ int static_scratch(double2 **out) {
 extern "C" int pf_residual_jacobian_static(pf_ctx *ctx, const double *x, double *F, double *vals, void *stream) {
   pf::Ctx *c = pf::ctx_of(ctx);
   if (!c) return pf::fail(PF_ERR_INVALID, "ctx is NULL");
+  PF_ON_DEVICE(*c);
   if (!x) return pf::fail(PF_ERR_INVALID, "x is NULL");
   if (c->v.n_bus_inst > pf::kStaticPhasorBuses)
     return pf::fail(PF_ERR_UNSUPPORTED,
