@@ -249,14 +249,23 @@ def oracle_pool(kind, n_inst, seconds):
     seconds, processes)."""
     import multiprocessing as mp
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
-    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        os.environ[var] = "1"                       # one thread per process
+    threads = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {var: os.environ.get(var) for var in threads}
     ctx = mp.get_context("spawn")
     barrier, queue = ctx.Barrier(cores), ctx.Queue()
     procs = [ctx.Process(target=_oracle_share, args=(kind, list(range(w, n_inst, cores)), seconds, barrier, queue))
              for w in range(cores)]
-    for pr in procs:
-        pr.start()
+    try:
+        for var in threads:
+            os.environ[var] = "1"                   # one thread per process (read by the children)
+        for pr in procs:
+            pr.start()
+    finally:
+        for var, val in saved.items():
+            if val is None:
+                os.environ.pop(var, None)
+            else:
+                os.environ[var] = val
     import queue as queue_mod
     res, deadline = [], time.time() + seconds + 900
     try:
