@@ -411,6 +411,16 @@ PF_API int pf_sincos(pf_ctx *ctx, const double *theta, int64_t n, double *cos_ou
  * caller-owned.  Asynchronous on `stream`. */
 PF_API int pf_voltage_records(pf_ctx *ctx, const double *x, double *rec, void *stream);
 
+/* Measurement helper (not part of the method): the FP64 fused multiply-add
+ * rate of `device`, in G operations/s (one FMA counts one operation), from
+ * three timed launches of a kernel that keeps 2,048 threads per SM on eight
+ * independent FMA chains each (the fastest of the three is reported; *ms, if
+ * not NULL, receives its duration).  The denominator of the FP64 fractions
+ * the benchmark reports beside the evaluation's roofline.  Allocates and
+ * frees a small device buffer; synchronises `stream`.  Errors: PF_ERR_INVALID
+ * for a NULL gops, PF_ERR_CUDA. */
+PF_API int pf_fp64_peak(int32_t device, double *gops, double *ms, void *stream);
+
 /* ---- errors --------------------------------------------------------------------- */
 /* Test hook: with the environment variable PF_FAIL_ALLOC=<n> set when
  * pf_build / pf_build_batch starts, the n-th device allocation of that build

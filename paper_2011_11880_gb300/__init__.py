@@ -13,7 +13,7 @@ from ._lib import PFError, load as _load
 
 _load()
 
-from .context import Context, Dims  # noqa: E402
+from .context import Context, Dims, fp64_peak  # noqa: E402
 from .autograd import PFResidual, residual  # noqa: E402
 
-__all__ = ["Context", "Dims", "PFError", "PFResidual", "residual"]
+__all__ = ["Context", "Dims", "PFError", "PFResidual", "fp64_peak", "residual"]

@@ -104,6 +104,7 @@ SIGNATURES = {
                                     P(PfTuning), P(c_int32)]),
     "pf_sincos": (c_int32, [c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]),
     "pf_voltage_records": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "pf_fp64_peak": (c_int32, [c_int32, P(ctypes.c_double), P(ctypes.c_double), c_void_p]),
     "pf_error_string": (ctypes.c_char_p, [c_int32]),
     "pf_last_error": (ctypes.c_char_p, []),
     "pf_check_device": (c_int32, [c_void_p, c_void_p]),

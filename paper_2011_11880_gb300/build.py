@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpf.so")
 SOURCES = ["pf_api.cu", "pf_build.cu", "pf_eval.cu", "pf_adjoint.cu", "pf_sort_scan.cu", "pf_noalloc.cu",
-           "pf_newton.cu"]
+           "pf_newton.cu", "pf_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

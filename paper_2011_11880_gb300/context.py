@@ -371,3 +371,13 @@ class Context:
 
     def check_device(self, stream=None):
         check(self._lib.pf_check_device(self._h, _stream(stream)), "pf_check_device")
+
+
+def fp64_peak(device: int = 0, stream=None) -> tuple[float, float]:
+    """The device's FP64 FMA rate (G operations/s) and the timed launch's
+    duration (ms), measured by the library's pf_fp64_peak."""
+    gops, ms = ctypes.c_double(), ctypes.c_double()
+    with torch.cuda.device(device):
+        check(_lib.load().pf_fp64_peak(int(device), ctypes.byref(gops), ctypes.byref(ms), _stream(stream)),
+              "pf_fp64_peak")
+    return gops.value, ms.value

@@ -547,7 +547,7 @@ int launch_vjp(Ctx &c, const double *x, const pf_overrides *ov, const double *v,
   const int tb = 256;
   const int64_t cap_blocks = (int64_t)c.num_sms * 16;
   // E = V (cos, sin), V and 1/V of every bus: the forward kernels' per-bus records
-  PF_TRY(launch_phasor(c.v, c.num_sms, x, s));
+  PF_TRY(launch_phasor(c.v, c.num_sms, x, s, false));
   VjpArgs a{};
   a.x = x; a.v = v; a.n_cot = n_cot; a.n_f = c.n_f; a.n_x = c.n_x;
   a.gb = c.v.inc_gb; a.ac = c.v.inc_ac; a.hat = c.v.bus_hat;

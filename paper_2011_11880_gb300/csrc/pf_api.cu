@@ -501,7 +501,7 @@ int pf_voltage_records(pf_ctx *ctx, const double *x, double *rec, void *stream) 
   PF_ON_DEVICE(ctx->c);
   if (!x || !rec) return fail(PF_ERR_INVALID, "x or rec is NULL");
   const cudaStream_t s = as_stream(stream);
-  PF_TRY(pf::launch_phasor(ctx->c.v, ctx->c.num_sms, x, s));
+  PF_TRY(pf::launch_phasor(ctx->c.v, ctx->c.num_sms, x, s, false));
   PF_CUDA_TRY(cudaMemcpyAsync(rec, ctx->c.v.phasor, sizeof(double) * 4 * (size_t)ctx->c.v.n_bus_inst,
                               cudaMemcpyDeviceToDevice, s));
   return PF_OK;

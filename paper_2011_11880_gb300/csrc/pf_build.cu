@@ -9,6 +9,7 @@
 //   * per-end branch coefficients and per-bus sums of the constant terms.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -644,7 +645,7 @@ __global__ void k_round_base(const int64_t *S, int64_t n_rounds, int4 *desc, int
 // one thread per (round, lane): the slots of the lane's bus, one per group of
 // parallel branches (pair of buses) in incidence order, then padding
 __global__ void k_slot_fill(View v, int64_t n_rounds, const int4 *desc, const int32_t *rbus, int4 *smeta,
-                            int4 *spos) {
+                            int4 *spos, int4 *sidx) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 32 * n_rounds) return;
   const int64_t r = t >> 5;
@@ -659,7 +660,13 @@ __global__ void k_slot_fill(View v, int64_t n_rounds, const int4 *desc, const in
       if (len == 0) continue;
       const int64_t q = (int64_t)d.x + 32 * j + l;
       smeta[q] = make_int4(v.inc_other[e], len, v.inc_code[e], e);
-      spos[q] = v.inc_pos[e];
+      const int4 p = v.inc_pos[e];
+      spos[q] = p;
+      // the P and Q rows of a bus have the same columns: one in-row offset each for theta_k, V_k
+      const int32_t bp = v.base_p[b], bq = v.base_q[b];
+      const int32_t ot = p.x >= 0 ? p.x - bp : (p.z >= 0 ? p.z - bq : -1);
+      const int32_t ov = p.y >= 0 ? p.y - bp : (p.w >= 0 ? p.w - bq : -1);
+      sidx[q] = make_int4(v.inc_other[e], (ot & 0xffff) | (ov << 16), len, len == 1 ? v.inc_code[e] : e);
       ++j;
     }
   }
@@ -667,6 +674,7 @@ __global__ void k_slot_fill(View v, int64_t n_rounds, const int4 *desc, const in
     const int64_t q = (int64_t)d.x + 32 * j + l;
     smeta[q] = make_int4(0, -1, 0, 0);
     spos[q] = make_int4(-1, -1, -1, -1);
+    sidx[q] = make_int4(0, -1, -1, 0);
   }
 }
 
@@ -745,6 +753,32 @@ __global__ void k_slot_coeff(View v, int64_t n_slots, const int4 *smeta, const d
     sac[q] = make_double2(0.0, 0.0);
     sgbm[q] = make_double2(0.0, 0.0);
   }
+}
+
+// per slot: the larger of sum |G_i| and sum |B_i| over its group's ends (any
+// subset of the group under a mask stays below it), maximised over all slots
+// into *mx (the bit pattern of a non-negative double orders as an integer)
+__global__ void k_slot_absmax(int64_t n_slots, const int4 *smeta, const double2 *gb, unsigned long long *mx) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_slots) return;
+  const int4 m = smeta[q];
+  if (m.y <= 0) return;
+  double sg = 0.0, sb = 0.0;
+  for (int32_t i = 0; i < m.y; ++i) {
+    const double2 gi = gb[m.w + i];
+    sg += fabs(gi.x);
+    sb += fabs(gi.y);
+  }
+  const double a = fmax(sg, sb);
+  if (a > 0.0) atomicMax(mx, (unsigned long long)__double_as_longlong(isfinite(a) ? a : 0x1p1000));
+}
+
+// per slot: its merged (G, B) in the fixed point of the evaluation kernels
+__global__ void k_slot_fix(int64_t n_slots, const int4 *smeta, const double2 *sgb, double scale, int4 *sgbx) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_slots) return;
+  const double2 g = sgb[q];
+  sgbx[q] = smeta[q].y > 0 ? coef_limbs(to_fix(g.x, scale), to_fix(g.y, scale)) : make_int4(0, 0, 0, 0);
 }
 
 template <class T>
@@ -856,10 +890,11 @@ int build_rounds(Ctx &c, cudaStream_t s) {
   if (herr[0]) return fail(PF_ERR_UNSUPPORTED, "more than 2^31 evaluation slots");
   const int64_t NS = total[0];
   c.n_slots = NS;
-  int4 *smeta, *spos, *m1, *m2;
+  int4 *smeta, *spos, *sidx, *m1, *m2;
   double2 *sgb, *sac, *sgbm, *rh, *ri;
   PF_TRY(dev_alloc(c, &smeta, NS));
   PF_TRY(dev_alloc(c, &spos, NS));
+  PF_TRY(dev_alloc(c, &sidx, NS));
   PF_TRY(dev_alloc(c, &sgb, NS));
   PF_TRY(dev_alloc(c, &sac, NS));
   PF_TRY(dev_alloc(c, &sgbm, NS));
@@ -872,12 +907,39 @@ int build_rounds(Ctx &c, cudaStream_t s) {
   PF_TRY(dev_alloc(c, &c.ov_slot_ac, NS));
   PF_TRY(dev_alloc(c, &c.ov_rbus_hat, 32 * R));
   if (NS > 0) {
-    k_slot_fill<<<nblk(32 * R), TB, 0, s>>>(v, R, desc, rbus, smeta, spos);
+    k_slot_fill<<<nblk(32 * R), TB, 0, s>>>(v, R, desc, rbus, smeta, spos, sidx);
     k_slot_coeff<<<nblk(NS), TB, 0, s>>>(v, NS, smeta, v.inc_gb, v.inc_ac, sgb, sac, sgbm);
     PF_CUDA_TRY(cudaGetLastError());
   }
   k_rbus_fill<<<nblk(32 * R), TB, 0, s>>>(v, 32 * R, rbus, v.bus_hat, m1, m2, rh, ri);
   PF_CUDA_TRY(cudaGetLastError());
+  // fixed-point coefficients: 2^coef_log2 bounds |G|, |B| over every group
+  // (capped at kMaxCoefLog2; larger coefficients are marked kBadFix)
+  {
+    unsigned long long *mx;
+    PF_TRY(tmp.alloc(&mx, 1));
+    PF_CUDA_TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s));
+    if (NS > 0) {
+      k_slot_absmax<<<nblk(NS), TB, 0, s>>>(NS, smeta, v.inc_gb, mx);
+      PF_CUDA_TRY(cudaGetLastError());
+    }
+    std::vector<unsigned long long> hm = to_host(mx, 1, s, &rc);
+    if (rc) return rc;
+    double m = 0.0;
+    std::memcpy(&m, &hm[0], sizeof(double));
+    int lg = 1;
+    while (lg < kMaxCoefLog2 && !(m < std::ldexp(1.0, lg))) ++lg;
+    v.coef_log2 = lg;
+    v.coef_scale = std::ldexp(1.0, 59 - lg);
+    int4 *sgbx;
+    PF_TRY(dev_alloc(c, &sgbx, NS));
+    PF_TRY(dev_alloc(c, &c.ov_slot_gbx, NS));
+    if (NS > 0) {
+      k_slot_fix<<<nblk(NS), TB, 0, s>>>(NS, smeta, sgb, v.coef_scale, sgbx);
+      PF_CUDA_TRY(cudaGetLastError());
+    }
+    v.slot_gbx = sgbx;
+  }
   v.grid_round_off = d_round_off;
   v.round_desc = desc;
   v.rbus = rbus;
@@ -887,6 +949,7 @@ int build_rounds(Ctx &c, cudaStream_t s) {
   v.rbus_inj = ri;
   v.slot_meta = smeta;
   v.slot_pos = spos;
+  v.slot_idx = sidx;
   v.slot_gb = sgb;
   v.slot_ac = sac;
   v.slot_gbm = sgbm;
@@ -928,6 +991,8 @@ int permute_overrides(Ctx &c, cudaStream_t s) {
   if (c.n_slots > 0) {
     k_slot_coeff<<<nblk(c.n_slots), TB, 0, s>>>(c.v, c.n_slots, c.v.slot_meta, c.ov_gb, c.ov_ac, c.ov_slot_gb,
                                                 c.ov_slot_ac, c.ov_slot_gbm);
+    k_slot_fix<<<nblk(c.n_slots), TB, 0, s>>>(c.n_slots, c.v.slot_meta, c.ov_slot_gb, c.v.coef_scale,
+                                              c.ov_slot_gbx);
     PF_CUDA_TRY(cudaGetLastError());
   }
   k_rbus_fill<<<nblk(32 * c.n_rounds), TB, 0, s>>>(c.v, 32 * c.n_rounds, c.v.rbus, c.ov_hat, nullptr, nullptr,

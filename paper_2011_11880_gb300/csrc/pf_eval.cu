@@ -19,11 +19,16 @@
 //     dF_P/dt_o = S_Y,   dF_Q/dt_o = -S_X,
 //     dF_P/dV_o = (2 V_o^2 A^ - S_X) / V_o,   dF_Q/dV_o = -(2 V_o^2 C^ + S_Y) / V_o,
 // where A^ = sum A + shunt g and C^ = sum C + shunt b.  1/V is formed once
-// per bus by k_phasor.  Per pair of connected buses (parallel branches merged
-// into one end with their coefficients summed): 8 FP64 operations for u, w,
-// X, Y, no operation for a theta-column J value (a sign flip on the integer
-// pipe) and one multiply for a V-column J value; the sums S_X, S_Y are exact,
-// in 128-bit fixed point on the integer pipe, rounded once.
+// per bus by k_phasor_fx.  GB300 issues FP64 arithmetic at 2 operations per
+// clock per SM, so the pair terms are formed in fixed point on the integer
+// pipe instead (see "Fixed-point arithmetic of the pair terms" below): the
+// unit phasors (cos t, sin t), V and the merged coefficients (G, B) of a pair
+// of connected buses (parallel branches merged) as 30-bit limbs, products from
+// 32 x 32 -> 64-bit multiplies, the bus sums S_X, S_Y exact in 128 bits; each
+// J value is rounded once to double (two per pair by the FP64 pipe's
+// conversion, two on the integer pipe).  The per-bus rows (F, the diagonal
+// values) stay in FP64: 9 operations per bus.  A bus whose inputs fall outside
+// the fixed-point ranges is evaluated in FP64 from x (the form above).
 //
 // Work decomposition.  The buses of each grid are sorted by their number of
 // neighbours and cut into rounds of 32; one warp evaluates one round, one bus
@@ -31,16 +36,17 @@
 // each pair's terms, writes the pair's four off-diagonal J entries, keeps the
 // bus sums in registers, and finally writes the bus's F rows and diagonal J
 // entries.  Because the buses of a round have the same number of pairs,
-// nearly every lane does useful FP64 work at every step.  A bus with more
+// nearly every lane does useful work at every step.  A bus with more
 // than 32 neighbours is evaluated by a whole warp in a second kernel.  With
 // split rounds (a tuning choice) a warp takes half a round, two lanes per bus
 // taking alternate pairs, their exact partial sums merged by a shuffle.  The
 // launch has one one-warp CTA per round, or (ctas_per_sm > 0) a persistent
 // grid whose warps claim rounds from a counter.
 //
-// Determinism: every operation is an explicitly rounded intrinsic, the bus
-// sums of a bus with up to 32 neighbours are exact (so independent of the
-// order of the terms), and every other sum runs in a fixed order -- a group's
+// Determinism: every operation is an explicitly rounded intrinsic or exact
+// integer arithmetic, the bus sums of a bus with up to 32 neighbours are exact
+// (so independent of the order of the terms), and every other sum runs in a
+// fixed order -- a group's
 // coefficients in incidence-list order, the FP64 fallback of the bus sums in
 // list order, lane-strided partial sums over the ends combined by a fixed
 // butterfly for a larger bus -- so results are bit-identical run to run,
@@ -115,15 +121,10 @@ struct RectV {
   double rv;
 };
 
-__device__ __forceinline__ RectV rect_voltage(double t, double sv, const longlong2 *__restrict__ tabf) {
-  RectV o;
-  if ((__double2hiint(t) & 0x7fffffff) >= 0x40400000 || (__double2hiint(sv) & 0x7ff00000) >= 0x7d000000) {
-    double sn, cs;
-    sincos(t, &sn, &cs);
-    o.E = make_double2(__dmul_rn(sv, cs), __dmul_rn(sv, sn));
-    o.rv = __drcp_rn(sv);
-    return o;
-  }
+// (cos t, sin |t|) 2^62 for |t| < 32 by the table-driven routine above (the
+// fixed-point values before any rounding to double; the caller applies the
+// sign of t to the sine).
+__device__ __forceinline__ longlong2 unit_fix_small(double t, const longlong2 *__restrict__ tabf) {
   const unsigned long long tb = (unsigned long long)__double_as_longlong(t);
   const int et = (int)((tb >> 52) & 0x7ff);
   const unsigned long long mt = (tb & 0xfffffffffffffULL) | (et ? (1ULL << 52) : 0ULL);
@@ -147,88 +148,202 @@ __device__ __forceinline__ RectV rect_voltage(double t, double sv, const longlon
   const int h32 = (int)(H >> 17), c32 = (int)(Tf.x >> 32), s32 = (int)(Tf.y >> 32);
   const long long dc = -(((long long)c32 * h32) >> 15) - __mul64hi(Tf.y, SR);          // 2^73
   const long long ds = __mul64hi(Tf.x, SR) - (((long long)s32 * h32) >> 15);
-  const double ct = fix62_to_double(Tf.x + (dc >> 11));                              // cos t
-  const double st = fix62_to_double(Tf.y + (ds >> 11));                              // sin |t|
-  const double ey = __dmul_rn(sv, st);
-  o.E = make_double2(__dmul_rn(sv, ct), (long long)tb < 0 ? neg(ey) : ey);          // sin is odd
+  return make_longlong2(Tf.x + (dc >> 11), Tf.y + (ds >> 11));                      // (cos t, sin |t|)
+}
+
+// Arguments the fixed-point routine does not take: |t| >= 32 or t not finite
+// (or a voltage too large for the routine's FP64 products).
+__device__ __forceinline__ bool phasor_slow(double t, double sv) {
+  return (__double2hiint(t) & 0x7fffffff) >= 0x40400000 || (__double2hiint(sv) & 0x7ff00000) >= 0x7d000000;
+}
+
+__device__ __forceinline__ RectV rect_voltage(double t, double sv, const longlong2 *__restrict__ tabf) {
+  RectV o;
+  if (phasor_slow(t, sv)) {
+    double sn, cs;
+    sincos(t, &sn, &cs);
+    o.E = make_double2(__dmul_rn(sv, cs), __dmul_rn(sv, sn));
+    o.rv = __drcp_rn(sv);
+    return o;
+  }
+  const longlong2 u = unit_fix_small(t, tabf);
+  const double ey = __dmul_rn(sv, fix62_to_double(u.y));
+  o.E = make_double2(__dmul_rn(sv, fix62_to_double(u.x)), __double2hiint(t) < 0 ? neg(ey) : ey);   // sin is odd
   o.rv = recip(sv);
   return o;
 }
 
-// Per bus of every instance: the voltage in rectangular form
-// E = V (cos theta, sin theta), then V and 1/V, side by side in one 32-byte
-// record, so the fused kernel's gathers of a neighbour's data hit L2 in one
-// sector.  A voltage below 2^-500 in magnitude (a dead bus) is replaced by
+// The voltage in rectangular form E = V (cos theta, sin theta), then V and
+// 1/V.  A voltage below 2^-500 in magnitude (a dead bus) is replaced by
 // 2^-600 in E and 1/V: every term then carries a factor of at most 2^-600
 // where it should carry V (terms that are zero to far below any tolerance),
 // and the dF/dV values, which divide that factor out again, stay exact.
 constexpr double kDeadV = 0x1p-600;
 
-// One thread per instance-bus; the block looks up the instances of its
-// first and last bus once, a thread searches only between them.
-__global__ void __launch_bounds__(256) k_phasor(View v, const double *__restrict__ x) {
-  // Let the fused kernel start launching; it waits for this grid's results.
-  cudaTriggerProgrammaticLaunchCompletion();
-  __shared__ int s_inst[2];
-  const int64_t q0 = v.bus_inst_begin + (int64_t)blockIdx.x * blockDim.x;
-  const int64_t q = q0 + threadIdx.x;
+__device__ __forceinline__ double dead_sub(double vm) {
+  return (__double2hiint(vm) & 0x7ff00000) < 0x20b00000 ? kDeadV : vm;   // |V| < 2^-500
+}
+
+// The instance of instance-bus q; the block looks up the instances of its
+// first and last bus once (s_inst), a thread searches only between them.
+__device__ __forceinline__ int phasor_instance(const View &v, int64_t q, const int *s_inst) {
+  const int i0 = v.n_inst > 1 ? s_inst[0] : 0, i1 = v.n_inst > 1 ? s_inst[1] : 0;
+  return i0 == i1 ? i0 : i0 + find_segment(v.inst_bus_off + i0, i1 - i0 + 1, q);
+}
+
+__device__ __forceinline__ void phasor_block_instances(const View &v, int64_t q0, int *s_inst) {
   if (v.n_inst > 1 && threadIdx.x < 2) {
     const int64_t key = threadIdx.x == 0 ? q0 : min(q0 + (int64_t)blockDim.x, v.n_bus_inst) - 1;
     s_inst[threadIdx.x] = find_segment(v.inst_bus_off, v.n_inst, key);
   }
   __syncthreads();
+}
+
+// FP64 records for the adjoint kernels, one thread per instance-bus:
+// (V cos theta, V sin theta) and (V, 1/V) side by side in 32 bytes, so that a
+// gather of a neighbour's data hits one sector.
+__global__ void __launch_bounds__(256) k_phasor(View v, const double *__restrict__ x) {
+  // Let the dependent kernel start launching; it waits for this grid's results.
+  cudaTriggerProgrammaticLaunchCompletion();
+  __shared__ int s_inst[2];
+  const int64_t q0 = v.bus_inst_begin + (int64_t)blockIdx.x * blockDim.x;
+  const int64_t q = q0 + threadIdx.x;
+  phasor_block_instances(v, q0, s_inst);
   if (q < v.n_bus_inst) {
-    const int i0 = v.n_inst > 1 ? s_inst[0] : 0, i1 = v.n_inst > 1 ? s_inst[1] : 0;
-    const int inst = i0 == i1 ? i0 : i0 + find_segment(v.inst_bus_off + i0, i1 - i0 + 1, q);
+    const int inst = phasor_instance(v, q, s_inst);
     const int64_t lb = q - v.inst_bus_off[inst];
     const double *xi = x + v.inst_x_off[inst];
     const double th = __ldg(xi + lb);
     const double vm = __ldg(xi + v.grid_nbus[v.inst_grid[inst]] + lb);
-    const double sv = (__double2hiint(vm) & 0x7ff00000) < 0x20b00000 ? kDeadV : vm;   // |V| < 2^-500
-    const RectV r = rect_voltage(th, sv, v.sincos_fix);
+    const RectV r = rect_voltage(th, dead_sub(vm), v.sincos_fix);
     v.phasor[2 * q] = r.E;
     v.phasor[2 * q + 1] = make_double2(vm, r.rv);
   }
 }
 
-// Exact sums of FP64 terms on the integer pipe: a 128-bit two's-complement
-// accumulator with 64 fraction bits (|term| < 2^57; bits below 2^-64 are
-// dropped, an absolute error below 2^-64 per term).  The sum is exact up to
-// that, so it does not depend on the order of the terms, and it is rounded
-// to a double once (to nearest, ties away from zero).
+// x 2^60 as a signed integer for |x| < 2 (exact for |x| >= 2^-8, truncated
+// toward zero below), from the bits of x on the integer pipe.
+__device__ __forceinline__ long long fix60_of(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  const unsigned long long m = (b & 0xfffffffffffffULL) | (e ? (1ULL << 52) : 0ULL);
+  const int sh = e - 1015;                                    // x 2^60 = m 2^(e - 1015)
+  const long long a = (long long)(sh >= 0 ? m << sh : (sh > -64 ? m >> -sh : 0ULL));
+  return (long long)b < 0 ? -a : a;
+}
+
+// 30-bit limbs {h, l} of a fixed-point value below 2^61 in magnitude:
+// value = h 2^30 + l with 0 <= l < 2^30.
+__device__ __forceinline__ int2 limbs(long long z) { return make_int2((int)(z >> 30), (int)(z & 0x3fffffff)); }
+
+// Fixed-point records for the F / J kernels, one thread per instance-bus:
+// {cos theta 2^60, sin theta 2^60} as 30-bit limbs, then {V 2^60} as limbs
+// and the bits of 1/V, in 32 bytes.  The trigonometric routine runs on the
+// integer pipe and its fixed-point result is kept (rounded from 2^62 to 2^60,
+// no rounding to double); V 2^60 is exact for 2^-8 <= |V| < 2.  A voltage
+// outside (-2, 2), or an angle that is not finite, gets kBadLimb in place of
+// V's high limb: the buses that see it evaluate in FP64 from x.  1/V (with
+// the dead-bus substitution) serves the own bus's diagonal values.
+__global__ void __launch_bounds__(256) k_phasor_fx(View v, const double *__restrict__ x) {
+  cudaTriggerProgrammaticLaunchCompletion();
+  __shared__ int s_inst[2];
+  const int64_t q0 = v.bus_inst_begin + (int64_t)blockIdx.x * blockDim.x;
+  const int64_t q = q0 + threadIdx.x;
+  phasor_block_instances(v, q0, s_inst);
+  if (q < v.n_bus_inst) {
+    const int inst = phasor_instance(v, q, s_inst);
+    const int64_t lb = q - v.inst_bus_off[inst];
+    const double *xi = x + v.inst_x_off[inst];
+    const double th = __ldg(xi + lb);
+    const double vm = __ldg(xi + v.grid_nbus[v.inst_grid[inst]] + lb);
+    const double sv = dead_sub(vm);
+    long long c60, s60;
+    bool finite = true;
+    if ((__double2hiint(th) & 0x7fffffff) < 0x40400000) {       // |t| < 32
+      const longlong2 u = unit_fix_small(th, v.sincos_fix);
+      c60 = (u.x + 2) >> 2;
+      s60 = (u.y + 2) >> 2;
+      if (__double2hiint(th) < 0) s60 = -s60;                    // sin is odd
+    } else {
+      double sn, cs;
+      sincos(th, &sn, &cs);
+      c60 = __double2ll_rn(__dmul_rn(cs, 0x1p60));
+      s60 = __double2ll_rn(__dmul_rn(sn, 0x1p60));
+      finite = (__double2hiint(th) & 0x7ff00000) != 0x7ff00000;
+    }
+    int2 vl = limbs(fix60_of(vm));
+    if (!(finite && fabs(vm) < 2.0)) vl = make_int2(kBadLimb, 0);
+    const int2 cl = limbs(c60), sl = limbs(s60);
+    const double rv = (__double2hiint(sv) & 0x7ff00000) >= 0x7d000000 ? __drcp_rn(sv) : recip(sv);
+    int4 *rec = reinterpret_cast<int4 *>(v.phasor);
+    rec[2 * q] = make_int4(cl.x, cl.y, sl.x, sl.y);
+    rec[2 * q + 1] = make_int4(vl.x, vl.y, __double2loint(rv), __double2hiint(rv));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fixed-point arithmetic of the pair terms (integer pipe).
+//
+// With the unit phasors U = (cos theta, sin theta) of k_phasor_fx, the own
+// voltage E_o = V_o U_o and the merged coefficients (G, B) of a pair,
+//     T = (G + jB) conj(E_o) U_k = (X - jY) / V_k,
+// so that the pair's values are
+//     X = V_k Re T,  -Y = V_k Im T          (the theta-column values and the bus sums)
+//     -X / V_k = -Re T,  -Y / V_k = Im T    (the V-column values).
+// Every fixed-point factor is held as 30-bit limbs (value = h 2^30 + l,
+// 0 <= l < 2^30) and a product a b 2^-60 is formed from three 32 x 32 -> 64
+// multiplies, h_a h_b + ((h_a l_b + l_a h_b) >> 30), the l_a l_b term dropped:
+// low by less than 2 units (3 for a sum of two products).  Scales: U, V and
+// E_o at 2^60 (|U| <= 1, |V|, |E_o| < 2), conj(E_o) U_k at 2^60, (G, B) at
+// 2^(59 - c) with |G|, |B| < 2^c, T and X, Y at 2^(59 - c); every partial
+// sum stays below 2^63.  With the 2^-57 error of the phasor routine the
+// absolute error of T is below 2^(c - 55) (about 3e-17 max(|G|, |B|)), of X,
+// Y below 2^(c - 54); X and Y are summed exactly in 128 bits and every value is
+// rounded once to double (to nearest, ties away from zero).
+// ---------------------------------------------------------------------------
+
+// a b, exact, from 32-bit factors (one 32 x 32 -> 64 multiply).
+__device__ __forceinline__ long long wmul(int a, int b) { return (long long)a * (long long)b; }
+
+// (a1 b1 + a2 b2) 2^-60 from limbs.
+__device__ __forceinline__ long long dot60(int2 a1, int2 b1, int2 a2, int2 b2) {
+  const long long m = wmul(a1.x, b1.y) + wmul(a1.y, b1.x) + wmul(a2.x, b2.y) + wmul(a2.y, b2.x);
+  return wmul(a1.x, b1.x) + wmul(a2.x, b2.x) + (m >> 30);
+}
+
+// a b 2^-60 from limbs.
+__device__ __forceinline__ long long mul60(int2 a, int2 b) {
+  const long long m = wmul(a.x, b.y) + wmul(a.y, b.x);
+  return wmul(a.x, b.x) + (m >> 30);
+}
+
+// z 2^-s as a double, rounded to nearest (ties away from zero); 2^-s |z| must
+// be a normal double.
+__device__ __forceinline__ double fix_to_double(long long z, int s) {
+  if (z == 0) return 0.0;
+  const unsigned long long sign = (unsigned long long)z & 0x8000000000000000ULL;
+  const unsigned long long a = sign ? 0ULL - (unsigned long long)z : (unsigned long long)z;
+  const int lz = __clzll((long long)a);
+  const unsigned long long n = a << lz;                                              // top bit 63
+  const unsigned long long mag =
+      ((unsigned long long)(1086 - s - lz) << 52) + ((n >> 11) & 0xfffffffffffffULL) + ((n >> 10) & 1ULL);
+  return __longlong_as_double((long long)(sign | mag));
+}
+
+// Exact sums on the integer pipe: a 128-bit two's-complement accumulator of
+// fixed-point terms.  The sum does not depend on the order of the terms, so
+// every schedule and tuning gives the same bits; it is rounded to a double
+// once (to nearest, ties away from zero).
 struct Acc128 {
   unsigned long long lo;
   long long hi;
 };
 
-// Adds x; clears `ok` when |x| >= 2^57 or x is not finite (the caller then
-// sums in FP64 instead).
-__device__ __forceinline__ void acc_add(Acc128 &a, double x, bool &ok) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int e = (int)((b >> 52) & 0x7ff);
-  ok = ok && e < 1080;                        // |x| < 2^57: 32 terms stay below 2^62
-  const unsigned long long m = (b & 0xfffffffffffffULL) | (e ? (1ULL << 52) : 0ULL);
-  const int s = e - 1011;                      // x = m 2^(e - 1075) = (m 2^s) 2^-64
-  unsigned long long lo, hi;
-  if (s >= 64) {
-    hi = m << min(s - 64, 63);
-    lo = 0ULL;
-  } else if (s > 0) {
-    hi = m >> (64 - s);
-    lo = m << s;
-  } else {
-    hi = 0ULL;
-    lo = s > -64 ? m >> -s : 0ULL;
-  }
-  if (b >> 63) {                               // subtract
-    const unsigned long long nlo = a.lo - lo;
-    a.hi = (long long)((unsigned long long)a.hi - hi - (a.lo < lo ? 1ULL : 0ULL));
-    a.lo = nlo;
-  } else {
-    const unsigned long long nlo = a.lo + lo;
-    a.hi = (long long)((unsigned long long)a.hi + hi + (nlo < lo ? 1ULL : 0ULL));
-    a.lo = nlo;
-  }
+// Adds a signed 64-bit term.
+__device__ __forceinline__ void acc_add64(Acc128 &a, long long x) {
+  const unsigned long long nlo = a.lo + (unsigned long long)x;
+  a.hi = (long long)((unsigned long long)a.hi + (unsigned long long)(x >> 63) + (nlo < a.lo ? 1ULL : 0ULL));
+  a.lo = nlo;
 }
 
 // Adds another accumulator's value (lo, hi).
@@ -238,7 +353,8 @@ __device__ __forceinline__ void acc_merge(Acc128 &a, unsigned long long lo, long
   a.lo = nlo;
 }
 
-__device__ __forceinline__ double acc_value(const Acc128 &a) {
+// The accumulator's value 2^-s as a double.
+__device__ __forceinline__ double acc_value(const Acc128 &a, int s) {
   unsigned long long hi = (unsigned long long)a.hi, lo = a.lo;
   const unsigned long long sign = hi & 0x8000000000000000ULL;
   if (sign) {                                  // magnitude
@@ -251,9 +367,9 @@ __device__ __forceinline__ double acc_value(const Acc128 &a) {
   const int sh = lz & 63;
   // (bits below n's 11 lowest are dropped: the rounding uses bit 10 of n)
   const unsigned long long n = lz < 64 ? (sh ? (hi << sh) | (lo >> (64 - sh)) : hi) : lo << sh;
-  const int p = 127 - lz;                      // value = 2^(p - 64) * (n / 2^63)
+  const int p = 127 - lz;                      // value = 2^(p - s) * (n / 2^63)
   const unsigned long long mag =
-      ((unsigned long long)(p - 64 + 1023) << 52) + ((n >> 11) & 0xfffffffffffffULL) + ((n >> 10) & 1ULL);
+      ((unsigned long long)(p - s + 1023) << 52) + ((n >> 11) & 0xfffffffffffffULL) + ((n >> 10) & 1ULL);
   return __longlong_as_double((long long)(sign | mag));
 }
 
@@ -265,6 +381,7 @@ struct EvalArgs {
   const double2 *ac;
   const double2 *hat;       // per bus
   const double2 *sgb;       // per end, slot order of the rounds
+  const int4 *sgbx;         // sgb in fixed point (limbs)
   const double2 *sac;
   const double2 *rhat;      // per bus, round order
   const double *p_inj;     // per-instance-bus override or nullptr
@@ -279,7 +396,8 @@ struct EvalArgs {
   unsigned long long *work;
 };
 
-// X and Y of one branch end (own voltage Eo, other voltage Ek, rectangular).
+// X and Y of one branch end (own voltage Eo, other voltage Ek, rectangular),
+// in FP64.
 struct EndTerms {
   double X, Y;
 };
@@ -295,12 +413,40 @@ __device__ __forceinline__ EndTerms end_terms(double2 G, double2 Eo, double2 Ek)
 }
 
 // The four off-diagonal values of a pair (CSR positions p, -1 where the
-// formulation has no such entry) from its X, Y and 1/V_k.
+// formulation has no such entry) from its X, Y and 1/V_k (FP64 path).
 __device__ __forceinline__ void write_pair(double *vi, int4 p, double X, double Y, double rvk) {
   if (p.x >= 0) vi[p.x] = neg(Y);                    // dP_o / dtheta_k
   if (p.y >= 0) vi[p.y] = __dmul_rn(-X, rvk);        // dP_o / dV_k
   if (p.z >= 0) vi[p.z] = X;                         // dQ_o / dtheta_k
   if (p.w >= 0) vi[p.w] = __dmul_rn(-Y, rvk);        // dQ_o / dV_k
+}
+
+// FP64 voltage of a bus for the FP64 path: E = V (cos, sin) (V after the
+// dead-bus substitution) from the record's unit phasor and x's V -- the
+// values of the adjoint's FP64 records -- and 1/V from the record.  An angle
+// that is not finite gives E = NaN, as the FP64 form would.
+struct VoltD {
+  double2 E;
+  double v, rv;
+};
+
+__device__ __forceinline__ VoltD volt_fp64(const int4 *__restrict__ rec4, const double *__restrict__ xi, int32_t nb,
+                                           int64_t lb, int64_t rb) {
+  const int4 u = rec4[2 * rb];
+  const int4 w = rec4[2 * rb + 1];
+  const double th = xi[lb], vm = xi[nb + lb];
+  const double sv = dead_sub(vm);
+  VoltD r;
+  if ((__double2hiint(th) & 0x7ff00000) == 0x7ff00000) {
+    const double nan = __dsub_rn(th, th);
+    r.E = make_double2(nan, nan);
+  } else {
+    const long long c = ((long long)u.x << 30) + u.y, s = ((long long)u.z << 30) + u.w;
+    r.E = make_double2(__dmul_rn(sv, fix_to_double(c, 60)), __dmul_rn(sv, fix_to_double(s, 60)));
+  }
+  r.v = vm;
+  r.rv = __hiloint2double(w.w, w.z);
+  return r;
 }
 
 __device__ __forceinline__ bool end_in_service(const View &v, int32_t e, int32_t outage, const uint8_t *status,
@@ -313,25 +459,23 @@ __device__ __forceinline__ int64_t gb0_of(const View &v, int g) { return __ldg(v
 
 // Off-diagonal entries of a group of `len` parallel branch ends e, e+1, ...
 // (same own bus o, same other bus k, so the same four CSR positions), from
-// X and Y summed over the group in list order.  For a group of one branch
-// these are the single end's terms.
-__device__ __forceinline__ void write_group(const View &v, const EvalArgs &a, int32_t e, int32_t len, int32_t o,
-                                            int32_t k, int4 p, const double2 *rec, double *vi, bool masked,
-                                            int32_t outage, int64_t st_base) {
-  const double2 Eo = rec[2 * o], Ek = rec[2 * k];
-  const double rvk = rec[2 * k + 1].y;
+// X and Y summed over the group in list order (FP64).  For a group of one
+// branch these are the single end's terms.
+__device__ __forceinline__ void write_group(const View &v, const EvalArgs &a, int32_t e, int32_t len, double2 Eo,
+                                            const VoltD &Ek, int4 p, double *vi, bool masked, int32_t outage,
+                                            int64_t st_base) {
   double X = 0.0, Y = 0.0;
   for (int32_t q = 0; q < len; ++q) {
     double2 G = __ldg(a.gb + e + q);
     if (masked && !end_in_service(v, e + q, outage, a.status, st_base)) G = make_double2(0.0, 0.0);
-    const EndTerms tq = end_terms(G, Eo, Ek);
+    const EndTerms tq = end_terms(G, Eo, Ek.E);
     if (q == 0) {
       X = tq.X; Y = tq.Y;
     } else {
       X = __dadd_rn(X, tq.X); Y = __dadd_rn(Y, tq.Y);
     }
   }
-  write_pair(vi, p, X, Y, rvk);
+  write_pair(vi, p, X, Y, Ek.rv);
 }
 
 // Under an outage mask: the coefficients of the branches in service of the
@@ -387,15 +531,64 @@ __device__ __forceinline__ double2 masked_hat(const View &v, const EvalArgs &a, 
   return make_double2(__dadd_rn(sa, sh.x), __dadd_rn(sc, sh.y));
 }
 
+// Rows of J a warp stages in shared memory before writing them out whole:
+// a bus with at most kStageMaxD neighbours has rows of at most
+// 2 (kStageMaxD + 1) + 1 = kStageLen entries (theta and V columns of itself and
+// its neighbours, plus P_s or Q_g in the extended formulation).  Each bus
+// lane owns kStageStride doubles (its P row, then its Q row, one spare so
+// that the lanes' strides are odd and their accesses spread over the banks).
+constexpr int kStageMaxD = 6;
+constexpr int kStageLen = 16;
+constexpr int kStageStride = 2 * kStageLen + 1;
+constexpr int kStageBytes = 32 * kStageStride * 8;
+
+// n staged values to dst: one value first when dst is not 16-byte aligned,
+// then pairs of values per store.
+__device__ __forceinline__ void write_row(double *dst, const double *src, int32_t n) {
+  int32_t i = 0;
+  if ((reinterpret_cast<uintptr_t>(dst) & 8) && n > 0) {
+    dst[0] = src[0];
+    i = 1;
+  }
+  for (; i + 1 < n; i += 2) *reinterpret_cast<double2 *>(dst + i) = make_double2(src[i], src[i + 1]);
+  if (i < n) dst[i] = src[i];
+}
+
+// z 2^-s as a double by the hardware conversion on the FP64 pipe (rounded to
+// nearest even), the scale applied to the exponent; 2^-s |z| must be a normal
+// double.  The FP64 pipe is otherwise idle in the pair loop, so half of the
+// pair's conversions go there and half to the integer pipe (fix_to_double).
+__device__ __forceinline__ double fix_to_double_cvt(long long z, int s) {
+  const double d = __ll2double_rn(z);
+  return __hiloint2double(z == 0 ? 0 : __double2hiint(d) - (s << 20), __double2loint(d));
+}
+
+// Where a lane's in-row J values go: the shared-memory rows of its bus, or
+// straight to J at the rows' CSR positions (bp, bq: -1 for an absent row).
+struct RowSink {
+  double *srow;     // staged: P row at srow[0..), Q row at srow[kStageLen..); nullptr: direct
+  double *vi;
+  int32_t bp, bq;
+  __device__ __forceinline__ void p(int32_t off, double x) const {
+    if (srow) srow[off] = x;
+    else if (bp >= 0) vi[bp + off] = x;
+  }
+  __device__ __forceinline__ void q(int32_t off, double x) const {
+    if (srow) srow[kStageLen + off] = x;
+    else if (bq >= 0) vi[bq + off] = x;
+  }
+};
+
 // F rows, the extended formulation's extra rows and the diagonal of J for
-// bus o (global id) of one instance, from the sums over its ends.
+// bus o (global id) of one instance, from the sums over its ends; in-row
+// values through the sink.
 template <bool WF, bool WJ>
 __device__ __forceinline__ void finalize_bus(const View &v, const EvalArgs &a, int inst, int g, int32_t o,
-                                             int64_t gb0, int32_t nb, const double *xi, double *vi, double vo,
-                                             double rvo, double sx, double sy, double ah, double ch, int4 bm,
-                                             int4 bm2, double2 inj) {
+                                             int64_t gb0, int32_t nb, const double *xi, double *vi, const RowSink &rs,
+                                             double vo, double rvo, double sx, double sy, double ah, double ch,
+                                             int4 bm, int4 bm2, double2 inj) {
   const int64_t lb = o - gb0;
-  const int32_t rp = bm.x, rq = bm.y, bp = bm.z, bq = bm.w;
+  const int32_t rp = bm.x, rq = bm.y;
   const int32_t gi = bm2.w;
   const bool is_slack = (v.formulation == PF_EXTENDED) && (lb == v.grid_slack[g]);
   const double v2 = __dmul_rn(vo, vo);
@@ -422,20 +615,20 @@ __device__ __forceinline__ void finalize_bus(const View &v, const EvalArgs &a, i
     if (rq >= 0) Fi[rq] = fq;
   }
   if (WJ) {
-    if (bp >= 0) {
-      if (bm2.x >= 0) vi[bp + bm2.x] = sy;
-      if (bm2.y >= 0) vi[bp + bm2.y] = __dmul_rn(__fma_rn(v2, ah, tp), rvo);
+    if (bm2.x >= 0) {
+      rs.p(bm2.x, sy);                                   // dF_P / dtheta_o
+      rs.q(bm2.x, neg(sx));                              // dF_Q / dtheta_o
     }
-    if (bq >= 0) {
-      if (bm2.x >= 0) vi[bq + bm2.x] = neg(sx);
-      if (bm2.y >= 0) vi[bq + bm2.y] = __dmul_rn(__fma_rn(v2, ch, tq), -rvo);
+    if (bm2.y >= 0) {
+      rs.p(bm2.y, __dmul_rn(__fma_rn(v2, ah, tp), rvo));  // dF_P / dV_o
+      rs.q(bm2.y, __dmul_rn(__fma_rn(v2, ch, tq), -rvo)); // dF_Q / dV_o
     }
     if (is_slack) {
-      vi[bp + bm2.z] = -1.0;                // d g_p / d P_s
+      rs.p(bm2.z, -1.0);                    // d g_p / d P_s
       vi[v.grid_pos_gth[g]] = 1.0;         // d g_theta / d theta_s
     }
     if (gi >= 0) {
-      vi[bq + bm2.z] = -1.0;                // d g_q / d Q_g
+      rs.q(bm2.z, -1.0);                    // d g_q / d Q_g
       const bool held = a.gen_mode && a.gen_mode[v.inst_gen_off[inst] + gi];
       const int32_t p = v.gen_pos[v.grid_gen_off[g] + gi];
       vi[p] = held ? 0.0 : 1.0;             // d g_V / d V
@@ -444,52 +637,95 @@ __device__ __forceinline__ void finalize_bus(const View &v, const EvalArgs &a, i
   }
 }
 
-// The merged coefficients (G, B) of slot q (meta: its slot_meta entry) as
-// the mask leaves them: the built value, zero for a single branch out of
-// service, or the re-summed branches in service of a group.
+// The merged coefficients (G, B) of a slot (len: its group length, cw: the
+// code of a single branch or the first end of a group) as the mask leaves
+// them: the built value, zero for a single branch out of service, or the
+// re-summed branches in service of a group.
 template <bool MASKED>
-__device__ __forceinline__ double2 slot_gb(const View &v, const EvalArgs &a, int4 meta, double2 G, int32_t outage,
-                                           int64_t st_base, bool &any_out) {
+__device__ __forceinline__ double2 slot_gb(const View &v, const EvalArgs &a, int32_t len, int32_t cw, double2 G,
+                                           int32_t outage, int64_t st_base, bool &any_out) {
   if (!MASKED) return G;
-  if (meta.y == 1) {
-    const int32_t l = meta.z >> 1;
+  if (len == 1) {
+    const int32_t l = cw >> 1;
     if (l == outage || (a.status != nullptr && a.status[st_base + l] == 0)) {
       any_out = true;
       return make_double2(0.0, 0.0);
     }
     return G;
   }
-  const GroupCoeff mg = masked_group(v, a, meta.w, meta.y, outage, st_base);
+  const GroupCoeff mg = masked_group(v, a, cw, len, outage, st_base);
   any_out |= mg.any_out;
   return mg.gb;
 }
 
-// One-warp CTAs that must fit on one SM (the register budget of k_fused):
-// the largest count each variant compiles to without spilling -- for the
-// unmasked F + J evaluation 64 registers with one slot per fetch, 80 with
-// two; fewer CTAs for the other variants and for deeper fetches.
-// The persistent variants (DYN: dynamic schedule) keep a claimed unit index
-// live across the loop, and a persistent grid holds fewer CTAs per SM: a
-// bound of 4 (one slot per fetch: 12) fewer CTAs leaves them room without
-// spilling.
+// The same in fixed point (GX: the slot's sgbx entry); a re-summed group is
+// converted as the build converts it.
+template <bool MASKED>
+__device__ __forceinline__ int4 slot_gbx(const View &v, const EvalArgs &a, int32_t len, int32_t cw, int4 GX,
+                                         int32_t outage, int64_t st_base, bool &any_out) {
+  if (!MASKED) return GX;
+  if (len == 1) {
+    const int32_t l = cw >> 1;
+    if (l == outage || (a.status != nullptr && a.status[st_base + l] == 0)) {
+      any_out = true;
+      return make_int4(0, 0, 0, 0);
+    }
+    return GX;
+  }
+  const GroupCoeff mg = masked_group(v, a, cw, len, outage, st_base);
+  any_out |= mg.any_out;
+  return coef_limbs(to_fix(mg.gb.x, v.coef_scale), to_fix(mg.gb.y, v.coef_scale));
+}
+
+// The 32-byte record of a bus in one load: {cos h, cos l, sin h, sin l} and
+// {V h, V l, 1/V lo, 1/V hi} (fixed-point form) -- the record starts on a
+// 32-byte boundary.
+struct Rec {
+  int4 u, w;
+};
+
+__device__ __forceinline__ Rec load_rec(const int4 *p) {
+  Rec r;
+  asm("ld.global.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r.u.x), "=r"(r.u.y), "=r"(r.u.z), "=r"(r.u.w), "=r"(r.w.x), "=r"(r.w.y), "=r"(r.w.z),
+                 "=r"(r.w.w)
+               : "l"(p));
+  return r;
+}
+
+// One-warp CTAs that must fit on one SM (the register budget of k_fused).
 template <int ITEMS, bool WF, bool WJ, bool MASKED, bool DYN>
 struct FusedMinCtas {
   static constexpr bool plain = WF && WJ && !MASKED;     // the F + J evaluation without a mask
-  static constexpr int base = ITEMS == 1 ? (plain ? 32 : 28) : ITEMS == 2 ? (plain ? 24 : 20) : 16;
-  static constexpr int value = DYN ? base - (ITEMS == 1 ? 12 : 4) : base;
+  static constexpr int base = ITEMS == 1 ? (plain ? 24 : 20) : ITEMS == 2 ? 16 : 12;
+  static constexpr int value = DYN ? base - 4 : base;
 };
 
 // One warp per round.  A round holds up to 32 buses with equal (or
 // adjacent) numbers of neighbours, one per lane; lane l walks its bus's
 // groups of parallel branches in incidence order (slot first + 32 j + l holds
-// group j, so every fetch of the round's data is coalesced), keeps the bus
-// sums in registers and writes the group's four off-diagonal entries.  A
+// group j, so every fetch of the round's data is coalesced), keeps the exact
+// bus sums in registers and produces the group's four off-diagonal values.  A
 // group's coefficients are summed at build time, so a pair of buses joined by
 // several branches costs one merged branch end.  Under an outage mask a
 // group with more than one branch re-sums the coefficients of its branches in
 // service.  Slots are fetched ITEMS at a time.
+//
+// The pair terms are formed in fixed point on the integer pipe (see above).
+// A bus whose own voltage is outside [1/4, 2), or that sees a neighbour's
+// record or a coefficient marked kBadLimb, is evaluated in FP64 instead: its
+// lead lane recomputes every value of the bus from x and the records, summing
+// in list order.  Which form a bus takes depends only on the inputs, so every
+// tuning and schedule gives the same bits.
+//
+// J values: in a round of buses with at most kStageMaxD neighbours each bus
+// lane stages its P and Q rows in shared memory and then writes them out
+// whole, two values per store (half the stores of writing each value where it
+// goes, and each row's sectors written by consecutive stores of one lane);
+// larger rounds write each value where it goes.
 template <int ITEMS, bool WF, bool WJ, bool MASKED, bool DYN>
 __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED, DYN>::value)) k_fused(View v, EvalArgs a) {
+  extern __shared__ double s_stage[];           // kStageBytes when WJ
   const int lane = threadIdx.x & 31;
   // split rounds: a warp takes half a round (16 buses), two lanes per bus,
   // lane l the pairs l >> 4, (l >> 4) + 2, ... of bus l & 15
@@ -498,6 +734,7 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED, DYN>:
   const int bl0 = split ? (lane & 15) : lane;    // bus lane within the (half) round
   const int par = split ? (lane >> 4) : 0;       // this lane's first pair
   const int step = 1 + split;                    // and its stride
+  const int sT = 59 - v.coef_log2;               // scale of T, X, Y and the sums
   // Dynamic schedule of a persistent grid: lane 0 claims the warp's next unit
   // from a counter as it starts a unit, so the claim's latency hides behind
   // the unit's work; units of uneven weight then even out over the CTAs.
@@ -516,77 +753,103 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED, DYN>:
     if (work && lane == 0) claim = atomicAdd(work, 1ULL);
     const int4 ur = __ldg(v.unit_rec + (u >> split));   // {instance, round, first slot, D | buses << 8}
     const int inst = ur.x;
-    const int64_t r = ur.y;
     const int g = __ldg(v.inst_grid + inst);
     const double *__restrict__ xi = a.x + __ldg(v.inst_x_off + inst);
-    // E = V (cos, sin) at rec[2 k], (V, 1/V) at rec[2 k + 1], by global bus id k
-    const double2 *__restrict__ rec = v.phasor + 2 * __ldg(v.inst_rec_base + inst);
+    // unit phasor limbs at rec4[2 k], {V limbs, bits of 1/V} at rec4[2 k + 1], by global bus id k
+    const int4 *__restrict__ rec4 = reinterpret_cast<const int4 *>(v.phasor) + 2 * __ldg(v.inst_rec_base + inst);
     double *__restrict__ vi = WJ ? a.vals + __ldg(v.inst_v_off + inst) : nullptr;
     const int32_t outage = MASKED ? v.inst_outage[inst] : -1;
     const int64_t st_base = MASKED ? v.inst_br_off[inst] - v.grid_br_off[g] : 0;
+    const int32_t D = ur.w & 0xff;
+    const bool staged = WJ && D <= kStageMaxD;
 
     // this lane's bus: records in round order, fetched before the wait
     const int bl = bl0 + (split ? 16 * (int)(u & 1) : 0);
-    const int64_t rb = 32 * r + bl;
+    const int32_t rb = 32 * ur.y + bl;            // below 2^31: the build checks the round count
     const bool owner = bl < (ur.w >> 8);
     const bool lead = owner && par == 0;         // the lane that finishes the bus
     int32_t o = 0;
     int4 bm = make_int4(-1, -1, -1, -1), bm2 = make_int4(-1, -1, 0, -1);
     double2 hat = make_double2(0.0, 0.0), inj = make_double2(0.0, 0.0);
-    if (owner) o = __ldg(v.rbus + rb);
-    if (lead) {
+    if (owner) {
+      o = __ldg(v.rbus + rb);
       bm = __ldg(v.rbus_meta + rb);
+    }
+    if (lead) {
       bm2 = __ldg(v.rbus_meta2 + rb);
       hat = __ldg(a.rhat + rb);
       if (WF) inj = __ldg(v.rbus_inj + rb);
     }
-    Acc128 ax{0ULL, 0LL}, ay{0ULL, 0LL};       // exact S_X, S_Y
-    bool exact = true;
+    const RowSink rs{staged ? s_stage + bl0 * kStageStride : nullptr, vi, bm.z, bm.w};
+    Acc128 ax{0ULL, 0LL}, ay{0ULL, 0LL};       // exact S_X and -S_Y
+    bool fast = true;                            // the fixed-point form holds for this bus
     bool any_out = false;                        // masked: an end of this bus is out of service
-    double2 Eo = make_double2(0.0, 0.0), vr = make_double2(0.0, 0.0);
-    const int32_t D = ur.w & 0xff;
-    const int64_t q0 = (int64_t)ur.z + bl;
+    int2 eo = make_int2(0, 0), fo = make_int2(0, 0), nfo = make_int2(0, 0);   // E_o 2^60 as limbs, and -f_o
+    long long vof = 0;                           // V_o 2^60
+    double rvo = 0.0;
+    const int32_t q0 = ur.z + bl;                 // slot indices are below 2^31 (checked at build)
 
-    for (int32_t j0 = par; j0 < D; j0 += ITEMS * step) {
-      int4 meta[ITEMS], pos[ITEMS];
-      double2 G[ITEMS];
+    // (the first pass always runs: it waits for the records and loads the own bus's)
+    for (int32_t j0 = par; j0 == par || j0 < D; j0 += ITEMS * step) {
+      int4 idx[ITEMS], GX[ITEMS];
 #pragma unroll
       for (int it = 0; it < ITEMS; ++it) {
-        meta[it] = make_int4(0, -1, 0, 0);
+        idx[it] = make_int4(0, -1, -1, 0);
         const int32_t j = j0 + it * step;
         if (j < D) {
-          const int64_t q = q0 + 32 * j;
-          meta[it] = __ldg(v.slot_meta + q);
-          if (WJ) pos[it] = __ldg(v.slot_pos + q);
-          G[it] = __ldg(a.sgb + q);
+          const int32_t q = q0 + 32 * j;
+          idx[it] = __ldg(v.slot_idx + q);
+          GX[it] = __ldg(a.sgbx + q);
         }
       }
       if (j0 == par) {
-        // the per-bus records come from k_phasor (programmatic dependent launch)
+        // the per-bus records come from k_phasor_fx (programmatic dependent launch)
         cudaGridDependencySynchronize();
         if (owner) {
-          Eo = rec[2 * o];
-          vr = rec[2 * o + 1];
+          const Rec ro = load_rec(rec4 + 2 * o);
+          rvo = __hiloint2double(ro.w.w, ro.w.z);
+          const int2 vl = make_int2(ro.w.x, ro.w.y);
+          vof = ((long long)ro.w.x << 30) + ro.w.y;
+          fast = ro.w.x >= (1 << 28);            // V_o in [1/4, 2) (kBadLimb is negative)
+          eo = limbs(mul60(vl, make_int2(ro.u.x, ro.u.y)));
+          const long long f = mul60(vl, make_int2(ro.u.z, ro.u.w));
+          fo = limbs(f);
+          nfo = limbs(-f);
         }
       }
 #pragma unroll
       for (int it = 0; it < ITEMS; ++it) {
-        const int32_t len = meta[it].y;          // branches in the group, -1 padding
+        const int32_t len = idx[it].z;           // branches in the group, -1 padding
         if (len < 0) continue;
-        const int32_t k = meta[it].x;
-        const double2 Gi = slot_gb<MASKED>(v, a, meta[it], G[it], outage, st_base, any_out);
-        const double2 Ek = rec[2 * k];
-        const EndTerms tm = end_terms(Gi, Eo, Ek);
-        acc_add(ax, tm.X, exact);
-        acc_add(ay, tm.Y, exact);
-        if (WJ) write_pair(vi, pos[it], tm.X, tm.Y, rec[2 * k + 1].y);
-      }
-    }
-    if (D <= par) {                              // no pair on this lane (a round of isolated buses)
-      cudaGridDependencySynchronize();
-      if (owner) {
-        Eo = rec[2 * o];
-        vr = rec[2 * o + 1];
+        const int32_t k = idx[it].x;
+        const int4 gx = slot_gbx<MASKED>(v, a, len, idx[it].w, GX[it], outage, st_base, any_out);
+        const Rec rk = load_rec(rec4 + 2 * k);
+        fast = fast && rk.w.x != kBadLimb && gx.x != kBadLimb && gx.z != kBadLimb;
+        const int2 ck = make_int2(rk.u.x, rk.u.y), sk = make_int2(rk.u.z, rk.u.w), vk = make_int2(rk.w.x, rk.w.y);
+        // conj(E_o) U_k 2^60
+        const long long pr = dot60(eo, ck, fo, sk);
+        const long long pi = dot60(eo, sk, nfo, ck);
+        const int2 prl = limbs(pr), pil = limbs(pi), npil = limbs(-pi);
+        // T = (G + jB) conj(E_o) U_k 2^(59 - c)
+        const int2 gl = make_int2(gx.x, gx.y), bl2 = make_int2(gx.z, gx.w);
+        const long long tr = dot60(gl, prl, bl2, npil);
+        const long long ti = dot60(gl, pil, bl2, prl);
+        // X = V_k Re T, -Y = V_k Im T, 2^(59 - c)
+        const long long xx = mul60(vk, limbs(tr));
+        const long long my = mul60(vk, limbs(ti));
+        acc_add64(ax, xx);
+        acc_add64(ay, my);
+        if (WJ) {
+          const int32_t ot = (short)(idx[it].y & 0xffff), ov = idx[it].y >> 16;
+          if (ot >= 0) {
+            rs.p(ot, fix_to_double(my, sT));         // dP_o / dtheta_k = -Y
+            rs.q(ot, fix_to_double(xx, sT));         // dQ_o / dtheta_k = X
+          }
+          if (ov >= 0) {
+            rs.p(ov, neg(fix_to_double_cvt(tr, sT)));    // dP_o / dV_k = -X / V_k
+            rs.q(ov, fix_to_double_cvt(ti, sT));         // dQ_o / dV_k = -Y / V_k
+          }
+        }
       }
     }
     if (split) {
@@ -594,36 +857,63 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED, DYN>:
       // sums are exact, so the result is the unsplit one, bit for bit
       acc_merge(ax, __shfl_down_sync(0xffffffffu, ax.lo, 16), __shfl_down_sync(0xffffffffu, ax.hi, 16));
       acc_merge(ay, __shfl_down_sync(0xffffffffu, ay.lo, 16), __shfl_down_sync(0xffffffffu, ay.hi, 16));
-      exact = __shfl_down_sync(0xffffffffu, (int)exact, 16) != 0 && exact;
+      fast = __shfl_down_sync(0xffffffffu, (int)fast, 16) != 0 && fast;
       any_out = __shfl_down_sync(0xffffffffu, (int)any_out, 16) != 0 || any_out;
+      __syncwarp();                              // the FP64 path below rewrites the other lane's values
     }
     if (lead) {
-      // S_X, S_Y: the exact sums, rounded once; in FP64, in list order, when a
-      // term is out of the accumulator's range or the bus is dead (its terms
-      // carry the 2^-600 factor that 1/V divides out again)
-      double sx, sy;
-      if (exact && (__double2hiint(vr.x) & 0x7ff00000) >= 0x20b00000) {
-        sx = acc_value(ax);
-        sy = acc_value(ay);
+      const int64_t gb0 = gb0_of(v, g);
+      const int32_t nb = v.grid_nbus[g];
+      double sx, sy, vo;
+      if (fast) {
+        sx = acc_value(ax, sT);
+        sy = neg(acc_value(ay, sT));
+        vo = fix_to_double(vof, 60);
       } else {
+        // FP64 form of the whole bus, pairs in list order
+        const VoltD Vo = volt_fp64(rec4, xi, nb, o - gb0, o);
+        vo = Vo.v;
+        rvo = Vo.rv;
         sx = 0.0;
         sy = 0.0;
         bool unused = false;
         for (int32_t j = 0; j < D; ++j) {
           const int64_t q = q0 + 32 * j;
-          const int4 m = __ldg(v.slot_meta + q);
-          if (m.y < 0) continue;
-          const double2 Gi = slot_gb<MASKED>(v, a, m, __ldg(a.sgb + q), outage, st_base, unused);
-          const EndTerms tm = end_terms(Gi, Eo, rec[2 * m.x]);
+          const int4 m = __ldg(v.slot_idx + q);
+          if (m.z < 0) continue;
+          const double2 Gi = slot_gb<MASKED>(v, a, m.z, m.w, __ldg(a.sgb + q), outage, st_base, unused);
+          const VoltD Vk = volt_fp64(rec4, xi, nb, m.x - gb0, m.x);
+          const EndTerms tm = end_terms(Gi, Vo.E, Vk.E);
           sx = __dadd_rn(sx, tm.X);
           sy = __dadd_rn(sy, tm.Y);
+          if (WJ) {
+            const int32_t ot = (short)(m.y & 0xffff), ov = m.y >> 16;
+            if (ot >= 0) {
+              rs.p(ot, neg(tm.Y));
+              rs.q(ot, tm.X);
+            }
+            if (ov >= 0) {
+              rs.p(ov, __dmul_rn(-tm.X, Vk.rv));
+              rs.q(ov, __dmul_rn(-tm.Y, Vk.rv));
+            }
+          }
         }
       }
       // A^, C^: built (every end in service), else re-summed over the ends in
       // service in the same order as the built value
       if (MASKED && any_out) hat = masked_hat(v, a, q0, D, outage, st_base, o);
-      finalize_bus<WF, WJ>(v, a, inst, g, o, gb0_of(v, g), v.grid_nbus[g], xi, vi, vr.x, vr.y, sx, sy, hat.x,
-                           hat.y, bm, bm2, inj);
+      finalize_bus<WF, WJ>(v, a, inst, g, o, gb0, nb, xi, vi, rs, vo, rvo, sx, sy, hat.x, hat.y, bm, bm2, inj);
+    }
+    if (staged) {
+      // the lead lane writes its bus's rows out whole, two values per store
+      if (lead) {
+        const bool ext = v.formulation == PF_EXTENDED;
+        const int32_t lp = bm2.z + (ext && o - gb0_of(v, g) == v.grid_slack[g] ? 1 : 0);
+        const int32_t lq = bm2.z + (ext && bm2.w >= 0 ? 1 : 0);
+        if (bm.z >= 0) write_row(vi + bm.z, rs.srow, lp);
+        if (bm.w >= 0) write_row(vi + bm.w, rs.srow + kStageLen, lq);
+      }
+      __syncwarp();                              // the next round reuses the rows
     }
   }
   // Every CTA leaves the loop once, after a claim past the last unit; the last
@@ -638,10 +928,10 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED, DYN>:
 }
 
 // Buses with more than 32 ends, one warp each (launched after k_fused, so the
-// phasor records are complete).  Lane l takes ends l, l + 32, l + 64, ... of
+// records are complete), in FP64.  Lane l takes ends l, l + 32, l + 64, ... of
 // the bus's list and sums them in that order; the 32 partial sums are then
 // combined by a fixed butterfly, so the result depends on neither the
-// tuning nor the schedule.  Off-diagonal entries as in k_fused.
+// tuning nor the schedule.  Off-diagonal entries as in k_fused's FP64 form.
 template <int ITEMS, bool WF, bool WJ, bool MASKED>
 __global__ void __launch_bounds__(32) k_fused_large(View v, EvalArgs a) {
   const int lane = threadIdx.x & 31;
@@ -651,13 +941,14 @@ __global__ void __launch_bounds__(32) k_fused_large(View v, EvalArgs a) {
     const int32_t o = lr.y;
     const int g = __ldg(v.inst_grid + inst);
     const double *__restrict__ xi = a.x + __ldg(v.inst_x_off + inst);
-    const double2 *__restrict__ rec = v.phasor + 2 * __ldg(v.inst_rec_base + inst);
+    const int4 *__restrict__ rec4 = reinterpret_cast<const int4 *>(v.phasor) + 2 * __ldg(v.inst_rec_base + inst);
     double *__restrict__ vi = WJ ? a.vals + __ldg(v.inst_v_off + inst) : nullptr;
     const int32_t outage = MASKED ? v.inst_outage[inst] : -1;
     const int64_t st_base = MASKED ? v.inst_br_off[inst] - v.grid_br_off[g] : 0;
     const int32_t e0 = __ldg(v.inc_ptr + o), e1 = __ldg(v.inc_ptr + o + 1);
-    const double2 Eo = rec[2 * o];
-    const double2 vr = rec[2 * o + 1];
+    const int64_t gb0 = gb0_of(v, g);
+    const int32_t nb = v.grid_nbus[g];
+    const VoltD Vo = volt_fp64(rec4, xi, nb, o - gb0, o);
     double sx = 0.0, sy = 0.0, acc_ma = 0.0, acc_mc = 0.0;
     for (int32_t cs = e0; cs < e1; cs += 32 * ITEMS) {
       int4 meta[ITEMS];
@@ -682,7 +973,8 @@ __global__ void __launch_bounds__(32) k_fused_large(View v, EvalArgs a) {
           if (!in) Gi = make_double2(0.0, 0.0);
         }
         const int32_t k = meta[it].y;
-        const EndTerms tm = end_terms(Gi, Eo, rec[2 * k]);
+        const VoltD Vk = volt_fp64(rec4, xi, nb, k - gb0, k);
+        const EndTerms tm = end_terms(Gi, Vo.E, Vk.E);
         sx = __dadd_rn(sx, tm.X);
         sy = __dadd_rn(sy, tm.Y);
         if (MASKED) {
@@ -693,9 +985,9 @@ __global__ void __launch_bounds__(32) k_fused_large(View v, EvalArgs a) {
         if (WJ) {
           const int4 p = __ldg(v.inc_pos + e);
           if (meta[it].z == 1) {
-            write_pair(vi, p, tm.X, tm.Y, rec[2 * k + 1].y);
+            write_pair(vi, p, tm.X, tm.Y, Vk.rv);
           } else if (meta[it].z > 1) {
-            write_group(v, a, e, meta[it].z, o, k, p, rec, vi, MASKED, outage, st_base);
+            write_group(v, a, e, meta[it].z, Vo.E, Vk, p, vi, MASKED, outage, st_base);
           }
         }
       }
@@ -722,8 +1014,10 @@ __global__ void __launch_bounds__(32) k_fused_large(View v, EvalArgs a) {
         ch = hat.y;
       }
       const double2 inj = WF ? __ldg(v.bus_inj + o) : make_double2(0.0, 0.0);
-      finalize_bus<WF, WJ>(v, a, inst, g, o, gb0_of(v, g), v.grid_nbus[g], xi, vi, vr.x, vr.y, sx, sy, ah, ch,
-                           __ldg(v.bus_meta + o), __ldg(v.bus_meta2 + o), inj);
+      const int4 bm = __ldg(v.bus_meta + o);
+      const RowSink rs{nullptr, vi, bm.z, bm.w};
+      finalize_bus<WF, WJ>(v, a, inst, g, o, gb0, nb, xi, vi, rs, Vo.v, Vo.rv, sx, sy, ah, ch, bm,
+                           __ldg(v.bus_meta2 + o), inj);
     }
   }
 }
@@ -743,7 +1037,7 @@ int launch_fused_t(const View &v, int num_sms, const pf_tuning &t, const EvalArg
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(32);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = WJ ? kStageBytes : 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -804,6 +1098,7 @@ void built_coefficients(const View &v, EvalArgs &a) {
   a.ac = v.inc_ac;
   a.hat = v.bus_hat;
   a.sgb = v.slot_gb;
+  a.sgbx = v.slot_gbx;
   a.sac = v.slot_ac;
   a.rhat = v.rbus_hat;
 }
@@ -819,12 +1114,13 @@ __global__ void k_sincos(const double *__restrict__ t, int64_t n, const longlong
 
 }  // namespace
 
-int launch_phasor(const View &v, int num_sms, const double *x, cudaStream_t s) {
+int launch_phasor(const View &v, int num_sms, const double *x, cudaStream_t s, bool fixed) {
   (void)num_sms;
   const int tb = 256;
   const int64_t blocks = (v.n_bus_inst - v.bus_inst_begin + tb - 1) / tb;
   if (blocks <= 0) return PF_OK;
-  k_phasor<<<(unsigned)blocks, tb, 0, s>>>(v, x);
+  if (fixed) k_phasor_fx<<<(unsigned)blocks, tb, 0, s>>>(v, x);
+  else k_phasor<<<(unsigned)blocks, tb, 0, s>>>(v, x);
   PF_CUDA_TRY(cudaGetLastError());
   return PF_OK;
 }
@@ -863,12 +1159,13 @@ int launch_eval_stages(Ctx &c, int stages, const double *x, const pf_overrides *
       a.ac = c.ov_ac;
       a.hat = c.ov_hat;
       a.sgb = c.ov_slot_gb;
+      a.sgbx = c.ov_slot_gbx;
       a.sac = c.ov_slot_ac;
       a.rhat = c.ov_rbus_hat;
     }
   }
   const bool masked = c.any_outage || a.status != nullptr;
-  if (stages & 1) PF_TRY(launch_phasor(c.v, c.num_sms, x, s));
+  if (stages & 1) PF_TRY(launch_phasor(c.v, c.num_sms, x, s, true));
   if (!(stages & 2)) return PF_OK;
   // the fused stage alone with per-call branch parameters: the kernel that
   // wrote its coefficients comes directly before it
@@ -889,7 +1186,7 @@ int launch_eval_range(Ctx &c, int i0, int i1, const double *x, double *F, double
   a.split = c.tuning.split_rounds ? 1 : 0;
   a.work = c.work_ctr;
   built_coefficients(c.v, a);
-  PF_TRY(launch_phasor(v, c.num_sms, x, s));
+  PF_TRY(launch_phasor(v, c.num_sms, x, s, true));
   return launch_fused(v, c.num_sms, c.tuning, a, c.any_outage, s);
 }
 
@@ -908,7 +1205,7 @@ int launch_eval_scratch(Ctx &c, const double *x, double *F, double *vals, double
   a.split = c.tuning.split_rounds ? 1 : 0;
   a.work = c.work_ctr;
   built_coefficients(c.v, a);
-  PF_TRY(launch_phasor(v, c.num_sms, x, s));
+  PF_TRY(launch_phasor(v, c.num_sms, x, s, true));
   return launch_fused(v, c.num_sms, c.tuning, a, c.any_outage, s);
 }
 

@@ -30,6 +30,35 @@ constexpr int kMaxGroup = 32;      // parallel branches between one pair of buse
 constexpr int kLaneMaxDegree = 32;
 constexpr int kSinCosTable = 32768;  // table of (cos, sin)(i pi / 16384)
 
+// Fixed-point form of the evaluation kernels (pf_eval.cu).  The merged branch
+// coefficients (G, B) of a slot are stored as round((G, B) 2^(59 - coef_log2)),
+// where 2^coef_log2 bounds |G| and |B| (over the sums of |G|, |B| of a group
+// of parallel branches, so that any subset under a mask stays in range), as
+// 30-bit limbs (value = h 2^30 + l, 0 <= l < 2^30).  kMaxCoefLog2 caps that
+// bound: a slot with a larger coefficient holds kBadLimb in h and its buses
+// are evaluated in FP64 instead.  kBadLimb also marks a per-bus record whose
+// voltage is outside (-2, 2) or whose angle is not finite.
+constexpr int kMaxCoefLog2 = 12;
+constexpr long long kBadFix = (long long)0x8000000000000000ULL;
+constexpr int kBadLimb = (int)0x80000000;
+
+// round(g * scale) for a power-of-two scale, or kBadFix when the result would
+// not be below 2^59 in magnitude (or g is not finite).  The build and the
+// masked evaluation path both convert with this function, so a group
+// re-summed under a mask with every branch in service gives the built bits.
+__device__ __forceinline__ long long to_fix(double g, double scale) {
+  const double s = __dmul_rn(g, scale);                // exact: scale is a power of two
+  if (!(fabs(s) < 0x1p59)) return kBadFix;
+  return __double2ll_rn(s);
+}
+
+// (G, B) fixed-point values as limbs {G h, G l, B h, B l}; kBadLimb marks a
+// value out of range.
+__device__ __forceinline__ int4 coef_limbs(long long g, long long b) {
+  if (g == kBadFix || b == kBadFix) return make_int4(kBadLimb, 0, kBadLimb, 0);
+  return make_int4((int)(g >> 30), (int)(g & 0x3fffffff), (int)(b >> 30), (int)(b & 0x3fffffff));
+}
+
 // Grid of a kernel whose CTAs walk `work` units with a grid-stride loop,
 // capped at ctas_per_sm CTAs per SM when that is set.  The units of a grid
 // alternate between heavy and light rounds, so a capped grid is made odd:
@@ -131,14 +160,24 @@ struct View {
   const int4 *slot_pos;                       // the group's four CSR positions
   const double2 *slot_gb, *slot_ac;           // the group's coefficients summed in incidence order
   const double2 *slot_gbm;                    // the same for the group's mirror ends (at the other bus)
+  const int4 *slot_gbx;                       // slot_gb in fixed point (see to_fix, coef_limbs)
+  const int4 *slot_idx;                       // {other bus, in-row offsets of (theta_k, V_k) as two int16
+                                              //  (-1 absent), group length (-1 padding), code of a
+                                              //  single branch or first end of a group}
+  int coef_log2;                              // 2^coef_log2 bounds the coefficients of slot_gbx
+  double coef_scale;                          // 2^(59 - coef_log2)
 
   // per instance
   const int32_t *inst_grid, *inst_outage;     // outage: global branch id or -1
   const int64_t *inst_x_off, *inst_f_off, *inst_v_off, *inst_bus_off, *inst_br_off;
   const int64_t *inst_gen_off;                // extended: generators of earlier instances
 
-  // scratch
-  double2 *phasor;                            // [2 n_bus_inst]: (V cos theta, V sin theta), (V, 1/V) per bus
+  // scratch: one 32-byte record per instance bus.  The F / J kernels use the
+  // fixed-point form {cos theta 2^60, sin theta 2^60, V 2^60 as 30-bit limbs
+  // (V h = kBadLimb when |V| >= 2 or theta is not finite), bits of 1/V}; the
+  // adjoint kernels the FP64 form {V cos theta, V sin theta, V, 1/V}
+  // (launch_phasor chooses).
+  double2 *phasor;
   int32_t *dev_error;
   const longlong2 *sincos_fix;                // [kSinCosTable] (cos, sin)(i pi / 16384) times 2^62, rounded
 };
@@ -170,6 +209,7 @@ struct Ctx {
   // incidence order and permuted to slot / round order
   double2 *ov_gb = nullptr, *ov_ac = nullptr, *ov_hat = nullptr;
   double2 *ov_slot_gb = nullptr, *ov_slot_ac = nullptr, *ov_slot_gbm = nullptr, *ov_rbus_hat = nullptr;
+  int4 *ov_slot_gbx = nullptr;
   int64_t n_slots = 0, n_rounds = 0;
   std::vector<int64_t> grid_round_off;
   std::vector<int64_t> lane_off, large_off;   // per instance: first unit of k_fused / k_fused_large
@@ -276,8 +316,10 @@ int fdlf(Ctx &c, double *x, double tol, int max_iter, cudaStream_t s, pf_newton_
 int newton_update(Ctx &c, double *x, const double *dx, cudaStream_t s);
 // F and J of the instances [i0, i1) only (pf_eval.cu; built coefficients, no overrides).
 int launch_eval_range(Ctx &c, int i0, int i1, const double *x, double *F, double *vals, cudaStream_t s);
-// (cos theta, sin theta) and V of every instance bus into v.phasor (pf_eval.cu).
-int launch_phasor(const View &v, int num_sms, const double *x, cudaStream_t s);
+// The per-bus records of every instance bus into v.phasor (pf_eval.cu): the
+// fixed-point form of the F / J kernels (fixed = true) or the FP64 form of the
+// adjoint kernels.
+int launch_phasor(const View &v, int num_sms, const double *x, cudaStream_t s, bool fixed);
 // Per-end coefficients (G, B, A, C) and per-bus sums (A^, C^) from the branch
 // parameters; any of r, x, b, tap may be overridden by device arrays.
 int compute_coefficients(Ctx &c, const double *r, const double *x, const double *b,

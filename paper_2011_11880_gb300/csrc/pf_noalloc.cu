@@ -6,10 +6,10 @@
 // memory up front, or plug-in layers that may only use memory handed to
 // them.  pf_residual_jacobian_static serves them: it allocates nothing.
 // Inputs, outputs and the built context come from the caller; the only
-// scratch the evaluation needs -- (cos theta, sin theta) and V of every bus
-// of every instance -- lives in g_static_phasor below, a fixed device array
-// that exists on every GPU that loads this library until the process
-// exits.
+// scratch the evaluation needs -- the 32-byte per-bus record of every bus of
+// every instance (the unit phasor (cos theta, sin theta) and V in fixed point,
+// and 1/V) -- lives in g_static_phasor below, a fixed device array that
+// exists on every GPU that loads this library until the process exits.
 #include <mutex>
 #include <string>
 #include <vector>
@@ -19,8 +19,8 @@
 namespace pf {
 namespace {
 
-// Capacity of the static scratch: 2^18 instance-buses, two double2 each
-// ((cos theta, sin theta) and (V, 0)): 8 MiB.
+// Capacity of the static scratch: 2^18 instance-buses, one 32-byte record
+// each: 8 MiB.
 constexpr int64_t kStaticPhasorBuses = int64_t(1) << 18;
 
 static __device__ __align__(256) double2 g_static_phasor[2 * kStaticPhasorBuses];
