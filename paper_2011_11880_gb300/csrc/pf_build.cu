@@ -702,7 +702,9 @@ __global__ void k_rbus_fill(View v, int64_t n, const int32_t *rbus, const double
 // units take them heaviest and lightest alternately (n-1, 0, n-2, 1, ...), so
 // the CTAs that run side by side -- all of them, when one instance fills less
 // than a wave -- carry a mix of long and short rounds.
-__global__ void k_unit_fill(View v, const int64_t *lane_off, int4 *unit) {
+// Each unit also carries its grid and instance offsets, so that the
+// evaluation kernel has every pointer of a unit after one round of loads.
+__global__ void k_unit_fill(View v, const int64_t *lane_off, int4 *unit, int4 *info, longlong2 *ptr) {
   const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= v.n_lane_units) return;
   const int inst = find_segment(lane_off, v.n_inst, u);
@@ -711,6 +713,9 @@ __global__ void k_unit_fill(View v, const int64_t *lane_off, int4 *unit) {
   const int64_t r = v.grid_round_off[g] + ((j & 1) ? (j >> 1) : n - 1 - (j >> 1));
   const int4 d = v.round_desc[r];
   unit[u] = make_int4(inst, (int32_t)r, d.x, d.y | (d.z << 8));
+  info[u] = make_int4(g, v.grid_nbus[g], (int32_t)v.grid_bus_off[g], 0);
+  ptr[2 * u] = make_longlong2(v.inst_x_off[inst], v.inst_f_off[inst]);
+  ptr[2 * u + 1] = make_longlong2(v.inst_v_off[inst], v.inst_bus_off[inst] - v.grid_bus_off[g]);
 }
 
 // per large bus of every instance: its instance and bus (the rounds after
@@ -722,6 +727,15 @@ __global__ void k_large_fill(View v, const int64_t *large_off, const int64_t *la
   const int g = v.inst_grid[inst];
   const int64_t r = v.grid_round_off[g] + lane_rounds[g] + (u - large_off[inst]);
   out[u] = make_int2(inst, v.rbus[32 * r]);
+}
+
+// per chunk of instance-buses: the instance of its first bus; one more entry
+// for the last bus
+__global__ void k_chunk_inst(View v, int64_t n_chunks, int32_t *out) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c > n_chunks) return;
+  const int64_t q = c < n_chunks ? (c << kChunkLog2) : v.n_bus_inst - 1;
+  out[c] = find_segment(v.inst_bus_off, v.n_inst, q);
 }
 
 __global__ void k_rec_base(View v, int64_t *base) {
@@ -968,19 +982,32 @@ int build_rounds(Ctx &c, cudaStream_t s) {
   c.lane_off = lane_off;
   c.large_off = large_off;
   int64_t *d_lane_off, *d_large_off, *d_lane_rounds, *rec_base;
-  int4 *unit;
+  int4 *unit, *uinfo;
+  longlong2 *uptr;
   int2 *large;
   PF_TRY(upload(c, &d_lane_off, lane_off, s));
   PF_TRY(upload(c, &d_large_off, large_off, s));
   PF_TRY(upload(c, &d_lane_rounds, lane_rounds, s));
   PF_TRY(dev_alloc(c, &unit, v.n_lane_units));
+  PF_TRY(dev_alloc(c, &uinfo, v.n_lane_units));
+  PF_TRY(dev_alloc(c, &uptr, 2 * v.n_lane_units));
+  if (c.v.n_bus >= 0x7fffffffLL) return fail(PF_ERR_UNSUPPORTED, "more than 2^31 buses");
   PF_TRY(dev_alloc(c, &large, v.n_large_units));
   PF_TRY(dev_alloc(c, &rec_base, I));
-  if (v.n_lane_units > 0) k_unit_fill<<<nblk(v.n_lane_units), TB, 0, s>>>(v, d_lane_off, unit);
+  if (v.n_lane_units > 0) k_unit_fill<<<nblk(v.n_lane_units), TB, 0, s>>>(v, d_lane_off, unit, uinfo, uptr);
   if (v.n_large_units > 0) k_large_fill<<<nblk(v.n_large_units), TB, 0, s>>>(v, d_large_off, d_lane_rounds, large);
   k_rec_base<<<nblk(I), TB, 0, s>>>(v, rec_base);
+  {
+    const int64_t n_chunks = (v.n_bus_inst + (1 << kChunkLog2) - 1) >> kChunkLog2;
+    int32_t *ci;
+    PF_TRY(dev_alloc(c, &ci, n_chunks + 1));
+    k_chunk_inst<<<nblk(n_chunks + 1), TB, 0, s>>>(v, n_chunks, ci);
+    v.chunk_inst = ci;
+  }
   PF_CUDA_TRY(cudaGetLastError());
   v.unit_rec = unit;
+  v.unit_info = uinfo;
+  v.unit_ptr = uptr;
   v.large_rec = large;
   v.inst_rec_base = rec_base;
   PF_CUDA_TRY(cudaStreamSynchronize(s));

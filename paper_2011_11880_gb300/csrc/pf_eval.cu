@@ -184,19 +184,16 @@ __device__ __forceinline__ double dead_sub(double vm) {
   return (__double2hiint(vm) & 0x7ff00000) < 0x20b00000 ? kDeadV : vm;   // |V| < 2^-500
 }
 
-// The instance of instance-bus q; the block looks up the instances of its
-// first and last bus once (s_inst), a thread searches only between them.
-__device__ __forceinline__ int phasor_instance(const View &v, int64_t q, const int *s_inst) {
-  const int i0 = v.n_inst > 1 ? s_inst[0] : 0, i1 = v.n_inst > 1 ? s_inst[1] : 0;
+// The instance of instance-bus q: chunk_inst holds the instance of the first
+// bus of every chunk of 2^kChunkLog2 instance-buses, so a thread searches only
+// between its chunk's first instance and the next chunk's (no search at all
+// when one instance spans the chunk, as it mostly does for grids larger than
+// a chunk), and no thread waits for another.
+__device__ __forceinline__ int bus_instance(const View &v, int64_t q) {
+  if (v.n_inst <= 1) return 0;
+  const int64_t c = q >> kChunkLog2;
+  const int i0 = __ldg(v.chunk_inst + c), i1 = __ldg(v.chunk_inst + c + 1);
   return i0 == i1 ? i0 : i0 + find_segment(v.inst_bus_off + i0, i1 - i0 + 1, q);
-}
-
-__device__ __forceinline__ void phasor_block_instances(const View &v, int64_t q0, int *s_inst) {
-  if (v.n_inst > 1 && threadIdx.x < 2) {
-    const int64_t key = threadIdx.x == 0 ? q0 : min(q0 + (int64_t)blockDim.x, v.n_bus_inst) - 1;
-    s_inst[threadIdx.x] = find_segment(v.inst_bus_off, v.n_inst, key);
-  }
-  __syncthreads();
 }
 
 // FP64 records for the adjoint kernels, one thread per instance-bus:
@@ -205,12 +202,9 @@ __device__ __forceinline__ void phasor_block_instances(const View &v, int64_t q0
 __global__ void __launch_bounds__(256) k_phasor(View v, const double *__restrict__ x) {
   // Let the dependent kernel start launching; it waits for this grid's results.
   cudaTriggerProgrammaticLaunchCompletion();
-  __shared__ int s_inst[2];
-  const int64_t q0 = v.bus_inst_begin + (int64_t)blockIdx.x * blockDim.x;
-  const int64_t q = q0 + threadIdx.x;
-  phasor_block_instances(v, q0, s_inst);
+  const int64_t q = v.bus_inst_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q < v.n_bus_inst) {
-    const int inst = phasor_instance(v, q, s_inst);
+    const int inst = bus_instance(v, q);
     const int64_t lb = q - v.inst_bus_off[inst];
     const double *xi = x + v.inst_x_off[inst];
     const double th = __ldg(xi + lb);
@@ -246,12 +240,9 @@ __device__ __forceinline__ int2 limbs(long long z) { return make_int2((int)(z >>
 // the dead-bus substitution) serves the own bus's diagonal values.
 __global__ void __launch_bounds__(256) k_phasor_fx(View v, const double *__restrict__ x) {
   cudaTriggerProgrammaticLaunchCompletion();
-  __shared__ int s_inst[2];
-  const int64_t q0 = v.bus_inst_begin + (int64_t)blockIdx.x * blockDim.x;
-  const int64_t q = q0 + threadIdx.x;
-  phasor_block_instances(v, q0, s_inst);
+  const int64_t q = v.bus_inst_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q < v.n_bus_inst) {
-    const int inst = phasor_instance(v, q, s_inst);
+    const int inst = bus_instance(v, q);
     const int64_t lb = q - v.inst_bus_off[inst];
     const double *xi = x + v.inst_x_off[inst];
     const double th = __ldg(xi + lb);
@@ -584,7 +575,8 @@ struct RowSink {
 // values through the sink.
 template <bool WF, bool WJ>
 __device__ __forceinline__ void finalize_bus(const View &v, const EvalArgs &a, int inst, int g, int32_t o,
-                                             int64_t gb0, int32_t nb, const double *xi, double *vi, const RowSink &rs,
+                                             int64_t gb0, int32_t nb, const double *xi, double *Fi, double *vi,
+                                             const RowSink &rs,
                                              double vo, double rvo, double sx, double sy, double ah, double ch,
                                              int4 bm, int4 bm2, double2 inj) {
   const int64_t lb = o - gb0;
@@ -595,7 +587,6 @@ __device__ __forceinline__ void finalize_bus(const View &v, const EvalArgs &a, i
   const double tp = __fma_rn(v2, ah, -sx);          // V_o^2 A^ - S_X
   const double tq = __fma_rn(v2, ch, sy);           // V_o^2 C^ + S_Y
   if (WF) {
-    double *__restrict__ Fi = a.F + v.inst_f_off[inst];
     const double pin = a.p_inj ? a.p_inj[v.inst_bus_off[inst] + lb] : inj.x;
     const double qin = a.q_inj ? a.q_inj[v.inst_bus_off[inst] + lb] : inj.y;
     double fp = __dsub_rn(tp, pin);
@@ -751,19 +742,23 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED, DYN>:
   }
   for (; u < n_units; u = work ? (int64_t)__shfl_sync(0xffffffffu, claim, 0) : u + gridDim.x) {
     if (work && lane == 0) claim = atomicAdd(work, 1ULL);
-    const int4 ur = __ldg(v.unit_rec + (u >> split));   // {instance, round, first slot, D | buses << 8}
+    const int32_t uu = (int32_t)(u >> split);
+    const int4 ur = __ldg(v.unit_rec + uu);     // {instance, round, first slot, D | buses << 8}
+    const int4 ui = __ldg(v.unit_info + uu);    // {grid, buses of the grid, first bus of the grid}
+    const longlong2 up0 = __ldg(v.unit_ptr + 2 * uu), up1 = __ldg(v.unit_ptr + 2 * uu + 1);
     const int inst = ur.x;
-    const int g = __ldg(v.inst_grid + inst);
-    const double *__restrict__ xi = a.x + __ldg(v.inst_x_off + inst);
+    const int g = ui.x;
+    const double *__restrict__ xi = a.x + up0.x;
+    double *__restrict__ Fi = WF ? a.F + up0.y : nullptr;
     // unit phasor limbs at rec4[2 k], {V limbs, bits of 1/V} at rec4[2 k + 1], by global bus id k
-    const int4 *__restrict__ rec4 = reinterpret_cast<const int4 *>(v.phasor) + 2 * __ldg(v.inst_rec_base + inst);
-    double *__restrict__ vi = WJ ? a.vals + __ldg(v.inst_v_off + inst) : nullptr;
+    const int4 *__restrict__ rec4 = reinterpret_cast<const int4 *>(v.phasor) + 2 * up1.y;
+    double *__restrict__ vi = WJ ? a.vals + up1.x : nullptr;
     const int32_t outage = MASKED ? v.inst_outage[inst] : -1;
     const int64_t st_base = MASKED ? v.inst_br_off[inst] - v.grid_br_off[g] : 0;
     const int32_t D = ur.w & 0xff;
     const bool staged = WJ && D <= kStageMaxD;
 
-    // this lane's bus: records in round order, fetched before the wait
+    // this lane's bus: its records in round order
     const int bl = bl0 + (split ? 16 * (int)(u & 1) : 0);
     const int32_t rb = 32 * ur.y + bl;            // below 2^31: the build checks the round count
     const bool owner = bl < (ur.w >> 8);
@@ -774,11 +769,6 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED, DYN>:
     if (owner) {
       o = __ldg(v.rbus + rb);
       bm = __ldg(v.rbus_meta + rb);
-    }
-    if (lead) {
-      bm2 = __ldg(v.rbus_meta2 + rb);
-      hat = __ldg(a.rhat + rb);
-      if (WF) inj = __ldg(v.rbus_inj + rb);
     }
     const RowSink rs{staged ? s_stage + bl0 * kStageStride : nullptr, vi, bm.z, bm.w};
     Acc128 ax{0ULL, 0LL}, ay{0ULL, 0LL};       // exact S_X and -S_Y
@@ -862,8 +852,12 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED, DYN>:
       __syncwarp();                              // the FP64 path below rewrites the other lane's values
     }
     if (lead) {
-      const int64_t gb0 = gb0_of(v, g);
-      const int32_t nb = v.grid_nbus[g];
+      // the bus's own row data, loaded only now (fewer registers live across the pairs)
+      bm2 = __ldg(v.rbus_meta2 + rb);
+      hat = __ldg(a.rhat + rb);
+      if (WF) inj = __ldg(v.rbus_inj + rb);
+      const int64_t gb0 = ui.z;
+      const int32_t nb = ui.y;
       double sx, sy, vo;
       if (fast) {
         sx = acc_value(ax, sT);
@@ -902,13 +896,13 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED, DYN>:
       // A^, C^: built (every end in service), else re-summed over the ends in
       // service in the same order as the built value
       if (MASKED && any_out) hat = masked_hat(v, a, q0, D, outage, st_base, o);
-      finalize_bus<WF, WJ>(v, a, inst, g, o, gb0, nb, xi, vi, rs, vo, rvo, sx, sy, hat.x, hat.y, bm, bm2, inj);
+      finalize_bus<WF, WJ>(v, a, inst, g, o, gb0, nb, xi, Fi, vi, rs, vo, rvo, sx, sy, hat.x, hat.y, bm, bm2, inj);
     }
     if (staged) {
       // the lead lane writes its bus's rows out whole, two values per store
       if (lead) {
         const bool ext = v.formulation == PF_EXTENDED;
-        const int32_t lp = bm2.z + (ext && o - gb0_of(v, g) == v.grid_slack[g] ? 1 : 0);
+        const int32_t lp = bm2.z + (ext && o - ui.z == v.grid_slack[g] ? 1 : 0);
         const int32_t lq = bm2.z + (ext && bm2.w >= 0 ? 1 : 0);
         if (bm.z >= 0) write_row(vi + bm.z, rs.srow, lp);
         if (bm.w >= 0) write_row(vi + bm.w, rs.srow + kStageLen, lq);
@@ -1016,7 +1010,8 @@ __global__ void __launch_bounds__(32) k_fused_large(View v, EvalArgs a) {
       const double2 inj = WF ? __ldg(v.bus_inj + o) : make_double2(0.0, 0.0);
       const int4 bm = __ldg(v.bus_meta + o);
       const RowSink rs{nullptr, vi, bm.z, bm.w};
-      finalize_bus<WF, WJ>(v, a, inst, g, o, gb0, nb, xi, vi, rs, Vo.v, Vo.rv, sx, sy, ah, ch, bm,
+      finalize_bus<WF, WJ>(v, a, inst, g, o, gb0, nb, xi, WF ? a.F + v.inst_f_off[inst] : nullptr, vi, rs, Vo.v,
+                           Vo.rv, sx, sy, ah, ch, bm,
                            __ldg(v.bus_meta2 + o), inj);
     }
   }
@@ -1085,6 +1080,8 @@ int launch_fused(const View &v, int num_sms, const pf_tuning &t, const EvalArgs 
 View range_view(const Ctx &c, int i0, int i1) {
   View v = c.v;
   v.unit_rec = c.v.unit_rec + c.lane_off[i0];
+  v.unit_info = c.v.unit_info + c.lane_off[i0];
+  v.unit_ptr = c.v.unit_ptr + 2 * c.lane_off[i0];
   v.n_lane_units = c.lane_off[i1] - c.lane_off[i0];
   v.large_rec = c.v.large_rec + c.large_off[i0];
   v.n_large_units = c.large_off[i1] - c.large_off[i0];

@@ -29,6 +29,9 @@ constexpr int kMaxGroup = 32;      // parallel branches between one pair of buse
 // kLaneMaxDegree neighbours is evaluated by a whole warp.
 constexpr int kLaneMaxDegree = 32;
 constexpr int kSinCosTable = 32768;  // table of (cos, sin)(i pi / 16384)
+// Instance-buses are grouped in chunks of 2^kChunkLog2 for the per-bus kernels'
+// instance lookup (View::chunk_inst).
+constexpr int kChunkLog2 = 8;
 
 // Fixed-point form of the evaluation kernels (pf_eval.cu).  The merged branch
 // coefficients (G, B) of a slot are stored as round((G, B) 2^(59 - coef_log2)),
@@ -148,6 +151,9 @@ struct View {
   const int64_t *grid_round_off;              // [n_grids+1]
   const int4 *unit_rec;                       // per round of 32 buses of every instance:
                                               //   {instance, round, first slot, items per lane | buses << 8}
+  const int4 *unit_info;                      // per unit: {grid, buses of the grid, first bus of the grid, 0}
+  const longlong2 *unit_ptr;                  // per unit, two entries: {x offset, F offset},
+                                              //   {J offset, record base} of its instance
   const int2 *large_rec;                      // per large bus of every instance: {instance, bus}
   const int64_t *inst_rec_base;               // per instance: inst_bus_off - grid_bus_off of its grid
   const int4 *round_desc;                     // {first slot, items per lane, buses, flags (1 = one large bus)}
@@ -171,6 +177,8 @@ struct View {
   const int32_t *inst_grid, *inst_outage;     // outage: global branch id or -1
   const int64_t *inst_x_off, *inst_f_off, *inst_v_off, *inst_bus_off, *inst_br_off;
   const int64_t *inst_gen_off;                // extended: generators of earlier instances
+  const int32_t *chunk_inst;                  // per chunk of 2^kChunkLog2 instance-buses (and one past the
+                                              //   last): the instance of its first bus (of the last bus)
 
   // scratch: one 32-byte record per instance bus.  The F / J kernels use the
   // fixed-point form {cos theta 2^60, sin theta 2^60, V 2^60 as 30-bit limbs
