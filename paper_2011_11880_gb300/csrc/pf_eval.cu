@@ -311,14 +311,14 @@ __device__ __forceinline__ long long mul60(int2 a, int2 b) {
 // z 2^-s as a double, rounded to nearest (ties away from zero); 2^-s |z| must
 // be a normal double.
 __device__ __forceinline__ double fix_to_double(long long z, int s) {
-  if (z == 0) return 0.0;
+  // branch-free: for z = 0 the bits formed below are discarded by the final select
   const unsigned long long sign = (unsigned long long)z & 0x8000000000000000ULL;
   const unsigned long long a = sign ? 0ULL - (unsigned long long)z : (unsigned long long)z;
   const int lz = __clzll((long long)a);
-  const unsigned long long n = a << lz;                                              // top bit 63
+  const unsigned long long n = a << (lz & 63);                                       // top bit 63
   const unsigned long long mag =
       ((unsigned long long)(1086 - s - lz) << 52) + ((n >> 11) & 0xfffffffffffffULL) + ((n >> 10) & 1ULL);
-  return __longlong_as_double((long long)(sign | mag));
+  return __longlong_as_double(z == 0 ? 0LL : (long long)(sign | mag));
 }
 
 // Exact sums on the integer pipe: a 128-bit two's-complement accumulator of
@@ -684,6 +684,154 @@ __device__ __forceinline__ Rec load_rec(const int4 *p) {
   return r;
 }
 
+// The own bus's voltage for the fixed-point pair terms, from its record:
+// E_o = V_o U_o at 2^60 as limbs (and -f_o), V_o at 2^60 and 1/V_o; `fast`
+// when V_o lies in [1/4, 2) (kBadLimb is negative).
+struct OwnV {
+  int2 eo, fo, nfo;
+  long long vof;
+  double rvo;
+  bool fast;
+};
+
+__device__ __forceinline__ OwnV own_voltage(const Rec &ro) {
+  OwnV w;
+  w.rvo = __hiloint2double(ro.w.w, ro.w.z);
+  const int2 vl = make_int2(ro.w.x, ro.w.y);
+  w.vof = ((long long)ro.w.x << 30) + ro.w.y;
+  w.fast = ro.w.x >= (1 << 28);
+  w.eo = limbs(mul60(vl, make_int2(ro.u.x, ro.u.y)));
+  const long long f = mul60(vl, make_int2(ro.u.z, ro.u.w));
+  w.fo = limbs(f);
+  w.nfo = limbs(-f);
+  return w;
+}
+
+// One pair's fixed-point terms from the neighbour's record rk and the merged
+// coefficients gx: T = (G + jB) conj(E_o) U_k and X = V_k Re T, -Y = V_k Im T,
+// all at 2^(59 - c).  `ok` is false when the record or a coefficient is
+// marked out of range.
+struct PairT {
+  long long xx, my, tr, ti;
+  bool ok;
+};
+
+__device__ __forceinline__ PairT pair_terms(const OwnV &w, const Rec &rk, int4 gx) {
+  PairT t;
+  t.ok = rk.w.x != kBadLimb && gx.x != kBadLimb && gx.z != kBadLimb;
+  const int2 ck = make_int2(rk.u.x, rk.u.y), sk = make_int2(rk.u.z, rk.u.w), vk = make_int2(rk.w.x, rk.w.y);
+  // conj(E_o) U_k 2^60
+  const long long pr = dot60(w.eo, ck, w.fo, sk);
+  const long long pi = dot60(w.eo, sk, w.nfo, ck);
+  const int2 prl = limbs(pr), pil = limbs(pi), npil = limbs(-pi);
+  // T = (G + jB) conj(E_o) U_k 2^(59 - c)
+  const int2 gl = make_int2(gx.x, gx.y), bl = make_int2(gx.z, gx.w);
+  t.tr = dot60(gl, prl, bl, npil);
+  t.ti = dot60(gl, pil, bl, prl);
+  // X = V_k Re T, -Y = V_k Im T, 2^(59 - c)
+  t.xx = mul60(vk, limbs(t.tr));
+  t.my = mul60(vk, limbs(t.ti));
+  return t;
+}
+
+// Adds a pair to the bus sums and its four J values (in-row offsets packed in
+// offs: theta_k low, V_k high, -1 absent) to the sink.
+template <bool WJ>
+__device__ __forceinline__ void put_pair(Acc128 &ax, Acc128 &ay, const RowSink &rs, int32_t offs, const PairT &t,
+                                         int sT) {
+  acc_add64(ax, t.xx);
+  acc_add64(ay, t.my);
+  if (WJ) {
+    const int32_t ot = (short)(offs & 0xffff), ov = offs >> 16;
+    if (ot >= 0) {
+      rs.p(ot, fix_to_double(t.my, sT));            // dP_o / dtheta_k = -Y
+      rs.q(ot, fix_to_double(t.xx, sT));            // dQ_o / dtheta_k = X
+    }
+    if (ov >= 0) {
+      rs.p(ov, neg(fix_to_double_cvt(t.tr, sT)));   // dP_o / dV_k = -X / V_k
+      rs.q(ov, fix_to_double_cvt(t.ti, sT));        // dQ_o / dV_k = -Y / V_k
+    }
+  }
+}
+
+// A unit's instance: its grid and where its state, outputs and records live.
+struct UnitCtx {
+  int inst, g;
+  int64_t gb0;
+  int32_t nb;
+  const double *xi;
+  double *Fi, *vi;
+  const int4 *rec4;
+  int32_t outage;
+  int64_t st_base;
+};
+
+// The rest of bus o after its pairs, on its lead lane: the sums rounded to
+// double (or, when the fixed-point form does not hold for the bus, every value
+// of the bus again in FP64 from x and the records, pairs in list order), A^
+// and C^ re-summed under a mask, the F rows and diagonal values
+// (finalize_bus), and the staged rows written out.  The slots of the bus are
+// q0 + 32 j, j < D.
+template <bool WF, bool WJ, bool MASKED>
+__device__ __forceinline__ void finish_bus(const View &v, const EvalArgs &a, const UnitCtx &uc, int32_t o,
+                                           int32_t rb, int4 bm, const RowSink &rs, bool fast, bool any_out,
+                                           const Acc128 &ax, const Acc128 &ay, const OwnV &w, int32_t D,
+                                           int32_t q0, int sT, bool staged) {
+  // the bus's own row data, loaded only now (fewer registers live across the pairs)
+  const int4 bm2 = __ldg(v.rbus_meta2 + rb);
+  double2 hat = __ldg(a.rhat + rb);
+  const double2 inj = WF ? __ldg(v.rbus_inj + rb) : make_double2(0.0, 0.0);
+  double sx, sy, vo, rvo;
+  if (fast) {
+    sx = acc_value(ax, sT);
+    sy = neg(acc_value(ay, sT));
+    vo = fix_to_double(w.vof, 60);
+    rvo = w.rvo;
+  } else {
+    // FP64 form of the whole bus, pairs in list order
+    const VoltD Vo = volt_fp64(uc.rec4, uc.xi, uc.nb, o - uc.gb0, o);
+    vo = Vo.v;
+    rvo = Vo.rv;
+    sx = 0.0;
+    sy = 0.0;
+    bool unused = false;
+    for (int32_t j = 0; j < D; ++j) {
+      const int32_t q = q0 + 32 * j;
+      const int4 m = __ldg(v.slot_idx + q);
+      if (m.z < 0) continue;
+      const double2 Gi = slot_gb<MASKED>(v, a, m.z, m.w, __ldg(a.sgb + q), uc.outage, uc.st_base, unused);
+      const VoltD Vk = volt_fp64(uc.rec4, uc.xi, uc.nb, m.x - uc.gb0, m.x);
+      const EndTerms tm = end_terms(Gi, Vo.E, Vk.E);
+      sx = __dadd_rn(sx, tm.X);
+      sy = __dadd_rn(sy, tm.Y);
+      if (WJ) {
+        const int32_t ot = (short)(m.y & 0xffff), ov = m.y >> 16;
+        if (ot >= 0) {
+          rs.p(ot, neg(tm.Y));
+          rs.q(ot, tm.X);
+        }
+        if (ov >= 0) {
+          rs.p(ov, __dmul_rn(-tm.X, Vk.rv));
+          rs.q(ov, __dmul_rn(-tm.Y, Vk.rv));
+        }
+      }
+    }
+  }
+  // A^, C^: built (every end in service), else re-summed over the ends in
+  // service in the same order as the built value
+  if (MASKED && any_out) hat = masked_hat(v, a, q0, D, uc.outage, uc.st_base, o);
+  finalize_bus<WF, WJ>(v, a, uc.inst, uc.g, o, uc.gb0, uc.nb, uc.xi, uc.Fi, uc.vi, rs, vo, rvo, sx, sy, hat.x,
+                       hat.y, bm, bm2, inj);
+  if (staged) {
+    // the rows out whole, two values per store
+    const bool ext = v.formulation == PF_EXTENDED;
+    const int32_t lp = bm2.z + (ext && o - uc.gb0 == v.grid_slack[uc.g] ? 1 : 0);
+    const int32_t lq = bm2.z + (ext && bm2.w >= 0 ? 1 : 0);
+    if (bm.z >= 0) write_row(uc.vi + bm.z, rs.srow, lp);
+    if (bm.w >= 0) write_row(uc.vi + bm.w, rs.srow + kStageLen, lq);
+  }
+}
+
 // One-warp CTAs that must fit on one SM (the register budget of k_fused).
 template <int ITEMS, bool WF, bool WJ, bool MASKED, bool DYN>
 struct FusedMinCtas {
@@ -764,8 +912,7 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED, DYN>:
     const bool owner = bl < (ur.w >> 8);
     const bool lead = owner && par == 0;         // the lane that finishes the bus
     int32_t o = 0;
-    int4 bm = make_int4(-1, -1, -1, -1), bm2 = make_int4(-1, -1, 0, -1);
-    double2 hat = make_double2(0.0, 0.0), inj = make_double2(0.0, 0.0);
+    int4 bm = make_int4(-1, -1, -1, -1);
     if (owner) {
       o = __ldg(v.rbus + rb);
       bm = __ldg(v.rbus_meta + rb);
@@ -774,9 +921,7 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED, DYN>:
     Acc128 ax{0ULL, 0LL}, ay{0ULL, 0LL};       // exact S_X and -S_Y
     bool fast = true;                            // the fixed-point form holds for this bus
     bool any_out = false;                        // masked: an end of this bus is out of service
-    int2 eo = make_int2(0, 0), fo = make_int2(0, 0), nfo = make_int2(0, 0);   // E_o 2^60 as limbs, and -f_o
-    long long vof = 0;                           // V_o 2^60
-    double rvo = 0.0;
+    OwnV w{make_int2(0, 0), make_int2(0, 0), make_int2(0, 0), 0LL, 0.0, true};   // the own bus's voltage
     const int32_t q0 = ur.z + bl;                 // slot indices are below 2^31 (checked at build)
 
     // (the first pass always runs: it waits for the records and loads the own bus's)
@@ -796,15 +941,8 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED, DYN>:
         // the per-bus records come from k_phasor_fx (programmatic dependent launch)
         cudaGridDependencySynchronize();
         if (owner) {
-          const Rec ro = load_rec(rec4 + 2 * o);
-          rvo = __hiloint2double(ro.w.w, ro.w.z);
-          const int2 vl = make_int2(ro.w.x, ro.w.y);
-          vof = ((long long)ro.w.x << 30) + ro.w.y;
-          fast = ro.w.x >= (1 << 28);            // V_o in [1/4, 2) (kBadLimb is negative)
-          eo = limbs(mul60(vl, make_int2(ro.u.x, ro.u.y)));
-          const long long f = mul60(vl, make_int2(ro.u.z, ro.u.w));
-          fo = limbs(f);
-          nfo = limbs(-f);
+          w = own_voltage(load_rec(rec4 + 2 * o));
+          fast = w.fast;                         // V_o in [1/4, 2)
         }
       }
 #pragma unroll
@@ -813,33 +951,9 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED, DYN>:
         if (len < 0) continue;
         const int32_t k = idx[it].x;
         const int4 gx = slot_gbx<MASKED>(v, a, len, idx[it].w, GX[it], outage, st_base, any_out);
-        const Rec rk = load_rec(rec4 + 2 * k);
-        fast = fast && rk.w.x != kBadLimb && gx.x != kBadLimb && gx.z != kBadLimb;
-        const int2 ck = make_int2(rk.u.x, rk.u.y), sk = make_int2(rk.u.z, rk.u.w), vk = make_int2(rk.w.x, rk.w.y);
-        // conj(E_o) U_k 2^60
-        const long long pr = dot60(eo, ck, fo, sk);
-        const long long pi = dot60(eo, sk, nfo, ck);
-        const int2 prl = limbs(pr), pil = limbs(pi), npil = limbs(-pi);
-        // T = (G + jB) conj(E_o) U_k 2^(59 - c)
-        const int2 gl = make_int2(gx.x, gx.y), bl2 = make_int2(gx.z, gx.w);
-        const long long tr = dot60(gl, prl, bl2, npil);
-        const long long ti = dot60(gl, pil, bl2, prl);
-        // X = V_k Re T, -Y = V_k Im T, 2^(59 - c)
-        const long long xx = mul60(vk, limbs(tr));
-        const long long my = mul60(vk, limbs(ti));
-        acc_add64(ax, xx);
-        acc_add64(ay, my);
-        if (WJ) {
-          const int32_t ot = (short)(idx[it].y & 0xffff), ov = idx[it].y >> 16;
-          if (ot >= 0) {
-            rs.p(ot, fix_to_double(my, sT));         // dP_o / dtheta_k = -Y
-            rs.q(ot, fix_to_double(xx, sT));         // dQ_o / dtheta_k = X
-          }
-          if (ov >= 0) {
-            rs.p(ov, neg(fix_to_double_cvt(tr, sT)));    // dP_o / dV_k = -X / V_k
-            rs.q(ov, fix_to_double_cvt(ti, sT));         // dQ_o / dV_k = -Y / V_k
-          }
-        }
+        const PairT t = pair_terms(w, load_rec(rec4 + 2 * k), gx);
+        fast = fast && t.ok;
+        put_pair<WJ>(ax, ay, rs, idx[it].y, t, sT);
       }
     }
     if (split) {
@@ -852,61 +966,10 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED, DYN>:
       __syncwarp();                              // the FP64 path below rewrites the other lane's values
     }
     if (lead) {
-      // the bus's own row data, loaded only now (fewer registers live across the pairs)
-      bm2 = __ldg(v.rbus_meta2 + rb);
-      hat = __ldg(a.rhat + rb);
-      if (WF) inj = __ldg(v.rbus_inj + rb);
-      const int64_t gb0 = ui.z;
-      const int32_t nb = ui.y;
-      double sx, sy, vo;
-      if (fast) {
-        sx = acc_value(ax, sT);
-        sy = neg(acc_value(ay, sT));
-        vo = fix_to_double(vof, 60);
-      } else {
-        // FP64 form of the whole bus, pairs in list order
-        const VoltD Vo = volt_fp64(rec4, xi, nb, o - gb0, o);
-        vo = Vo.v;
-        rvo = Vo.rv;
-        sx = 0.0;
-        sy = 0.0;
-        bool unused = false;
-        for (int32_t j = 0; j < D; ++j) {
-          const int64_t q = q0 + 32 * j;
-          const int4 m = __ldg(v.slot_idx + q);
-          if (m.z < 0) continue;
-          const double2 Gi = slot_gb<MASKED>(v, a, m.z, m.w, __ldg(a.sgb + q), outage, st_base, unused);
-          const VoltD Vk = volt_fp64(rec4, xi, nb, m.x - gb0, m.x);
-          const EndTerms tm = end_terms(Gi, Vo.E, Vk.E);
-          sx = __dadd_rn(sx, tm.X);
-          sy = __dadd_rn(sy, tm.Y);
-          if (WJ) {
-            const int32_t ot = (short)(m.y & 0xffff), ov = m.y >> 16;
-            if (ot >= 0) {
-              rs.p(ot, neg(tm.Y));
-              rs.q(ot, tm.X);
-            }
-            if (ov >= 0) {
-              rs.p(ov, __dmul_rn(-tm.X, Vk.rv));
-              rs.q(ov, __dmul_rn(-tm.Y, Vk.rv));
-            }
-          }
-        }
-      }
-      // A^, C^: built (every end in service), else re-summed over the ends in
-      // service in the same order as the built value
-      if (MASKED && any_out) hat = masked_hat(v, a, q0, D, outage, st_base, o);
-      finalize_bus<WF, WJ>(v, a, inst, g, o, gb0, nb, xi, Fi, vi, rs, vo, rvo, sx, sy, hat.x, hat.y, bm, bm2, inj);
+      const UnitCtx uc{inst, g, ui.z, ui.y, xi, Fi, vi, rec4, outage, st_base};
+      finish_bus<WF, WJ, MASKED>(v, a, uc, o, rb, bm, rs, fast, any_out, ax, ay, w, D, q0, sT, staged);
     }
     if (staged) {
-      // the lead lane writes its bus's rows out whole, two values per store
-      if (lead) {
-        const bool ext = v.formulation == PF_EXTENDED;
-        const int32_t lp = bm2.z + (ext && o - ui.z == v.grid_slack[g] ? 1 : 0);
-        const int32_t lq = bm2.z + (ext && bm2.w >= 0 ? 1 : 0);
-        if (bm.z >= 0) write_row(vi + bm.z, rs.srow, lp);
-        if (bm.w >= 0) write_row(vi + bm.w, rs.srow + kStageLen, lq);
-      }
       __syncwarp();                              // the next round reuses the rows
     }
   }

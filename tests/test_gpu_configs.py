@@ -64,6 +64,10 @@ def test_contingency_batch_full_size(P):
         rp, ci = ctx.pattern(gi)
         rpo, cio, _ = oracle.jacobian(sys, gridgen.flat_state(sys))
         assert np.array_equal(rp, rpo) and np.array_equal(ci, cio)
+    # F of every instance (its outage applied) against the oracle
+    for k, ins in enumerate(insts):
+        f = Fh[ctx.f_off[k]:ctx.f_off[k + 1]]
+        assert_tol(f, oracle.residual(with_outage(grids[ins.grid], ins.outage), ins.x), f"instance {k} F")
     rng = np.random.default_rng(33)
     sample = sorted({0, 1, 1023, 2047, 2048, 2175, 2303, *rng.integers(0, 2304, 5).tolist()})
     for k in sample:
@@ -151,6 +155,10 @@ def test_mixed_batch_full_size_iteration(P):
     captured(iteration, s)
     assert torch.isfinite(F).all() and torch.isfinite(V).all() and torch.isfinite(G).all()
     Fh, Vh, Gh = F.cpu().numpy(), V.cpu().numpy(), G.cpu().numpy()
+    # F of every instance against the oracle (with its injection overrides)
+    for k, (ins, sys) in enumerate(zip(insts, grids)):
+        f = Fh[ctx.f_off[k]:ctx.f_off[k + 1]]
+        assert_tol(f, oracle.residual(sys, ins.x, p_inj=ins.p_inj, q_inj=ins.q_inj), f"instance {k} F")
     sizes = np.array([g.n_bus for g in grids])
     rng = np.random.default_rng(55)
     sample = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), 0, 4095, *rng.integers(0, 4096, 4).tolist()})

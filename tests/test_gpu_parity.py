@@ -195,6 +195,22 @@ def test_full_70k_against_oracle(P):
     ctx.check_device()
 
 
+def test_full_70k_extended_against_oracle(P):
+    """The 70,000-bus grid in the paper's extended formulation (Sec. II-A, Eqs. 1-3): the pattern
+    bit-exact, every F row and J value at the flat start and two perturbed states."""
+    sys = gridgen.grid_70k()
+    ctx = P.Context(sys, "extended")
+    rp, ci = ctx.pattern()
+    rpo, cio, _ = oracle.jacobian(sys, gridgen.flat_state(sys, True), EXTENDED)
+    assert np.array_equal(rp, rpo) and np.array_equal(ci, cio)
+    for k in (0, 1, 10):
+        xn = state(sys, k, extended=True)
+        F, v = ctx.residual_jacobian(torch.from_numpy(xn).cuda())
+        assert_tol(F.cpu().numpy(), oracle.residual(sys, xn, EXTENDED), f"70k extended F {k}")
+        assert_tol(v.cpu().numpy(), oracle.jacobian(sys, xn, EXTENDED)[2], f"70k extended J {k}")
+    ctx.check_device()
+
+
 def test_phasor_routine_against_libm(P):
     """The table-driven sin / cos of the phasor kernel vs the host libm (numpy): the fixed-point
     path (|t| < 32) on a grid, at and between table points, near the switch to sincos() at 32, on
