@@ -232,12 +232,12 @@ __device__ __forceinline__ int2 limbs(long long z) { return make_int2((int)(z >>
 
 // Fixed-point records for the F / J kernels, one thread per instance-bus:
 // {cos theta 2^60, sin theta 2^60} as 30-bit limbs, then {V 2^60} as limbs
-// and the bits of 1/V, in 32 bytes.  The trigonometric routine runs on the
+// and the bits of V, in 32 bytes.  The trigonometric routine runs on the
 // integer pipe and its fixed-point result is kept (rounded from 2^62 to 2^60,
 // no rounding to double); V 2^60 is exact for 2^-8 <= |V| < 2.  A voltage
 // outside (-2, 2), or an angle that is not finite, gets kBadLimb in place of
-// V's high limb: the buses that see it evaluate in FP64 from x.  1/V (with
-// the dead-bus substitution) serves the own bus's diagonal values.
+// V's high limb: the buses that see it evaluate in FP64 from x.  No FP64
+// arithmetic (the reciprocal of V is formed where it is used).
 __global__ void __launch_bounds__(256) k_phasor_fx(View v, const double *__restrict__ x) {
   cudaTriggerProgrammaticLaunchCompletion();
   const int64_t q = v.bus_inst_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -247,7 +247,6 @@ __global__ void __launch_bounds__(256) k_phasor_fx(View v, const double *__restr
     const double *xi = x + v.inst_x_off[inst];
     const double th = __ldg(xi + lb);
     const double vm = __ldg(xi + v.grid_nbus[v.inst_grid[inst]] + lb);
-    const double sv = dead_sub(vm);
     long long c60, s60;
     bool finite = true;
     if ((__double2hiint(th) & 0x7fffffff) < 0x40400000) {       // |t| < 32
@@ -263,12 +262,11 @@ __global__ void __launch_bounds__(256) k_phasor_fx(View v, const double *__restr
       finite = (__double2hiint(th) & 0x7ff00000) != 0x7ff00000;
     }
     int2 vl = limbs(fix60_of(vm));
-    if (!(finite && fabs(vm) < 2.0)) vl = make_int2(kBadLimb, 0);
+    if (!finite || (__double2hiint(vm) & 0x7fffffff) >= 0x40000000) vl = make_int2(kBadLimb, 0);   // |V| >= 2, NaN
     const int2 cl = limbs(c60), sl = limbs(s60);
-    const double rv = (__double2hiint(sv) & 0x7ff00000) >= 0x7d000000 ? __drcp_rn(sv) : recip(sv);
     int4 *rec = reinterpret_cast<int4 *>(v.phasor);
     rec[2 * q] = make_int4(cl.x, cl.y, sl.x, sl.y);
-    rec[2 * q + 1] = make_int4(vl.x, vl.y, __double2loint(rv), __double2hiint(rv));
+    rec[2 * q + 1] = make_int4(vl.x, vl.y, __double2loint(vm), __double2hiint(vm));
   }
 }
 
@@ -413,9 +411,9 @@ __device__ __forceinline__ void write_pair(double *vi, int4 p, double X, double 
 }
 
 // FP64 voltage of a bus for the FP64 path: E = V (cos, sin) (V after the
-// dead-bus substitution) from the record's unit phasor and x's V -- the
-// values of the adjoint's FP64 records -- and 1/V from the record.  An angle
-// that is not finite gives E = NaN, as the FP64 form would.
+// dead-bus substitution) from the record's unit phasor and x's V, and 1/V --
+// the values of the adjoint's FP64 records.  An angle that is not finite
+// gives E = NaN, as the FP64 form would.
 struct VoltD {
   double2 E;
   double v, rv;
@@ -424,7 +422,6 @@ struct VoltD {
 __device__ __forceinline__ VoltD volt_fp64(const int4 *__restrict__ rec4, const double *__restrict__ xi, int32_t nb,
                                            int64_t lb, int64_t rb) {
   const int4 u = rec4[2 * rb];
-  const int4 w = rec4[2 * rb + 1];
   const double th = xi[lb], vm = xi[nb + lb];
   const double sv = dead_sub(vm);
   VoltD r;
@@ -436,7 +433,7 @@ __device__ __forceinline__ VoltD volt_fp64(const int4 *__restrict__ rec4, const 
     r.E = make_double2(__dmul_rn(sv, fix_to_double(c, 60)), __dmul_rn(sv, fix_to_double(s, 60)));
   }
   r.v = vm;
-  r.rv = __hiloint2double(w.w, w.z);
+  r.rv = (__double2hiint(sv) & 0x7ff00000) >= 0x7d000000 ? __drcp_rn(sv) : recip(sv);
   return r;
 }
 
@@ -685,18 +682,18 @@ __device__ __forceinline__ Rec load_rec(const int4 *p) {
 }
 
 // The own bus's voltage for the fixed-point pair terms, from its record:
-// E_o = V_o U_o at 2^60 as limbs (and -f_o), V_o at 2^60 and 1/V_o; `fast`
-// when V_o lies in [1/4, 2) (kBadLimb is negative).
+// E_o = V_o U_o at 2^60 as limbs (and -f_o), V_o at 2^60 and as a double;
+// `fast` when V_o lies in [1/4, 2) (kBadLimb is negative).
 struct OwnV {
   int2 eo, fo, nfo;
   long long vof;
-  double rvo;
+  double vo;                                      // V_o
   bool fast;
 };
 
 __device__ __forceinline__ OwnV own_voltage(const Rec &ro) {
   OwnV w;
-  w.rvo = __hiloint2double(ro.w.w, ro.w.z);
+  w.vo = __hiloint2double(ro.w.w, ro.w.z);
   const int2 vl = make_int2(ro.w.x, ro.w.y);
   w.vof = ((long long)ro.w.x << 30) + ro.w.y;
   w.fast = ro.w.x >= (1 << 28);
@@ -785,8 +782,8 @@ __device__ __forceinline__ void finish_bus(const View &v, const EvalArgs &a, con
   if (fast) {
     sx = acc_value(ax, sT);
     sy = neg(acc_value(ay, sT));
-    vo = fix_to_double(w.vof, 60);
-    rvo = w.rvo;
+    vo = w.vo;
+    rvo = recip(vo);                             // V_o in [1/4, 2)
   } else {
     // FP64 form of the whole bus, pairs in list order
     const VoltD Vo = volt_fp64(uc.rec4, uc.xi, uc.nb, o - uc.gb0, o);
@@ -921,7 +918,7 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED, DYN>:
     Acc128 ax{0ULL, 0LL}, ay{0ULL, 0LL};       // exact S_X and -S_Y
     bool fast = true;                            // the fixed-point form holds for this bus
     bool any_out = false;                        // masked: an end of this bus is out of service
-    OwnV w{make_int2(0, 0), make_int2(0, 0), make_int2(0, 0), 0LL, 0.0, true};   // the own bus's voltage
+    OwnV w{make_int2(0, 0), make_int2(0, 0), make_int2(0, 0), 0LL, 1.0, true};   // the own bus's voltage
     const int32_t q0 = ur.z + bl;                 // slot indices are below 2^31 (checked at build)
 
     // (the first pass always runs: it waits for the records and loads the own bus's)

@@ -182,7 +182,7 @@ struct View {
 
   // scratch: one 32-byte record per instance bus.  The F / J kernels use the
   // fixed-point form {cos theta 2^60, sin theta 2^60, V 2^60 as 30-bit limbs
-  // (V h = kBadLimb when |V| >= 2 or theta is not finite), bits of 1/V}; the
+  // (V h = kBadLimb when |V| >= 2 or theta is not finite), bits of V}; the
   // adjoint kernels the FP64 form {V cos theta, V sin theta, V, 1/V}
   // (launch_phasor chooses).
   double2 *phasor;

@@ -8,7 +8,7 @@
 // Inputs, outputs and the built context come from the caller; the only
 // scratch the evaluation needs -- the 32-byte per-bus record of every bus of
 // every instance (the unit phasor (cos theta, sin theta) and V in fixed point,
-// and 1/V) -- lives in g_static_phasor below, a fixed device array that
+// and V) -- lives in g_static_phasor below, a fixed device array that
 // exists on every GPU that loads this library until the process exits.
 #include <mutex>
 #include <string>
