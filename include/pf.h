@@ -174,9 +174,10 @@ typedef struct pf_tuning {
   int32_t ctas_per_sm;           /* persistent CTAs per SM of the fused kernels and the adjoint
                                     state kernel (the fused kernel's warps then claim rounds
                                     from a counter); 0 = one CTA for every round */
-  int32_t split_rounds;          /* 1: a warp takes half a round, two lanes per bus (each every
-                                    other pair; twice the warps, for contexts that fill less than
-                                    a wave); 0: one lane per bus.  Results are bit-identical. */
+  int32_t split_rounds;          /* 0: one lane per bus; 1: a warp takes half a round, two lanes per
+                                    bus (each every other pair); 2: a quarter round, four lanes per
+                                    bus (every fourth pair) -- more warps with shorter chains, for
+                                    contexts that fill less than a wave.  Results are bit-identical. */
 } pf_tuning;
 
 /* ---- build (once) -------------------------------------------------------- */
@@ -371,7 +372,7 @@ PF_API int pf_get_tuning(const pf_ctx *ctx, pf_tuning *t);
  * `stream` first; allocates the schedule counters of ctas_per_sm > 0 on
  * first use).  Never changes results.  PF_ERR_INVALID for values outside
  * the documented range (tile_inc 32/64/96/128, ctas_per_sm 0..32,
- * split_rounds 0/1). */
+ * split_rounds 0/1/2). */
 PF_API int pf_set_tuning(pf_ctx *ctx, const pf_tuning *t, void *stream);
 /* Times the fused evaluation at x for each candidate tuning (a batch of
  * about 2 ms of back-to-back evaluations, 5 to 200, the faster of two

@@ -40,7 +40,7 @@ constexpr const char *kTuningTag = "pf-tuning-v1";
 
 bool tuning_valid(const pf_tuning &t) {
   return t.tile_inc >= pf::kMinTileInc && t.tile_inc <= pf::kMaxTileInc && t.tile_inc % 32 == 0 &&
-         t.ctas_per_sm >= 0 && t.ctas_per_sm <= 32 && (t.split_rounds == 0 || t.split_rounds == 1);
+         t.ctas_per_sm >= 0 && t.ctas_per_sm <= 32 && t.split_rounds >= 0 && t.split_rounds <= 2;
 }
 
 // 64-bit FNV-1a over the bytes of v.
@@ -385,7 +385,7 @@ int pf_set_tuning(pf_ctx *ctx, const pf_tuning *t, void *stream) {
   if (t->tile_inc < pf::kMinTileInc || t->tile_inc > pf::kMaxTileInc || t->tile_inc % 32 != 0)
     return fail(PF_ERR_INVALID, "tile_inc must be 32, 64, 96 or 128");
   if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return fail(PF_ERR_INVALID, "ctas_per_sm must be in [0, 32]");
-  if (t->split_rounds != 0 && t->split_rounds != 1) return fail(PF_ERR_INVALID, "split_rounds must be 0 or 1");
+  if (t->split_rounds < 0 || t->split_rounds > 2) return fail(PF_ERR_INVALID, "split_rounds must be 0, 1 or 2");
   cudaStream_t s = as_stream(stream);
   PF_CUDA_TRY(cudaStreamSynchronize(s));
   pf::Ctx &c = ctx->c;
@@ -426,7 +426,7 @@ int pf_autotune(pf_ctx *ctx, const double *x, double *F, double *vals, void *str
     return PF_OK;
   };
   int rc = PF_OK;
-  for (int k = 0; k < 2 * 4 * 3 && !rc; ++k) {       // split rounds x tiles x CTAs per SM
+  for (int k = 0; k < 3 * 4 * 3 && !rc; ++k) {       // split rounds x tiles x CTAs per SM
     const pf_tuning t{tiles[(k / 3) % 4], ctas[k % 3], k / 12};
     rc = pf_set_tuning(ctx, &t, stream);
     if (rc) break;

@@ -38,8 +38,9 @@
 // entries.  Because the buses of a round have the same number of pairs,
 // nearly every lane does useful work at every step.  A bus with more
 // than 32 neighbours is evaluated by a whole warp in a second kernel.  With
-// split rounds (a tuning choice) a warp takes half a round, two lanes per bus
-// taking alternate pairs, their exact partial sums merged by a shuffle.  The
+// split rounds (a tuning choice) a warp takes half (a quarter of) a round, two
+// (four) lanes per bus taking alternate pairs, their exact partial sums merged
+// by shuffles.  The
 // launch has one one-warp CTA per round, or (ctas_per_sm > 0) a persistent
 // grid whose warps claim rounds from a counter.
 //
@@ -378,7 +379,7 @@ struct EvalArgs {
   const uint8_t *status;   // per-instance-branch mask or nullptr
   const uint8_t *gen_mode; // extended, per instance-generator: != 0 holds Q_g at gen_qlim, or nullptr
   const double *gen_qlim;
-  int split;               // 1: half a round per warp, two lanes per bus
+  int split;               // log2 of the lanes per bus: 0, 1 (half a round per warp) or 2 (a quarter)
   // a persistent (capped) k_fused grid: {next unit, CTAs done} counters of
   // its dynamic schedule, zero at launch and reset by the grid's last CTA;
   // nullptr: CTA b takes units b, b + grid, ...
@@ -863,13 +864,15 @@ template <int ITEMS, bool WF, bool WJ, bool MASKED, bool DYN>
 __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED, DYN>::value)) k_fused(View v, EvalArgs a) {
   extern __shared__ double s_stage[];           // kStageBytes when WJ
   const int lane = threadIdx.x & 31;
-  // split rounds: a warp takes half a round (16 buses), two lanes per bus,
-  // lane l the pairs l >> 4, (l >> 4) + 2, ... of bus l & 15
+  // split rounds: a warp takes a half (quarter) round of 16 (8) buses, 2 (4)
+  // lanes per bus, lane l the pairs p, p + 2 (4), ... of bus l & 15 (7),
+  // p = l >> 4 (3)
   const int split = a.split;
   const int64_t n_units = v.n_lane_units << split;
-  const int bl0 = split ? (lane & 15) : lane;    // bus lane within the (half) round
-  const int par = split ? (lane >> 4) : 0;       // this lane's first pair
-  const int step = 1 + split;                    // and its stride
+  const int nbw = 32 >> split;                   // buses per warp
+  const int bl0 = lane & (nbw - 1);              // bus lane within the warp's part of the round
+  const int par = lane >> (5 - split);           // this lane's first pair
+  const int step = 1 << split;                   // and its stride
   const int sT = 59 - v.coef_log2;               // scale of T, X, Y and the sums
   // Dynamic schedule of a persistent grid: lane 0 claims the warp's next unit
   // from a counter as it starts a unit, so the claim's latency hides behind
@@ -904,7 +907,7 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED, DYN>:
     const bool staged = WJ && D <= kStageMaxD;
 
     // this lane's bus: its records in round order
-    const int bl = bl0 + (split ? 16 * (int)(u & 1) : 0);
+    const int bl = bl0 + nbw * (int)(u & ((1 << split) - 1));
     const int32_t rb = 32 * ur.y + bl;            // below 2^31: the build checks the round count
     const bool owner = bl < (ur.w >> 8);
     const bool lead = owner && par == 0;         // the lane that finishes the bus
@@ -954,13 +957,16 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED, DYN>:
       }
     }
     if (split) {
-      // the second lane of each bus hands its partial sums to the first: the
-      // sums are exact, so the result is the unsplit one, bit for bit
-      acc_merge(ax, __shfl_down_sync(0xffffffffu, ax.lo, 16), __shfl_down_sync(0xffffffffu, ax.hi, 16));
-      acc_merge(ay, __shfl_down_sync(0xffffffffu, ay.lo, 16), __shfl_down_sync(0xffffffffu, ay.hi, 16));
-      fast = __shfl_down_sync(0xffffffffu, (int)fast, 16) != 0 && fast;
-      any_out = __shfl_down_sync(0xffffffffu, (int)any_out, 16) != 0 || any_out;
-      __syncwarp();                              // the FP64 path below rewrites the other lane's values
+      // the other lanes of each bus hand their partial sums to the first (a
+      // halving tree): the sums are exact, so the result is the unsplit one,
+      // bit for bit
+      for (int off = 16; off >= nbw; off >>= 1) {
+        acc_merge(ax, __shfl_down_sync(0xffffffffu, ax.lo, off), __shfl_down_sync(0xffffffffu, ax.hi, off));
+        acc_merge(ay, __shfl_down_sync(0xffffffffu, ay.lo, off), __shfl_down_sync(0xffffffffu, ay.hi, off));
+        fast = __shfl_down_sync(0xffffffffu, (int)fast, off) != 0 && fast;
+        any_out = __shfl_down_sync(0xffffffffu, (int)any_out, off) != 0 || any_out;
+      }
+      __syncwarp();                              // the FP64 path below rewrites the other lanes' values
     }
     if (lead) {
       const UnitCtx uc{inst, g, ui.z, ui.y, xi, Fi, vi, rec4, outage, st_base};
@@ -1195,7 +1201,7 @@ int launch_eval_stages(Ctx &c, int stages, const double *x, const pf_overrides *
   a.x = x;
   a.F = F;
   a.vals = vals;
-  a.split = c.tuning.split_rounds ? 1 : 0;
+  a.split = c.tuning.split_rounds;
   a.work = c.work_ctr;
   built_coefficients(c.v, a);
   bool params = false;                           // per-call branch parameters
@@ -1240,7 +1246,7 @@ int launch_eval_range(Ctx &c, int i0, int i1, const double *x, double *F, double
   a.x = x;
   a.F = F;
   a.vals = vals;
-  a.split = c.tuning.split_rounds ? 1 : 0;
+  a.split = c.tuning.split_rounds;
   a.work = c.work_ctr;
   built_coefficients(c.v, a);
   PF_TRY(launch_phasor(v, c.num_sms, x, s, true));
@@ -1259,7 +1265,7 @@ int launch_eval_scratch(Ctx &c, const double *x, double *F, double *vals, double
   a.x = x;
   a.F = F;
   a.vals = vals;
-  a.split = c.tuning.split_rounds ? 1 : 0;
+  a.split = c.tuning.split_rounds;
   a.work = c.work_ctr;
   built_coefficients(c.v, a);
   PF_TRY(launch_phasor(v, c.num_sms, x, s, true));

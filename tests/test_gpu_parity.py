@@ -120,7 +120,7 @@ def test_deterministic_across_runs_and_tunings(P, name):
         F1, v1 = ctx.residual_jacobian(x)
         assert torch.equal(F0, F1) and torch.equal(v0, v1)
     nan = float("nan")
-    for split in (0, 1):
+    for split in (0, 1, 2):
         for tile in (32, 64, 96, 128):
             for ctas in (0, 1, 3, 16):
                 ctx.set_tuning(tile, ctas, split)
@@ -307,7 +307,7 @@ def test_split_rounds_bit_identical_under_masks(P, mode):
         kw["gen_mode"] = torch.from_numpy(rng.integers(0, 3, ctx.dims.n_gen_inst).astype(np.uint8)).cuda()
         kw["gen_qlim"] = torch.from_numpy(rng.uniform(-0.5, 0.8, ctx.dims.n_gen_inst)).cuda()
     outs = []
-    for split in (0, 1):
+    for split in (0, 1, 2):
         for tile in (32, 128):
             ctx.set_tuning(tile, 0, split)
             outs.append(ctx.eval(x, ctx.empty_f(), ctx.empty_vals(), **kw))
