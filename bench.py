@@ -231,10 +231,10 @@ def fp64_ops(d, pattern):
     """FP64-pipe operations of one instance's F and J evaluation (an FMA, a
     multiply, an add or a conversion each count one).  k_fused forms the pair
     terms in fixed point on the integer pipe; the FP64 pipe converts each
-    V-column off-diagonal value to double (one conversion), and each bus's rows
-    take V_o^2, V_o^2 A^ - S_X, V_o^2 C^ + S_Y and the two F rows (5) plus two
-    FMAs and two multiplies for the diagonal V values where the bus has a V
-    column (4).  k_phasor_fx takes 3 per bus (the reciprocal of V).  Returns
+    V-column off-diagonal value to double (one conversion), and each bus takes
+    1/V_o (3), V_o^2, V_o^2 A^ - S_X, V_o^2 C^ + S_Y and the two F rows (5),
+    plus two FMAs and two multiplies for the diagonal V values where the bus
+    has a V column (4).  k_phasor_fx has no FP64 arithmetic.  Returns
     (k_fused, k_phasor_fx)."""
     n = d.n_bus
     rp, ci = pattern
@@ -246,7 +246,7 @@ def fp64_ops(d, pattern):
         n_v = int(np.count_nonzero((row < 2 * n) & (ci >= n) & (ci < 2 * n)))
         n_vbus = n
     n_voff = n_v - 2 * n_vbus
-    return n_voff + 5 * n + 4 * n_vbus, 3 * n
+    return n_voff + 8 * n + 4 * n_vbus, 0
 
 
 def _oracle_share(kind, idx, seconds, barrier, queue):
