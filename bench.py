@@ -667,7 +667,9 @@ def _clocked(torch, stream, g, K):
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     time.sleep(0.3)
+    torch.cuda.nvtx.range_push("bench_timed")
     t = _time_graph(torch, stream, g, K)
+    torch.cuda.nvtx.range_pop()
     return t, sampler.stop()
 
 
@@ -941,14 +943,17 @@ def measure_newton(args):
 
 def load_traffic():
     """DRAM bytes per k_fused launch from the committed ncu summary, used only
-    while the kernel source is the one that was profiled."""
+    while the kernel source is the one that was profiled and for the number of
+    states it was profiled with."""
     path = os.path.join(ROOT, "profiles", "k_fused_traffic_70k.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)
     except Exception:
         return None
-    return rec if rec.get("source_sha256_16") == source_hash() else None
+    if rec.get("source_sha256_16") != source_hash() or rec.get("states") != N_STATES:
+        return None
+    return rec
 
 
 if __name__ == "__main__":
