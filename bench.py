@@ -2,7 +2,7 @@
 
 One step = one batched launch that evaluates the bus mismatches F and the
 Jacobian values J (tasks 1 and 2 of Newton power flow) at 48 Newton-like
-states of the grid (48 instances of one context; k_phasor + k_fused,
+states of the grid (48 instances of one context; k_phasor_fx + k_tile,
 replayed as a captured CUDA graph) through the library's C ABI.  Inputs are
 resident in HBM; the 48 states' x, F and J (444 MB) exceed the 129 MB L2.
 value = evaluations / s.  The same states evaluated one launch at a time are
@@ -191,10 +191,10 @@ def l2_note(step_bytes):
 def hbm_roofline(bytes_alg, kernel_ms, step_s, peaks, peak_kind, traffic):
     """The roofline of the dominant kernel against the measured HBM copy rate:
     achieved = the step's algorithmic bytes (read the state, the branch and
-    model parameters, write F and J) over k_fused's own CUDA-event time, and
-    the same bytes over the whole step (k_phasor_fx + k_fused) beside it."""
+    model parameters, write F and J) over k_tile's own CUDA-event time, and
+    the same bytes over the whole step (k_phasor_fx + k_tile) beside it."""
     ach = bytes_alg / (kernel_ms * 1e-3) / 1e9
-    return {"bound": "hbm", "kernel": "k_fused", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+    return {"bound": "hbm", "kernel": "k_tile", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": ach / peaks["hbm_gbs"], "peak_kind": f"{peak_kind} copy peak (MEASURED_PEAKS.json hbm_gbs)",
             "traffic": traffic.get("dram_bytes_per_launch") if traffic else None,
             "algorithmic_bytes": bytes_alg, "kernel_ms": kernel_ms,
@@ -209,33 +209,34 @@ def compact_line(r):
                                              "kernel_ms")},
            "clocks": r["clocks"], "tuning": r.get("config", {}).get("tuning")}
     if "fp64" in roof:
-        out["roofline"]["fp64_k_fused_frac"] = roof["fp64"]["k_fused_frac"]
+        out["roofline"]["fp64_k_tile_frac"] = roof["fp64"]["k_tile_frac"]
     if "breakdown" in r:
         out["breakdown"] = r["breakdown"]
     return out
 
 
-def fp64_view(ops_fused, ops_phasor, kernel_ms, step_s, dev):
+def fp64_view(ops_tile, ops_phasor, kernel_ms, step_s, dev):
     """FP64-pipe operations of a launch against the FP64 FMA rate measured in
     this run by the library's pf_fp64_peak (the pair terms run on the integer
     pipe, so this is a secondary view)."""
     from paper_2011_11880_gb300 import fp64_peak
     peak, _ = fp64_peak(dev.index if dev.index is not None else 0)
-    return {"executed_ops_k_fused": ops_fused, "executed_ops_step": ops_fused + ops_phasor,
+    return {"executed_ops_k_tile": ops_tile, "executed_ops_step": ops_tile + ops_phasor,
             "peak_gops": peak, "peak_kind": "measured in this run by pf_fp64_peak (FP64 FMA chains)",
-            "k_fused_frac": ops_fused / (kernel_ms * 1e-3) / 1e9 / peak,
-            "step_frac": (ops_fused + ops_phasor) / step_s / 1e9 / peak}
+            "k_tile_frac": ops_tile / (kernel_ms * 1e-3) / 1e9 / peak,
+            "step_frac": (ops_tile + ops_phasor) / step_s / 1e9 / peak}
 
 
 def fp64_ops(d, pattern):
     """FP64-pipe operations of one instance's F and J evaluation (an FMA, a
-    multiply, an add or a conversion each count one).  k_fused forms the pair
+    multiply, an add or a conversion each count one).  k_tile forms the pair
     terms in fixed point on the integer pipe; the FP64 pipe converts each
     V-column off-diagonal value to double (one conversion), and each bus takes
-    1/V_o (3), V_o^2, V_o^2 A^ - S_X, V_o^2 C^ + S_Y and the two F rows (5),
-    plus two FMAs and two multiplies for the diagonal V values where the bus
-    has a V column (4).  k_phasor_fx has no FP64 arithmetic.  Returns
-    (k_fused, k_phasor_fx)."""
+    V_o from its fixed-point form and the two exact bus sums to double (3),
+    V_o^2, V_o^2 A^ - S_X, V_o^2 C^ + S_Y and the two F rows (5), plus two
+    FMAs and two multiplies for the diagonal V values where the bus has a V
+    column (4).  k_phasor_fx forms 1/V_o (3 FMAs after the hardware's
+    reciprocal estimate) for every bus.  Returns (k_tile, k_phasor_fx)."""
     n = d.n_bus
     rp, ci = pattern
     if d.formulation == 0:                   # reduced: theta columns of the n - 1 non-slack buses first
@@ -246,7 +247,7 @@ def fp64_ops(d, pattern):
         n_v = int(np.count_nonzero((row < 2 * n) & (ci >= n) & (ci < 2 * n)))
         n_vbus = n
     n_voff = n_v - 2 * n_vbus
-    return n_voff + 8 * n + 4 * n_vbus, 0
+    return n_voff + 8 * n + 4 * n_vbus, 3 * n
 
 
 def _oracle_share(kind, idx, seconds, barrier, queue):
@@ -350,14 +351,14 @@ def host_cpu():
 
 
 def launches_per_eval(ctx):
-    """Kernels one evaluation of the context launches: k_phasor and k_fused, and
-    k_fused_large where a bus has more than 32 neighbours."""
+    """Kernels one evaluation of the context launches: k_phasor_fx and k_tile,
+    and k_fused_large where a bus has more than 32 neighbours."""
     return 2 + (1 if ctx.dims.max_degree > 32 else 0)
 
 
 def source_hash():
     """Hash of the code (comments and blank space removed) of the sources that
-    decide k_fused's memory traffic: the kernel and the data layout."""
+    decide k_tile's memory traffic: the kernel and the data layout."""
     import hashlib
     import re
     h = hashlib.sha256()
@@ -506,7 +507,7 @@ def main():
     value = job_throughput(world, K * N_STATES, t_max)
     ms_per_step = 1000.0 * t_max / K
 
-    # ---- the dominant kernel alone: the batched k_fused launch between events ----
+    # ---- the dominant kernel alone: the batched k_tile launch between events ----
     KF = min(K, 200)
     with torch.cuda.stream(stream):
         g_ph.replay()
@@ -586,7 +587,7 @@ def main():
                    "l2": l2_note(N_STATES * 8 * (d1.n_x + d1.n_f + d1.nnz)),
                    "tuning": tuning, "timed_region_wall_s": wall, "parallelism": f"replicas x{world}"},
         "single_instance": {"value": single_rate, "unit": "evals/s", "tuning": one_tuning,
-                            "how": f"one evaluation per launch pair (k_phasor, k_fused), {N_STATES} states with their "
+                            "how": f"one evaluation per launch pair (k_phasor_fx, k_tile), {N_STATES} states with their "
                                    "own buffers evaluated one after the other from one CUDA graph"},
         "batched_over_single": value / world / single_rate,
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": 8 * d.n_x,
@@ -707,7 +708,7 @@ def measure_contingency(torch, stream, K, W, cpu_seconds=0.0):
                       "n_f": ctx.dims.n_f, "nnz": ctx.dims.nnz, "tuning": tuning,
                       "l2": "inputs larger than L2 (x, F, J of 2,304 instances: 1 GB)"},
            "roofline": hbm_roofline(bytes_alg, 1e3 * kf, t, peaks, peak_kind, None),
-           "breakdown": {"k_fused_ms": 1e3 * kf}, "clocks": clocks,
+           "breakdown": {"k_tile_ms": 1e3 * kf}, "clocks": clocks,
            "gpu_launches": launches_per_eval(ctx) * K}
     ctx.close()
     if cpu_seconds > 0:
@@ -942,10 +943,10 @@ def measure_newton(args):
 
 
 def load_traffic():
-    """DRAM bytes per k_fused launch from the committed ncu summary, used only
+    """DRAM bytes per k_tile launch from the committed ncu summary, used only
     while the kernel source is the one that was profiled and for the number of
     states it was profiled with."""
-    path = os.path.join(ROOT, "profiles", "k_fused_traffic_70k.json")
+    path = os.path.join(ROOT, "profiles", "k_tile_traffic_70k.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)

@@ -134,7 +134,7 @@ class PowerSystem:
 # --------------------------------------------------------------------------
 
 def _ring_of_meshes(n_bus: int, n_branch: int, rng: np.random.Generator, cluster: int,
-                    parallel_frac: float):
+                    parallel_frac: float, backbone: str = "ring"):
     n_cl = max(1, int(round(n_bus / cluster)))
     bounds = np.linspace(0, n_bus, n_cl + 1).round().astype(np.int64)
     start, size = bounds[:-1], np.diff(bounds)
@@ -155,11 +155,24 @@ def _ring_of_meshes(n_bus: int, n_branch: int, rng: np.random.Generator, cluster
     f = np.concatenate(ring_f) if ring_f else np.zeros(0, np.int64)
     t = np.concatenate(ring_t) if ring_t else np.zeros(0, np.int64)
 
-    # ties between neighbouring clusters, arranged in a ring of clusters
+    # ties between neighbouring clusters: the clusters arranged in a ring, or
+    # ("mesh") row by row on a rectangle, each tied to its right and lower
+    # neighbour
     if n_cl > 1:
-        n_links = n_cl if n_cl > 2 else 1
-        k = np.arange(n_links)
-        nxt = (k + 1) % n_cl
+        if backbone == "ring":
+            n_links = n_cl if n_cl > 2 else 1
+            k = np.arange(n_links)
+            nxt = (k + 1) % n_cl
+        elif backbone == "mesh":
+            cols = int(np.ceil(np.sqrt(n_cl)))
+            c = np.arange(n_cl)
+            right = c[(c % cols != cols - 1) & (c + 1 < n_cl)]
+            down = c[c + cols < n_cl]
+            k = np.concatenate([right, down])
+            nxt = np.concatenate([right + 1, down + cols])
+            n_links = k.shape[0]
+        else:
+            raise ValueError("backbone must be 'ring' or 'mesh'")
         n_tie = rng.integers(2, 4, size=n_links)
         ka, kb = np.repeat(k, n_tie), np.repeat(nxt, n_tie)
         ta = start[ka] + rng.integers(0, size[ka])
@@ -195,7 +208,9 @@ def synthetic_grid(n_bus: int, seed: int, *, n_branch: int | None = None,
                    shift_frac: float = 0.01, end_g_frac: float = 0.0,
                    parallel_frac: float = 0.01, cluster: int = 50,
                    n_pv: int | None = None, n_load: int | None = None,
-                   n_shunt: int | None = None, load_scale: float = 1.0) -> PowerSystem:
+                   n_shunt: int | None = None, load_scale: float = 1.0,
+                   backbone: str = "ring", pv_total: float | None = None,
+                   z_scale: float = 1.0) -> PowerSystem:
     """Ring-of-meshes grid with the parameter distributions of the paper-shaped workloads.
 
     r ~ U[0.002, 0.02], x = r * U[5, 12], b ~ U[0, 0.05]; a fraction
@@ -211,10 +226,10 @@ def synthetic_grid(n_bus: int, seed: int, *, n_branch: int | None = None,
     rng = np.random.default_rng(seed)
     if n_branch is None:
         n_branch = int(round(1.257 * n_bus))
-    f, t = _ring_of_meshes(n_bus, n_branch, rng, cluster, parallel_frac)
+    f, t = _ring_of_meshes(n_bus, n_branch, rng, cluster, parallel_frac, backbone)
     m = f.shape[0]
 
-    r = rng.uniform(0.002, 0.02, m)
+    r = rng.uniform(0.002, 0.02, m) * z_scale
     x = r * rng.uniform(5.0, 12.0, m)
     b = rng.uniform(0.0, 0.05, m)
     tap = np.ones(m)
@@ -246,6 +261,9 @@ def synthetic_grid(n_bus: int, seed: int, *, n_branch: int | None = None,
     pf = rng.uniform(0.9, 0.98, load_bus.shape[0])
     load_q = load_p * np.tan(np.arccos(pf))
     pv_p = 1.03 * load_p.sum() / (n_pv + 1) * rng.uniform(0.5, 1.5, n_pv)
+    if pv_total is not None and n_pv > 0:
+        # PV outputs rescaled so that they add up to pv_total times the load
+        pv_p = pv_p * (pv_total * load_p.sum() / pv_p.sum())
     pv_vset = rng.uniform(0.98, 1.05, n_pv)
     n_shunt = int(round(shunt_frac * n_bus)) if n_shunt is None else n_shunt
     sh_bus = np.sort(rng.choice(n_bus, size=min(n_shunt, n_bus), replace=False)).astype(np.int32)

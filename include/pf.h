@@ -169,15 +169,18 @@ typedef struct pf_grads {
 } pf_grads;
 
 typedef struct pf_tuning {
-  int32_t tile_inc;              /* 32, 64, 96 or 128: each lane fetches tile_inc / 32 pairs of
-                                    connected buses ahead (the chunk of a bus with > 32 neighbours) */
+  int32_t tile_inc;              /* 32, 64, 96 or 128: each lane of the fused kernel has tile_inc / 32
+                                    pairs of connected buses (and their voltage records) in flight
+                                    at once (the chunk of a bus with > 32 neighbours) */
   int32_t ctas_per_sm;           /* persistent CTAs per SM of the fused kernels and the adjoint
-                                    state kernel (the fused kernel's warps then claim rounds
-                                    from a counter); 0 = one CTA for every round */
-  int32_t split_rounds;          /* 0: one lane per bus; 1: a warp takes half a round, two lanes per
-                                    bus (each every other pair); 2: a quarter round, four lanes per
-                                    bus (every fourth pair) -- more warps with shorter chains, for
-                                    contexts that fill less than a wave.  Results are bit-identical. */
+                                    state kernel (the fused kernel's warps then claim their work
+                                    from a counter); 0 = one CTA for every unit of work */
+  int32_t split_rounds;          /* size of the fused kernel's tiles (one warp per tile and
+                                    instance): 0 = up to 32 consecutive buses and 96 pairs of
+                                    connected buses, 1 = 16 and 48, 2 = 8 and 24 -- more warps with
+                                    shorter work, for contexts that fill less than a wave (the
+                                    smaller tilings are built on first use).  Results are
+                                    bit-identical. */
 } pf_tuning;
 
 /* ---- build (once) -------------------------------------------------------- */

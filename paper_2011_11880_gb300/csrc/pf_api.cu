@@ -397,6 +397,7 @@ int pf_set_tuning(pf_ctx *ctx, const pf_tuning *t, void *stream) {
     PF_CUDA_TRY(cudaMemset(p, 0, bytes));
     c.work_ctr = static_cast<unsigned long long *>(p);
   }
+  PF_TRY(pf::use_tile_set(c, t->split_rounds, s));
   c.tuning.tile_inc = t->tile_inc;
   c.tuning.ctas_per_sm = t->ctas_per_sm;
   c.tuning.split_rounds = t->split_rounds;

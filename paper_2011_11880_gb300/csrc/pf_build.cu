@@ -761,11 +761,11 @@ __global__ void k_slot_coeff(View v, int64_t n_slots, const int4 *smeta, const d
     }
     sgb[q] = g;
     sac[q] = a;
-    sgbm[q] = gm;
+    if (sgbm) sgbm[q] = gm;
   } else {
     sgb[q] = make_double2(0.0, 0.0);
     sac[q] = make_double2(0.0, 0.0);
-    sgbm[q] = make_double2(0.0, 0.0);
+    if (sgbm) sgbm[q] = make_double2(0.0, 0.0);
   }
 }
 
@@ -1014,6 +1014,266 @@ int build_rounds(Ctx &c, cudaStream_t s) {
   return PF_OK;
 }
 
+// ---- tiles of the fused kernel: consecutive buses, pairs listed bus by bus ---------------
+
+// per bus: its pairs in the tile kernel's list (none for a large bus)
+__global__ void k_pair_count(View v, int32_t *cnt) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= v.n_bus) return;
+  const int32_t d = v.bus_npair[b];
+  cnt[b] = d > kLaneMaxDegree ? 0 : d;
+}
+
+__global__ void k_pair_ptr(const int64_t *S, int64_t n_bus, int32_t *ptr, int32_t *err) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b > n_bus) return;
+  if (S[b] > 0x7fffffffLL) atomicOr(err, kErrMap);
+  ptr[b] = (int32_t)S[b];
+}
+
+// The tiles of grid g, formed greedily along the bus order: a tile takes the
+// next bus while it holds fewer than kTileBuses buses and the bus's pairs keep
+// it within kTilePairs; a large bus ends the tile and belongs to none.
+// (split_rounds = s: at most cap_bus = kTileBuses >> s buses and cap_pairs =
+// kTilePairs >> s pairs, a bus with more pairs alone in its tile.)
+// Pass 0 counts them (cnt[g]); pass 1 writes, per tile t (global index from
+// off[g]), {first bus, buses, first pair, pairs}, the J segments of its P and Q
+// rows {P start, P length, Q start, Q length}, its F rows {first P row, P
+// rows, first Q row, Q rows}, and each bus's index in its tile.  The rows of a
+// tile's buses must be consecutive (they are in both formulations); a tile
+// where they are not sets kErrMap.
+__global__ void k_tiles(View v, int pass, int cap_bus, int cap_pairs, int64_t *cnt, const int64_t *off, int4 *desc,
+                        int4 *seg, int4 *frow, int32_t *bus_local, int32_t *max_stage, int32_t *err) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= v.n_grids) return;
+  const int64_t gb0 = v.grid_bus_off[g], nb = v.grid_nbus[g];
+  const bool ext = v.formulation == PF_EXTENDED;
+  const int32_t slack = v.grid_slack[g];
+  int64_t t = pass ? off[g] : 0;
+  int64_t b = 0;
+  while (b < nb) {
+    if (v.bus_npair[gb0 + b] > kLaneMaxDegree) {       // large: in no tile
+      ++b;
+      continue;
+    }
+    const int64_t b0 = b;
+    int32_t pairs = 0;
+    while (b < nb && b - b0 < cap_bus) {
+      const int32_t d = v.bus_npair[gb0 + b];
+      if (d > kLaneMaxDegree || (b > b0 && pairs + d > cap_pairs)) break;
+      pairs += d;
+      ++b;
+    }
+    if (pass) {
+      int32_t rp0 = -1, rp1 = -1, rq0 = -1, rq1 = -1, np_ = 0, nq_ = 0;
+      int32_t sp0 = 0, sp1 = 0, sq0 = 0, sq1 = 0;
+      for (int64_t i = b0; i < b; ++i) {
+        const int64_t o = gb0 + i;
+        bus_local[o] = (int32_t)(i - b0);
+        const int4 bm = v.bus_meta[o], bm2 = v.bus_meta2[o];
+        const int32_t lp = bm2.z + (ext && i == slack ? 1 : 0);
+        const int32_t lq = bm2.z + (ext && bm2.w >= 0 ? 1 : 0);
+        if (bm.x >= 0) {
+          if (rp0 < 0) { rp0 = bm.x; sp0 = bm.z; }
+          rp1 = bm.x;
+          sp1 = bm.z + lp;
+          ++np_;
+        }
+        if (bm.y >= 0) {
+          if (rq0 < 0) { rq0 = bm.y; sq0 = bm.w; }
+          rq1 = bm.y;
+          sq1 = bm.w + lq;
+          ++nq_;
+        }
+      }
+      if ((np_ && rp1 - rp0 + 1 != np_) || (nq_ && rq1 - rq0 + 1 != nq_)) atomicOr(err, kErrMap);
+      desc[t] = make_int4((int32_t)(gb0 + b0), (int32_t)(b - b0), v.pair_ptr[gb0 + b0], pairs);
+      seg[t] = make_int4(sp0, sp1 - sp0, sq0, sq1 - sq0);
+      frow[t] = make_int4(rp0, np_, rq0, nq_);
+      atomicMax(max_stage, (sp1 - sp0) + (sq1 - sq0) + 3);
+    }
+    ++t;
+  }
+  if (!pass) cnt[g] = t;
+}
+
+// per bus of a tile: its pairs (groups of parallel branches in incidence
+// order) in the formats of the slot arrays (pmeta: nullptr to leave it)
+__global__ void k_pair_fill(View v, const int32_t *bus_local, int4 *pmeta, int4 *pidx) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= v.n_bus) return;
+  if (v.bus_npair[b] > kLaneMaxDegree) return;
+  int64_t q = v.pair_ptr[b];
+  const int32_t bp = v.base_p[b], bq = v.base_q[b];
+  for (int32_t e = v.inc_ptr[b]; e < v.inc_ptr[b + 1]; ++e) {
+    const int32_t len = v.inc_grp[e];
+    if (len == 0) continue;
+    if (pmeta) pmeta[q] = make_int4(v.inc_other[e], len, v.inc_code[e], e);
+    const int4 p = v.inc_pos[e];
+    const int32_t ot = p.x >= 0 ? p.x - bp : (p.z >= 0 ? p.z - bq : -1);
+    const int32_t ov = p.y >= 0 ? p.y - bp : (p.w >= 0 ? p.w - bq : -1);
+    pidx[q] = make_int4(v.inc_other[e], (ot & 0xffff) | (ov << 16), len | (bus_local[b] << 16),
+                        len == 1 ? v.inc_code[e] : e);
+    ++q;
+  }
+}
+
+// per tile of every instance: its six-int4 unit record
+__global__ void k_tunit_fill(View v, const int64_t *tile_off, const int64_t *grid_tile_off, const int4 *desc,
+                             const int4 *seg, const int4 *frow, int4 *unit) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= v.n_tile_units) return;
+  const int inst = find_segment(tile_off, v.n_inst, u);
+  const int g = v.inst_grid[inst];
+  const int64_t t = grid_tile_off[g] + (u - tile_off[inst]);
+  int4 *r = unit + 6 * u;
+  r[0] = desc[t];
+  r[1] = seg[t];
+  r[2] = frow[t];
+  r[3] = make_int4(inst, g, (int32_t)v.grid_bus_off[g], v.grid_nbus[g]);
+  const int64_t xo = v.inst_x_off[inst], fo = v.inst_f_off[inst], vo = v.inst_v_off[inst],
+                rb = v.inst_bus_off[inst] - v.grid_bus_off[g];
+  r[4] = make_int4((int32_t)(xo & 0xffffffff), (int32_t)(xo >> 32), (int32_t)(fo & 0xffffffff), (int32_t)(fo >> 32));
+  r[5] = make_int4((int32_t)(vo & 0xffffffff), (int32_t)(vo >> 32), (int32_t)(rb & 0xffffffff), (int32_t)(rb >> 32));
+}
+
+// The tiles of split_rounds = split: the partition, each pair's bus index in
+// its tile (the pair index records of this partition) and the unit records.
+int build_tile_set(Ctx &c, int split, cudaStream_t s) {
+  View &v = c.v;
+  Ctx::TileSet &ts = c.tiles[split];
+  const int G = v.n_grids;
+  const int64_t N = v.n_bus, NP = c.n_pairs;
+  const int cap_bus = kTileBuses >> split, cap_pairs = kTilePairs >> split;
+  TempList tmp;
+  int rc = PF_OK;
+  int32_t *err, *bus_local, *max_stage;
+  int64_t *gcnt;
+  PF_TRY(tmp.alloc(&err, 1));
+  PF_TRY(tmp.alloc(&max_stage, 1));
+  PF_TRY(tmp.alloc(&gcnt, G));
+  PF_TRY(tmp.alloc(&bus_local, N));
+  PF_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
+  PF_CUDA_TRY(cudaMemsetAsync(max_stage, 0, sizeof(int32_t), s));
+  k_tiles<<<nblk(G, 64), 64, 0, s>>>(v, 0, cap_bus, cap_pairs, gcnt, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                      nullptr, err);
+  PF_CUDA_TRY(cudaGetLastError());
+  std::vector<int64_t> h_cnt = to_host(gcnt, G, s, &rc);
+  if (rc) return rc;
+  std::vector<int64_t> grid_tile_off(G + 1, 0);
+  for (int g = 0; g < G; ++g) grid_tile_off[g + 1] = grid_tile_off[g] + h_cnt[g];
+  const int64_t T = grid_tile_off[G];
+  int64_t *d_gto;
+  int4 *desc, *seg, *frow, *pidx;
+  PF_TRY(tmp.alloc(&d_gto, G + 1));
+  PF_CUDA_TRY(cudaMemcpyAsync(d_gto, grid_tile_off.data(), (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  PF_TRY(tmp.alloc(&desc, T));
+  PF_TRY(tmp.alloc(&seg, T));
+  PF_TRY(tmp.alloc(&frow, T));
+  k_tiles<<<nblk(G, 64), 64, 0, s>>>(v, 1, cap_bus, cap_pairs, nullptr, d_gto, desc, seg, frow, bus_local,
+                                      max_stage, err);
+  PF_CUDA_TRY(cudaGetLastError());
+  PF_TRY(dev_alloc(c, &pidx, NP));
+  k_pair_fill<<<nblk(N), TB, 0, s>>>(v, bus_local, nullptr, pidx);
+  PF_CUDA_TRY(cudaGetLastError());
+  // units: the tiles of every instance, instance by instance
+  const int I = v.n_inst;
+  ts.tile_off.assign(I + 1, 0);
+  for (int i = 0; i < I; ++i) ts.tile_off[i + 1] = ts.tile_off[i] + h_cnt[c.inst_grid[i]];
+  ts.n_units = ts.tile_off[I];
+  int64_t *d_tile_off;
+  int4 *unit;
+  PF_TRY(tmp.alloc(&d_tile_off, I + 1));
+  PF_CUDA_TRY(cudaMemcpyAsync(d_tile_off, ts.tile_off.data(), (I + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  PF_TRY(dev_alloc(c, &unit, 6 * ts.n_units));
+  if (ts.n_units > 0) {
+    View vu = v;
+    vu.n_tile_units = ts.n_units;
+    k_tunit_fill<<<nblk(ts.n_units), TB, 0, s>>>(vu, d_tile_off, d_gto, desc, seg, frow, unit);
+    PF_CUDA_TRY(cudaGetLastError());
+  }
+  std::vector<int32_t> herr = to_host(err, 1, s, &rc);
+  if (rc) return rc;
+  std::vector<int32_t> hstage = to_host(max_stage, 1, s, &rc);
+  if (rc) return rc;
+  if (herr[0]) return fail(PF_ERR_UNSUPPORTED, "tile layout: rows of consecutive buses are not consecutive");
+  ts.pair_idx = pidx;
+  ts.tunit = unit;
+  ts.stage = (hstage[0] + 1) & ~1;
+  PF_CUDA_TRY(cudaStreamSynchronize(s));
+  return PF_OK;
+}
+
+int use_tile_set(Ctx &c, int split, cudaStream_t s) {
+  if (!c.tiles[split].tunit) PF_TRY(build_tile_set(c, split, s));
+  const Ctx::TileSet &ts = c.tiles[split];
+  c.v.pair_idx = ts.pair_idx;
+  c.v.tunit = ts.tunit;
+  c.v.n_tile_units = ts.n_units;
+  c.v.tile_stage = ts.stage;
+  return PF_OK;
+}
+
+// The list of pairs of connected buses bus by bus (shared by every tiling),
+// their coefficients, and the tiles of split_rounds = 0.
+int build_tiles(Ctx &c, cudaStream_t s) {
+  View &v = c.v;
+  const int64_t N = v.n_bus;
+  TempList tmp;
+  int rc = PF_OK;
+  int32_t *cnt, *err, *ptr;
+  int64_t *S, *stmp;
+  PF_TRY(tmp.alloc(&cnt, N));
+  PF_TRY(tmp.alloc(&S, N + 1));
+  PF_TRY(tmp.alloc(&stmp, scan_tmp_elems(N) + 1));
+  PF_TRY(tmp.alloc(&err, 1));
+  PF_TRY(dev_alloc(c, &ptr, N + 1));
+  PF_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
+  k_pair_count<<<nblk(N), TB, 0, s>>>(v, cnt);
+  PF_CUDA_TRY(cudaGetLastError());
+  PF_TRY(exclusive_scan<int32_t>(cnt, S, N, stmp, s));
+  k_pair_ptr<<<nblk(N + 1), TB, 0, s>>>(S, N, ptr, err);
+  PF_CUDA_TRY(cudaGetLastError());
+  v.pair_ptr = ptr;
+  std::vector<int64_t> total = to_host(S + N, 1, s, &rc);
+  if (rc) return rc;
+  std::vector<int32_t> herr = to_host(err, 1, s, &rc);
+  if (rc) return rc;
+  if (herr[0]) return fail(PF_ERR_UNSUPPORTED, "more than 2^31 pairs of connected buses");
+  const int64_t NP = total[0];
+  c.n_pairs = NP;
+  int4 *pmeta, *pgbx;
+  double2 *pgb, *pac;
+  PF_TRY(dev_alloc(c, &pmeta, NP));
+  PF_TRY(dev_alloc(c, &pgb, NP));
+  PF_TRY(dev_alloc(c, &pac, NP));
+  PF_TRY(dev_alloc(c, &pgbx, NP));
+  PF_TRY(dev_alloc(c, &c.ov_pair_gb, NP));
+  PF_TRY(dev_alloc(c, &c.ov_pair_ac, NP));
+  PF_TRY(dev_alloc(c, &c.ov_pair_gbx, NP));
+  {
+    // the pair metadata (any tiling's bus indices would do; these are rewritten per tiling)
+    int4 *scratch;
+    int32_t *zero_local;
+    PF_TRY(tmp.alloc(&scratch, NP));
+    PF_TRY(tmp.alloc(&zero_local, N));
+    PF_CUDA_TRY(cudaMemsetAsync(zero_local, 0, N * sizeof(int32_t), s));
+    k_pair_fill<<<nblk(N), TB, 0, s>>>(v, zero_local, pmeta, scratch);
+    PF_CUDA_TRY(cudaGetLastError());
+    if (NP > 0) {
+      k_slot_coeff<<<nblk(NP), TB, 0, s>>>(v, NP, pmeta, v.inc_gb, v.inc_ac, pgb, pac, nullptr);
+      k_slot_fix<<<nblk(NP), TB, 0, s>>>(NP, pmeta, pgb, v.coef_scale, pgbx);
+      PF_CUDA_TRY(cudaGetLastError());
+    }
+    PF_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  v.pair_meta = pmeta;
+  v.pair_gb = pgb;
+  v.pair_ac = pac;
+  v.pair_gbx = pgbx;
+  return use_tile_set(c, 0, s);
+}
+
 int permute_overrides(Ctx &c, cudaStream_t s) {
   if (c.n_slots > 0) {
     k_slot_coeff<<<nblk(c.n_slots), TB, 0, s>>>(c.v, c.n_slots, c.v.slot_meta, c.ov_gb, c.ov_ac, c.ov_slot_gb,
@@ -1024,6 +1284,12 @@ int permute_overrides(Ctx &c, cudaStream_t s) {
   }
   k_rbus_fill<<<nblk(32 * c.n_rounds), TB, 0, s>>>(c.v, 32 * c.n_rounds, c.v.rbus, c.ov_hat, nullptr, nullptr,
                                                    c.ov_rbus_hat, nullptr);
+  if (c.n_pairs > 0) {
+    k_slot_coeff<<<nblk(c.n_pairs), TB, 0, s>>>(c.v, c.n_pairs, c.v.pair_meta, c.ov_gb, c.ov_ac, c.ov_pair_gb,
+                                                c.ov_pair_ac, nullptr);
+    k_slot_fix<<<nblk(c.n_pairs), TB, 0, s>>>(c.n_pairs, c.v.pair_meta, c.ov_pair_gb, c.v.coef_scale,
+                                              c.ov_pair_gbx);
+  }
   PF_CUDA_TRY(cudaGetLastError());
   return PF_OK;
 }
@@ -1519,6 +1785,7 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
     v.br_k_gb = kgb; v.br_k_ab = kab; v.br_k_tc = ktc; v.br_k_ph = kph;
   }
   PF_TRY(build_rounds(c, s));
+  PF_TRY(build_tiles(c, s));
   PF_CUDA_TRY(cudaStreamSynchronize(s));
   return PF_OK;
 }

@@ -27,22 +27,21 @@
 // 32 x 32 -> 64-bit multiplies, the bus sums S_X, S_Y exact in 128 bits; each
 // J value is rounded once to double (two per pair by the FP64 pipe's
 // conversion, two on the integer pipe).  The per-bus rows (F, the diagonal
-// values) stay in FP64: 9 operations per bus.  A bus whose inputs fall outside
+// values) stay in FP64: 8 operations per bus.  A bus whose inputs fall outside
 // the fixed-point ranges is evaluated in FP64 from x (the form above).
 //
-// Work decomposition.  The buses of each grid are sorted by their number of
-// neighbours and cut into rounds of 32; one warp evaluates one round, one bus
-// per lane.  A lane walks its bus's pairs in incidence-list order, computes
-// each pair's terms, writes the pair's four off-diagonal J entries, keeps the
-// bus sums in registers, and finally writes the bus's F rows and diagonal J
-// entries.  Because the buses of a round have the same number of pairs,
-// nearly every lane does useful work at every step.  A bus with more
-// than 32 neighbours is evaluated by a whole warp in a second kernel.  With
-// split rounds (a tuning choice) a warp takes half (a quarter of) a round, two
-// (four) lanes per bus taking alternate pairs, their exact partial sums merged
-// by shuffles.  The
-// launch has one one-warp CTA per round, or (ctas_per_sm > 0) a persistent
-// grid whose warps claim rounds from a counter.
+// Work decomposition (k_tile).  The buses of each grid are cut, in bus order,
+// into tiles of up to 32 consecutive buses with at most kTilePairs pairs of
+// connected buses, so that a tile's rows of J and of F are contiguous ranges.
+// One warp evaluates one tile of one instance: the lanes share the tile's
+// pairs evenly (pair p on lane p mod 32), each pair's four off-diagonal J
+// entries go to the tile's rows staged in shared memory and its terms X, Y to
+// shared memory; then lane l sums the terms of bus l exactly and writes the
+// bus's diagonal entries and F rows to the staging, and the warp writes the
+// staged rows out whole, every store of the warp to consecutive addresses.  A
+// bus with more than 32 neighbours is evaluated by a whole warp in a second
+// kernel.  The launch has one one-warp CTA per tile and instance, or
+// (ctas_per_sm > 0) a persistent grid whose warps claim units from a counter.
 //
 // Determinism: every operation is an explicitly rounded intrinsic or exact
 // integer arithmetic, the bus sums of a bus with up to 32 neighbours are exact
@@ -267,7 +266,11 @@ __global__ void __launch_bounds__(256) k_phasor_fx(View v, const double *__restr
     const int2 cl = limbs(c60), sl = limbs(s60);
     int4 *rec = reinterpret_cast<int4 *>(v.phasor);
     rec[2 * q] = make_int4(cl.x, cl.y, sl.x, sl.y);
-    rec[2 * q + 1] = make_int4(vl.x, vl.y, __double2loint(vm), __double2hiint(vm));
+    // 1/V for the buses the fixed-point form takes (V in [1/4, 2)): the FP64
+    // pipe is otherwise idle here, and the reciprocal is off the F / J
+    // kernel's dependence chain
+    const double rv = vl.x >= (1 << 28) ? recip(vm) : 0.0;
+    rec[2 * q + 1] = make_int4(vl.x, vl.y, __double2loint(rv), __double2hiint(rv));
   }
 }
 
@@ -336,15 +339,12 @@ __device__ __forceinline__ void acc_add64(Acc128 &a, long long x) {
   a.lo = nlo;
 }
 
-// Adds another accumulator's value (lo, hi).
-__device__ __forceinline__ void acc_merge(Acc128 &a, unsigned long long lo, long long hi) {
-  const unsigned long long nlo = a.lo + lo;
-  a.hi = (long long)((unsigned long long)a.hi + (unsigned long long)hi + (nlo < lo ? 1ULL : 0ULL));
-  a.lo = nlo;
-}
-
 // The accumulator's value 2^-s as a double.
+__device__ __forceinline__ double fix_to_double_cvt(long long z, int s);
 __device__ __forceinline__ double acc_value(const Acc128 &a, int s) {
+  // a sum within 64 bits (the usual case): the hardware conversion, rounded
+  // to nearest even
+  if (a.hi == ((long long)a.lo >> 63)) return fix_to_double_cvt((long long)a.lo, s);
   unsigned long long hi = (unsigned long long)a.hi, lo = a.lo;
   const unsigned long long sign = hi & 0x8000000000000000ULL;
   if (sign) {                                  // magnitude
@@ -370,17 +370,14 @@ struct EvalArgs {
   const double2 *gb;        // per end, incidence order
   const double2 *ac;
   const double2 *hat;       // per bus
-  const double2 *sgb;       // per end, slot order of the rounds
-  const int4 *sgbx;         // sgb in fixed point (limbs)
-  const double2 *sac;
-  const double2 *rhat;      // per bus, round order
+  const double2 *pgb, *pac; // per pair of the tile kernel's list
+  const int4 *pgbx;
   const double *p_inj;     // per-instance-bus override or nullptr
   const double *q_inj;
   const uint8_t *status;   // per-instance-branch mask or nullptr
   const uint8_t *gen_mode; // extended, per instance-generator: != 0 holds Q_g at gen_qlim, or nullptr
   const double *gen_qlim;
-  int split;               // log2 of the lanes per bus: 0, 1 (half a round per warp) or 2 (a quarter)
-  // a persistent (capped) k_fused grid: {next unit, CTAs done} counters of
+  // a persistent (capped) k_tile grid: {next unit, CTAs done} counters of
   // its dynamic schedule, zero at launch and reset by the grid's last CTA;
   // nullptr: CTA b takes units b, b + grid, ...
   unsigned long long *work;
@@ -497,19 +494,31 @@ __device__ __forceinline__ GroupCoeff masked_group(const View &v, const EvalArgs
   return r;
 }
 
-// Under an outage mask, for a bus (lane slots q0 + 32 j, j < D) with an end
-// out of service: A^ and C^ summed over its groups' ends in service (groups
-// merged in incidence order, then summed in list order, as k_hat builds
-// them), plus the shunt.
-__device__ __forceinline__ double2 masked_hat(const View &v, const EvalArgs &a, int64_t q0, int32_t D,
+// The groups of a bus as laid out for a kernel: group j at q0 + stride j,
+// j < n (slots of a round: stride 32, padding marked by a negative group
+// length; the tile kernel's pair list: stride 1), with the arrays of that
+// layout (meta, idx, coefficients).
+struct Walk {
+  const int4 *meta, *idx;
+  const double2 *gb, *ac;
+  int64_t q0;
+  int stride;
+  int32_t n;
+};
+
+// Under an outage mask, for a bus with an end out of service: A^ and C^
+// summed over its groups' ends in service (groups merged in incidence order,
+// then summed in list order, as k_hat builds them), plus the shunt.
+__device__ __forceinline__ double2 masked_hat(const View &v, const EvalArgs &a, const Walk &wk,
                                            int32_t outage, int64_t st_base, int32_t o) {
   double sa = 0.0, sc = 0.0;
-  for (int32_t j = 0; j < D; ++j) {
-    const int4 m = __ldg(v.slot_meta + q0 + 32 * j);
+  for (int32_t j = 0; j < wk.n; ++j) {
+    const int64_t q = wk.q0 + (int64_t)wk.stride * j;
+    const int4 m = __ldg(wk.meta + q);
     if (m.y < 0) continue;
     double2 ac;
     if (m.y == 1) {
-      ac = end_in_service(v, m.w, outage, a.status, st_base) ? __ldg(a.sac + q0 + 32 * j) : make_double2(0.0, 0.0);
+      ac = end_in_service(v, m.w, outage, a.status, st_base) ? __ldg(wk.ac + q) : make_double2(0.0, 0.0);
     } else {
       ac = masked_group(v, a, m.w, m.y, outage, st_base).ac;
     }
@@ -518,29 +527,6 @@ __device__ __forceinline__ double2 masked_hat(const View &v, const EvalArgs &a, 
   }
   const double2 sh = __ldg(v.bus_sh + o);
   return make_double2(__dadd_rn(sa, sh.x), __dadd_rn(sc, sh.y));
-}
-
-// Rows of J a warp stages in shared memory before writing them out whole:
-// a bus with at most kStageMaxD neighbours has rows of at most
-// 2 (kStageMaxD + 1) + 1 = kStageLen entries (theta and V columns of itself and
-// its neighbours, plus P_s or Q_g in the extended formulation).  Each bus
-// lane owns kStageStride doubles (its P row, then its Q row, one spare so
-// that the lanes' strides are odd and their accesses spread over the banks).
-constexpr int kStageMaxD = 6;
-constexpr int kStageLen = 16;
-constexpr int kStageStride = 2 * kStageLen + 1;
-constexpr int kStageBytes = 32 * kStageStride * 8;
-
-// n staged values to dst: one value first when dst is not 16-byte aligned,
-// then pairs of values per store.
-__device__ __forceinline__ void write_row(double *dst, const double *src, int32_t n) {
-  int32_t i = 0;
-  if ((reinterpret_cast<uintptr_t>(dst) & 8) && n > 0) {
-    dst[0] = src[0];
-    i = 1;
-  }
-  for (; i + 1 < n; i += 2) *reinterpret_cast<double2 *>(dst + i) = make_double2(src[i], src[i + 1]);
-  if (i < n) dst[i] = src[i];
 }
 
 // z 2^-s as a double by the hardware conversion on the FP64 pipe (rounded to
@@ -552,33 +538,31 @@ __device__ __forceinline__ double fix_to_double_cvt(long long z, int s) {
   return __hiloint2double(z == 0 ? 0 : __double2hiint(d) - (s << 20), __double2loint(d));
 }
 
-// Where a lane's in-row J values go: the shared-memory rows of its bus, or
-// straight to J at the rows' CSR positions (bp, bq: -1 for an absent row).
+// Where a bus's in-row J values go: the first entry of its P row and of its
+// Q row, either staged in shared memory or in J itself (nullptr: the row
+// does not exist, or J is not wanted).
 struct RowSink {
-  double *srow;     // staged: P row at srow[0..), Q row at srow[kStageLen..); nullptr: direct
-  double *vi;
-  int32_t bp, bq;
+  double *prow, *qrow;
   __device__ __forceinline__ void p(int32_t off, double x) const {
-    if (srow) srow[off] = x;
-    else if (bp >= 0) vi[bp + off] = x;
+    if (prow) prow[off] = x;
   }
   __device__ __forceinline__ void q(int32_t off, double x) const {
-    if (srow) srow[kStageLen + off] = x;
-    else if (bq >= 0) vi[bq + off] = x;
+    if (qrow) qrow[off] = x;
   }
 };
 
 // F rows, the extended formulation's extra rows and the diagonal of J for
 // bus o (global id) of one instance, from the sums over its ends; in-row
-// values through the sink.
+// values through the sink, the bus's F_P and F_Q to fpr and fqr (nullptr:
+// no such row), the extended formulation's g_V and g_theta rows straight to
+// F and J.
 template <bool WF, bool WJ>
 __device__ __forceinline__ void finalize_bus(const View &v, const EvalArgs &a, int inst, int g, int32_t o,
                                              int64_t gb0, int32_t nb, const double *xi, double *Fi, double *vi,
-                                             const RowSink &rs,
+                                             const RowSink &rs, double *fpr, double *fqr,
                                              double vo, double rvo, double sx, double sy, double ah, double ch,
                                              int4 bm, int4 bm2, double2 inj) {
   const int64_t lb = o - gb0;
-  const int32_t rp = bm.x, rq = bm.y;
   const int32_t gi = bm2.w;
   const bool is_slack = (v.formulation == PF_EXTENDED) && (lb == v.grid_slack[g]);
   const double v2 = __dmul_rn(vo, vo);
@@ -600,8 +584,8 @@ __device__ __forceinline__ void finalize_bus(const View &v, const EvalArgs &a, i
       Fi[2 * nb + gi] = (a.gen_mode && a.gen_mode[gq]) ? __dsub_rn(qg, a.gen_qlim[gq])       // held at a limit
                                                        : __dsub_rn(vo, v.gen_vset[v.grid_gen_off[g] + gi]);
     }
-    if (rp >= 0) Fi[rp] = fp;
-    if (rq >= 0) Fi[rq] = fq;
+    if (fpr) *fpr = fp;
+    if (fqr) *fqr = fq;
   }
   if (WJ) {
     if (bm2.x >= 0) {
@@ -687,16 +671,16 @@ __device__ __forceinline__ Rec load_rec(const int4 *p) {
 // `fast` when V_o lies in [1/4, 2) (kBadLimb is negative).
 struct OwnV {
   int2 eo, fo, nfo;
-  long long vof;
+  double rvo;
   double vo;                                      // V_o
   bool fast;
 };
 
 __device__ __forceinline__ OwnV own_voltage(const Rec &ro) {
   OwnV w;
-  w.vo = __hiloint2double(ro.w.w, ro.w.z);
   const int2 vl = make_int2(ro.w.x, ro.w.y);
-  w.vof = ((long long)ro.w.x << 30) + ro.w.y;
+  w.rvo = __hiloint2double(ro.w.w, ro.w.z);
+  w.vo = fix_to_double_cvt(((long long)ro.w.x << 30) + ro.w.y, 60);   // exact for 2^-8 <= V < 2
   w.fast = ro.w.x >= (1 << 28);
   w.eo = limbs(mul60(vl, make_int2(ro.u.x, ro.u.y)));
   const long long f = mul60(vl, make_int2(ro.u.z, ro.u.w));
@@ -732,13 +716,10 @@ __device__ __forceinline__ PairT pair_terms(const OwnV &w, const Rec &rk, int4 g
   return t;
 }
 
-// Adds a pair to the bus sums and its four J values (in-row offsets packed in
-// offs: theta_k low, V_k high, -1 absent) to the sink.
+// A pair's four J values (in-row offsets packed in offs: theta_k low, V_k
+// high, -1 absent) to the sink.
 template <bool WJ>
-__device__ __forceinline__ void put_pair(Acc128 &ax, Acc128 &ay, const RowSink &rs, int32_t offs, const PairT &t,
-                                         int sT) {
-  acc_add64(ax, t.xx);
-  acc_add64(ay, t.my);
+__device__ __forceinline__ void put_pair_values(const RowSink &rs, int32_t offs, const PairT &t, int sT) {
   if (WJ) {
     const int32_t ot = (short)(offs & 0xffff), ov = offs >> 16;
     if (ot >= 0) {
@@ -751,6 +732,7 @@ __device__ __forceinline__ void put_pair(Acc128 &ax, Acc128 &ay, const RowSink &
     }
   }
 }
+
 
 // A unit's instance: its grid and where its state, outputs and records live.
 struct UnitCtx {
@@ -768,23 +750,18 @@ struct UnitCtx {
 // double (or, when the fixed-point form does not hold for the bus, every value
 // of the bus again in FP64 from x and the records, pairs in list order), A^
 // and C^ re-summed under a mask, the F rows and diagonal values
-// (finalize_bus), and the staged rows written out.  The slots of the bus are
-// q0 + 32 j, j < D.
+// (finalize_bus).  bm2, hat, inj: the bus's row data; wk: its groups.
 template <bool WF, bool WJ, bool MASKED>
 __device__ __forceinline__ void finish_bus(const View &v, const EvalArgs &a, const UnitCtx &uc, int32_t o,
-                                           int32_t rb, int4 bm, const RowSink &rs, bool fast, bool any_out,
-                                           const Acc128 &ax, const Acc128 &ay, const OwnV &w, int32_t D,
-                                           int32_t q0, int sT, bool staged) {
-  // the bus's own row data, loaded only now (fewer registers live across the pairs)
-  const int4 bm2 = __ldg(v.rbus_meta2 + rb);
-  double2 hat = __ldg(a.rhat + rb);
-  const double2 inj = WF ? __ldg(v.rbus_inj + rb) : make_double2(0.0, 0.0);
+                                           int4 bm, int4 bm2, double2 hat, double2 inj, const RowSink &rs,
+                                           double *fpr, double *fqr, bool fast, bool any_out, const Acc128 &ax,
+                                           const Acc128 &ay, const OwnV &w, const Walk &wk, int sT) {
   double sx, sy, vo, rvo;
   if (fast) {
     sx = acc_value(ax, sT);
     sy = neg(acc_value(ay, sT));
     vo = w.vo;
-    rvo = recip(vo);                             // V_o in [1/4, 2)
+    rvo = w.rvo;                                 // V_o in [1/4, 2): from k_phasor_fx
   } else {
     // FP64 form of the whole bus, pairs in list order
     const VoltD Vo = volt_fp64(uc.rec4, uc.xi, uc.nb, o - uc.gb0, o);
@@ -793,11 +770,12 @@ __device__ __forceinline__ void finish_bus(const View &v, const EvalArgs &a, con
     sx = 0.0;
     sy = 0.0;
     bool unused = false;
-    for (int32_t j = 0; j < D; ++j) {
-      const int32_t q = q0 + 32 * j;
-      const int4 m = __ldg(v.slot_idx + q);
-      if (m.z < 0) continue;
-      const double2 Gi = slot_gb<MASKED>(v, a, m.z, m.w, __ldg(a.sgb + q), uc.outage, uc.st_base, unused);
+    for (int32_t j = 0; j < wk.n; ++j) {
+      const int64_t q = wk.q0 + (int64_t)wk.stride * j;
+      const int4 m = __ldg(wk.idx + q);
+      const int32_t len = (short)(m.z & 0xffff);
+      if (len < 0) continue;
+      const double2 Gi = slot_gb<MASKED>(v, a, len, m.w, __ldg(wk.gb + q), uc.outage, uc.st_base, unused);
       const VoltD Vk = volt_fp64(uc.rec4, uc.xi, uc.nb, m.x - uc.gb0, m.x);
       const EndTerms tm = end_terms(Gi, Vo.E, Vk.E);
       sx = __dadd_rn(sx, tm.X);
@@ -817,66 +795,75 @@ __device__ __forceinline__ void finish_bus(const View &v, const EvalArgs &a, con
   }
   // A^, C^: built (every end in service), else re-summed over the ends in
   // service in the same order as the built value
-  if (MASKED && any_out) hat = masked_hat(v, a, q0, D, uc.outage, uc.st_base, o);
-  finalize_bus<WF, WJ>(v, a, uc.inst, uc.g, o, uc.gb0, uc.nb, uc.xi, uc.Fi, uc.vi, rs, vo, rvo, sx, sy, hat.x,
-                       hat.y, bm, bm2, inj);
-  if (staged) {
-    // the rows out whole, two values per store
-    const bool ext = v.formulation == PF_EXTENDED;
-    const int32_t lp = bm2.z + (ext && o - uc.gb0 == v.grid_slack[uc.g] ? 1 : 0);
-    const int32_t lq = bm2.z + (ext && bm2.w >= 0 ? 1 : 0);
-    if (bm.z >= 0) write_row(uc.vi + bm.z, rs.srow, lp);
-    if (bm.w >= 0) write_row(uc.vi + bm.w, rs.srow + kStageLen, lq);
-  }
+  if (MASKED && any_out) hat = masked_hat(v, a, wk, uc.outage, uc.st_base, o);
+  finalize_bus<WF, WJ>(v, a, uc.inst, uc.g, o, uc.gb0, uc.nb, uc.xi, uc.Fi, uc.vi, rs, fpr, fqr, vo, rvo, sx, sy,
+                       hat.x, hat.y, bm, bm2, inj);
 }
 
-// One-warp CTAs that must fit on one SM (the register budget of k_fused).
+// n values from shared memory (src) to global memory (dst) by the 32 lanes of
+// a warp, two values per store; src and dst lie at the same offset modulo 16
+// bytes.
+__device__ __forceinline__ void copy_out(double *dst, const double *src, int32_t n, int lane) {
+  if (n <= 0) return;
+  const int32_t i0 = (int32_t)((reinterpret_cast<uintptr_t>(dst) >> 3) & 1);
+  if (i0 && lane == 0) dst[0] = src[0];
+  const int32_t n2 = (n - i0) >> 1;
+  for (int32_t j = lane; j < n2; j += 32)
+    *reinterpret_cast<double2 *>(dst + i0 + 2 * j) = *reinterpret_cast<const double2 *>(src + i0 + 2 * j);
+  if (((n - i0) & 1) && lane == 0) dst[n - 1] = src[n - 1];
+}
+
+// Shared memory of a k_tile warp (byte offsets, 16-byte aligned): E_o limbs
+// of each bus (32 int4), staging index of each bus's P and Q row (32 int2,
+// -1 none), per-bus flags (32 int: 1 FP64 form, 2 an end out of service), X
+// and -Y of each pair (kTilePairs longlong2), the tile's F values (P rows,
+// then Q rows: 64 doubles), then the staged J rows (v.tile_stage doubles).
+constexpr int kTsOwn = 0;
+constexpr int kTsBase = kTsOwn + 32 * 16;
+constexpr int kTsFlag = kTsBase + 32 * 8;
+constexpr int kTsXY = kTsFlag + 32 * 4;
+constexpr int kTsF = kTsXY + kTilePairs * 16;
+constexpr int kTileSmemFixed = kTsF + 64 * 8;
+static_assert(kTileSmemFixed % 16 == 0, "shared-memory layout of k_tile");
+
+// One-warp CTAs resident per SM (the register budget of k_tile): 28 for the
+// F + J evaluation (72 registers), fewer where a mask or a persistent
+// schedule needs more state.
 template <int ITEMS, bool WF, bool WJ, bool MASKED, bool DYN>
-struct FusedMinCtas {
-  static constexpr bool plain = WF && WJ && !MASKED;     // the F + J evaluation without a mask
-  static constexpr int base = ITEMS == 1 ? (plain ? 24 : 20) : ITEMS == 2 ? 16 : 12;
-  static constexpr int value = DYN ? base - 4 : base;
+struct TileMinCtas {
+  static constexpr int value = (MASKED || DYN) ? 20 : 28;
 };
 
-// One warp per round.  A round holds up to 32 buses with equal (or
-// adjacent) numbers of neighbours, one per lane; lane l walks its bus's
-// groups of parallel branches in incidence order (slot first + 32 j + l holds
-// group j, so every fetch of the round's data is coalesced), keeps the exact
-// bus sums in registers and produces the group's four off-diagonal values.  A
-// group's coefficients are summed at build time, so a pair of buses joined by
-// several branches costs one merged branch end.  Under an outage mask a
-// group with more than one branch re-sums the coefficients of its branches in
-// service.  Slots are fetched ITEMS at a time.
-//
-// The pair terms are formed in fixed point on the integer pipe (see above).
-// A bus whose own voltage is outside [1/4, 2), or that sees a neighbour's
-// record or a coefficient marked kBadLimb, is evaluated in FP64 instead: its
-// lead lane recomputes every value of the bus from x and the records, summing
-// in list order.  Which form a bus takes depends only on the inputs, so every
-// tuning and schedule gives the same bits.
-//
-// J values: in a round of buses with at most kStageMaxD neighbours each bus
-// lane stages its P and Q rows in shared memory and then writes them out
-// whole, two values per store (half the stores of writing each value where it
-// goes, and each row's sectors written by consecutive stores of one lane);
-// larger rounds write each value where it goes.
+// One warp per tile of one instance: up to 32 consecutive buses of a grid and
+// their pairs of connected buses (at most kTilePairs), so that the tile's J
+// values form two contiguous ranges of J (its P rows and its Q rows) and its
+// F values two contiguous ranges of F.
+//   phase 0: lane l takes bus l of the tile: its record gives E_o, kept in
+//            shared memory for every lane;
+//   phase 1: lane l takes pairs l, l + 32, l + 64 of the tile's list (so the
+//            lanes share the pairs evenly whatever the buses' numbers of
+//            neighbours), ITEMS of them with their records in flight at once:
+//            the pair's fixed-point terms, its four J values into the staged
+//            rows and X, -Y into shared memory;
+//   phase 2: lane l sums its bus's X, -Y exactly (128-bit integers, so the
+//            order does not matter) and finishes the bus (finish_bus: the FP64
+//            form where the fixed-point one does not hold, F rows, diagonal
+//            values);
+//   phase 3: the warp writes the staged rows of J and F out whole, two values
+//            per store, every store of the warp to consecutive addresses.
+// With a persistent grid (DYN) the warps claim their units from a counter;
+// the last CTA resets it.
 template <int ITEMS, bool WF, bool WJ, bool MASKED, bool DYN>
-__global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED, DYN>::value)) k_fused(View v, EvalArgs a) {
-  extern __shared__ double s_stage[];           // kStageBytes when WJ
+__global__ void __launch_bounds__(32, (TileMinCtas<ITEMS, WF, WJ, MASKED, DYN>::value)) k_tile(View v, EvalArgs a) {
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  int4 *const s_own = reinterpret_cast<int4 *>(s_raw + kTsOwn);
+  int2 *const s_base = reinterpret_cast<int2 *>(s_raw + kTsBase);
+  int *const s_flag = reinterpret_cast<int *>(s_raw + kTsFlag);
+  longlong2 *const s_xy = reinterpret_cast<longlong2 *>(s_raw + kTsXY);
+  double *const s_f = reinterpret_cast<double *>(s_raw + kTsF);
+  double *const s_j = reinterpret_cast<double *>(s_raw + kTileSmemFixed);
   const int lane = threadIdx.x & 31;
-  // split rounds: a warp takes a half (quarter) round of 16 (8) buses, 2 (4)
-  // lanes per bus, lane l the pairs p, p + 2 (4), ... of bus l & 15 (7),
-  // p = l >> 4 (3)
-  const int split = a.split;
-  const int64_t n_units = v.n_lane_units << split;
-  const int nbw = 32 >> split;                   // buses per warp
-  const int bl0 = lane & (nbw - 1);              // bus lane within the warp's part of the round
-  const int par = lane >> (5 - split);           // this lane's first pair
-  const int step = 1 << split;                   // and its stride
-  const int sT = 59 - v.coef_log2;               // scale of T, X, Y and the sums
-  // Dynamic schedule of a persistent grid: lane 0 claims the warp's next unit
-  // from a counter as it starts a unit, so the claim's latency hides behind
-  // the unit's work; units of uneven weight then even out over the CTAs.
+  const int sT = 59 - v.coef_log2;
   unsigned long long *const work = DYN ? a.work : nullptr;
   int64_t u = blockIdx.x;
   unsigned long long claim = 0;
@@ -888,93 +875,113 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED, DYN>:
     if (lane == 0) claim = atomicAdd(work, 1ULL);
     u = (int64_t)__shfl_sync(0xffffffffu, claim, 0);
   }
-  for (; u < n_units; u = work ? (int64_t)__shfl_sync(0xffffffffu, claim, 0) : u + gridDim.x) {
+  for (; u < v.n_tile_units; u = work ? (int64_t)__shfl_sync(0xffffffffu, claim, 0) : u + gridDim.x) {
     if (work && lane == 0) claim = atomicAdd(work, 1ULL);
-    const int32_t uu = (int32_t)(u >> split);
-    const int4 ur = __ldg(v.unit_rec + uu);     // {instance, round, first slot, D | buses << 8}
-    const int4 ui = __ldg(v.unit_info + uu);    // {grid, buses of the grid, first bus of the grid}
-    const longlong2 up0 = __ldg(v.unit_ptr + 2 * uu), up1 = __ldg(v.unit_ptr + 2 * uu + 1);
-    const int inst = ur.x;
-    const int g = ui.x;
+    const int4 *ur = v.tunit + 6 * u;
+    const int4 td = __ldg(ur), ts = __ldg(ur + 1), tf = __ldg(ur + 2), ti = __ldg(ur + 3);
+    const longlong2 up0 = __ldg(reinterpret_cast<const longlong2 *>(ur + 4));
+    const longlong2 up1 = __ldg(reinterpret_cast<const longlong2 *>(ur + 5));
+    const int inst = ti.x, g = ti.y;
+    const int32_t fp = td.z, np = td.w;
     const double *__restrict__ xi = a.x + up0.x;
     double *__restrict__ Fi = WF ? a.F + up0.y : nullptr;
-    // unit phasor limbs at rec4[2 k], {V limbs, bits of 1/V} at rec4[2 k + 1], by global bus id k
-    const int4 *__restrict__ rec4 = reinterpret_cast<const int4 *>(v.phasor) + 2 * up1.y;
     double *__restrict__ vi = WJ ? a.vals + up1.x : nullptr;
+    const int4 *__restrict__ rec4 = reinterpret_cast<const int4 *>(v.phasor) + 2 * up1.y;
     const int32_t outage = MASKED ? v.inst_outage[inst] : -1;
     const int64_t st_base = MASKED ? v.inst_br_off[inst] - v.grid_br_off[g] : 0;
-    const int32_t D = ur.w & 0xff;
-    const bool staged = WJ && D <= kStageMaxD;
+    // staged J: the P rows at s_j[padP ..), the Q rows at s_j[offQ + padQ ..),
+    // each at the offset modulo 16 bytes of its destination
+    const int32_t padP = WJ ? (int32_t)((reinterpret_cast<uintptr_t>(vi + ts.x) >> 3) & 1) : 0;
+    const int32_t offQ = (padP + ts.y + 1) & ~1;
+    const int32_t padQ = WJ ? (int32_t)((reinterpret_cast<uintptr_t>(vi + ts.z) >> 3) & 1) : 0;
 
-    // this lane's bus: its records in round order
-    const int bl = bl0 + nbw * (int)(u & ((1 << split) - 1));
-    const int32_t rb = 32 * ur.y + bl;            // below 2^31: the build checks the round count
-    const bool owner = bl < (ur.w >> 8);
-    const bool lead = owner && par == 0;         // the lane that finishes the bus
-    int32_t o = 0;
+    const bool owner = lane < td.y;
+    const int32_t o = td.x + lane;
     int4 bm = make_int4(-1, -1, -1, -1);
-    if (owner) {
-      o = __ldg(v.rbus + rb);
-      bm = __ldg(v.rbus_meta + rb);
-    }
-    const RowSink rs{staged ? s_stage + bl0 * kStageStride : nullptr, vi, bm.z, bm.w};
-    Acc128 ax{0ULL, 0LL}, ay{0ULL, 0LL};       // exact S_X and -S_Y
-    bool fast = true;                            // the fixed-point form holds for this bus
-    bool any_out = false;                        // masked: an end of this bus is out of service
-    OwnV w{make_int2(0, 0), make_int2(0, 0), make_int2(0, 0), 0LL, 1.0, true};   // the own bus's voltage
-    const int32_t q0 = ur.z + bl;                 // slot indices are below 2^31 (checked at build)
+    if (owner) bm = __ldg(v.bus_meta + o);
+    OwnV w{make_int2(0, 0), make_int2(0, 0), make_int2(0, 0), 0.0, 1.0, true};
 
-    // (the first pass always runs: it waits for the records and loads the own bus's)
-    for (int32_t j0 = par; j0 == par || j0 < D; j0 += ITEMS * step) {
+    // (the first pass always runs: it waits for the records and sets up the buses)
+    for (int32_t p0 = 0; p0 == 0 || p0 < np; p0 += 32 * ITEMS) {
       int4 idx[ITEMS], GX[ITEMS];
 #pragma unroll
       for (int it = 0; it < ITEMS; ++it) {
+        const int32_t p = p0 + 32 * it + lane;
         idx[it] = make_int4(0, -1, -1, 0);
-        const int32_t j = j0 + it * step;
-        if (j < D) {
-          const int32_t q = q0 + 32 * j;
-          idx[it] = __ldg(v.slot_idx + q);
-          GX[it] = __ldg(a.sgbx + q);
+        if (p < np) {
+          idx[it] = __ldg(v.pair_idx + fp + p);
+          GX[it] = __ldg(a.pgbx + fp + p);
         }
       }
-      if (j0 == par) {
-        // the per-bus records come from k_phasor_fx (programmatic dependent launch)
+      if (p0 == 0) {
+        // phase 0 (the records come from k_phasor_fx, a programmatic dependent launch)
         cudaGridDependencySynchronize();
         if (owner) {
           w = own_voltage(load_rec(rec4 + 2 * o));
-          fast = w.fast;                         // V_o in [1/4, 2)
+          s_own[lane] = make_int4(w.eo.x, w.eo.y, w.fo.x, w.fo.y);
+          s_base[lane] = make_int2((WJ && bm.z >= 0) ? padP + bm.z - ts.x : -1,
+                                   (WJ && bm.w >= 0) ? offQ + padQ + bm.w - ts.z : -1);
+          s_flag[lane] = 0;
         }
+        __syncwarp();
       }
+      // phase 1
 #pragma unroll
       for (int it = 0; it < ITEMS; ++it) {
-        const int32_t len = idx[it].z;           // branches in the group, -1 padding
-        if (len < 0) continue;
-        const int32_t k = idx[it].x;
-        const int4 gx = slot_gbx<MASKED>(v, a, len, idx[it].w, GX[it], outage, st_base, any_out);
-        const PairT t = pair_terms(w, load_rec(rec4 + 2 * k), gx);
-        fast = fast && t.ok;
-        put_pair<WJ>(ax, ay, rs, idx[it].y, t, sT);
+        const int32_t p = p0 + 32 * it + lane;
+        if (idx[it].z < 0) continue;
+        const int32_t len = idx[it].z & 0xffff, ol = (idx[it].z >> 16) & 0xff;
+        bool anyo = false;
+        const int4 gx = slot_gbx<MASKED>(v, a, len, idx[it].w, GX[it], outage, st_base, anyo);
+        const int4 e = s_own[ol];
+        OwnV wo;
+        wo.eo = make_int2(e.x, e.y);
+        wo.fo = make_int2(e.z, e.w);
+        wo.nfo = limbs(-(((long long)e.z << 30) + e.w));
+        const PairT t = pair_terms(wo, load_rec(rec4 + 2 * idx[it].x), gx);
+        s_xy[p] = make_longlong2(t.xx, t.my);
+        if (!t.ok || anyo) atomicOr(s_flag + ol, (t.ok ? 0 : 1) | (anyo ? 2 : 0));
+        if (WJ) {
+          const int2 bs = s_base[ol];
+          const RowSink rs{bs.x >= 0 ? s_j + bs.x : nullptr, bs.y >= 0 ? s_j + bs.y : nullptr};
+          put_pair_values<WJ>(rs, idx[it].y, t, sT);
+        }
       }
     }
-    if (split) {
-      // the other lanes of each bus hand their partial sums to the first (a
-      // halving tree): the sums are exact, so the result is the unsplit one,
-      // bit for bit
-      for (int off = 16; off >= nbw; off >>= 1) {
-        acc_merge(ax, __shfl_down_sync(0xffffffffu, ax.lo, off), __shfl_down_sync(0xffffffffu, ax.hi, off));
-        acc_merge(ay, __shfl_down_sync(0xffffffffu, ay.lo, off), __shfl_down_sync(0xffffffffu, ay.hi, off));
-        fast = __shfl_down_sync(0xffffffffu, (int)fast, off) != 0 && fast;
-        any_out = __shfl_down_sync(0xffffffffu, (int)any_out, off) != 0 || any_out;
+    __syncwarp();
+    // phase 2
+    if (owner) {
+      const int32_t pr0 = __ldg(v.pair_ptr + o) - fp, pr1 = __ldg(v.pair_ptr + o + 1) - fp;
+      Acc128 ax{0ULL, 0LL}, ay{0ULL, 0LL};
+      for (int32_t q = pr0; q < pr1; ++q) {
+        const longlong2 xy = s_xy[q];
+        acc_add64(ax, xy.x);
+        acc_add64(ay, xy.y);
       }
-      __syncwarp();                              // the FP64 path below rewrites the other lanes' values
+      const int fl = s_flag[lane];
+      const bool fast = w.fast && !(fl & 1);
+      const int4 bm2 = __ldg(v.bus_meta2 + o);
+      const double2 hat = __ldg(a.hat + o);
+      const double2 inj = WF ? __ldg(v.bus_inj + o) : make_double2(0.0, 0.0);
+      const int2 bs = s_base[lane];
+      const RowSink rs{bs.x >= 0 ? s_j + bs.x : nullptr, bs.y >= 0 ? s_j + bs.y : nullptr};
+      const UnitCtx uc{inst, g, ti.z, ti.w, xi, Fi, vi, rec4, outage, st_base};
+      const Walk wk{v.pair_meta, v.pair_idx, a.pgb, a.pac, (int64_t)fp + pr0, 1, pr1 - pr0};
+      finish_bus<WF, WJ, MASKED>(v, a, uc, o, bm, bm2, hat, inj, rs, (WF && bm.x >= 0) ? s_f + (bm.x - tf.x) : nullptr,
+                                 (WF && bm.y >= 0) ? s_f + 32 + (bm.y - tf.z) : nullptr, fast, (fl & 2) != 0, ax, ay,
+                                 w, wk, sT);
     }
-    if (lead) {
-      const UnitCtx uc{inst, g, ui.z, ui.y, xi, Fi, vi, rec4, outage, st_base};
-      finish_bus<WF, WJ, MASKED>(v, a, uc, o, rb, bm, rs, fast, any_out, ax, ay, w, D, q0, sT, staged);
+    __syncwarp();
+    // phase 3
+    if (WJ) {
+      copy_out(vi + ts.x, s_j + padP, ts.y, lane);
+      copy_out(vi + ts.z, s_j + offQ + padQ, ts.w, lane);
     }
-    if (staged) {
-      __syncwarp();                              // the next round reuses the rows
+    if (WF) {
+      if (lane < tf.y) Fi[tf.x + lane] = s_f[lane];
+      if (lane < tf.w) Fi[tf.z + lane] = s_f[32 + lane];
     }
+    __syncwarp();                                // the next unit reuses the staging
   }
   // Every CTA leaves the loop once, after a claim past the last unit; the last
   // one to leave resets both counters for the next launch.
@@ -987,11 +994,11 @@ __global__ void __launch_bounds__(32, (FusedMinCtas<ITEMS, WF, WJ, MASKED, DYN>:
   }
 }
 
-// Buses with more than 32 ends, one warp each (launched after k_fused, so the
+// Buses with more than 32 ends, one warp each (launched after k_tile, so the
 // records are complete), in FP64.  Lane l takes ends l, l + 32, l + 64, ... of
 // the bus's list and sums them in that order; the 32 partial sums are then
 // combined by a fixed butterfly, so the result depends on neither the
-// tuning nor the schedule.  Off-diagonal entries as in k_fused's FP64 form.
+// tuning nor the schedule.  Off-diagonal entries as in k_tile's FP64 form.
 template <int ITEMS, bool WF, bool WJ, bool MASKED>
 __global__ void __launch_bounds__(32) k_fused_large(View v, EvalArgs a) {
   const int lane = threadIdx.x & 31;
@@ -1075,38 +1082,38 @@ __global__ void __launch_bounds__(32) k_fused_large(View v, EvalArgs a) {
       }
       const double2 inj = WF ? __ldg(v.bus_inj + o) : make_double2(0.0, 0.0);
       const int4 bm = __ldg(v.bus_meta + o);
-      const RowSink rs{nullptr, vi, bm.z, bm.w};
-      finalize_bus<WF, WJ>(v, a, inst, g, o, gb0, nb, xi, WF ? a.F + v.inst_f_off[inst] : nullptr, vi, rs, Vo.v,
-                           Vo.rv, sx, sy, ah, ch, bm,
+      const RowSink rs{(WJ && bm.z >= 0) ? vi + bm.z : nullptr, (WJ && bm.w >= 0) ? vi + bm.w : nullptr};
+      double *Fi = WF ? a.F + v.inst_f_off[inst] : nullptr;
+      finalize_bus<WF, WJ>(v, a, inst, g, o, gb0, nb, xi, Fi, vi, rs, (WF && bm.x >= 0) ? Fi + bm.x : nullptr,
+                           (WF && bm.y >= 0) ? Fi + bm.y : nullptr, Vo.v, Vo.rv, sx, sy, ah, ch, bm,
                            __ldg(v.bus_meta2 + o), inj);
     }
   }
 }
 
-// pdl: k_fused is launched as a programmatic dependent of the stream's
+// pdl: k_tile is launched as a programmatic dependent of the stream's
 // previous kernel (k_phasor), so its CTAs start before that grid ends and
 // load the static maps and the branch coefficients ahead of their wait for
 // it; set only where no kernel that wrote those coefficients comes directly
 // before it.
 template <int ITEMS, bool WF, bool WJ, bool MASKED>
 int launch_fused_t(const View &v, int num_sms, const pf_tuning &t, const EvalArgs &a, bool pdl, cudaStream_t s) {
-  if (v.n_lane_units > 0) {
-    const int64_t n_units = v.n_lane_units << a.split;
-    const int64_t grid = capped_grid(n_units, t.ctas_per_sm, num_sms);
+  if (v.n_tile_units > 0) {
+    const int64_t grid = capped_grid(v.n_tile_units, t.ctas_per_sm, num_sms);
     EvalArgs ak = a;
-    if (grid == n_units) ak.work = nullptr;       // one CTA per unit: the hardware schedules them
+    if (grid == v.n_tile_units) ak.work = nullptr;   // one CTA per unit: the hardware schedules them
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(32);
-    cfg.dynamicSmemBytes = WJ ? kStageBytes : 0;
+    cfg.dynamicSmemBytes = kTileSmemFixed + (WJ ? 8 * v.tile_stage : 0);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    if (ak.work) PF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_fused<ITEMS, WF, WJ, MASKED, true>, v, ak));
-    else PF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_fused<ITEMS, WF, WJ, MASKED, false>, v, ak));
+    if (ak.work) PF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tile<ITEMS, WF, WJ, MASKED, true>, v, ak));
+    else PF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tile<ITEMS, WF, WJ, MASKED, false>, v, ak));
   }
   if (v.n_large_units > 0) {
     const int64_t grid = capped_grid(v.n_large_units, t.ctas_per_sm, num_sms);
@@ -1153,6 +1160,9 @@ View range_view(const Ctx &c, int i0, int i1) {
   v.n_large_units = c.large_off[i1] - c.large_off[i0];
   v.bus_inst_begin = c.bus_off[i0];
   v.n_bus_inst = c.bus_off[i1];
+  const std::vector<int64_t> &toff = c.tiles[c.tuning.split_rounds].tile_off;
+  v.tunit = c.v.tunit + 6 * toff[i0];
+  v.n_tile_units = toff[i1] - toff[i0];
   return v;
 }
 
@@ -1160,10 +1170,9 @@ void built_coefficients(const View &v, EvalArgs &a) {
   a.gb = v.inc_gb;
   a.ac = v.inc_ac;
   a.hat = v.bus_hat;
-  a.sgb = v.slot_gb;
-  a.sgbx = v.slot_gbx;
-  a.sac = v.slot_ac;
-  a.rhat = v.rbus_hat;
+  a.pgb = v.pair_gb;
+  a.pac = v.pair_ac;
+  a.pgbx = v.pair_gbx;
 }
 
 __global__ void k_sincos(const double *__restrict__ t, int64_t n, const longlong2 *__restrict__ tabf,
@@ -1201,7 +1210,6 @@ int launch_eval_stages(Ctx &c, int stages, const double *x, const pf_overrides *
   a.x = x;
   a.F = F;
   a.vals = vals;
-  a.split = c.tuning.split_rounds;
   a.work = c.work_ctr;
   built_coefficients(c.v, a);
   bool params = false;                           // per-call branch parameters
@@ -1221,10 +1229,9 @@ int launch_eval_stages(Ctx &c, int stages, const double *x, const pf_overrides *
       a.gb = c.ov_gb;
       a.ac = c.ov_ac;
       a.hat = c.ov_hat;
-      a.sgb = c.ov_slot_gb;
-      a.sgbx = c.ov_slot_gbx;
-      a.sac = c.ov_slot_ac;
-      a.rhat = c.ov_rbus_hat;
+      a.pgb = c.ov_pair_gb;
+      a.pac = c.ov_pair_ac;
+      a.pgbx = c.ov_pair_gbx;
     }
   }
   const bool masked = c.any_outage || a.status != nullptr;
@@ -1246,7 +1253,6 @@ int launch_eval_range(Ctx &c, int i0, int i1, const double *x, double *F, double
   a.x = x;
   a.F = F;
   a.vals = vals;
-  a.split = c.tuning.split_rounds;
   a.work = c.work_ctr;
   built_coefficients(c.v, a);
   PF_TRY(launch_phasor(v, c.num_sms, x, s, true));
@@ -1265,7 +1271,6 @@ int launch_eval_scratch(Ctx &c, const double *x, double *F, double *vals, double
   a.x = x;
   a.F = F;
   a.vals = vals;
-  a.split = c.tuning.split_rounds;
   a.work = c.work_ctr;
   built_coefficients(c.v, a);
   PF_TRY(launch_phasor(v, c.num_sms, x, s, true));

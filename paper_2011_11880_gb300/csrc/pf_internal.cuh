@@ -28,6 +28,16 @@ constexpr int kMaxGroup = 32;      // parallel branches between one pair of buse
 // numbers of neighbours, one bus per lane; a bus with more than
 // kLaneMaxDegree neighbours is evaluated by a whole warp.
 constexpr int kLaneMaxDegree = 32;
+// Tiles of the fused F / J kernel: up to kTileBuses consecutive buses of a
+// grid (no large bus among them) with at most kTilePairs pairs of connected
+// buses, so that the tile's rows of J and F are contiguous ranges that one
+// warp stages in shared memory and writes out whole.  The tuning choice
+// split_rounds = s cuts smaller tiles, of up to kTileBuses >> s buses and
+// kTilePairs >> s pairs (more warps with shorter work, for contexts that fill
+// less than a wave).
+constexpr int kTileBuses = 32;
+constexpr int kTilePairs = 96;
+
 constexpr int kSinCosTable = 32768;  // table of (cos, sin)(i pi / 16384)
 // Instance-buses are grouped in chunks of 2^kChunkLog2 for the per-bus kernels'
 // instance lookup (View::chunk_inst).
@@ -170,6 +180,24 @@ struct View {
   const int4 *slot_idx;                       // {other bus, in-row offsets of (theta_k, V_k) as two int16
                                               //  (-1 absent), group length (-1 padding), code of a
                                               //  single branch or first end of a group}
+  // tiles of the fused F / J kernel: consecutive buses, their pairs of
+  // connected buses listed bus by bus (the groups of parallel branches in
+  // incidence order), in the formats of the slot arrays
+  const int32_t *pair_ptr;                    // [n_bus+1] first pair of each bus (none for a large bus)
+  const int4 *pair_meta;                      // as slot_meta
+  const int4 *pair_idx;                       // as slot_idx, with the bus's index in its tile in
+                                              //   bits 16..23 of the group length field
+  const double2 *pair_gb, *pair_ac;           // as slot_gb, slot_ac
+  const int4 *pair_gbx;                       // as slot_gbx
+  const int4 *tunit;                          // per tile of every instance, six int4: {first bus, buses,
+                                              //   first pair, pairs}, {J position of the first P row and
+                                              //   length of the tile's P rows, the same for Q}, {first P
+                                              //   row, P rows, first Q row, Q rows}, {instance, grid, first
+                                              //   bus of the grid, buses of the grid}, then {x offset,
+                                              //   F offset}, {J offset, record base} as int64
+  int64_t n_tile_units;                       // tiles over all instances
+  int32_t tile_stage;                         // doubles of J a tile stages (its P and Q rows, two pads)
+
   int coef_log2;                              // 2^coef_log2 bounds the coefficients of slot_gbx
   double coef_scale;                          // 2^(59 - coef_log2)
 
@@ -218,6 +246,20 @@ struct Ctx {
   double2 *ov_gb = nullptr, *ov_ac = nullptr, *ov_hat = nullptr;
   double2 *ov_slot_gb = nullptr, *ov_slot_ac = nullptr, *ov_slot_gbm = nullptr, *ov_rbus_hat = nullptr;
   int4 *ov_slot_gbx = nullptr;
+  double2 *ov_pair_gb = nullptr, *ov_pair_ac = nullptr;
+  int4 *ov_pair_gbx = nullptr;
+  int64_t n_pairs = 0;
+  // the tiles of each split_rounds value (built on first use): the pair list's
+  // index records with each pair's bus index in its tile, the unit records,
+  // the staged J doubles per tile, and per instance its first unit
+  struct TileSet {
+    int4 *pair_idx = nullptr;
+    int4 *tunit = nullptr;
+    int64_t n_units = 0;
+    int32_t stage = 0;
+    std::vector<int64_t> tile_off;
+  };
+  TileSet tiles[3];
   int64_t n_slots = 0, n_rounds = 0;
   std::vector<int64_t> grid_round_off;
   std::vector<int64_t> lane_off, large_off;   // per instance: first unit of k_fused / k_fused_large
@@ -314,6 +356,8 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
                   int n_inst, int formulation, cudaStream_t s);
 // Copies per-call coefficients (incidence / bus order) into slot / round order.
 int permute_overrides(Ctx &c, cudaStream_t s);
+// The tiles of split_rounds = split (built once) become the fused kernel's.
+int use_tile_set(Ctx &c, int split, cudaStream_t s);
 // Newton iterations (pf_newton.cu).
 int newton(Ctx &c, double *x, double tol, int max_iter, cudaStream_t s, pf_newton_info *info,
            const pf_overrides *ov = nullptr);
