@@ -181,6 +181,11 @@ typedef struct pf_tuning {
                                     shorter work, for contexts that fill less than a wave (the
                                     smaller tilings are built on first use).  Results are
                                     bit-identical. */
+  int32_t fuse_phasor;           /* 1: the fused kernel forms the voltage records of each tile's
+                                    buses and of their neighbours outside the tile itself (one
+                                    launch per evaluation, no record gathers; neighbours' records
+                                    are formed again by every tile that reaches them); 0: a phasor
+                                    kernel forms every record once before it.  Bit-identical. */
 } pf_tuning;
 
 /* ---- build (once) -------------------------------------------------------- */
@@ -248,12 +253,14 @@ PF_API int pf_eval(pf_ctx *ctx, const double *x, const pf_overrides *ov, double 
             void *stream);
 
 /* The two kernels of an evaluation, one at a time: PF_STAGE_PHASOR computes
- * the per-bus records (the bus voltage V (cos theta, sin theta), V and 1/V,
- * as pf_voltage_records returns them) into the context's scratch;
- * PF_STAGE_FUSED runs the fused F / J kernel, reading that scratch (a
- * PF_STAGE_PHASOR call at the same x must precede it on the stream).
- * pf_eval runs both.  For timing each kernel and for overlapping the stages
- * with other work.  ov may be NULL; F or vals may be NULL. */
+ * the per-bus records (the unit phasor (cos theta, sin theta) and V in fixed
+ * point, and 1/V) into the context's scratch; PF_STAGE_FUSED runs the fused
+ * F / J kernel, reading that scratch (a PF_STAGE_PHASOR call at the same x
+ * must precede it on the stream).  Under the tuning fuse_phasor = 1 the fused
+ * kernel forms the records it needs itself, and PF_STAGE_PHASOR computes only
+ * those of buses with more than 32 neighbours.  pf_eval runs both.  For
+ * timing each kernel and for overlapping the stages with other work.  ov may
+ * be NULL; F or vals may be NULL. */
 #define PF_STAGE_PHASOR 1
 #define PF_STAGE_FUSED 2
 PF_API int pf_eval_stage(pf_ctx *ctx, int32_t stage, const double *x, const pf_overrides *ov, double *F,

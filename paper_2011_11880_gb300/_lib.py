@@ -62,7 +62,8 @@ class PfGrads(ctypes.Structure):
 
 
 class PfTuning(ctypes.Structure):
-    _fields_ = [("tile_inc", c_int32), ("ctas_per_sm", c_int32), ("split_rounds", c_int32)]
+    _fields_ = [("tile_inc", c_int32), ("ctas_per_sm", c_int32), ("split_rounds", c_int32),
+                ("fuse_phasor", c_int32)]
 
 
 class PfNewtonInfo(ctypes.Structure):

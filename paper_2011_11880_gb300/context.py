@@ -325,15 +325,17 @@ class Context:
     # ---- tuning / errors ----
     @staticmethod
     def _tuning_dict(t):
-        return {"tile_inc": t.tile_inc, "ctas_per_sm": t.ctas_per_sm, "split_rounds": t.split_rounds}
+        return {"tile_inc": t.tile_inc, "ctas_per_sm": t.ctas_per_sm, "split_rounds": t.split_rounds,
+                "fuse_phasor": t.fuse_phasor}
 
     def tuning(self):
         t = PfTuning()
         check(self._lib.pf_get_tuning(self._h, ctypes.byref(t)), "pf_get_tuning")
         return self._tuning_dict(t)
 
-    def set_tuning(self, tile_inc: int, ctas_per_sm: int = 0, split_rounds: int = 0, stream=None):
-        t = PfTuning(int(tile_inc), int(ctas_per_sm), int(split_rounds))
+    def set_tuning(self, tile_inc: int, ctas_per_sm: int = 0, split_rounds: int = 0, fuse_phasor: int = 0,
+                   stream=None):
+        t = PfTuning(int(tile_inc), int(ctas_per_sm), int(split_rounds), int(fuse_phasor))
         check(self._lib.pf_set_tuning(self._h, ctypes.byref(t), _stream(stream)), "pf_set_tuning")
 
     def autotune(self, x, F, vals, stream=None, cache=None):

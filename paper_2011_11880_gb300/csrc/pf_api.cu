@@ -35,12 +35,13 @@ namespace {
 
 cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
 
-// Tuning cache: a line is "<tag> <key> <tile_inc> <ctas_per_sm> <split_rounds>".
-constexpr const char *kTuningTag = "pf-tuning-v1";
+// Tuning cache: a line is "<tag> <key> <tile_inc> <ctas_per_sm> <split_rounds> <fuse_phasor>".
+constexpr const char *kTuningTag = "pf-tuning-v2";
 
 bool tuning_valid(const pf_tuning &t) {
   return t.tile_inc >= pf::kMinTileInc && t.tile_inc <= pf::kMaxTileInc && t.tile_inc % 32 == 0 &&
-         t.ctas_per_sm >= 0 && t.ctas_per_sm <= 32 && t.split_rounds >= 0 && t.split_rounds <= 2;
+         t.ctas_per_sm >= 0 && t.ctas_per_sm <= 32 && t.split_rounds >= 0 && t.split_rounds <= 2 &&
+         (t.fuse_phasor == 0 || t.fuse_phasor == 1);
 }
 
 // 64-bit FNV-1a over the bytes of v.
@@ -386,6 +387,7 @@ int pf_set_tuning(pf_ctx *ctx, const pf_tuning *t, void *stream) {
     return fail(PF_ERR_INVALID, "tile_inc must be 32, 64, 96 or 128");
   if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return fail(PF_ERR_INVALID, "ctas_per_sm must be in [0, 32]");
   if (t->split_rounds < 0 || t->split_rounds > 2) return fail(PF_ERR_INVALID, "split_rounds must be 0, 1 or 2");
+  if (t->fuse_phasor != 0 && t->fuse_phasor != 1) return fail(PF_ERR_INVALID, "fuse_phasor must be 0 or 1");
   cudaStream_t s = as_stream(stream);
   PF_CUDA_TRY(cudaStreamSynchronize(s));
   pf::Ctx &c = ctx->c;
@@ -401,6 +403,7 @@ int pf_set_tuning(pf_ctx *ctx, const pf_tuning *t, void *stream) {
   c.tuning.tile_inc = t->tile_inc;
   c.tuning.ctas_per_sm = t->ctas_per_sm;
   c.tuning.split_rounds = t->split_rounds;
+  c.tuning.fuse_phasor = t->fuse_phasor;
   return PF_OK;
 }
 
@@ -427,8 +430,8 @@ int pf_autotune(pf_ctx *ctx, const double *x, double *F, double *vals, void *str
     return PF_OK;
   };
   int rc = PF_OK;
-  for (int k = 0; k < 3 * 4 * 3 && !rc; ++k) {       // split rounds x tiles x CTAs per SM
-    const pf_tuning t{tiles[(k / 3) % 4], ctas[k % 3], k / 12};
+  for (int k = 0; k < 2 * 3 * 4 * 3 && !rc; ++k) {   // phasor form x tile sizes x fetch widths x CTAs per SM
+    const pf_tuning t{tiles[(k / 3) % 4], ctas[k % 3], (k / 12) % 3, k / 36};
     rc = pf_set_tuning(ctx, &t, stream);
     if (rc) break;
     for (int w = 0; w < 2 && !rc; ++w) rc = pf::launch_eval(ctx->c, x, nullptr, F, vals, s);
@@ -470,7 +473,8 @@ int pf_autotune_cache(pf_ctx *ctx, const char *path, const double *x, double *F,
       std::istringstream ls(line);
       std::string tag, k;
       pf_tuning t{};
-      if (ls >> tag >> k >> t.tile_inc >> t.ctas_per_sm >> t.split_rounds && tag == kTuningTag && k == key &&
+      if (ls >> tag >> k >> t.tile_inc >> t.ctas_per_sm >> t.split_rounds >> t.fuse_phasor && tag == kTuningTag &&
+          k == key &&
           tuning_valid(t)) {
         found = t;
         have = true;
@@ -486,7 +490,9 @@ int pf_autotune_cache(pf_ctx *ctx, const char *path, const double *x, double *F,
   pf_tuning t{};
   PF_TRY(pf_autotune(ctx, x, F, vals, stream, &t));
   std::ofstream out(path, std::ios::app);
-  if (out) out << kTuningTag << ' ' << key << ' ' << t.tile_inc << ' ' << t.ctas_per_sm << ' ' << t.split_rounds << '\n';
+  if (out)
+    out << kTuningTag << ' ' << key << ' ' << t.tile_inc << ' ' << t.ctas_per_sm << ' ' << t.split_rounds << ' '
+        << t.fuse_phasor << '\n';
   if (chosen) *chosen = t;
   return PF_OK;
 }

@@ -1118,15 +1118,61 @@ __global__ void k_pair_fill(View v, const int32_t *bus_local, int4 *pmeta, int4 
   }
 }
 
-// per tile of every instance: its six-int4 unit record
+// Per tile: its external neighbours -- the buses outside the tile that its
+// pairs reach -- in ascending order (pass 0 counts them, pass 1 writes them at
+// ext_off[t]), and in bits 24..31 of each pair's group-length field the
+// index of the neighbour's voltage record among the tile's records (buses of
+// the tile first, in order, then the external neighbours), for the form of
+// the fused kernel that computes the records itself.
+__global__ void k_tile_ext(int64_t n_tiles, const int4 *desc, int pass, const int64_t *ext_off, int32_t *ext_cnt,
+                           int32_t *ext, int4 *pidx) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tiles) return;
+  const int4 d = desc[t];                            // {first bus, buses, first pair, pairs}
+  int32_t list[kTilePairs];
+  int n = 0;
+  for (int32_t p = 0; p < d.w; ++p) {
+    const int32_t k = pidx[d.z + p].x;
+    if (k >= d.x && k < d.x + d.y) continue;
+    int i = n;                                       // insertion into the sorted list, no duplicates
+    while (i > 0 && list[i - 1] > k) --i;
+    if (i > 0 && list[i - 1] == k) continue;
+    for (int j = n; j > i; --j) list[j] = list[j - 1];
+    list[i] = k;
+    ++n;
+  }
+  if (pass == 0) {
+    ext_cnt[t] = n;
+    return;
+  }
+  for (int i = 0; i < n; ++i) ext[ext_off[t] + i] = list[i];
+  for (int32_t p = 0; p < d.w; ++p) {
+    int4 q = pidx[d.z + p];
+    int32_t loc;
+    if (q.x >= d.x && q.x < d.x + d.y) {
+      loc = q.x - d.x;
+    } else {
+      int lo = 0, hi = n - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (list[mid] < q.x) lo = mid + 1; else hi = mid;
+      }
+      loc = kTileBuses + lo;
+    }
+    q.z = (q.z & 0x00ffffff) | (loc << 24);
+    pidx[d.z + p] = q;
+  }
+}
+
+// per tile of every instance: its eight-int4 unit record
 __global__ void k_tunit_fill(View v, const int64_t *tile_off, const int64_t *grid_tile_off, const int4 *desc,
-                             const int4 *seg, const int4 *frow, int4 *unit) {
+                             const int4 *seg, const int4 *frow, const int64_t *ext_off, int4 *unit) {
   const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= v.n_tile_units) return;
   const int inst = find_segment(tile_off, v.n_inst, u);
   const int g = v.inst_grid[inst];
   const int64_t t = grid_tile_off[g] + (u - tile_off[inst]);
-  int4 *r = unit + 6 * u;
+  int4 *r = unit + 8 * u;
   r[0] = desc[t];
   r[1] = seg[t];
   r[2] = frow[t];
@@ -1135,6 +1181,8 @@ __global__ void k_tunit_fill(View v, const int64_t *tile_off, const int64_t *gri
                 rb = v.inst_bus_off[inst] - v.grid_bus_off[g];
   r[4] = make_int4((int32_t)(xo & 0xffffffff), (int32_t)(xo >> 32), (int32_t)(fo & 0xffffffff), (int32_t)(fo >> 32));
   r[5] = make_int4((int32_t)(vo & 0xffffffff), (int32_t)(vo >> 32), (int32_t)(rb & 0xffffffff), (int32_t)(rb >> 32));
+  r[6] = make_int4((int32_t)ext_off[t], (int32_t)(ext_off[t + 1] - ext_off[t]), 0, 0);
+  r[7] = make_int4(0, 0, 0, 0);
 }
 
 // The tiles of split_rounds = split: the partition, each pair's bus index in
@@ -1176,6 +1224,25 @@ int build_tile_set(Ctx &c, int split, cudaStream_t s) {
   PF_TRY(dev_alloc(c, &pidx, NP));
   k_pair_fill<<<nblk(N), TB, 0, s>>>(v, bus_local, nullptr, pidx);
   PF_CUDA_TRY(cudaGetLastError());
+  // external neighbours of every tile and the pairs' record indices
+  int32_t *ext_cnt, *ext;
+  int64_t *ext_S, *ext_tmp;
+  PF_TRY(tmp.alloc(&ext_cnt, T));
+  PF_TRY(tmp.alloc(&ext_S, T + 1));
+  PF_TRY(tmp.alloc(&ext_tmp, scan_tmp_elems(T) + 1));
+  if (T > 0) {
+    k_tile_ext<<<nblk(T, 64), 64, 0, s>>>(T, desc, 0, nullptr, ext_cnt, nullptr, pidx);
+    PF_CUDA_TRY(cudaGetLastError());
+  }
+  PF_TRY(exclusive_scan<int32_t>(ext_cnt, ext_S, T, ext_tmp, s));
+  std::vector<int64_t> n_ext = to_host(ext_S + T, 1, s, &rc);
+  if (rc) return rc;
+  if (n_ext[0] > 0x7fffffffLL) return fail(PF_ERR_UNSUPPORTED, "more than 2^31 external neighbours of tiles");
+  PF_TRY(dev_alloc(c, &ext, n_ext[0]));
+  if (T > 0) {
+    k_tile_ext<<<nblk(T, 64), 64, 0, s>>>(T, desc, 1, ext_S, nullptr, ext, pidx);
+    PF_CUDA_TRY(cudaGetLastError());
+  }
   // units: the tiles of every instance, instance by instance
   const int I = v.n_inst;
   ts.tile_off.assign(I + 1, 0);
@@ -1185,11 +1252,11 @@ int build_tile_set(Ctx &c, int split, cudaStream_t s) {
   int4 *unit;
   PF_TRY(tmp.alloc(&d_tile_off, I + 1));
   PF_CUDA_TRY(cudaMemcpyAsync(d_tile_off, ts.tile_off.data(), (I + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-  PF_TRY(dev_alloc(c, &unit, 6 * ts.n_units));
+  PF_TRY(dev_alloc(c, &unit, 8 * ts.n_units));
   if (ts.n_units > 0) {
     View vu = v;
     vu.n_tile_units = ts.n_units;
-    k_tunit_fill<<<nblk(ts.n_units), TB, 0, s>>>(vu, d_tile_off, d_gto, desc, seg, frow, unit);
+    k_tunit_fill<<<nblk(ts.n_units), TB, 0, s>>>(vu, d_tile_off, d_gto, desc, seg, frow, ext_S, unit);
     PF_CUDA_TRY(cudaGetLastError());
   }
   std::vector<int32_t> herr = to_host(err, 1, s, &rc);
@@ -1199,6 +1266,7 @@ int build_tile_set(Ctx &c, int split, cudaStream_t s) {
   if (herr[0]) return fail(PF_ERR_UNSUPPORTED, "tile layout: rows of consecutive buses are not consecutive");
   ts.pair_idx = pidx;
   ts.tunit = unit;
+  ts.ext = ext;
   ts.stage = (hstage[0] + 1) & ~1;
   PF_CUDA_TRY(cudaStreamSynchronize(s));
   return PF_OK;
@@ -1209,6 +1277,7 @@ int use_tile_set(Ctx &c, int split, cudaStream_t s) {
   const Ctx::TileSet &ts = c.tiles[split];
   c.v.pair_idx = ts.pair_idx;
   c.v.tunit = ts.tunit;
+  c.v.tile_ext = ts.ext;
   c.v.n_tile_units = ts.n_units;
   c.v.tile_stage = ts.stage;
   return PF_OK;

@@ -230,14 +230,42 @@ __device__ __forceinline__ long long fix60_of(double x) {
 // value = h 2^30 + l with 0 <= l < 2^30.
 __device__ __forceinline__ int2 limbs(long long z) { return make_int2((int)(z >> 30), (int)(z & 0x3fffffff)); }
 
-// Fixed-point records for the F / J kernels, one thread per instance-bus:
+// The fixed-point record of a bus for the F / J kernels, as two int4:
 // {cos theta 2^60, sin theta 2^60} as 30-bit limbs, then {V 2^60} as limbs
-// and the bits of V, in 32 bytes.  The trigonometric routine runs on the
+// and 1/V (a double), 32 bytes.  The trigonometric routine runs on the
 // integer pipe and its fixed-point result is kept (rounded from 2^62 to 2^60,
 // no rounding to double); V 2^60 is exact for 2^-8 <= |V| < 2.  A voltage
 // outside (-2, 2), or an angle that is not finite, gets kBadLimb in place of
-// V's high limb: the buses that see it evaluate in FP64 from x.  No FP64
-// arithmetic (the reciprocal of V is formed where it is used).
+// V's high limb: the buses that see it evaluate in FP64 from x.  1/V is
+// formed (on the FP64 pipe, otherwise idle here) only for the buses the
+// fixed-point form takes, V in [1/4, 2).
+__device__ __forceinline__ void make_record(double th, double vm, const longlong2 *__restrict__ tabf, int4 &r0,
+                                          int4 &r1) {
+  long long c60, s60;
+  bool finite = true;
+  if ((__double2hiint(th) & 0x7fffffff) < 0x40400000) {       // |t| < 32
+    const longlong2 u = unit_fix_small(th, tabf);
+    c60 = (u.x + 2) >> 2;
+    s60 = (u.y + 2) >> 2;
+    if (__double2hiint(th) < 0) s60 = -s60;                    // sin is odd
+  } else {
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    c60 = __double2ll_rn(__dmul_rn(cs, 0x1p60));
+    s60 = __double2ll_rn(__dmul_rn(sn, 0x1p60));
+    finite = (__double2hiint(th) & 0x7ff00000) != 0x7ff00000;
+  }
+  int2 vl = limbs(fix60_of(vm));
+  if (!finite || (__double2hiint(vm) & 0x7fffffff) >= 0x40000000) vl = make_int2(kBadLimb, 0);   // |V| >= 2, NaN
+  const int2 cl = limbs(c60), sl = limbs(s60);
+  r0 = make_int4(cl.x, cl.y, sl.x, sl.y);
+  const double rv = vl.x >= (1 << 28) ? recip(vm) : 0.0;
+  r1 = make_int4(vl.x, vl.y, __double2loint(rv), __double2hiint(rv));
+}
+
+// The records of every instance-bus, one thread each (the F / J kernel then
+// gathers its buses' and their neighbours' records; 1/V is formed here, off
+// that kernel's dependence chain).
 __global__ void __launch_bounds__(256) k_phasor_fx(View v, const double *__restrict__ x) {
   cudaTriggerProgrammaticLaunchCompletion();
   const int64_t q = v.bus_inst_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -247,30 +275,11 @@ __global__ void __launch_bounds__(256) k_phasor_fx(View v, const double *__restr
     const double *xi = x + v.inst_x_off[inst];
     const double th = __ldg(xi + lb);
     const double vm = __ldg(xi + v.grid_nbus[v.inst_grid[inst]] + lb);
-    long long c60, s60;
-    bool finite = true;
-    if ((__double2hiint(th) & 0x7fffffff) < 0x40400000) {       // |t| < 32
-      const longlong2 u = unit_fix_small(th, v.sincos_fix);
-      c60 = (u.x + 2) >> 2;
-      s60 = (u.y + 2) >> 2;
-      if (__double2hiint(th) < 0) s60 = -s60;                    // sin is odd
-    } else {
-      double sn, cs;
-      sincos(th, &sn, &cs);
-      c60 = __double2ll_rn(__dmul_rn(cs, 0x1p60));
-      s60 = __double2ll_rn(__dmul_rn(sn, 0x1p60));
-      finite = (__double2hiint(th) & 0x7ff00000) != 0x7ff00000;
-    }
-    int2 vl = limbs(fix60_of(vm));
-    if (!finite || (__double2hiint(vm) & 0x7fffffff) >= 0x40000000) vl = make_int2(kBadLimb, 0);   // |V| >= 2, NaN
-    const int2 cl = limbs(c60), sl = limbs(s60);
+    int4 r0, r1;
+    make_record(th, vm, v.sincos_fix, r0, r1);
     int4 *rec = reinterpret_cast<int4 *>(v.phasor);
-    rec[2 * q] = make_int4(cl.x, cl.y, sl.x, sl.y);
-    // 1/V for the buses the fixed-point form takes (V in [1/4, 2)): the FP64
-    // pipe is otherwise idle here, and the reciprocal is off the F / J
-    // kernel's dependence chain
-    const double rv = vl.x >= (1 << 28) ? recip(vm) : 0.0;
-    rec[2 * q + 1] = make_int4(vl.x, vl.y, __double2loint(rv), __double2hiint(rv));
+    rec[2 * q] = r0;
+    rec[2 * q + 1] = r1;
   }
 }
 
@@ -417,9 +426,7 @@ struct VoltD {
   double v, rv;
 };
 
-__device__ __forceinline__ VoltD volt_fp64(const int4 *__restrict__ rec4, const double *__restrict__ xi, int32_t nb,
-                                           int64_t lb, int64_t rb) {
-  const int4 u = rec4[2 * rb];
+__device__ __forceinline__ VoltD volt_fp64(int4 u, const double *__restrict__ xi, int32_t nb, int64_t lb) {
   const double th = xi[lb], vm = xi[nb + lb];
   const double sv = dead_sub(vm);
   VoltD r;
@@ -744,6 +751,8 @@ struct UnitCtx {
   const int4 *rec4;
   int32_t outage;
   int64_t st_base;
+  const int4 *srec;          // the tile's records in shared memory (the kernel forms them), or nullptr
+  int own_loc;               // the bus's record index among them
 };
 
 // The rest of bus o after its pairs, on its lead lane: the sums rounded to
@@ -764,7 +773,7 @@ __device__ __forceinline__ void finish_bus(const View &v, const EvalArgs &a, con
     rvo = w.rvo;                                 // V_o in [1/4, 2): from k_phasor_fx
   } else {
     // FP64 form of the whole bus, pairs in list order
-    const VoltD Vo = volt_fp64(uc.rec4, uc.xi, uc.nb, o - uc.gb0, o);
+    const VoltD Vo = volt_fp64(uc.srec ? uc.srec[2 * uc.own_loc] : uc.rec4[2 * o], uc.xi, uc.nb, o - uc.gb0);
     vo = Vo.v;
     rvo = Vo.rv;
     sx = 0.0;
@@ -776,7 +785,8 @@ __device__ __forceinline__ void finish_bus(const View &v, const EvalArgs &a, con
       const int32_t len = (short)(m.z & 0xffff);
       if (len < 0) continue;
       const double2 Gi = slot_gb<MASKED>(v, a, len, m.w, __ldg(wk.gb + q), uc.outage, uc.st_base, unused);
-      const VoltD Vk = volt_fp64(uc.rec4, uc.xi, uc.nb, m.x - uc.gb0, m.x);
+      const VoltD Vk = volt_fp64(uc.srec ? uc.srec[2 * ((m.z >> 24) & 0xff)] : uc.rec4[2 * m.x], uc.xi, uc.nb,
+                                 m.x - uc.gb0);
       const EndTerms tm = end_terms(Gi, Vo.E, Vk.E);
       sx = __dadd_rn(sx, tm.X);
       sy = __dadd_rn(sy, tm.Y);
@@ -824,12 +834,16 @@ constexpr int kTsFlag = kTsBase + 32 * 8;
 constexpr int kTsXY = kTsFlag + 32 * 4;
 constexpr int kTsF = kTsXY + kTilePairs * 16;
 constexpr int kTileSmemFixed = kTsF + 64 * 8;
+// With the records formed in the kernel (PHX), they follow: the tile's buses
+// at 0..31, its external neighbours from kTileBuses on (32 bytes each), and
+// the staged J rows after them.
+constexpr int kTileRecBytes = (kTileBuses + kTilePairs) * 32;
 static_assert(kTileSmemFixed % 16 == 0, "shared-memory layout of k_tile");
 
 // One-warp CTAs resident per SM (the register budget of k_tile): 28 for the
 // F + J evaluation (72 registers), fewer where a mask or a persistent
 // schedule needs more state.
-template <int ITEMS, bool WF, bool WJ, bool MASKED, bool DYN>
+template <int ITEMS, bool WF, bool WJ, bool MASKED, bool DYN, bool PHX>
 struct TileMinCtas {
   static constexpr int value = (MASKED || DYN) ? 20 : 28;
 };
@@ -852,16 +866,21 @@ struct TileMinCtas {
 //   phase 3: the warp writes the staged rows of J and F out whole, two values
 //            per store, every store of the warp to consecutive addresses.
 // With a persistent grid (DYN) the warps claim their units from a counter;
-// the last CTA resets it.
-template <int ITEMS, bool WF, bool WJ, bool MASKED, bool DYN>
-__global__ void __launch_bounds__(32, (TileMinCtas<ITEMS, WF, WJ, MASKED, DYN>::value)) k_tile(View v, EvalArgs a) {
+// the last CTA resets it.  With PHX the warp first forms the records of its
+// tile's buses and of their external neighbours itself (from x, into shared
+// memory): no phasor kernel before it and no record gathers from L2, at the
+// price of forming a neighbour's record in every tile that reaches it.
+template <int ITEMS, bool WF, bool WJ, bool MASKED, bool DYN, bool PHX>
+__global__ void __launch_bounds__(32, (TileMinCtas<ITEMS, WF, WJ, MASKED, DYN, PHX>::value))
+    k_tile(View v, EvalArgs a) {
   extern __shared__ __align__(16) unsigned char s_raw[];
   int4 *const s_own = reinterpret_cast<int4 *>(s_raw + kTsOwn);
   int2 *const s_base = reinterpret_cast<int2 *>(s_raw + kTsBase);
   int *const s_flag = reinterpret_cast<int *>(s_raw + kTsFlag);
   longlong2 *const s_xy = reinterpret_cast<longlong2 *>(s_raw + kTsXY);
   double *const s_f = reinterpret_cast<double *>(s_raw + kTsF);
-  double *const s_j = reinterpret_cast<double *>(s_raw + kTileSmemFixed);
+  int4 *const s_rec = reinterpret_cast<int4 *>(s_raw + kTileSmemFixed);
+  double *const s_j = reinterpret_cast<double *>(s_raw + kTileSmemFixed + (PHX ? kTileRecBytes : 0));
   const int lane = threadIdx.x & 31;
   const int sT = 59 - v.coef_log2;
   unsigned long long *const work = DYN ? a.work : nullptr;
@@ -877,7 +896,7 @@ __global__ void __launch_bounds__(32, (TileMinCtas<ITEMS, WF, WJ, MASKED, DYN>::
   }
   for (; u < v.n_tile_units; u = work ? (int64_t)__shfl_sync(0xffffffffu, claim, 0) : u + gridDim.x) {
     if (work && lane == 0) claim = atomicAdd(work, 1ULL);
-    const int4 *ur = v.tunit + 6 * u;
+    const int4 *ur = v.tunit + 8 * u;
     const int4 td = __ldg(ur), ts = __ldg(ur + 1), tf = __ldg(ur + 2), ti = __ldg(ur + 3);
     const longlong2 up0 = __ldg(reinterpret_cast<const longlong2 *>(ur + 4));
     const longlong2 up1 = __ldg(reinterpret_cast<const longlong2 *>(ur + 5));
@@ -900,6 +919,20 @@ __global__ void __launch_bounds__(32, (TileMinCtas<ITEMS, WF, WJ, MASKED, DYN>::
     int4 bm = make_int4(-1, -1, -1, -1);
     if (owner) bm = __ldg(v.bus_meta + o);
     OwnV w{make_int2(0, 0), make_int2(0, 0), make_int2(0, 0), 0.0, 1.0, true};
+    if (PHX) {
+      // the records of the tile's buses and of its external neighbours
+      const int4 te = __ldg(ur + 6);             // {first external neighbour, external neighbours}
+      for (int32_t r = lane; r < td.y + te.y; r += 32) {
+        const int32_t b = r < td.y ? td.x + r : __ldg(v.tile_ext + te.x + (r - td.y));
+        const int64_t lb = b - ti.z;
+        int4 r0, r1;
+        make_record(__ldg(xi + lb), __ldg(xi + ti.w + lb), v.sincos_fix, r0, r1);
+        const int32_t slot = r < td.y ? r : kTileBuses + (r - td.y);
+        s_rec[2 * slot] = r0;
+        s_rec[2 * slot + 1] = r1;
+      }
+      __syncwarp();
+    }
 
     // (the first pass always runs: it waits for the records and sets up the buses)
     for (int32_t p0 = 0; p0 == 0 || p0 < np; p0 += 32 * ITEMS) {
@@ -915,9 +948,9 @@ __global__ void __launch_bounds__(32, (TileMinCtas<ITEMS, WF, WJ, MASKED, DYN>::
       }
       if (p0 == 0) {
         // phase 0 (the records come from k_phasor_fx, a programmatic dependent launch)
-        cudaGridDependencySynchronize();
+        if (!PHX) cudaGridDependencySynchronize();
         if (owner) {
-          w = own_voltage(load_rec(rec4 + 2 * o));
+          w = own_voltage(PHX ? Rec{s_rec[2 * lane], s_rec[2 * lane + 1]} : load_rec(rec4 + 2 * o));
           s_own[lane] = make_int4(w.eo.x, w.eo.y, w.fo.x, w.fo.y);
           s_base[lane] = make_int2((WJ && bm.z >= 0) ? padP + bm.z - ts.x : -1,
                                    (WJ && bm.w >= 0) ? offQ + padQ + bm.w - ts.z : -1);
@@ -938,7 +971,9 @@ __global__ void __launch_bounds__(32, (TileMinCtas<ITEMS, WF, WJ, MASKED, DYN>::
         wo.eo = make_int2(e.x, e.y);
         wo.fo = make_int2(e.z, e.w);
         wo.nfo = limbs(-(((long long)e.z << 30) + e.w));
-        const PairT t = pair_terms(wo, load_rec(rec4 + 2 * idx[it].x), gx);
+        const int loc = (idx[it].z >> 24) & 0xff;
+        const PairT t = pair_terms(wo, PHX ? Rec{s_rec[2 * loc], s_rec[2 * loc + 1]} : load_rec(rec4 + 2 * idx[it].x),
+                                   gx);
         s_xy[p] = make_longlong2(t.xx, t.my);
         if (!t.ok || anyo) atomicOr(s_flag + ol, (t.ok ? 0 : 1) | (anyo ? 2 : 0));
         if (WJ) {
@@ -965,7 +1000,7 @@ __global__ void __launch_bounds__(32, (TileMinCtas<ITEMS, WF, WJ, MASKED, DYN>::
       const double2 inj = WF ? __ldg(v.bus_inj + o) : make_double2(0.0, 0.0);
       const int2 bs = s_base[lane];
       const RowSink rs{bs.x >= 0 ? s_j + bs.x : nullptr, bs.y >= 0 ? s_j + bs.y : nullptr};
-      const UnitCtx uc{inst, g, ti.z, ti.w, xi, Fi, vi, rec4, outage, st_base};
+      const UnitCtx uc{inst, g, ti.z, ti.w, xi, Fi, vi, rec4, outage, st_base, PHX ? s_rec : nullptr, lane};
       const Walk wk{v.pair_meta, v.pair_idx, a.pgb, a.pac, (int64_t)fp + pr0, 1, pr1 - pr0};
       finish_bus<WF, WJ, MASKED>(v, a, uc, o, bm, bm2, hat, inj, rs, (WF && bm.x >= 0) ? s_f + (bm.x - tf.x) : nullptr,
                                  (WF && bm.y >= 0) ? s_f + 32 + (bm.y - tf.z) : nullptr, fast, (fl & 2) != 0, ax, ay,
@@ -1015,7 +1050,7 @@ __global__ void __launch_bounds__(32) k_fused_large(View v, EvalArgs a) {
     const int32_t e0 = __ldg(v.inc_ptr + o), e1 = __ldg(v.inc_ptr + o + 1);
     const int64_t gb0 = gb0_of(v, g);
     const int32_t nb = v.grid_nbus[g];
-    const VoltD Vo = volt_fp64(rec4, xi, nb, o - gb0, o);
+    const VoltD Vo = volt_fp64(rec4[2 * o], xi, nb, o - gb0);
     double sx = 0.0, sy = 0.0, acc_ma = 0.0, acc_mc = 0.0;
     for (int32_t cs = e0; cs < e1; cs += 32 * ITEMS) {
       int4 meta[ITEMS];
@@ -1040,7 +1075,7 @@ __global__ void __launch_bounds__(32) k_fused_large(View v, EvalArgs a) {
           if (!in) Gi = make_double2(0.0, 0.0);
         }
         const int32_t k = meta[it].y;
-        const VoltD Vk = volt_fp64(rec4, xi, nb, k - gb0, k);
+        const VoltD Vk = volt_fp64(rec4[2 * k], xi, nb, k - gb0);
         const EndTerms tm = end_terms(Gi, Vo.E, Vk.E);
         sx = __dadd_rn(sx, tm.X);
         sy = __dadd_rn(sy, tm.Y);
@@ -1092,28 +1127,32 @@ __global__ void __launch_bounds__(32) k_fused_large(View v, EvalArgs a) {
 }
 
 // pdl: k_tile is launched as a programmatic dependent of the stream's
-// previous kernel (k_phasor), so its CTAs start before that grid ends and
+// previous kernel (k_phasor_fx), so its CTAs start before that grid ends and
 // load the static maps and the branch coefficients ahead of their wait for
 // it; set only where no kernel that wrote those coefficients comes directly
-// before it.
+// before it.  With t.fuse_phasor k_tile forms the records itself and follows
+// the stream's previous work in plain order (a persistent grid then takes
+// its units by a static stride).
 template <int ITEMS, bool WF, bool WJ, bool MASKED>
 int launch_fused_t(const View &v, int num_sms, const pf_tuning &t, const EvalArgs &a, bool pdl, cudaStream_t s) {
   if (v.n_tile_units > 0) {
+    const bool phx = t.fuse_phasor != 0;
     const int64_t grid = capped_grid(v.n_tile_units, t.ctas_per_sm, num_sms);
     EvalArgs ak = a;
-    if (grid == v.n_tile_units) ak.work = nullptr;   // one CTA per unit: the hardware schedules them
+    if (grid == v.n_tile_units || phx) ak.work = nullptr;   // one CTA per unit: the hardware schedules them
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(32);
-    cfg.dynamicSmemBytes = kTileSmemFixed + (WJ ? 8 * v.tile_stage : 0);
+    cfg.dynamicSmemBytes = kTileSmemFixed + (phx ? kTileRecBytes : 0) + (WJ ? 8 * v.tile_stage : 0);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = pdl ? 1 : 0;
-    if (ak.work) PF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tile<ITEMS, WF, WJ, MASKED, true>, v, ak));
-    else PF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tile<ITEMS, WF, WJ, MASKED, false>, v, ak));
+    cfg.numAttrs = (pdl && !phx) ? 1 : 0;
+    if (phx) PF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tile<ITEMS, WF, WJ, MASKED, false, true>, v, ak));
+    else if (ak.work) PF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tile<ITEMS, WF, WJ, MASKED, true, false>, v, ak));
+    else PF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tile<ITEMS, WF, WJ, MASKED, false, false>, v, ak));
   }
   if (v.n_large_units > 0) {
     const int64_t grid = capped_grid(v.n_large_units, t.ctas_per_sm, num_sms);
@@ -1161,7 +1200,7 @@ View range_view(const Ctx &c, int i0, int i1) {
   v.bus_inst_begin = c.bus_off[i0];
   v.n_bus_inst = c.bus_off[i1];
   const std::vector<int64_t> &toff = c.tiles[c.tuning.split_rounds].tile_off;
-  v.tunit = c.v.tunit + 6 * toff[i0];
+  v.tunit = c.v.tunit + 8 * toff[i0];
   v.n_tile_units = toff[i1] - toff[i0];
   return v;
 }
@@ -1196,6 +1235,9 @@ int launch_phasor(const View &v, int num_sms, const double *x, cudaStream_t s, b
   PF_CUDA_TRY(cudaGetLastError());
   return PF_OK;
 }
+
+// Whether an evaluation launches the phasor kernel before the fused one.
+bool needs_phasor_kernel(const Ctx &c) { return !c.tuning.fuse_phasor || c.v.n_large_units > 0; }
 
 int launch_eval(Ctx &c, const double *x, const pf_overrides *ov, double *F, double *vals, cudaStream_t s) {
   return launch_eval_stages(c, 3, x, ov, F, vals, s);
@@ -1235,7 +1277,9 @@ int launch_eval_stages(Ctx &c, int stages, const double *x, const pf_overrides *
     }
   }
   const bool masked = c.any_outage || a.status != nullptr;
-  if (stages & 1) PF_TRY(launch_phasor(c.v, c.num_sms, x, s, true));
+  // (with the records formed in the fused kernel, the phasor kernel runs only
+  // for the buses of more than 32 neighbours, whose kernel reads records)
+  if ((stages & 1) && needs_phasor_kernel(c)) PF_TRY(launch_phasor(c.v, c.num_sms, x, s, true));
   if (!(stages & 2)) return PF_OK;
   // the fused stage alone with per-call branch parameters: the kernel that
   // wrote its coefficients comes directly before it
@@ -1255,7 +1299,7 @@ int launch_eval_range(Ctx &c, int i0, int i1, const double *x, double *F, double
   a.vals = vals;
   a.work = c.work_ctr;
   built_coefficients(c.v, a);
-  PF_TRY(launch_phasor(v, c.num_sms, x, s, true));
+  if (needs_phasor_kernel(c)) PF_TRY(launch_phasor(v, c.num_sms, x, s, true));
   return launch_fused(v, c.num_sms, c.tuning, a, c.any_outage, s);
 }
 
@@ -1273,7 +1317,7 @@ int launch_eval_scratch(Ctx &c, const double *x, double *F, double *vals, double
   a.vals = vals;
   a.work = c.work_ctr;
   built_coefficients(c.v, a);
-  PF_TRY(launch_phasor(v, c.num_sms, x, s, true));
+  if (needs_phasor_kernel(c)) PF_TRY(launch_phasor(v, c.num_sms, x, s, true));
   return launch_fused(v, c.num_sms, c.tuning, a, c.any_outage, s);
 }
 

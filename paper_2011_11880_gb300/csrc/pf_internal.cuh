@@ -186,15 +186,19 @@ struct View {
   const int32_t *pair_ptr;                    // [n_bus+1] first pair of each bus (none for a large bus)
   const int4 *pair_meta;                      // as slot_meta
   const int4 *pair_idx;                       // as slot_idx, with the bus's index in its tile in
-                                              //   bits 16..23 of the group length field
+                                              //   bits 16..23 of the group length field and the index of
+                                              //   the other bus's record among the tile's records (the
+                                              //   tile's buses, then its external neighbours) in bits 24..31
   const double2 *pair_gb, *pair_ac;           // as slot_gb, slot_ac
   const int4 *pair_gbx;                       // as slot_gbx
-  const int4 *tunit;                          // per tile of every instance, six int4: {first bus, buses,
+  const int4 *tunit;                          // per tile of every instance, eight int4: {first bus, buses,
                                               //   first pair, pairs}, {J position of the first P row and
                                               //   length of the tile's P rows, the same for Q}, {first P
                                               //   row, P rows, first Q row, Q rows}, {instance, grid, first
-                                              //   bus of the grid, buses of the grid}, then {x offset,
-                                              //   F offset}, {J offset, record base} as int64
+                                              //   bus of the grid, buses of the grid}, {x offset, F offset}
+                                              //   and {J offset, record base} as int64, {first external
+                                              //   neighbour in tile_ext, external neighbours, 0, 0}, padding
+  const int32_t *tile_ext;                    // per tile: the buses outside it that its pairs reach, ascending
   int64_t n_tile_units;                       // tiles over all instances
   int32_t tile_stage;                         // doubles of J a tile stages (its P and Q rows, two pads)
 
@@ -222,7 +226,7 @@ struct Ctx {
   View v{};
   int device = 0;                  // the device current at pf_build: every call runs on it
   int num_sms = kNumSMsDefault;
-  pf_tuning tuning{64, 0, 0};
+  pf_tuning tuning{64, 0, 0, 0};
   int max_degree = 0, max_group = 0;
   int64_t n_x = 0, n_f = 0, nnz = 0, n_branch_inst = 0;
 
@@ -255,6 +259,7 @@ struct Ctx {
   struct TileSet {
     int4 *pair_idx = nullptr;
     int4 *tunit = nullptr;
+    int32_t *ext = nullptr;
     int64_t n_units = 0;
     int32_t stage = 0;
     std::vector<int64_t> tile_off;

@@ -8,8 +8,10 @@
 // Inputs, outputs and the built context come from the caller; the only
 // scratch the evaluation needs -- the 32-byte per-bus record of every bus of
 // every instance (the unit phasor (cos theta, sin theta) and V in fixed point,
-// and V) -- lives in g_static_phasor below, a fixed device array that
-// exists on every GPU that loads this library until the process exits.
+// and 1/V) -- lives in g_static_phasor below, a fixed device array that
+// exists on every GPU that loads this library until the process exits.  (A
+// context tuned to form the records inside the fused kernel, fuse_phasor = 1,
+// uses the array only for buses with more than 32 neighbours.)
 #include <mutex>
 #include <string>
 #include <vector>

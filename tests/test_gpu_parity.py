@@ -120,16 +120,17 @@ def test_deterministic_across_runs_and_tunings(P, name):
         F1, v1 = ctx.residual_jacobian(x)
         assert torch.equal(F0, F1) and torch.equal(v0, v1)
     nan = float("nan")
-    for split in (0, 1, 2):
-        for tile in (32, 64, 96, 128):
-            for ctas in (0, 1, 3, 16):
-                ctx.set_tuning(tile, ctas, split)
-                for _ in range(2):                     # a persistent grid's counters are reused
-                    F1, v1 = ctx.residual_jacobian(x, ctx.empty_f().fill_(nan), ctx.empty_vals().fill_(nan))
-                    assert torch.equal(F0, F1) and torch.equal(v0, v1), (tile, ctas, split)
-                F2 = ctx.residual(x, ctx.empty_f().fill_(nan))   # F alone takes the same sums
-                assert torch.equal(F0, F2), (tile, ctas, split)
-                ctx.check_device()
+    for fuse in (0, 1):
+        for split in (0, 1, 2):
+            for tile in (32, 64, 96, 128):
+                for ctas in (0, 1, 3, 16):
+                    ctx.set_tuning(tile, ctas, split, fuse)
+                    for _ in range(2):                     # a persistent grid's counters are reused
+                        F1, v1 = ctx.residual_jacobian(x, ctx.empty_f().fill_(nan), ctx.empty_vals().fill_(nan))
+                        assert torch.equal(F0, F1) and torch.equal(v0, v1), (tile, ctas, split, fuse)
+                    F2 = ctx.residual(x, ctx.empty_f().fill_(nan))   # F alone takes the same sums
+                    assert torch.equal(F0, F2), (tile, ctas, split, fuse)
+                    ctx.check_device()
 
 
 def test_autotune_keeps_results(P):
@@ -293,8 +294,9 @@ def test_out_of_range_terms_match_oracle(P, mode):
 
 @pytest.mark.parametrize("mode", MODES)
 def test_split_rounds_bit_identical_under_masks(P, mode):
-    """Two lanes per bus (split rounds) give the one-lane results bit for bit: a batch with
-    outage instances, a per-call status mask, and (extended) generators held at limits."""
+    """Smaller tiles (split rounds) and the records formed in the fused kernel give the
+    default results bit for bit: a batch with outage instances, a per-call status mask,
+    and (extended) generators held at limits."""
     grids = [GRIDS["grid200"], GRIDS["grid30"], GRIDS["edge300"]]
     inst = [(0, -1), (0, 7), (1, 3), (2, -1), (2, 11), (1, -1)]
     ctx = P.Context(grids, MNAME[mode], instances=inst)
@@ -307,11 +309,12 @@ def test_split_rounds_bit_identical_under_masks(P, mode):
         kw["gen_mode"] = torch.from_numpy(rng.integers(0, 3, ctx.dims.n_gen_inst).astype(np.uint8)).cuda()
         kw["gen_qlim"] = torch.from_numpy(rng.uniform(-0.5, 0.8, ctx.dims.n_gen_inst)).cuda()
     outs = []
-    for split in (0, 1, 2):
-        for tile in (32, 128):
-            ctx.set_tuning(tile, 0, split)
-            outs.append(ctx.eval(x, ctx.empty_f(), ctx.empty_vals(), **kw))
-            outs.append(ctx.residual_jacobian(x))
+    for fuse in (0, 1):
+        for split in (0, 1, 2):
+            for tile in (32, 128):
+                ctx.set_tuning(tile, 0, split, fuse)
+                outs.append(ctx.eval(x, ctx.empty_f(), ctx.empty_vals(), **kw))
+                outs.append(ctx.residual_jacobian(x))
     for k in range(2, len(outs), 2):
         assert torch.equal(outs[0][0], outs[k][0]) and torch.equal(outs[0][1], outs[k][1]), k
         assert torch.equal(outs[1][0], outs[k + 1][0]) and torch.equal(outs[1][1], outs[k + 1][1]), k
@@ -358,8 +361,9 @@ def test_persistent_schedule_bit_identical(P, mode):
     ref = run()
     assert torch.equal(ref[5][0], ref[0][0]) and torch.equal(ref[5][1], ref[0][1])   # stages == one call
     assert torch.equal(ref[4][0], ref[1][0]) and torch.equal(ref[4][1], ref[1][1])
-    for tile, cps, split in ((64, 16, 0), (64, 20, 0), (32, 1, 0), (128, 16, 1), (96, 3, 1)):
-        ctx.set_tuning(tile, cps, split)
+    for tile, cps, split, fuse in ((64, 16, 0, 0), (64, 20, 0, 0), (32, 1, 0, 0), (128, 16, 1, 0), (96, 3, 1, 0),
+                                   (64, 0, 0, 1), (32, 4, 2, 1)):
+        ctx.set_tuning(tile, cps, split, fuse)
         for _ in range(2):
             got = run()
             for k in (0, 1, 4, 5):
@@ -402,7 +406,7 @@ def test_autotune_cache(P, tmp_path):
     t1 = c1.autotune(x, F1, V1, cache=str(path))
     assert t1["from_cache"] is False
     lines = path.read_text().splitlines()
-    assert len(lines) == 1 and lines[0].startswith("pf-tuning-v1 ")
+    assert len(lines) == 1 and lines[0].startswith("pf-tuning-v2 ") and len(lines[0].split()) == 6
     c2, F2, V2 = ctx_of([(0, -1), (0, 3)])
     t2 = c2.autotune(x, F2, V2, cache=str(path))
     assert t2["from_cache"] is True and {k: t2[k] for k in t1 if k != "from_cache"} == \
@@ -416,10 +420,12 @@ def test_autotune_cache(P, tmp_path):
     assert c3.autotune(x, F3, V3, cache=str(path))["from_cache"] is False
     assert len(path.read_text().splitlines()) == 2
     key = lines[0].split()[1]
-    path.write_text(f"garbage line\npf-tuning-v1 {key} 48 0 0\npf-tuning-v1 {key} 64 99 0\n")
+    # an out-of-range tile, CTA count and phasor form, and a line of the older format
+    path.write_text(f"garbage line\npf-tuning-v2 {key} 48 0 0 0\npf-tuning-v2 {key} 64 99 0 0\n"
+                    f"pf-tuning-v2 {key} 64 0 0 2\npf-tuning-v1 {key} 64 0 0\n")
     c4, F4, V4 = ctx_of([(0, -1), (0, 3)])
     assert c4.autotune(x, F4, V4, cache=str(path))["from_cache"] is False   # nothing valid: timed again
-    assert len(path.read_text().splitlines()) == 4
+    assert len(path.read_text().splitlines()) == 6
     c5, F5, V5 = ctx_of([(0, -1), (0, 3)])
     assert c5.autotune(x, F5, V5, cache=str(path))["from_cache"] is True
     for c in (c1, c2, c3, c4, c5):
