@@ -231,23 +231,23 @@ def fp64_ops(d, pattern):
     """FP64-pipe operations of one instance's F and J evaluation (an FMA, a
     multiply, an add or a conversion each count one).  k_tile forms the pair
     terms in fixed point on the integer pipe; the FP64 pipe converts each
-    V-column off-diagonal value to double (one conversion), and each bus takes
+    off-diagonal value of a pair to double (one conversion), and each bus takes
     V_o from its fixed-point form and the two exact bus sums to double (3),
     V_o^2, V_o^2 A^ - S_X, V_o^2 C^ + S_Y and the two F rows (5), plus two
     FMAs and two multiplies for the diagonal V values where the bus has a V
     column (4).  k_phasor_fx forms 1/V_o (3 FMAs after the hardware's
     reciprocal estimate) for every bus.  Returns (k_tile, k_phasor_fx)."""
     n = d.n_bus
-    rp, ci = pattern
-    if d.formulation == 0:                   # reduced: theta columns of the n - 1 non-slack buses first
-        n_v = int(np.count_nonzero(ci >= n - 1))
-        n_vbus = d.n_f - (n - 1)             # PQ buses (their P and Q rows have a V_o column)
-    else:                                    # extended: g_p, g_q rows and V columns of every bus
-        row = np.repeat(np.arange(rp.shape[0] - 1), np.diff(rp))
-        n_v = int(np.count_nonzero((row < 2 * n) & (ci >= n) & (ci < 2 * n)))
+    nnz = int(pattern[0][-1])
+    if d.formulation == 0:                   # reduced: P rows of the n - 1 non-slack buses, Q rows of the PQ buses
+        n_pq = d.n_f - (n - 1)
+        n_diag = (n - 1) + 3 * n_pq          # (P, theta_o) of each; (P, V_o), (Q, theta_o), (Q, V_o) of a PQ bus
+        n_vbus = n_pq
+    else:                                    # extended: four diagonal entries per bus, and the generator rows
+        n_gen = d.n_x - 2 * n - 1
+        n_diag = 4 * n + 1 + n_gen + 2 * n_gen + 1   # P_s, Q_g columns, g_V rows, g_theta
         n_vbus = n
-    n_voff = n_v - 2 * n_vbus
-    return n_voff + 8 * n + 4 * n_vbus, 3 * n
+    return (nnz - n_diag) + 8 * n + 4 * n_vbus, 3 * n
 
 
 def _oracle_share(kind, idx, seconds, barrier, queue):
@@ -587,8 +587,11 @@ def main():
                    "l2": l2_note(N_STATES * 8 * (d1.n_x + d1.n_f + d1.nnz)),
                    "tuning": tuning, "timed_region_wall_s": wall, "parallelism": f"replicas x{world}"},
         "single_instance": {"value": single_rate, "unit": "evals/s", "tuning": one_tuning,
-                            "how": f"one evaluation per launch pair (k_phasor_fx, k_tile), {N_STATES} states with their "
-                                   "own buffers evaluated one after the other from one CUDA graph"},
+                            "how": ("one launch per evaluation (k_tile forming its voltage records)"
+                                    if one_tuning.get("fuse_phasor") else
+                                    "one launch pair per evaluation (k_phasor_fx, k_tile)")
+                                   + f", {N_STATES} states with their own buffers evaluated one after the other "
+                                     "from one CUDA graph"},
         "batched_over_single": value / world / single_rate,
         "e2e": {"value": e2e_value, "unit": "evals/s", "h2d_bytes_per_step": 8 * d.n_x,
                 "d2h_bytes_per_step": 8 * (d.n_f + d.nnz), "steps": E},

@@ -1600,7 +1600,7 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
     int64_t *ptr64;
     PF_TRY(tmp.alloc(&keys, np));
     PF_TRY(tmp.alloc(&vals, np));
-    PF_TRY(tmp.alloc(&pos_of, NI));
+    PF_TRY(dev_alloc(c, &pos_of, NI));
     PF_TRY(tmp.alloc(&deg, N));
     PF_TRY(tmp.alloc(&ptr64, N + 1));
     PF_TRY(tmp.alloc(&stats, 4));
@@ -1625,7 +1625,7 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
       k_mirror_groups<<<nblk(NI), TB, 0, s>>>(v, pos_of, mirror, grp, stats);
       PF_CUDA_TRY(cudaGetLastError());
     }
-    v.inc_mirror = mirror; v.inc_grp = grp;
+    v.inc_mirror = mirror; v.inc_grp = grp; v.inc_of_code = pos_of;
     {
       int32_t *npair;
       PF_TRY(dev_alloc(c, &npair, N));

@@ -25,8 +25,9 @@
 // unit phasors (cos t, sin t), V and the merged coefficients (G, B) of a pair
 // of connected buses (parallel branches merged) as 30-bit limbs, products from
 // 32 x 32 -> 64-bit multiplies, the bus sums S_X, S_Y exact in 128 bits; each
-// J value is rounded once to double (two per pair by the FP64 pipe's
-// conversion, two on the integer pipe).  The per-bus rows (F, the diagonal
+// J value and each sum is rounded once to double, to nearest even, by the
+// FP64 pipe's conversion (a sum beyond 64 bits by the integer routine
+// acc_value, ties away from zero).  The per-bus rows (F, the diagonal
 // values) stay in FP64: 8 operations per bus.  A bus whose inputs fall outside
 // the fixed-point ranges is evaluated in FP64 from x (the form above).
 //
@@ -301,7 +302,7 @@ __global__ void __launch_bounds__(256) k_phasor_fx(View v, const double *__restr
 // sum stays below 2^63.  With the 2^-57 error of the phasor routine the
 // absolute error of T is below 2^(c - 55) (about 3e-17 max(|G|, |B|)), of X,
 // Y below 2^(c - 54); X and Y are summed exactly in 128 bits and every value is
-// rounded once to double (to nearest, ties away from zero).
+// rounded once to double (to nearest).
 // ---------------------------------------------------------------------------
 
 // a b, exact, from 32-bit factors (one 32 x 32 -> 64 multiply).
@@ -335,7 +336,7 @@ __device__ __forceinline__ double fix_to_double(long long z, int s) {
 // Exact sums on the integer pipe: a 128-bit two's-complement accumulator of
 // fixed-point terms.  The sum does not depend on the order of the terms, so
 // every schedule and tuning gives the same bits; it is rounded to a double
-// once (to nearest, ties away from zero).
+// once (to nearest: even within 64 bits, else ties away from zero).
 struct Acc128 {
   unsigned long long lo;
   long long hi;
@@ -538,8 +539,9 @@ __device__ __forceinline__ double2 masked_hat(const View &v, const EvalArgs &a, 
 
 // z 2^-s as a double by the hardware conversion on the FP64 pipe (rounded to
 // nearest even), the scale applied to the exponent; 2^-s |z| must be a normal
-// double.  The FP64 pipe is otherwise idle in the pair loop, so half of the
-// pair's conversions go there and half to the integer pipe (fix_to_double).
+// double.  The pair loop converts its four values this way: one FP64-pipe
+// instruction each, where the integer routine (fix_to_double) takes some
+// twenty instructions of the issue slots the kernel is bound by.
 __device__ __forceinline__ double fix_to_double_cvt(long long z, int s) {
   const double d = __ll2double_rn(z);
   return __hiloint2double(z == 0 ? 0 : __double2hiint(d) - (s << 20), __double2loint(d));
@@ -617,14 +619,29 @@ __device__ __forceinline__ void finalize_bus(const View &v, const EvalArgs &a, i
   }
 }
 
+// Without a per-call status mask the only branch out of service is the
+// instance's outage, whose two ends sit at incidence positions oute (-1: no
+// outage): a group of parallel ends [e, e + len) holding neither keeps its
+// built coefficients, so only the groups that hold it are summed again.
+__device__ __forceinline__ bool outside_group(const EvalArgs &a, int32_t e, int32_t len, int2 oute) {
+  return a.status == nullptr && (unsigned)(oute.x - e) >= (unsigned)len && (unsigned)(oute.y - e) >= (unsigned)len;
+}
+
+// The incidence positions of the two ends of branch `outage` (-1 none).
+__device__ __forceinline__ int2 outage_ends(const View &v, int32_t outage) {
+  return outage >= 0 ? make_int2(__ldg(v.inc_of_code + 2 * outage), __ldg(v.inc_of_code + 2 * outage + 1))
+                     : make_int2(-1, -1);
+}
+
 // The merged coefficients (G, B) of a slot (len: its group length, cw: the
 // code of a single branch or the first end of a group) as the mask leaves
 // them: the built value, zero for a single branch out of service, or the
 // re-summed branches in service of a group.
 template <bool MASKED>
 __device__ __forceinline__ double2 slot_gb(const View &v, const EvalArgs &a, int32_t len, int32_t cw, double2 G,
-                                           int32_t outage, int64_t st_base, bool &any_out) {
+                                           int32_t outage, int64_t st_base, bool &any_out, int2 oute) {
   if (!MASKED) return G;
+  if (len > 1 && outside_group(a, cw, len, oute)) return G;
   if (len == 1) {
     const int32_t l = cw >> 1;
     if (l == outage || (a.status != nullptr && a.status[st_base + l] == 0)) {
@@ -642,8 +659,9 @@ __device__ __forceinline__ double2 slot_gb(const View &v, const EvalArgs &a, int
 // converted as the build converts it.
 template <bool MASKED>
 __device__ __forceinline__ int4 slot_gbx(const View &v, const EvalArgs &a, int32_t len, int32_t cw, int4 GX,
-                                         int32_t outage, int64_t st_base, bool &any_out) {
+                                         int32_t outage, int64_t st_base, bool &any_out, int2 oute) {
   if (!MASKED) return GX;
+  if (len > 1 && outside_group(a, cw, len, oute)) return GX;
   if (len == 1) {
     const int32_t l = cw >> 1;
     if (l == outage || (a.status != nullptr && a.status[st_base + l] == 0)) {
@@ -723,24 +741,6 @@ __device__ __forceinline__ PairT pair_terms(const OwnV &w, const Rec &rk, int4 g
   return t;
 }
 
-// A pair's four J values (in-row offsets packed in offs: theta_k low, V_k
-// high, -1 absent) to the sink.
-template <bool WJ>
-__device__ __forceinline__ void put_pair_values(const RowSink &rs, int32_t offs, const PairT &t, int sT) {
-  if (WJ) {
-    const int32_t ot = (short)(offs & 0xffff), ov = offs >> 16;
-    if (ot >= 0) {
-      rs.p(ot, fix_to_double(t.my, sT));            // dP_o / dtheta_k = -Y
-      rs.q(ot, fix_to_double(t.xx, sT));            // dQ_o / dtheta_k = X
-    }
-    if (ov >= 0) {
-      rs.p(ov, neg(fix_to_double_cvt(t.tr, sT)));   // dP_o / dV_k = -X / V_k
-      rs.q(ov, fix_to_double_cvt(t.ti, sT));        // dQ_o / dV_k = -Y / V_k
-    }
-  }
-}
-
-
 // A unit's instance: its grid and where its state, outputs and records live.
 struct UnitCtx {
   int inst, g;
@@ -784,7 +784,8 @@ __device__ __forceinline__ void finish_bus(const View &v, const EvalArgs &a, con
       const int4 m = __ldg(wk.idx + q);
       const int32_t len = (short)(m.z & 0xffff);
       if (len < 0) continue;
-      const double2 Gi = slot_gb<MASKED>(v, a, len, m.w, __ldg(wk.gb + q), uc.outage, uc.st_base, unused);
+      const double2 Gi = slot_gb<MASKED>(v, a, len, m.w, __ldg(wk.gb + q), uc.outage, uc.st_base, unused,
+                                         MASKED ? outage_ends(v, uc.outage) : make_int2(-1, -1));
       const VoltD Vk = volt_fp64(uc.srec ? uc.srec[2 * ((m.z >> 24) & 0xff)] : uc.rec4[2 * m.x], uc.xi, uc.nb,
                                  m.x - uc.gb0);
       const EndTerms tm = end_terms(Gi, Vo.E, Vk.E);
@@ -824,12 +825,12 @@ __device__ __forceinline__ void copy_out(double *dst, const double *src, int32_t
 }
 
 // Shared memory of a k_tile warp (byte offsets, 16-byte aligned): E_o limbs
-// of each bus (32 int4), staging index of each bus's P and Q row (32 int2,
+// of each bus ({e, f} and {-f, -}: 32 x 2 int4), staging index of each bus's P and Q row (32 int2,
 // -1 none), per-bus flags (32 int: 1 FP64 form, 2 an end out of service), X
 // and -Y of each pair (kTilePairs longlong2), the tile's F values (P rows,
 // then Q rows: 64 doubles), then the staged J rows (v.tile_stage doubles).
 constexpr int kTsOwn = 0;
-constexpr int kTsBase = kTsOwn + 32 * 16;
+constexpr int kTsBase = kTsOwn + 32 * 32;
 constexpr int kTsFlag = kTsBase + 32 * 8;
 constexpr int kTsXY = kTsFlag + 32 * 4;
 constexpr int kTsF = kTsXY + kTilePairs * 16;
@@ -841,11 +842,11 @@ constexpr int kTileRecBytes = (kTileBuses + kTilePairs) * 32;
 static_assert(kTileSmemFixed % 16 == 0, "shared-memory layout of k_tile");
 
 // One-warp CTAs resident per SM (the register budget of k_tile): 28 for the
-// F + J evaluation (72 registers), fewer where a mask or a persistent
-// schedule needs more state.
+// F + J evaluation (72 registers), 24 under a mask, 20 for a persistent
+// schedule.
 template <int ITEMS, bool WF, bool WJ, bool MASKED, bool DYN, bool PHX>
 struct TileMinCtas {
-  static constexpr int value = (MASKED || DYN) ? 20 : 28;
+  static constexpr int value = DYN ? 20 : MASKED ? 24 : 28;
 };
 
 // One warp per tile of one instance: up to 32 consecutive buses of a grid and
@@ -908,6 +909,7 @@ __global__ void __launch_bounds__(32, (TileMinCtas<ITEMS, WF, WJ, MASKED, DYN, P
     const int4 *__restrict__ rec4 = reinterpret_cast<const int4 *>(v.phasor) + 2 * up1.y;
     const int32_t outage = MASKED ? v.inst_outage[inst] : -1;
     const int64_t st_base = MASKED ? v.inst_br_off[inst] - v.grid_br_off[g] : 0;
+    const int2 oute = MASKED ? outage_ends(v, outage) : make_int2(-1, -1);
     // staged J: the P rows at s_j[padP ..), the Q rows at s_j[offQ + padQ ..),
     // each at the offset modulo 16 bytes of its destination
     const int32_t padP = WJ ? (int32_t)((reinterpret_cast<uintptr_t>(vi + ts.x) >> 3) & 1) : 0;
@@ -951,7 +953,8 @@ __global__ void __launch_bounds__(32, (TileMinCtas<ITEMS, WF, WJ, MASKED, DYN, P
         if (!PHX) cudaGridDependencySynchronize();
         if (owner) {
           w = own_voltage(PHX ? Rec{s_rec[2 * lane], s_rec[2 * lane + 1]} : load_rec(rec4 + 2 * o));
-          s_own[lane] = make_int4(w.eo.x, w.eo.y, w.fo.x, w.fo.y);
+          s_own[2 * lane] = make_int4(w.eo.x, w.eo.y, w.fo.x, w.fo.y);
+          s_own[2 * lane + 1] = make_int4(w.nfo.x, w.nfo.y, 0, 0);
           s_base[lane] = make_int2((WJ && bm.z >= 0) ? padP + bm.z - ts.x : -1,
                                    (WJ && bm.w >= 0) ? offQ + padQ + bm.w - ts.z : -1);
           s_flag[lane] = 0;
@@ -965,21 +968,29 @@ __global__ void __launch_bounds__(32, (TileMinCtas<ITEMS, WF, WJ, MASKED, DYN, P
         if (idx[it].z < 0) continue;
         const int32_t len = idx[it].z & 0xffff, ol = (idx[it].z >> 16) & 0xff;
         bool anyo = false;
-        const int4 gx = slot_gbx<MASKED>(v, a, len, idx[it].w, GX[it], outage, st_base, anyo);
-        const int4 e = s_own[ol];
+        const int4 gx = slot_gbx<MASKED>(v, a, len, idx[it].w, GX[it], outage, st_base, anyo, oute);
+        const int4 e = s_own[2 * ol], e2 = s_own[2 * ol + 1];
         OwnV wo;
         wo.eo = make_int2(e.x, e.y);
         wo.fo = make_int2(e.z, e.w);
-        wo.nfo = limbs(-(((long long)e.z << 30) + e.w));
+        wo.nfo = make_int2(e2.x, e2.y);
         const int loc = (idx[it].z >> 24) & 0xff;
         const PairT t = pair_terms(wo, PHX ? Rec{s_rec[2 * loc], s_rec[2 * loc + 1]} : load_rec(rec4 + 2 * idx[it].x),
                                    gx);
         s_xy[p] = make_longlong2(t.xx, t.my);
         if (!t.ok || anyo) atomicOr(s_flag + ol, (t.ok ? 0 : 1) | (anyo ? 2 : 0));
         if (WJ) {
+          // the pair's four values into the staged rows (staging indices, -1: no such row)
           const int2 bs = s_base[ol];
-          const RowSink rs{bs.x >= 0 ? s_j + bs.x : nullptr, bs.y >= 0 ? s_j + bs.y : nullptr};
-          put_pair_values<WJ>(rs, idx[it].y, t, sT);
+          const int32_t ot = (short)(idx[it].y & 0xffff), ov = idx[it].y >> 16;
+          if (ot >= 0) {
+            if (bs.x >= 0) s_j[bs.x + ot] = fix_to_double_cvt(t.my, sT);       // dP_o / dtheta_k = -Y
+            if (bs.y >= 0) s_j[bs.y + ot] = fix_to_double_cvt(t.xx, sT);       // dQ_o / dtheta_k = X
+          }
+          if (ov >= 0) {
+            if (bs.x >= 0) s_j[bs.x + ov] = neg(fix_to_double_cvt(t.tr, sT));  // dP_o / dV_k = -X / V_k
+            if (bs.y >= 0) s_j[bs.y + ov] = fix_to_double_cvt(t.ti, sT);       // dQ_o / dV_k = -Y / V_k
+          }
         }
       }
     }

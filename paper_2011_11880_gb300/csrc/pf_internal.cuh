@@ -143,6 +143,7 @@ struct View {
   const int2 *inc_rt;       // in-row offsets of (theta_k, V_k) columns, -1 absent
   const int32_t *inc_grp;   // at a group head: parallel ends to the same bus; else 0
   const int32_t *inc_mirror;// position of the other end of the same branch
+  const int32_t *inc_of_code;// [2 n_branch] position of branch end `code` (= 2 branch + end)
   const int4 *inc_meta;     // {own, other, parallel-group length at a head else 0, code}
   const int4 *inc_pos;      // local CSR positions of this end's (P,theta_k), (P,V_k), (Q,theta_k), (Q,V_k); -1 absent
 
