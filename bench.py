@@ -472,7 +472,8 @@ def main():
         ctx.residual_jacobian(X, F, V)
         torch.cuda.synchronize()
         g_eval = capture(lambda: ctx.residual_jacobian(X, F, V))
-        g_ph = capture(lambda: ctx.eval_stage(1, X, F, V))
+        # (with fuse_phasor the fused stage forms its records: no phasor stage to replay)
+        g_ph = None if tuning.get("fuse_phasor") else capture(lambda: ctx.eval_stage(1, X, F, V))
         g_fu = capture(lambda: ctx.eval_stage(2, X, F, V))
     torch.cuda.synchronize()
 
@@ -510,7 +511,8 @@ def main():
     # ---- the dominant kernel alone: the batched k_tile launch between events ----
     KF = min(K, 200)
     with torch.cuda.stream(stream):
-        g_ph.replay()
+        if g_ph is not None:
+            g_ph.replay()
         ev_a.record(stream)
         for k in range(KF):
             g_fu.replay()
@@ -689,12 +691,13 @@ def measure_contingency(torch, stream, K, W, cpu_seconds=0.0):
     with torch.cuda.stream(stream):
         tuning = ctx.autotune(X, F, V, stream=stream)
     g = _graph(torch, stream, lambda: ctx.residual_jacobian(X, F, V, stream=stream))
-    gp = _graph(torch, stream, lambda: ctx.eval_stage(1, X, F, V, stream=stream))
+    gp = None if tuning.get("fuse_phasor") else _graph(torch, stream, lambda: ctx.eval_stage(1, X, F, V, stream=stream))
     gf = _graph(torch, stream, lambda: ctx.eval_stage(2, X, F, V, stream=stream))
     for _ in range(W):
         g.replay()
     t, clocks = _clocked(torch, stream, g, K)
-    gp.replay()
+    if gp is not None:
+        gp.replay()
     kf = _time_graph(torch, stream, gf, K)
     n = len(insts)
     bytes_alg = 0
@@ -846,12 +849,13 @@ def measure_extended(torch, stream, K, W, cpu_seconds=0.0):
     with torch.cuda.stream(stream):
         tuning = ctx.autotune(X, F, V, stream=stream)
     g = _graph(torch, stream, lambda: ctx.residual_jacobian(X, F, V, stream=stream))
-    gp = _graph(torch, stream, lambda: ctx.eval_stage(1, X, F, V, stream=stream))
+    gp = None if tuning.get("fuse_phasor") else _graph(torch, stream, lambda: ctx.eval_stage(1, X, F, V, stream=stream))
     gf = _graph(torch, stream, lambda: ctx.eval_stage(2, X, F, V, stream=stream))
     for _ in range(W):
         g.replay()
     t, clocks = _clocked(torch, stream, g, K)
-    gp.replay()
+    if gp is not None:
+        gp.replay()
     kf = _time_graph(torch, stream, gf, K)
     bytes_alg = S * (algorithmic_bytes(d1, sys_.n_pv, sys_.load_bus.shape[0], sys_.sh_bus.shape[0])
                      + 8 * (d1.n_x - 2 * d1.n_bus))          # the Q_g and P_s entries of x

@@ -266,16 +266,33 @@ __device__ __forceinline__ void make_record(double th, double vm, const longlong
 
 // The records of every instance-bus, one thread each (the F / J kernel then
 // gathers its buses' and their neighbours' records; 1/V is formed here, off
-// that kernel's dependence chain).
-__global__ void __launch_bounds__(256) k_phasor_fx(View v, const double *__restrict__ x) {
+// that kernel's dependence chain).  GRID1: every instance is of the one grid
+// of the context, so instance blockIdx.y + i0 holds buses blockIdx.x * 256 +
+// threadIdx.x at the same offsets (no instance lookup); otherwise a 1-D grid
+// over the instance-buses and a lookup of each one's instance.
+template <bool GRID1>
+__global__ void __launch_bounds__(256) k_phasor_fx(View v, const double *__restrict__ x, int i0) {
   cudaTriggerProgrammaticLaunchCompletion();
-  const int64_t q = v.bus_inst_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < v.n_bus_inst) {
-    const int inst = bus_instance(v, q);
-    const int64_t lb = q - v.inst_bus_off[inst];
-    const double *xi = x + v.inst_x_off[inst];
+  int inst;
+  int64_t q, lb;
+  int32_t nb;
+  if (GRID1) {
+    nb = v.grid_nbus[0];
+    inst = i0 + (int)blockIdx.y;
+    lb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (lb >= nb) return;
+    q = (int64_t)inst * nb + lb;
+  } else {
+    q = v.bus_inst_begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= v.n_bus_inst) return;
+    inst = bus_instance(v, q);
+    lb = q - v.inst_bus_off[inst];
+    nb = v.grid_nbus[v.inst_grid[inst]];
+  }
+  {
+    const double *xi = x + (GRID1 ? (int64_t)inst * v.grid1_nx : v.inst_x_off[inst]);
     const double th = __ldg(xi + lb);
-    const double vm = __ldg(xi + v.grid_nbus[v.inst_grid[inst]] + lb);
+    const double vm = __ldg(xi + nb + lb);
     int4 r0, r1;
     make_record(th, vm, v.sincos_fix, r0, r1);
     int4 *rec = reinterpret_cast<int4 *>(v.phasor);
@@ -843,10 +860,11 @@ static_assert(kTileSmemFixed % 16 == 0, "shared-memory layout of k_tile");
 
 // One-warp CTAs resident per SM (the register budget of k_tile): 28 for the
 // F + J evaluation (72 registers), 24 under a mask, 20 for a persistent
-// schedule.
+// schedule, 16 where the kernel forms its records (the form for one instance,
+// which fills only about 14 warps per SM).
 template <int ITEMS, bool WF, bool WJ, bool MASKED, bool DYN, bool PHX>
 struct TileMinCtas {
-  static constexpr int value = DYN ? 20 : MASKED ? 24 : 28;
+  static constexpr int value = DYN ? 20 : PHX ? 16 : MASKED ? 24 : 28;
 };
 
 // One warp per tile of one instance: up to 32 consecutive buses of a grid and
@@ -874,6 +892,9 @@ struct TileMinCtas {
 template <int ITEMS, bool WF, bool WJ, bool MASKED, bool DYN, bool PHX>
 __global__ void __launch_bounds__(32, (TileMinCtas<ITEMS, WF, WJ, MASKED, DYN, PHX>::value))
     k_tile(View v, EvalArgs a) {
+  // Let a dependent launch start (the next evaluation's k_tile with
+  // fuse_phasor: it waits for this grid before it reads x or writes).
+  cudaTriggerProgrammaticLaunchCompletion();
   extern __shared__ __align__(16) unsigned char s_raw[];
   int4 *const s_own = reinterpret_cast<int4 *>(s_raw + kTsOwn);
   int2 *const s_base = reinterpret_cast<int2 *>(s_raw + kTsBase);
@@ -922,16 +943,39 @@ __global__ void __launch_bounds__(32, (TileMinCtas<ITEMS, WF, WJ, MASKED, DYN, P
     if (owner) bm = __ldg(v.bus_meta + o);
     OwnV w{make_int2(0, 0), make_int2(0, 0), make_int2(0, 0), 0.0, 1.0, true};
     if (PHX) {
-      // the records of the tile's buses and of its external neighbours
+      // the records of the tile's buses and of its external neighbours, records
+      // lane, lane + 32, ...: every bus and every value of x first, then the
+      // arithmetic
+      constexpr int kRecPerLane = (kTileBuses + kTilePairs) / 32;
       const int4 te = __ldg(ur + 6);             // {first external neighbour, external neighbours}
-      for (int32_t r = lane; r < td.y + te.y; r += 32) {
-        const int32_t b = r < td.y ? td.x + r : __ldg(v.tile_ext + te.x + (r - td.y));
-        const int64_t lb = b - ti.z;
-        int4 r0, r1;
-        make_record(__ldg(xi + lb), __ldg(xi + ti.w + lb), v.sincos_fix, r0, r1);
-        const int32_t slot = r < td.y ? r : kTileBuses + (r - td.y);
-        s_rec[2 * slot] = r0;
-        s_rec[2 * slot + 1] = r1;
+      const int32_t n_rec = td.y + te.y;
+      int32_t bl[kRecPerLane];
+#pragma unroll
+      for (int i = 0; i < kRecPerLane; ++i) {
+        const int32_t r = lane + 32 * i;
+        bl[i] = r < td.y ? td.x + r : (r < n_rec ? __ldg(v.tile_ext + te.x + (r - td.y)) : -1);
+      }
+      // x may come from the stream's previous kernel (a programmatic dependent launch)
+      cudaGridDependencySynchronize();
+      double th[kRecPerLane], vm[kRecPerLane];
+#pragma unroll
+      for (int i = 0; i < kRecPerLane; ++i) {
+        if (bl[i] >= 0) {
+          const int64_t lb = bl[i] - ti.z;
+          th[i] = __ldg(xi + lb);
+          vm[i] = __ldg(xi + ti.w + lb);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < kRecPerLane; ++i) {
+        if (bl[i] >= 0) {
+          int4 r0, r1;
+          make_record(th[i], vm[i], v.sincos_fix, r0, r1);
+          const int32_t r = lane + 32 * i;
+          const int32_t slot = r < td.y ? r : kTileBuses + (r - td.y);
+          s_rec[2 * slot] = r0;
+          s_rec[2 * slot + 1] = r1;
+        }
       }
       __syncwarp();
     }
@@ -1141,9 +1185,10 @@ __global__ void __launch_bounds__(32) k_fused_large(View v, EvalArgs a) {
 // previous kernel (k_phasor_fx), so its CTAs start before that grid ends and
 // load the static maps and the branch coefficients ahead of their wait for
 // it; set only where no kernel that wrote those coefficients comes directly
-// before it.  With t.fuse_phasor k_tile forms the records itself and follows
-// the stream's previous work in plain order (a persistent grid then takes
-// its units by a static stride).
+// before it.  With t.fuse_phasor k_tile forms the records itself: it waits for
+// the stream's previous kernel before it reads x, so that an evaluation's
+// k_tile starts while the previous one's last tiles run (a persistent grid
+// then takes its units by a static stride).
 template <int ITEMS, bool WF, bool WJ, bool MASKED>
 int launch_fused_t(const View &v, int num_sms, const pf_tuning &t, const EvalArgs &a, bool pdl, cudaStream_t s) {
   if (v.n_tile_units > 0) {
@@ -1160,7 +1205,7 @@ int launch_fused_t(const View &v, int num_sms, const pf_tuning &t, const EvalArg
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = (pdl && !phx) ? 1 : 0;
+    cfg.numAttrs = pdl ? 1 : 0;
     if (phx) PF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tile<ITEMS, WF, WJ, MASKED, false, true>, v, ak));
     else if (ak.work) PF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tile<ITEMS, WF, WJ, MASKED, true, false>, v, ak));
     else PF_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tile<ITEMS, WF, WJ, MASKED, false, false>, v, ak));
@@ -1241,8 +1286,19 @@ int launch_phasor(const View &v, int num_sms, const double *x, cudaStream_t s, b
   const int tb = 256;
   const int64_t blocks = (v.n_bus_inst - v.bus_inst_begin + tb - 1) / tb;
   if (blocks <= 0) return PF_OK;
-  if (fixed) k_phasor_fx<<<(unsigned)blocks, tb, 0, s>>>(v, x);
-  else k_phasor<<<(unsigned)blocks, tb, 0, s>>>(v, x);
+  if (fixed && v.n_grids == 1) {
+    // one grid: instances [i0, i1) of the range, a 2-D launch without instance lookup
+    const int64_t nb = v.n_bus;
+    const int64_t i0 = v.bus_inst_begin / nb, i1 = v.n_bus_inst / nb;
+    for (int64_t c0 = i0; c0 < i1; c0 += 65535) {
+      const dim3 grid((unsigned)((nb + tb - 1) / tb), (unsigned)std::min<int64_t>(65535, i1 - c0));
+      k_phasor_fx<true><<<grid, tb, 0, s>>>(v, x, (int)c0);
+    }
+  } else if (fixed) {
+    k_phasor_fx<false><<<(unsigned)blocks, tb, 0, s>>>(v, x, 0);
+  } else {
+    k_phasor<<<(unsigned)blocks, tb, 0, s>>>(v, x);
+  }
   PF_CUDA_TRY(cudaGetLastError());
   return PF_OK;
 }
