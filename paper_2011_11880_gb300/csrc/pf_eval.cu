@@ -828,17 +828,24 @@ __device__ __forceinline__ void finish_bus(const View &v, const EvalArgs &a, con
                        hat.x, hat.y, bm, bm2, inj);
 }
 
-// n values from shared memory (src) to global memory (dst) by the 32 lanes of
-// a warp, two values per store; src and dst lie at the same offset modulo 16
-// bytes.
-__device__ __forceinline__ void copy_out(double *dst, const double *src, int32_t n, int lane) {
+// n values from shared memory (src) to global memory (dst) by one thread: the
+// 16-byte aligned middle as one bulk copy of the tensor memory accelerator
+// (cp.async.bulk, asynchronous: the caller commits the group and waits for its
+// reads of shared memory before the buffer is written again), a value at
+// either end outside it by a plain store; src and dst lie at the same offset
+// modulo 16 bytes.  The warp's writes to src must be made visible to the
+// async proxy first (fence.proxy.async.shared::cta and a warp barrier).
+__device__ __forceinline__ void bulk_out(double *dst, const double *src, int32_t n) {
   if (n <= 0) return;
   const int32_t i0 = (int32_t)((reinterpret_cast<uintptr_t>(dst) >> 3) & 1);
-  if (i0 && lane == 0) dst[0] = src[0];
+  if (i0) dst[0] = src[0];
   const int32_t n2 = (n - i0) >> 1;
-  for (int32_t j = lane; j < n2; j += 32)
-    *reinterpret_cast<double2 *>(dst + i0 + 2 * j) = *reinterpret_cast<const double2 *>(src + i0 + 2 * j);
-  if (((n - i0) & 1) && lane == 0) dst[n - 1] = src[n - 1];
+  if (n2 > 0) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(src + i0);
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                 ::"l"(dst + i0), "r"(sa), "r"(16 * n2));
+  }
+  if ((n - i0) & 1) dst[n - 1] = src[n - 1];
 }
 
 // Shared memory of a k_tile warp (byte offsets, 16-byte aligned): E_o limbs
@@ -882,8 +889,10 @@ struct TileMinCtas {
 //            order does not matter) and finishes the bus (finish_bus: the FP64
 //            form where the fixed-point one does not hold, F rows, diagonal
 //            values);
-//   phase 3: the warp writes the staged rows of J and F out whole, two values
-//            per store, every store of the warp to consecutive addresses.
+//   phase 3: the staged rows of J leave whole, each by one bulk copy of the
+//            tensor memory accelerator (lane 0 issues it and waits for it
+//            to have read the staging before the next unit), F's rows by
+//            the lanes.
 // With a persistent grid (DYN) the warps claim their units from a counter;
 // the last CTA resets it.  With PHX the warp first forms the records of its
 // tile's buses and of their external neighbours itself (from x, into shared
@@ -1062,15 +1071,22 @@ __global__ void __launch_bounds__(32, (TileMinCtas<ITEMS, WF, WJ, MASKED, DYN, P
                                  w, wk, sT);
     }
     __syncwarp();
-    // phase 3
+    // phase 3: the staged rows of J leave by bulk copies issued by lane 0, the
+    // F rows by the lanes
     if (WJ) {
-      copy_out(vi + ts.x, s_j + padP, ts.y, lane);
-      copy_out(vi + ts.z, s_j + offQ + padQ, ts.w, lane);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        bulk_out(vi + ts.x, s_j + padP, ts.y);
+        bulk_out(vi + ts.z, s_j + offQ + padQ, ts.w);
+        asm volatile("cp.async.bulk.commit_group;");
+      }
     }
     if (WF) {
       if (lane < tf.y) Fi[tf.x + lane] = s_f[lane];
       if (lane < tf.w) Fi[tf.z + lane] = s_f[32 + lane];
     }
+    if (WJ && lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     __syncwarp();                                // the next unit reuses the staging
   }
   // Every CTA leaves the loop once, after a claim past the last unit; the last
