@@ -611,6 +611,12 @@ def main():
         for name, fn in (("extended_70k", measure_extended), ("contingency", measure_contingency),
                          ("adjoint_70k_64cot", measure_adjoint), ("mixed", measure_mixed)):
             line["extra"][name] = compact_line(fn(torch, stream, KX, 3))
+        # Newton power flow at the paper's four grid sizes (outside the hot path; host-timed)
+        nt = measure_newton(argparse.Namespace(steps=1, cpu_seconds=0.0))
+        line["extra"]["newton"] = {"metric": nt["metric"], "value": nt["value"], "unit": nt["unit"],
+                                   "runs": [{k: r[k] for k in ("n_bus", "case", "method", "solver", "seconds",
+                                                               "iterations", "converged", "max_mismatch")}
+                                            for r in nt["runs"]]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if distributed:
@@ -875,21 +881,51 @@ def measure_extended(torch, stream, K, W, cpu_seconds=0.0):
 
 
 
+def _finite(info):
+    """A solver's info with non-finite numbers (a diverged run's mismatch) as null."""
+    return {k: (None if isinstance(v, float) and not math.isfinite(v) else v) for k, v in info.items()}
+
+
+def constructed_case(n_bus, seed):
+    """A synthetic grid with a known power-flow solution: the point drawn by
+    gridgen.target_state, and per-bus injections equal to the network's own
+    flows there, evaluated by this library (the extended formulation's g_p,
+    g_q rows at zero injections, Q_g = P_s = 0)."""
+    import torch
+    from paper_2011_11880_gb300 import Context
+    g = gridgen.grid_70k() if n_bus == 70000 else gridgen.synthetic_grid(n_bus, seed)
+    th, V = gridgen.target_state(g, seed + 1)
+    n = g.n_bus
+    z = np.zeros(n)
+    g0 = gridgen.with_injections(g, z, z, V)
+    ctx = Context(g0, "extended")
+    x = np.zeros(gridgen.state_size(g0, True))
+    x[:n], x[n:2 * n] = th, V
+    F = ctx.residual(torch.from_numpy(x).cuda()).cpu().numpy()
+    ctx.close()
+    return gridgen.with_injections(g, F[:n], F[n:2 * n], V)
+
+
 def measure_newton(args):
     """Flat-start Newton power flow and fast decoupled iterations (F, J, the
     convergence test and the update in this library's kernels; the sparse
-    solve in cuSOLVER), timed on the host around each solve."""
+    solve in cuSOLVER), timed on the host around each solve, on grids of the
+    four sizes of the paper's Newton comparison (2,000 to 70,000 buses)."""
     import torch
     import oracle
     from paper_2011_11880_gb300 import Context
-    # flat-start Newton power flow (F, J, convergence test and update in this library's
-    # kernels; the sparse solve in cuSOLVER).  The synthetic grids have a flat-start Newton
-    # solution only at light load at these sizes (a CPU sparse Newton agrees), so the loads are
-    # scaled down: 2,000 buses x 0.2, 10,000 buses x 0.1.
+    # The ring-of-meshes grids have a flat-start Newton solution from their drawn loads only at
+    # light load (2,000 buses x 0.2, 10,000 x 0.1; a CPU sparse Newton agrees), and none at
+    # 25,000 or 70,000 buses: the losses the single slack must cover travel the whole ring.
+    # Those two sizes use a constructed case (constructed_case) whose solution is known.
+    cases = [(2000, "drawn loads x 0.2", lambda: gridgen.synthetic_grid(2000, 3000, load_scale=0.2), ("lu", "qr")),
+             (10000, "drawn loads x 0.1", lambda: gridgen.synthetic_grid(10000, 3001, load_scale=0.1), ("lu", "qr")),
+             (25000, "constructed", lambda: constructed_case(25000, 2500), ("lu",)),
+             (70000, "constructed", lambda: constructed_case(70000, 2500), ("lu",))]
     runs = []
-    for n_bus, seed, load in ((2000, 3000, 0.2), (10000, 3001, 0.1)):
-        sk = gridgen.synthetic_grid(n_bus, seed, load_scale=load)
-        for solver in ("lu", "qr"):
+    for n_bus, kind, make, solvers in cases:
+        sk = make()
+        for solver in solvers:
             ctx = Context(sk)
             ctx.set_newton_solver(solver)
             x0 = torch.from_numpy(gridgen.flat_state(sk)).cuda()
@@ -905,8 +941,8 @@ def measure_newton(args):
                 t0 = time.perf_counter()
                 info = ctx.newton(x, tol=1e-8, max_iter=15)
                 ts.append(time.perf_counter() - t0)
-            runs.append({"n_bus": n_bus, "load_scale": load, "method": "newton", "solver": solver,
-                         "seconds": float(np.median(ts)), "seconds_first_call": t_first, **info})
+            runs.append({"n_bus": n_bus, "case": kind, "method": "newton", "solver": solver,
+                         "seconds": float(np.median(ts)), "seconds_first_call": t_first, **_finite(info)})
             ctx.check_device()
             ctx.close()
         # fast decoupled iterations (B', B'' factored once, on the first call)
@@ -921,27 +957,29 @@ def measure_newton(args):
             t0 = time.perf_counter()
             info = ctx.fdlf(x, tol=1e-8, max_iter=100)
             ts.append(time.perf_counter() - t0)
-        runs.append({"n_bus": n_bus, "load_scale": load, "method": "fast decoupled", "solver": "lu",
-                     "seconds": float(np.median(ts)), **info})
+        runs.append({"n_bus": n_bus, "case": kind, "method": "fast decoupled", "solver": "lu",
+                     "seconds": float(np.median(ts)), **_finite(info)})
         ctx.check_device()
         ctx.close()
     ctx = None
     clocks = {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled (host-synchronous loop)"],
               "samples": 0}
-    t = [r for r in runs if r["n_bus"] == 10000 and r["method"] == "newton" and r["solver"] == "lu"][0]["seconds"]
+    t = [r for r in runs if r["n_bus"] == 70000 and r["method"] == "newton" and r["solver"] == "lu"][0]["seconds"]
     s2 = gridgen.synthetic_grid(2000, 3000, load_scale=0.2)
     t0, m = time.perf_counter(), 0
-    while time.perf_counter() - t0 < args.cpu_seconds and m < 3:
+    while time.perf_counter() - t0 < args.cpu_seconds and m < 3:   # (0 s: no CPU baseline)
         oracle.newton_dense(s2, gridgen.flat_state(s2), tol=1e-8)
         m += 1
     el = time.perf_counter() - t0
-    return {"metric": "flat-start Newton power flow, seconds per solve (10,000-bus grid)", "value": t,
+    return {"metric": "flat-start Newton power flow, seconds per solve (70,000-bus grid)", "value": t,
                 "unit": "s", "higher_is_better": False, "ms_per_step": 1e3 * t,
-                "config": {"workload": "seeded synthetic 2,000-bus (load x 0.2) and 10,000-bus (load x 0.1) "
-                                       "grids, reduced formulation, flat start, max |F| <= 1e-8",
+                "config": {"workload": "seeded synthetic grids, reduced formulation, flat start, max |F| <= 1e-8: "
+                                       "2,000 buses (drawn loads x 0.2), 10,000 (x 0.1), and 25,000 and the "
+                                       "70,000-bus grid with constructed injections (the network's flows at "
+                                       "theta ~ U[-0.003, 0.003], V ~ 1 + U[-0.005, 0.005])",
                            "solver": "LU refactorization (host LU of the first J, cuSOLVER-Rf on the "
-                                     "device after it; later solves reuse it) and, for comparison, "
-                                     "cuSOLVER sparse QR every iteration"},
+                                     "device after it; later solves reuse it) and, up to 10,000 buses, "
+                                     "cuSOLVER sparse QR every iteration for comparison"},
                 "runs": runs, "clocks": clocks, "gpu_launches": 0,
                 "cpu_baseline": {"value": el / max(m, 1), "unit": "s", "cores": 1, "kind": "oracle", "host": host_cpu(),
                                  "sample": f"{m} dense-Newton solves of the 2,000-bus grid in {el:.1f} s "

@@ -33,6 +33,8 @@ __all__ = [
     "grid_70k",
     "flat_state",
     "perturbed_state",
+    "target_state",
+    "with_injections",
     "state_size",
     "gaussian_cotangents",
     "contingency_batch",
@@ -330,6 +332,52 @@ def perturbed_state(sys: PowerSystem, seed: int, extended: bool = False,
     if extended:
         x[2 * n:] = rng.uniform(-1.0, 1.0, x.shape[0] - 2 * n)
     return x
+
+
+def target_state(sys: PowerSystem, seed: int, theta_max: float = 0.003,
+                 dv: float = 0.005) -> tuple[np.ndarray, np.ndarray]:
+    """An operating point (theta, V) to build a solvable case around:
+    theta ~ U[-theta_max, theta_max] (the slack at its set angle), V ~ 1 + U[-dv, dv].
+
+    A case whose injections are the network's own flows at this point (see
+    ``with_injections``) has it as a power-flow solution; the small spread
+    keeps the flows, and the losses the slack must cover, small enough for
+    flat-start Newton to reach it on the long ring of the 70k-bus grid."""
+    rng = np.random.default_rng(seed)
+    theta = rng.uniform(-theta_max, theta_max, sys.n_bus)
+    theta[sys.slack_bus] = sys.slack_theta
+    V = 1.0 + rng.uniform(-dv, dv, sys.n_bus)
+    return theta, V
+
+
+def with_injections(sys: PowerSystem, p_inj: np.ndarray, q_inj: np.ndarray,
+                    v_set: np.ndarray) -> PowerSystem:
+    """A copy of ``sys`` whose per-bus net injections are ``p_inj``, ``q_inj``
+    (P_g - P_L, Q_g - Q_L) and whose PV units and slack hold the voltages
+    ``v_set`` of their buses.
+
+    Network unchanged; every PV unit produces the bus's p_inj; every other bus
+    (the slack included) carries one load of -p_inj, -q_inj.  A PV bus's Q
+    injection becomes 0 (its Q is a free variable of the power flow)."""
+    n = sys.n_bus
+    p_inj = np.asarray(p_inj, np.float64)
+    q_inj = np.asarray(q_inj, np.float64)
+    v_set = np.asarray(v_set, np.float64)
+    if p_inj.shape != (n,) or q_inj.shape != (n,) or v_set.shape != (n,):
+        raise ValueError("p_inj, q_inj and v_set need one value per bus")
+    if np.unique(sys.pv_bus).shape[0] != sys.n_pv:
+        raise ValueError("with_injections needs at most one PV unit per bus")
+    out = sys.copy()
+    is_pv = np.zeros(n, bool)
+    is_pv[sys.pv_bus] = True
+    load_bus = np.flatnonzero(~is_pv).astype(np.int32)
+    out.load_bus = load_bus
+    out.load_p = -p_inj[load_bus]
+    out.load_q = -q_inj[load_bus]
+    out.pv_p = p_inj[sys.pv_bus].copy()
+    out.pv_vset = v_set[sys.pv_bus].copy()
+    out.slack_vset = float(v_set[sys.slack_bus])
+    return out
 
 
 def gaussian_cotangents(n_rows: int, n_cot: int, seed: int = 4000) -> np.ndarray:

@@ -55,3 +55,36 @@ def test_pv_total_and_z_scale():
     h = gridgen.synthetic_grid(2000, 5)
     assert np.allclose(g.br_r, 0.25 * h.br_r, rtol=1e-15) and np.allclose(g.br_x, 0.25 * h.br_x, rtol=1e-15)
     assert np.array_equal(g.br_from, h.br_from) and np.array_equal(g.br_b, h.br_b)
+
+
+def test_with_injections_sets_the_net_injections():
+    import oracle
+    g = gridgen.synthetic_grid(1500, 21)
+    rng = np.random.default_rng(5)
+    p, q, v = rng.normal(size=g.n_bus), rng.normal(size=g.n_bus), 1 + 0.01 * rng.normal(size=g.n_bus)
+    h = gridgen.with_injections(g, p, q, v)
+    p1, q1 = oracle.net_injections(h)
+    is_pv = np.zeros(g.n_bus, bool)
+    is_pv[g.pv_bus] = True
+    assert np.array_equal(p1, p)
+    assert np.array_equal(q1[~is_pv], q[~is_pv]) and not np.any(q1[is_pv])
+    assert np.array_equal(h.pv_vset, v[g.pv_bus]) and h.slack_vset == v[g.slack_bus]
+    for name in ("br_from", "br_to", "br_r", "br_x", "br_b", "br_tap", "br_shift", "sh_b"):
+        assert np.array_equal(getattr(h, name), getattr(g, name)), name
+
+
+def test_constructed_case_solved_from_flat_start():
+    """A case built around target_state (injections = the network's own flows there) has that
+    point as its solution, and flat-start Newton (the oracle's dense form) reaches it."""
+    import oracle
+    g = gridgen.synthetic_grid(300, 31)
+    th, V = gridgen.target_state(g, 9)
+    assert th[g.slack_bus] == g.slack_theta and np.all(np.abs(V - 1) <= 0.005)
+    z = np.zeros(g.n_bus)
+    fp, fq = oracle.bus_mismatch(g, th, V, p_inj=z, q_inj=z)
+    h = gridgen.with_injections(g, fp, fq, V)
+    xs = np.concatenate([th, V])
+    assert np.max(np.abs(oracle.residual(h, xs))) == 0.0
+    x, hist = oracle.newton_dense(h, gridgen.flat_state(h), tol=1e-10)
+    assert hist[-1] <= 1e-10 and len(hist) <= 8
+    np.testing.assert_allclose(x, xs, rtol=0, atol=1e-9)
