@@ -951,6 +951,30 @@ __global__ void __launch_bounds__(32, (TileMinCtas<ITEMS, WF, WJ, MASKED, DYN, P
     int4 bm = make_int4(-1, -1, -1, -1);
     if (owner) bm = __ldg(v.bus_meta + o);
     OwnV w{make_int2(0, 0), make_int2(0, 0), make_int2(0, 0), 0.0, 1.0, true};
+    // the first pass's pairs (static data: loaded before any wait for the
+    // previous grid)
+    int4 idx[ITEMS], GX[ITEMS];
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+      const int32_t p = 32 * it + lane;
+      idx[it] = make_int4(0, -1, -1, 0);
+      if (p < np) {
+        idx[it] = __ldg(v.pair_idx + fp + p);
+        GX[it] = __ldg(a.pgbx + fp + p);
+      }
+    }
+    // the bus's row data for phase 2, also static: early where the kernel
+    // forms its records (registers to spare), after the pairs otherwise
+    int32_t pr0 = 0, pr1 = 0;
+    int4 bm2 = make_int4(-1, -1, -1, -1);
+    double2 hat = make_double2(0.0, 0.0), inj = make_double2(0.0, 0.0);
+    if (PHX && owner) {
+      pr0 = __ldg(v.pair_ptr + o) - fp;
+      pr1 = __ldg(v.pair_ptr + o + 1) - fp;
+      bm2 = __ldg(v.bus_meta2 + o);
+      hat = __ldg(a.hat + o);
+      if (WF) inj = __ldg(v.bus_inj + o);
+    }
     if (PHX) {
       // the records of the tile's buses and of its external neighbours, records
       // lane, lane + 32, ...: every bus and every value of x first, then the
@@ -991,14 +1015,15 @@ __global__ void __launch_bounds__(32, (TileMinCtas<ITEMS, WF, WJ, MASKED, DYN, P
 
     // (the first pass always runs: it waits for the records and sets up the buses)
     for (int32_t p0 = 0; p0 == 0 || p0 < np; p0 += 32 * ITEMS) {
-      int4 idx[ITEMS], GX[ITEMS];
+      if (p0 > 0) {
 #pragma unroll
-      for (int it = 0; it < ITEMS; ++it) {
-        const int32_t p = p0 + 32 * it + lane;
-        idx[it] = make_int4(0, -1, -1, 0);
-        if (p < np) {
-          idx[it] = __ldg(v.pair_idx + fp + p);
-          GX[it] = __ldg(a.pgbx + fp + p);
+        for (int it = 0; it < ITEMS; ++it) {
+          const int32_t p = p0 + 32 * it + lane;
+          idx[it] = make_int4(0, -1, -1, 0);
+          if (p < np) {
+            idx[it] = __ldg(v.pair_idx + fp + p);
+            GX[it] = __ldg(a.pgbx + fp + p);
+          }
         }
       }
       if (p0 == 0) {
@@ -1050,7 +1075,10 @@ __global__ void __launch_bounds__(32, (TileMinCtas<ITEMS, WF, WJ, MASKED, DYN, P
     __syncwarp();
     // phase 2
     if (owner) {
-      const int32_t pr0 = __ldg(v.pair_ptr + o) - fp, pr1 = __ldg(v.pair_ptr + o + 1) - fp;
+      if (!PHX) {
+        pr0 = __ldg(v.pair_ptr + o) - fp;
+        pr1 = __ldg(v.pair_ptr + o + 1) - fp;
+      }
       Acc128 ax{0ULL, 0LL}, ay{0ULL, 0LL};
       for (int32_t q = pr0; q < pr1; ++q) {
         const longlong2 xy = s_xy[q];
@@ -1059,9 +1087,11 @@ __global__ void __launch_bounds__(32, (TileMinCtas<ITEMS, WF, WJ, MASKED, DYN, P
       }
       const int fl = s_flag[lane];
       const bool fast = w.fast && !(fl & 1);
-      const int4 bm2 = __ldg(v.bus_meta2 + o);
-      const double2 hat = __ldg(a.hat + o);
-      const double2 inj = WF ? __ldg(v.bus_inj + o) : make_double2(0.0, 0.0);
+      if (!PHX) {
+        bm2 = __ldg(v.bus_meta2 + o);
+        hat = __ldg(a.hat + o);
+        if (WF) inj = __ldg(v.bus_inj + o);
+      }
       const int2 bs = s_base[lane];
       const RowSink rs{bs.x >= 0 ? s_j + bs.x : nullptr, bs.y >= 0 ? s_j + bs.y : nullptr};
       const UnitCtx uc{inst, g, ti.z, ti.w, xi, Fi, vi, rec4, outage, st_base, PHX ? s_rec : nullptr, lane};
