@@ -1802,6 +1802,7 @@ int build_context(Ctx &c, const pf_system *grids, int n_grids, const pf_instance
   }
   c.n_gen_inst = c.gen_off[n_inst];
   v.grid1_nx = n_grids == 1 ? c.grid_nx[0] : 0;
+  v.grid1_nbus = n_grids == 1 ? h_grid_nbus[0] : 0;
   c.n_x = c.x_off[n_inst];
   c.n_f = c.f_off[n_inst];
   c.nnz = c.v_off[n_inst];

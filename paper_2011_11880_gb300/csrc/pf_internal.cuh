@@ -112,6 +112,7 @@ struct View {
   int64_t n_lane_units;     // sum over instances of the rounds of 32 buses of its grid
   int64_t n_large_units;    // sum over instances of the buses with more than 32 ends
   int64_t grid1_nx;         // a context of one grid: the length of an instance's x (0 otherwise)
+  int32_t grid1_nbus;       // a context of one grid: its number of buses (0 otherwise)
 
   // per bus
   const int32_t *inc_ptr;   // [n_bus+1] first incidence of each bus
