@@ -232,8 +232,8 @@ def fp64_ops(d, pattern):
     multiply, an add or a conversion each count one).  k_tile forms the pair
     terms in fixed point on the integer pipe; the FP64 pipe converts each
     off-diagonal value of a pair to double (one conversion), and each bus takes
-    V_o from its fixed-point form and the two exact bus sums to double (3),
-    V_o^2, V_o^2 A^ - S_X, V_o^2 C^ + S_Y and the two F rows (5), plus two
+    the two exact bus sums to double (2; V_o is converted exactly on the integer
+    pipe), V_o^2, V_o^2 A^ - S_X, V_o^2 C^ + S_Y and the two F rows (5), plus two
     FMAs and two multiplies for the diagonal V values where the bus has a V
     column (4).  k_phasor_fx forms 1/V_o (3 FMAs after the hardware's
     reciprocal estimate) for every bus.  Returns (k_tile, k_phasor_fx)."""
@@ -247,7 +247,7 @@ def fp64_ops(d, pattern):
         n_gen = d.n_x - 2 * n - 1
         n_diag = 4 * n + 1 + n_gen + 2 * n_gen + 1   # P_s, Q_g columns, g_V rows, g_theta
         n_vbus = n
-    return (nnz - n_diag) + 8 * n + 4 * n_vbus, 3 * n
+    return (nnz - n_diag) + 7 * n + 4 * n_vbus, 3 * n
 
 
 def _oracle_share(kind, idx, seconds, barrier, queue):

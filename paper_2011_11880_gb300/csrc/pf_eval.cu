@@ -375,6 +375,16 @@ __device__ __forceinline__ double fix_to_double(long long z, int s) {
   return __longlong_as_double(z == 0 ? 0LL : (long long)(sign | mag));
 }
 
+// z 2^-s as a double on the integer pipe, for z > 0 with at most 53
+// significant bits (so the value is exact: no rounding step), such as V 2^60
+// formed from the double V; other z give meaningless bits.
+__device__ __forceinline__ double exact_fix_to_double(long long z, int s) {
+  const int lz = __clzll(z);
+  const unsigned long long n = (unsigned long long)z << (lz & 63);                  // top bit 63
+  return __longlong_as_double(
+      (long long)(((unsigned long long)(1086 - s - lz) << 52) + ((n >> 11) & 0xfffffffffffffULL)));
+}
+
 // Exact sums on the integer pipe: a 128-bit two's-complement accumulator of
 // fixed-point terms.  The sum does not depend on the order of the terms, so
 // every schedule and tuning gives the same bits; it is rounded to a double
@@ -747,7 +757,8 @@ __device__ __forceinline__ OwnV own_voltage(const Rec &ro) {
   OwnV w;
   const int2 vl = make_int2(ro.w.x, ro.w.y);
   w.rvo = __hiloint2double(ro.w.w, ro.w.z);
-  w.vo = fix_to_double_cvt(((long long)ro.w.x << 30) + ro.w.y, 60);   // exact for 2^-8 <= V < 2
+  // exact for 2^-8 <= V < 2 (the only V used, `fast`), on the integer pipe
+  w.vo = exact_fix_to_double(((long long)ro.w.x << 30) + ro.w.y, 60);
   w.fast = ro.w.x >= (1 << 28);
   w.eo = limbs(mul60(vl, make_int2(ro.u.x, ro.u.y)));
   const long long f = mul60(vl, make_int2(ro.u.z, ro.u.w));
