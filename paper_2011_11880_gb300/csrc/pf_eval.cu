@@ -624,8 +624,9 @@ __device__ __forceinline__ void finalize_bus(const View &v, const EvalArgs &a, i
                                              double vo, double rvo, double sx, double sy, double ah, double ch,
                                              int4 bm, int4 bm2, double2 inj) {
   const int64_t lb = o - gb0;
-  const int32_t gi = bm2.w;
-  const bool is_slack = (v.formulation == PF_EXTENDED) && (lb == v.grid_slack[g]);
+  // the extended formulation's rows behind one branch on a launch-wide value,
+  // so that the reduced formulation's buses jump over them
+  const bool ext = v.formulation == PF_EXTENDED;
   const double v2 = __dmul_rn(vo, vo);
   const double tp = __fma_rn(v2, ah, -sx);          // V_o^2 A^ - S_X
   const double tq = __fma_rn(v2, ch, sy);           // V_o^2 C^ + S_Y
@@ -634,16 +635,19 @@ __device__ __forceinline__ void finalize_bus(const View &v, const EvalArgs &a, i
     const double qin = a.q_inj ? a.q_inj[v.inst_bus_off[inst] + lb] : inj.y;
     double fp = __dsub_rn(tp, pin);
     double fq = __dadd_rn(-tq, -qin);
-    if (is_slack) {
-      fp = __dsub_rn(fp, xi[2 * nb + v.grid_ngen[g]]);
-      Fi[v.grid_row_gth[g]] = __dsub_rn(xi[lb], v.grid_theta_set[g]);
-    }
-    if (gi >= 0) {
-      const double qg = xi[2 * nb + gi];
-      fq = __dsub_rn(fq, qg);
-      const int64_t gq = v.inst_gen_off[inst] + gi;
-      Fi[2 * nb + gi] = (a.gen_mode && a.gen_mode[gq]) ? __dsub_rn(qg, a.gen_qlim[gq])       // held at a limit
-                                                       : __dsub_rn(vo, v.gen_vset[v.grid_gen_off[g] + gi]);
+    if (ext) {
+      const int32_t gi = bm2.w;
+      if (lb == v.grid_slack[g]) {
+        fp = __dsub_rn(fp, xi[2 * nb + v.grid_ngen[g]]);
+        Fi[v.grid_row_gth[g]] = __dsub_rn(xi[lb], v.grid_theta_set[g]);
+      }
+      if (gi >= 0) {
+        const double qg = xi[2 * nb + gi];
+        fq = __dsub_rn(fq, qg);
+        const int64_t gq = v.inst_gen_off[inst] + gi;
+        Fi[2 * nb + gi] = (a.gen_mode && a.gen_mode[gq]) ? __dsub_rn(qg, a.gen_qlim[gq])       // held at a limit
+                                                         : __dsub_rn(vo, v.gen_vset[v.grid_gen_off[g] + gi]);
+      }
     }
     if (fpr) *fpr = fp;
     if (fqr) *fqr = fq;
@@ -657,16 +661,19 @@ __device__ __forceinline__ void finalize_bus(const View &v, const EvalArgs &a, i
       rs.p(bm2.y, __dmul_rn(__fma_rn(v2, ah, tp), rvo));  // dF_P / dV_o
       rs.q(bm2.y, __dmul_rn(__fma_rn(v2, ch, tq), -rvo)); // dF_Q / dV_o
     }
-    if (is_slack) {
-      rs.p(bm2.z, -1.0);                    // d g_p / d P_s
-      vi[v.grid_pos_gth[g]] = 1.0;         // d g_theta / d theta_s
-    }
-    if (gi >= 0) {
-      rs.q(bm2.z, -1.0);                    // d g_q / d Q_g
-      const bool held = a.gen_mode && a.gen_mode[v.inst_gen_off[inst] + gi];
-      const int32_t p = v.gen_pos[v.grid_gen_off[g] + gi];
-      vi[p] = held ? 0.0 : 1.0;             // d g_V / d V
-      vi[p + 1] = held ? 1.0 : 0.0;         // d g_V / d Q_g
+    if (ext) {
+      const int32_t gi = bm2.w;
+      if (lb == v.grid_slack[g]) {
+        rs.p(bm2.z, -1.0);                    // d g_p / d P_s
+        vi[v.grid_pos_gth[g]] = 1.0;         // d g_theta / d theta_s
+      }
+      if (gi >= 0) {
+        rs.q(bm2.z, -1.0);                    // d g_q / d Q_g
+        const bool held = a.gen_mode && a.gen_mode[v.inst_gen_off[inst] + gi];
+        const int32_t p = v.gen_pos[v.grid_gen_off[g] + gi];
+        vi[p] = held ? 0.0 : 1.0;             // d g_V / d V
+        vi[p + 1] = held ? 1.0 : 0.0;         // d g_V / d Q_g
+      }
     }
   }
 }
