@@ -24,10 +24,10 @@
 // pipe instead (see "Fixed-point arithmetic of the pair terms" below): the
 // unit phasors (cos t, sin t), V and the merged coefficients (G, B) of a pair
 // of connected buses (parallel branches merged) as 30-bit limbs, products from
-// 32 x 32 -> 64-bit multiplies, the bus sums S_X, S_Y exact in 128 bits; each
+// 32 x 32 -> 64-bit multiplies, the bus sums S_X, S_Y exact in 96 bits; each
 // J value and each sum is rounded once to double, to nearest even, by the
-// FP64 pipe's conversion (a sum beyond 64 bits by the integer routine
-// acc_value, ties away from zero).  The per-bus rows (F, the diagonal
+// FP64 pipe's conversion (a bus whose sum does not fit in 64 bits takes the
+// FP64 form below).  The per-bus rows (F, the diagonal
 // values) stay in FP64: 8 operations per bus.  A bus whose inputs fall outside
 // the fixed-point ranges is evaluated in FP64 from x (the form above).
 //
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(256, 8) k_phasor_fx2(View v, const double *__r
 // 2^(59 - c) with |G|, |B| < 2^c, T and X, Y at 2^(59 - c); every partial
 // sum stays below 2^63.  With the 2^-57 error of the phasor routine the
 // absolute error of T is below 2^(c - 55) (about 3e-17 max(|G|, |B|)), of X,
-// Y below 2^(c - 54); X and Y are summed exactly in 128 bits and every value is
+// Y below 2^(c - 54); X and Y are summed exactly in 96 bits and every value is
 // rounded once to double (to nearest).
 // ---------------------------------------------------------------------------
 
@@ -385,44 +385,32 @@ __device__ __forceinline__ double exact_fix_to_double(long long z, int s) {
       (long long)(((unsigned long long)(1086 - s - lz) << 52) + ((n >> 11) & 0xfffffffffffffULL)));
 }
 
-// Exact sums on the integer pipe: a 128-bit two's-complement accumulator of
-// fixed-point terms.  The sum does not depend on the order of the terms, so
-// every schedule and tuning gives the same bits; it is rounded to a double
-// once (to nearest: even within 64 bits, else ties away from zero).
-struct Acc128 {
-  unsigned long long lo;
-  long long hi;
+// Exact sums on the integer pipe: a 96-bit two's-complement accumulator of
+// fixed-point terms (|term| < 2^63; 2^31 terms cannot overflow it).  The sum
+// does not depend on the order of the terms, so every schedule and tuning
+// gives the same bits.  An add is one carry chain of three 32-bit adds.
+struct Acc96 {
+  unsigned l0, l1;
+  int h;
 };
 
 // Adds a signed 64-bit term.
-__device__ __forceinline__ void acc_add64(Acc128 &a, long long x) {
-  const unsigned long long nlo = a.lo + (unsigned long long)x;
-  a.hi = (long long)((unsigned long long)a.hi + (unsigned long long)(x >> 63) + (nlo < a.lo ? 1ULL : 0ULL));
-  a.lo = nlo;
+__device__ __forceinline__ void acc_add64(Acc96 &a, long long x) {
+  const unsigned x0 = (unsigned)x, x1 = (unsigned)((unsigned long long)x >> 32);
+  const int sx = (int)x1 >> 31;
+  asm("add.cc.u32 %0, %0, %3;\n\taddc.cc.u32 %1, %1, %4;\n\taddc.s32 %2, %2, %5;"
+      : "+r"(a.l0), "+r"(a.l1), "+r"(a.h)
+      : "r"(x0), "r"(x1), "r"(sx));
 }
 
-// The accumulator's value 2^-s as a double.
-__device__ __forceinline__ double fix_to_double_cvt(long long z, int s);
-__device__ __forceinline__ double acc_value(const Acc128 &a, int s) {
-  // a sum within 64 bits (the usual case): the hardware conversion, rounded
-  // to nearest even
-  if (a.hi == ((long long)a.lo >> 63)) return fix_to_double_cvt((long long)a.lo, s);
-  unsigned long long hi = (unsigned long long)a.hi, lo = a.lo;
-  const unsigned long long sign = hi & 0x8000000000000000ULL;
-  if (sign) {                                  // magnitude
-    lo = 0ULL - lo;
-    hi = ~hi + (lo == 0ULL ? 1ULL : 0ULL);
-  }
-  if ((hi | lo) == 0ULL) return 0.0;
-  // normalise the 128-bit magnitude so that its top bit is bit 63 of n
-  const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
-  const int sh = lz & 63;
-  // (bits below n's 11 lowest are dropped: the rounding uses bit 10 of n)
-  const unsigned long long n = lz < 64 ? (sh ? (hi << sh) | (lo >> (64 - sh)) : hi) : lo << sh;
-  const int p = 127 - lz;                      // value = 2^(p - s) * (n / 2^63)
-  const unsigned long long mag =
-      ((unsigned long long)(p - s + 1023) << 52) + ((n >> 11) & 0xfffffffffffffULL) + ((n >> 10) & 1ULL);
-  return __longlong_as_double((long long)(sign | mag));
+// Whether the accumulator's value fits in 64 bits (the usual case: it is then
+// rounded to double once by the FP64 pipe's conversion; a bus whose sums do
+// not fit takes the FP64 form, a choice that depends only on the inputs).
+__device__ __forceinline__ bool fits64(const Acc96 &a) { return a.h == ((int)a.l1 >> 31); }
+
+// The low 64 bits (the value, when fits64).
+__device__ __forceinline__ long long low64(const Acc96 &a) {
+  return (long long)(((unsigned long long)a.l1 << 32) | a.l0);
 }
 
 struct EvalArgs {
@@ -631,8 +619,12 @@ __device__ __forceinline__ void finalize_bus(const View &v, const EvalArgs &a, i
   const double tp = __fma_rn(v2, ah, -sx);          // V_o^2 A^ - S_X
   const double tq = __fma_rn(v2, ch, sy);           // V_o^2 C^ + S_Y
   if (WF) {
-    const double pin = a.p_inj ? a.p_inj[v.inst_bus_off[inst] + lb] : inj.x;
-    const double qin = a.q_inj ? a.q_inj[v.inst_bus_off[inst] + lb] : inj.y;
+    double pin = inj.x, qin = inj.y;
+    if (a.p_inj || a.q_inj) {                      // per-call injections (a launch-wide choice)
+      const int64_t q = v.inst_bus_off[inst] + lb;
+      if (a.p_inj) pin = a.p_inj[q];
+      if (a.q_inj) qin = a.q_inj[q];
+    }
     double fp = __dsub_rn(tp, pin);
     double fq = __dadd_rn(-tq, -qin);
     if (ext) {
@@ -823,12 +815,12 @@ struct UnitCtx {
 template <bool WF, bool WJ, bool MASKED>
 __device__ __forceinline__ void finish_bus(const View &v, const EvalArgs &a, const UnitCtx &uc, int32_t o,
                                            int4 bm, int4 bm2, double2 hat, double2 inj, const RowSink &rs,
-                                           double *fpr, double *fqr, bool fast, bool any_out, const Acc128 &ax,
-                                           const Acc128 &ay, const OwnV &w, const Walk &wk, int sT) {
+                                           double *fpr, double *fqr, bool fast, bool any_out, const Acc96 &ax,
+                                           const Acc96 &ay, const OwnV &w, const Walk &wk, int sT) {
   double sx, sy, vo, rvo;
   if (fast) {
-    sx = acc_value(ax, sT);
-    sy = neg(acc_value(ay, sT));
+    sx = fix_to_double_cvt(low64(ax), sT);   // (fast: both sums fit in 64 bits)
+    sy = neg(fix_to_double_cvt(low64(ay), sT));
     vo = w.vo;
     rvo = w.rvo;                                 // V_o in [1/4, 2): from k_phasor_fx
   } else {
@@ -928,7 +920,7 @@ struct TileMinCtas {
 //            neighbours), ITEMS of them with their records in flight at once:
 //            the pair's fixed-point terms, its four J values into the staged
 //            rows and X, -Y into shared memory;
-//   phase 2: lane l sums its bus's X, -Y exactly (128-bit integers, so the
+//   phase 2: lane l sums its bus's X, -Y exactly (96-bit integers, so the
 //            order does not matter) and finishes the bus (finish_bus: the FP64
 //            form where the fixed-point one does not hold, F rows, diagonal
 //            values);
@@ -1122,14 +1114,14 @@ __global__ void __launch_bounds__(32, (TileMinCtas<ITEMS, WF, WJ, MASKED, DYN, P
         pr0 = __ldg(v.pair_ptr + o) - fp;
         pr1 = __ldg(v.pair_ptr + o + 1) - fp;
       }
-      Acc128 ax{0ULL, 0LL}, ay{0ULL, 0LL};
+      Acc96 ax{0u, 0u, 0}, ay{0u, 0u, 0};
       for (int32_t q = pr0; q < pr1; ++q) {
         const longlong2 xy = s_xy[q];
         acc_add64(ax, xy.x);
         acc_add64(ay, xy.y);
       }
       const int fl = s_flag[lane];
-      const bool fast = w.fast && !(fl & 1);
+      const bool fast = w.fast && !(fl & 1) && fits64(ax) && fits64(ay);
       if (!PHX) {
         bm2 = __ldg(v.bus_meta2 + o);
         hat = __ldg(a.hat + o);

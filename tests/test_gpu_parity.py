@@ -430,3 +430,24 @@ def test_autotune_cache(P, tmp_path):
     assert c5.autotune(x, F5, V5, cache=str(path))["from_cache"] is True
     for c in (c1, c2, c3, c4, c5):
         c.check_device()
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_wide_bus_sums_match_oracle(P, mode):
+    """A hub with 16 branches of |y| ~ 1000 at V = 1.99 and equal angles: its exact bus sums
+    exceed 64 bits at the kernel's fixed-point scale (16 terms of about 2^61), so the hub takes
+    the FP64 form; F and J match the oracle, and every tuning gives the same bits."""
+    from gridgen import PowerSystem
+    n = 18
+    br = [(0, k, 1e-5, 1e-3) for k in range(1, 17)] + [(16, 17, 0.01, 0.1)]
+    sys = PowerSystem.build(n, br, loads=[(0, 0.5, 0.1)], pvs=[(5, 0.2, 1.99)], slack=(17, 1.99, 0.0))
+    x = np.zeros(gridgen.state_size(sys, mode == EXTENDED))
+    x[n:2 * n] = 1.99
+    ctx, F, v = gpu_eval(P, sys, x, mode)
+    # the hub's dF_P/dtheta_o is its sum S_Y itself (the flows cancel in F at equal voltages)
+    assert np.max(np.abs(v)) > 5e4
+    assert_tol(F, oracle.residual(sys, x, mode), "F wide sums")
+    assert_tol(v, oracle.jacobian(sys, x, mode)[2], "J wide sums")
+    for tile in (32, 96):
+        _, F2, v2 = gpu_eval(P, sys, x, mode, (tile, 0, 0, 0))
+        assert np.array_equal(F2, F) and np.array_equal(v2, v)
