@@ -981,6 +981,21 @@ __global__ void __launch_bounds__(32, (TileMinCtas<ITEMS, WF, WJ, MASKED, DYN, P
     const int32_t offQ = (padP + ts.y + 1) & ~1;
     const int32_t padQ = WJ ? (int32_t)((reinterpret_cast<uintptr_t>(vi + ts.z) >> 3) & 1) : 0;
 
+    // Under a mask, only a tile holding an end of its instance's outaged branch
+    // (or any tile, with a per-call status mask) needs the masked coefficients:
+    // a pair's group holds the outaged branch only if its own bus is an end of
+    // it, and the tile's buses' ends are one contiguous range of incidence
+    // positions.  The other tiles take the built coefficients, the same bits.
+    bool um = false;
+    if (MASKED) {
+      if (a.status != nullptr) {
+        um = true;
+      } else if (outage >= 0) {
+        const int32_t e0 = __ldg(v.inc_ptr + td.x), e1 = __ldg(v.inc_ptr + td.x + td.y);
+        um = (oute.x >= e0 && oute.x < e1) || (oute.y >= e0 && oute.y < e1);
+      }
+    }
+
     const bool owner = lane < td.y;
     const int32_t o = td.x + lane;
     int4 bm = make_int4(-1, -1, -1, -1);
@@ -1081,7 +1096,8 @@ __global__ void __launch_bounds__(32, (TileMinCtas<ITEMS, WF, WJ, MASKED, DYN, P
         if (idx[it].z < 0) continue;
         const int32_t len = idx[it].z & 0xffff, ol = (idx[it].z >> 16) & 0xff;
         bool anyo = false;
-        const int4 gx = slot_gbx<MASKED>(v, a, len, idx[it].w, GX[it], outage, st_base, anyo, oute);
+        const int4 gx = (MASKED && um) ? slot_gbx<true>(v, a, len, idx[it].w, GX[it], outage, st_base, anyo, oute)
+                                       : GX[it];
         const int4 e = s_own[2 * ol], e2 = s_own[2 * ol + 1];
         OwnV wo;
         wo.eo = make_int2(e.x, e.y);
